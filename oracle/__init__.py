@@ -1,0 +1,247 @@
+"""CPU oracle for the short-range MD hot path -- TEST INFRASTRUCTURE ONLY.
+
+A plain FP64 C implementation (``oracle.c``) of what the hot path computes,
+written from the paper: brute-force neighbour sets over all periodic images,
+the paper's cell-list Verlet-list algorithm, LJ and tabulated-EAM energies,
+forces and virials, velocity-Verlet NVE integration and the Appendix per-bin
+statistics.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of
+``bench.py`` may import this package; the CUDA product path never does.
+
+Parity pins (what fixes the oracle independently of itself) live in
+``tests/test_oracle_*.py``; every function here is pinned there.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (no FMA contraction) into liboracle.so."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        D = ctypes.c_double
+        I = ctypes.c_int
+        L.ora_neighbors_brute.argtypes = [I64, P, P, P, P, D, P, P, P, I64]
+        L.ora_neighbors_brute.restype = I64
+        L.ora_neighbors_cells.argtypes = [I64, P, P, P, P, D, P, P, P, I64]
+        L.ora_neighbors_cells.restype = I64
+        L.ora_wrap.argtypes = [I64, P, P, P, P]
+        L.ora_wrap.restype = None
+        L.ora_spline_eval_many.argtypes = [P, I, D, I64, P, P, P]
+        L.ora_spline_eval_many.restype = None
+        L.ora_spline_slopes.argtypes = [P, I, D, P]
+        L.ora_spline_slopes.restype = None
+        L.ora_lj.argtypes = [I64, P, P, P, P, D, D, D, I, P, P, P, P, P]
+        L.ora_lj.restype = I
+        L.ora_eam.argtypes = [I64, P, P, P, P, I, D, P, P, I, D, P, P, P, P, P, P, P, P]
+        L.ora_eam.restype = I
+        L.ora_sampled.argtypes = [I, I64, P, P, P, P, P, I, D, P, P, I, D, P, I64, P, P, P]
+        L.ora_sampled.restype = I
+        L.ora_md_run.argtypes = [I64, P, P, P, P, P, P, I, P, I, D, P, P, I, D, P, D, D,
+                                 I64, I, P, D, P, P]
+        L.ora_md_run.restype = I64
+        L.ora_profiles.argtypes = [I64, P, P, P, P, P, I, D, D, I, D, P]
+        L.ora_profiles.restype = None
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _box(lo, hi, periodic):
+    return (_f64(lo, (3,)), _f64(hi, (3,)),
+            np.ascontiguousarray(periodic, dtype=np.int32).reshape(3))
+
+
+# ---------------------------------------------------------------------------
+def neighbors(x, lo, hi, periodic, rns, method="brute"):
+    """Neighbour set: list over atoms of int64 arrays of shape (k, 4) with
+    rows (j, nx, ny, nz), in the order the oracle produces them."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    lo, hi, per = _box(lo, hi, periodic)
+    off = np.zeros(n + 1, dtype=np.int64)
+    fn = lib().ora_neighbors_brute if method == "brute" else lib().ora_neighbors_cells
+    tot = fn(n, _p(x), _p(lo), _p(hi), _p(per), rns, _p(off), None, None, 0)
+    if tot < 0:
+        raise ValueError(f"oracle neighbour search failed ({tot})")
+    j = np.zeros(max(tot, 1), dtype=np.int32)
+    im = np.zeros((max(tot, 1), 3), dtype=np.int32)
+    fn(n, _p(x), _p(lo), _p(hi), _p(per), rns, _p(off), _p(j), _p(im), tot)
+    out = []
+    for i in range(n):
+        a, b = off[i], off[i + 1]
+        out.append(np.concatenate([j[a:b, None].astype(np.int64),
+                                   im[a:b].astype(np.int64)], axis=1))
+    return out
+
+
+def wrap(x, lo, hi, periodic):
+    x = _f64(x, (-1, 3)).copy()
+    lo, hi, per = _box(lo, hi, periodic)
+    lib().ora_wrap(x.shape[0], _p(x), _p(lo), _p(hi), _p(per))
+    return x
+
+
+def spline_eval(y, h, xs):
+    y = _f64(y)
+    xs = _f64(xs)
+    val = np.zeros_like(xs)
+    der = np.zeros_like(xs)
+    lib().ora_spline_eval_many(_p(y), y.shape[0], h, xs.shape[0], _p(xs), _p(val), _p(der))
+    return val, der
+
+
+def spline_slopes(y, h):
+    y = _f64(y)
+    m = np.zeros_like(y)
+    lib().ora_spline_slopes(_p(y), y.shape[0], h, _p(m))
+    return m
+
+
+def lj(x, lo, hi, periodic, eps, sigma, rc, shift_mode=1, per_atom=False):
+    """LJ by brute force: returns dict(E, F, W[6], Ea?, Wa?)."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    lo, hi, per = _box(lo, hi, periodic)
+    E = np.zeros(1)
+    F = np.zeros((n, 3))
+    W = np.zeros(6)
+    Ea = np.zeros(n) if per_atom else None
+    Wa = np.zeros((n, 6)) if per_atom else None
+    rc_ = lib().ora_lj(n, _p(x), _p(lo), _p(hi), _p(per), eps, sigma, rc, shift_mode,
+                       _p(E), _p(F), _p(W), _p(Ea), _p(Wa))
+    if rc_ < 0:
+        raise RuntimeError("oracle lj failed")
+    out = {"E": float(E[0]), "F": F, "W": W}
+    if per_atom:
+        out["Ea"] = Ea
+        out["Wa"] = Wa
+    return out
+
+
+def eam(x, lo, hi, periodic, tables, per_atom=False):
+    """EAM by brute force from knot tables (workloads.EAMTables-like)."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    lo, hi, per = _box(lo, hi, periodic)
+    phi, rho, Ft = _f64(tables.phi), _f64(tables.rho), _f64(tables.F)
+    E = np.zeros(1)
+    F = np.zeros((n, 3))
+    W = np.zeros(6)
+    Ea = np.zeros(n) if per_atom else None
+    Wa = np.zeros((n, 6)) if per_atom else None
+    rho_o = np.zeros(n)
+    fp_o = np.zeros(n)
+    flag = lib().ora_eam(n, _p(x), _p(lo), _p(hi), _p(per), phi.shape[0], tables.rc,
+                         _p(phi), _p(rho), Ft.shape[0], tables.rho_max, _p(Ft),
+                         _p(E), _p(F), _p(W), _p(Ea), _p(Wa), _p(rho_o), _p(fp_o))
+    if flag < 0:
+        raise RuntimeError("oracle eam failed")
+    out = {"E": float(E[0]), "F": F, "W": W, "rho": rho_o, "Fp": fp_o,
+           "rho_flag": bool(flag & 1)}
+    if per_atom:
+        out["Ea"] = Ea
+        out["Wa"] = Wa
+    return out
+
+
+def sampled(kind, x, lo, hi, periodic, sel, lj_params=None, tables=None):
+    """Force (and per-atom energy) of the atoms in `sel`, by brute force."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    lo, hi, per = _box(lo, hi, periodic)
+    sel = np.ascontiguousarray(sel, dtype=np.int64)
+    Fs = np.zeros((sel.shape[0], 3))
+    Es = np.zeros(sel.shape[0])
+    if kind == "lj":
+        par = _f64([lj_params.eps, lj_params.sigma, lj_params.rc, lj_params.shift_mode])
+        flag = lib().ora_sampled(0, n, _p(x), _p(lo), _p(hi), _p(per), _p(par), 0, 0.0,
+                                 None, None, 0, 0.0, None, sel.shape[0], _p(sel),
+                                 _p(Fs), _p(Es))
+    else:
+        phi, rho, Ft = _f64(tables.phi), _f64(tables.rho), _f64(tables.F)
+        flag = lib().ora_sampled(1, n, _p(x), _p(lo), _p(hi), _p(per), None,
+                                 phi.shape[0], tables.rc, _p(phi), _p(rho), Ft.shape[0],
+                                 tables.rho_max, _p(Ft), sel.shape[0], _p(sel),
+                                 _p(Fs), _p(Es))
+    return {"F": Fs, "E": Es, "rho_flag": bool(flag & 1)}
+
+
+def md_run(x, v, masses, lo, hi, periodic, dt, nsteps, skin, lj_params=None,
+           tables=None, rebuild_every=0, piston=None, u_p=0.0):
+    """Velocity-Verlet NVE with Verlet lists (the paper's algorithm).
+
+    Returns dict(x, v, F, thermo (nsteps, 3): K, U, W-trace, n_builds)."""
+    x = _f64(x, (-1, 3)).copy()
+    v = _f64(v, (-1, 3)).copy()
+    n = x.shape[0]
+    m = _f64(masses, (n,))
+    lo, hi, per = _box(lo, hi, periodic)
+    thermo = np.zeros((max(nsteps, 1), 3))
+    F = np.zeros((n, 3))
+    pis = None if piston is None else np.ascontiguousarray(piston, dtype=np.uint8)
+    if lj_params is not None:
+        par = _f64([lj_params.eps, lj_params.sigma, lj_params.rc, lj_params.shift_mode])
+        nb = lib().ora_md_run(n, _p(x), _p(v), _p(m), _p(lo), _p(hi), _p(per), 0, _p(par),
+                              0, 0.0, None, None, 0, 0.0, None, skin, dt, nsteps,
+                              rebuild_every, _p(pis), u_p, _p(thermo), _p(F))
+    else:
+        phi, rho, Ft = _f64(tables.phi), _f64(tables.rho), _f64(tables.F)
+        nb = lib().ora_md_run(n, _p(x), _p(v), _p(m), _p(lo), _p(hi), _p(per), 1, None,
+                              phi.shape[0], tables.rc, _p(phi), _p(rho), Ft.shape[0],
+                              tables.rho_max, _p(Ft), skin, dt, nsteps, rebuild_every,
+                              _p(pis), u_p, _p(thermo), _p(F))
+    if nb < 0:
+        raise RuntimeError(f"oracle md_run failed ({nb})")
+    return {"x": x, "v": v, "F": F, "thermo": thermo[:nsteps], "n_builds": int(nb)}
+
+
+def profiles(x, v, masses, axis, origin, width, nbins, cross_area, Ua=None, Wa=None):
+    x = _f64(x, (-1, 3))
+    v = _f64(v, (-1, 3))
+    n = x.shape[0]
+    m = _f64(masses, (n,))
+    Ua = None if Ua is None else _f64(Ua, (n,))
+    Wa = None if Wa is None else _f64(Wa, (n, 6))
+    out = np.zeros((nbins, 17))
+    lib().ora_profiles(n, _p(x), _p(v), _p(m), _p(Ua), _p(Wa), axis, origin, width,
+                       nbins, cross_area, _p(out))
+    return out
+
+
+if __name__ == "__main__":  # pragma: no cover
+    print(build(force="--force" in sys.argv))

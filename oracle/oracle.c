@@ -1,0 +1,976 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU oracle for the short-range MD hot path
+ * of MDcraft (arXiv 2511.22951).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  The
+ * CUDA product path never links, calls or reads it; it shares no code,
+ * header, table or constant with the CUDA sources.
+ *
+ * Compiled with -O2 -ffp-contract=off so that every floating-point
+ * operation below is rounded exactly as written (no fused multiply-add).
+ *
+ * What is computed (each function cites the passage it follows):
+ *   - Verlet neighbour set within r_ns = rc + skin       (Sec. "Neighbor lists
+ *     construction", Eq. rhrz: r_ns = (1+beta) r_cut; absolute skin reading)
+ *       * brute force over every atom and every periodic image (definition)
+ *       * the paper's algorithm: bucket sort of atoms into a virtual grid of
+ *         cells of size >= R, then a 3x3x3 cell stencil
+ *   - Lennard-Jones energy / force / virial               (Sec. "Potentials
+ *     support": f_i = sum_j V'(r_ij) r_ji / r_ji)
+ *   - EAM energy / force / virial from tabulated functions (Sec. "Comparison of
+ *     aluminum shock Hugoniot ...": single-element EAM read from a table; the
+ *     standard embedded-atom form U = 1/2 sum phi + sum F(rho_i))
+ *   - velocity-Verlet NVE integration                     (Sec. "Molecular
+ *     dynamics", Eq. MD-system: m_i r_i'' = f_i = -grad_i U)
+ *   - per-bin profiles of the Appendix (mass, COM velocity, temperature per
+ *     degree of freedom, pressure tensor with the virial term)
+ *
+ * Readings of the paper that this file fixes (all listed in the design doc):
+ *   * pair vector d_ij = (x_j - x_i) + n*L, rounded in that order;
+ *     r^2 = (dx*dx + dy*dy) + dz*dz; a pair is a neighbour iff r^2 < r_ns^2;
+ *   * the neighbour list is a full list over (j, image n) with (j,n) != (i,0);
+ *   * LJ is cut at rc with an energy shift (shift_mode 1), plain truncation
+ *     (0) or shifted force (2);
+ *   * EAM tables are cubic Hermite splines through the knot values, knot
+ *     slopes from 3-point differences (one-sided 3-point at both ends);
+ *     r >= rc gives 0; rho > rho_max is extrapolated linearly and flagged;
+ *   * positions of periodic dimensions are wrapped into [lo, lo+L) at every
+ *     list rebuild, by whole box lengths.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* 1 eV/(Angstrom u) in Angstrom/fs^2 (e / u / 1e-10 m * 1e-20). */
+static const double ORA_ACC = 9.648533212331e-3;
+
+typedef struct {
+    double lo[3];
+    double L[3];
+    int per[3];
+} ora_box;
+
+static ora_box make_box(const double *lo, const double *hi, const int *per) {
+    ora_box b;
+    for (int d = 0; d < 3; ++d) {
+        b.lo[d] = lo[d];
+        b.L[d] = hi[d] - lo[d];
+        b.per[d] = per[d] ? 1 : 0;
+    }
+    return b;
+}
+
+/* ---------------------------------------------------------------------- */
+/* pair geometry                                                           */
+/* ---------------------------------------------------------------------- */
+
+/* d = (xj - xi) + n*L per component; returns r^2 = (dx^2 + dy^2) + dz^2. */
+static double pair_vec(const double *xi, const double *xj, const int n[3],
+                       const ora_box *b, double d[3]) {
+    for (int k = 0; k < 3; ++k) {
+        double t = xj[k] - xi[k];
+        double s = (double)n[k] * b->L[k];
+        d[k] = t + s;
+    }
+    double r2 = d[0] * d[0];
+    r2 = r2 + d[1] * d[1];
+    r2 = r2 + d[2] * d[2];
+    return r2;
+}
+
+/* Images n of dimension k that can bring |t + n L| below rcut (with a tiny
+ * outward margin so that rounding never hides a candidate). */
+static void image_range(double t, const ora_box *b, int k, double rcut,
+                        int *nlo, int *nhi) {
+    if (!b->per[k]) {
+        *nlo = 0;
+        *nhi = 0;
+        return;
+    }
+    double L = b->L[k];
+    double m = rcut * (1.0 + 1e-9) + 1e-12;
+    *nlo = (int)ceil((-m - t) / L) - 1;
+    *nhi = (int)floor((m - t) / L) + 1;
+}
+
+/* ---------------------------------------------------------------------- */
+/* neighbour set by brute force: the definition                           */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * For every atom i (in input order) append every (j, n) with
+ * r^2 < rns^2 and (j,n) != (i,0); j ascending, then images lexicographic.
+ * offsets[N+1] always written; entries written only while < cap.
+ * Returns the total number of entries.  (Sec. "Neighbor lists construction":
+ * the list holds the atoms within the search radius r_ns.)
+ */
+int64_t ora_neighbors_brute(int64_t N, const double *x, const double *lo,
+                            const double *hi, const int *per, double rns,
+                            int64_t *offsets, int32_t *jout, int32_t *nout,
+                            int64_t cap) {
+    ora_box b = make_box(lo, hi, per);
+    double r2c = rns * rns;
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        offsets[i] = cnt;
+        const double *xi = x + 3 * i;
+        for (int64_t j = 0; j < N; ++j) {
+            const double *xj = x + 3 * j;
+            int lo_[3], hi_[3];
+            for (int k = 0; k < 3; ++k)
+                image_range(xj[k] - xi[k], &b, k, rns, &lo_[k], &hi_[k]);
+            int n[3];
+            for (n[0] = lo_[0]; n[0] <= hi_[0]; ++n[0])
+                for (n[1] = lo_[1]; n[1] <= hi_[1]; ++n[1])
+                    for (n[2] = lo_[2]; n[2] <= hi_[2]; ++n[2]) {
+                        if (j == i && n[0] == 0 && n[1] == 0 && n[2] == 0)
+                            continue;
+                        double d[3];
+                        double r2 = pair_vec(xi, xj, n, &b, d);
+                        if (r2 < r2c) {
+                            if (cnt < cap) {
+                                jout[cnt] = (int32_t)j;
+                                nout[3 * cnt + 0] = n[0];
+                                nout[3 * cnt + 1] = n[1];
+                                nout[3 * cnt + 2] = n[2];
+                            }
+                            ++cnt;
+                        }
+                    }
+        }
+    }
+    offsets[N] = cnt;
+    return cnt;
+}
+
+/* ---------------------------------------------------------------------- */
+/* wrapping and the paper's cell-list algorithm                            */
+/* ---------------------------------------------------------------------- */
+
+/* Wrap periodic coordinates into [lo, lo+L) by whole box lengths. */
+void ora_wrap(int64_t N, double *x, const double *lo, const double *hi,
+              const int *per) {
+    for (int64_t i = 0; i < N; ++i)
+        for (int k = 0; k < 3; ++k) {
+            if (!per[k]) continue;
+            double L = hi[k] - lo[k];
+            double v = x[3 * i + k];
+            while (v >= hi[k]) v = v - L;
+            while (v < lo[k]) v = v + L;
+            if (v >= hi[k]) v = lo[k]; /* only via rounding at the upper edge */
+            x[3 * i + k] = v;
+        }
+}
+
+typedef struct {
+    int nc[3];        /* cells per dimension                            */
+    double glo[3];    /* grid origin                                    */
+    double h[3];      /* cell size                                      */
+    int64_t ncell;
+    int64_t *start;   /* ncell + 1                                      */
+    int64_t *atoms;   /* N, atom indices bucket-sorted by cell          */
+} ora_grid;
+
+/*
+ * Virtual Cartesian grid of cells of size >= R over the domain, and a
+ * one-pass bucket sort of the atoms into it (Sec. "Neighbor lists
+ * construction").  Periodic dimensions: nc = floor(L/R) cells of size L/nc.
+ * Free dimensions: the grid spans the atoms' extent at build time.
+ */
+static int grid_build(ora_grid *g, int64_t N, const double *x, const ora_box *b,
+                      double R) {
+    for (int k = 0; k < 3; ++k) {
+        double glo, ext;
+        if (b->per[k]) {
+            glo = b->lo[k];
+            ext = b->L[k];
+        } else {
+            double mn = INFINITY, mx = -INFINITY;
+            for (int64_t i = 0; i < N; ++i) {
+                double v = x[3 * i + k];
+                if (v < mn) mn = v;
+                if (v > mx) mx = v;
+            }
+            if (N == 0) { mn = 0.0; mx = 0.0; }
+            glo = mn;
+            ext = (mx - mn) + 1e-9;
+        }
+        /* the 1e-10 margin keeps h strictly above R, so that one rounding
+         * of (x - lo)/h cannot separate two atoms closer than R by 2 cells */
+        int nc = (int)floor(ext / (R * (1.0 + 1e-10)));
+        if (nc < 1) nc = 1;
+        g->nc[k] = nc;
+        g->glo[k] = glo;
+        g->h[k] = ext / nc;
+    }
+    g->ncell = (int64_t)g->nc[0] * g->nc[1] * g->nc[2];
+    g->start = (int64_t *)calloc((size_t)g->ncell + 1, sizeof(int64_t));
+    g->atoms = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    int64_t *cell_of = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    if (!g->start || !g->atoms || !cell_of) return -1;
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t c[3];
+        for (int k = 0; k < 3; ++k) {
+            int64_t ck = (int64_t)floor((x[3 * i + k] - g->glo[k]) / g->h[k]);
+            if (ck < 0) ck = 0;
+            if (ck >= g->nc[k]) ck = g->nc[k] - 1;
+            c[k] = ck;
+        }
+        cell_of[i] = c[0] + (int64_t)g->nc[0] * (c[1] + (int64_t)g->nc[1] * c[2]);
+        g->start[cell_of[i] + 1] += 1;
+    }
+    for (int64_t c = 0; c < g->ncell; ++c) g->start[c + 1] += g->start[c];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)g->ncell);
+    if (!fill) return -1;
+    memcpy(fill, g->start, sizeof(int64_t) * (size_t)g->ncell);
+    for (int64_t i = 0; i < N; ++i) g->atoms[fill[cell_of[i]]++] = i;
+    free(fill);
+    free(cell_of);
+    return 0;
+}
+
+static void grid_free(ora_grid *g) {
+    free(g->start);
+    free(g->atoms);
+    g->start = NULL;
+    g->atoms = NULL;
+}
+
+/* Verlet list in CSR form: for atom i, entries [off[i], off[i+1]). */
+typedef struct {
+    int64_t *off;
+    int32_t *j;
+    int32_t *n;   /* 3 per entry */
+    int64_t cap;
+} ora_vlist;
+
+static int vlist_push(ora_vlist *vl, int64_t *cnt, int32_t j, const int n[3]) {
+    if (*cnt >= vl->cap) {
+        int64_t nc = vl->cap ? 2 * vl->cap : 1024;
+        int32_t *nj = (int32_t *)realloc(vl->j, sizeof(int32_t) * (size_t)nc);
+        if (!nj) return -1;
+        vl->j = nj;
+        int32_t *nn = (int32_t *)realloc(vl->n, sizeof(int32_t) * 3 * (size_t)nc);
+        if (!nn) return -1;
+        vl->n = nn;
+        vl->cap = nc;
+    }
+    vl->j[*cnt] = j;
+    vl->n[3 * *cnt + 0] = n[0];
+    vl->n[3 * *cnt + 1] = n[1];
+    vl->n[3 * *cnt + 2] = n[2];
+    ++*cnt;
+    return 0;
+}
+
+/*
+ * The paper's neighbour search: for the cell of atom i, visit the 3x3x3
+ * block of cells around it and keep the atoms within r_ns.  Each stencil
+ * offset s is one distinct periodic image of the visited cell, so grids with
+ * fewer than 3 cells in a periodic dimension still give every (j, image)
+ * exactly once (a stencil position that wraps onto the same cell is another
+ * image of it).  Free dimensions skip stencil cells outside the grid.
+ */
+static int vlist_build(ora_vlist *vl, int64_t N, const double *x,
+                       const ora_box *b, double rns) {
+    ora_grid g;
+    if (grid_build(&g, N, x, b, rns) != 0) return -1;
+    double r2c = rns * rns;
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        vl->off[i] = cnt;
+        const double *xi = x + 3 * i;
+        int ci[3];
+        for (int k = 0; k < 3; ++k) {
+            int64_t ck = (int64_t)floor((xi[k] - g.glo[k]) / g.h[k]);
+            if (ck < 0) ck = 0;
+            if (ck >= g.nc[k]) ck = g.nc[k] - 1;
+            ci[k] = (int)ck;
+        }
+        int s[3];
+        for (s[2] = -1; s[2] <= 1; ++s[2])
+            for (s[1] = -1; s[1] <= 1; ++s[1])
+                for (s[0] = -1; s[0] <= 1; ++s[0]) {
+                    int cj[3], n[3], skip = 0;
+                    for (int k = 0; k < 3; ++k) {
+                        int c = ci[k] + s[k];
+                        if (b->per[k]) {
+                            /* n = floor(c / nc); cell = c - n nc */
+                            int q = (c >= 0) ? c / g.nc[k] : -((-c + g.nc[k] - 1) / g.nc[k]);
+                            n[k] = q;
+                            cj[k] = c - q * g.nc[k];
+                        } else {
+                            if (c < 0 || c >= g.nc[k]) skip = 1;
+                            n[k] = 0;
+                            cj[k] = c;
+                        }
+                    }
+                    if (skip) continue;
+                    int64_t c = cj[0] + (int64_t)g.nc[0] * (cj[1] + (int64_t)g.nc[1] * cj[2]);
+                    /* image n of cell cj seen from ci: positions were wrapped,
+                     * so the image shift in box lengths is the cell wrap count */
+                    for (int64_t q = g.start[c]; q < g.start[c + 1]; ++q) {
+                        int64_t j = g.atoms[q];
+                        if (j == i && n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
+                        double d[3];
+                        double r2 = pair_vec(xi, x + 3 * j, n, b, d);
+                        if (r2 < r2c)
+                            if (vlist_push(vl, &cnt, (int32_t)j, n) != 0) {
+                                grid_free(&g);
+                                return -1;
+                            }
+                    }
+                }
+    }
+    vl->off[N] = cnt;
+    grid_free(&g);
+    return 0;
+}
+
+/*
+ * Cell-list neighbour set (the paper's algorithm) for positions that are
+ * already inside the primary box on periodic dimensions.  Same output
+ * format as ora_neighbors_brute (the order within a list differs).
+ */
+int64_t ora_neighbors_cells(int64_t N, const double *x, const double *lo,
+                            const double *hi, const int *per, double rns,
+                            int64_t *offsets, int32_t *jout, int32_t *nout,
+                            int64_t cap) {
+    ora_box b = make_box(lo, hi, per);
+    for (int k = 0; k < 3; ++k)
+        if (b.per[k] && b.L[k] < rns) return -1;
+    ora_vlist vl;
+    memset(&vl, 0, sizeof(vl));
+    vl.off = offsets;
+    if (vlist_build(&vl, N, x, &b, rns) != 0) return -2;
+    int64_t tot = offsets[N];
+    for (int64_t q = 0; q < tot && q < cap; ++q) {
+        jout[q] = vl.j[q];
+        nout[3 * q + 0] = vl.n[3 * q + 0];
+        nout[3 * q + 1] = vl.n[3 * q + 1];
+        nout[3 * q + 2] = vl.n[3 * q + 2];
+    }
+    free(vl.j);
+    free(vl.n);
+    return tot;
+}
+
+/* ---------------------------------------------------------------------- */
+/* tabulated functions: cubic Hermite spline through knot values           */
+/* ---------------------------------------------------------------------- */
+
+/* Knot slopes dy/dx from 3-point differences; one-sided 3-point at the ends. */
+void ora_spline_slopes(const double *y, int n, double h, double *m) {
+    if (n < 3) {
+        for (int k = 0; k < n; ++k) m[k] = (n == 2) ? (y[1] - y[0]) / h : 0.0;
+        return;
+    }
+    m[0] = (-3.0 * y[0] + 4.0 * y[1] - y[2]) / (2.0 * h);
+    for (int k = 1; k < n - 1; ++k) m[k] = (y[k + 1] - y[k - 1]) / (2.0 * h);
+    m[n - 1] = (3.0 * y[n - 1] - 4.0 * y[n - 2] + y[n - 3]) / (2.0 * h);
+}
+
+/*
+ * Hermite evaluation on the knot grid x_k = k h, k = 0..n-1:
+ *   u = x/h, k = min(floor(u), n-2), t = u - k,
+ *   y = h00 y_k + h10 h m_k + h01 y_{k+1} + h11 h m_{k+1}.
+ * Valid for 0 <= x <= (n-1) h; callers handle the outside.
+ */
+static double spline_eval(const double *y, const double *m, int n, double h,
+                          double x, double *dydx) {
+    double u = x / h;
+    int k = (int)floor(u);
+    if (k > n - 2) k = n - 2;
+    if (k < 0) k = 0;
+    double t = u - (double)k;
+    double t2 = t * t, t3 = t2 * t;
+    double h00 = 2.0 * t3 - 3.0 * t2 + 1.0;
+    double h10 = t3 - 2.0 * t2 + t;
+    double h01 = -2.0 * t3 + 3.0 * t2;
+    double h11 = t3 - t2;
+    double d00 = 6.0 * t2 - 6.0 * t;
+    double d10 = 3.0 * t2 - 4.0 * t + 1.0;
+    double d01 = -6.0 * t2 + 6.0 * t;
+    double d11 = 3.0 * t2 - 2.0 * t;
+    double yk = y[k], yk1 = y[k + 1], mk = h * m[k], mk1 = h * m[k + 1];
+    if (dydx) *dydx = (d00 * yk + d10 * mk + d01 * yk1 + d11 * mk1) / h;
+    return h00 * yk + h10 * mk + h01 * yk1 + h11 * mk1;
+}
+
+/* Exported for the spline pins: evaluate n_x points through ora_spline_slopes. */
+void ora_spline_eval_many(const double *y, int n, double h, int64_t nx,
+                          const double *xs, double *val, double *der) {
+    double *m = (double *)malloc(sizeof(double) * (size_t)n);
+    ora_spline_slopes(y, n, h, m);
+    for (int64_t q = 0; q < nx; ++q) val[q] = spline_eval(y, m, n, h, xs[q], &der[q]);
+    free(m);
+}
+
+/* A radial table on [0, rc]: value and derivative, 0 for r >= rc. */
+typedef struct {
+    const double *y;
+    double *m;
+    int n;
+    double h;
+    double xmax;
+} ora_table;
+
+static void table_init(ora_table *t, const double *y, int n, double xmax) {
+    t->y = y;
+    t->n = n;
+    t->xmax = xmax;
+    t->h = xmax / (double)(n - 1);
+    t->m = (double *)malloc(sizeof(double) * (size_t)n);
+    ora_spline_slopes(y, n, t->h, t->m);
+}
+
+static double radial(const ora_table *t, double r, double *d) {
+    if (r >= t->xmax) {
+        *d = 0.0;
+        return 0.0;
+    }
+    return spline_eval(t->y, t->m, t->n, t->h, r, d);
+}
+
+/* Embedding F(rho): spline on [0, rho_max]; linear extrapolation above. */
+static double embed(const ora_table *t, double rho, double *d, int *flag) {
+    if (rho > t->xmax) {
+        double d0;
+        double f0 = spline_eval(t->y, t->m, t->n, t->h, t->xmax, &d0);
+        *d = d0;
+        if (flag) *flag = 1;
+        return f0 + d0 * (rho - t->xmax);
+    }
+    return spline_eval(t->y, t->m, t->n, t->h, rho, d);
+}
+
+/* ---------------------------------------------------------------------- */
+/* potentials                                                              */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    int kind;              /* 0 = LJ, 1 = EAM */
+    /* LJ */
+    double eps, sigma, rc;
+    int shift_mode;
+    double u_rc, du_rc;
+    /* EAM */
+    ora_table phi, rho, F;
+} ora_pot;
+
+static double lj_u(const ora_pot *p, double r, double *du) {
+    double sr = p->sigma / r;
+    double s2 = sr * sr;
+    double s6 = s2 * s2 * s2;
+    double s12 = s6 * s6;
+    *du = -24.0 * p->eps * (2.0 * s12 - s6) / r;
+    return 4.0 * p->eps * (s12 - s6);
+}
+
+static void pot_lj_init(ora_pot *p, double eps, double sigma, double rc, int mode) {
+    memset(p, 0, sizeof(*p));
+    p->kind = 0;
+    p->eps = eps;
+    p->sigma = sigma;
+    p->rc = rc;
+    p->shift_mode = mode;
+    double du;
+    double u = lj_u(p, rc, &du);
+    p->u_rc = (mode >= 1) ? u : 0.0;
+    p->du_rc = (mode == 2) ? du : 0.0;
+}
+
+/* LJ pair term with its truncation: value and dV/dr for r < rc. */
+static double lj_pair(const ora_pot *p, double r, double *dv) {
+    double du;
+    double u = lj_u(p, r, &du);
+    *dv = du - p->du_rc;
+    return u - p->u_rc - (r - p->rc) * p->du_rc;
+}
+
+static void pot_eam_init(ora_pot *p, int nr, double rc, const double *phi,
+                         const double *rho, int nrho, double rho_max,
+                         const double *F) {
+    memset(p, 0, sizeof(*p));
+    p->kind = 1;
+    p->rc = rc;
+    table_init(&p->phi, phi, nr, rc);
+    table_init(&p->rho, rho, nr, rc);
+    table_init(&p->F, F, nrho, rho_max);
+}
+
+static void pot_free(ora_pot *p) {
+    if (p->kind == 1) {
+        free(p->phi.m);
+        free(p->rho.m);
+        free(p->F.m);
+    }
+}
+
+/*
+ * Energy, forces and virial from an explicit pair list (CSR over atoms,
+ * entries (j, n)).  f_i = sum_j V'(r_ij) d_ij / r_ij with d_ij = r_j - r_i
+ * (Sec. "Potentials support"); virial W^{ab} = 1/2 sum_i sum_j r_ij^a f_ij^b
+ * with r_ij = r_i - r_j and f_ij the force on i from j (Appendix, read with
+ * the pair force).  EAM: rho_i = sum_j rho(r_ij), U = 1/2 sum phi + sum F(rho_i),
+ * f_i = sum_j [phi'(r) + (F'(rho_i) + F'(rho_j)) rho'(r)] d_ij / r.
+ * Per-atom outputs may be NULL.  Returns a bitmask: 1 = rho above the F table.
+ */
+static int forces_from_list(const ora_pot *p, int64_t N, const double *x,
+                            const ora_box *b, const int64_t *off,
+                            const int32_t *jl, const int32_t *nl, double *E,
+                            double *F, double *W, double *Ea, double *Wa,
+                            double *rho_out, double *fp_out) {
+    int flag = 0;
+    double rc2 = p->rc * p->rc;
+    double Etot = 0.0;
+    double Wt[6] = {0, 0, 0, 0, 0, 0};
+    double *fp = NULL;
+    if (p->kind == 1) {
+        fp = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+        /* pass 1: densities, embedding energy and F'(rho_i) */
+        for (int64_t i = 0; i < N; ++i) {
+            double rho_i = 0.0;
+            for (int64_t q = off[i]; q < off[i + 1]; ++q) {
+                double d[3];
+                double r2 = pair_vec(x + 3 * i, x + 3 * (int64_t)jl[q], nl + 3 * q, b, d);
+                if (r2 < rc2) {
+                    double dr;
+                    rho_i += radial(&p->rho, sqrt(r2), &dr);
+                }
+            }
+            int fl = 0;
+            double dF;
+            double Fi = embed(&p->F, rho_i, &dF, &fl);
+            flag |= fl;
+            fp[i] = dF;
+            if (rho_out) rho_out[i] = rho_i;
+            if (fp_out) fp_out[i] = dF;
+            if (Ea) Ea[i] = Fi;
+            Etot += Fi;
+        }
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        double fi[3] = {0, 0, 0};
+        double ei = 0.0;
+        double wi[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t q = off[i]; q < off[i + 1]; ++q) {
+            int64_t j = jl[q];
+            double d[3];
+            double r2 = pair_vec(x + 3 * i, x + 3 * j, nl + 3 * q, b, d);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2);
+            double v, dv;
+            if (p->kind == 0) {
+                v = lj_pair(p, r, &dv);
+            } else {
+                double dphi, drho;
+                v = radial(&p->phi, r, &dphi);
+                radial(&p->rho, r, &drho);
+                dv = dphi + (fp[i] + fp[j]) * drho;
+            }
+            ei += 0.5 * v;
+            double s = dv / r;
+            double f[3] = {s * d[0], s * d[1], s * d[2]};
+            fi[0] += f[0];
+            fi[1] += f[1];
+            fi[2] += f[2];
+            /* r_ij = -d */
+            wi[0] += 0.5 * (-d[0]) * f[0];
+            wi[1] += 0.5 * (-d[1]) * f[1];
+            wi[2] += 0.5 * (-d[2]) * f[2];
+            wi[3] += 0.5 * (-d[0]) * f[1];
+            wi[4] += 0.5 * (-d[0]) * f[2];
+            wi[5] += 0.5 * (-d[1]) * f[2];
+        }
+        if (F) {
+            F[3 * i + 0] = fi[0];
+            F[3 * i + 1] = fi[1];
+            F[3 * i + 2] = fi[2];
+        }
+        if (Ea) Ea[i] = (p->kind == 1 ? Ea[i] : 0.0) + ei;
+        if (Wa)
+            for (int c = 0; c < 6; ++c) Wa[6 * i + c] = wi[c];
+        Etot += ei;
+        for (int c = 0; c < 6; ++c) Wt[c] += wi[c];
+    }
+    if (E) *E = Etot;
+    if (W)
+        for (int c = 0; c < 6; ++c) W[c] = Wt[c];
+    free(fp);
+    return flag;
+}
+
+/* full brute-force list (helper for the all-pairs evaluations) */
+static int brute_list(int64_t N, const double *x, const ora_box *b, double rcut,
+                      ora_vlist *vl) {
+    double r2c = rcut * rcut;
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        vl->off[i] = cnt;
+        for (int64_t j = 0; j < N; ++j) {
+            int lo_[3], hi_[3];
+            for (int k = 0; k < 3; ++k)
+                image_range(x[3 * j + k] - x[3 * i + k], b, k, rcut, &lo_[k], &hi_[k]);
+            int n[3];
+            for (n[0] = lo_[0]; n[0] <= hi_[0]; ++n[0])
+                for (n[1] = lo_[1]; n[1] <= hi_[1]; ++n[1])
+                    for (n[2] = lo_[2]; n[2] <= hi_[2]; ++n[2]) {
+                        if (j == i && n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
+                        double d[3];
+                        if (pair_vec(x + 3 * i, x + 3 * j, n, b, d) < r2c)
+                            if (vlist_push(vl, &cnt, (int32_t)j, n) != 0) return -1;
+                    }
+        }
+    }
+    vl->off[N] = cnt;
+    return 0;
+}
+
+/* LJ by brute force over all pairs and images (the definition). */
+int ora_lj(int64_t N, const double *x, const double *lo, const double *hi,
+           const int *per, double eps, double sigma, double rc, int shift_mode,
+           double *E, double *F, double *W, double *Ea, double *Wa) {
+    ora_box b = make_box(lo, hi, per);
+    ora_pot p;
+    pot_lj_init(&p, eps, sigma, rc, shift_mode);
+    ora_vlist vl;
+    memset(&vl, 0, sizeof(vl));
+    vl.off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N + 1));
+    if (brute_list(N, x, &b, rc, &vl) != 0) return -1;
+    int fl = forces_from_list(&p, N, x, &b, vl.off, vl.j, vl.n, E, F, W, Ea, Wa, NULL, NULL);
+    free(vl.off);
+    free(vl.j);
+    free(vl.n);
+    return fl;
+}
+
+/* EAM by brute force over all pairs and images (the definition). */
+int ora_eam(int64_t N, const double *x, const double *lo, const double *hi,
+            const int *per, int nr, double rc, const double *phi,
+            const double *rho, int nrho, double rho_max, const double *Ftab,
+            double *E, double *F, double *W, double *Ea, double *Wa,
+            double *rho_out, double *fp_out) {
+    ora_box b = make_box(lo, hi, per);
+    ora_pot p;
+    pot_eam_init(&p, nr, rc, phi, rho, nrho, rho_max, Ftab);
+    ora_vlist vl;
+    memset(&vl, 0, sizeof(vl));
+    vl.off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N + 1));
+    if (brute_list(N, x, &b, rc, &vl) != 0) return -1;
+    int fl = forces_from_list(&p, N, x, &b, vl.off, vl.j, vl.n, E, F, W, Ea, Wa,
+                              rho_out, fp_out);
+    free(vl.off);
+    free(vl.j);
+    free(vl.n);
+    pot_free(&p);
+    return fl;
+}
+
+/*
+ * Force and energy of selected atoms only, by brute force over all j and
+ * images (for parity spot checks on systems too large for all pairs).
+ * kind 0 = LJ (params: eps, sigma, rc, shift_mode); kind 1 = EAM.
+ * For EAM, rho of the selected atom and of each of its neighbours is itself
+ * summed over all atoms.
+ */
+int ora_sampled(int kind, int64_t N, const double *x, const double *lo,
+                const double *hi, const int *per, const double *lj_par,
+                int nr, double rc_eam, const double *phi, const double *rho,
+                int nrho, double rho_max, const double *Ftab, int64_t nsel,
+                const int64_t *sel, double *Fsel, double *Esel) {
+    ora_box b = make_box(lo, hi, per);
+    ora_pot p;
+    if (kind == 0)
+        pot_lj_init(&p, lj_par[0], lj_par[1], lj_par[2], (int)lj_par[3]);
+    else
+        pot_eam_init(&p, nr, rc_eam, phi, rho, nrho, rho_max, Ftab);
+    double rc = p.rc, rc2 = rc * rc;
+    int flag = 0;
+    /* collect the (j, n) within rc of one atom */
+    int64_t cap = 4096;
+    int32_t *js = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    int32_t *ns = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)cap);
+    for (int64_t q = 0; q < nsel; ++q) {
+        int64_t i = sel[q];
+        const double *xi = x + 3 * i;
+        int64_t cnt = 0;
+        for (int64_t j = 0; j < N; ++j) {
+            int lo_[3], hi_[3];
+            for (int k = 0; k < 3; ++k)
+                image_range(x[3 * j + k] - xi[k], &b, k, rc, &lo_[k], &hi_[k]);
+            int n[3];
+            for (n[0] = lo_[0]; n[0] <= hi_[0]; ++n[0])
+                for (n[1] = lo_[1]; n[1] <= hi_[1]; ++n[1])
+                    for (n[2] = lo_[2]; n[2] <= hi_[2]; ++n[2]) {
+                        if (j == i && n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
+                        double d[3];
+                        if (pair_vec(xi, x + 3 * j, n, &b, d) < rc2) {
+                            if (cnt == cap) {
+                                cap *= 2;
+                                js = (int32_t *)realloc(js, sizeof(int32_t) * (size_t)cap);
+                                ns = (int32_t *)realloc(ns, sizeof(int32_t) * 3 * (size_t)cap);
+                            }
+                            js[cnt] = (int32_t)j;
+                            ns[3 * cnt] = n[0];
+                            ns[3 * cnt + 1] = n[1];
+                            ns[3 * cnt + 2] = n[2];
+                            ++cnt;
+                        }
+                    }
+        }
+        double fpi = 0.0, Fi_emb = 0.0;
+        double *fpj = NULL;
+        if (kind == 1) {
+            /* rho_i, then rho_j of every neighbour j by its own all-atom sum */
+            double rho_i = 0.0;
+            for (int64_t c = 0; c < cnt; ++c) {
+                double d[3], dr;
+                double r2 = pair_vec(xi, x + 3 * (int64_t)js[c], ns + 3 * c, &b, d);
+                rho_i += radial(&p.rho, sqrt(r2), &dr);
+            }
+            int fl = 0;
+            Fi_emb = embed(&p.F, rho_i, &fpi, &fl);
+            flag |= fl;
+            fpj = (double *)malloc(sizeof(double) * (size_t)(cnt > 0 ? cnt : 1));
+            for (int64_t c = 0; c < cnt; ++c) {
+                const double *xj = x + 3 * (int64_t)js[c];
+                double rho_j = 0.0;
+                for (int64_t k2 = 0; k2 < N; ++k2) {
+                    int lo2[3], hi2[3];
+                    for (int k = 0; k < 3; ++k)
+                        image_range(x[3 * k2 + k] - xj[k], &b, k, rc, &lo2[k], &hi2[k]);
+                    int n[3];
+                    for (n[0] = lo2[0]; n[0] <= hi2[0]; ++n[0])
+                        for (n[1] = lo2[1]; n[1] <= hi2[1]; ++n[1])
+                            for (n[2] = lo2[2]; n[2] <= hi2[2]; ++n[2]) {
+                                if (k2 == js[c] && n[0] == 0 && n[1] == 0 && n[2] == 0)
+                                    continue;
+                                double d[3], dr;
+                                double r2 = pair_vec(xj, x + 3 * k2, n, &b, d);
+                                if (r2 < rc2) rho_j += radial(&p.rho, sqrt(r2), &dr);
+                            }
+                }
+                int fl2 = 0;
+                embed(&p.F, rho_j, &fpj[c], &fl2);
+                flag |= fl2;
+            }
+        }
+        double fi[3] = {0, 0, 0}, ei = 0.0;
+        for (int64_t c = 0; c < cnt; ++c) {
+            double d[3];
+            double r2 = pair_vec(xi, x + 3 * (int64_t)js[c], ns + 3 * c, &b, d);
+            double r = sqrt(r2), v, dv;
+            if (kind == 0) {
+                v = lj_pair(&p, r, &dv);
+            } else {
+                double dphi, drho;
+                v = radial(&p.phi, r, &dphi);
+                radial(&p.rho, r, &drho);
+                dv = dphi + (fpi + fpj[c]) * drho;
+            }
+            ei += 0.5 * v;
+            double s = dv / r;
+            fi[0] += s * d[0];
+            fi[1] += s * d[1];
+            fi[2] += s * d[2];
+        }
+        free(fpj);
+        Fsel[3 * q + 0] = fi[0];
+        Fsel[3 * q + 1] = fi[1];
+        Fsel[3 * q + 2] = fi[2];
+        if (Esel) Esel[q] = ei + Fi_emb;
+    }
+    free(js);
+    free(ns);
+    pot_free(&p);
+    return flag;
+}
+
+/* ---------------------------------------------------------------------- */
+/* velocity-Verlet MD with Verlet lists (the paper's algorithm)            */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * NVE integration (Sec. "Molecular dynamics": conventional Verlet, here in
+ * velocity form):  v += dt/2 a;  x += dt v;  [rebuild list if needed];
+ * a = f/m;  v += dt/2 a.   Accelerations a = f/m * ORA_ACC (Angstrom/fs^2).
+ *
+ * The Verlet list (search radius rc + skin) is rebuilt when the largest
+ * displacement since the last build exceeds skin/2 (rebuild_every = 0), or
+ * every rebuild_every steps.  Every rebuild wraps periodic coordinates into
+ * the primary box and bins the atoms into cells of size >= rc + skin (Sec.
+ * "Neighbor lists construction").
+ *
+ * Piston atoms (piston[i] != 0, may be NULL) move rigidly: v = (u_p, 0, 0)
+ * and x += u_p dt; they ignore forces (reading of the piston boundary of the
+ * shock problems).
+ *
+ * thermo (may be NULL) receives per step: K, U, W_xx+W_yy+W_zz.
+ * Returns the number of list builds (>= 1) or a negative error code.
+ */
+int64_t ora_md_run(int64_t N, double *x, double *v, const double *mass,
+                   const double *lo, const double *hi, const int *per,
+                   int kind, const double *lj_par, int nr, double rc_eam,
+                   const double *phi, const double *rho, int nrho,
+                   double rho_max, const double *Ftab, double skin, double dt,
+                   int64_t nsteps, int rebuild_every, const uint8_t *piston,
+                   double u_p, double *thermo, double *F_out) {
+    ora_box b = make_box(lo, hi, per);
+    ora_pot p;
+    if (kind == 0)
+        pot_lj_init(&p, lj_par[0], lj_par[1], lj_par[2], (int)lj_par[3]);
+    else
+        pot_eam_init(&p, nr, rc_eam, phi, rho, nrho, rho_max, Ftab);
+    double rns = p.rc + skin;
+    for (int k = 0; k < 3; ++k)
+        if (b.per[k] && b.L[k] < rns) return -1;
+    ora_vlist vl;
+    memset(&vl, 0, sizeof(vl));
+    vl.off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N + 1));
+    double *F = (double *)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    double *xref = (double *)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    int64_t nbuild = 0;
+    double half_skin2 = 0.25 * skin * skin;
+
+    ora_wrap(N, x, lo, hi, per);
+    if (vlist_build(&vl, N, x, &b, rns) != 0) return -2;
+    memcpy(xref, x, sizeof(double) * 3 * (size_t)N);
+    ++nbuild;
+    double E, W[6];
+    forces_from_list(&p, N, x, &b, vl.off, vl.j, vl.n, &E, F, W, NULL, NULL, NULL, NULL);
+
+    for (int64_t step = 0; step < nsteps; ++step) {
+        for (int64_t i = 0; i < N; ++i) {
+            if (piston && piston[i]) {
+                v[3 * i + 0] = u_p;
+                v[3 * i + 1] = 0.0;
+                v[3 * i + 2] = 0.0;
+            } else {
+                double c = 0.5 * dt * ORA_ACC / mass[i];
+                for (int k = 0; k < 3; ++k) v[3 * i + k] += c * F[3 * i + k];
+            }
+            for (int k = 0; k < 3; ++k) x[3 * i + k] += dt * v[3 * i + k];
+        }
+        int rebuild = 0;
+        if (rebuild_every > 0) {
+            rebuild = ((step + 1) % rebuild_every) == 0;
+        } else {
+            for (int64_t i = 0; i < N && !rebuild; ++i) {
+                double dx = x[3 * i] - xref[3 * i];
+                double dy = x[3 * i + 1] - xref[3 * i + 1];
+                double dz = x[3 * i + 2] - xref[3 * i + 2];
+                double d2 = dx * dx;
+                d2 = d2 + dy * dy;
+                d2 = d2 + dz * dz;
+                if (d2 > half_skin2) rebuild = 1;
+            }
+        }
+        if (rebuild) {
+            ora_wrap(N, x, lo, hi, per);
+            if (vlist_build(&vl, N, x, &b, rns) != 0) return -2;
+            memcpy(xref, x, sizeof(double) * 3 * (size_t)N);
+            ++nbuild;
+        }
+        forces_from_list(&p, N, x, &b, vl.off, vl.j, vl.n, &E, F, W, NULL, NULL, NULL, NULL);
+        double K = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            if (!(piston && piston[i])) {
+                double c = 0.5 * dt * ORA_ACC / mass[i];
+                for (int k = 0; k < 3; ++k) v[3 * i + k] += c * F[3 * i + k];
+            }
+            double v2 = v[3 * i] * v[3 * i];
+            v2 = v2 + v[3 * i + 1] * v[3 * i + 1];
+            v2 = v2 + v[3 * i + 2] * v[3 * i + 2];
+            K += 0.5 * mass[i] * v2 / ORA_ACC;
+        }
+        if (thermo) {
+            thermo[3 * step + 0] = K;
+            thermo[3 * step + 1] = E;
+            thermo[3 * step + 2] = W[0] + W[1] + W[2];
+        }
+    }
+    if (F_out) memcpy(F_out, F, sizeof(double) * 3 * (size_t)N);
+    free(vl.off);
+    free(vl.j);
+    free(vl.n);
+    free(F);
+    free(xref);
+    pot_free(&p);
+    return nbuild;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Appendix: per-bin statistics                                            */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Bins of width w along `axis` starting at origin (bin l covers
+ * [origin + l w, origin + (l+1) w)); atoms outside [0, nbins) are ignored.
+ * Output per bin, 17 values:
+ *   [0] N_l  [1] M_l  [2..4] u_l (COM velocity)  [5..7] T^x, T^y, T^z
+ *   [8] E_pot,l (sum of per-atom U_i)
+ *   [9..14] P^{xx,yy,zz,xy,xz,yz} = (sum m du du + W_l) / V_l
+ *   [15] E_kin,l (peculiar, eV)  [16] V_l
+ * Temperatures: T^a = 2 E^a_kin / (k_B N_l) per degree of freedom.
+ * W_l = sum over the bin's atoms of the per-atom virial Wa (6 per atom).
+ * (Appendix "Analysis of MD simulation results"; virial read with the pair
+ * force, see the file header.)
+ */
+void ora_profiles(int64_t N, const double *x, const double *v, const double *mass,
+                  const double *Ua, const double *Wa, int axis, double origin,
+                  double w, int nbins, double cross_area, double *out) {
+    const double KB = 8.617333262e-5;
+    memset(out, 0, sizeof(double) * 17 * (size_t)nbins);
+    int *bin = (int *)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
+    for (int64_t i = 0; i < N; ++i) {
+        double u = (x[3 * i + axis] - origin) / w;
+        int l = (int)floor(u);
+        bin[i] = (l >= 0 && l < nbins) ? l : -1;
+    }
+    /* mass and momentum */
+    for (int64_t i = 0; i < N; ++i) {
+        int l = bin[i];
+        if (l < 0) continue;
+        double *o = out + 17 * l;
+        o[0] += 1.0;
+        o[1] += mass[i];
+        for (int k = 0; k < 3; ++k) o[2 + k] += mass[i] * v[3 * i + k];
+        if (Ua) o[8] += Ua[i];
+    }
+    for (int l = 0; l < nbins; ++l) {
+        double *o = out + 17 * l;
+        for (int k = 0; k < 3; ++k) o[2 + k] = (o[1] > 0.0) ? o[2 + k] / o[1] : 0.0;
+        o[16] = w * cross_area;
+    }
+    /* peculiar kinetic tensor and virial */
+    double *kt = (double *)calloc(6 * (size_t)nbins, sizeof(double));
+    for (int64_t i = 0; i < N; ++i) {
+        int l = bin[i];
+        if (l < 0) continue;
+        double *o = out + 17 * l;
+        double du[3];
+        for (int k = 0; k < 3; ++k) du[k] = v[3 * i + k] - o[2 + k];
+        double m = mass[i] / ORA_ACC; /* u Angstrom^2/fs^2 -> eV */
+        double *t = kt + 6 * l;
+        t[0] += m * du[0] * du[0];
+        t[1] += m * du[1] * du[1];
+        t[2] += m * du[2] * du[2];
+        t[3] += m * du[0] * du[1];
+        t[4] += m * du[0] * du[2];
+        t[5] += m * du[1] * du[2];
+        if (Wa)
+            for (int c = 0; c < 6; ++c) o[9 + c] += Wa[6 * i + c];
+    }
+    for (int l = 0; l < nbins; ++l) {
+        double *o = out + 17 * l, *t = kt + 6 * l;
+        double nl = o[0];
+        for (int k = 0; k < 3; ++k) o[5 + k] = (nl > 0.0) ? t[k] / (KB * nl) : 0.0;
+        o[15] = 0.5 * (t[0] + t[1] + t[2]);
+        for (int c = 0; c < 6; ++c) o[9 + c] = (t[c] + o[9 + c]) / o[16];
+    }
+    free(kt);
+    free(bin);
+}
