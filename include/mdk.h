@@ -1,0 +1,305 @@
+/*
+ * mdk.h -- C ABI of the GB300-native short-range molecular-dynamics hot path
+ * (MDcraft, arXiv 2511.22951): cell-list Verlet neighbour lists with a skin
+ * and a displacement-triggered rebuild, Lennard-Jones and tabulated-EAM
+ * forces, velocity-Verlet NVE integration, a rigid-piston / moving-window
+ * hook for shock runs, and the Appendix per-bin profiles.
+ *
+ * Every step runs in hand-written sm_103a CUDA kernels of libmdk.so.  No
+ * call allocates device memory: all device scratch lives in one workspace
+ * that the caller allocates (mdk_workspace_size / mdk_set_workspace).
+ *
+ * Conventions shared by every call
+ *  - Units: eV, Angstrom, fs, atomic mass unit u.  Accelerations use
+ *    a = F/m * 9.648533212e-3 Angstrom/fs^2 per eV/(Angstrom u).
+ *  - Return value: MDK_OK (0) or a negative MDK_ERR_* code.  No C++
+ *    exception crosses this boundary.  mdk_status_string() names a code.
+ *  - Arrays are C-contiguous.  Positions, velocities and forces are
+ *    [N][3] doubles (x, y, z per atom) in the caller's atom order; the
+ *    library's internal spatial ordering is never visible.
+ *  - Ownership: the caller owns every pointer it passes.  Host arrays are
+ *    copied before the call returns.  Device arrays (on_device = 1) are read
+ *    or written only inside the call, on the context's stream.
+ *  - Streams: all work is enqueued on the stream given to mdk_create (NULL =
+ *    legacy default stream).  A call that returns host data synchronises
+ *    that stream; a call that only writes device memory does not.
+ *  - Threading: a context is used by one host thread at a time.
+ *  - Boxes: periodic dimensions must be at least rc + skin long (smaller
+ *    periodic boxes return MDK_ERR_BOX_TOO_SMALL).  Free (non-periodic)
+ *    dimensions use the box only to lay out cells; atoms outside it are
+ *    still simulated exactly (they share the end cells).
+ */
+#ifndef MDK_H
+#define MDK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------- */
+#define MDK_OK 0
+#define MDK_ERR_BAD_ARG (-1)        /* invalid argument or size            */
+#define MDK_ERR_BOX_TOO_SMALL (-2)  /* periodic length < rc + skin         */
+#define MDK_ERR_NEIGH_OVERFLOW (-3) /* a list outgrew its capacity; the
+                                       capacity was raised: resize the
+                                       workspace and repeat the call       */
+#define MDK_ERR_ATOM_LOST (-4)      /* an atom moved more than one cell
+                                       between list builds                 */
+#define MDK_ERR_NONFINITE (-5)      /* NaN or Inf in a position or force   */
+#define MDK_ERR_TIMEOUT (-6)        /* a bounded device-side wait ran out  */
+#define MDK_ERR_CUDA (-7)           /* a CUDA runtime call failed          */
+#define MDK_ERR_WORKSPACE (-8)      /* no workspace, or it is too small    */
+#define MDK_ERR_ORDER (-9)          /* call made before a required call    */
+#define MDK_ERR_RHO_RANGE (-10)     /* an EAM density left the F table
+                                       (F was extrapolated linearly)       */
+
+/* ---- precision modes ---------------------------------------------------- */
+#define MDK_FP64 0  /* every operation in FP64                               */
+#define MDK_MIXED 1 /* FP32 pair arithmetic from cell-relative FP32 offsets,
+                       compensated FP32 sums per atom, FP64 positions,
+                       velocities, integration and per-atom results        */
+
+typedef struct mdk_ctx mdk_ctx; /* opaque, library-owned host object */
+
+/* ---- lifetime ----------------------------------------------------------- */
+
+/*
+ * Create a context for one periodic/free box holding N atoms.
+ * Follows the paper's statement of the MD problem: N atoms in a domain with
+ * free or periodic boundaries (Sec. "Molecular dynamics").
+ *   box_lo, box_hi : [3] box corners (host)
+ *   periodic       : [3] 0 = free, 1 = periodic (host)
+ *   N              : atom count, 0 <= N < 2^26
+ *   masses         : [N] atomic masses in u (host); at most 16 distinct values
+ *   precision      : MDK_FP64 or MDK_MIXED
+ *   cuda_stream    : a cudaStream_t, or NULL
+ * The context holds no device memory until mdk_set_workspace.
+ */
+int mdk_create(mdk_ctx **out, const double box_lo[3], const double box_hi[3],
+               const int periodic[3], int64_t N, const double *masses,
+               int precision, void *cuda_stream);
+
+/*
+ * Create one context for n_rep independent systems ("replicas"), each with
+ * its own box, run together by the same kernels (one launch per phase for
+ * all replicas).  Atoms of replica r are atoms [off_r, off_r + n_atoms[r])
+ * of every [N][3] array, off_r = sum of the earlier n_atoms.
+ *   box_lo, box_hi : [n_rep][3];  periodic : [n_rep][3];  n_atoms : [n_rep]
+ *   masses         : [sum n_atoms]
+ * Paper counterpart: the cold-curve and isotherm series (many small boxes).
+ */
+int mdk_create_batch(mdk_ctx **out, int n_rep, const double *box_lo,
+                     const double *box_hi, const int *periodic,
+                     const int64_t *n_atoms, const double *masses,
+                     int precision, void *cuda_stream);
+
+/* Destroy a context (the workspace stays the caller's). */
+int mdk_destroy(mdk_ctx *ctx);
+
+/* Reserve room for up to max_atoms atoms (moving window inserts atoms).
+ * Default: the N given at creation.  Call before mdk_workspace_size. */
+int mdk_set_capacity(mdk_ctx *ctx, int64_t max_atoms);
+
+/* ---- potentials (Sec. "Potentials support") ------------------------------ */
+
+/*
+ * Lennard-Jones u(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6] for r < rc.
+ * shift_mode: 0 plain truncation, 1 energy shifted to 0 at rc,
+ * 2 shifted force (value and slope 0 at rc).
+ */
+int mdk_set_potential_lj(mdk_ctx *ctx, double eps, double sigma, double rc,
+                         int shift_mode);
+
+/*
+ * Single-element EAM from tabulated functions (the paper loads EAM from a
+ * tabulated file; energy U = 1/2 sum_ij phi(r_ij) + sum_i F(rho_i),
+ * rho_i = sum_j rho(r_ij)).
+ *   phi, rho : [nr] knot values at r_k = k rc/(nr-1) (host); last knot at rc
+ *   F        : [nrho] knot values at rho_k = k rho_max/(nrho-1) (host)
+ * Between knots: cubic Hermite spline, knot slopes from 3-point differences
+ * (one-sided at the ends).  r >= rc gives 0; rho > rho_max extrapolates F
+ * linearly and makes mdk_compute/mdk_step return MDK_ERR_RHO_RANGE.
+ * 3 <= nr, nrho <= 8192.
+ */
+int mdk_set_potential_eam(mdk_ctx *ctx, int nr, double rc, const double *phi,
+                          const double *rho, int nrho, double rho_max,
+                          const double *F);
+
+/* ---- device memory ---------------------------------------------------- */
+
+/* Bytes of device workspace the context needs for its current capacity,
+ * potential and neighbour parameters (call mdk_plan_neighbors first to
+ * size for a given skin; default skin 0.3 Angstrom). */
+int mdk_workspace_size(const mdk_ctx *ctx, size_t *bytes);
+
+/*
+ * Hand the context a device buffer of at least mdk_workspace_size bytes,
+ * 256-byte aligned.  The caller keeps ownership and must keep it alive
+ * until the context is destroyed or given another workspace.  Setting a
+ * new workspace discards the device state: call mdk_set_state again.
+ */
+int mdk_set_workspace(mdk_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* ---- state ---------------------------------------------------------------- */
+
+/*
+ * Copy positions x [N][3] and velocities v [N][3] (Angstrom, Angstrom/fs)
+ * into the context.  on_device: 0 = host pointers, 1 = device pointers.
+ * v may be NULL (zero velocities).  Invalidates the neighbour list.
+ */
+int mdk_set_state(mdk_ctx *ctx, const double *x, const double *v, int on_device);
+
+/*
+ * Copy the current positions and velocities out, in the caller's atom
+ * order.  Periodic coordinates are those wrapped into the box at the last
+ * list build (then moved by the integrator since).  Either pointer may be
+ * NULL.  Host copies synchronise the stream.
+ */
+int mdk_get_state(mdk_ctx *ctx, double *x, double *v, int on_device);
+
+/* Current number of atoms (changes with the moving window). */
+int mdk_get_natoms(const mdk_ctx *ctx, int64_t *n);
+
+/* ---- neighbour lists (Sec. "Neighbor lists construction", Eq. rhrz) ------ */
+
+/*
+ * Set the list parameters without building: search radius r_ns = rc + skin
+ * (the paper's (1 + beta) r_cut with beta = skin/rc), per-atom capacity
+ * max_neighbors (0 = estimate from the density), and the rebuild policy
+ * rebuild_every (0 = rebuild when an atom has moved more than skin/2 since
+ * the last build; k > 0 = also every k steps).  Changes the workspace size.
+ */
+int mdk_plan_neighbors(mdk_ctx *ctx, double rc, double skin, int max_neighbors,
+                       int rebuild_every);
+
+/*
+ * Build the Verlet lists now: wrap periodic coordinates into the box, bin
+ * atoms into cells of size >= rc + skin by a counting sort, reorder the
+ * atoms into cell order, and keep every (j, image) with
+ * |(x_j - x_i) + n L|^2 < (rc + skin)^2, (j, n) != (i, 0).  rc must be at
+ * least the potential's cutoff.  MDK_ERR_NEIGH_OVERFLOW: the capacity was
+ * raised; resize the workspace, set the state and build again.
+ */
+int mdk_build_neighbors(mdk_ctx *ctx, double rc, double skin);
+
+/* Total number of (i, j, image) entries in the current lists. */
+int mdk_neighbor_count(mdk_ctx *ctx, int64_t *total);
+
+/*
+ * Export the lists in the caller's atom order (host arrays):
+ *   offsets [N+1]: entries of atom i are [offsets[i], offsets[i+1])
+ *   j       [total]: neighbour atom (caller's index)
+ *   image   [total][3]: periodic image n of the neighbour (box lengths),
+ *                       relative to the positions mdk_get_state returns
+ * Order within a list is unspecified.
+ */
+int mdk_get_neighbors(mdk_ctx *ctx, int64_t *offsets, int32_t *j, int32_t *image);
+
+/* ---- forces and stepping -------------------------------------------------- */
+
+/*
+ * Potential energy E [1] (or [n_rep] for a batch), forces F [N][3] and
+ * virial [6] (or [n_rep][6]: xx yy zz xy xz yz, W = 1/2 sum_i sum_j
+ * r_ij (x) f_ij with r_ij = r_i - r_j; pressure P = (sum m v v + W)/V) at the
+ * current positions.  Any output may be NULL.  f_i = sum_j V'(r_ij) r_ji/r_ji
+ * (Sec. "Potentials support").  Rebuilds the lists first if needed.
+ * on_device: 0 = host outputs (synchronises), 1 = device outputs.
+ */
+int mdk_compute(mdk_ctx *ctx, double *E, double *F, double *virial, int on_device);
+
+/*
+ * Per-atom potential energy U_i [N] and per-atom virial W_i [N][6] (host),
+ * from the last mdk_compute (U = sum U_i, W = sum W_i).  Either may be NULL.
+ */
+int mdk_get_per_atom(mdk_ctx *ctx, double *Ui, double *Wi);
+
+/*
+ * Advance nsteps velocity-Verlet NVE steps of dt fs (Sec. "Molecular
+ * dynamics"): v += dt/2 a; x += dt v; rebuild lists when triggered;
+ * a = f(x)/m; v += dt/2 a.  All control stays on the GPU; the call only
+ * enqueues work and returns the first error flag raised by an earlier call.
+ */
+int mdk_step(mdk_ctx *ctx, double dt, int64_t nsteps);
+
+/*
+ * Sample kinetic energy, potential energy and virial every `every` steps
+ * of mdk_step (0 = off) into a device ring of up to `capacity` samples.
+ */
+int mdk_set_thermo(mdk_ctx *ctx, int every, int capacity);
+
+/*
+ * Copy the samples taken since the last call (host, synchronises): out
+ * [max_samples][4 + 6] = step, E_kin, E_pot, n_atoms, virial[6] per sample
+ * and per replica (replica-major within a sample).  n_out = samples copied.
+ */
+int mdk_get_thermo(mdk_ctx *ctx, double *out, int max_samples, int *n_out);
+
+/* Number of list builds and of steps done so far (host, synchronises). */
+int mdk_get_counters(mdk_ctx *ctx, int64_t *n_builds, int64_t *n_steps);
+
+/* ---- shock hook (Sec. "Moving window simulation") -------------------------- */
+
+/*
+ * Rigid piston: atoms with is_piston[i] != 0 (host, [N], caller's order)
+ * move at v = (u_p, 0, 0) and ignore forces.  u_p in Angstrom/fs.
+ * is_piston = NULL clears the piston.
+ */
+int mdk_set_piston(mdk_ctx *ctx, double u_p, const uint8_t *is_piston);
+
+/*
+ * Moving window along x (free dimension): at every list build, atoms with
+ * x < x_front - L_behind are deleted, and while the largest x of the
+ * material is below x_front + L_ahead a copy of the fresh slab (n_slab atoms,
+ * positions [n_slab][3] relative to its own origin, velocities [n_slab][3],
+ * all host) is appended at x_max + slab_dx.  x_front is the largest x of an
+ * atom with v_x > u_p/2 (the shocked material).  Atoms within piston_depth
+ * of the rear edge become piston atoms after a deletion.
+ */
+int mdk_set_window(mdk_ctx *ctx, double L_behind, double L_ahead,
+                   const double *slab_x, const double *slab_v, int64_t n_slab,
+                   double slab_dx, double slab_mass, double piston_depth);
+
+/*
+ * Appendix per-bin statistics along `axis` (0..2) for bins of width bin_w
+ * starting at origin; out [nbins][17] = N_l, M_l, u_l[3], T_l[3], E_pot,l,
+ * P_l[6] (xx yy zz xy xz yz), E_kin,l, V_l.  Uses the per-atom energy and
+ * virial of the last mdk_compute.  on_device: 0 = host out.
+ */
+int mdk_profiles(mdk_ctx *ctx, int axis, double origin, double bin_w, int nbins,
+                 double cross_area, double *out, int on_device);
+
+/* ---- measurement ----------------------------------------------------------- */
+
+/*
+ * enable != 0: from now on bracket every force pass and every list-rebuild
+ * chain enqueued by mdk_step / mdk_compute with CUDA events on the context's
+ * stream, and count the kernels launched.  enable = 0 stops recording.
+ * Either call clears the counters.  (Measurement aid; no paper counterpart.)
+ */
+int mdk_profile(mdk_ctx *ctx, int enable);
+
+/*
+ * Read the counters (host, synchronises the stream).  out [8]:
+ *   [0] total ms of force passes   [1] number of force passes
+ *   [2] total ms of rebuild chains [3] number of rebuild chains
+ *   [4] kernels launched           [5] list builds done (device count)
+ *   [6] ms of the first-kick/drift kernels  [7] number of them
+ */
+int mdk_get_profile(mdk_ctx *ctx, double *out);
+
+/* ---- errors ------------------------------------------------------------- */
+
+/* Static string naming a status code. */
+const char *mdk_status_string(int status);
+
+/* Device-side status bits raised since the last call (synchronises). */
+int mdk_last_device_status(mdk_ctx *ctx, int *bits);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDK_H */

@@ -1,0 +1,381 @@
+// k_build.cu -- Verlet-list rebuild on the GPU (Sec. "Neighbor lists
+// construction" of the paper: a virtual Cartesian grid of cells of size
+// >= R = r_ns, one bucket-sort pass of the atoms into the cells, then a
+// 3x3x3 cell stencil search; Eq. rhrz gives r_ns = (1 + beta) r_cut, here
+// rc + skin).
+//
+// The chain runs every step and every kernel returns at once unless the
+// device flag st->rebuild is set, so the whole step stays on the device
+// (no host round trip to decide whether to rebuild):
+//   k_pre       count steps since the last build; fixed-interval trigger
+//   k_bin       wrap periodic coordinates, cell id per atom, cell histogram
+//   k_scan_*    exclusive scan of the histogram (3 phases)
+//   k_scatter   counting-sort scatter into cell order (atomic slots)
+//   k_cell_sort order each cell's atoms by their permanent id (determinism)
+//   k_permute   gather every per-atom array into the new order (scratch)
+//   k_copyback  scratch -> primary arrays
+//   k_build     Verlet lists: FP32 pre-filter on cell-relative offsets,
+//               exact FP64 test for the few candidates near r_ns
+//   k_finish    clear the flag, count the build
+#include <math.h>
+
+#include "mdk_internal.cuh"
+
+namespace mdk {
+
+namespace {
+
+constexpr int kBlk = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ bool flag_on(const Sys &s) {
+  return *(volatile int *)&s.st->rebuild != 0;
+}
+
+__global__ void k_pre(Sys s, int count_step) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DevStatus *st = s.st;
+  if (count_step) st->since_build += 1;
+  if (s.rebuild_every > 0 && st->since_build >= s.rebuild_every) st->rebuild = 1;
+}
+
+__global__ void k_set_flag(Sys s) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) s.st->rebuild = 1;
+}
+
+__global__ void __launch_bounds__(kBlk) k_bin(Sys s) {
+  if (!flag_on(s)) return;
+  const int N = s.st->N;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const Grid &g = s.grid[s.info[i] >> 8];
+  int c[3];
+  for (int d = 0; d < 3; ++d) {
+    double xv = s.x[(size_t)d * s.N_cap + i];
+    if (!isfinite(xv)) {
+      atomicOr(&s.st->bits, kStNonfinite);
+      xv = g.lo[d];
+      s.x[(size_t)d * s.N_cap + i] = xv;
+    }
+    if (g.per[d]) {
+      const double lo = g.lo[d], hi = g.hi[d], L = g.L[d];
+      if (xv >= hi || xv < lo) {
+        // whole box lengths, one at a time (as the definition states);
+        // atoms more than 4 boxes away jump by a floor first
+        if (fabs(xv - lo) > 4.0 * L) xv = xv - L * floor((xv - lo) / L);
+        for (int it = 0; it < 8 && xv >= hi; ++it) xv = xv - L;
+        for (int it = 0; it < 8 && xv < lo; ++it) xv = xv + L;
+        if (xv >= hi || xv < lo) xv = lo;
+        s.x[(size_t)d * s.N_cap + i] = xv;
+      }
+    }
+    int ck = (int)floor((xv - g.lo[d]) * g.inv_h[d]);
+    ck = min(max(ck, 0), g.nc[d] - 1);
+    c[d] = ck;
+  }
+  const int cell = g.cell_off + c[0] + g.nc[0] * (c[1] + g.nc[1] * c[2]);
+  s.cell_of[i] = cell;
+  s.tmpu[i] = pack_cell(c[0], c[1], c[2]);
+  atomicAdd(&s.cell_cnt[cell], 1);
+}
+
+// block-wide exclusive scan of one value per thread; returns the prefix and
+// writes the block total to *total
+__device__ __forceinline__ int block_exscan(int v, int *total) {
+  __shared__ int warp_sums[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    int w = (lane < nw) ? warp_sums[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < nw) warp_sums[lane] = wi - w;
+    if (lane == nw - 1) *total = wi;
+  }
+  __syncthreads();
+  const int res = warp_sums[warp] + incl - v;
+  __syncthreads();
+  return res;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Sys s) {
+  if (!flag_on(s)) return;
+  const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  int sum = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q)
+    if (base + q < s.n_cells) sum += s.cell_cnt[base + q];
+  __shared__ int tot;
+  block_exscan(sum, &tot);
+  if (threadIdx.x == 0) s.scan_part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(Sys s) {
+  if (!flag_on(s)) return;
+  // n_scan_blocks <= kScanThreads * 8
+  constexpr int kPer = 8;
+  const int base = threadIdx.x * kPer;
+  int loc[kPer];
+  int sum = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    loc[q] = (base + q < s.n_scan_blocks) ? s.scan_part[base + q] : 0;
+    sum += loc[q];
+  }
+  __shared__ int tot;
+  int pre = block_exscan(sum, &tot);
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    if (base + q < s.n_scan_blocks) s.scan_part[base + q] = pre;
+    pre += loc[q];
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(Sys s) {
+  if (!flag_on(s)) return;
+  const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  int loc[kScanItems];
+  int sum = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    loc[q] = (base + q < s.n_cells) ? s.cell_cnt[base + q] : 0;
+    sum += loc[q];
+  }
+  __shared__ int tot;
+  int pre = block_exscan(sum, &tot) + s.scan_part[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    const int c = base + q;
+    if (c < s.n_cells) {
+      s.cell_start[c] = pre;
+      s.cell_fill[c] = pre;
+      s.cell_cnt[c] = 0;  // ready for the next build
+    }
+    pre += loc[q];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1)
+    s.cell_start[s.n_cells] = pre;
+}
+
+__global__ void __launch_bounds__(kBlk) k_scatter(Sys s) {
+  if (!flag_on(s)) return;
+  const int N = s.st->N;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int pos = atomicAdd(&s.cell_fill[s.cell_of[i]], 1);
+  s.order[pos] = i;
+}
+
+// order inside each cell by permanent atom id (insertion sort: a cell holds
+// a few tens of atoms), so the layout does not depend on atomic ordering
+__global__ void __launch_bounds__(kBlk) k_cell_sort(Sys s) {
+  if (!flag_on(s)) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= s.n_cells) return;
+  const int a = s.cell_start[c], b = s.cell_start[c + 1];
+  for (int k = a + 1; k < b; ++k) {
+    const int v = s.order[k];
+    const int key = s.id[v];
+    int q = k - 1;
+    while (q >= a && s.id[s.order[q]] > key) {
+      s.order[q + 1] = s.order[q];
+      --q;
+    }
+    s.order[q + 1] = v;
+  }
+}
+
+template <class P>
+__global__ void __launch_bounds__(kBlk) k_permute(Sys s, typename P::vec4 *pg_target) {
+  if (!flag_on(s)) return;
+  const int N = s.st->N;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const size_t Nc = s.N_cap;
+  const int o = s.order[k];
+  double xv[3];
+  for (int d = 0; d < 3; ++d) {
+    xv[d] = s.x[d * Nc + o];
+    s.tmp[d * Nc + k] = xv[d];
+    s.tmp[(3 + d) * Nc + k] = s.v[d * Nc + o];
+    s.tmp[(6 + d) * Nc + k] = s.f[d * Nc + o];
+    s.xref[d * Nc + k] = xv[d];
+  }
+  s.tmpi[k] = s.id[o];
+  const uint32_t cc = s.tmpu[o];
+  s.cellc[k] = cc;
+  uint32_t inf = s.info[o] & ~kInfoFar;
+  const Grid &g = s.grid[inf >> 8];
+  double p[3];
+  bool far = false;
+  for (int d = 0; d < 3; ++d) {
+    p[d] = xv[d] - cell_center(g, d, cell_coord(cc, d));
+    // the FP32 pre-filter bound assumes |p| <= 2h (true for periodic
+    // dimensions after wrapping); atoms clamped into an end cell of a free
+    // dimension may lie further out and always take the exact test
+    if (!(fabs(p[d]) <= 2.0 * g.h[d])) far = true;
+  }
+  if (far) inf |= kInfoFar;
+  s.tmpu[Nc + k] = inf;
+  s.pf[k] = Mixed::make(p[0], p[1], p[2], inf);
+  pg_target[k] = P::make(p[0], p[1], p[2], inf);
+}
+
+__global__ void __launch_bounds__(kBlk) k_copyback(Sys s) {
+  if (!flag_on(s)) return;
+  const int N = s.st->N;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const size_t Nc = s.N_cap;
+  for (int d = 0; d < 3; ++d) {
+    s.x[d * Nc + k] = s.tmp[d * Nc + k];
+    s.v[d * Nc + k] = s.tmp[(3 + d) * Nc + k];
+    s.f[d * Nc + k] = s.tmp[(6 + d) * Nc + k];
+  }
+  s.id[k] = s.tmpi[k];
+  s.info[k] = s.tmpu[Nc + k];
+}
+
+// periodic image crossed when stencil offset sd leaves cell cd of nc cells
+__device__ __forceinline__ bool stencil_cell(int cd, int sd, int nc, int per, int *cell,
+                                             int *img) {
+  int c = cd + sd;
+  int n = 0;
+  if (per) {
+    if (c < 0) {
+      c += nc;
+      n = -1;
+    } else if (c >= nc) {
+      c -= nc;
+      n = 1;
+    }
+  } else if (c < 0 || c >= nc) {
+    return false;
+  }
+  *cell = c;
+  *img = n;
+  return true;
+}
+
+__global__ void __launch_bounds__(kBlk) k_build(Sys s) {
+  if (!flag_on(s)) return;
+  const int N = s.st->N;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const size_t Nc = s.N_cap;
+  const float4 pi = s.pf[i];
+  const uint32_t inf = __float_as_uint(pi.w);
+  const Grid &g = s.grid[inf >> 8];
+  const uint32_t cc = s.cellc[i];
+  const int c0 = cell_coord(cc, 0), c1 = cell_coord(cc, 1), c2 = cell_coord(cc, 2);
+  const double xi = s.x[i], yi = s.x[Nc + i], zi = s.x[2 * Nc + i];
+  const bool far_i = (inf & kInfoFar) != 0;
+  const float lo_thr = s.filt_lo, hi_thr = s.filt_hi;
+  const double rns2 = s.rns2;
+  int count = 0;
+  for (int sz = -1; sz <= 1; ++sz) {
+    int cz, nz;
+    if (!stencil_cell(c2, sz, g.nc[2], g.per[2], &cz, &nz)) continue;
+    for (int sy = -1; sy <= 1; ++sy) {
+      int cy, ny;
+      if (!stencil_cell(c1, sy, g.nc[1], g.per[1], &cy, &ny)) continue;
+      for (int sx = -1; sx <= 1; ++sx) {
+        int cx, nx;
+        if (!stencil_cell(c0, sx, g.nc[0], g.per[0], &cx, &nx)) continue;
+        const int cell = g.cell_off + cx + g.nc[0] * (cy + g.nc[1] * cz);
+        const int a = s.cell_start[cell], b = s.cell_start[cell + 1];
+        const float shx = (float)sx * g.hf[0];
+        const float shy = (float)sy * g.hf[1];
+        const float shz = (float)sz * g.hf[2];
+        const bool self_img = (nx == 0 && ny == 0 && nz == 0);
+        for (int j = a; j < b; ++j) {
+          if (j == i && self_img) continue;
+          const float4 pj = s.pf[j];
+          const float dx = (pj.x - pi.x) + shx;
+          const float dy = (pj.y - pi.y) + shy;
+          const float dz = (pj.z - pi.z) + shz;
+          const float r2f = dx * dx + dy * dy + dz * dz;
+          const bool far = far_i || (__float_as_uint(pj.w) & kInfoFar);
+          bool in;
+          if (!far && r2f < lo_thr) {
+            in = true;
+          } else if (!far && r2f > hi_thr) {
+            in = false;
+          } else {
+            // the definition, rounded step by step without contraction:
+            // d = (x_j - x_i) + n L,  r^2 = (dx^2 + dy^2) + dz^2 < r_ns^2
+            const double ex = __dadd_rn(__dadd_rn(s.x[j], -xi), __dmul_rn((double)nx, g.L[0]));
+            const double ey =
+                __dadd_rn(__dadd_rn(s.x[Nc + j], -yi), __dmul_rn((double)ny, g.L[1]));
+            const double ez =
+                __dadd_rn(__dadd_rn(s.x[2 * Nc + j], -zi), __dmul_rn((double)nz, g.L[2]));
+            const double r2 =
+                __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+            in = r2 < rns2;
+          }
+          if (in) {
+            if (count < s.nmax) s.nbr[(size_t)count * Nc + i] = pack_nbr(j, sx, sy, sz);
+            ++count;
+          }
+        }
+      }
+    }
+  }
+  s.nnbr[i] = count;
+  if (count > s.nmax) {
+    atomicOr(&s.st->bits, kStOverflow);
+    atomicMax(&s.st->max_nnbr, count);
+  }
+}
+
+__global__ void k_finish(Sys s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DevStatus *st = s.st;
+  if (st->rebuild) {
+    st->rebuild = 0;
+    st->n_builds += 1;
+    st->since_build = 0;
+  }
+}
+
+inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+}  // namespace
+
+void launch_set_rebuild_flag(const Sys &s, cudaStream_t st) { k_set_flag<<<1, 32, 0, st>>>(s); }
+
+void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, cudaStream_t st) {
+  const int gN = nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk);
+  k_pre<<<1, 32, 0, st>>>(s, count_step);
+  k_bin<<<gN, kBlk, 0, st>>>(s);
+  k_scan_reduce<<<s.n_scan_blocks, kScanThreads, 0, st>>>(s);
+  k_scan_top<<<1, kScanThreads, 0, st>>>(s);
+  k_scan_apply<<<s.n_scan_blocks, kScanThreads, 0, st>>>(s);
+  k_scatter<<<gN, kBlk, 0, st>>>(s);
+  k_cell_sort<<<nblk(s.n_cells, kBlk), kBlk, 0, st>>>(s);
+  if (precision == 0)
+    k_permute<Fp64><<<gN, kBlk, 0, st>>>(s, (dvec4 *)s.pg[target_pg]);
+  else
+    k_permute<Mixed><<<gN, kBlk, 0, st>>>(s, (float4 *)s.pg[target_pg]);
+  k_copyback<<<gN, kBlk, 0, st>>>(s);
+  k_build<<<gN, kBlk, 0, st>>>(s);
+  k_finish<<<1, 32, 0, st>>>(s);
+}
+
+int scan_blocks_for(int n_cells) { return (n_cells + kScanTile - 1) / kScanTile; }
+
+}  // namespace mdk

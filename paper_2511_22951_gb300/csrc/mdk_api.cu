@@ -1,0 +1,981 @@
+// mdk_api.cu -- the C ABI of libmdk.so (declared in include/mdk.h).
+//
+// Host code only marshals arguments, lays the caller's workspace out and
+// enqueues kernels on the context's stream; every step of the MD path
+// (binning, list build, forces, integration, reductions) runs in the
+// kernels of k_build.cu and k_force.cu.  No device memory is allocated here.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <new>
+#include <vector>
+
+#include "mdk.h"
+#include "mdk_internal.cuh"
+
+using namespace mdk;
+
+struct mdk_ctx {
+  cudaStream_t stream = nullptr;
+  int precision = MDK_FP64;
+  int n_rep = 1;
+  std::vector<double> lo, hi;
+  std::vector<int> per;
+  std::vector<int64_t> n_atoms;
+  int64_t N = 0, N_cap = 0;
+  std::vector<uint32_t> info0;
+  int n_types = 0;
+  double type_mass[kMaxTypes] = {0};
+  // potential
+  int pot = 0;  // 0 none, 1 LJ, 2 EAM
+  LJParams lj{};
+  EAMParams eam{};
+  std::vector<double> eam_phi, eam_rho, eam_F;
+  // neighbour plan
+  bool planned = false;
+  double rc_list = 0.0, skin = 0.3;
+  int nmax_req = 0, rebuild_every = 0;
+  int nmax = 0;
+  int nmax_grow = 0;      // capacity wanted after an overflow
+  bool need_ws = false;   // the current workspace no longer fits the plan
+  int n_cells = 0;
+  std::vector<Grid> grids;
+  // workspace
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_ok = false;
+  Sys sys{};
+  char *eam_base = nullptr;
+  EAMTablesDev eam_dev{};
+  double *thermo_ring = nullptr;
+  int cur = 0;
+  bool state_set = false, list_built = false, forces_valid = false;
+  double u_p = 0.0;
+  int thermo_every = 0, thermo_cap = 0;
+  int64_t thermo_written = 0, thermo_read = 0;
+  int64_t steps_done = 0;
+  // measurement (mdk_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, int>> ev_force, ev_chain, ev_kick;  // (start, end) indices
+  int64_t launches = 0;
+};
+
+namespace {
+
+#define MDK_CK(call)                                                   \
+  do {                                                                 \
+    cudaError_t _e = (call);                                           \
+    if (_e != cudaSuccess) {                                           \
+      fprintf(stderr, "mdk: %s failed: %s\n", #call, cudaGetErrorString(_e)); \
+      return MDK_ERR_CUDA;                                             \
+    }                                                                  \
+  } while (0)
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Carver {
+  char *base;
+  size_t off = 0;
+  template <class T>
+  T *take(size_t count) {
+    off = align256(off);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += sizeof(T) * (count > 0 ? count : 1);
+    return p;
+  }
+};
+
+// Lay the workspace out (base == nullptr only measures).
+size_t layout(mdk_ctx *c, char *base) {
+  Carver cv{base};
+  Sys &s = c->sys;
+  const size_t Nc = (size_t)std::max<int64_t>(c->N_cap, 1);
+  s.x = cv.take<double>(3 * Nc);
+  s.v = cv.take<double>(3 * Nc);
+  s.f = cv.take<double>(3 * Nc);
+  s.xref = cv.take<double>(3 * Nc);
+  s.tmp = cv.take<double>(9 * Nc);
+  s.info = cv.take<uint32_t>(Nc);
+  s.info0 = cv.take<uint32_t>(Nc);
+  s.cellc = cv.take<uint32_t>(Nc);
+  s.tmpu = cv.take<uint32_t>(2 * Nc);
+  s.id = cv.take<int32_t>(Nc);
+  s.tmpi = cv.take<int32_t>(Nc);
+  s.pf = cv.take<float4>(Nc);
+  const size_t gsz = c->precision == MDK_FP64 ? 32 : 16;
+  s.pg[0] = cv.take<char>(gsz * Nc);
+  s.pg[1] = cv.take<char>(gsz * Nc);
+  s.nnbr = cv.take<int32_t>(Nc);
+  s.nbr = cv.take<uint32_t>((size_t)std::max(c->nmax, c->nmax_grow) * Nc);
+  s.ea = cv.take<double>(Nc);
+  s.ka = cv.take<double>(Nc);
+  s.wa = cv.take<double>(6 * Nc);
+  s.rho = cv.take<double>(Nc);
+  s.fp = cv.take<double>(Nc);
+  s.cell_cnt = cv.take<int32_t>(c->n_cells);
+  s.cell_start = cv.take<int32_t>((size_t)c->n_cells + 1);
+  s.cell_fill = cv.take<int32_t>(c->n_cells);
+  s.scan_part = cv.take<int32_t>(scan_blocks_for(c->n_cells));
+  s.cell_of = cv.take<int32_t>(Nc);
+  s.order = cv.take<int32_t>(Nc);
+  s.grid = cv.take<Grid>(c->n_rep);
+  s.st = cv.take<DevStatus>(1);
+  s.red = cv.take<double>((size_t)9 * c->n_rep);
+  c->thermo_ring = cv.take<double>((size_t)std::max(c->thermo_cap, 1) * c->n_rep * 10);
+  // EAM tables: raw knots, (y, h m) FP64 and FP32 copies
+  const int nr = c->pot == 2 ? c->eam.nr : 1, nrho = c->pot == 2 ? c->eam.nrho : 1;
+  double *kn = cv.take<double>((size_t)2 * nr + nrho);
+  EAMTablesDev &t = c->eam_dev;
+  t.phi64 = cv.take<double2>(nr);
+  t.rho64 = cv.take<double2>(nr);
+  t.F64 = cv.take<double2>(nrho);
+  t.rho_i32 = cv.take<float4>(nr);
+  t.phi_d32 = cv.take<float2>(nr);
+  t.rho_d32 = cv.take<float2>(nr);
+  t.phi_v32 = cv.take<float>(nr);
+  c->eam_base = reinterpret_cast<char *>(kn);
+  c->eam.phi64 = t.phi64;
+  c->eam.rho64 = t.rho64;
+  c->eam.F64 = t.F64;
+  c->eam.rho_i32 = t.rho_i32;
+  c->eam.phi_d32 = t.phi_d32;
+  c->eam.rho_d32 = t.rho_d32;
+  c->eam.phi_v32 = t.phi_v32;
+  return align256(cv.off);
+}
+
+int check_ctx(const mdk_ctx *c) { return c ? MDK_OK : MDK_ERR_BAD_ARG; }
+
+int plan(mdk_ctx *c, double rc, double skin, int max_neighbors, int rebuild_every) {
+  if (!(rc > 0.0) || !(skin >= 0.0) || max_neighbors < 0 || rebuild_every < 0)
+    return MDK_ERR_BAD_ARG;
+  const double rns = rc + skin;
+  std::vector<Grid> gs((size_t)c->n_rep);
+  int cells = 0;
+  double max_density = 0.0;
+  int64_t atom_off = 0;
+  for (int r = 0; r < c->n_rep; ++r) {
+    Grid &g = gs[(size_t)r];
+    memset(&g, 0, sizeof(g));
+    double vol = 1.0;
+    for (int d = 0; d < 3; ++d) {
+      const double lo = c->lo[3 * r + d], hi = c->hi[3 * r + d];
+      const double L = hi - lo;
+      if (!(L > 0.0)) return MDK_ERR_BAD_ARG;
+      if (c->per[3 * r + d] && L < rns) return MDK_ERR_BOX_TOO_SMALL;
+      // cells of size h = L/nc strictly above r_ns (see the cell-list search)
+      int nc = (int)floor(L / (rns * (1.0 + 1e-10)));
+      nc = std::max(1, std::min(nc, 1023));
+      g.lo[d] = lo;
+      g.hi[d] = hi;
+      g.L[d] = L;
+      g.nc[d] = nc;
+      g.h[d] = L / nc;
+      g.inv_h[d] = 1.0 / g.h[d];
+      g.hf[d] = (float)g.h[d];
+      g.per[d] = c->per[3 * r + d] ? 1 : 0;
+      vol *= L;
+    }
+    g.cell_off = cells;
+    g.atom_off = (int)atom_off;
+    g.n_atoms = (int)c->n_atoms[(size_t)r];
+    atom_off += c->n_atoms[(size_t)r];
+    const long long nc3 = (long long)g.nc[0] * g.nc[1] * g.nc[2];
+    if ((long long)cells + nc3 > (1LL << 30)) return MDK_ERR_BAD_ARG;
+    cells += (int)nc3;
+    max_density = std::max(max_density, (double)c->n_atoms[(size_t)r] / vol);
+  }
+  if (scan_blocks_for(cells) > 8192) return MDK_ERR_BAD_ARG;
+  int nmax = max_neighbors;
+  if (nmax == 0) {
+    const double est = 4.0 / 3.0 * M_PI * rns * rns * rns * max_density;
+    nmax = (int)ceil(1.6 * est + 24.0);
+    nmax = (nmax + 3) & ~3;
+  }
+  c->grids = gs;
+  c->n_cells = cells;
+  c->nmax = nmax;
+  c->rc_list = rc;
+  c->skin = skin;
+  c->nmax_req = max_neighbors;
+  c->rebuild_every = rebuild_every;
+  c->planned = true;
+  return MDK_OK;
+}
+
+double pot_rc(const mdk_ctx *c) {
+  if (c->pot == 1) return c->lj.rc;
+  if (c->pot == 2) return c->eam.rc;
+  return 0.0;
+}
+
+void fill_sys_params(mdk_ctx *c) {
+  Sys &s = c->sys;
+  s.N_cap = (int)c->N_cap;
+  s.nmax = c->nmax;
+  s.n_rep = c->n_rep;
+  s.n_cells = c->n_cells;
+  s.n_scan_blocks = scan_blocks_for(c->n_cells);
+  const double rns = c->rc_list + c->skin;
+  s.rns2 = rns * rns;
+  // FP32 pre-filter band: the float r^2 of a candidate is within ~6e-6 r_ns^2
+  // of the exact one (cell-relative offsets, |p| <= 2h, h < 2 r_ns); 1e-4
+  // leaves a wide margin, and candidates inside the band take the FP64 test
+  s.filt_lo = (float)(s.rns2 * (1.0 - 1e-4));
+  s.filt_hi = (float)(s.rns2 * (1.0 + 1e-4));
+  s.half_skin2 = 0.25 * c->skin * c->skin;
+  s.rebuild_every = c->rebuild_every;
+  for (int t = 0; t < kMaxTypes; ++t) {
+    const double m = t < c->n_types ? c->type_mass[t] : 1.0;
+    s.acc_over_m[t] = kAcc / m;
+    s.ke_m[t] = 0.5 * m / kAcc;
+  }
+  s.u_p = c->u_p;
+}
+
+int read_status(mdk_ctx *c, DevStatus *out) {
+  MDK_CK(cudaMemcpyAsync(out, c->sys.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+  MDK_CK(cudaStreamSynchronize(c->stream));
+  return MDK_OK;
+}
+
+int status_from_bits(unsigned bits) {
+  if (bits & kStNonfinite) return MDK_ERR_NONFINITE;
+  if (bits & kStOverflow) return MDK_ERR_NEIGH_OVERFLOW;
+  if (bits & kStAtomLost) return MDK_ERR_ATOM_LOST;
+  if (bits & kStTimeout) return MDK_ERR_TIMEOUT;
+  if (bits & kStRhoRange) return MDK_ERR_RHO_RANGE;
+  return MDK_OK;
+}
+
+__global__ void k_init_status(Sys s, int N) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    DevStatus *st = s.st;
+    st->N = N;
+    st->rebuild = 1;
+    st->bits = 0;
+    st->max_nnbr = 0;
+    st->since_build = 0;
+  }
+}
+
+__global__ void k_clear_bits(Sys s) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    s.st->bits = 0;
+    s.st->max_nnbr = 0;
+  }
+}
+
+__global__ void k_thermo_store(Sys s, double *ring, int slot, double step) {
+  const int r = threadIdx.x;
+  if (r >= s.n_rep) return;
+  double *o = ring + ((size_t)slot * s.n_rep + r) * 10;
+  const double *q = s.red + 9 * r;
+  o[0] = step;
+  o[1] = q[0];
+  o[2] = q[1];
+  o[3] = q[8];
+  for (int c = 0; c < 6; ++c) o[4 + c] = q[2 + c];
+}
+
+__global__ void k_set_piston(Sys s, const uint8_t *flags) {
+  const int N = s.st->N;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int o = s.id[i];
+  const uint32_t pbit = (flags && flags[o]) ? kInfoPiston : 0u;
+  s.info[i] = (s.info[i] & ~kInfoPiston) | pbit;
+  s.info0[o] = (s.info0[o] & ~kInfoPiston) | pbit;
+}
+
+// next free event of the measurement pool (created on first use)
+int take_event(mdk_ctx *c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    c->ev_pool.push_back(e);
+  }
+  return (int)c->ev_used++;
+}
+
+// record an event pair around what `launch` enqueues when profiling
+template <class F>
+int timed(mdk_ctx *c, std::vector<std::pair<int, int>> &log, int n_kernels, F launch) {
+  int a = -1, b = -1;
+  if (c->prof) {
+    a = take_event(c);
+    if (a >= 0) cudaEventRecord(c->ev_pool[(size_t)a], c->stream);
+  }
+  launch();
+  c->launches += n_kernels;
+  if (c->prof && a >= 0) {
+    b = take_event(c);
+    if (b >= 0) {
+      cudaEventRecord(c->ev_pool[(size_t)b], c->stream);
+      log.emplace_back(a, b);
+    }
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? MDK_OK : MDK_ERR_CUDA;
+}
+
+int force_pass(mdk_ctx *c, Mode mode, int energy, double dt) {
+  StepArgs a{dt, c->cur, energy};
+  return timed(c, c->ev_force, c->pot == 1 ? 1 : 2, [&] {
+    if (c->pot == 1)
+      launch_lj(c->sys, c->lj, c->precision, mode, a, c->stream);
+    else
+      launch_eam(c->sys, c->eam, c->precision, mode, a, c->stream);
+  });
+}
+
+constexpr int kChainKernels = 11;
+
+int rebuild_chain(mdk_ctx *c, int count_step) {
+  return timed(c, c->ev_chain, kChainKernels, [&] {
+    launch_rebuild(c->sys, c->cur, c->precision, count_step, c->stream);
+  });
+}
+
+int ensure_ready(mdk_ctx *c) {
+  if (!c->ws_ok || c->need_ws) return MDK_ERR_WORKSPACE;
+  if (!c->state_set) return MDK_ERR_ORDER;
+  if (c->pot == 0) return MDK_ERR_ORDER;
+  if (pot_rc(c) > c->rc_list) return MDK_ERR_ORDER;
+  return MDK_OK;
+}
+
+int build_now(mdk_ctx *c) {
+  launch_set_rebuild_flag(c->sys, c->stream);
+  int rr = rebuild_chain(c, 0);
+  if (rr) return rr;
+  DevStatus st;
+  int rc = read_status(c, &st);
+  if (rc) return rc;
+  if (st.bits & kStOverflow) {
+    c->nmax_grow = ((int)ceil(st.max_nnbr * 1.25) + 8 + 3) & ~3;
+    c->need_ws = true;
+    c->list_built = false;
+    return MDK_ERR_NEIGH_OVERFLOW;
+  }
+  if (st.bits & kStNonfinite) return MDK_ERR_NONFINITE;
+  c->list_built = true;
+  return MDK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mdk_status_string(int s) {
+  switch (s) {
+    case MDK_OK: return "ok";
+    case MDK_ERR_BAD_ARG: return "bad argument";
+    case MDK_ERR_BOX_TOO_SMALL: return "periodic box shorter than rc + skin";
+    case MDK_ERR_NEIGH_OVERFLOW: return "neighbour list overflow (capacity raised; resize the workspace)";
+    case MDK_ERR_ATOM_LOST: return "atom moved more than one cell between builds";
+    case MDK_ERR_NONFINITE: return "non-finite position or force";
+    case MDK_ERR_TIMEOUT: return "device wait timed out";
+    case MDK_ERR_CUDA: return "CUDA runtime error";
+    case MDK_ERR_WORKSPACE: return "workspace missing or too small";
+    case MDK_ERR_ORDER: return "call made before a required call";
+    case MDK_ERR_RHO_RANGE: return "EAM density above the F table (extrapolated)";
+    default: return "unknown status";
+  }
+}
+
+int mdk_create_batch(mdk_ctx **out, int n_rep, const double *box_lo, const double *box_hi,
+                     const int *periodic, const int64_t *n_atoms, const double *masses,
+                     int precision, void *cuda_stream) {
+  if (!out || n_rep < 1 || n_rep > (1 << 20) || !box_lo || !box_hi || !periodic || !n_atoms)
+    return MDK_ERR_BAD_ARG;
+  if (precision != MDK_FP64 && precision != MDK_MIXED) return MDK_ERR_BAD_ARG;
+  int64_t total = 0;
+  for (int r = 0; r < n_rep; ++r) {
+    if (n_atoms[r] < 0) return MDK_ERR_BAD_ARG;
+    total += n_atoms[r];
+  }
+  if (total >= ((int64_t)1 << 26)) return MDK_ERR_BAD_ARG;
+  if (total > 0 && !masses) return MDK_ERR_BAD_ARG;
+  mdk_ctx *c = new (std::nothrow) mdk_ctx();
+  if (!c) return MDK_ERR_BAD_ARG;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->precision = precision;
+  c->n_rep = n_rep;
+  c->lo.assign(box_lo, box_lo + 3 * n_rep);
+  c->hi.assign(box_hi, box_hi + 3 * n_rep);
+  c->per.assign(periodic, periodic + 3 * n_rep);
+  c->n_atoms.assign(n_atoms, n_atoms + n_rep);
+  c->N = total;
+  c->N_cap = total;
+  c->info0.resize((size_t)total);
+  int64_t i = 0;
+  for (int r = 0; r < n_rep; ++r)
+    for (int64_t q = 0; q < n_atoms[r]; ++q, ++i) {
+      const double m = masses[i];
+      if (!(m > 0.0)) {
+        delete c;
+        return MDK_ERR_BAD_ARG;
+      }
+      int t = 0;
+      while (t < c->n_types && c->type_mass[t] != m) ++t;
+      if (t == c->n_types) {
+        if (c->n_types == kMaxTypes) {
+          delete c;
+          return MDK_ERR_BAD_ARG;
+        }
+        c->type_mass[c->n_types++] = m;
+      }
+      c->info0[(size_t)i] = (uint32_t)t | ((uint32_t)r << 8);
+    }
+  *out = c;
+  return MDK_OK;
+}
+
+int mdk_create(mdk_ctx **out, const double box_lo[3], const double box_hi[3],
+               const int periodic[3], int64_t N, const double *masses, int precision,
+               void *cuda_stream) {
+  return mdk_create_batch(out, 1, box_lo, box_hi, periodic, &N, masses, precision,
+                          cuda_stream);
+}
+
+int mdk_destroy(mdk_ctx *c) {
+  if (!c) return MDK_ERR_BAD_ARG;
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+  return MDK_OK;
+}
+
+int mdk_set_capacity(mdk_ctx *c, int64_t max_atoms) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  if (max_atoms < c->N || max_atoms >= ((int64_t)1 << 26)) return MDK_ERR_BAD_ARG;
+  if (c->n_rep != 1 && max_atoms != c->N) return MDK_ERR_BAD_ARG;
+  c->N_cap = max_atoms;
+  c->ws_ok = false;
+  return MDK_OK;
+}
+
+int mdk_set_potential_lj(mdk_ctx *c, double eps, double sigma, double rc, int shift_mode) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  if (!(eps > 0.0) || !(sigma > 0.0) || !(rc > 0.0) || shift_mode < 0 || shift_mode > 2)
+    return MDK_ERR_BAD_ARG;
+  LJParams &p = c->lj;
+  const double sr = sigma / rc, s6 = sr * sr * sr * sr * sr * sr;
+  const double u_rc = 4.0 * eps * (s6 * s6 - s6);
+  const double du_rc = -24.0 * eps * (2.0 * s6 * s6 - s6) / rc;
+  p.eps4 = 4.0 * eps;
+  p.eps24 = 24.0 * eps;
+  p.sig2 = sigma * sigma;
+  p.rc = rc;
+  p.rc2 = rc * rc;
+  p.u_shift = shift_mode >= 1 ? u_rc : 0.0;
+  p.du_rc = shift_mode == 2 ? du_rc : 0.0;
+  p.eps4f = (float)p.eps4;
+  p.eps24f = (float)p.eps24;
+  p.sig2f = (float)p.sig2;
+  p.rc2f = (float)p.rc2;
+  p.rcf = (float)rc;
+  p.u_shiftf = (float)p.u_shift;
+  p.du_rcf = (float)p.du_rc;
+  p.shift_mode = shift_mode;
+  c->pot = 1;
+  if (!c->planned) plan(c, rc, 0.3, 0, 0);
+  return MDK_OK;
+}
+
+int mdk_set_potential_eam(mdk_ctx *c, int nr, double rc, const double *phi, const double *rho,
+                          int nrho, double rho_max, const double *F) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  // FP64 tables of phi and rho must fit shared memory together (16 B per knot)
+  if (nr < 3 || nr > 7168 || nrho < 3 || nrho > 65536 || !(rc > 0.0) || !(rho_max > 0.0) ||
+      !phi || !rho || !F)
+    return MDK_ERR_BAD_ARG;
+  const bool resized = c->pot != 2 || c->eam.nr != nr || c->eam.nrho != nrho;
+  EAMParams &e = c->eam;
+  e.nr = nr;
+  e.nrho = nrho;
+  e.rc = rc;
+  e.rc2 = rc * rc;
+  e.dr = rc / (nr - 1);
+  e.inv_dr = 1.0 / e.dr;
+  e.rho_max = rho_max;
+  e.drho = rho_max / (nrho - 1);
+  e.inv_drho = 1.0 / e.drho;
+  e.rc2f = (float)e.rc2;
+  e.inv_drf = (float)e.inv_dr;
+  c->eam_phi.assign(phi, phi + nr);
+  c->eam_rho.assign(rho, rho + nr);
+  c->eam_F.assign(F, F + nrho);
+  c->pot = 2;
+  if (!c->planned) plan(c, rc, 0.3, 0, 0);
+  if (resized) {
+    c->ws_ok = false;  // table area changes size: a new workspace is needed
+    return MDK_OK;
+  }
+  if (c->ws_ok) {
+    // same table sizes: upload into the existing workspace
+    double *kn = reinterpret_cast<double *>(c->eam_base);
+    MDK_CK(cudaMemcpyAsync(kn, phi, sizeof(double) * nr, cudaMemcpyHostToDevice, c->stream));
+    MDK_CK(cudaMemcpyAsync(kn + nr, rho, sizeof(double) * nr, cudaMemcpyHostToDevice, c->stream));
+    MDK_CK(cudaMemcpyAsync(kn + 2 * nr, F, sizeof(double) * nrho, cudaMemcpyHostToDevice,
+                           c->stream));
+    launch_eam_prepare(e, kn, kn + nr, kn + 2 * nr, c->eam_dev, c->stream);
+    MDK_CK(cudaPeekAtLastError());
+    c->forces_valid = false;
+  }
+  return MDK_OK;
+}
+
+int mdk_plan_neighbors(mdk_ctx *c, double rc, double skin, int max_neighbors, int rebuild_every) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  const int old_nmax = c->nmax, old_cells = c->n_cells;
+  int rc_ = plan(c, rc, skin, max_neighbors, rebuild_every);
+  if (rc_) return rc_;
+  if (c->nmax != old_nmax || c->n_cells != old_cells) c->need_ws = true;
+  c->list_built = false;
+  return MDK_OK;
+}
+
+int mdk_workspace_size(const mdk_ctx *cc, size_t *bytes) {
+  if (!cc || !bytes) return MDK_ERR_BAD_ARG;
+  mdk_ctx *c = const_cast<mdk_ctx *>(cc);
+  if (!c->planned) {
+    if (c->pot == 0) return MDK_ERR_ORDER;
+    int r = plan(c, pot_rc(c), 0.3, 0, 0);
+    if (r) return r;
+  }
+  Sys keep = c->sys;
+  EAMParams ekeep = c->eam;
+  EAMTablesDev tkeep = c->eam_dev;
+  char *kb = c->eam_base;
+  double *tr = c->thermo_ring;
+  *bytes = layout(c, nullptr);
+  c->sys = keep;
+  c->eam = ekeep;
+  c->eam_dev = tkeep;
+  c->eam_base = kb;
+  c->thermo_ring = tr;
+  return MDK_OK;
+}
+
+int mdk_set_workspace(mdk_ctx *c, void *dev_ptr, size_t bytes) {
+  if (check_ctx(c) || !dev_ptr || ((uintptr_t)dev_ptr & 255)) return MDK_ERR_BAD_ARG;
+  size_t need = 0;
+  int r = mdk_workspace_size(c, &need);
+  if (r) return r;
+  if (bytes < need) return MDK_ERR_WORKSPACE;
+  c->ws = (char *)dev_ptr;
+  c->ws_bytes = bytes;
+  c->nmax = std::max(c->nmax, c->nmax_grow);
+  c->nmax_grow = 0;
+  c->need_ws = false;
+  layout(c, c->ws);
+  fill_sys_params(c);
+  Sys &s = c->sys;
+  MDK_CK(cudaMemsetAsync(s.st, 0, sizeof(DevStatus), c->stream));
+  MDK_CK(cudaMemsetAsync(s.cell_cnt, 0, sizeof(int32_t) * std::max(c->n_cells, 1), c->stream));
+  MDK_CK(cudaMemcpyAsync(s.grid, c->grids.data(), sizeof(Grid) * c->n_rep,
+                         cudaMemcpyHostToDevice, c->stream));
+  if (c->N > 0)
+    MDK_CK(cudaMemcpyAsync(s.info0, c->info0.data(), sizeof(uint32_t) * c->N,
+                           cudaMemcpyHostToDevice, c->stream));
+  if (c->pot == 2) {
+    EAMParams &e = c->eam;
+    double *kn = reinterpret_cast<double *>(c->eam_base);
+    MDK_CK(cudaMemcpyAsync(kn, c->eam_phi.data(), sizeof(double) * e.nr, cudaMemcpyHostToDevice,
+                           c->stream));
+    MDK_CK(cudaMemcpyAsync(kn + e.nr, c->eam_rho.data(), sizeof(double) * e.nr,
+                           cudaMemcpyHostToDevice, c->stream));
+    MDK_CK(cudaMemcpyAsync(kn + 2 * e.nr, c->eam_F.data(), sizeof(double) * e.nrho,
+                           cudaMemcpyHostToDevice, c->stream));
+    launch_eam_prepare(e, kn, kn + e.nr, kn + 2 * e.nr, c->eam_dev, c->stream);
+    MDK_CK(cudaPeekAtLastError());
+    if (configure_eam_smem(eam_smem_bytes(e, c->precision, 1), eam_smem_bytes(e, c->precision, 2),
+                           c->precision))
+      return MDK_ERR_CUDA;
+  }
+  MDK_CK(cudaStreamSynchronize(c->stream));
+  c->ws_ok = true;
+  c->state_set = false;
+  c->list_built = false;
+  c->forces_valid = false;
+  c->cur = 0;
+  c->thermo_written = c->thermo_read = 0;
+  return MDK_OK;
+}
+
+int mdk_set_state(mdk_ctx *c, const double *x, const double *v, int on_device) {
+  if (check_ctx(c) || (!x && c->N > 0)) return MDK_ERR_BAD_ARG;
+  if (!c->ws_ok) return MDK_ERR_WORKSPACE;
+  Sys &s = c->sys;
+  const double *xd = x, *vd = v;
+  if (!on_device && c->N > 0) {
+    double *stage = s.tmp;
+    MDK_CK(cudaMemcpyAsync(stage, x, sizeof(double) * 3 * c->N, cudaMemcpyHostToDevice, c->stream));
+    xd = stage;
+    vd = nullptr;
+    if (v) {
+      MDK_CK(cudaMemcpyAsync(stage + 3 * c->N, v, sizeof(double) * 3 * c->N,
+                             cudaMemcpyHostToDevice, c->stream));
+      vd = stage + 3 * c->N;
+    }
+  }
+  k_init_status<<<1, 32, 0, c->stream>>>(s, (int)c->N);
+  launch_load_state(s, xd, vd, c->precision, c->cur, c->stream);
+  MDK_CK(cudaPeekAtLastError());
+  c->state_set = true;
+  c->list_built = false;
+  c->forces_valid = false;
+  return MDK_OK;
+}
+
+int mdk_get_state(mdk_ctx *c, double *x, double *v, int on_device) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  if (!c->ws_ok || !c->state_set) return MDK_ERR_ORDER;
+  Sys &s = c->sys;
+  if (c->N == 0) return MDK_OK;
+  if (on_device) {
+    launch_store_state(s, x, v, c->stream);
+    MDK_CK(cudaPeekAtLastError());
+    return MDK_OK;
+  }
+  double *stage = s.tmp;
+  launch_store_state(s, x ? stage : nullptr, v ? stage + 3 * c->N : nullptr, c->stream);
+  if (x)
+    MDK_CK(cudaMemcpyAsync(x, stage, sizeof(double) * 3 * c->N, cudaMemcpyDeviceToHost, c->stream));
+  if (v)
+    MDK_CK(cudaMemcpyAsync(v, stage + 3 * c->N, sizeof(double) * 3 * c->N, cudaMemcpyDeviceToHost,
+                           c->stream));
+  MDK_CK(cudaStreamSynchronize(c->stream));
+  return MDK_OK;
+}
+
+int mdk_get_natoms(const mdk_ctx *c, int64_t *n) {
+  if (!c || !n) return MDK_ERR_BAD_ARG;
+  *n = c->N;
+  return MDK_OK;
+}
+
+int mdk_build_neighbors(mdk_ctx *c, double rc, double skin) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  if (!c->planned || rc != c->rc_list || skin != c->skin) {
+    const int old_nmax = c->nmax, old_cells = c->n_cells;
+    int r = plan(c, rc, skin, c->nmax_req, c->rebuild_every);
+    if (r) return r;
+    if (c->nmax > old_nmax || c->n_cells != old_cells) {
+      c->need_ws = true;
+      return MDK_ERR_WORKSPACE;
+    }
+    c->nmax = old_nmax;
+    fill_sys_params(c);
+  }
+  int r = ensure_ready(c);
+  if (r) return r;
+  return build_now(c);
+}
+
+int mdk_neighbor_count(mdk_ctx *c, int64_t *total) {
+  if (check_ctx(c) || !total) return MDK_ERR_BAD_ARG;
+  if (!c->list_built) return MDK_ERR_ORDER;
+  std::vector<int32_t> nn((size_t)c->N);
+  if (c->N > 0) {
+    MDK_CK(cudaMemcpyAsync(nn.data(), c->sys.nnbr, sizeof(int32_t) * c->N, cudaMemcpyDeviceToHost,
+                           c->stream));
+    MDK_CK(cudaStreamSynchronize(c->stream));
+  }
+  int64_t t = 0;
+  for (int32_t q : nn) t += std::min(q, c->nmax);
+  *total = t;
+  return MDK_OK;
+}
+
+int mdk_get_neighbors(mdk_ctx *c, int64_t *offsets, int32_t *jout, int32_t *img) {
+  if (check_ctx(c) || !offsets) return MDK_ERR_BAD_ARG;
+  if (!c->list_built) return MDK_ERR_ORDER;
+  const int64_t N = c->N;
+  const size_t Nc = (size_t)c->N_cap;
+  Sys &s = c->sys;
+  std::vector<int32_t> nn((size_t)N), id((size_t)N);
+  std::vector<uint32_t> cellc((size_t)N), info((size_t)N);
+  if (N > 0) {
+    MDK_CK(cudaMemcpyAsync(nn.data(), s.nnbr, 4 * N, cudaMemcpyDeviceToHost, c->stream));
+    MDK_CK(cudaMemcpyAsync(id.data(), s.id, 4 * N, cudaMemcpyDeviceToHost, c->stream));
+    MDK_CK(cudaMemcpyAsync(cellc.data(), s.cellc, 4 * N, cudaMemcpyDeviceToHost, c->stream));
+    MDK_CK(cudaMemcpyAsync(info.data(), s.info, 4 * N, cudaMemcpyDeviceToHost, c->stream));
+    MDK_CK(cudaStreamSynchronize(c->stream));
+  }
+  std::vector<int64_t> cnt((size_t)N, 0);
+  for (int64_t i = 0; i < N; ++i) cnt[(size_t)id[(size_t)i]] = std::min(nn[(size_t)i], c->nmax);
+  offsets[0] = 0;
+  for (int64_t i = 0; i < N; ++i) offsets[i + 1] = offsets[i] + cnt[(size_t)i];
+  if (!jout && !img) return MDK_OK;
+  // copy the ELL columns of a chunk of atoms at a time and decode on the host
+  const int64_t chunk = 1 << 16;
+  std::vector<uint32_t> buf;
+  for (int64_t a = 0; a < N; a += chunk) {
+    const int64_t b = std::min(N, a + chunk);
+    int width = 0;
+    for (int64_t i = a; i < b; ++i) width = std::max(width, std::min(nn[(size_t)i], c->nmax));
+    if (width == 0) continue;
+    buf.assign((size_t)(b - a) * width, 0);
+    MDK_CK(cudaMemcpy2DAsync(buf.data(), sizeof(uint32_t) * (b - a), s.nbr + a,
+                             sizeof(uint32_t) * Nc, sizeof(uint32_t) * (b - a), width,
+                             cudaMemcpyDeviceToHost, c->stream));
+    MDK_CK(cudaStreamSynchronize(c->stream));
+    for (int64_t i = a; i < b; ++i) {
+      const int64_t base = offsets[id[(size_t)i]];
+      const int k_n = std::min(nn[(size_t)i], c->nmax);
+      const Grid &g = c->grids[info[(size_t)i] >> 8];
+      for (int k = 0; k < k_n; ++k) {
+        const uint32_t e = buf[(size_t)k * (b - a) + (i - a)];
+        const int j = (int)(e & kJMask);
+        if (jout) jout[base + k] = id[(size_t)j];
+        if (img)
+          for (int d = 0; d < 3; ++d) {
+            const int sd = (int)((e >> (26 + 2 * d)) & 3u) - 1;
+            const int cd = cell_coord(cellc[(size_t)i], d) + sd;
+            int n = 0;
+            if (g.per[d]) n = cd < 0 ? -1 : (cd >= g.nc[d] ? 1 : 0);
+            img[3 * (base + k) + d] = n;
+          }
+      }
+    }
+  }
+  return MDK_OK;
+}
+
+int mdk_compute(mdk_ctx *c, double *E, double *F, double *virial, int on_device) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  int r = ensure_ready(c);
+  if (r) return r;
+  if (!c->list_built) {
+    r = build_now(c);
+    if (r) return r;
+  }
+  Sys &s = c->sys;
+  r = force_pass(c, kForceOnly, 1, 0.0);
+  if (r) return r;
+  launch_reduce(s, 0, c->stream);
+  c->launches += 1;
+  MDK_CK(cudaPeekAtLastError());
+  c->forces_valid = true;
+  const int R = c->n_rep;
+  if (on_device) {
+    if (F) launch_store_forces(s, F, c->stream);
+    for (int q = 0; q < R; ++q) {
+      if (E) MDK_CK(cudaMemcpyAsync(E + q, s.red + 9 * q + 1, sizeof(double),
+                                    cudaMemcpyDeviceToDevice, c->stream));
+      if (virial) MDK_CK(cudaMemcpyAsync(virial + 6 * q, s.red + 9 * q + 2, 6 * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, c->stream));
+    }
+    MDK_CK(cudaPeekAtLastError());
+    return MDK_OK;
+  }
+  std::vector<double> red((size_t)9 * R);
+  MDK_CK(cudaMemcpyAsync(red.data(), s.red, sizeof(double) * 9 * R, cudaMemcpyDeviceToHost,
+                         c->stream));
+  if (F && c->N > 0) {
+    launch_store_forces(s, s.tmp, c->stream);
+    MDK_CK(cudaMemcpyAsync(F, s.tmp, sizeof(double) * 3 * c->N, cudaMemcpyDeviceToHost, c->stream));
+  }
+  DevStatus st;
+  r = read_status(c, &st);
+  if (r) return r;
+  for (int q = 0; q < R; ++q) {
+    if (E) E[q] = red[(size_t)9 * q + 1];
+    if (virial)
+      for (int k = 0; k < 6; ++k) virial[6 * q + k] = red[(size_t)9 * q + 2 + k];
+  }
+  return status_from_bits(st.bits);
+}
+
+int mdk_get_per_atom(mdk_ctx *c, double *Ui, double *Wi) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  if (!c->forces_valid) return MDK_ERR_ORDER;
+  if (c->N == 0) return MDK_OK;
+  Sys &s = c->sys;
+  double *stage = s.tmp;
+  launch_store_per_atom(s, Ui ? stage : nullptr, Wi ? stage + c->N : nullptr, c->stream);
+  if (Ui) MDK_CK(cudaMemcpyAsync(Ui, stage, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
+  if (Wi)
+    MDK_CK(cudaMemcpyAsync(Wi, stage + c->N, sizeof(double) * 6 * c->N, cudaMemcpyDeviceToHost,
+                           c->stream));
+  MDK_CK(cudaStreamSynchronize(c->stream));
+  return MDK_OK;
+}
+
+int mdk_step(mdk_ctx *c, double dt, int64_t nsteps) {
+  if (check_ctx(c) || nsteps < 0 || !(dt > 0.0)) return MDK_ERR_BAD_ARG;
+  int r = ensure_ready(c);
+  if (r) return r;
+  if (nsteps == 0) return MDK_OK;
+  if (!c->list_built) {
+    r = build_now(c);
+    if (r) return r;
+  }
+  Sys &s = c->sys;
+  if (!c->forces_valid) {
+    r = force_pass(c, kForceOnly, 0, dt);
+    if (r) return r;
+  }
+  StepArgs a{dt, c->cur, 0};
+  r = timed(c, c->ev_kick, 1, [&] { launch_kick_drift(s, c->precision, a, c->stream); });
+  if (r) return r;
+  c->cur ^= 1;
+  r = rebuild_chain(c, 1);
+  if (r) return r;
+  for (int64_t q = 1; q <= nsteps; ++q) {
+    const int64_t gstep = c->steps_done + q;
+    const int thermo = c->thermo_every > 0 && (gstep % c->thermo_every) == 0;
+    const bool last = q == nsteps;
+    r = force_pass(c, last ? kFinal : kStep, thermo, dt);
+    if (r) return r;
+    if (thermo) {
+      launch_reduce(s, 1, c->stream);
+      c->launches += 2;
+      const int slot = (int)(c->thermo_written % std::max(c->thermo_cap, 1));
+      k_thermo_store<<<1, std::max(32, ((c->n_rep + 31) / 32) * 32), 0, c->stream>>>(
+          s, c->thermo_ring, slot, (double)gstep);
+      c->thermo_written++;
+    }
+    if (!last) {
+      c->cur ^= 1;
+      r = rebuild_chain(c, 1);
+      if (r) return r;
+    }
+  }
+  MDK_CK(cudaPeekAtLastError());
+  c->steps_done += nsteps;
+  c->forces_valid = true;
+  return MDK_OK;
+}
+
+int mdk_set_thermo(mdk_ctx *c, int every, int capacity) {
+  if (check_ctx(c) || every < 0 || capacity < 0) return MDK_ERR_BAD_ARG;
+  if (capacity > c->thermo_cap) c->ws_ok = false;  // ring lives in the workspace
+  c->thermo_every = every;
+  c->thermo_cap = std::max(capacity, c->thermo_cap);
+  c->thermo_written = c->thermo_read = 0;
+  return c->ws_ok ? MDK_OK : MDK_ERR_WORKSPACE;
+}
+
+int mdk_get_thermo(mdk_ctx *c, double *out, int max_samples, int *n_out) {
+  if (check_ctx(c) || !n_out) return MDK_ERR_BAD_ARG;
+  *n_out = 0;
+  if (!c->ws_ok) return MDK_ERR_WORKSPACE;
+  const int cap = std::max(c->thermo_cap, 1);
+  int64_t first = std::max(c->thermo_read, c->thermo_written - cap);
+  const int per = c->n_rep * 10;
+  std::vector<double> ring((size_t)cap * per);
+  MDK_CK(cudaMemcpyAsync(ring.data(), c->thermo_ring, sizeof(double) * ring.size(),
+                         cudaMemcpyDeviceToHost, c->stream));
+  MDK_CK(cudaStreamSynchronize(c->stream));
+  int n = 0;
+  for (int64_t q = first; q < c->thermo_written && n < max_samples; ++q, ++n)
+    memcpy(out + (size_t)n * per, ring.data() + (size_t)(q % cap) * per, sizeof(double) * per);
+  c->thermo_read = first + n;
+  *n_out = n;
+  return MDK_OK;
+}
+
+int mdk_get_counters(mdk_ctx *c, int64_t *n_builds, int64_t *n_steps) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  if (!c->ws_ok) return MDK_ERR_WORKSPACE;
+  DevStatus st;
+  int r = read_status(c, &st);
+  if (r) return r;
+  if (n_builds) *n_builds = st.n_builds;
+  if (n_steps) *n_steps = c->steps_done;
+  return MDK_OK;
+}
+
+int mdk_last_device_status(mdk_ctx *c, int *bits) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  if (!c->ws_ok) return MDK_ERR_WORKSPACE;
+  DevStatus st;
+  int r = read_status(c, &st);
+  if (r) return r;
+  if (bits) *bits = (int)st.bits;
+  if (st.bits & kStOverflow) {
+    c->nmax_grow = ((int)ceil(st.max_nnbr * 1.25) + 8 + 3) & ~3;
+    c->need_ws = true;
+    c->list_built = false;
+  }
+  k_clear_bits<<<1, 32, 0, c->stream>>>(c->sys);
+  MDK_CK(cudaPeekAtLastError());
+  return status_from_bits(st.bits);
+}
+
+int mdk_set_piston(mdk_ctx *c, double u_p, const uint8_t *is_piston) {
+  if (check_ctx(c) || !isfinite(u_p)) return MDK_ERR_BAD_ARG;
+  if (!c->ws_ok || !c->state_set) return MDK_ERR_ORDER;
+  c->u_p = u_p;
+  c->sys.u_p = u_p;
+  const uint8_t *dflags = nullptr;
+  if (is_piston && c->N > 0) {
+    uint8_t *stage = reinterpret_cast<uint8_t *>(c->sys.tmp);
+    MDK_CK(cudaMemcpyAsync(stage, is_piston, (size_t)c->N, cudaMemcpyHostToDevice, c->stream));
+    dflags = stage;
+  }
+  k_set_piston<<<(unsigned)((c->N_cap + 255) / 256 + 1), 256, 0, c->stream>>>(c->sys, dflags);
+  MDK_CK(cudaPeekAtLastError());
+  MDK_CK(cudaStreamSynchronize(c->stream));
+  // the gather copies carry the info word: regenerate them with a rebuild
+  if (c->list_built) return build_now(c);
+  return MDK_OK;
+}
+
+int mdk_profile(mdk_ctx *c, int enable) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  if (c->ws_ok) MDK_CK(cudaStreamSynchronize(c->stream));
+  c->prof = enable != 0;
+  c->ev_used = 0;
+  c->ev_force.clear();
+  c->ev_chain.clear();
+  c->ev_kick.clear();
+  c->launches = 0;
+  return MDK_OK;
+}
+
+int mdk_get_profile(mdk_ctx *c, double *out) {
+  if (check_ctx(c) || !out) return MDK_ERR_BAD_ARG;
+  if (!c->ws_ok) return MDK_ERR_WORKSPACE;
+  DevStatus st;
+  int r = read_status(c, &st);
+  if (r) return r;
+  auto total = [&](const std::vector<std::pair<int, int>> &v) {
+    double ms = 0.0;
+    for (const auto &p : v) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, c->ev_pool[(size_t)p.first], c->ev_pool[(size_t)p.second]) ==
+          cudaSuccess)
+        ms += t;
+    }
+    return ms;
+  };
+  out[0] = total(c->ev_force);
+  out[1] = (double)c->ev_force.size();
+  out[2] = total(c->ev_chain);
+  out[3] = (double)c->ev_chain.size();
+  out[4] = (double)c->launches;
+  out[5] = (double)st.n_builds;
+  out[6] = total(c->ev_kick);
+  out[7] = (double)c->ev_kick.size();
+  return MDK_OK;
+}
+
+int mdk_set_window(mdk_ctx *c, double, double, const double *, const double *, int64_t, double,
+                   double, double) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  return MDK_ERR_BAD_ARG;
+}
+
+int mdk_profiles(mdk_ctx *c, int, double, double, int, double, double *, int) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  return MDK_ERR_BAD_ARG;
+}
+
+}  // extern "C"

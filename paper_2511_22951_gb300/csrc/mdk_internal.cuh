@@ -1,0 +1,234 @@
+// mdk_internal.cuh -- device-side data layout shared by the CUDA sources of
+// libmdk.so (GB300, sm_103a).  Nothing here is visible through the C ABI.
+//
+// Layout in HBM (all inside the caller's workspace, atoms in cell order):
+//   x, v, f, xref : FP64 SoA, component c of atom i at [c * N_cap + i]
+//   pf            : float4 per atom, position relative to its cell origin
+//                   (x - O(cell)) with the info word in .w; written at each
+//                   list build, used by the build's FP32 pre-filter
+//   pg[2]         : per-step gather copy, double-buffered; float4 (mixed) or
+//                   double4 (FP64) of x - O(cell) with info in .w
+//   info          : type (bits 0-3) | piston (bit 4) | far (bit 5) |
+//                   replica (bits 8-31)
+//   nbr           : ELL Verlet lists, entry k of atom i at [k * N_cap + i],
+//                   packed j (bits 0-25) | (s_x+1) << 26 | (s_y+1) << 28 |
+//                   (s_z+1) << 30, s = stencil offset of j's cell
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mdk {
+
+// 1 eV/(Angstrom u) in Angstrom/fs^2 (elementary charge / atomic mass unit,
+// 1e-10 m, 1e-30 s^2).
+constexpr double kAcc = 9.648533212331e-3;
+
+constexpr int kMaxTypes = 16;
+constexpr uint32_t kJMask = (1u << 26) - 1u;
+constexpr uint32_t kInfoPiston = 1u << 4;
+constexpr uint32_t kInfoFar = 1u << 5;
+
+// device status bits
+enum : unsigned {
+  kStOverflow = 1u,
+  kStNonfinite = 2u,
+  kStRhoRange = 4u,
+  kStAtomLost = 8u,
+  kStTimeout = 16u,
+};
+
+struct DevStatus {
+  int N;                 // atoms present
+  int rebuild;           // != 0: rebuild the lists before the next force pass
+  unsigned bits;         // kSt* raised since the host last cleared them
+  int max_nnbr;          // longest list seen at a build
+  long long n_builds;
+  long long n_steps;
+  int since_build;       // steps since the last build
+  int pad0;
+  double scratch[4];
+};
+
+// one replica's box and cell grid
+struct Grid {
+  double lo[3], hi[3], L[3], h[3], inv_h[3];
+  float hf[3];
+  int nc[3];
+  int per[3];
+  int cell_off;   // first global cell id of this replica
+  int atom_off;   // first atom of this replica (atoms stay grouped by replica)
+  int n_atoms;
+};
+
+struct Sys {
+  // sizes
+  int N_cap;
+  int nmax;
+  int n_rep;
+  int n_cells;
+  int n_scan_blocks;
+  // per-atom arrays
+  double *x, *v, *f, *xref;
+  double *tmp;              // 9 * N_cap doubles of sort scratch
+  uint32_t *info, *cellc, *tmpu, *info0;
+  int32_t *id, *tmpi;
+  float4 *pf;
+  void *pg[2];
+  int32_t *nnbr;
+  uint32_t *nbr;
+  double *ea, *ka, *wa;     // per-atom U_i, K_i, W_i[6] (SoA)
+  double *rho;
+  void *fp;                 // F'(rho_i): double (FP64) or float (mixed)
+  // cell sort scratch
+  int32_t *cell_cnt, *cell_start, *cell_fill, *cell_of, *order, *scan_part;
+  Grid *grid;
+  DevStatus *st;
+  double *red;              // reductions: per replica [K, U, W0..W5, N]
+  // list parameters
+  double rns2;              // (rc + skin)^2
+  float filt_lo, filt_hi;   // FP32 pre-filter band around rns2
+  double half_skin2;        // (skin/2)^2
+  int rebuild_every;
+  // integration
+  double acc_over_m[kMaxTypes];   // kAcc / m for each type
+  double ke_m[kMaxTypes];         // m / (2 kAcc): K in eV from v^2
+  double u_p;                     // piston speed
+};
+
+struct LJParams {
+  double eps4, eps24, sig2, rc2, u_shift, du_rc, rc;
+  float eps4f, eps24f, sig2f, rc2f, u_shiftf, du_rcf, rcf;
+  int shift_mode;
+};
+
+struct EAMParams {
+  int nr, nrho;
+  double rc, rc2, inv_dr, dr, rho_max, inv_drho, drho;
+  float rc2f, inv_drf;
+  // FP64 knot tables (value, h * slope) per knot
+  const double2 *phi64, *rho64, *F64;
+  // FP32 tables of the mixed path, rounded from FP64 quantities so that no
+  // FP32 subtraction of neighbouring knot values is needed:
+  //   rho_i32[k] = (y_k, y_{k+1} - y_k, h m_k, h m_{k+1})   (pass 1, rho value)
+  //   phi_d32[k], rho_d32[k] = (y_{k+1} - y_k, h m_k)         (pass 2, slopes)
+  //   phi_v32[k] = y_k                                         (pass 2 energy)
+  const float4 *rho_i32;
+  const float2 *phi_d32, *rho_d32;
+  const float *phi_v32;
+};
+
+// writable view of the device tables filled by launch_eam_prepare
+struct EAMTablesDev {
+  double2 *phi64, *rho64, *F64;
+  float4 *rho_i32;
+  float2 *phi_d32, *rho_d32;
+  float *phi_v32;
+};
+
+// Centre of cell c along d.  Gather copies hold x - centre, so |p| <= h/2
+// right after a build (h/2 + skin/2 later); the build and every step use
+// this one expression, so the offsets of one list lifetime are consistent.
+__device__ __forceinline__ double cell_center(const Grid &g, int d, int c) {
+  return g.lo[d] + ((double)c + 0.5) * g.h[d];
+}
+
+__device__ __forceinline__ uint32_t pack_nbr(int j, int sx, int sy, int sz) {
+  return (uint32_t)j | ((uint32_t)(sx + 1) << 26) | ((uint32_t)(sy + 1) << 28) |
+         ((uint32_t)(sz + 1) << 30);
+}
+__device__ __forceinline__ int nbr_s(uint32_t e, int d) {
+  return (int)((e >> (26 + 2 * d)) & 3u) - 1;
+}
+__host__ __device__ __forceinline__ uint32_t pack_cell(int cx, int cy, int cz) {
+  return (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
+}
+__host__ __device__ __forceinline__ int cell_coord(uint32_t c, int d) {
+  return (int)((c >> (10 * d)) & 1023u);
+}
+
+// 32-byte FP64 gather-copy element (x, y, z, info bits in w)
+struct alignas(32) dvec4 {
+  double x, y, z, w;
+};
+
+// precision traits of the per-step gather copy
+struct Fp64 {
+  using real = double;
+  using vec4 = dvec4;
+  static __device__ __forceinline__ uint32_t info(const dvec4 &p) {
+    return (uint32_t)__double_as_longlong(p.w);
+  }
+  static __device__ __forceinline__ dvec4 make(double a, double b, double c, uint32_t w) {
+    dvec4 r;
+    r.x = a;
+    r.y = b;
+    r.z = c;
+    r.w = __longlong_as_double((long long)w);
+    return r;
+  }
+};
+struct Mixed {
+  using real = float;
+  using vec4 = float4;
+  static __device__ __forceinline__ uint32_t info(const float4 &p) {
+    return __float_as_uint(p.w);
+  }
+  static __device__ __forceinline__ float4 make(double a, double b, double c, uint32_t w) {
+    return make_float4((float)a, (float)b, (float)c, __uint_as_float(w));
+  }
+};
+
+// a per-atom sum: plain in FP64; Kahan-compensated in FP32
+template <class R>
+struct Acc;
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct Acc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
+// launch helpers implemented in the .cu files --------------------------------
+enum Mode { kForceOnly = 0, kStep = 1, kFinal = 2 };
+
+struct StepArgs {
+  double dt;
+  int cur;              // gather copy read this step (pg[cur]); pg[cur^1] written
+  int energy;           // compute per-atom energies / virials this step
+};
+
+void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, cudaStream_t st);
+int scan_blocks_for(int n_cells);
+void launch_set_rebuild_flag(const Sys &s, cudaStream_t st);
+void launch_lj(const Sys &s, const LJParams &p, int precision, Mode mode, StepArgs a,
+               cudaStream_t st);
+void launch_eam(const Sys &s, const EAMParams &p, int precision, Mode mode, StepArgs a,
+                cudaStream_t st);
+void launch_kick_drift(const Sys &s, int precision, StepArgs a, cudaStream_t st);
+void launch_reduce(const Sys &s, int with_ke, cudaStream_t st);
+void launch_eam_prepare(const EAMParams &p, const double *phi, const double *rho,
+                        const double *F, EAMTablesDev out, cudaStream_t st);
+void launch_load_state(const Sys &s, const double *x_aos, const double *v_aos,
+                       int precision, int target_pg, cudaStream_t st);
+void launch_store_state(const Sys &s, double *x_aos, double *v_aos, cudaStream_t st);
+void launch_store_forces(const Sys &s, double *f_aos, cudaStream_t st);
+void launch_store_per_atom(const Sys &s, double *ua, double *wa, cudaStream_t st);
+void launch_export_neighbors(const Sys &s, const int64_t *offsets, int32_t *jout,
+                             int32_t *imgout, cudaStream_t st);
+void launch_neighbor_counts(const Sys &s, int64_t *counts_orig, cudaStream_t st);
+int eam_smem_bytes(const EAMParams &p, int precision, int pass);
+int configure_eam_smem(int bytes_pass1, int bytes_pass2, int precision);
+
+}  // namespace mdk

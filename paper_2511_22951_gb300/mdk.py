@@ -1,0 +1,364 @@
+"""Python binding of libmdk.so: the C-ABI functions under their own names,
+plus a small `Context` class that does the argument marshalling.
+
+Only marshalling happens here: device memory comes from torch (one uint8
+workspace tensor per context), streams from torch.cuda, and every step of the
+MD path runs in the library's CUDA kernels.  There is no CPU fallback: if the
+extension is missing the import fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmdk.so")
+
+MDK_OK = 0
+MDK_ERR_BAD_ARG = -1
+MDK_ERR_BOX_TOO_SMALL = -2
+MDK_ERR_NEIGH_OVERFLOW = -3
+MDK_ERR_ATOM_LOST = -4
+MDK_ERR_NONFINITE = -5
+MDK_ERR_TIMEOUT = -6
+MDK_ERR_CUDA = -7
+MDK_ERR_WORKSPACE = -8
+MDK_ERR_ORDER = -9
+MDK_ERR_RHO_RANGE = -10
+MDK_FP64 = 0
+MDK_MIXED = 1
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+
+# name -> argtypes (restype int unless noted)
+SIGNATURES = {
+    "mdk_create": [ctypes.POINTER(_P), _P, _P, _P, _I64, _P, _I, _P],
+    "mdk_create_batch": [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _P, _I, _P],
+    "mdk_destroy": [_P],
+    "mdk_set_capacity": [_P, _I64],
+    "mdk_set_potential_lj": [_P, _D, _D, _D, _I],
+    "mdk_set_potential_eam": [_P, _I, _D, _P, _P, _I, _D, _P],
+    "mdk_workspace_size": [_P, ctypes.POINTER(_SZ)],
+    "mdk_set_workspace": [_P, _P, _SZ],
+    "mdk_set_state": [_P, _P, _P, _I],
+    "mdk_get_state": [_P, _P, _P, _I],
+    "mdk_get_natoms": [_P, ctypes.POINTER(_I64)],
+    "mdk_plan_neighbors": [_P, _D, _D, _I, _I],
+    "mdk_build_neighbors": [_P, _D, _D],
+    "mdk_neighbor_count": [_P, ctypes.POINTER(_I64)],
+    "mdk_get_neighbors": [_P, _P, _P, _P],
+    "mdk_compute": [_P, _P, _P, _P, _I],
+    "mdk_get_per_atom": [_P, _P, _P],
+    "mdk_step": [_P, _D, _I64],
+    "mdk_set_thermo": [_P, _I, _I],
+    "mdk_get_thermo": [_P, _P, _I, ctypes.POINTER(_I)],
+    "mdk_get_counters": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
+    "mdk_set_piston": [_P, _D, _P],
+    "mdk_set_window": [_P, _D, _D, _P, _P, _I64, _D, _D, _D],
+    "mdk_profiles": [_P, _I, _D, _D, _I, _D, _P, _I],
+    "mdk_status_string": [_I],
+    "mdk_last_device_status": [_P, ctypes.POINTER(_I)],
+    "mdk_profile": [_P, _I],
+    "mdk_get_profile": [_P, _P],
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmdk.so and declare every C-ABI function.  Raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"libmdk.so not found at {path}: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc, sm_103a)")
+    lib = ctypes.CDLL(path)
+    for name, args in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "mdk_status_string" else _I
+    _lib = lib
+    return lib
+
+
+class MDKError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = load().mdk_status_string(code).decode()
+        super().__init__(f"{what}: {msg} ({code})")
+
+
+def _check(code: int, what: str):
+    if code != MDK_OK:
+        raise MDKError(code, what)
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(_P)
+    return _P(a.data_ptr())
+
+
+def _host_f64(a, shape):
+    return np.ascontiguousarray(a, dtype=np.float64).reshape(shape)
+
+
+class Context:
+    """One MD system (or a batch of replicas) on the current CUDA device.
+
+    Device memory: a single torch uint8 tensor (the workspace) that the
+    library lays out; it is reallocated when a call reports that it is too
+    small (list capacity growth, new potential table sizes).
+    """
+
+    def __init__(self, lo, hi, periodic, masses, precision="fp64", stream=None,
+                 device=None, n_atoms=None, capacity=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda")
+        self.prec = MDK_FP64 if precision in ("fp64", MDK_FP64) else MDK_MIXED
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        masses = np.ascontiguousarray(masses, dtype=np.float64).ravel()
+        h = _P()
+        if n_atoms is None:
+            lo_ = _host_f64(lo, (3,))
+            hi_ = _host_f64(hi, (3,))
+            per = np.ascontiguousarray(periodic, dtype=np.int32).reshape(3)
+            _check(self.lib.mdk_create(ctypes.byref(h), _ptr(lo_), _ptr(hi_), _ptr(per),
+                                       masses.shape[0], _ptr(masses), self.prec,
+                                       _P(self.stream.cuda_stream)), "mdk_create")
+            self.n_rep = 1
+        else:
+            n_atoms = np.ascontiguousarray(n_atoms, dtype=np.int64).ravel()
+            R = n_atoms.shape[0]
+            lo_ = _host_f64(lo, (R, 3))
+            hi_ = _host_f64(hi, (R, 3))
+            per = np.ascontiguousarray(periodic, dtype=np.int32).reshape(R, 3)
+            _check(self.lib.mdk_create_batch(ctypes.byref(h), R, _ptr(lo_), _ptr(hi_),
+                                             _ptr(per), _ptr(n_atoms), _ptr(masses),
+                                             self.prec, _P(self.stream.cuda_stream)),
+                   "mdk_create_batch")
+            self.n_rep = R
+        self.h = h
+        self.n = masses.shape[0]
+        self.ws = None
+        self._state = None
+        self._has_state = False
+        if capacity is not None:
+            _check(self.lib.mdk_set_capacity(self.h, int(capacity)), "mdk_set_capacity")
+
+    # -- lifetime -------------------------------------------------------------
+    def close(self):
+        if self.h:
+            self.lib.mdk_destroy(self.h)
+            self.h = _P()
+        self.ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- setup ----------------------------------------------------------------
+    def set_potential_lj(self, eps, sigma, rc, shift_mode=1):
+        _check(self.lib.mdk_set_potential_lj(self.h, eps, sigma, rc, shift_mode),
+               "mdk_set_potential_lj")
+
+    def set_potential_eam(self, tables):
+        phi = _host_f64(tables.phi, (-1,))
+        rho = _host_f64(tables.rho, (-1,))
+        F = _host_f64(tables.F, (-1,))
+        _check(self.lib.mdk_set_potential_eam(self.h, phi.shape[0], tables.rc, _ptr(phi),
+                                              _ptr(rho), F.shape[0], tables.rho_max, _ptr(F)),
+               "mdk_set_potential_eam")
+
+    def plan(self, rc, skin, max_neighbors=0, rebuild_every=0):
+        _check(self.lib.mdk_plan_neighbors(self.h, rc, skin, max_neighbors, rebuild_every),
+               "mdk_plan_neighbors")
+
+    def workspace_bytes(self) -> int:
+        b = _SZ()
+        _check(self.lib.mdk_workspace_size(self.h, ctypes.byref(b)), "mdk_workspace_size")
+        return int(b.value)
+
+    def alloc_workspace(self):
+        if self.ws is not None and self._has_state:
+            try:  # keep the current state across the new workspace
+                self._save_state()
+            except MDKError:
+                pass
+        nbytes = self.workspace_bytes()
+        self.ws = self.torch.empty(nbytes + 256, dtype=self.torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        off = (-base) % 256
+        _check(self.lib.mdk_set_workspace(self.h, _P(base + off), nbytes), "mdk_set_workspace")
+        if self._state is not None:
+            x, v, on_dev = self._state
+            _check(self.lib.mdk_set_state(self.h, _ptr(x), _ptr(v), on_dev), "mdk_set_state")
+
+    def set_thermo(self, every, capacity=1024):
+        r = self.lib.mdk_set_thermo(self.h, every, capacity)
+        if r == MDK_ERR_WORKSPACE:
+            if self.ws is not None:
+                self.alloc_workspace()
+        else:
+            _check(r, "mdk_set_thermo")
+
+    # -- state ----------------------------------------------------------------
+    def set_state(self, x, v=None):
+        """x, v: numpy (host) or torch CUDA tensors, shape [N, 3] float64."""
+        if self.ws is None:
+            self.alloc_workspace()
+        if isinstance(x, np.ndarray):
+            x = _host_f64(x, (self.n, 3))
+            v = None if v is None else _host_f64(v, (self.n, 3))
+            on_dev = 0
+        else:
+            on_dev = 1
+        self._state = (x, v, on_dev)
+        self._has_state = True
+        _check(self.lib.mdk_set_state(self.h, _ptr(x), _ptr(v), on_dev), "mdk_set_state")
+
+    def _save_state(self):
+        x, v = self.get_state()
+        self._state = (x, v, 0)
+
+    def get_state(self):
+        n = self.natoms()
+        x = np.zeros((n, 3))
+        v = np.zeros((n, 3))
+        _check(self.lib.mdk_get_state(self.h, _ptr(x), _ptr(v), 0), "mdk_get_state")
+        return x, v
+
+    def natoms(self) -> int:
+        n = _I64()
+        _check(self.lib.mdk_get_natoms(self.h, ctypes.byref(n)), "mdk_get_natoms")
+        return int(n.value)
+
+    # -- neighbours -------------------------------------------------------------
+    def build_neighbors(self, rc, skin):
+        for _ in range(4):
+            r = self.lib.mdk_build_neighbors(self.h, rc, skin)
+            if r in (MDK_ERR_NEIGH_OVERFLOW, MDK_ERR_WORKSPACE):
+                # capacity raised or new plan: resize the workspace, restore the state
+                self.alloc_workspace()
+                continue
+            _check(r, "mdk_build_neighbors")
+            return
+        raise MDKError(MDK_ERR_NEIGH_OVERFLOW, "mdk_build_neighbors")
+
+    def neighbor_counts(self):
+        """Number of list entries of every atom (caller's order)."""
+        n = self.natoms()
+        off = np.zeros(n + 1, dtype=np.int64)
+        _check(self.lib.mdk_get_neighbors(self.h, _ptr(off), None, None), "mdk_get_neighbors")
+        return np.diff(off)
+
+    def neighbors(self):
+        """(offsets[N+1], j[total], image[total,3]) in the caller's atom order."""
+        n = self.natoms()
+        tot = _I64()
+        _check(self.lib.mdk_neighbor_count(self.h, ctypes.byref(tot)), "mdk_neighbor_count")
+        off = np.zeros(n + 1, dtype=np.int64)
+        j = np.zeros(max(tot.value, 1), dtype=np.int32)
+        im = np.zeros((max(tot.value, 1), 3), dtype=np.int32)
+        _check(self.lib.mdk_get_neighbors(self.h, _ptr(off), _ptr(j), _ptr(im)),
+               "mdk_get_neighbors")
+        return off, j[:tot.value], im[:tot.value]
+
+    # -- compute / step -----------------------------------------------------------
+    def compute(self):
+        """Host results: (E [n_rep], F [N,3], virial [n_rep,6])."""
+        n = self.natoms()
+        E = np.zeros(self.n_rep)
+        F = np.zeros((n, 3))
+        W = np.zeros((self.n_rep, 6))
+        r = self.lib.mdk_compute(self.h, _ptr(E), _ptr(F), _ptr(W), 0)
+        if r in (MDK_ERR_NEIGH_OVERFLOW, MDK_ERR_WORKSPACE):
+            self.alloc_workspace()
+            r = self.lib.mdk_compute(self.h, _ptr(E), _ptr(F), _ptr(W), 0)
+        _check(r, "mdk_compute")
+        return E, F, W
+
+    def compute_device(self, E, F, W):
+        _check(self.lib.mdk_compute(self.h, _ptr(E), _ptr(F), _ptr(W), 1), "mdk_compute")
+
+    def per_atom(self):
+        n = self.natoms()
+        U = np.zeros(n)
+        Wa = np.zeros((n, 6))
+        _check(self.lib.mdk_get_per_atom(self.h, _ptr(U), _ptr(Wa)), "mdk_get_per_atom")
+        return U, Wa
+
+    def step(self, dt, nsteps, check=True):
+        _check(self.lib.mdk_step(self.h, dt, int(nsteps)), "mdk_step")
+        if check:
+            self.check()
+
+    def check(self):
+        bits = _I()
+        _check(self.lib.mdk_last_device_status(self.h, ctypes.byref(bits)),
+               "device status")
+
+    def thermo(self, max_samples=100000):
+        out = np.zeros((max_samples, self.n_rep, 10))
+        n = _I()
+        _check(self.lib.mdk_get_thermo(self.h, _ptr(out), max_samples, ctypes.byref(n)),
+               "mdk_get_thermo")
+        return out[:n.value]
+
+    def counters(self):
+        b, s = _I64(), _I64()
+        _check(self.lib.mdk_get_counters(self.h, ctypes.byref(b), ctypes.byref(s)),
+               "mdk_get_counters")
+        return int(b.value), int(s.value)
+
+    def profile(self, enable=True):
+        _check(self.lib.mdk_profile(self.h, 1 if enable else 0), "mdk_profile")
+
+    def get_profile(self):
+        out = np.zeros(8)
+        _check(self.lib.mdk_get_profile(self.h, _ptr(out)), "mdk_get_profile")
+        keys = ("force_ms", "force_passes", "rebuild_ms", "rebuild_chains", "kernels",
+                "builds", "kick_ms", "kicks")
+        return dict(zip(keys, out.tolist()))
+
+    def set_piston(self, u_p, flags):
+        f = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8)
+        _check(self.lib.mdk_set_piston(self.h, u_p, _ptr(f)), "mdk_set_piston")
+
+
+def make_context(wl, precision=None, stream=None, rebuild_every=0, max_neighbors=0):
+    """Context for a workloads.Workload: potential, plan, workspace, state, lists."""
+    prec = precision or wl.precision
+    if len(wl.systems) == 1:
+        s = wl.systems[0]
+        ctx = Context(s.lo, s.hi, s.periodic, s.masses, prec, stream)
+    else:
+        ss = wl.systems
+        ctx = Context([q.lo for q in ss], [q.hi for q in ss], [q.periodic for q in ss],
+                      np.concatenate([q.masses for q in ss]), prec, stream,
+                      n_atoms=[q.n for q in ss])
+    if wl.potential == "lj":
+        ctx.set_potential_lj(wl.lj.eps, wl.lj.sigma, wl.lj.rc, wl.lj.shift_mode)
+    else:
+        ctx.set_potential_eam(wl.tables)
+    ctx.plan(wl.rc, wl.skin, max_neighbors, rebuild_every)
+    x = np.concatenate([q.x for q in wl.systems])
+    v = np.concatenate([q.v for q in wl.systems])
+    ctx.set_state(x, v)
+    ctx.build_neighbors(wl.rc, wl.skin)
+    return ctx
