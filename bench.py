@@ -49,13 +49,13 @@ def peaks():
 
 
 # ---------------------------------------------------------------------------
-def workload(cfg: int):
+def workload(cfg: int, cells: int = 128):
     if cfg == 0:
         return W.config0()
     if cfg == 1:
         return W.config1()
     if cfg == 2:
-        return W.config2()
+        return W.config2(n=cells)
     raise SystemExit(f"config {cfg} is not a bench workload")
 
 
@@ -191,6 +191,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--cells", type=int, default=128, help="FCC cells per side (config 2)")
     ap.add_argument("--precision", default=None)
     ap.add_argument("--impl", default="mdk")
     ap.add_argument("--fp64-steps", type=int, default=20)
@@ -198,7 +199,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
-    wl = workload(args.config)
+    wl = workload(args.config, args.cells)
     if args.impl == "reference":
         return run_reference(args, wl)
 
