@@ -55,6 +55,8 @@ extern "C" {
 #define MDK_ERR_ORDER (-9)          /* call made before a required call    */
 #define MDK_ERR_RHO_RANGE (-10)     /* an EAM density left the F table
                                        (F was extrapolated linearly)       */
+#define MDK_ERR_TOO_LARGE (-11)     /* size above the fixed maximum of
+                                       mdk_lj_compute_noalloc             */
 
 /* ---- precision modes ---------------------------------------------------- */
 #define MDK_FP64 0  /* every operation in FP64                               */
@@ -270,6 +272,49 @@ int mdk_set_window(mdk_ctx *ctx, double L_behind, double L_ahead,
  */
 int mdk_profiles(mdk_ctx *ctx, int axis, double origin, double bin_w, int nbins,
                  double cross_area, double *out, int on_device);
+
+/* ---- allocation-free variant ------------------------------------------------ */
+
+/* Fixed maximum sizes of mdk_lj_compute_noalloc. */
+#define MDK_NOALLOC_MAX_ATOMS 32768
+#define MDK_NOALLOC_MAX_CELLS 32768
+
+/*
+ * Lennard-Jones energy and forces of one small system, for callers that
+ * cannot allocate device memory: code whose device memory is owned by
+ * another allocator (a framework's caching pool or a fixed arena reserved at
+ * start-up, where an extra cudaMalloc would fail or fragment it), or a host
+ * loop that must not pay for an allocation or the device-wide
+ * synchronisation cudaFree implies.  This entry point allocates nothing and
+ * needs no context or workspace.  (No counterpart in the paper; it is a
+ * variant of the force kernel behind mdk_compute.)
+ *
+ * Its scratch (cell histogram and starts, atoms sorted by cell, wrapped
+ * positions, per-atom energies: about 1.7 MB) is one file-scope __device__
+ * array in libmdk.so, which every GPU that loads the library holds until the
+ * process exits.  The first call on a device looks that array's address up
+ * (with the device current); make the first call on each device before any
+ * stream capture.  All calls share the array and each call clears what it
+ * needs, so two calls whose work overlaps on one GPU (for example, calls on
+ * two streams) race: serialise them.
+ *
+ *   x        : device [N][3] positions (Angstrom), read only
+ *   N        : 0 <= N <= MDK_NOALLOC_MAX_ATOMS, else MDK_ERR_TOO_LARGE
+ *   box_lo/hi, periodic : host [3]; periodic lengths must be >= rc; the
+ *              grid of cells of size >= rc must have at most
+ *              MDK_NOALLOC_MAX_CELLS cells (else MDK_ERR_TOO_LARGE)
+ *   eps, sigma, rc, shift_mode : as mdk_set_potential_lj
+ *   F        : device [N][3] forces (eV/Angstrom), written
+ *   E        : device [1] potential energy (eV), written
+ *   cuda_stream : stream to run on (NULL = legacy default stream)
+ * Same definitions, pair vectors and FP64 arithmetic as mdk_compute in
+ * MDK_FP64 mode (the cell search replaces the Verlet list; pairs with
+ * r < rc only).  Returns without synchronising.
+ */
+int mdk_lj_compute_noalloc(const double *x, int64_t N, const double box_lo[3],
+                           const double box_hi[3], const int periodic[3], double eps,
+                           double sigma, double rc, int shift_mode, double *F, double *E,
+                           void *cuda_stream);
 
 /* ---- measurement ----------------------------------------------------------- */
 

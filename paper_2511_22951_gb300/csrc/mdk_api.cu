@@ -383,6 +383,7 @@ const char *mdk_status_string(int s) {
     case MDK_ERR_WORKSPACE: return "workspace missing or too small";
     case MDK_ERR_ORDER: return "call made before a required call";
     case MDK_ERR_RHO_RANGE: return "EAM density above the F table (extrapolated)";
+    case MDK_ERR_TOO_LARGE: return "size above the fixed maximum of the allocation-free entry point";
     default: return "unknown status";
   }
 }

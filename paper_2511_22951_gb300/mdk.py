@@ -27,6 +27,7 @@ MDK_ERR_CUDA = -7
 MDK_ERR_WORKSPACE = -8
 MDK_ERR_ORDER = -9
 MDK_ERR_RHO_RANGE = -10
+MDK_ERR_TOO_LARGE = -11
 MDK_FP64 = 0
 MDK_MIXED = 1
 
@@ -66,6 +67,7 @@ SIGNATURES = {
     "mdk_last_device_status": [_P, ctypes.POINTER(_I)],
     "mdk_profile": [_P, _I],
     "mdk_get_profile": [_P, _P],
+    "mdk_lj_compute_noalloc": [_P, _I64, _P, _P, _P, _D, _D, _D, _I, _P, _P, _P],
 }
 
 _lib = None
