@@ -19,6 +19,8 @@
 //   k_finish    clear the flag, count the build
 #include <math.h>
 
+#include <algorithm>
+
 #include "mdk_internal.cuh"
 
 namespace mdk {
@@ -48,8 +50,7 @@ __global__ void k_set_flag(Sys s) {
 __global__ void __launch_bounds__(kBlk) k_bin(Sys s) {
   if (!flag_on(s)) return;
   const int N = s.st->N;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
   const Grid &g = s.grid[s.info[i] >> 8];
   int c[3];
   for (int d = 0; d < 3; ++d) {
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(kBlk) k_bin(Sys s) {
   s.cell_of[i] = cell;
   s.tmpu[i] = pack_cell(c[0], c[1], c[2]);
   atomicAdd(&s.cell_cnt[cell], 1);
+  }
 }
 
 // block-wide exclusive scan of one value per thread; returns the prefix and
@@ -174,18 +176,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Sys s) {
 __global__ void __launch_bounds__(kBlk) k_scatter(Sys s) {
   if (!flag_on(s)) return;
   const int N = s.st->N;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
   const int pos = atomicAdd(&s.cell_fill[s.cell_of[i]], 1);
   s.order[pos] = i;
+  }
 }
 
 // order inside each cell by permanent atom id (insertion sort: a cell holds
 // a few tens of atoms), so the layout does not depend on atomic ordering
 __global__ void __launch_bounds__(kBlk) k_cell_sort(Sys s) {
   if (!flag_on(s)) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= s.n_cells) return;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s.n_cells; c += gridDim.x * blockDim.x) {
   const int a = s.cell_start[c], b = s.cell_start[c + 1];
   for (int k = a + 1; k < b; ++k) {
     const int v = s.order[k];
@@ -197,14 +198,14 @@ __global__ void __launch_bounds__(kBlk) k_cell_sort(Sys s) {
     }
     s.order[q + 1] = v;
   }
+  }
 }
 
 template <class P>
 __global__ void __launch_bounds__(kBlk) k_permute(Sys s, typename P::vec4 *pg_target) {
   if (!flag_on(s)) return;
   const int N = s.st->N;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= N) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
   const size_t Nc = s.N_cap;
   const int o = s.order[k];
   double xv[3];
@@ -231,15 +232,18 @@ __global__ void __launch_bounds__(kBlk) k_permute(Sys s, typename P::vec4 *pg_ta
   }
   if (far) inf |= kInfoFar;
   s.tmpu[Nc + k] = inf;
-  s.pf[k] = Mixed::make(p[0], p[1], p[2], inf);
+  // a far atom's pre-filter offset is NaN: every float r^2 with it is NaN,
+  // fails both band tests and so always takes the exact FP64 test
+  s.pf[k] = far ? make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, __uint_as_float(inf))
+                : Mixed::make(p[0], p[1], p[2], inf);
   pg_target[k] = P::make(p[0], p[1], p[2], inf);
+  }
 }
 
 __global__ void __launch_bounds__(kBlk) k_copyback(Sys s) {
   if (!flag_on(s)) return;
   const int N = s.st->N;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= N) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
   const size_t Nc = s.N_cap;
   for (int d = 0; d < 3; ++d) {
     s.x[d * Nc + k] = s.tmp[d * Nc + k];
@@ -248,6 +252,7 @@ __global__ void __launch_bounds__(kBlk) k_copyback(Sys s) {
   }
   s.id[k] = s.tmpi[k];
   s.info[k] = s.tmpu[Nc + k];
+  }
 }
 
 // periodic image crossed when stencil offset sd leaves cell cd of nc cells
@@ -271,74 +276,121 @@ __device__ __forceinline__ bool stencil_cell(int cd, int sd, int nc, int per, in
   return true;
 }
 
+// Verlet lists (the paper's 3x3x3 cell template), one thread per atom in
+// cell order, so the lanes of a warp share most of their stencil cells.
+// Accepted entries are staged in shared memory (two groups of 8 per thread,
+// written while the other is flushed) and reach HBM as full 32-byte sectors
+// of the list layout.  The candidate loop is branch-free: every candidate is
+// stored into the next slot and the count advances only when it is accepted.
+// Candidates near r_ns, and far atoms (NaN offsets), take the exact FP64 test
+// of the definition.
+__device__ __forceinline__ int image_of(int c, int sd, int nc, int per) {
+  if (!per) return 0;
+  const int q = c + sd;
+  return q < 0 ? -1 : (q >= nc ? 1 : 0);
+}
+
+// The definition, rounded step by step without contraction, for a candidate
+// inside the pre-filter band or with a far atom:
+// d = (x_j - x_i) + n L,  r^2 = (dx^2 + dy^2) + dz^2 < r_ns^2.
+__device__ __noinline__ bool exact_pair(const Sys &s, const Grid &g, int i, uint32_t code, int c0,
+                                        int c1, int c2, double rns2) {
+  const size_t Nc = s.N_cap;
+  const int j = (int)(code & kJMask);
+  const int nx = image_of(c0, nbr_s(code, 0), g.nc[0], g.per[0]);
+  const int ny = image_of(c1, nbr_s(code, 1), g.nc[1], g.per[1]);
+  const int nz = image_of(c2, nbr_s(code, 2), g.nc[2], g.per[2]);
+  const double ex = __dadd_rn(__dadd_rn(s.x[j], -s.x[i]), __dmul_rn((double)nx, g.L[0]));
+  const double ey = __dadd_rn(__dadd_rn(s.x[Nc + j], -s.x[Nc + i]), __dmul_rn((double)ny, g.L[1]));
+  const double ez =
+      __dadd_rn(__dadd_rn(s.x[2 * Nc + j], -s.x[2 * Nc + i]), __dmul_rn((double)nz, g.L[2]));
+  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+  return r2 < rns2;
+}
+
 __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
+  __shared__ uint32_t stage[2 * kGroup][kBlk];
   if (!flag_on(s)) return;
   const int N = s.st->N;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
   const size_t Nc = s.N_cap;
-  const float4 pi = s.pf[i];
-  const uint32_t inf = __float_as_uint(pi.w);
-  const Grid &g = s.grid[inf >> 8];
-  const uint32_t cc = s.cellc[i];
-  const int c0 = cell_coord(cc, 0), c1 = cell_coord(cc, 1), c2 = cell_coord(cc, 2);
-  const double xi = s.x[i], yi = s.x[Nc + i], zi = s.x[2 * Nc + i];
-  const bool far_i = (inf & kInfoFar) != 0;
   const float lo_thr = s.filt_lo, hi_thr = s.filt_hi;
   const double rns2 = s.rns2;
-  int count = 0;
-  for (int sz = -1; sz <= 1; ++sz) {
-    int cz, nz;
-    if (!stencil_cell(c2, sz, g.nc[2], g.per[2], &cz, &nz)) continue;
-    for (int sy = -1; sy <= 1; ++sy) {
-      int cy, ny;
-      if (!stencil_cell(c1, sy, g.nc[1], g.per[1], &cy, &ny)) continue;
-      for (int sx = -1; sx <= 1; ++sx) {
-        int cx, nx;
-        if (!stencil_cell(c0, sx, g.nc[0], g.per[0], &cx, &nx)) continue;
-        const int cell = g.cell_off + cx + g.nc[0] * (cy + g.nc[1] * cz);
-        const int a = s.cell_start[cell], b = s.cell_start[cell + 1];
-        const float shx = (float)sx * g.hf[0];
-        const float shy = (float)sy * g.hf[1];
-        const float shz = (float)sz * g.hf[2];
-        const bool self_img = (nx == 0 && ny == 0 && nz == 0);
-        for (int j = a; j < b; ++j) {
-          if (j == i && self_img) continue;
-          const float4 pj = s.pf[j];
-          const float dx = (pj.x - pi.x) + shx;
-          const float dy = (pj.y - pi.y) + shy;
-          const float dz = (pj.z - pi.z) + shz;
+  const int ngroups = s.nmax / kGroup;
+  const int tx = threadIdx.x;
+  for (int i = blockIdx.x * kBlk + tx; i < N; i += gridDim.x * kBlk) {
+    const float4 pi = __ldg(s.pf + i);
+    const Grid &g = s.grid[__float_as_uint(pi.w) >> 8];
+    const uint32_t cc = s.cellc[i];
+    const int c0 = cell_coord(cc, 0), c1 = cell_coord(cc, 1), c2 = cell_coord(cc, 2);
+    int count = 0;
+    auto flush = [&](int grp, int fill) {
+      if (grp >= ngroups) return;
+      const int h = (grp & 1) * kGroup;
+      uint32_t w[kGroup];
+#pragma unroll
+      for (int q = 0; q < kGroup; ++q) w[q] = q < fill ? stage[h + q][tx] : 0u;
+      uint4 *o = reinterpret_cast<uint4 *>(s.nbr) + ((size_t)grp * Nc + i) * 2;
+      o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    };
+    for (int t = 0; t < 27; ++t) {
+      const int sx = t % 3 - 1, sy = (t / 3) % 3 - 1, sz = t / 9 - 1;
+      int cx, cy, cz, nx, ny, nz;
+      if (!stencil_cell(c0, sx, g.nc[0], g.per[0], &cx, &nx) ||
+          !stencil_cell(c1, sy, g.nc[1], g.per[1], &cy, &ny) ||
+          !stencil_cell(c2, sz, g.nc[2], g.per[2], &cz, &nz))
+        continue;
+      const int cj = g.cell_off + cx + g.nc[0] * (cy + g.nc[1] * cz);
+      const int a = s.cell_start[cj], b = s.cell_start[cj + 1];
+      // d = p_j - q with q = p_i - s h (the shifted own offset, once per cell)
+      const float qx = pi.x - (float)sx * g.hf[0];
+      const float qy = pi.y - (float)sy * g.hf[1];
+      const float qz = pi.z - (float)sz * g.hf[2];
+      const int self = (nx == 0 && ny == 0 && nz == 0) ? i : -1;
+      const uint32_t code = pack_nbr(0, sx, sy, sz);
+      for (int j0 = a; j0 < b; j0 += 4) {
+        const int before = count;
+        float4 pj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pj[u] = __ldg(s.pf + min(j0 + u, b - 1));
+        bool band = false;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u;
+          const float dx = pj[u].x - qx, dy = pj[u].y - qy, dz = pj[u].z - qz;
           const float r2f = dx * dx + dy * dy + dz * dz;
-          const bool far = far_i || (__float_as_uint(pj.w) & kInfoFar);
-          bool in;
-          if (!far && r2f < lo_thr) {
-            in = true;
-          } else if (!far && r2f > hi_thr) {
-            in = false;
-          } else {
-            // the definition, rounded step by step without contraction:
-            // d = (x_j - x_i) + n L,  r^2 = (dx^2 + dy^2) + dz^2 < r_ns^2
-            const double ex = __dadd_rn(__dadd_rn(s.x[j], -xi), __dmul_rn((double)nx, g.L[0]));
-            const double ey =
-                __dadd_rn(__dadd_rn(s.x[Nc + j], -yi), __dmul_rn((double)ny, g.L[1]));
-            const double ez =
-                __dadd_rn(__dadd_rn(s.x[2 * Nc + j], -zi), __dmul_rn((double)nz, g.L[2]));
-            const double r2 =
-                __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-            in = r2 < rns2;
-          }
-          if (in) {
-            if (count < s.nmax) s.nbr[(size_t)count * Nc + i] = pack_nbr(j, sx, sy, sz);
-            ++count;
+          const bool ok = j < b && j != self;
+          const bool acc = ok && r2f < lo_thr;
+          band = band || (ok && !acc && !(r2f > hi_thr));
+          stage[count & 15][tx] = code | (uint32_t)j;  // kept only if accepted
+          count += acc ? 1 : 0;
+        }
+        if (band) {
+          // rare: redo this block of four with the exact test where needed
+          count = before;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u;
+            const float dx = pj[u].x - qx, dy = pj[u].y - qy, dz = pj[u].z - qz;
+            const float r2f = dx * dx + dy * dy + dz * dz;
+            const bool ok = j < b && j != self;
+            bool acc = ok && r2f < lo_thr;
+            if (ok && !acc && !(r2f > hi_thr))
+              acc = exact_pair(s, g, i, code | (uint32_t)j, c0, c1, c2, rns2);
+            stage[count & 15][tx] = code | (uint32_t)j;
+            count += acc ? 1 : 0;
           }
         }
+        // a group of 8 completed in this block: write it out
+        if ((before >> 3) != (count >> 3)) flush(before >> 3, kGroup);
       }
     }
-  }
-  s.nnbr[i] = count;
-  if (count > s.nmax) {
-    atomicOr(&s.st->bits, kStOverflow);
-    atomicMax(&s.st->max_nnbr, count);
+    if (count & 7) flush(count >> 3, count & 7);
+    s.nnbr[i] = count;
+    if (count > s.nmax) {
+      atomicOr(&s.st->bits, kStOverflow);
+      atomicMax(&s.st->max_nnbr, count);
+    }
   }
 }
 
@@ -358,21 +410,48 @@ inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
 void launch_set_rebuild_flag(const Sys &s, cudaStream_t st) { k_set_flag<<<1, 32, 0, st>>>(s); }
 
+// The chain is enqueued every step and usually has nothing to do: a grid of
+// N/256 blocks that all exit at once still costs ~0.1 ms of block
+// scheduling, so every kernel of the chain runs on a persistent grid (a few
+// blocks per SM) with grid-stride loops; a skipped rebuild costs a few us.
+int persistent_blocks(const void *fn, int threads, int smem) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess ||
+      occ <= 0)
+    occ = 1;
+  return sms * occ;
+}
+
 void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, cudaStream_t st) {
-  const int gN = nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk);
+  static int g_atom = 0, g_build = 0, g_cells = 0;
+  if (g_atom == 0) {
+    g_atom = persistent_blocks((const void *)k_bin, kBlk, 0);
+    g_build = persistent_blocks((const void *)k_build, kBlk, 0);
+    g_cells = persistent_blocks((const void *)k_cell_sort, kBlk, 0);
+  }
+  const int gN = std::min(g_atom, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
+  const int gC = std::min(g_cells, nblk(s.n_cells, kBlk));
+  const int gB = std::min(g_build, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
   k_pre<<<1, 32, 0, st>>>(s, count_step);
   k_bin<<<gN, kBlk, 0, st>>>(s);
   k_scan_reduce<<<s.n_scan_blocks, kScanThreads, 0, st>>>(s);
   k_scan_top<<<1, kScanThreads, 0, st>>>(s);
   k_scan_apply<<<s.n_scan_blocks, kScanThreads, 0, st>>>(s);
   k_scatter<<<gN, kBlk, 0, st>>>(s);
-  k_cell_sort<<<nblk(s.n_cells, kBlk), kBlk, 0, st>>>(s);
+  k_cell_sort<<<gC, kBlk, 0, st>>>(s);
   if (precision == 0)
     k_permute<Fp64><<<gN, kBlk, 0, st>>>(s, (dvec4 *)s.pg[target_pg]);
   else
     k_permute<Mixed><<<gN, kBlk, 0, st>>>(s, (float4 *)s.pg[target_pg]);
   k_copyback<<<gN, kBlk, 0, st>>>(s);
-  k_build<<<gN, kBlk, 0, st>>>(s);
+  k_build<<<gB, kBlk, 0, st>>>(s);
   k_finish<<<1, 32, 0, st>>>(s);
 }
 

@@ -10,9 +10,9 @@
 //
 // One thread owns one atom i and walks its Verlet list (full list, so no
 // atomics and a fixed summation order).  The list is stored column-major
-// (entry k of atom i at k*N_cap + i): a warp's 32 loads of entry k are one
-// 128-byte line.  Neighbour positions come from the per-step gather copy,
-// float4 (mixed) or 32-byte FP64 vectors, holding x - O(cell): the pair
+// in groups of 8 entries per atom (one 32-byte sector, two 16-byte loads per
+// thread; a warp's loads of one group are 1 KB contiguous).  Neighbour positions come from the per-step gather copy,
+// float4 (mixed) or 32-byte FP64 vectors, holding x - centre(cell): the pair
 // vector is d = (p_j - p_i) + s h, s the stencil offset stored in the list
 // entry, so FP32 pair math never subtracts two large coordinates.
 //
@@ -156,6 +156,48 @@ struct G<Mixed> {
   }
 };
 
+// ---- the neighbour walk ------------------------------------------------------------
+// Unit stencil offset s_d in {-1, 0, 1} of a list entry, exactly, in the pair
+// precision, without an int-to-float conversion: the 2-bit code c = s_d + 1 is
+// placed in the low mantissa bits of 2^23 (2^52) and 2^23 + 1 (2^52 + 1) is
+// subtracted.
+__device__ __forceinline__ float s_unit(float, uint32_t e, int d) {
+  return __uint_as_float(((e >> (26 + 2 * d)) & 3u) | 0x4B000000u) - 8388609.0f;
+}
+__device__ __forceinline__ double s_unit(double, uint32_t e, int d) {
+  return __longlong_as_double((long long)((e >> (26 + 2 * d)) & 3u) | 0x4330000000000000LL) -
+         4503599627370497.0;
+}
+
+// Walk the list of one atom: a group of 8 list words comes in two 16-byte
+// loads; its neighbour records are loaded four at a time before the four
+// bodies run, so each thread keeps several independent loads in flight.
+// `commit` runs after every four pairs: the compensated per-atom sums take one
+// block sum per four pairs instead of one term per pair.
+template <class Load, class Body, class Commit>
+__device__ __forceinline__ void walk(const uint32_t *__restrict__ nbr, size_t Nc, int i, int nn,
+                                     Load &&load, Body &&body, Commit &&commit) {
+  using Rec = decltype(load(0u));
+  const uint4 *__restrict__ row = reinterpret_cast<const uint4 *>(nbr) + (size_t)i * 2;
+  const size_t gstride = Nc * 2;
+  for (int k = 0; k < nn; k += kGroup, row += gstride) {
+    const uint4 a = __ldcs(row), b = __ldcs(row + 1);
+    const uint32_t e[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    const int m = nn - k;  // valid entries in this group
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      Rec q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (4 * h + u < m) q[u] = load(e[4 * h + u] & kJMask);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (4 * h + u < m) body(e[4 * h + u], q[u]);
+      commit();
+    }
+  }
+}
+
 // ---- per-atom epilogue: store forces or integrate -----------------------------
 template <class P>
 __device__ __forceinline__ void drift_publish(const Sys &s, const StepArgs &a, int i,
@@ -258,42 +300,47 @@ __global__ void __launch_bounds__(kBlk) k_lj(Sys s, LJParams lp, StepArgs a) {
   if (nn > s.nmax) nn = s.nmax;
   Acc<R> fx, fy, fz;
   R e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
-  const uint32_t *__restrict__ nb = s.nbr + i;
-  for (int k = 0; k < nn; ++k) {
-    const uint32_t ent = __ldcs(nb + (size_t)k * Nc);
-    const int j = (int)(ent & kJMask);
-    const V pj = GP::ld(pg + j);
-    const R dx = (R)(pj.x - pi.x) + (R)nbr_s(ent, 0) * hx;
-    const R dy = (R)(pj.y - pi.y) + (R)nbr_s(ent, 1) * hy;
-    const R dz = (R)(pj.z - pi.z) + (R)nbr_s(ent, 2) * hz;
-    const R r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 < rc2) {
-      const R inv = GP::rcp(r2);
-      const R s2 = sig2 * inv;
-      const R s6 = s2 * s2 * s2;
-      R fr = -eps24 * (R(2) * s6 * s6 - s6) * inv;  // V'(r)/r
-      R r = 0;
-      if (SHIFT == 2) {
-        r = GP::sqr(r2);
-        fr -= durc / r;
-      }
-      fx.add(fr * dx);
-      fy.add(fr * dy);
-      fz.add(fr * dz);
-      if (ENERGY) {
-        R v = eps4 * (s6 * s6 - s6) - ush;
-        if (SHIFT == 2) v -= (r - rcut) * durc;
-        e += R(0.5) * v;
-        const R hf = R(-0.5) * fr;  // r_ij = -d
-        w0 += hf * dx * dx;
-        w1 += hf * dy * dy;
-        w2 += hf * dz * dz;
-        w3 += hf * dx * dy;
-        w4 += hf * dx * dz;
-        w5 += hf * dy * dz;
-      }
-    }
-  }
+  R bx = 0, by = 0, bz = 0;  // block sums of four pairs
+  walk(
+      s.nbr, Nc, i, nn, [&](uint32_t j) { return GP::ld(pg + j); },
+      [&](uint32_t ent, const V &pj) {
+        const R dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
+        const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
+        const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
+        const R r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < rc2) {
+          const R inv = GP::rcp(r2);
+          const R s2 = sig2 * inv;
+          const R s6 = s2 * s2 * s2;
+          R fr = -eps24 * (R(2) * s6 * s6 - s6) * inv;  // V'(r)/r
+          R r = 0;
+          if (SHIFT == 2) {
+            r = GP::sqr(r2);
+            fr -= durc / r;
+          }
+          bx += fr * dx;
+          by += fr * dy;
+          bz += fr * dz;
+          if (ENERGY) {
+            R v = eps4 * (s6 * s6 - s6) - ush;
+            if (SHIFT == 2) v -= (r - rcut) * durc;
+            e += R(0.5) * v;
+            const R hf = R(-0.5) * fr;  // r_ij = -d
+            w0 += hf * dx * dx;
+            w1 += hf * dy * dy;
+            w2 += hf * dz * dz;
+            w3 += hf * dx * dy;
+            w4 += hf * dx * dz;
+            w5 += hf * dy * dz;
+          }
+        }
+      },
+      [&] {
+        fx.add(bx);
+        fy.add(by);
+        fz.add(bz);
+        bx = by = bz = 0;
+      });
   if (ENERGY) {
     s.ea[i] = (double)e;
     s.wa[i] = w0;
@@ -336,24 +383,27 @@ __global__ void __launch_bounds__(kEamBlk) k_rho(Sys s, EAMParams ep, StepArgs a
     int nn = s.nnbr[i];
     if (nn > s.nmax) nn = s.nmax;
     Acc<R> rho;
-    const uint32_t *__restrict__ nb = s.nbr + i;
-    for (int k = 0; k < nn; ++k) {
-      const uint32_t ent = __ldcs(nb + (size_t)k * Nc);
-      const int j = (int)(ent & kJMask);
-      const V pj = GP::ld(pg + j);
-      const R dx = (R)(pj.x - pi.x) + (R)nbr_s(ent, 0) * hx;
-      const R dy = (R)(pj.y - pi.y) + (R)nbr_s(ent, 1) * hy;
-      const R dz = (R)(pj.z - pi.z) + (R)nbr_s(ent, 2) * hz;
-      const R r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < rc2) {
-        const R r = GP::sqr(r2);
-        const R u = r * inv_dr;
-        int kk = (int)u;
-        kk = kk > kmax ? kmax : kk;
-        const R t = u - (R)kk;
-        rho.add(GP::val1(rt, kk, t));
-      }
-    }
+    R br = 0;
+    walk(
+        s.nbr, Nc, i, nn, [&](uint32_t j) { return GP::ld(pg + j); },
+        [&](uint32_t ent, const V &pj) {
+          const R dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
+          const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
+          const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
+          const R r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < rc2) {
+            const R r = GP::sqr(r2);
+            const R u = r * inv_dr;
+            int kk = (int)u;
+            kk = kk > kmax ? kmax : kk;
+            const R t = u - (R)kk;
+            br += GP::val1(rt, kk, t);
+          }
+        },
+        [&] {
+          rho.add(br);
+          br = 0;
+        });
     const double rho_i = rho.get();
     // F(rho_i) and F'(rho_i) in FP64 (once per atom)
     double Fv, dF;
@@ -421,41 +471,56 @@ __global__ void __launch_bounds__(kEamBlk) k_eam(Sys s, EAMParams ep, StepArgs a
     if (nn > s.nmax) nn = s.nmax;
     Acc<R> fx, fy, fz;
     R e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
-    const uint32_t *__restrict__ nb = s.nbr + i;
-    for (int k = 0; k < nn; ++k) {
-      const uint32_t ent = __ldcs(nb + (size_t)k * Nc);
-      const int j = (int)(ent & kJMask);
-      const V pj = GP::ld(pg + j);
-      const R dx = (R)(pj.x - pi.x) + (R)nbr_s(ent, 0) * hx;
-      const R dy = (R)(pj.y - pi.y) + (R)nbr_s(ent, 1) * hy;
-      const R dz = (R)(pj.z - pi.z) + (R)nbr_s(ent, 2) * hz;
-      const R r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < rc2) {
-        const R inv_r = GP::rsq(r2);
-        const R r = r2 * inv_r;
-        const R u = r * inv_dr;
-        int kk = (int)u;
-        kk = kk > kmax ? kmax : kk;
-        const R t = u - (R)kk;
-        const R dphi = GP::der2(pt, kk, t) * inv_dr;
-        const R drho = GP::der2(rt, kk, t) * inv_dr;
-        const R fpj = __ldg(fpa + j);
-        const R fr = (dphi + (fpi + fpj) * drho) * inv_r;  // V'(r)/r
-        fx.add(fr * dx);
-        fy.add(fr * dy);
-        fz.add(fr * dz);
-        if (ENERGY) {
-          e += R(0.5) * GP::val2(pt, ep, kk, t);
-          const R hf = R(-0.5) * fr;
-          w0 += hf * dx * dx;
-          w1 += hf * dy * dy;
-          w2 += hf * dz * dz;
-          w3 += hf * dx * dy;
-          w4 += hf * dx * dz;
-          w5 += hf * dy * dz;
-        }
-      }
-    }
+    struct Rec {
+      V p;
+      R fp;
+    };
+    R bx = 0, by = 0, bz = 0;
+    walk(
+        s.nbr, Nc, i, nn,
+        [&](uint32_t j) {
+          Rec q;
+          q.p = GP::ld(pg + j);
+          q.fp = __ldg(fpa + j);
+          return q;
+        },
+        [&](uint32_t ent, const Rec &q) {
+          const V &pj = q.p;
+          const R dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
+          const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
+          const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
+          const R r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < rc2) {
+            const R inv_r = GP::rsq(r2);
+            const R r = r2 * inv_r;
+            const R u = r * inv_dr;
+            int kk = (int)u;
+            kk = kk > kmax ? kmax : kk;
+            const R t = u - (R)kk;
+            const R dphi = GP::der2(pt, kk, t) * inv_dr;
+            const R drho = GP::der2(rt, kk, t) * inv_dr;
+            const R fr = (dphi + (fpi + q.fp) * drho) * inv_r;  // V'(r)/r
+            bx += fr * dx;
+            by += fr * dy;
+            bz += fr * dz;
+            if (ENERGY) {
+              e += R(0.5) * GP::val2(pt, ep, kk, t);
+              const R hf = R(-0.5) * fr;
+              w0 += hf * dx * dx;
+              w1 += hf * dy * dy;
+              w2 += hf * dz * dz;
+              w3 += hf * dx * dy;
+              w4 += hf * dx * dz;
+              w5 += hf * dy * dz;
+            }
+          }
+        },
+        [&] {
+          fx.add(bx);
+          fy.add(by);
+          fz.add(bz);
+          bx = by = bz = 0;
+        });
     if (ENERGY) {
       s.ea[i] = s.ea[i] + (double)e;
       s.wa[i] = w0;
@@ -573,35 +638,7 @@ __global__ void __launch_bounds__(kBlk) k_store_per_atom(Sys s, double *ua, doub
     for (int c = 0; c < 6; ++c) wa[6 * o + c] = s.wa[c * Nc + i];
 }
 
-__global__ void __launch_bounds__(kBlk) k_neighbor_counts(Sys s, int64_t *cnt) {
-  const int N = s.st->N;
-  const int i = blockIdx.x * kBlk + threadIdx.x;
-  if (i >= N) return;
-  cnt[s.id[i]] = (int64_t)min(s.nnbr[i], s.nmax);
-}
 
-__global__ void __launch_bounds__(kBlk) k_export_neighbors(Sys s, const int64_t *off,
-                                                           int32_t *jout, int32_t *img) {
-  const int N = s.st->N;
-  const int i = blockIdx.x * kBlk + threadIdx.x;
-  if (i >= N) return;
-  const size_t Nc = s.N_cap;
-  const int nn = min(s.nnbr[i], s.nmax);
-  const int64_t base = off[s.id[i]];
-  const uint32_t cc = s.cellc[i];
-  const Grid &g = s.grid[s.info[i] >> 8];
-  for (int k = 0; k < nn; ++k) {
-    const uint32_t e = s.nbr[(size_t)k * Nc + i];
-    const int j = (int)(e & kJMask);
-    jout[base + k] = s.id[j];
-    for (int d = 0; d < 3; ++d) {
-      const int c = cell_coord(cc, d) + nbr_s(e, d);
-      int n = 0;
-      if (g.per[d]) n = (c < 0) ? -1 : (c >= g.nc[d] ? 1 : 0);
-      img[3 * (base + k) + d] = n;
-    }
-  }
-}
 
 // ---- EAM tables: knot slopes (3-point differences) -> (y, h*m) per knot --------------
 __device__ __forceinline__ double hslope(const double *y, int n, int k) {
@@ -795,13 +832,6 @@ void launch_store_per_atom(const Sys &s, double *ua, double *wa, cudaStream_t st
   k_store_per_atom<<<nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk), kBlk, 0, st>>>(s, ua, wa);
 }
 
-void launch_neighbor_counts(const Sys &s, int64_t *cnt, cudaStream_t st) {
-  k_neighbor_counts<<<nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk), kBlk, 0, st>>>(s, cnt);
-}
 
-void launch_export_neighbors(const Sys &s, const int64_t *off, int32_t *j, int32_t *img,
-                             cudaStream_t st) {
-  k_export_neighbors<<<nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk), kBlk, 0, st>>>(s, off, j, img);
-}
 
 }  // namespace mdk

@@ -190,11 +190,11 @@ int plan(mdk_ctx *c, double rc, double skin, int max_neighbors, int rebuild_ever
     max_density = std::max(max_density, (double)c->n_atoms[(size_t)r] / vol);
   }
   if (scan_blocks_for(cells) > 8192) return MDK_ERR_BAD_ARG;
-  int nmax = max_neighbors;
+  int nmax = (max_neighbors + kGroup - 1) / kGroup * kGroup;
   if (nmax == 0) {
     const double est = 4.0 / 3.0 * M_PI * rns * rns * rns * max_density;
     nmax = (int)ceil(1.6 * est + 24.0);
-    nmax = (nmax + 3) & ~3;
+    nmax = (nmax + kGroup - 1) / kGroup * kGroup;
   }
   c->grids = gs;
   c->n_cells = cells;
@@ -356,7 +356,7 @@ int build_now(mdk_ctx *c) {
   int rc = read_status(c, &st);
   if (rc) return rc;
   if (st.bits & kStOverflow) {
-    c->nmax_grow = ((int)ceil(st.max_nnbr * 1.25) + 8 + 3) & ~3;
+    c->nmax_grow = ((int)ceil(st.max_nnbr * 1.25) + 8 + kGroup - 1) / kGroup * kGroup;
     c->need_ws = true;
     c->list_built = false;
     return MDK_ERR_NEIGH_OVERFLOW;
@@ -713,7 +713,7 @@ int mdk_get_neighbors(mdk_ctx *c, int64_t *offsets, int32_t *jout, int32_t *img)
   offsets[0] = 0;
   for (int64_t i = 0; i < N; ++i) offsets[i + 1] = offsets[i] + cnt[(size_t)i];
   if (!jout && !img) return MDK_OK;
-  // copy the ELL columns of a chunk of atoms at a time and decode on the host
+  // copy the list groups of a chunk of atoms at a time and decode on the host
   const int64_t chunk = 1 << 16;
   std::vector<uint32_t> buf;
   for (int64_t a = 0; a < N; a += chunk) {
@@ -721,9 +721,11 @@ int mdk_get_neighbors(mdk_ctx *c, int64_t *offsets, int32_t *jout, int32_t *img)
     int width = 0;
     for (int64_t i = a; i < b; ++i) width = std::max(width, std::min(nn[(size_t)i], c->nmax));
     if (width == 0) continue;
-    buf.assign((size_t)(b - a) * width, 0);
-    MDK_CK(cudaMemcpy2DAsync(buf.data(), sizeof(uint32_t) * (b - a), s.nbr + a,
-                             sizeof(uint32_t) * Nc, sizeof(uint32_t) * (b - a), width,
+    const int groups = (width + kGroup - 1) / kGroup;
+    const size_t row = (size_t)(b - a) * kGroup;  // words of one group row
+    buf.assign(row * groups, 0);
+    MDK_CK(cudaMemcpy2DAsync(buf.data(), sizeof(uint32_t) * row, s.nbr + (size_t)a * kGroup,
+                             sizeof(uint32_t) * Nc * kGroup, sizeof(uint32_t) * row, groups,
                              cudaMemcpyDeviceToHost, c->stream));
     MDK_CK(cudaStreamSynchronize(c->stream));
     for (int64_t i = a; i < b; ++i) {
@@ -731,7 +733,7 @@ int mdk_get_neighbors(mdk_ctx *c, int64_t *offsets, int32_t *jout, int32_t *img)
       const int k_n = std::min(nn[(size_t)i], c->nmax);
       const Grid &g = c->grids[info[(size_t)i] >> 8];
       for (int k = 0; k < k_n; ++k) {
-        const uint32_t e = buf[(size_t)k * (b - a) + (i - a)];
+        const uint32_t e = buf[(size_t)(k / kGroup) * row + (size_t)(i - a) * kGroup + k % kGroup];
         const int j = (int)(e & kJMask);
         if (jout) jout[base + k] = id[(size_t)j];
         if (img)
@@ -901,7 +903,7 @@ int mdk_last_device_status(mdk_ctx *c, int *bits) {
   if (r) return r;
   if (bits) *bits = (int)st.bits;
   if (st.bits & kStOverflow) {
-    c->nmax_grow = ((int)ceil(st.max_nnbr * 1.25) + 8 + 3) & ~3;
+    c->nmax_grow = ((int)ceil(st.max_nnbr * 1.25) + 8 + kGroup - 1) / kGroup * kGroup;
     c->need_ws = true;
     c->list_built = false;
   }

@@ -10,7 +10,7 @@
 //                   double4 (FP64) of x - O(cell) with info in .w
 //   info          : type (bits 0-3) | piston (bit 4) | far (bit 5) |
 //                   replica (bits 8-31)
-//   nbr           : ELL Verlet lists, entry k of atom i at [k * N_cap + i],
+//   nbr           : Verlet lists in groups of 8 entries per atom (ell_index),
 //                   packed j (bits 0-25) | (s_x+1) << 26 | (s_y+1) << 28 |
 //                   (s_z+1) << 30, s = stencil offset of j's cell
 #pragma once
@@ -133,6 +133,15 @@ __device__ __forceinline__ double cell_center(const Grid &g, int d, int c) {
   return g.lo[d] + ((double)c + 0.5) * g.h[d];
 }
 
+// Verlet-list layout: entries in groups of 8 per atom; group g of atom i is
+// the 32-byte sector starting at word (g * N_cap + i) * 8.  A thread reads 8
+// entries with two 16-byte loads, a warp reads 1 KB contiguous, and the build
+// writes whole sectors (no partial-sector read-modify-write in L2).
+constexpr int kGroup = 8;
+__host__ __device__ __forceinline__ size_t ell_index(int k, int i, size_t Nc) {
+  return ((size_t)(k >> 3) * Nc + (size_t)i) * kGroup + (size_t)(k & 7);
+}
+
 __device__ __forceinline__ uint32_t pack_nbr(int j, int sx, int sy, int sz) {
   return (uint32_t)j | ((uint32_t)(sx + 1) << 26) | ((uint32_t)(sy + 1) << 28) |
          ((uint32_t)(sz + 1) << 30);
@@ -225,9 +234,6 @@ void launch_load_state(const Sys &s, const double *x_aos, const double *v_aos,
 void launch_store_state(const Sys &s, double *x_aos, double *v_aos, cudaStream_t st);
 void launch_store_forces(const Sys &s, double *f_aos, cudaStream_t st);
 void launch_store_per_atom(const Sys &s, double *ua, double *wa, cudaStream_t st);
-void launch_export_neighbors(const Sys &s, const int64_t *offsets, int32_t *jout,
-                             int32_t *imgout, cudaStream_t st);
-void launch_neighbor_counts(const Sys &s, int64_t *counts_orig, cudaStream_t st);
 int eam_smem_bytes(const EAMParams &p, int precision, int pass);
 int configure_eam_smem(int bytes_pass1, int bytes_pass2, int precision);
 
