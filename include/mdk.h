@@ -162,8 +162,9 @@ int mdk_set_state(mdk_ctx *ctx, const double *x, const double *v, int on_device)
  */
 int mdk_get_state(mdk_ctx *ctx, double *x, double *v, int on_device);
 
-/* Current number of atoms (changes with the moving window). */
-int mdk_get_natoms(const mdk_ctx *ctx, int64_t *n);
+/* Current number of atoms (changes with the moving window; synchronises
+ * when a window is set). */
+int mdk_get_natoms(mdk_ctx *ctx, int64_t *n);
 
 /* ---- neighbour lists (Sec. "Neighbor lists construction", Eq. rhrz) ------ */
 
@@ -252,23 +253,46 @@ int mdk_get_counters(mdk_ctx *ctx, int64_t *n_builds, int64_t *n_steps);
 int mdk_set_piston(mdk_ctx *ctx, double u_p, const uint8_t *is_piston);
 
 /*
- * Moving window along x (free dimension): at every list build, atoms with
- * x < x_front - L_behind are deleted, and while the largest x of the
- * material is below x_front + L_ahead a copy of the fresh slab (n_slab atoms,
- * positions [n_slab][3] relative to its own origin, velocities [n_slab][3],
- * all host) is appended at x_max + slab_dx.  x_front is the largest x of an
- * atom with v_x > u_p/2 (the shocked material).  Atoms within piston_depth
- * of the rear edge become piston atoms after a deletion.
+ * Moving window along x for a piston-driven shock (Sec. "Moving window
+ * simulation": atoms are inserted ahead of the shock from a prepared fresh
+ * sample and deleted behind it).  Applied at every list build after this
+ * call, on the device, in this order:
+ *   x_front = largest x of an atom with v_x > u_p/2 (none: nothing happens);
+ *   atoms with x < x_front - L_behind are deleted;
+ *   while the leading edge x_max < x_front + L_ahead, copies of the fresh
+ *   slab are appended: k = ceil((x_front + L_ahead - x_max)/slab_lx) copies,
+ *   copy c shifted by ((x_max + slab_gap) + c slab_lx, 0, 0), velocities
+ *   slab_v, mass slab_mass, new ids counting up from N;
+ *   atoms with x < x_min + piston_depth (x_min of the atoms left) join the
+ *   piston.
+ *   slab_x, slab_v : host [n_slab][3] positions (x in [0, slab_lx)) and
+ *                    velocities of one fresh slab; copied.
+ * The atom count changes: reserve room with mdk_set_capacity (appends that
+ * do not fit raise MDK_ERR_NEIGH_OVERFLOW's status bit).  Once a window is
+ * set, per-atom outputs come in ascending atom-id order (mdk_get_ids).
+ * Single-system contexts only.  Takes effect at the next list build.
  */
-int mdk_set_window(mdk_ctx *ctx, double L_behind, double L_ahead,
-                   const double *slab_x, const double *slab_v, int64_t n_slab,
-                   double slab_dx, double slab_mass, double piston_depth);
+int mdk_set_window(mdk_ctx *ctx, double L_behind, double L_ahead, const double *slab_x,
+                   const double *slab_v, int64_t n_slab, double slab_lx, double slab_gap,
+                   double slab_mass, double piston_depth);
+
+/* Ids of the atoms present, ascending (the order of every per-atom output). */
+int mdk_get_ids(mdk_ctx *ctx, int64_t *ids);
+
+/* Atoms appended and deleted by the moving window so far (synchronises). */
+int mdk_window_counts(mdk_ctx *ctx, int64_t *inserted, int64_t *deleted);
 
 /*
- * Appendix per-bin statistics along `axis` (0..2) for bins of width bin_w
- * starting at origin; out [nbins][17] = N_l, M_l, u_l[3], T_l[3], E_pot,l,
- * P_l[6] (xx yy zz xy xz yz), E_kin,l, V_l.  Uses the per-atom energy and
- * virial of the last mdk_compute.  on_device: 0 = host out.
+ * Per-bin statistics of the paper's Appendix along `axis` (0..2), for bins
+ * [origin + l bin_w, origin + (l+1) bin_w), l < nbins, of volume
+ * V_l = bin_w * cross_area; atoms outside every bin are ignored.
+ * out [nbins][17] = N_l, M_l (u), u_l[3] (COM velocity, Angstrom/fs),
+ * T_l[3] (K, per degree of freedom, about u_l), E_pot,l (sum of U_i, eV),
+ * P_l[6] (eV/Angstrom^3; xx yy zz xy xz yz; kinetic + virial), E_kin,l
+ * (peculiar, eV), V_l.  Per-atom energies and virials are taken at the
+ * current positions (one force evaluation if the last one was not an
+ * mdk_compute at these positions).  nbins * 41 <= 9 * capacity.
+ * on_device: 0 = host out (synchronises), 1 = device out.
  */
 int mdk_profiles(mdk_ctx *ctx, int axis, double origin, double bin_w, int nbins,
                  double cross_area, double *out, int on_device);

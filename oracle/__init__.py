@@ -66,6 +66,12 @@ def lib():
         L.ora_md_run.restype = I64
         L.ora_profiles.argtypes = [I64, P, P, P, P, P, I, D, D, I, D, P]
         L.ora_profiles.restype = None
+        L.ora_window_apply.argtypes = [I64, I64, P, P, P, P, P, P, D, D, D, P, P, I64, D, D,
+                                       D, D]
+        L.ora_window_apply.restype = I64
+        L.ora_md_window.argtypes = [P, I64, P, P, P, P, P, P, P, P, P, I, D, P, P, I, D, P, D,
+                                    D, I64, I, D, D, D, P, P, I64, D, D, D, D]
+        L.ora_md_window.restype = I64
         _lib = L
     return _lib
 
@@ -241,6 +247,60 @@ def profiles(x, v, masses, axis, origin, width, nbins, cross_area, Ua=None, Wa=N
     lib().ora_profiles(n, _p(x), _p(v), _p(m), _p(Ua), _p(Wa), axis, origin, width,
                        nbins, cross_area, _p(out))
     return out
+
+
+class WindowState:
+    """Atoms of a window run with room for `cap` atoms (ids, piston flags)."""
+
+    def __init__(self, x, v, masses, piston, cap):
+        n = x.shape[0]
+        self.cap = cap
+        self.x = np.zeros((cap, 3))
+        self.v = np.zeros((cap, 3))
+        self.m = np.zeros(cap)
+        self.pis = np.zeros(cap, dtype=np.uint8)
+        self.ids = np.zeros(cap, dtype=np.int64)
+        self.x[:n] = x
+        self.v[:n] = v
+        self.m[:n] = masses
+        self.pis[:n] = np.asarray(piston, dtype=np.uint8)
+        self.ids[:n] = np.arange(n)
+        self.n = n
+        self.next_id = np.array([n], dtype=np.int64)
+
+    def view(self):
+        n = self.n
+        return {"x": self.x[:n].copy(), "v": self.v[:n].copy(), "m": self.m[:n].copy(),
+                "piston": self.pis[:n].astype(bool), "ids": self.ids[:n].copy()}
+
+
+def window_apply(st, u_p, L_behind, L_ahead, slab_x, slab_v, slab_lx, slab_gap, slab_mass,
+                 piston_depth):
+    sx = _f64(slab_x, (-1, 3))
+    sv = _f64(slab_v, (-1, 3))
+    st.n = int(lib().ora_window_apply(st.n, st.cap, _p(st.x), _p(st.v), _p(st.m), _p(st.pis),
+                                      _p(st.ids), _p(st.next_id), u_p, L_behind, L_ahead,
+                                      _p(sx), _p(sv), sx.shape[0], slab_lx, slab_gap,
+                                      slab_mass, piston_depth))
+    return st
+
+
+def md_window(st, lo, hi, periodic, tables, dt, nsteps, skin, rebuild_every, u_p, L_behind,
+              L_ahead, slab_x, slab_v, slab_lx, slab_gap, slab_mass, piston_depth):
+    lo, hi, per = _box(lo, hi, periodic)
+    phi, rho, Ft = _f64(tables.phi), _f64(tables.rho), _f64(tables.F)
+    sx = _f64(slab_x, (-1, 3))
+    sv = _f64(slab_v, (-1, 3))
+    n = np.array([st.n], dtype=np.int64)
+    nb = lib().ora_md_window(_p(n), st.cap, _p(st.x), _p(st.v), _p(st.m), _p(st.pis),
+                             _p(st.ids), _p(st.next_id), _p(lo), _p(hi), _p(per), phi.shape[0],
+                             tables.rc, _p(phi), _p(rho), Ft.shape[0], tables.rho_max, _p(Ft),
+                             skin, dt, nsteps, rebuild_every, u_p, L_behind, L_ahead, _p(sx),
+                             _p(sv), sx.shape[0], slab_lx, slab_gap, slab_mass, piston_depth)
+    if nb < 0:
+        raise RuntimeError(f"oracle md_window failed ({nb})")
+    st.n = int(n[0])
+    return int(nb)
 
 
 if __name__ == "__main__":  # pragma: no cover

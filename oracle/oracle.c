@@ -974,3 +974,136 @@ void ora_profiles(int64_t N, const double *x, const double *v, const double *mas
     free(kt);
     free(bin);
 }
+
+/* ---------------------------------------------------------------------- */
+/* moving window (Sec. "Moving window simulation")                          */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * The window rules applied at a list build (reading of the paper's moving
+ * window for a piston-driven shock along x; the design doc lists it):
+ *   x_front = largest x of an atom with v_x > u_p/2 (none: no window action);
+ *   atoms with x < x_front - L_behind are deleted (order of the rest kept);
+ *   while the leading edge x_max < x_front + L_ahead, copies of a fresh slab
+ *   are appended: copy c at x offset x_max + gap + c * slab_lx, velocities
+ *   slab_v, ids next_id, next_id + 1, ...; k = ceil((x_front + L_ahead -
+ *   x_max) / slab_lx) copies, as many as the capacity allows;
+ *   atoms with x < x_min + piston_depth (x_min over the atoms left) become
+ *   piston atoms.
+ * Returns the new atom count.
+ */
+int64_t ora_window_apply(int64_t N, int64_t cap, double *x, double *v, double *mass,
+                         uint8_t *piston, int64_t *ids, int64_t *next_id, double u_p,
+                         double L_behind, double L_ahead, const double *slab_x,
+                         const double *slab_v, int64_t n_slab, double slab_lx,
+                         double slab_gap, double slab_mass, double piston_depth) {
+    double x_front = -INFINITY, x_max = -INFINITY;
+    for (int64_t i = 0; i < N; ++i) {
+        if (v[3 * i] > 0.5 * u_p && x[3 * i] > x_front) x_front = x[3 * i];
+        if (x[3 * i] > x_max) x_max = x[3 * i];
+    }
+    if (x_front == -INFINITY) return N;
+    double cut = x_front - L_behind;
+    int64_t n = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (x[3 * i] < cut) continue;
+        if (n != i) {
+            for (int k = 0; k < 3; ++k) {
+                x[3 * n + k] = x[3 * i + k];
+                v[3 * n + k] = v[3 * i + k];
+            }
+            mass[n] = mass[i];
+            piston[n] = piston[i];
+            ids[n] = ids[i];
+        }
+        ++n;
+    }
+    double need = x_front + L_ahead - x_max;
+    int64_t copies = need > 0.0 ? (int64_t)ceil(need / slab_lx) : 0;
+    for (int64_t c = 0; c < copies; ++c) {
+        double x0 = x_max + slab_gap + (double)c * slab_lx;
+        for (int64_t q = 0; q < n_slab && n < cap; ++q) {
+            x[3 * n] = slab_x[3 * q] + x0;
+            x[3 * n + 1] = slab_x[3 * q + 1];
+            x[3 * n + 2] = slab_x[3 * q + 2];
+            for (int k = 0; k < 3; ++k) v[3 * n + k] = slab_v[3 * q + k];
+            mass[n] = slab_mass;
+            piston[n] = 0;
+            ids[n] = (*next_id)++;
+            ++n;
+        }
+    }
+    double x_min = INFINITY;
+    for (int64_t i = 0; i < n; ++i)
+        if (x[3 * i] < x_min) x_min = x[3 * i];
+    for (int64_t i = 0; i < n; ++i)
+        if (x[3 * i] < x_min + piston_depth) piston[i] = 1;
+    return n;
+}
+
+/*
+ * Velocity-Verlet MD with a rigid piston and the moving window: as
+ * ora_md_run with rebuilds every rebuild_every steps, the window rules
+ * applied before every rebuild after the first build.  Arrays have room for
+ * cap atoms; *n_io is the atom count in and out.  Returns the number of
+ * builds or a negative error code.
+ */
+int64_t ora_md_window(int64_t *n_io, int64_t cap, double *x, double *v, double *mass,
+                      uint8_t *piston, int64_t *ids, int64_t *next_id, const double *lo,
+                      const double *hi, const int *per, int nr, double rc_eam,
+                      const double *phi, const double *rho, int nrho, double rho_max,
+                      const double *Ftab, double skin, double dt, int64_t nsteps,
+                      int rebuild_every, double u_p, double L_behind, double L_ahead,
+                      const double *slab_x, const double *slab_v, int64_t n_slab,
+                      double slab_lx, double slab_gap, double slab_mass,
+                      double piston_depth) {
+    int64_t N = *n_io;
+    ora_box b = make_box(lo, hi, per);
+    ora_pot p;
+    pot_eam_init(&p, nr, rc_eam, phi, rho, nrho, rho_max, Ftab);
+    double rns = p.rc + skin;
+    ora_vlist vl;
+    memset(&vl, 0, sizeof(vl));
+    vl.off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(cap + 1));
+    double *F = (double *)calloc(3 * (size_t)(cap > 0 ? cap : 1), sizeof(double));
+    int64_t nbuild = 0;
+    ora_wrap(N, x, lo, hi, per);
+    if (vlist_build(&vl, N, x, &b, rns) != 0) return -2;
+    ++nbuild;
+    double E, W[6];
+    forces_from_list(&p, N, x, &b, vl.off, vl.j, vl.n, &E, F, W, NULL, NULL, NULL, NULL);
+    for (int64_t step = 0; step < nsteps; ++step) {
+        for (int64_t i = 0; i < N; ++i) {
+            if (piston[i]) {
+                v[3 * i] = u_p;
+                v[3 * i + 1] = 0.0;
+                v[3 * i + 2] = 0.0;
+            } else {
+                double c = 0.5 * dt * ORA_ACC / mass[i];
+                for (int k = 0; k < 3; ++k) v[3 * i + k] += c * F[3 * i + k];
+            }
+            for (int k = 0; k < 3; ++k) x[3 * i + k] += dt * v[3 * i + k];
+        }
+        if (((step + 1) % rebuild_every) == 0) {
+            N = ora_window_apply(N, cap, x, v, mass, piston, ids, next_id, u_p, L_behind,
+                                 L_ahead, slab_x, slab_v, n_slab, slab_lx, slab_gap,
+                                 slab_mass, piston_depth);
+            ora_wrap(N, x, lo, hi, per);
+            if (vlist_build(&vl, N, x, &b, rns) != 0) return -2;
+            ++nbuild;
+        }
+        forces_from_list(&p, N, x, &b, vl.off, vl.j, vl.n, &E, F, W, NULL, NULL, NULL, NULL);
+        for (int64_t i = 0; i < N; ++i) {
+            if (piston[i]) continue;
+            double c = 0.5 * dt * ORA_ACC / mass[i];
+            for (int k = 0; k < 3; ++k) v[3 * i + k] += c * F[3 * i + k];
+        }
+    }
+    *n_io = N;
+    free(vl.off);
+    free(vl.j);
+    free(vl.n);
+    free(F);
+    pot_free(&p);
+    return nbuild;
+}

@@ -41,7 +41,98 @@ __global__ void k_pre(Sys s, int count_step) {
   DevStatus *st = s.st;
   if (count_step) st->since_build += 1;
   if (s.rebuild_every > 0 && st->since_build >= s.rebuild_every) st->rebuild = 1;
+  // the window acts at builds that stepping triggers, not at explicit builds
+  st->win_active = (s.win_on && count_step && st->rebuild) ? 1 : 0;
+  st->win_cut = -INFINITY;
+  if (st->win_active) {
+    st->key_front = dkey(-INFINITY);
+    st->key_xmax = dkey(-INFINITY);
+    st->key_xmin = dkey(INFINITY);
+    st->win_cut = -INFINITY;
+    st->win_insert = 0;
+  }
 }
+
+// ---- moving window (Sec. "Moving window simulation"; rules in the oracle) ----
+// shock front = largest x of an atom with v_x > u_p/2; leading edge = max x
+__global__ void __launch_bounds__(kBlk) k_win_stats(Sys s) {
+  if (!flag_on(s) || !s.st->win_active) return;
+  const int N = s.st->N;
+  long long front = dkey(-INFINITY), xmax = dkey(-INFINITY);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double x = s.x[i];
+    const long long k = dkey(x);
+    if (s.v[i] > 0.5 * s.u_p && k > front) front = k;
+    if (k > xmax) xmax = k;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    front = max(front, __shfl_xor_sync(0xffffffffu, front, o));
+    xmax = max(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&s.st->key_front, front);
+    atomicMax(&s.st->key_xmax, xmax);
+  }
+}
+
+// cut, number of fresh-slab copies to append (capped by the capacity)
+__global__ void k_win_plan(Sys s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || !flag_on(s) || !s.st->win_active) return;
+  DevStatus *st = s.st;
+  const double front = dkey_inv(st->key_front), xmax = dkey_inv(st->key_xmax);
+  st->win_n_old = st->N;
+  st->win_insert = 0;
+  st->win_cut = -INFINITY;
+  if (!(front > -INFINITY)) return;
+  st->win_cut = front - s.L_behind;
+  const double need = front + s.L_ahead - xmax;
+  long long copies = need > 0.0 ? (long long)ceil(need / s.slab_lx) : 0;
+  long long add = copies * (long long)s.n_slab;
+  const long long room = (long long)s.N_cap - st->N;
+  if (add > room) {
+    add = room;
+    atomicOr(&st->bits, kStOverflow);
+  }
+  st->win_insert = (int)add;
+  st->win_x0 = xmax;
+  st->win_id0 = st->next_id;
+  st->next_id += (int)add;
+  st->N += (int)add;
+  st->n_inserted += add;
+}
+
+__global__ void __launch_bounds__(kBlk) k_win_insert(Sys s) {
+  if (!flag_on(s) || !s.st->win_active) return;
+  const DevStatus *st = s.st;
+  const int add = st->win_insert, n0 = st->win_n_old, id0 = st->win_id0;
+  const size_t Nc = s.N_cap;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < add; q += gridDim.x * blockDim.x) {
+    const int c = q / s.n_slab, k = q % s.n_slab;
+    const double *a = s.slab + 6 * (size_t)k;
+    const int i = n0 + q;
+    // copy c sits at x offset (x_max + gap) + c * slab_lx, rounded in that order
+    const double x0 = __dadd_rn(__dadd_rn(st->win_x0, s.slab_gap), __dmul_rn((double)c, s.slab_lx));
+    s.x[i] = __dadd_rn(a[0], x0);
+    s.x[Nc + i] = a[1];
+    s.x[2 * Nc + i] = a[2];
+    for (int d = 0; d < 3; ++d) {
+      s.v[d * Nc + i] = a[3 + d];
+      s.f[d * Nc + i] = 0.0;
+    }
+    s.id[i] = id0 + q;
+    s.info[i] = s.slab_info;
+  }
+}
+
+// atoms a window deleted sit in the last bucket, past the kept ones: drop them
+__global__ void k_win_trim(Sys s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || !flag_on(s)) return;
+  DevStatus *st = s.st;
+  const int kept = s.cell_start[s.n_cells];
+  st->n_deleted += st->N - kept;
+  st->N = kept;
+}
+
 
 __global__ void k_set_flag(Sys s) {
   if (threadIdx.x == 0 && blockIdx.x == 0) s.st->rebuild = 1;
@@ -52,6 +143,16 @@ __global__ void __launch_bounds__(kBlk) k_bin(Sys s) {
   const int N = s.st->N;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
   const Grid &g = s.grid[s.info[i] >> 8];
+  if (s.win_on && s.st->win_active) {
+    const double x = s.x[i];
+    if (x < s.st->win_cut) {  // behind the window: to the deletion bucket
+      s.cell_of[i] = s.n_cells;
+      s.tmpu[i] = 0;
+      atomicAdd(&s.cell_cnt[s.n_cells], 1);
+      continue;
+    }
+    atomicMin(&s.st->key_xmin, dkey(x));
+  }
   int c[3];
   for (int d = 0; d < 3; ++d) {
     double xv = s.x[(size_t)d * s.N_cap + i];
@@ -120,7 +221,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Sys s) {
   int sum = 0;
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q)
-    if (base + q < s.n_cells) sum += s.cell_cnt[base + q];
+    if (base + q <= s.n_cells) sum += s.cell_cnt[base + q];
   __shared__ int tot;
   block_exscan(sum, &tot);
   if (threadIdx.x == 0) s.scan_part[blockIdx.x] = tot;
@@ -154,7 +255,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Sys s) {
   int sum = 0;
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q) {
-    loc[q] = (base + q < s.n_cells) ? s.cell_cnt[base + q] : 0;
+    loc[q] = (base + q <= s.n_cells) ? s.cell_cnt[base + q] : 0;
     sum += loc[q];
   }
   __shared__ int tot;
@@ -162,7 +263,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Sys s) {
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q) {
     const int c = base + q;
-    if (c < s.n_cells) {
+    if (c <= s.n_cells) {
       s.cell_start[c] = pre;
       s.cell_fill[c] = pre;
       s.cell_cnt[c] = 0;  // ready for the next build
@@ -170,7 +271,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Sys s) {
     pre += loc[q];
   }
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1)
-    s.cell_start[s.n_cells] = pre;
+    s.cell_start[s.n_cells + 1] = pre;
 }
 
 __global__ void __launch_bounds__(kBlk) k_scatter(Sys s) {
@@ -220,6 +321,9 @@ __global__ void __launch_bounds__(kBlk) k_permute(Sys s, typename P::vec4 *pg_ta
   const uint32_t cc = s.tmpu[o];
   s.cellc[k] = cc;
   uint32_t inf = s.info[o] & ~kInfoFar;
+  if (s.win_on && s.st->win_active && s.st->win_cut > -INFINITY &&
+      xv[0] < dkey_inv(s.st->key_xmin) + s.piston_depth)
+    inf |= kInfoPiston;
   const Grid &g = s.grid[inf >> 8];
   double p[3];
   bool far = false;
@@ -440,6 +544,11 @@ void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, 
   const int gC = std::min(g_cells, nblk(s.n_cells, kBlk));
   const int gB = std::min(g_build, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
   k_pre<<<1, 32, 0, st>>>(s, count_step);
+  if (s.win_on) {
+    k_win_stats<<<gN, kBlk, 0, st>>>(s);
+    k_win_plan<<<1, 32, 0, st>>>(s);
+    k_win_insert<<<gN, kBlk, 0, st>>>(s);
+  }
   k_bin<<<gN, kBlk, 0, st>>>(s);
   k_scan_reduce<<<s.n_scan_blocks, kScanThreads, 0, st>>>(s);
   k_scan_top<<<1, kScanThreads, 0, st>>>(s);
@@ -451,10 +560,28 @@ void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, 
   else
     k_permute<Mixed><<<gN, kBlk, 0, st>>>(s, (float4 *)s.pg[target_pg]);
   k_copyback<<<gN, kBlk, 0, st>>>(s);
+  if (s.win_on) k_win_trim<<<1, 32, 0, st>>>(s);
   k_build<<<gB, kBlk, 0, st>>>(s);
   k_finish<<<1, 32, 0, st>>>(s);
 }
 
-int scan_blocks_for(int n_cells) { return (n_cells + kScanTile - 1) / kScanTile; }
+int scan_blocks_for(int n_buckets) { return (n_buckets + kScanTile - 1) / kScanTile; }
+
+namespace {
+__global__ void k_set_piston(Sys s, const uint8_t *flags, int64_t n_flags) {
+  const int N = s.st->N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const int o = s.id[i];
+    const uint32_t pbit = (flags && o < n_flags && flags[o]) ? kInfoPiston : 0u;
+    s.info[i] = (s.info[i] & ~kInfoPiston) | pbit;
+    if (o < s.N_cap) s.info0[o] = (s.info0[o] & ~kInfoPiston) | pbit;
+  }
+}
+}  // namespace
+
+void launch_set_piston(const Sys &s, const uint8_t *flags, int64_t n_flags, cudaStream_t st) {
+  const int g = std::min(1024, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
+  k_set_piston<<<g, kBlk, 0, st>>>(s, flags, n_flags);
+}
 
 }  // namespace mdk

@@ -52,10 +52,19 @@ struct mdk_ctx {
   double *thermo_ring = nullptr;
   int cur = 0;
   bool state_set = false, list_built = false, forces_valid = false;
+  bool per_atom_valid = false;  // ea/wa hold U_i, W_i of the current order
   double u_p = 0.0;
   int thermo_every = 0, thermo_cap = 0;
   int64_t thermo_written = 0, thermo_read = 0;
   int64_t steps_done = 0;
+  // moving window
+  bool win_on = false;
+  double win_L_behind = 0.0, win_L_ahead = 0.0, win_slab_lx = 0.0, win_gap = 0.0,
+         win_depth = 0.0;
+  uint32_t win_info = 0;
+  std::vector<double> win_slab;  // [n][6]
+  int64_t win_slab_cap = 0;      // slab atoms the workspace has room for
+  double *win_slab_dev = nullptr;
   // measurement (mdk_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -116,10 +125,12 @@ size_t layout(mdk_ctx *c, char *base) {
   s.wa = cv.take<double>(6 * Nc);
   s.rho = cv.take<double>(Nc);
   s.fp = cv.take<double>(Nc);
-  s.cell_cnt = cv.take<int32_t>(c->n_cells);
-  s.cell_start = cv.take<int32_t>((size_t)c->n_cells + 1);
-  s.cell_fill = cv.take<int32_t>(c->n_cells);
-  s.scan_part = cv.take<int32_t>(scan_blocks_for(c->n_cells));
+  s.cell_cnt = cv.take<int32_t>((size_t)c->n_cells + 1);
+  s.cell_start = cv.take<int32_t>((size_t)c->n_cells + 2);
+  s.cell_fill = cv.take<int32_t>((size_t)c->n_cells + 1);
+  s.scan_part = cv.take<int32_t>(scan_blocks_for(c->n_cells + 1));
+  c->win_slab_cap = (int64_t)(c->win_slab.size() / 6);
+  c->win_slab_dev = cv.take<double>(c->win_slab.size());
   s.cell_of = cv.take<int32_t>(Nc);
   s.order = cv.take<int32_t>(Nc);
   s.grid = cv.take<Grid>(c->n_rep);
@@ -189,7 +200,7 @@ int plan(mdk_ctx *c, double rc, double skin, int max_neighbors, int rebuild_ever
     cells += (int)nc3;
     max_density = std::max(max_density, (double)c->n_atoms[(size_t)r] / vol);
   }
-  if (scan_blocks_for(cells) > 8192) return MDK_ERR_BAD_ARG;
+  if (scan_blocks_for(cells + 1) > 8192) return MDK_ERR_BAD_ARG;
   int nmax = (max_neighbors + kGroup - 1) / kGroup * kGroup;
   if (nmax == 0) {
     const double est = 4.0 / 3.0 * M_PI * rns * rns * rns * max_density;
@@ -219,7 +230,7 @@ void fill_sys_params(mdk_ctx *c) {
   s.nmax = c->nmax;
   s.n_rep = c->n_rep;
   s.n_cells = c->n_cells;
-  s.n_scan_blocks = scan_blocks_for(c->n_cells);
+  s.n_scan_blocks = scan_blocks_for(c->n_cells + 1);
   const double rns = c->rc_list + c->skin;
   s.rns2 = rns * rns;
   // FP32 pre-filter band: the float r^2 of a candidate is within ~6e-6 r_ns^2
@@ -231,10 +242,20 @@ void fill_sys_params(mdk_ctx *c) {
   s.rebuild_every = c->rebuild_every;
   for (int t = 0; t < kMaxTypes; ++t) {
     const double m = t < c->n_types ? c->type_mass[t] : 1.0;
+    s.mass[t] = m;
     s.acc_over_m[t] = kAcc / m;
     s.ke_m[t] = 0.5 * m / kAcc;
   }
   s.u_p = c->u_p;
+  s.win_on = c->win_on ? 1 : 0;
+  s.n_slab = (int)(c->win_slab.size() / 6);
+  s.L_behind = c->win_L_behind;
+  s.L_ahead = c->win_L_ahead;
+  s.slab_lx = c->win_slab_lx;
+  s.slab_gap = c->win_gap;
+  s.piston_depth = c->win_depth;
+  s.slab = c->win_slab_dev;
+  s.slab_info = c->win_info;
 }
 
 int read_status(mdk_ctx *c, DevStatus *out) {
@@ -260,6 +281,9 @@ __global__ void k_init_status(Sys s, int N) {
     st->bits = 0;
     st->max_nnbr = 0;
     st->since_build = 0;
+    st->next_id = N;
+    st->n_inserted = 0;
+    st->n_deleted = 0;
   }
 }
 
@@ -282,15 +306,6 @@ __global__ void k_thermo_store(Sys s, double *ring, int slot, double step) {
   for (int c = 0; c < 6; ++c) o[4 + c] = q[2 + c];
 }
 
-__global__ void k_set_piston(Sys s, const uint8_t *flags) {
-  const int N = s.st->N;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int o = s.id[i];
-  const uint32_t pbit = (flags && flags[o]) ? kInfoPiston : 0u;
-  s.info[i] = (s.info[i] & ~kInfoPiston) | pbit;
-  s.info0[o] = (s.info0[o] & ~kInfoPiston) | pbit;
-}
 
 // next free event of the measurement pool (created on first use)
 int take_event(mdk_ctx *c) {
@@ -363,6 +378,59 @@ int build_now(mdk_ctx *c) {
   }
   if (st.bits & kStNonfinite) return MDK_ERR_NONFINITE;
   c->list_built = true;
+  return MDK_OK;
+}
+
+// Atoms present: the host count, or the device's once a window can change it.
+int device_n(mdk_ctx *c, int64_t *n) {
+  if (!c->win_on) {
+    *n = c->N;
+    return MDK_OK;
+  }
+  DevStatus st;
+  int r = read_status(c, &st);
+  if (r) return r;
+  c->N = st.N;
+  *n = st.N;
+  return MDK_OK;
+}
+
+// Internal index of the atom of rank r in ascending-id order (the caller's
+// order once a window has appended or deleted atoms).
+int caller_order(mdk_ctx *c, int64_t n, std::vector<int32_t> &ord, std::vector<int32_t> &id) {
+  id.resize((size_t)n);
+  ord.resize((size_t)n);
+  if (n > 0) {
+    MDK_CK(cudaMemcpyAsync(id.data(), c->sys.id, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
+                           c->stream));
+    MDK_CK(cudaStreamSynchronize(c->stream));
+  }
+  for (int64_t r = 0; r < n; ++r) ord[(size_t)r] = (int32_t)r;
+  std::sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return id[(size_t)a] < id[(size_t)b]; });
+  return MDK_OK;
+}
+
+// comp doubles per atom of the SoA array src (component stride N_cap) in the
+// caller's order into out (host, or device when on_device).
+int gather_by_id(mdk_ctx *c, int64_t n, const double *src, int comp, double *out, int on_device) {
+  std::vector<int32_t> ord, id;
+  int r = caller_order(c, n, ord, id);
+  if (r) return r;
+  std::vector<double> buf((size_t)n * comp), res((size_t)n * comp);
+  for (int k = 0; k < comp && n > 0; ++k)
+    MDK_CK(cudaMemcpyAsync(buf.data() + (size_t)k * n, src + (size_t)k * c->N_cap,
+                           sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  MDK_CK(cudaStreamSynchronize(c->stream));
+  for (int64_t q = 0; q < n; ++q)
+    for (int k = 0; k < comp; ++k) res[(size_t)q * comp + k] = buf[(size_t)k * n + ord[(size_t)q]];
+  if (n == 0) return MDK_OK;
+  if (on_device) {
+    MDK_CK(cudaMemcpyAsync(out, res.data(), sizeof(double) * res.size(), cudaMemcpyHostToDevice,
+                           c->stream));
+    MDK_CK(cudaStreamSynchronize(c->stream));
+  } else {
+    memcpy(out, res.data(), sizeof(double) * res.size());
+  }
   return MDK_OK;
 }
 
@@ -577,7 +645,10 @@ int mdk_set_workspace(mdk_ctx *c, void *dev_ptr, size_t bytes) {
   fill_sys_params(c);
   Sys &s = c->sys;
   MDK_CK(cudaMemsetAsync(s.st, 0, sizeof(DevStatus), c->stream));
-  MDK_CK(cudaMemsetAsync(s.cell_cnt, 0, sizeof(int32_t) * std::max(c->n_cells, 1), c->stream));
+  MDK_CK(cudaMemsetAsync(s.cell_cnt, 0, sizeof(int32_t) * (c->n_cells + 1), c->stream));
+  if (!c->win_slab.empty())
+    MDK_CK(cudaMemcpyAsync(c->win_slab_dev, c->win_slab.data(), sizeof(double) * c->win_slab.size(),
+                           cudaMemcpyHostToDevice, c->stream));
   MDK_CK(cudaMemcpyAsync(s.grid, c->grids.data(), sizeof(Grid) * c->n_rep,
                          cudaMemcpyHostToDevice, c->stream));
   if (c->N > 0)
@@ -637,6 +708,13 @@ int mdk_get_state(mdk_ctx *c, double *x, double *v, int on_device) {
   if (check_ctx(c)) return MDK_ERR_BAD_ARG;
   if (!c->ws_ok || !c->state_set) return MDK_ERR_ORDER;
   Sys &s = c->sys;
+  if (c->win_on) {
+    int64_t n = 0;
+    int r = device_n(c, &n);
+    if (!r && x) r = gather_by_id(c, n, s.x, 3, x, on_device);
+    if (!r && v) r = gather_by_id(c, n, s.v, 3, v, on_device);
+    return r;
+  }
   if (c->N == 0) return MDK_OK;
   if (on_device) {
     launch_store_state(s, x, v, c->stream);
@@ -654,8 +732,9 @@ int mdk_get_state(mdk_ctx *c, double *x, double *v, int on_device) {
   return MDK_OK;
 }
 
-int mdk_get_natoms(const mdk_ctx *c, int64_t *n) {
+int mdk_get_natoms(mdk_ctx *c, int64_t *n) {
   if (!c || !n) return MDK_ERR_BAD_ARG;
+  if (c->win_on && c->ws_ok && c->state_set) return device_n(c, n);
   *n = c->N;
   return MDK_OK;
 }
@@ -680,7 +759,7 @@ int mdk_build_neighbors(mdk_ctx *c, double rc, double skin) {
 
 int mdk_neighbor_count(mdk_ctx *c, int64_t *total) {
   if (check_ctx(c) || !total) return MDK_ERR_BAD_ARG;
-  if (!c->list_built) return MDK_ERR_ORDER;
+  if (!c->list_built || c->win_on) return MDK_ERR_ORDER;
   std::vector<int32_t> nn((size_t)c->N);
   if (c->N > 0) {
     MDK_CK(cudaMemcpyAsync(nn.data(), c->sys.nnbr, sizeof(int32_t) * c->N, cudaMemcpyDeviceToHost,
@@ -695,7 +774,7 @@ int mdk_neighbor_count(mdk_ctx *c, int64_t *total) {
 
 int mdk_get_neighbors(mdk_ctx *c, int64_t *offsets, int32_t *jout, int32_t *img) {
   if (check_ctx(c) || !offsets) return MDK_ERR_BAD_ARG;
-  if (!c->list_built) return MDK_ERR_ORDER;
+  if (!c->list_built || c->win_on) return MDK_ERR_ORDER;
   const int64_t N = c->N;
   const size_t Nc = (size_t)c->N_cap;
   Sys &s = c->sys;
@@ -765,7 +844,15 @@ int mdk_compute(mdk_ctx *c, double *E, double *F, double *virial, int on_device)
   c->launches += 1;
   MDK_CK(cudaPeekAtLastError());
   c->forces_valid = true;
+  c->per_atom_valid = true;
   const int R = c->n_rep;
+  if (c->win_on && F) {
+    int64_t n = 0;
+    r = device_n(c, &n);
+    if (!r) r = gather_by_id(c, n, s.f, 3, F, on_device);
+    if (r) return r;
+    F = nullptr;  // written
+  }
   if (on_device) {
     if (F) launch_store_forces(s, F, c->stream);
     for (int q = 0; q < R; ++q) {
@@ -797,9 +884,16 @@ int mdk_compute(mdk_ctx *c, double *E, double *F, double *virial, int on_device)
 
 int mdk_get_per_atom(mdk_ctx *c, double *Ui, double *Wi) {
   if (check_ctx(c)) return MDK_ERR_BAD_ARG;
-  if (!c->forces_valid) return MDK_ERR_ORDER;
-  if (c->N == 0) return MDK_OK;
+  if (!c->per_atom_valid) return MDK_ERR_ORDER;
   Sys &s = c->sys;
+  if (c->win_on) {
+    int64_t n = 0;
+    int r = device_n(c, &n);
+    if (!r && Ui) r = gather_by_id(c, n, s.ea, 1, Ui, 0);
+    if (!r && Wi) r = gather_by_id(c, n, s.wa, 6, Wi, 0);
+    return r;
+  }
+  if (c->N == 0) return MDK_OK;
   double *stage = s.tmp;
   launch_store_per_atom(s, Ui ? stage : nullptr, Wi ? stage + c->N : nullptr, c->stream);
   if (Ui) MDK_CK(cudaMemcpyAsync(Ui, stage, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
@@ -853,6 +947,7 @@ int mdk_step(mdk_ctx *c, double dt, int64_t nsteps) {
   MDK_CK(cudaPeekAtLastError());
   c->steps_done += nsteps;
   c->forces_valid = true;
+  c->per_atom_valid = false;
   return MDK_OK;
 }
 
@@ -915,15 +1010,20 @@ int mdk_last_device_status(mdk_ctx *c, int *bits) {
 int mdk_set_piston(mdk_ctx *c, double u_p, const uint8_t *is_piston) {
   if (check_ctx(c) || !isfinite(u_p)) return MDK_ERR_BAD_ARG;
   if (!c->ws_ok || !c->state_set) return MDK_ERR_ORDER;
+  if (c->win_on) return MDK_ERR_ORDER;  // ids are no longer 0..N-1
   c->u_p = u_p;
   c->sys.u_p = u_p;
+  // the host copy of the info words keeps the flags across a new workspace
+  for (int64_t q = 0; q < c->N; ++q)
+    c->info0[(size_t)q] = (c->info0[(size_t)q] & ~kInfoPiston) |
+                          ((is_piston && is_piston[q]) ? kInfoPiston : 0u);
   const uint8_t *dflags = nullptr;
   if (is_piston && c->N > 0) {
     uint8_t *stage = reinterpret_cast<uint8_t *>(c->sys.tmp);
     MDK_CK(cudaMemcpyAsync(stage, is_piston, (size_t)c->N, cudaMemcpyHostToDevice, c->stream));
     dflags = stage;
   }
-  k_set_piston<<<(unsigned)((c->N_cap + 255) / 256 + 1), 256, 0, c->stream>>>(c->sys, dflags);
+  launch_set_piston(c->sys, dflags, c->N, c->stream);
   MDK_CK(cudaPeekAtLastError());
   MDK_CK(cudaStreamSynchronize(c->stream));
   // the gather copies carry the info word: regenerate them with a rebuild
@@ -970,15 +1070,102 @@ int mdk_get_profile(mdk_ctx *c, double *out) {
   return MDK_OK;
 }
 
-int mdk_set_window(mdk_ctx *c, double, double, const double *, const double *, int64_t, double,
-                   double, double) {
-  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
-  return MDK_ERR_BAD_ARG;
+int mdk_set_window(mdk_ctx *c, double L_behind, double L_ahead, const double *slab_x,
+                   const double *slab_v, int64_t n_slab, double slab_lx, double slab_gap,
+                   double slab_mass, double piston_depth) {
+  if (check_ctx(c) || c->n_rep != 1 || !slab_x || !slab_v || n_slab < 1 ||
+      n_slab >= ((int64_t)1 << 26) || !(slab_lx > 0.0) || !(L_behind >= 0.0) ||
+      !(L_ahead >= 0.0) || !isfinite(slab_gap) || !(slab_mass > 0.0) || !(piston_depth >= 0.0))
+    return MDK_ERR_BAD_ARG;
+  int t = 0;
+  while (t < c->n_types && c->type_mass[t] != slab_mass) ++t;
+  if (t == c->n_types) {
+    if (c->n_types == kMaxTypes) return MDK_ERR_BAD_ARG;
+    c->type_mass[c->n_types++] = slab_mass;
+  }
+  c->win_on = true;
+  c->win_L_behind = L_behind;
+  c->win_L_ahead = L_ahead;
+  c->win_slab_lx = slab_lx;
+  c->win_gap = slab_gap;
+  c->win_depth = piston_depth;
+  c->win_info = (uint32_t)t;
+  c->win_slab.assign((size_t)n_slab * 6, 0.0);
+  for (int64_t q = 0; q < n_slab; ++q)
+    for (int k = 0; k < 3; ++k) {
+      c->win_slab[(size_t)q * 6 + k] = slab_x[3 * q + k];
+      c->win_slab[(size_t)q * 6 + 3 + k] = slab_v[3 * q + k];
+    }
+  if (!c->ws_ok) return MDK_OK;
+  if (n_slab > c->win_slab_cap) {  // the slab area of the workspace is too small
+    c->need_ws = true;
+    return MDK_ERR_WORKSPACE;
+  }
+  MDK_CK(cudaMemcpyAsync(c->win_slab_dev, c->win_slab.data(), sizeof(double) * c->win_slab.size(),
+                         cudaMemcpyHostToDevice, c->stream));
+  fill_sys_params(c);
+  MDK_CK(cudaStreamSynchronize(c->stream));
+  return MDK_OK;
 }
 
-int mdk_profiles(mdk_ctx *c, int, double, double, int, double, double *, int) {
+int mdk_get_ids(mdk_ctx *c, int64_t *ids) {
+  if (check_ctx(c) || !ids) return MDK_ERR_BAD_ARG;
+  if (!c->ws_ok || !c->state_set) return MDK_ERR_ORDER;
+  int64_t n = 0;
+  int r = device_n(c, &n);
+  if (r) return r;
+  std::vector<int32_t> ord, id;
+  r = caller_order(c, n, ord, id);
+  if (r) return r;
+  for (int64_t q = 0; q < n; ++q) ids[q] = id[(size_t)ord[(size_t)q]];
+  return MDK_OK;
+}
+
+int mdk_window_counts(mdk_ctx *c, int64_t *inserted, int64_t *deleted) {
   if (check_ctx(c)) return MDK_ERR_BAD_ARG;
-  return MDK_ERR_BAD_ARG;
+  if (!c->ws_ok) return MDK_ERR_WORKSPACE;
+  DevStatus st;
+  int r = read_status(c, &st);
+  if (r) return r;
+  if (inserted) *inserted = st.n_inserted;
+  if (deleted) *deleted = st.n_deleted;
+  return MDK_OK;
+}
+
+int mdk_profiles(mdk_ctx *c, int axis, double origin, double bin_w, int nbins,
+                 double cross_area, double *out, int on_device) {
+  if (check_ctx(c) || axis < 0 || axis > 2 || !(bin_w > 0.0) || nbins < 1 || !out ||
+      !(cross_area > 0.0))
+    return MDK_ERR_BAD_ARG;
+  // accumulators live in the sort scratch (9 N_cap doubles)
+  if ((size_t)nbins * (kProfWidth + kProfOut) > 9 * (size_t)std::max<int64_t>(c->N_cap, 1))
+    return MDK_ERR_BAD_ARG;
+  int r = ensure_ready(c);
+  if (r) return r;
+  if (!c->list_built) {
+    r = build_now(c);
+    if (r) return r;
+  }
+  // per-atom energies and virials at the current positions
+  if (!c->per_atom_valid) {
+    r = force_pass(c, kForceOnly, 1, 0.0);
+    if (r) return r;
+    c->forces_valid = true;
+    c->per_atom_valid = true;
+  }
+  double *acc = c->sys.tmp;
+  launch_profiles(c->sys, axis, origin, bin_w, nbins, cross_area, acc, c->stream);
+  c->launches += 5;
+  MDK_CK(cudaPeekAtLastError());
+  acc += (size_t)nbins * kProfWidth;  // the outputs follow the accumulators
+  const size_t bytes = sizeof(double) * kProfOut * nbins;
+  if (on_device) {
+    MDK_CK(cudaMemcpyAsync(out, acc, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    return MDK_OK;
+  }
+  MDK_CK(cudaMemcpyAsync(out, acc, bytes, cudaMemcpyDeviceToHost, c->stream));
+  MDK_CK(cudaStreamSynchronize(c->stream));
+  return MDK_OK;
 }
 
 }  // extern "C"

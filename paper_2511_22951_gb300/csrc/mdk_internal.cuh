@@ -3,13 +3,15 @@
 //
 // Layout in HBM (all inside the caller's workspace, atoms in cell order):
 //   x, v, f, xref : FP64 SoA, component c of atom i at [c * N_cap + i]
-//   pf            : float4 per atom, position relative to its cell origin
-//                   (x - O(cell)) with the info word in .w; written at each
-//                   list build, used by the build's FP32 pre-filter
+//   pf            : float4 per atom, position relative to its cell centre
+//                   with the info word in .w; written at each list build,
+//                   used by the build's FP32 pre-filter (NaN for far atoms)
 //   pg[2]         : per-step gather copy, double-buffered; float4 (mixed) or
-//                   double4 (FP64) of x - O(cell) with info in .w
+//                   32-byte FP64 vector of x - centre(cell), info in .w
 //   info          : type (bits 0-3) | piston (bit 4) | far (bit 5) |
 //                   replica (bits 8-31)
+//   cell buckets  : n_cells real cells + 1 bucket for atoms a moving window
+//                   deletes (the counting sort moves them past the kept atoms)
 //   nbr           : Verlet lists in groups of 8 entries per atom (ell_index),
 //                   packed j (bits 0-25) | (s_x+1) << 26 | (s_y+1) << 28 |
 //                   (s_z+1) << 30, s = stencil offset of j's cell
@@ -46,8 +48,16 @@ struct DevStatus {
   long long n_builds;
   long long n_steps;
   int since_build;       // steps since the last build
-  int pad0;
-  double scratch[4];
+  int next_id;           // id of the next atom a moving window appends
+  // moving window (order-preserving integer keys of doubles, for atomics)
+  long long key_front, key_xmax, key_xmin;
+  double win_cut;        // atoms with x below are deleted at this build
+  double win_x0;         // x offset of the first appended slab copy
+  int win_insert;        // atoms appended at this build
+  int win_n_old;         // atom count before the append
+  int win_id0;           // id of the first appended atom
+  int win_active;        // the window acts at this build (builds during steps)
+  long long n_inserted, n_deleted;
 };
 
 // one replica's box and cell grid
@@ -66,8 +76,8 @@ struct Sys {
   int N_cap;
   int nmax;
   int n_rep;
-  int n_cells;
-  int n_scan_blocks;
+  int n_cells;           // real cells; bucket n_cells holds atoms a window deletes
+  int n_scan_blocks;     // scan blocks over n_cells + 1 buckets
   // per-atom arrays
   double *x, *v, *f, *xref;
   double *tmp;              // 9 * N_cap doubles of sort scratch
@@ -91,10 +101,26 @@ struct Sys {
   double half_skin2;        // (skin/2)^2
   int rebuild_every;
   // integration
+  double mass[kMaxTypes];         // m of each type (u)
   double acc_over_m[kMaxTypes];   // kAcc / m for each type
   double ke_m[kMaxTypes];         // m / (2 kAcc): K in eV from v^2
   double u_p;                     // piston speed
+  // moving window along x (off when win_on == 0)
+  int win_on;
+  int n_slab;
+  double L_behind, L_ahead, slab_lx, slab_gap, piston_depth;
+  const double *slab;             // fresh slab: [n_slab][6] = x, y, z, vx, vy, vz
+  uint32_t slab_info;             // info word of appended atoms
 };
+
+// order-preserving map of a double onto a signed 64-bit key (for atomicMax/Min)
+__device__ __forceinline__ long long dkey(double v) {
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : b ^ 0x7FFFFFFFFFFFFFFFLL;
+}
+__device__ __forceinline__ double dkey_inv(long long k) {
+  return __longlong_as_double(k >= 0 ? k : k ^ 0x7FFFFFFFFFFFFFFFLL);
+}
 
 struct LJParams {
   double eps4, eps24, sig2, rc2, u_shift, du_rc, rc;
@@ -219,6 +245,7 @@ struct StepArgs {
 };
 
 void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, cudaStream_t st);
+void launch_set_piston(const Sys &s, const uint8_t *flags, int64_t n_flags, cudaStream_t st);
 int scan_blocks_for(int n_cells);
 void launch_set_rebuild_flag(const Sys &s, cudaStream_t st);
 void launch_lj(const Sys &s, const LJParams &p, int precision, Mode mode, StepArgs a,
@@ -234,6 +261,12 @@ void launch_load_state(const Sys &s, const double *x_aos, const double *v_aos,
 void launch_store_state(const Sys &s, double *x_aos, double *v_aos, cudaStream_t st);
 void launch_store_forces(const Sys &s, double *f_aos, cudaStream_t st);
 void launch_store_per_atom(const Sys &s, double *ua, double *wa, cudaStream_t st);
+// Appendix profiles: kProfOut outputs per bin (see mdk_profiles), computed in
+// an accumulator of kProfWidth doubles per bin
+constexpr int kProfOut = 17;
+constexpr int kProfWidth = 24;
+void launch_profiles(const Sys &s, int axis, double origin, double bin_w, int nbins,
+                     double cross_area, double *acc, cudaStream_t st);
 int eam_smem_bytes(const EAMParams &p, int precision, int pass);
 int configure_eam_smem(int bytes_pass1, int bytes_pass2, int precision);
 

@@ -61,7 +61,9 @@ SIGNATURES = {
     "mdk_get_thermo": [_P, _P, _I, ctypes.POINTER(_I)],
     "mdk_get_counters": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "mdk_set_piston": [_P, _D, _P],
-    "mdk_set_window": [_P, _D, _D, _P, _P, _I64, _D, _D, _D],
+    "mdk_set_window": [_P, _D, _D, _P, _P, _I64, _D, _D, _D, _D],
+    "mdk_get_ids": [_P, _P],
+    "mdk_window_counts": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "mdk_profiles": [_P, _I, _D, _D, _I, _D, _P, _I],
     "mdk_status_string": [_I],
     "mdk_last_device_status": [_P, ctypes.POINTER(_I)],
@@ -337,6 +339,30 @@ class Context:
         keys = ("force_ms", "force_passes", "rebuild_ms", "rebuild_chains", "kernels",
                 "builds", "kick_ms", "kicks")
         return dict(zip(keys, out.tolist()))
+
+    def set_window(self, L_behind, L_ahead, slab_x, slab_v, slab_lx, slab_gap, slab_mass,
+                   piston_depth):
+        sx = _host_f64(slab_x, (-1, 3))
+        sv = _host_f64(slab_v, (-1, 3))
+        r = self.lib.mdk_set_window(self.h, L_behind, L_ahead, _ptr(sx), _ptr(sv), sx.shape[0],
+                                    slab_lx, slab_gap, slab_mass, piston_depth)
+        if r == MDK_ERR_WORKSPACE:
+            self.alloc_workspace()
+            r = self.lib.mdk_set_window(self.h, L_behind, L_ahead, _ptr(sx), _ptr(sv),
+                                        sx.shape[0], slab_lx, slab_gap, slab_mass, piston_depth)
+        _check(r, "mdk_set_window")
+
+    def ids(self):
+        n = self.natoms()
+        out = np.zeros(n, dtype=np.int64)
+        _check(self.lib.mdk_get_ids(self.h, _ptr(out)), "mdk_get_ids")
+        return out
+
+    def window_counts(self):
+        a, b = _I64(), _I64()
+        _check(self.lib.mdk_window_counts(self.h, ctypes.byref(a), ctypes.byref(b)),
+               "mdk_window_counts")
+        return int(a.value), int(b.value)
 
     def set_piston(self, u_p, flags):
         f = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8)
