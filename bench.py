@@ -225,6 +225,7 @@ def main():
     ctx = mdk.make_context(wl, precision=prec)
     stream = ctx.stream
     n_avg = float(ctx.neighbor_counts().mean())
+    tpa, block, _ = ctx.autotune()
 
     # warm-up (untimed)
     ctx.step(wl.dt, args.warmup, check=True)
@@ -319,6 +320,8 @@ def main():
             "config": {"workload": wl.name, "atoms": n_atoms, "potential": wl.potential,
                        "precision": prec, "dt_fs": wl.dt, "skin_A": wl.skin,
                        "neighbors_per_atom": n_avg,
+                       "launch": {"threads_per_atom": tpa, "block": block,
+                                  "picked_by": "mdk_autotune"},
                        "rebuild": "when an atom moved > skin/2 since the last build",
                        "list_builds_in_timed_region": prof["builds"],
                        "l2": "inputs larger than L2 (~4 GB touched per step); no flush",

@@ -340,6 +340,22 @@ int mdk_lj_compute_noalloc(const double *x, int64_t N, const double box_lo[3],
                            double sigma, double rc, int shift_mode, double *F, double *E,
                            void *cuda_stream);
 
+/* ---- launch shape ---------------------------------------------------------- */
+
+/*
+ * Autotuner: time every launch shape of the force kernels -- threads per atom
+ * in {1, 2, 4} x threads per block in {128, 256, 512} -- on this context's
+ * system (reps force passes each, CUDA events on the context's stream) and
+ * keep the fastest for later calls.  Outputs may be NULL.  Small systems
+ * (few atoms per SM) and long lists favour several threads per atom.  The
+ * state must be set; the lists are built if needed.  (No paper counterpart:
+ * the paper chunks arrays over a thread pool.)
+ */
+int mdk_autotune(mdk_ctx *ctx, int reps, int *tpa, int *block, double *ms);
+
+/* Set the launch shape directly (tpa in {1, 2, 4}, block in {128, 256, 512}). */
+int mdk_set_launch(mdk_ctx *ctx, int tpa, int block);
+
 /* ---- measurement ----------------------------------------------------------- */
 
 /*

@@ -1,0 +1,374 @@
+// k_eam.cu -- two-pass embedded-atom force loop (GB300, sm_103a).
+//
+// Paper passages: single-element EAM read from a table (Sec. "Comparison of
+// aluminum shock Hugoniot ..."), forces f_i = sum_j V'(r_ij) r_ji / r_ji
+// (Sec. "Potentials support"), in the standard embedded-atom form
+//   U = 1/2 sum_ij phi(r_ij) + sum_i F(rho_i),   rho_i = sum_j rho(r_ij),
+//   f_i = sum_j [phi'(r) + (F'(rho_i) + F'(rho_j)) rho'(r)] r_ji / r.
+// Pass 1 sums rho_i and evaluates F(rho_i), F'(rho_i) (FP64, once per atom);
+// pass 2 needs F'(rho_j) of every neighbour, so it is a second launch.  Both
+// stage their spline tables in shared memory once per block and run on a
+// persistent grid (one or two blocks per SM), so a table is read from L2 a
+// few hundred times per launch, not once per atom tile.  T lanes own one atom
+// (autotuned), as in the LJ kernel.
+#include "k_pair.cuh"
+
+namespace mdk {
+namespace {
+
+using namespace pair;
+
+template <class P, bool ENERGY, int T>
+__global__ void __launch_bounds__(512) k_rho(Sys s, EAMParams ep, StepArgs a) {
+  using GP = G<P>;
+  using R = typename GP::R;
+  using V = typename GP::V;
+  using T1 = typename GP::Tab1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T1 *rt = reinterpret_cast<T1 *>(smem);
+  {
+    const T1 *src = GP::tab1(ep);
+    const int n = GP::n1(ep);
+    for (int q = threadIdx.x; q < n; q += blockDim.x) rt[q] = src[q];
+  }
+  __syncthreads();
+  const int N = s.st->N;
+  const size_t Nc = s.N_cap;
+  const V *__restrict__ pg = (const V *)s.pg[a.cur];
+  const R rc2 = sizeof(R) == 8 ? (R)ep.rc2 : (R)ep.rc2f;
+  const R inv_dr = sizeof(R) == 8 ? (R)ep.inv_dr : (R)ep.inv_drf;
+  const int kmax = ep.nr - 2;
+  const Tiles<T> tl;
+  for (int w = tl.w0; w * Tiles<T>::kPerWarp < N; w += tl.nw) {
+    const int i = tl.atom(w);
+    const bool valid = i < N;
+    V pi;
+    R hx = 0, hy = 0, hz = 0;
+    int nn = 0;
+    if (valid) {
+      pi = GP::ld(pg + i);
+      GP::h(s.grid[GP::info(pi) >> 8], hx, hy, hz);
+      nn = min(s.nnbr[i], s.nmax);
+    }
+    Acc<R> rho;
+    R br = 0;
+    walk<T>(
+        s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pg + j); },
+        [&](uint32_t ent, const V &pj) {
+          const R dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
+          const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
+          const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
+          const R r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < rc2) {
+            const R r = GP::sqr(r2);
+            const R u = r * inv_dr;
+            int kk = (int)u;
+            kk = kk > kmax ? kmax : kk;
+            const R t = u - (R)kk;
+            br += GP::val1(rt, kk, t);
+          }
+        },
+        [&] {
+          rho.add(br);
+          br = 0;
+        });
+    const double rho_i = lanes_sum<T>(rho.get());
+    if (!valid || tl.t != 0) continue;
+    // F(rho_i) and F'(rho_i) in FP64 (once per atom)
+    double Fv, dF;
+    if (rho_i > ep.rho_max) {
+      // above the table: linear continuation of the last knot
+      const int n = ep.nrho;
+      const double2 a0 = ep.F64[n - 2], a1 = ep.F64[n - 1];
+      const double d1 = herm_der<double>(1.0, a0.x, a0.y, a1.x, a1.y) * ep.inv_drho;
+      Fv = a1.x + d1 * (rho_i - ep.rho_max);
+      dF = d1;
+      atomicOr(&s.st->bits, isfinite(rho_i) ? kStRhoRange : kStNonfinite);
+    } else if (!(rho_i == rho_i)) {
+      Fv = 0.0;
+      dF = 0.0;
+      atomicOr(&s.st->bits, kStNonfinite);
+    } else {
+      // inside (or below, by the first piece extended) the table
+      const double u = rho_i * ep.inv_drho;
+      int kk = (int)floor(u);
+      kk = kk > ep.nrho - 2 ? ep.nrho - 2 : (kk < 0 ? 0 : kk);
+      const double t = u - (double)kk;
+      const double2 a0 = ep.F64[kk], a1 = ep.F64[kk + 1];
+      Fv = herm_val<double>(t, a0.x, a0.y, a1.x, a1.y);
+      dF = herm_der<double>(t, a0.x, a0.y, a1.x, a1.y) * ep.inv_drho;
+    }
+    s.rho[i] = rho_i;
+    ((R *)s.fp)[i] = (R)dF;
+    if (ENERGY) s.ea[i] = Fv;
+  }
+}
+
+template <class P, int MODE, bool ENERGY, int T>
+__global__ void __launch_bounds__(512) k_eam(Sys s, EAMParams ep, StepArgs a) {
+  using GP = G<P>;
+  using R = typename GP::R;
+  using V = typename GP::V;
+  using T2 = typename GP::Tab2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T2 *pt = reinterpret_cast<T2 *>(smem);
+  T2 *rt = pt + ep.nr;
+  {
+    const T2 *sp = GP::phi2(ep), *sr = GP::rho2(ep);
+    for (int q = threadIdx.x; q < ep.nr; q += blockDim.x) {
+      pt[q] = sp[q];
+      rt[q] = sr[q];
+    }
+  }
+  __syncthreads();
+  const int N = s.st->N;
+  const size_t Nc = s.N_cap;
+  const V *__restrict__ pg = (const V *)s.pg[a.cur];
+  const R *__restrict__ fpa = (const R *)s.fp;
+  const R rc2 = sizeof(R) == 8 ? (R)ep.rc2 : (R)ep.rc2f;
+  const R inv_dr = sizeof(R) == 8 ? (R)ep.inv_dr : (R)ep.inv_drf;
+  const int kmax = ep.nr - 2;
+  const Tiles<T> tl;
+  for (int w = tl.w0; w * Tiles<T>::kPerWarp < N; w += tl.nw) {
+    const int i = tl.atom(w);
+    const bool valid = i < N;
+    V pi;
+    uint32_t inf = 0;
+    R hx = 0, hy = 0, hz = 0, fpi = 0;
+    int nn = 0;
+    if (valid) {
+      pi = GP::ld(pg + i);
+      inf = GP::info(pi);
+      GP::h(s.grid[inf >> 8], hx, hy, hz);
+      fpi = fpa[i];
+      nn = min(s.nnbr[i], s.nmax);
+    }
+    Acc<R> fx, fy, fz;
+    R e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+    R bx = 0, by = 0, bz = 0;
+    struct Rec {
+      V p;
+      R fp;
+    };
+    walk<T>(
+        s.nbr, Nc, i, nn, tl.t,
+        [&](uint32_t j) {
+          Rec q;
+          q.p = GP::ld(pg + j);
+          q.fp = __ldg(fpa + j);
+          return q;
+        },
+        [&](uint32_t ent, const Rec &q) {
+          const V &pj = q.p;
+          const R dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
+          const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
+          const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
+          const R r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < rc2) {
+            const R inv_r = GP::rsq(r2);
+            const R r = r2 * inv_r;
+            const R u = r * inv_dr;
+            int kk = (int)u;
+            kk = kk > kmax ? kmax : kk;
+            const R t = u - (R)kk;
+            const R dphi = GP::der2(pt, kk, t) * inv_dr;
+            const R drho = GP::der2(rt, kk, t) * inv_dr;
+            const R fr = (dphi + (fpi + q.fp) * drho) * inv_r;  // V'(r)/r
+            bx += fr * dx;
+            by += fr * dy;
+            bz += fr * dz;
+            if (ENERGY) {
+              e += R(0.5) * GP::val2(pt, ep, kk, t);
+              const R hf = R(-0.5) * fr;
+              w0 += hf * dx * dx;
+              w1 += hf * dy * dy;
+              w2 += hf * dz * dz;
+              w3 += hf * dx * dy;
+              w4 += hf * dx * dz;
+              w5 += hf * dy * dz;
+            }
+          }
+        },
+        [&] {
+          fx.add(bx);
+          fy.add(by);
+          fz.add(bz);
+          bx = by = bz = 0;
+        });
+    const double Fx = lanes_sum<T>(fx.get()), Fy = lanes_sum<T>(fy.get()),
+                 Fz = lanes_sum<T>(fz.get());
+    double E = 0, W0 = 0, W1 = 0, W2 = 0, W3 = 0, W4 = 0, W5 = 0;
+    if (ENERGY) {
+      E = lanes_sum<T>((double)e);
+      W0 = lanes_sum<T>((double)w0);
+      W1 = lanes_sum<T>((double)w1);
+      W2 = lanes_sum<T>((double)w2);
+      W3 = lanes_sum<T>((double)w3);
+      W4 = lanes_sum<T>((double)w4);
+      W5 = lanes_sum<T>((double)w5);
+    }
+    if (valid && tl.t == 0) {
+      if (ENERGY) {
+        s.ea[i] = s.ea[i] + E;
+        s.wa[i] = W0;
+        s.wa[Nc + i] = W1;
+        s.wa[2 * Nc + i] = W2;
+        s.wa[3 * Nc + i] = W3;
+        s.wa[4 * Nc + i] = W4;
+        s.wa[5 * Nc + i] = W5;
+      }
+      epilogue<P, MODE, ENERGY>(s, a, i, inf, Fx, Fy, Fz);
+    }
+  }
+}
+
+// ---- tables: knot slopes (3-point differences) -> per-knot data ---------------------
+__device__ __forceinline__ double hslope(const double *y, int n, int k) {
+  if (k == 0) return 0.5 * (-3.0 * y[0] + 4.0 * y[1] - y[2]);
+  if (k == n - 1) return 0.5 * (3.0 * y[n - 1] - 4.0 * y[n - 2] + y[n - 3]);
+  return 0.5 * (y[k + 1] - y[k - 1]);
+}
+
+__global__ void k_eam_prepare(int nr, int nrho, const double *phi, const double *rho,
+                              const double *F, EAMTablesDev o) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nr) {
+    const double mp = hslope(phi, nr, k), mr = hslope(rho, nr, k);
+    o.phi64[k] = make_double2(phi[k], mp);
+    o.rho64[k] = make_double2(rho[k], mr);
+    const double dp = k + 1 < nr ? phi[k + 1] - phi[k] : 0.0;
+    const double dr = k + 1 < nr ? rho[k + 1] - rho[k] : 0.0;
+    o.phi_d32[k] = make_float2((float)dp, (float)mp);
+    o.rho_d32[k] = make_float2((float)dr, (float)mr);
+    o.phi_v32[k] = (float)phi[k];
+    if (k + 1 < nr)
+      o.rho_i32[k] = make_float4((float)rho[k], (float)dr, (float)mr, (float)hslope(rho, nr, k + 1));
+  }
+  if (k < nrho) o.F64[k] = make_double2(F[k], hslope(F, nrho, k));
+}
+
+inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <class K>
+int grid_for(K kern, int block, int smem, long long threads_needed) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  const int g = sm_count() * occ;
+  const int need = nblk(threads_needed > 0 ? threads_needed : 1, block);
+  return g < need ? g : need;
+}
+
+template <class P, int MODE, bool EN, int T>
+void go(const Sys &s, const EAMParams &p, StepArgs a, int block, int prec, cudaStream_t st) {
+  const int b1 = eam_smem_bytes(p, prec, 1), b2 = eam_smem_bytes(p, prec, 2);
+  auto k1 = k_rho<P, EN, T>;
+  auto k2 = k_eam<P, MODE, EN, T>;
+  static int cb = 0, cs = -1, g1 = 0, g2 = 0, cap = -1;
+  if (cb != block || cs != b2 || cap != s.N_cap) {
+    g1 = grid_for(k1, block, b1, (long long)s.N_cap * T);
+    g2 = grid_for(k2, block, b2, (long long)s.N_cap * T);
+    cb = block;
+    cs = b2;
+    cap = s.N_cap;
+  }
+  k1<<<g1, block, b1, st>>>(s, p, a);
+  k2<<<g2, block, b2, st>>>(s, p, a);
+}
+
+template <class P, int MODE, bool EN>
+void by_tpa(const Sys &s, const EAMParams &p, StepArgs a, const LaunchCfg &c, int prec,
+            cudaStream_t st) {
+  if (c.tpa == 4)
+    go<P, MODE, EN, 4>(s, p, a, c.block, prec, st);
+  else if (c.tpa == 2)
+    go<P, MODE, EN, 2>(s, p, a, c.block, prec, st);
+  else
+    go<P, MODE, EN, 1>(s, p, a, c.block, prec, st);
+}
+
+template <class P, int MODE>
+void by_energy(const Sys &s, const EAMParams &p, StepArgs a, const LaunchCfg &c, int prec,
+               cudaStream_t st) {
+  if (a.energy)
+    by_tpa<P, MODE, true>(s, p, a, c, prec, st);
+  else
+    by_tpa<P, MODE, false>(s, p, a, c, prec, st);
+}
+
+template <class P>
+void by_mode(const Sys &s, const EAMParams &p, Mode m, StepArgs a, const LaunchCfg &c, int prec,
+             cudaStream_t st) {
+  if (m == kForceOnly)
+    by_energy<P, kForceOnly>(s, p, a, c, prec, st);
+  else if (m == kStep)
+    by_energy<P, kStep>(s, p, a, c, prec, st);
+  else
+    by_energy<P, kFinal>(s, p, a, c, prec, st);
+}
+
+template <class K>
+cudaError_t smem_attr(K k, int bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <class P, int T>
+cudaError_t attrs_t(int b1, int b2) {
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = smem_attr(k_rho<P, true, T>, b1);
+  if (e == cudaSuccess) e = smem_attr(k_rho<P, false, T>, b1);
+  if (e == cudaSuccess) e = smem_attr(k_eam<P, kForceOnly, true, T>, b2);
+  if (e == cudaSuccess) e = smem_attr(k_eam<P, kForceOnly, false, T>, b2);
+  if (e == cudaSuccess) e = smem_attr(k_eam<P, kStep, true, T>, b2);
+  if (e == cudaSuccess) e = smem_attr(k_eam<P, kStep, false, T>, b2);
+  if (e == cudaSuccess) e = smem_attr(k_eam<P, kFinal, true, T>, b2);
+  if (e == cudaSuccess) e = smem_attr(k_eam<P, kFinal, false, T>, b2);
+  return e;
+}
+
+template <class P>
+int attrs(int b1, int b2) {
+  cudaError_t e = attrs_t<P, 1>(b1, b2);
+  if (e == cudaSuccess) e = attrs_t<P, 2>(b1, b2);
+  if (e == cudaSuccess) e = attrs_t<P, 4>(b1, b2);
+  return e == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+int eam_smem_bytes(const EAMParams &p, int precision, int pass) {
+  if (precision == 0) return (pass == 1 ? 1 : 2) * p.nr * (int)sizeof(double2);
+  return pass == 1 ? (p.nr - 1) * (int)sizeof(float4) : 2 * p.nr * (int)sizeof(float2);
+}
+
+int configure_eam_smem(int b1, int b2, int precision) {
+  return precision == 0 ? attrs<Fp64>(b1, b2) : attrs<Mixed>(b1, b2);
+}
+
+void launch_eam(const Sys &s, const EAMParams &p, int precision, Mode mode, StepArgs a,
+                const LaunchCfg &cfg, cudaStream_t st) {
+  if (precision == 0)
+    by_mode<Fp64>(s, p, mode, a, cfg, 0, st);
+  else
+    by_mode<Mixed>(s, p, mode, a, cfg, 1, st);
+}
+
+void launch_eam_prepare(const EAMParams &p, const double *phi, const double *rho,
+                        const double *F, EAMTablesDev out, cudaStream_t st) {
+  const int n = p.nr > p.nrho ? p.nr : p.nrho;
+  k_eam_prepare<<<nblk(n, 256), 256, 0, st>>>(p.nr, p.nrho, phi, rho, F, out);
+}
+
+}  // namespace mdk

@@ -1,0 +1,187 @@
+// k_lj.cu -- Lennard-Jones force loop with the fused velocity-Verlet update
+// (GB300, sm_103a).
+//
+// Paper passages: f_i = sum_j V'(r_ij) r_ji / r_ji (Sec. "Potentials
+// support"); m r'' = f integrated by velocity Verlet (Sec. "Molecular
+// dynamics").  V(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6] - shift, cut at rc.
+//
+// Launch bounds: at most 256 threads per block and 5 blocks per SM, so the
+// kernel fits 48 registers (40 resident warps per SM; a few spilled constants
+// are cheaper than the lost occupancy).
+// T lanes own one atom (T = 1, 2 or 4, picked by the autotuner): lane t walks
+// the list groups t, t + T, ... of the full Verlet list, the lanes' sums are
+// combined with shuffles in a fixed order, and lane 0 runs the epilogue
+// (store the force, or finish step n and start step n + 1).  The pair vector
+// is d = (p_j - p_i) + s h with p the cell-centre offsets of the gather copy
+// and s the stencil offset stored in the list entry, so FP32 pair arithmetic
+// never subtracts two large coordinates.
+#include "k_pair.cuh"
+
+namespace mdk {
+namespace {
+
+using namespace pair;
+
+template <class P, int MODE, bool ENERGY, int SHIFT, int T>
+__global__ void __launch_bounds__(256, 5) k_lj(Sys s, LJParams lp, StepArgs a) {
+  using GP = G<P>;
+  using R = typename GP::R;
+  using V = typename GP::V;
+  const int N = s.st->N;
+  const size_t Nc = s.N_cap;
+  const V *__restrict__ pg = (const V *)s.pg[a.cur];
+  const bool f64 = sizeof(R) == 8;
+  const R rc2 = f64 ? (R)lp.rc2 : (R)lp.rc2f;
+  const R sig2 = f64 ? (R)lp.sig2 : (R)lp.sig2f;
+  const R eps24 = f64 ? (R)lp.eps24 : (R)lp.eps24f;
+  const R eps4 = f64 ? (R)lp.eps4 : (R)lp.eps4f;
+  const R ush = f64 ? (R)lp.u_shift : (R)lp.u_shiftf;
+  const R durc = f64 ? (R)lp.du_rc : (R)lp.du_rcf;
+  const R rcut = f64 ? (R)lp.rc : (R)lp.rcf;
+  // one warp tile per warp (no shared tables to amortise, so no persistent
+  // loop: the loop's extra state costs registers and occupancy)
+  const Tiles<T> tl;
+  {
+    const int w = tl.w0;
+    const int i = tl.atom(w);
+    // T = 1: a lane is an atom and exits on its own; T > 1: the whole warp
+    // stays for the shuffles and idle lanes carry valid = false
+    if (T == 1 ? i >= N : w * Tiles<T>::kPerWarp >= N) return;
+    const bool valid = T == 1 || i < N;
+    V pi;
+    uint32_t inf = 0;
+    R hx = 0, hy = 0, hz = 0;
+    int nn = 0;
+    if (valid) {
+      pi = GP::ld(pg + i);
+      inf = GP::info(pi);
+      GP::h(s.grid[inf >> 8], hx, hy, hz);
+      nn = min(s.nnbr[i], s.nmax);
+    }
+    Acc<R> fx, fy, fz;
+    R e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+    R bx = 0, by = 0, bz = 0;  // block sums of four pairs
+    walk<T>(
+        s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pg + j); },
+        [&](uint32_t ent, const V &pj) {
+          const R dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
+          const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
+          const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
+          const R r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < rc2) {
+            const R inv = GP::rcp(r2);
+            const R s2 = sig2 * inv;
+            const R s6 = s2 * s2 * s2;
+            R fr = -eps24 * (R(2) * s6 * s6 - s6) * inv;  // V'(r)/r
+            R r = 0;
+            if (SHIFT == 2) {
+              r = GP::sqr(r2);
+              fr -= durc / r;
+            }
+            bx += fr * dx;
+            by += fr * dy;
+            bz += fr * dz;
+            if (ENERGY) {
+              R v = eps4 * (s6 * s6 - s6) - ush;
+              if (SHIFT == 2) v -= (r - rcut) * durc;
+              e += R(0.5) * v;
+              const R hf = R(-0.5) * fr;  // r_ij = -d
+              w0 += hf * dx * dx;
+              w1 += hf * dy * dy;
+              w2 += hf * dz * dz;
+              w3 += hf * dx * dy;
+              w4 += hf * dx * dz;
+              w5 += hf * dy * dz;
+            }
+          }
+        },
+        [&] {
+          fx.add(bx);
+          fy.add(by);
+          fz.add(bz);
+          bx = by = bz = 0;
+        });
+    const double Fx = lanes_sum<T>(fx.get()), Fy = lanes_sum<T>(fy.get()),
+                 Fz = lanes_sum<T>(fz.get());
+    double E = 0, W0 = 0, W1 = 0, W2 = 0, W3 = 0, W4 = 0, W5 = 0;
+    if (ENERGY) {
+      E = lanes_sum<T>((double)e);
+      W0 = lanes_sum<T>((double)w0);
+      W1 = lanes_sum<T>((double)w1);
+      W2 = lanes_sum<T>((double)w2);
+      W3 = lanes_sum<T>((double)w3);
+      W4 = lanes_sum<T>((double)w4);
+      W5 = lanes_sum<T>((double)w5);
+    }
+    if (valid && tl.t == 0) {
+      if (ENERGY) {
+        s.ea[i] = E;
+        s.wa[i] = W0;
+        s.wa[Nc + i] = W1;
+        s.wa[2 * Nc + i] = W2;
+        s.wa[3 * Nc + i] = W3;
+        s.wa[4 * Nc + i] = W4;
+        s.wa[5 * Nc + i] = W5;
+      }
+      epilogue<P, MODE, ENERGY>(s, a, i, inf, Fx, Fy, Fz);
+    }
+  }
+}
+
+inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+template <class P, int MODE, bool EN, int SH, int T>
+void go(const Sys &s, const LJParams &p, StepArgs a, int block, cudaStream_t st) {
+  if (block > 256) block = 256;  // the kernel is compiled for <= 256 threads (48 registers)
+  const int grid = nblk((long long)(s.N_cap > 0 ? s.N_cap : 1) * T, block);
+  k_lj<P, MODE, EN, SH, T><<<grid, block, 0, st>>>(s, p, a);
+}
+
+template <class P, int MODE, bool EN, int SH>
+void by_tpa(const Sys &s, const LJParams &p, StepArgs a, const LaunchCfg &c, cudaStream_t st) {
+  if (c.tpa == 4)
+    go<P, MODE, EN, SH, 4>(s, p, a, c.block, st);
+  else if (c.tpa == 2)
+    go<P, MODE, EN, SH, 2>(s, p, a, c.block, st);
+  else
+    go<P, MODE, EN, SH, 1>(s, p, a, c.block, st);
+}
+
+template <class P, int MODE, bool EN>
+void by_shift(const Sys &s, const LJParams &p, StepArgs a, const LaunchCfg &c, cudaStream_t st) {
+  if (p.shift_mode == 2)
+    by_tpa<P, MODE, EN, 2>(s, p, a, c, st);
+  else
+    by_tpa<P, MODE, EN, 1>(s, p, a, c, st);
+}
+
+template <class P, int MODE>
+void by_energy(const Sys &s, const LJParams &p, StepArgs a, const LaunchCfg &c, cudaStream_t st) {
+  if (a.energy)
+    by_shift<P, MODE, true>(s, p, a, c, st);
+  else
+    by_shift<P, MODE, false>(s, p, a, c, st);
+}
+
+template <class P>
+void by_mode(const Sys &s, const LJParams &p, Mode m, StepArgs a, const LaunchCfg &c,
+             cudaStream_t st) {
+  if (m == kForceOnly)
+    by_energy<P, kForceOnly>(s, p, a, c, st);
+  else if (m == kStep)
+    by_energy<P, kStep>(s, p, a, c, st);
+  else
+    by_energy<P, kFinal>(s, p, a, c, st);
+}
+
+}  // namespace
+
+void launch_lj(const Sys &s, const LJParams &p, int precision, Mode mode, StepArgs a,
+               const LaunchCfg &cfg, cudaStream_t st) {
+  if (precision == 0)
+    by_mode<Fp64>(s, p, mode, a, cfg, st);
+  else
+    by_mode<Mixed>(s, p, mode, a, cfg, st);
+}
+
+}  // namespace mdk

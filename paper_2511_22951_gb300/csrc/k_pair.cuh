@@ -1,0 +1,280 @@
+// k_pair.cuh -- device helpers shared by the pair kernels (k_lj.cu, k_eam.cu):
+// precision traits of the gather copy, spline pieces, the neighbour walk and
+// the fused velocity-Verlet epilogue.  Only the CUDA sources include it.
+#pragma once
+
+#include <math.h>
+
+#include "mdk_internal.cuh"
+
+namespace mdk {
+namespace pair {
+
+// cubic Hermite piece on [k, k+1] with knots (y, h*m): value and h*derivative
+template <class R>
+__device__ __forceinline__ R herm_val(R t, R y0, R m0, R y1, R m1) {
+  const R t2 = t * t, t3 = t2 * t;
+  const R h01 = R(3) * t2 - R(2) * t3;
+  const R h10 = t3 - R(2) * t2 + t;
+  const R h11 = t3 - t2;
+  return y0 + h01 * (y1 - y0) + h10 * m0 + h11 * m1;
+}
+template <class R>
+__device__ __forceinline__ R herm_der(R t, R y0, R m0, R y1, R m1) {
+  const R t2 = t * t;
+  const R d00 = R(6) * t2 - R(6) * t;
+  const R d10 = R(3) * t2 - R(4) * t + R(1);
+  const R d11 = R(3) * t2 - R(2) * t;
+  return d00 * (y0 - y1) + d10 * m0 + d11 * m1;
+}
+
+// ---- gather-copy access per precision ---------------------------------------
+template <class P>
+struct G;
+template <>
+struct G<Fp64> {
+  using R = double;
+  using V = dvec4;
+  using T2 = double2;
+  static __device__ __forceinline__ dvec4 ld(const dvec4 *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 a = __ldg(q), b = __ldg(q + 1);
+    dvec4 r;
+    r.x = a.x;
+    r.y = a.y;
+    r.z = b.x;
+    r.w = b.y;
+    return r;
+  }
+  static __device__ __forceinline__ void st(dvec4 *p, double a, double b, double c,
+                                            uint32_t w) {
+    double2 *q = reinterpret_cast<double2 *>(p);
+    q[0] = make_double2(a, b);
+    q[1] = make_double2(c, __longlong_as_double((long long)w));
+  }
+  static __device__ __forceinline__ uint32_t info(const dvec4 &p) {
+    return (uint32_t)__double_as_longlong(p.w);
+  }
+  static __device__ __forceinline__ void h(const Grid &g, double &hx, double &hy, double &hz) {
+    hx = g.h[0];
+    hy = g.h[1];
+    hz = g.h[2];
+  }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+  static __device__ __forceinline__ double sqr(double x) { return sqrt(x); }
+  // EAM tables: (y_k, h m_k) per knot for both passes
+  using Tab1 = double2;
+  using Tab2 = double2;
+  static __device__ __forceinline__ const double2 *tab1(const EAMParams &e) { return e.rho64; }
+  static __device__ __forceinline__ const double2 *phi2(const EAMParams &e) { return e.phi64; }
+  static __device__ __forceinline__ const double2 *rho2(const EAMParams &e) { return e.rho64; }
+  static __device__ __forceinline__ int n1(const EAMParams &e) { return e.nr; }
+  static __device__ __forceinline__ double val1(const double2 *t, int k, double u) {
+    const double2 a = t[k], b = t[k + 1];
+    return herm_val<double>(u, a.x, a.y, b.x, b.y);
+  }
+  // h * derivative
+  static __device__ __forceinline__ double der2(const double2 *t, int k, double u) {
+    const double2 a = t[k], b = t[k + 1];
+    return herm_der<double>(u, a.x, a.y, b.x, b.y);
+  }
+  static __device__ __forceinline__ double val2(const double2 *t, const EAMParams &, int k,
+                                                double u) {
+    const double2 a = t[k], b = t[k + 1];
+    return herm_val<double>(u, a.x, a.y, b.x, b.y);
+  }
+};
+template <>
+struct G<Mixed> {
+  using R = float;
+  using V = float4;
+  using T2 = float2;
+  static __device__ __forceinline__ float4 ld(const float4 *p) { return __ldg(p); }
+  static __device__ __forceinline__ void st(float4 *p, double a, double b, double c,
+                                            uint32_t w) {
+    *p = make_float4((float)a, (float)b, (float)c, __uint_as_float(w));
+  }
+  static __device__ __forceinline__ uint32_t info(const float4 &p) {
+    return __float_as_uint(p.w);
+  }
+  static __device__ __forceinline__ void h(const Grid &g, float &hx, float &hy, float &hz) {
+    hx = g.hf[0];
+    hy = g.hf[1];
+    hz = g.hf[2];
+  }
+  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+  static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+  static __device__ __forceinline__ float sqr(float x) { return sqrtf(x); }
+  // EAM tables rounded from FP64 differences (no FP32 cancellation):
+  // pass 1 per interval (y_k, dy_k, h m_k, h m_{k+1}); pass 2 per knot (dy_k, h m_k)
+  using Tab1 = float4;
+  using Tab2 = float2;
+  static __device__ __forceinline__ const float4 *tab1(const EAMParams &e) { return e.rho_i32; }
+  static __device__ __forceinline__ const float2 *phi2(const EAMParams &e) { return e.phi_d32; }
+  static __device__ __forceinline__ const float2 *rho2(const EAMParams &e) { return e.rho_d32; }
+  static __device__ __forceinline__ int n1(const EAMParams &e) { return e.nr - 1; }
+  static __device__ __forceinline__ float val1(const float4 *t, int k, float u) {
+    const float4 q = t[k];
+    const float u2 = u * u, u3 = u2 * u;
+    return q.x + (3.0f * u2 - 2.0f * u3) * q.y + (u3 - 2.0f * u2 + u) * q.z + (u3 - u2) * q.w;
+  }
+  static __device__ __forceinline__ float der2(const float2 *t, int k, float u) {
+    const float2 a = t[k], b = t[k + 1];
+    const float u2 = u * u;
+    return (6.0f * u - 6.0f * u2) * a.x + (3.0f * u2 - 4.0f * u + 1.0f) * a.y +
+           (3.0f * u2 - 2.0f * u) * b.y;
+  }
+  static __device__ __forceinline__ float val2(const float2 *t, const EAMParams &e, int k,
+                                               float u) {
+    const float2 a = t[k], b = t[k + 1];
+    const float u2 = u * u, u3 = u2 * u;
+    return __ldg(e.phi_v32 + k) + (3.0f * u2 - 2.0f * u3) * a.x + (u3 - 2.0f * u2 + u) * a.y +
+           (u3 - u2) * b.y;
+  }
+};
+
+// ---- the neighbour walk ------------------------------------------------------------
+// Unit stencil offset s_d in {-1, 0, 1} of a list entry, exactly, in the pair
+// precision, without an int-to-float conversion: the 2-bit code c = s_d + 1 is
+// placed in the low mantissa bits of 2^23 (2^52) and 2^23 + 1 (2^52 + 1) is
+// subtracted.
+__device__ __forceinline__ float s_unit(float, uint32_t e, int d) {
+  return __uint_as_float(((e >> (26 + 2 * d)) & 3u) | 0x4B000000u) - 8388609.0f;
+}
+__device__ __forceinline__ double s_unit(double, uint32_t e, int d) {
+  return __longlong_as_double((long long)((e >> (26 + 2 * d)) & 3u) | 0x4330000000000000LL) -
+         4503599627370497.0;
+}
+
+// Walk the list of one atom with T lanes: lane t takes the groups of 8 list
+// words t, t + T, t + 2T, ...  A group comes in two 16-byte loads; its
+// neighbour records are loaded four at a time before the four bodies run,
+// so each thread keeps several independent loads in flight.  `commit` runs
+// after every four pairs: the compensated per-atom sums take one block sum
+// per four pairs instead of one term per pair.
+template <int T, class Load, class Body, class Commit>
+__device__ __forceinline__ void walk(const uint32_t *__restrict__ nbr, size_t Nc, int i, int nn,
+                                     int t, Load &&load, Body &&body, Commit &&commit) {
+  using Rec = decltype(load(0u));
+  const size_t gstride = Nc * 2;  // uint4 per group row
+  const uint4 *__restrict__ row = reinterpret_cast<const uint4 *>(nbr) + (size_t)i * 2 +
+                                  (size_t)t * gstride;
+  for (int k = kGroup * t; k < nn; k += kGroup * T, row += gstride * T) {
+    const uint4 a = __ldcs(row), b = __ldcs(row + 1);
+    const uint32_t e[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    const int m = nn - k;  // valid entries in this group
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      Rec q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (4 * h + u < m) q[u] = load(e[4 * h + u] & kJMask);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (4 * h + u < m) body(e[4 * h + u], q[u]);
+      commit();
+    }
+  }
+}
+
+// sum of v over the T lanes of one atom (fixed order: deterministic)
+template <int T, class R>
+__device__ __forceinline__ R lanes_sum(R v) {
+#pragma unroll
+  for (int o = 1; o < T; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Atoms are handed out in warp tiles of 32/T atoms (T lanes each) over a
+// persistent grid; every lane of a warp runs the same number of tiles, so the
+// lanes_sum shuffles always see the whole warp.
+template <int T>
+struct Tiles {
+  static constexpr int kPerWarp = 32 / T;
+  int lane, t, w0, nw;
+  __device__ __forceinline__ Tiles() {
+    lane = threadIdx.x & 31;
+    t = lane & (T - 1);
+    w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    nw = (gridDim.x * blockDim.x) >> 5;
+  }
+  __device__ __forceinline__ int atom(int w) const { return w * kPerWarp + lane / T; }
+};
+
+// ---- per-atom epilogue: store forces or integrate -----------------------------
+template <class P>
+__device__ __forceinline__ void drift_publish(const Sys &s, const StepArgs &a, int i,
+                                              uint32_t inf, double vx, double vy, double vz) {
+  using GP = G<P>;
+  const size_t Nc = s.N_cap;
+  double x = s.x[i] + a.dt * vx;
+  double y = s.x[Nc + i] + a.dt * vy;
+  double z = s.x[2 * Nc + i] + a.dt * vz;
+  s.x[i] = x;
+  s.x[Nc + i] = y;
+  s.x[2 * Nc + i] = z;
+  s.v[i] = vx;
+  s.v[Nc + i] = vy;
+  s.v[2 * Nc + i] = vz;
+  const double ex = x - s.xref[i], ey = y - s.xref[Nc + i], ez = z - s.xref[2 * Nc + i];
+  const double d2 = ex * ex + ey * ey + ez * ez;
+  const bool bad = !isfinite(d2);
+  const bool trig = bad || d2 > s.half_skin2;
+  const unsigned act = __activemask();
+  const unsigned m = __ballot_sync(act, trig);
+  if (m && (threadIdx.x & 31) == (__ffs(m) - 1)) atomicOr(&s.st->rebuild, 1);
+  if (bad) atomicOr(&s.st->bits, kStNonfinite);
+  const Grid &g = s.grid[inf >> 8];
+  const uint32_t cc = s.cellc[i];
+  typename GP::V *out = (typename GP::V *)s.pg[a.cur ^ 1];
+  GP::st(out + i, x - cell_center(g, 0, cell_coord(cc, 0)),
+         y - cell_center(g, 1, cell_coord(cc, 1)), z - cell_center(g, 2, cell_coord(cc, 2)),
+         inf);
+}
+
+template <class P, int MODE, bool ENERGY>
+__device__ __forceinline__ void epilogue(const Sys &s, const StepArgs &a, int i, uint32_t inf,
+                                         double Fx, double Fy, double Fz) {
+  const size_t Nc = s.N_cap;
+  if (MODE == kForceOnly) {
+    s.f[i] = Fx;
+    s.f[Nc + i] = Fy;
+    s.f[2 * Nc + i] = Fz;
+    if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(&s.st->bits, kStNonfinite);
+    return;
+  }
+  const int type = inf & 15u;
+  const bool piston = (inf & kInfoPiston) != 0;
+  const double c = 0.5 * a.dt * s.acc_over_m[type];
+  double vx = s.v[i], vy = s.v[Nc + i], vz = s.v[2 * Nc + i];
+  if (piston) {
+    vx = s.u_p;
+    vy = 0.0;
+    vz = 0.0;
+  } else {
+    vx += c * Fx;
+    vy += c * Fy;
+    vz += c * Fz;
+  }
+  if (ENERGY) s.ka[i] = s.ke_m[type] * (vx * vx + vy * vy + vz * vz);
+  if (MODE == kFinal) {
+    s.v[i] = vx;
+    s.v[Nc + i] = vy;
+    s.v[2 * Nc + i] = vz;
+    s.f[i] = Fx;
+    s.f[Nc + i] = Fy;
+    s.f[2 * Nc + i] = Fz;
+    if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(&s.st->bits, kStNonfinite);
+    return;
+  }
+  if (!piston) {
+    vx += c * Fx;
+    vy += c * Fy;
+    vz += c * Fz;
+  }
+  drift_publish<P>(s, a, i, inf, vx, vy, vz);
+}
+
+}  // namespace pair
+}  // namespace mdk

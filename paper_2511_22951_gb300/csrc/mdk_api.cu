@@ -57,6 +57,7 @@ struct mdk_ctx {
   int thermo_every = 0, thermo_cap = 0;
   int64_t thermo_written = 0, thermo_read = 0;
   int64_t steps_done = 0;
+  LaunchCfg cfg;  // pair-kernel launch shape (mdk_autotune)
   // moving window
   bool win_on = false;
   double win_L_behind = 0.0, win_L_ahead = 0.0, win_slab_lx = 0.0, win_gap = 0.0,
@@ -341,9 +342,9 @@ int force_pass(mdk_ctx *c, Mode mode, int energy, double dt) {
   StepArgs a{dt, c->cur, energy};
   return timed(c, c->ev_force, c->pot == 1 ? 1 : 2, [&] {
     if (c->pot == 1)
-      launch_lj(c->sys, c->lj, c->precision, mode, a, c->stream);
+      launch_lj(c->sys, c->lj, c->precision, mode, a, c->cfg, c->stream);
     else
-      launch_eam(c->sys, c->eam, c->precision, mode, a, c->stream);
+      launch_eam(c->sys, c->eam, c->precision, mode, a, c->cfg, c->stream);
   });
 }
 
@@ -1028,6 +1029,66 @@ int mdk_set_piston(mdk_ctx *c, double u_p, const uint8_t *is_piston) {
   MDK_CK(cudaStreamSynchronize(c->stream));
   // the gather copies carry the info word: regenerate them with a rebuild
   if (c->list_built) return build_now(c);
+  return MDK_OK;
+}
+
+int mdk_autotune(mdk_ctx *c, int reps, int *tpa_out, int *block_out, double *ms_out) {
+  if (check_ctx(c) || reps < 0) return MDK_ERR_BAD_ARG;
+  int r = ensure_ready(c);
+  if (r) return r;
+  if (!c->list_built) {
+    r = build_now(c);
+    if (r) return r;
+  }
+  if (reps == 0) reps = 3;
+  cudaEvent_t e0, e1;
+  MDK_CK(cudaEventCreate(&e0));
+  MDK_CK(cudaEventCreate(&e1));
+  const LaunchCfg keep = c->cfg;
+  const bool prof = c->prof;
+  c->prof = false;
+  LaunchCfg best = keep;
+  float best_ms = -1.f;
+  static const int kTpa[3] = {1, 2, 4};
+  static const int kBlock[3] = {128, 256, 512};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      if (c->pot == 1 && kBlock[b] > 256) continue;  // the LJ kernel takes <= 256
+      c->cfg.tpa = kTpa[a];
+      c->cfg.block = kBlock[b];
+      r = force_pass(c, kForceOnly, 0, 0.0);  // warm-up (and grid set-up)
+      if (r) break;
+      MDK_CK(cudaEventRecord(e0, c->stream));
+      for (int q = 0; q < reps && !r; ++q) r = force_pass(c, kForceOnly, 0, 0.0);
+      MDK_CK(cudaEventRecord(e1, c->stream));
+      MDK_CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      MDK_CK(cudaEventElapsedTime(&ms, e0, e1));
+      ms /= (float)reps;
+      if (best_ms < 0.f || ms < best_ms) {
+        best_ms = ms;
+        best = c->cfg;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->prof = prof;
+  c->cfg = r ? keep : best;
+  if (r) return r;
+  c->forces_valid = true;  // the passes left the forces of the current positions
+  c->per_atom_valid = false;
+  if (tpa_out) *tpa_out = best.tpa;
+  if (block_out) *block_out = best.block;
+  if (ms_out) *ms_out = best_ms;
+  return MDK_OK;
+}
+
+int mdk_set_launch(mdk_ctx *c, int tpa, int block) {
+  if (check_ctx(c) || (tpa != 1 && tpa != 2 && tpa != 4) ||
+      (block != 128 && block != 256 && block != 512))
+    return MDK_ERR_BAD_ARG;
+  c->cfg.tpa = tpa;
+  c->cfg.block = block;
   return MDK_OK;
 }
 

@@ -248,10 +248,16 @@ void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, 
 void launch_set_piston(const Sys &s, const uint8_t *flags, int64_t n_flags, cudaStream_t st);
 int scan_blocks_for(int n_cells);
 void launch_set_rebuild_flag(const Sys &s, cudaStream_t st);
+// launch shape of the pair kernels, picked by the autotuner
+struct LaunchCfg {
+  int tpa = 1;      // threads per atom: 1, 2 or 4
+  int block = 256;  // threads per block: 128, 256 or 512
+};
+
 void launch_lj(const Sys &s, const LJParams &p, int precision, Mode mode, StepArgs a,
-               cudaStream_t st);
+               const LaunchCfg &cfg, cudaStream_t st);
 void launch_eam(const Sys &s, const EAMParams &p, int precision, Mode mode, StepArgs a,
-                cudaStream_t st);
+                const LaunchCfg &cfg, cudaStream_t st);
 void launch_kick_drift(const Sys &s, int precision, StepArgs a, cudaStream_t st);
 void launch_reduce(const Sys &s, int with_ke, cudaStream_t st);
 void launch_eam_prepare(const EAMParams &p, const double *phi, const double *rho,

@@ -67,6 +67,8 @@ SIGNATURES = {
     "mdk_profiles": [_P, _I, _D, _D, _I, _D, _P, _I],
     "mdk_status_string": [_I],
     "mdk_last_device_status": [_P, ctypes.POINTER(_I)],
+    "mdk_autotune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)],
+    "mdk_set_launch": [_P, _I, _I],
     "mdk_profile": [_P, _I],
     "mdk_get_profile": [_P, _P],
     "mdk_lj_compute_noalloc": [_P, _I64, _P, _P, _P, _D, _D, _D, _I, _P, _P, _P],
@@ -329,6 +331,16 @@ class Context:
         _check(self.lib.mdk_get_counters(self.h, ctypes.byref(b), ctypes.byref(s)),
                "mdk_get_counters")
         return int(b.value), int(s.value)
+
+    def autotune(self, reps=3):
+        """Pick threads-per-atom and block size by timing every shape."""
+        t, b, ms = _I(), _I(), _D()
+        _check(self.lib.mdk_autotune(self.h, reps, ctypes.byref(t), ctypes.byref(b),
+                                     ctypes.byref(ms)), "mdk_autotune")
+        return int(t.value), int(b.value), float(ms.value)
+
+    def set_launch(self, tpa, block):
+        _check(self.lib.mdk_set_launch(self.h, tpa, block), "mdk_set_launch")
 
     def profile(self, enable=True):
         _check(self.lib.mdk_profile(self.h, 1 if enable else 0), "mdk_profile")

@@ -384,3 +384,89 @@ def test_window_matches_oracle(mdk, ora):
     d[:, 1:] -= np.rint(d[:, 1:] / L[1:]) * L[1:]
     assert np.max(np.abs(d)) < 1e-9
     np.testing.assert_allclose(vg, o["v"][order], rtol=0, atol=1e-11)
+
+
+# --------------------------------------------------------------------------- batched replicas
+def small_coldcurve(n_rep=6, seed=2):
+    """A handful of Cu-like cold-curve replicas of uneven size and density
+    (1-cell and multi-cell boxes), jittered, as in the 64-replica workload."""
+    rng = np.random.default_rng(seed)
+    reps = []
+    for a, n in zip(rng.uniform(3.0, 4.2, n_rep), [3, 4, 3, 5, 6, 3][:n_rep]):
+        s = W.lattice_system(rng, (n, n, n), float(a), W.MASS_CU, 0.0, sigma_jitter=0.05)
+        reps.append(s)
+    return reps
+
+
+def batch_ctx(mdk, reps, prec, tab):
+    ctx = mdk.Context([r.lo for r in reps], [r.hi for r in reps], [r.periodic for r in reps],
+                      np.concatenate([r.masses for r in reps]), prec, n_atoms=[r.n for r in reps])
+    ctx.set_potential_eam(tab)
+    ctx.plan(tab.rc, 0.3)
+    ctx.set_state(np.concatenate([r.x for r in reps]), np.concatenate([r.v for r in reps]))
+    ctx.build_neighbors(tab.rc, 0.3)
+    return ctx
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_replicas_match_oracle(mdk, ora, prec):
+    tab = W.tabulate_fs_eam(W.CU_LIKE)
+    reps = small_coldcurve()
+    ctx = batch_ctx(mdk, reps, prec, tab)
+    E, F, Wv = ctx.compute()
+    off = 0
+    for q, r in enumerate(reps):
+        ref = ora.eam(r.x, r.lo, r.hi, r.periodic, tab)
+        Fq = F[off:off + r.n]
+        if prec == "fp64":
+            assert_fp64(E[q], Fq, Wv[q], ref)
+        else:
+            assert_mixed(E[q], Fq, ref)
+        off += r.n
+
+
+def test_launch_shapes_agree(mdk, ora):
+    """Every threads-per-atom x block-size shape gives the FP64 results."""
+    tab = W.tabulate_fs_eam(W.CU_LIKE)
+    reps = small_coldcurve()
+    ctx = batch_ctx(mdk, reps, "fp64", tab)
+    ref = [ora.eam(r.x, r.lo, r.hi, r.periodic, tab) for r in reps]
+    for tpa in (1, 2, 4):
+        for block in (128, 256, 512):
+            ctx.set_launch(tpa, block)
+            E, F, Wv = ctx.compute()
+            off = 0
+            for q, r in enumerate(reps):
+                assert_fp64(E[q], F[off:off + r.n], Wv[q], ref[q])
+                off += r.n
+    t, b, ms = ctx.autotune()
+    assert t in (1, 2, 4) and b in (128, 256, 512) and ms > 0.0
+    xj, lo, hi = jittered_lattice(7, 4, 5.26, 0.12)
+    c2 = lj_ctx(mdk, xj, lo, hi, [1, 1, 1], "mixed")
+    r0 = ora.lj(xj, lo, hi, [1, 1, 1], W.LJ_AR.eps, W.LJ_AR.sigma, W.LJ_AR.rc, 1)
+    for tpa in (2, 4):
+        c2.set_launch(tpa, 128)
+        E, F, _ = c2.compute()
+        assert_mixed(E[0], F, r0)
+
+
+def test_batched_dynamics_match_oracle(mdk, ora):
+    """Ten FP64 steps of the batch equal ten oracle steps of every replica."""
+    tab = W.tabulate_fs_eam(W.CU_LIKE)
+    reps = small_coldcurve(4)
+    rng = np.random.default_rng(4)
+    for r in reps:
+        r.v = W.maxwell_velocities(rng, r.masses, 500.0)
+    ctx = batch_ctx(mdk, reps, "fp64", tab)
+    ctx.set_launch(2, 128)
+    ctx.step(1.0, 10)
+    x, v = ctx.get_state()
+    off = 0
+    for r in reps:
+        o = ora.md_run(r.x, r.v, r.masses, r.lo, r.hi, r.periodic, 1.0, 10, 0.3, tables=tab)
+        L = r.hi - r.lo
+        d = x[off:off + r.n] - o["x"]
+        d -= np.rint(d / L) * L
+        assert np.max(np.abs(d)) < 1e-10
+        np.testing.assert_allclose(v[off:off + r.n], o["v"], rtol=0, atol=1e-11)
+        off += r.n
