@@ -227,12 +227,13 @@ def main():
     n_avg = float(ctx.neighbor_counts().mean())
     tpa, block, _ = ctx.autotune()
 
-    # warm-up (untimed)
+    # warm-up (untimed; also captures the step graphs)
     ctx.step(wl.dt, args.warmup, check=True)
     barrier()
     clocks = Clocks()
     clocks.start()
-    ctx.profile(True)
+    builds_before = ctx.counters()[0]
+    ctx.profile(False)          # clears the counters; kernels are still counted
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -241,9 +242,17 @@ def main():
     e1.record(stream)
     barrier()
     ms = e0.elapsed_time(e1)
+    launches = int(ctx.get_profile()["kernels"])
+    builds0 = ctx.counters()[0]
+    ck = clocks.stop()
+    ctx.check()
+    # per-kernel times: a separate segment with CUDA events around every force
+    # pass and rebuild chain (graphs off there, events on the same stream)
+    prof_steps = max(20, min(args.steps, 200))
+    ctx.profile(True)
+    ctx.step(wl.dt, prof_steps, check=False)
     prof = ctx.get_profile()
     ctx.profile(False)
-    ck = clocks.stop()
     ctx.check()
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
@@ -260,8 +269,10 @@ def main():
             "frac": achieved / hbm, "traffic": None,
             "kernel": f"k_lj<{prec}> fused force + velocity Verlet",
             "bytes_per_atom": bpa, "peak_kind": peak_kind,
-            "force_share_of_step": prof["force_ms"] / ms,
-            "rebuild_share_of_step": prof["rebuild_ms"] / ms}
+            "force_share_of_step": prof["force_ms"] / (ms * prof_steps / args.steps),
+            "rebuild_share_of_step": prof["rebuild_ms"] / (ms * prof_steps / args.steps),
+            "timed_from": f"CUDA events around each of {int(prof['force_passes'])} force "
+                          f"passes of a {prof_steps}-step profiled segment"}
 
     # end to end through the C ABI with host buffers: upload the state from
     # pinned memory, run the steps, read positions, velocities and energy back
@@ -323,14 +334,15 @@ def main():
                        "launch": {"threads_per_atom": tpa, "block": block,
                                   "picked_by": "mdk_autotune"},
                        "rebuild": "when an atom moved > skin/2 since the last build",
-                       "list_builds_in_timed_region": prof["builds"],
+                       "list_builds_in_timed_region": builds0 - builds_before,
+                       "step_graphs": "two-step CUDA graphs replayed by mdk_step",
                        "l2": "inputs larger than L2 (~4 GB touched per step); no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "pair_interactions_per_s": value * n_avg / 2.0,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": int(prof["kernels"]),
+            "gpu_launches": launches,
             "clocks": ck,
             "fp64_path": fp64,
         }

@@ -356,6 +356,15 @@ int mdk_autotune(mdk_ctx *ctx, int reps, int *tpa, int *block, double *ms);
 /* Set the launch shape directly (tpa in {1, 2, 4}, block in {128, 256, 512}). */
 int mdk_set_launch(mdk_ctx *ctx, int tpa, int block);
 
+/*
+ * enable != 0 (the default): mdk_step runs pairs of plain steps (neither a
+ * thermo step nor the last step of the call) as one CUDA graph -- force pass
+ * and rebuild chain twice -- captured on first use and re-captured whenever a
+ * parameter it baked in changes (workspace, potential, launch shape, dt,
+ * window...).  Steps taken while mdk_profile records run without graphs.
+ */
+int mdk_set_graphs(mdk_ctx *ctx, int enable);
+
 /* ---- measurement ----------------------------------------------------------- */
 
 /*

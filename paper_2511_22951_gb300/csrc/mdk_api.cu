@@ -58,6 +58,12 @@ struct mdk_ctx {
   int64_t thermo_written = 0, thermo_read = 0;
   int64_t steps_done = 0;
   LaunchCfg cfg;  // pair-kernel launch shape (mdk_autotune)
+  // CUDA graphs of two plain steps, one per parity of the gather copy
+  bool graphs_on = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  uint64_t gkey[2] = {0, 0};
+  int64_t graph_kernels = 0;  // kernels in one graph
   // moving window
   bool win_on = false;
   double win_L_behind = 0.0, win_L_ahead = 0.0, win_slab_lx = 0.0, win_gap = 0.0,
@@ -435,6 +441,68 @@ int gather_by_id(mdk_ctx *c, int64_t n, const double *src, int comp, double *out
   return MDK_OK;
 }
 
+// Fingerprint of everything a captured step bakes into its kernel
+// parameters (FNV-1a over the parameter structs and dt).
+uint64_t fnv(uint64_t h, const void *p, size_t n) {
+  const unsigned char *b = static_cast<const unsigned char *>(p);
+  for (size_t q = 0; q < n; ++q) {
+    h ^= b[q];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+uint64_t graph_key(const mdk_ctx *c, double dt) {
+  uint64_t h = 1469598103934665603ull;
+  h = fnv(h, &c->sys, sizeof(Sys));
+  h = fnv(h, &c->lj, sizeof(LJParams));
+  h = fnv(h, &c->eam, sizeof(EAMParams));
+  h = fnv(h, &c->cfg, sizeof(LaunchCfg));
+  h = fnv(h, &c->pot, sizeof(int));
+  h = fnv(h, &c->precision, sizeof(int));
+  h = fnv(h, &dt, sizeof(double));
+  return h;
+}
+
+// Capture two plain steps (force pass + rebuild chain, twice) starting from
+// gather-copy parity `parity`; the graph ends at the same parity.
+int capture_two_steps(mdk_ctx *c, int parity, double dt, uint64_t key) {
+  if (!c->cap_stream) MDK_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  const cudaStream_t keep_stream = c->stream;
+  const int keep_cur = c->cur;
+  const bool keep_prof = c->prof;
+  const int64_t keep_launches = c->launches;
+  MDK_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  c->stream = c->cap_stream;
+  c->cur = parity;
+  c->prof = false;
+  int r = MDK_OK;
+  for (int h = 0; h < 2 && !r; ++h) {
+    r = force_pass(c, kStep, 0, dt);
+    c->cur ^= 1;
+    if (!r) r = rebuild_chain(c, 1);
+  }
+  c->stream = keep_stream;
+  c->cur = keep_cur;
+  c->prof = keep_prof;
+  c->graph_kernels = c->launches - keep_launches;
+  c->launches = keep_launches;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (r || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return r ? r : MDK_ERR_CUDA;
+  }
+  if (c->gexec[parity]) cudaGraphExecDestroy(c->gexec[parity]);
+  c->gexec[parity] = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&c->gexec[parity], g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return MDK_ERR_CUDA;
+  c->gkey[parity] = key;
+  return MDK_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -515,6 +583,9 @@ int mdk_create(mdk_ctx **out, const double box_lo[3], const double box_hi[3],
 int mdk_destroy(mdk_ctx *c) {
   if (!c) return MDK_ERR_BAD_ARG;
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (int q = 0; q < 2; ++q)
+    if (c->gexec[q]) cudaGraphExecDestroy(c->gexec[q]);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return MDK_OK;
 }
@@ -925,9 +996,25 @@ int mdk_step(mdk_ctx *c, double dt, int64_t nsteps) {
   c->cur ^= 1;
   r = rebuild_chain(c, 1);
   if (r) return r;
+  const uint64_t key = c->graphs_on ? graph_key(c, dt) : 0;
+  auto is_thermo = [&](int64_t q) {
+    return c->thermo_every > 0 && ((c->steps_done + q) % c->thermo_every) == 0;
+  };
   for (int64_t q = 1; q <= nsteps; ++q) {
+    // two plain steps (neither the last nor a thermo step) run as one graph
+    if (c->graphs_on && !c->prof && q + 1 < nsteps && !is_thermo(q) && !is_thermo(q + 1)) {
+      const int par = c->cur;
+      if (!c->gexec[par] || c->gkey[par] != key) {
+        r = capture_two_steps(c, par, dt, key);
+        if (r) return r;
+      }
+      MDK_CK(cudaGraphLaunch(c->gexec[par], c->stream));
+      c->launches += c->graph_kernels;
+      ++q;  // the graph ran steps q and q + 1; the parity is back to par
+      continue;
+    }
     const int64_t gstep = c->steps_done + q;
-    const int thermo = c->thermo_every > 0 && (gstep % c->thermo_every) == 0;
+    const int thermo = is_thermo(q);
     const bool last = q == nsteps;
     r = force_pass(c, last ? kFinal : kStep, thermo, dt);
     if (r) return r;
@@ -1080,6 +1167,12 @@ int mdk_autotune(mdk_ctx *c, int reps, int *tpa_out, int *block_out, double *ms_
   if (tpa_out) *tpa_out = best.tpa;
   if (block_out) *block_out = best.block;
   if (ms_out) *ms_out = best_ms;
+  return MDK_OK;
+}
+
+int mdk_set_graphs(mdk_ctx *c, int enable) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  c->graphs_on = enable != 0;
   return MDK_OK;
 }
 

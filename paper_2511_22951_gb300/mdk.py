@@ -69,6 +69,7 @@ SIGNATURES = {
     "mdk_last_device_status": [_P, ctypes.POINTER(_I)],
     "mdk_autotune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)],
     "mdk_set_launch": [_P, _I, _I],
+    "mdk_set_graphs": [_P, _I],
     "mdk_profile": [_P, _I],
     "mdk_get_profile": [_P, _P],
     "mdk_lj_compute_noalloc": [_P, _I64, _P, _P, _P, _D, _D, _D, _I, _P, _P, _P],
@@ -338,6 +339,9 @@ class Context:
         _check(self.lib.mdk_autotune(self.h, reps, ctypes.byref(t), ctypes.byref(b),
                                      ctypes.byref(ms)), "mdk_autotune")
         return int(t.value), int(b.value), float(ms.value)
+
+    def set_graphs(self, enable=True):
+        _check(self.lib.mdk_set_graphs(self.h, 1 if enable else 0), "mdk_set_graphs")
 
     def set_launch(self, tpa, block):
         _check(self.lib.mdk_set_launch(self.h, tpa, block), "mdk_set_launch")

@@ -470,3 +470,24 @@ def test_batched_dynamics_match_oracle(mdk, ora):
         assert np.max(np.abs(d)) < 1e-10
         np.testing.assert_allclose(v[off:off + r.n], o["v"], rtol=0, atol=1e-11)
         off += r.n
+
+
+# --------------------------------------------------------------------------- CUDA graphs
+def test_graph_replay_is_bit_identical(mdk):
+    """Steps replayed from the captured two-step graph give exactly the state
+    of the same kernels launched one by one (thermo steps interleaved, and a
+    change of launch shape that forces a new capture)."""
+    wl = W.config0()
+    outs = []
+    for graphs in (True, False):
+        ctx = mdk.make_context(wl, precision="mixed")
+        ctx.set_graphs(graphs)
+        ctx.set_thermo(7, 64)
+        ctx.step(wl.dt, 23)
+        ctx.set_launch(2, 128)
+        ctx.step(wl.dt, 9)
+        x, v = ctx.get_state()
+        outs.append((x, v, ctx.thermo()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    np.testing.assert_array_equal(outs[0][2], outs[1][2])
