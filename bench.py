@@ -60,7 +60,7 @@ def workload(cfg: int, cells: int = 128):
 
 
 def algorithmic_bytes_per_atom(wl, prec, n_avg):
-    """Bytes one fused force+integration launch must move per atom (DESIGN.md):
+    """Bytes one fused force+integration launch must move per atom:
     own gather-copy element, list entries + count, x and v read+write, x_ref
     and cell word read, next gather-copy element written.  Neighbour
     positions are assumed to come from cache (spatial order)."""

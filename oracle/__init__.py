@@ -72,6 +72,10 @@ def lib():
         L.ora_md_window.argtypes = [P, I64, P, P, P, P, P, P, P, P, P, I, D, P, P, I, D, P, D,
                                     D, I64, I, D, D, D, P, P, I64, D, D, D, D]
         L.ora_md_window.restype = I64
+        L.ora_eam_vjp.argtypes = [I64, P, P, P, P, I, D, P, P, I, D, P, D, P, P]
+        L.ora_eam_vjp.restype = I
+        L.ora_eam_jvp.argtypes = [I64, P, P, P, P, I, D, P, P, I, D, P, P, P, P, D, P, P]
+        L.ora_eam_jvp.restype = I
         _lib = L
     return _lib
 
@@ -183,6 +187,43 @@ def eam(x, lo, hi, periodic, tables, per_atom=False):
         out["Ea"] = Ea
         out["Wa"] = Wa
     return out
+
+
+def eam_vjp(x, lo, hi, periodic, tables, gE=0.0, gF=None):
+    """Reverse-mode gradient of L = gE * E + sum_i gF_i . F_i with respect to
+    the knot values: returns (d_phi, d_rho, d_F), the three knot arrays."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    lo, hi, per = _box(lo, hi, periodic)
+    phi, rho, Ft = _f64(tables.phi), _f64(tables.rho), _f64(tables.F)
+    gF = np.zeros((n, 3)) if gF is None else _f64(gF, (n, 3))
+    nr, nrho = phi.shape[0], Ft.shape[0]
+    out = np.zeros(2 * nr + nrho)
+    rc = lib().ora_eam_vjp(n, _p(x), _p(lo), _p(hi), _p(per), nr, tables.rc, _p(phi),
+                           _p(rho), nrho, tables.rho_max, _p(Ft), float(gE), _p(gF), _p(out))
+    if rc < 0:
+        raise RuntimeError("oracle eam_vjp failed")
+    return out[:nr].copy(), out[nr:2 * nr].copy(), out[2 * nr:].copy()
+
+
+def eam_jvp(x, lo, hi, periodic, tables, dphi, drho, dF, gE=0.0, gF=None):
+    """Forward-mode (dual-number) value and directional derivative of
+    L = gE * E + sum_i gF_i . F_i along the knot tangent (dphi, drho, dF)."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    lo, hi, per = _box(lo, hi, periodic)
+    phi, rho, Ft = _f64(tables.phi), _f64(tables.rho), _f64(tables.F)
+    dphi, drho, dF = _f64(dphi), _f64(drho), _f64(dF)
+    gF = np.zeros((n, 3)) if gF is None else _f64(gF, (n, 3))
+    out = np.zeros(2)
+    rc = lib().ora_eam_jvp(n, _p(x), _p(lo), _p(hi), _p(per), phi.shape[0], tables.rc,
+                           _p(phi), _p(rho), Ft.shape[0], tables.rho_max, _p(Ft), _p(dphi),
+                           _p(drho), _p(dF), float(gE), _p(gF), _p(out))
+    if rc == -2:
+        raise ValueError("a density lies above the F table (forward mode needs rho <= rho_max)")
+    if rc < 0:
+        raise RuntimeError("oracle eam_jvp failed")
+    return float(out[0]), float(out[1])
 
 
 def sampled(kind, x, lo, hi, periodic, sel, lj_params=None, tables=None):

@@ -26,7 +26,7 @@
  *   - per-bin profiles of the Appendix (mass, COM velocity, temperature per
  *     degree of freedom, pressure tensor with the virial term)
  *
- * Readings of the paper that this file fixes (all listed in the design doc):
+ * Readings of the paper that this file fixes:
  *   * pair vector d_ij = (x_j - x_i) + n*L, rounded in that order;
  *     r^2 = (dx*dx + dy*dy) + dz*dz; a pair is a neighbour iff r^2 < r_ns^2;
  *   * the neighbour list is a full list over (j, image n) with (j,n) != (i,0);
@@ -981,7 +981,7 @@ void ora_profiles(int64_t N, const double *x, const double *v, const double *mas
 
 /*
  * The window rules applied at a list build (reading of the paper's moving
- * window for a piston-driven shock along x; the design doc lists it):
+ * window for a piston-driven shock along x):
  *   x_front = largest x of an atom with v_x > u_p/2 (none: no window action);
  *   atoms with x < x_front - L_behind are deleted (order of the rest kept);
  *   while the leading edge x_max < x_front + L_ahead, copies of a fresh slab
@@ -1106,4 +1106,287 @@ int64_t ora_md_window(int64_t *n_io, int64_t cap, double *x, double *v, double *
     free(F);
     pot_free(&p);
     return nbuild;
+}
+
+/* ---------------------------------------------------------------------- */
+/* adjoint of the tabulated EAM with respect to the knot values            */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Loss L = gE * E + sum_i gF_i . F_i for one periodic/free system, as a
+ * function of the knots theta = (phi knots, rho knots, F knots).  The spline
+ * of ora_spline_eval is linear in the knot values y and the scaled slopes
+ * M_k = h m_k, and M is a fixed linear map of y; derivatives with respect to
+ * (y, M) are collected first and M's transpose is applied at the end.
+ */
+
+/* Hermite basis weights of value (w) and x-derivative (dw, per unit x) on
+ * the interval of x: coefficients of y_k, M_k, y_{k+1}, M_{k+1}. */
+static int herm_weights(int n, double h, double x, double w[4], double dw[4], double ddw[4]) {
+    double u = x / h;
+    int k = (int)floor(u);
+    if (k > n - 2) k = n - 2;
+    if (k < 0) k = 0;
+    double t = u - (double)k, t2 = t * t, t3 = t2 * t;
+    w[0] = 2.0 * t3 - 3.0 * t2 + 1.0;
+    w[1] = t3 - 2.0 * t2 + t;
+    w[2] = -2.0 * t3 + 3.0 * t2;
+    w[3] = t3 - t2;
+    dw[0] = (6.0 * t2 - 6.0 * t) / h;
+    dw[1] = (3.0 * t2 - 4.0 * t + 1.0) / h;
+    dw[2] = (-6.0 * t2 + 6.0 * t) / h;
+    dw[3] = (3.0 * t2 - 2.0 * t) / h;
+    if (ddw) {
+        ddw[0] = (12.0 * t - 6.0) / (h * h);
+        ddw[1] = (6.0 * t - 4.0) / (h * h);
+        ddw[2] = (-12.0 * t + 6.0) / (h * h);
+        ddw[3] = (6.0 * t - 2.0) / (h * h);
+    }
+    return k;
+}
+
+/* add c_v * (d value / d (y, M)) + c_d * (d derivative / d (y, M)) at x */
+static void scatter_knots(int n, double h, double x, double cv, double cd, double *gy,
+                          double *gM) {
+    double w[4], dw[4];
+    int k = herm_weights(n, h, x, w, dw, NULL);
+    gy[k] += cv * w[0] + cd * dw[0];
+    gM[k] += cv * w[1] + cd * dw[1];
+    gy[k + 1] += cv * w[2] + cd * dw[2];
+    gM[k + 1] += cv * w[3] + cd * dw[3];
+}
+
+/* transpose of M(y): interior M_k = (y_{k+1} - y_{k-1})/2, one-sided ends */
+static void slope_map_T(int n, const double *gM, double *gy) {
+    gy[0] += -1.5 * gM[0];
+    gy[1] += 2.0 * gM[0];
+    gy[2] += -0.5 * gM[0];
+    for (int k = 1; k < n - 1; ++k) {
+        gy[k + 1] += 0.5 * gM[k];
+        gy[k - 1] -= 0.5 * gM[k];
+    }
+    gy[n - 1] += 1.5 * gM[n - 1];
+    gy[n - 2] -= 2.0 * gM[n - 1];
+    gy[n - 3] += 0.5 * gM[n - 1];
+}
+
+/* second derivative of the F spline at rho (0 beyond rho_max: linear there) */
+static double embed_dd(const ora_table *t, double rho) {
+    if (rho > t->xmax) return 0.0;
+    double w[4], dw[4], ddw[4];
+    int k = herm_weights(t->n, t->h, rho, w, dw, ddw);
+    return ddw[0] * t->y[k] + ddw[1] * t->h * t->m[k] + ddw[2] * t->y[k + 1] +
+           ddw[3] * t->h * t->m[k + 1];
+}
+
+/*
+ * Reverse mode, written out from the chain rule with f_i = sum_j V'(r_ij) d^_ij,
+ * V'(r) = phi'(r) + (F'(rho_i) + F'(rho_j)) rho'(r):
+ *   phi knots: per directed pair  1/2 gE d phi(r) + (gF_i . d^_ij) d phi'(r)
+ *   c_i = sum_j [(gF_i - gF_j) . d^_ij] rho'(r_ij)
+ *   F knots:   per atom  gE d F(rho_i) + c_i d F'(rho_i)
+ *   lambda_i = gE F'(rho_i) + c_i F''(rho_i)
+ *   rho knots: per directed pair  lambda_i d rho(r) + (gF_i . d^_ij)(F'_i + F'_j) d rho'(r)
+ * dtheta [nr + nr + nrho] = (phi, rho, F) knot gradients.
+ */
+int ora_eam_vjp(int64_t N, const double *x, const double *lo, const double *hi, const int *per,
+                int nr, double rc, const double *phi, const double *rho, int nrho,
+                double rho_max, const double *Ftab, double gE, const double *gF,
+                double *dtheta) {
+    ora_box b = make_box(lo, hi, per);
+    ora_pot p;
+    pot_eam_init(&p, nr, rc, phi, rho, nrho, rho_max, Ftab);
+    ora_vlist vl;
+    memset(&vl, 0, sizeof(vl));
+    vl.off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N + 1));
+    if (brute_list(N, x, &b, rc, &vl) != 0) return -1;
+    double rc2 = rc * rc;
+    double *rho_i = (double *)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    double *fp = (double *)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    double *ci = (double *)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    double *gyp = (double *)calloc((size_t)nr, sizeof(double));
+    double *gMp = (double *)calloc((size_t)nr, sizeof(double));
+    double *gyr = (double *)calloc((size_t)nr, sizeof(double));
+    double *gMr = (double *)calloc((size_t)nr, sizeof(double));
+    double *gyF = (double *)calloc((size_t)nrho, sizeof(double));
+    double *gMF = (double *)calloc((size_t)nrho, sizeof(double));
+    /* forward: densities and F'(rho_i) */
+    for (int64_t i = 0; i < N; ++i) {
+        for (int64_t q = vl.off[i]; q < vl.off[i + 1]; ++q) {
+            double d[3];
+            double r2 = pair_vec(x + 3 * i, x + 3 * (int64_t)vl.j[q], vl.n + 3 * q, &b, d);
+            if (r2 < rc2) {
+                double dr;
+                rho_i[i] += radial(&p.rho, sqrt(r2), &dr);
+            }
+        }
+        double dF;
+        embed(&p.F, rho_i[i], &dF, NULL);
+        fp[i] = dF;
+    }
+    /* c_i */
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t q = vl.off[i]; q < vl.off[i + 1]; ++q) {
+            int64_t j = vl.j[q];
+            double d[3];
+            double r2 = pair_vec(x + 3 * i, x + 3 * j, vl.n + 3 * q, &b, d);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2), drho;
+            radial(&p.rho, r, &drho);
+            double g = 0.0;
+            for (int k = 0; k < 3; ++k) g += (gF[3 * i + k] - gF[3 * j + k]) * d[k] / r;
+            ci[i] += g * drho;
+        }
+    /* F knots, and lambda_i */
+    double *lam = (double *)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    for (int64_t i = 0; i < N; ++i) {
+        double rh = rho_i[i];
+        if (rh > rho_max) {
+            /* F = y_{n-1} + (M_{n-1}/h)(rho - rho_max), F' = M_{n-1}/h */
+            double h = p.F.h;
+            gyF[nrho - 1] += gE;
+            gMF[nrho - 1] += gE * (rh - rho_max) / h + ci[i] / h;
+        } else {
+            scatter_knots(nrho, p.F.h, rh, gE, ci[i], gyF, gMF);
+        }
+        lam[i] = gE * fp[i] + ci[i] * embed_dd(&p.F, rh);
+    }
+    /* phi and rho knots over directed pairs */
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t q = vl.off[i]; q < vl.off[i + 1]; ++q) {
+            int64_t j = vl.j[q];
+            double d[3];
+            double r2 = pair_vec(x + 3 * i, x + 3 * j, vl.n + 3 * q, &b, d);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2);
+            if (r >= rc) continue; /* the radial tables are 0 from rc on */
+            double gd = 0.0;
+            for (int k = 0; k < 3; ++k) gd += gF[3 * i + k] * d[k] / r;
+            scatter_knots(nr, p.phi.h, r, 0.5 * gE, gd, gyp, gMp);
+            scatter_knots(nr, p.rho.h, r, lam[i], gd * (fp[i] + fp[j]), gyr, gMr);
+        }
+    slope_map_T(nr, gMp, gyp);
+    slope_map_T(nr, gMr, gyr);
+    slope_map_T(nrho, gMF, gyF);
+    memcpy(dtheta, gyp, sizeof(double) * (size_t)nr);
+    memcpy(dtheta + nr, gyr, sizeof(double) * (size_t)nr);
+    memcpy(dtheta + 2 * nr, gyF, sizeof(double) * (size_t)nrho);
+    free(rho_i); free(fp); free(ci); free(lam);
+    free(gyp); free(gMp); free(gyr); free(gMr); free(gyF); free(gMF);
+    free(vl.off); free(vl.j); free(vl.n);
+    pot_free(&p);
+    return 0;
+}
+
+/* ---- forward mode (dual numbers): an independent derivative ----------- */
+
+typedef struct {
+    double v, d;
+} dual;
+
+static dual dmk(double v, double d) { dual r = {v, d}; return r; }
+static dual dadd(dual a, dual b) { return dmk(a.v + b.v, a.d + b.d); }
+static dual dmul(dual a, dual b) { return dmk(a.v * b.v, a.v * b.d + a.d * b.v); }
+static dual dscale(dual a, double s) { return dmk(a.v * s, a.d * s); }
+
+/* spline value and x-derivative with tangent knots dy: both duals (x fixed,
+ * or x a dual for rho_i) */
+static void dual_spline(const double *y, const double *dy, int n, double h, dual x, dual *val,
+                        dual *der) {
+    /* slopes of y and of dy by the same 3-point rule */
+    double u = x.v / h;
+    int k = (int)floor(u);
+    if (k > n - 2) k = n - 2;
+    if (k < 0) k = 0;
+    dual t = dscale(x, 1.0 / h);
+    t.v -= (double)k;
+    double Mv[2], Md[2];
+    for (int q = 0; q < 2; ++q) {
+        int kk = k + q;
+        if (kk == 0) {
+            Mv[q] = 0.5 * (-3.0 * y[0] + 4.0 * y[1] - y[2]);
+            Md[q] = 0.5 * (-3.0 * dy[0] + 4.0 * dy[1] - dy[2]);
+        } else if (kk == n - 1) {
+            Mv[q] = 0.5 * (3.0 * y[n - 1] - 4.0 * y[n - 2] + y[n - 3]);
+            Md[q] = 0.5 * (3.0 * dy[n - 1] - 4.0 * dy[n - 2] + dy[n - 3]);
+        } else {
+            Mv[q] = 0.5 * (y[kk + 1] - y[kk - 1]);
+            Md[q] = 0.5 * (dy[kk + 1] - dy[kk - 1]);
+        }
+    }
+    dual y0 = dmk(y[k], dy[k]), y1 = dmk(y[k + 1], dy[k + 1]);
+    dual M0 = dmk(Mv[0], Md[0]), M1 = dmk(Mv[1], Md[1]);
+    dual t2 = dmul(t, t), t3 = dmul(t2, t);
+    dual h00 = dadd(dadd(dscale(t3, 2.0), dscale(t2, -3.0)), dmk(1.0, 0.0));
+    dual h10 = dadd(dadd(t3, dscale(t2, -2.0)), t);
+    dual h01 = dadd(dscale(t3, -2.0), dscale(t2, 3.0));
+    dual h11 = dadd(t3, dscale(t2, -1.0));
+    *val = dadd(dadd(dmul(h00, y0), dmul(h10, M0)), dadd(dmul(h01, y1), dmul(h11, M1)));
+    dual d00 = dadd(dscale(t2, 6.0), dscale(t, -6.0));
+    dual d10 = dadd(dadd(dscale(t2, 3.0), dscale(t, -4.0)), dmk(1.0, 0.0));
+    dual d01 = dadd(dscale(t2, -6.0), dscale(t, 6.0));
+    dual d11 = dadd(dscale(t2, 3.0), dscale(t, -2.0));
+    *der = dscale(dadd(dadd(dmul(d00, y0), dmul(d10, M0)), dadd(dmul(d01, y1), dmul(d11, M1))),
+                  1.0 / h);
+}
+
+/*
+ * Directional derivative of L = gE E + sum_i gF_i . F_i along the knot
+ * tangent (dphi, drho, dF), by forward mode through the whole evaluation
+ * (densities, embedding, forces).  Independent of ora_eam_vjp.  Requires
+ * every rho_i <= rho_max.
+ */
+int ora_eam_jvp(int64_t N, const double *x, const double *lo, const double *hi, const int *per,
+                int nr, double rc, const double *phi, const double *rho, int nrho,
+                double rho_max, const double *Ftab, const double *dphi, const double *drho,
+                const double *dF, double gE, const double *gF, double *out) {
+    ora_box b = make_box(lo, hi, per);
+    ora_vlist vl;
+    memset(&vl, 0, sizeof(vl));
+    vl.off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N + 1));
+    if (brute_list(N, x, &b, rc, &vl) != 0) return -1;
+    double rc2 = rc * rc, hr = rc / (double)(nr - 1), hF = rho_max / (double)(nrho - 1);
+    dual *rh = (dual *)calloc((size_t)(N > 0 ? N : 1), sizeof(dual));
+    dual *Fp = (dual *)calloc((size_t)(N > 0 ? N : 1), sizeof(dual));
+    dual L = dmk(0.0, 0.0);
+    for (int64_t i = 0; i < N; ++i) {
+        for (int64_t q = vl.off[i]; q < vl.off[i + 1]; ++q) {
+            double d[3];
+            double r2 = pair_vec(x + 3 * i, x + 3 * (int64_t)vl.j[q], vl.n + 3 * q, &b, d);
+            if (!(r2 < rc2) || sqrt(r2) >= rc) continue;
+            dual v, dv;
+            dual_spline(rho, drho, nr, hr, dmk(sqrt(r2), 0.0), &v, &dv);
+            rh[i] = dadd(rh[i], v);
+        }
+        if (rh[i].v > rho_max) return -2;
+        dual Fv, dFv;
+        dual_spline(Ftab, dF, nrho, hF, rh[i], &Fv, &dFv);
+        Fp[i] = dFv;
+        L = dadd(L, dscale(Fv, gE));
+    }
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t q = vl.off[i]; q < vl.off[i + 1]; ++q) {
+            int64_t j = vl.j[q];
+            double d[3];
+            double r2 = pair_vec(x + 3 * i, x + 3 * j, vl.n + 3 * q, &b, d);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2);
+            if (r >= rc) continue;
+            dual pv, pd, rv, rd;
+            dual_spline(phi, dphi, nr, hr, dmk(r, 0.0), &pv, &pd);
+            dual_spline(rho, drho, nr, hr, dmk(r, 0.0), &rv, &rd);
+            L = dadd(L, dscale(pv, 0.5 * gE));
+            dual s = dadd(pd, dmul(dadd(Fp[i], Fp[j]), rd));  /* V'(r) */
+            double gd = 0.0;
+            for (int k = 0; k < 3; ++k) gd += gF[3 * i + k] * d[k] / r;
+            L = dadd(L, dscale(s, gd));
+        }
+    out[0] = L.v;
+    out[1] = L.d;
+    free(rh);
+    free(Fp);
+    free(vl.off);
+    free(vl.j);
+    free(vl.n);
+    return 0;
 }

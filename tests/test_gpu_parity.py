@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Tolerances (written from the arithmetic, see DESIGN.md "Parity bars"):
+Tolerances (written from the arithmetic):
   * neighbour sets: bit-exact as sorted (j, image) lists, both precisions;
   * FP64 path: |dE| <= 1e-12 |E|;  max|dF| <= 1e-12 max|F| + 1e-13 eV/A;
     virial components within 1e-12 of max |W|;

@@ -1,5 +1,5 @@
 """Pins of the oracle's moving-window rules (Sec. "Moving window simulation",
-read for a piston-driven shock along x, reading 11).
+read for a piston-driven shock along x).
 
 The rules are bookkeeping, so the pins are their invariants: atom-count
 balance (kept + appended), nothing left behind the cut, appended atoms exactly
