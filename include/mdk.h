@@ -124,7 +124,9 @@ int mdk_set_potential_lj(mdk_ctx *ctx, double eps, double sigma, double rc,
  * Between knots: cubic Hermite spline, knot slopes from 3-point differences
  * (one-sided at the ends).  r >= rc gives 0; rho > rho_max extrapolates F
  * linearly and makes mdk_compute/mdk_step return MDK_ERR_RHO_RANGE.
- * 3 <= nr, nrho <= 8192.
+ * 3 <= nr <= 7168 (the FP64 phi and rho tables share 227 KB of shared
+ * memory), 3 <= nrho <= 65536; otherwise MDK_ERR_BAD_ARG.  Same-size tables
+ * replace the old ones in place (no new workspace needed).
  */
 int mdk_set_potential_eam(mdk_ctx *ctx, int nr, double rc, const double *phi,
                           const double *rho, int nrho, double rho_max,
@@ -296,6 +298,33 @@ int mdk_window_counts(mdk_ctx *ctx, int64_t *inserted, int64_t *deleted);
  */
 int mdk_profiles(mdk_ctx *ctx, int axis, double origin, double bin_w, int nbins,
                  double cross_area, double *out, int on_device);
+
+/* ---- adjoint of the EAM tables ------------------------------------------------ */
+
+/*
+ * Gradient of the loss L = sum_r gE[r] E_r + sum_i gF_i . F_i with respect to
+ * the knot values of the EAM tables (EAM as in mdk_set_potential_eam and the
+ * embedded-atom form of Sec. "Comparison of aluminum shock Hugoniot ...";
+ * forces f_i = sum_j V'(r_ij) r_ji / r_ji of Sec. "Potentials support"), at
+ * the current positions.  No counterpart in the paper, which evaluates the
+ * tables only; this is the vector-Jacobian product of mdk_compute's E and F.
+ *
+ *   gE     : [n_replicas] weight of each replica's potential energy, or NULL (0)
+ *   gF     : [N][3] weights of the forces, caller's atom order, or NULL (0)
+ *   dtheta : [2 nr + nrho] output: dL/dphi_k (k < nr), dL/drho_k (nr knots),
+ *            dL/dF_k (nrho knots), in the order of mdk_set_potential_eam
+ *   on_device : 0 = host arrays (the call synchronises and returns the
+ *            device status, as mdk_compute); 1 = device arrays (returns
+ *            after enqueueing).
+ * Pair distances are recomputed from the positions and the Verlet list (none
+ * are stored).  Pair arithmetic is in the context's precision (FP32 in
+ * MDK_MIXED); per-atom terms and all gradient sums are FP64.  Gradients are
+ * summed with FP64 atomics, so two calls agree to rounding, not bit for bit.
+ * The kernels need 32 * nr bytes of shared memory (nr <= 7168).
+ * Errors: MDK_ERR_ORDER when the potential is not EAM, the state is not set
+ * or the moving window is on; MDK_ERR_WORKSPACE as mdk_compute.
+ */
+int mdk_eam_vjp(mdk_ctx *ctx, const double *gE, const double *gF, double *dtheta, int on_device);
 
 /* ---- allocation-free variant ------------------------------------------------ */
 

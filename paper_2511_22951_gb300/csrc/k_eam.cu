@@ -365,6 +365,34 @@ void launch_eam(const Sys &s, const EAMParams &p, int precision, Mode mode, Step
     by_mode<Mixed>(s, p, mode, a, cfg, 1, st);
 }
 
+namespace {
+template <class P, int T>
+void rho_only(const Sys &s, const EAMParams &p, StepArgs a, int block, int prec,
+              cudaStream_t st) {
+  const int b1 = eam_smem_bytes(p, prec, 1);
+  auto k1 = k_rho<P, false, T>;
+  k1<<<grid_for(k1, block, b1, (long long)s.N_cap * T), block, b1, st>>>(s, p, a);
+}
+template <class P>
+void rho_by_tpa(const Sys &s, const EAMParams &p, StepArgs a, const LaunchCfg &c, int prec,
+                cudaStream_t st) {
+  if (c.tpa == 4)
+    rho_only<P, 4>(s, p, a, c.block, prec, st);
+  else if (c.tpa == 2)
+    rho_only<P, 2>(s, p, a, c.block, prec, st);
+  else
+    rho_only<P, 1>(s, p, a, c.block, prec, st);
+}
+}  // namespace
+
+void launch_eam_rho(const Sys &s, const EAMParams &p, int precision, StepArgs a,
+                    const LaunchCfg &cfg, cudaStream_t st) {
+  if (precision == 0)
+    rho_by_tpa<Fp64>(s, p, a, cfg, 0, st);
+  else
+    rho_by_tpa<Mixed>(s, p, a, cfg, 1, st);
+}
+
 void launch_eam_prepare(const EAMParams &p, const double *phi, const double *rho,
                         const double *F, EAMTablesDev out, cudaStream_t st) {
   const int n = p.nr > p.nrho ? p.nr : p.nrho;

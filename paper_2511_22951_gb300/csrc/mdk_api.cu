@@ -49,6 +49,9 @@ struct mdk_ctx {
   Sys sys{};
   char *eam_base = nullptr;
   EAMTablesDev eam_dev{};
+  double2 *adj_acc = nullptr;  // adjoint histograms: phi, rho (nr each), F (nrho)
+  double *adj_out = nullptr;   // [2 nr + nrho] knot gradients
+  double *adj_gE = nullptr;    // [n_rep] energy weights
   double *thermo_ring = nullptr;
   int cur = 0;
   bool state_set = false, list_built = false, forces_valid = false;
@@ -155,6 +158,9 @@ size_t layout(mdk_ctx *c, char *base) {
   t.phi_d32 = cv.take<float2>(nr);
   t.rho_d32 = cv.take<float2>(nr);
   t.phi_v32 = cv.take<float>(nr);
+  c->adj_acc = cv.take<double2>((size_t)2 * nr + nrho);
+  c->adj_out = cv.take<double>((size_t)2 * nr + nrho);
+  c->adj_gE = cv.take<double>(c->n_rep);
   c->eam_base = reinterpret_cast<char *>(kn);
   c->eam.phi64 = t.phi64;
   c->eam.rho64 = t.rho64;
@@ -951,6 +957,54 @@ int mdk_compute(mdk_ctx *c, double *E, double *F, double *virial, int on_device)
     if (virial)
       for (int k = 0; k < 6; ++k) virial[6 * q + k] = red[(size_t)9 * q + 2 + k];
   }
+  return status_from_bits(st.bits);
+}
+
+int mdk_eam_vjp(mdk_ctx *c, const double *gE, const double *gF, double *dtheta, int on_device) {
+  if (check_ctx(c) || !dtheta) return MDK_ERR_BAD_ARG;
+  if (c->pot != 2 || c->win_on) return MDK_ERR_ORDER;
+  int r = ensure_ready(c);
+  if (r) return r;
+  if (!c->list_built) {
+    r = build_now(c);
+    if (r) return r;
+  }
+  Sys &s = c->sys;
+  const EAMParams &e = c->eam;
+  const size_t Nc = (size_t)std::max<int64_t>(c->N_cap, 1);
+  const size_t n_out = (size_t)2 * e.nr + e.nrho;
+  const cudaMemcpyKind in_kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (gE)
+    MDK_CK(cudaMemcpyAsync(c->adj_gE, gE, sizeof(double) * c->n_rep, in_kind, c->stream));
+  else
+    MDK_CK(cudaMemsetAsync(c->adj_gE, 0, sizeof(double) * c->n_rep, c->stream));
+  // scratch: gF in internal order [0, 4 Nc), lambda [4 Nc, 5 Nc), staged gF [6 Nc, 9 Nc)
+  const double *gF_dev = (c->N > 0) ? gF : nullptr;
+  if (gF && !on_device && c->N > 0) {
+    MDK_CK(cudaMemcpyAsync(s.tmp + 6 * Nc, gF, sizeof(double) * 3 * c->N, cudaMemcpyHostToDevice,
+                           c->stream));
+    gF_dev = s.tmp + 6 * Nc;
+  }
+  MDK_CK(cudaMemsetAsync(c->adj_acc, 0, sizeof(double2) * n_out, c->stream));
+  AdjArgs a{};
+  a.cur = c->cur;
+  a.gE = c->adj_gE;
+  a.gint = s.tmp;
+  a.lam = s.tmp + 4 * Nc;
+  a.acc_phi = c->adj_acc;
+  a.acc_rho = c->adj_acc + e.nr;
+  a.acc_F = c->adj_acc + 2 * e.nr;
+  a.out = on_device ? dtheta : c->adj_out;
+  launch_eam_rho(s, e, c->precision, StepArgs{0.0, c->cur, 0}, c->cfg, c->stream);
+  if (launch_eam_adjoint(s, e, c->precision, gF_dev, a, c->N, c->stream)) return MDK_ERR_CUDA;
+  c->launches += 5;
+  MDK_CK(cudaPeekAtLastError());
+  if (on_device) return MDK_OK;
+  MDK_CK(cudaMemcpyAsync(dtheta, c->adj_out, sizeof(double) * n_out, cudaMemcpyDeviceToHost,
+                         c->stream));
+  DevStatus st;
+  r = read_status(c, &st);
+  if (r) return r;
   return status_from_bits(st.bits);
 }
 

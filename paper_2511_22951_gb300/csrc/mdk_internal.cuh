@@ -275,5 +275,24 @@ void launch_profiles(const Sys &s, int axis, double origin, double bin_w, int nb
                      double cross_area, double *acc, cudaStream_t st);
 int eam_smem_bytes(const EAMParams &p, int precision, int pass);
 int configure_eam_smem(int bytes_pass1, int bytes_pass2, int precision);
+// pass 1 of the EAM force loop alone (rho_i and F'(rho_i) of the current positions)
+void launch_eam_rho(const Sys &s, const EAMParams &p, int precision, StepArgs a,
+                    const LaunchCfg &cfg, cudaStream_t st);
+
+// EAM adjoint (k_adjoint.cu): gradient of sum_r gE_r E_r + sum_i gF_i . F_i with
+// respect to the phi, rho and F knot values
+struct AdjArgs {
+  int cur;                           // gather copy of the current positions
+  int f_in_smem;                     // F histogram privatised in shared memory
+  const double *gE;                  // [n_rep] energy weights
+  void *gint;                        // [N_cap] gF in internal order (gather-copy type)
+  double *lam;                       // [N_cap] lambda_i = gE F'(rho_i) + c_i F''(rho_i)
+  double2 *acc_phi, *acc_rho, *acc_F;  // per knot: (d/dy, d/dM) accumulators
+  double *out;                       // [2 nr + nrho] knot gradients (phi | rho | F)
+};
+int adjoint_smem_bytes(const EAMParams &ep, int precision, int pass);
+int adjoint_f_in_smem(const EAMParams &ep, int precision);
+int launch_eam_adjoint(const Sys &s, const EAMParams &ep, int precision, const double *gF,
+                       const AdjArgs &a, int64_t n_atoms, cudaStream_t st);
 
 }  // namespace mdk

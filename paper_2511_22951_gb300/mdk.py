@@ -73,6 +73,7 @@ SIGNATURES = {
     "mdk_profile": [_P, _I],
     "mdk_get_profile": [_P, _P],
     "mdk_lj_compute_noalloc": [_P, _I64, _P, _P, _P, _D, _D, _D, _I, _P, _P, _P],
+    "mdk_eam_vjp": [_P, _P, _P, _P, _I],
 }
 
 _lib = None
@@ -163,6 +164,8 @@ class Context:
         self.ws = None
         self._state = None
         self._has_state = False
+        self._eam_sizes = None
+        self.version = 0  # bumped by every call that changes positions or tables
         if capacity is not None:
             _check(self.lib.mdk_set_capacity(self.h, int(capacity)), "mdk_set_capacity")
 
@@ -181,6 +184,7 @@ class Context:
 
     # -- setup ----------------------------------------------------------------
     def set_potential_lj(self, eps, sigma, rc, shift_mode=1):
+        self.version += 1
         _check(self.lib.mdk_set_potential_lj(self.h, eps, sigma, rc, shift_mode),
                "mdk_set_potential_lj")
 
@@ -191,6 +195,8 @@ class Context:
         _check(self.lib.mdk_set_potential_eam(self.h, phi.shape[0], tables.rc, _ptr(phi),
                                               _ptr(rho), F.shape[0], tables.rho_max, _ptr(F)),
                "mdk_set_potential_eam")
+        self._eam_sizes = (phi.shape[0], F.shape[0])
+        self.version += 1
 
     def plan(self, rc, skin, max_neighbors=0, rebuild_every=0):
         _check(self.lib.mdk_plan_neighbors(self.h, rc, skin, max_neighbors, rebuild_every),
@@ -237,6 +243,7 @@ class Context:
             on_dev = 1
         self._state = (x, v, on_dev)
         self._has_state = True
+        self.version += 1
         _check(self.lib.mdk_set_state(self.h, _ptr(x), _ptr(v), on_dev), "mdk_set_state")
 
     def _save_state(self):
@@ -303,6 +310,25 @@ class Context:
     def compute_device(self, E, F, W):
         _check(self.lib.mdk_compute(self.h, _ptr(E), _ptr(F), _ptr(W), 1), "mdk_compute")
 
+    def eam_vjp(self, gE=None, gF=None):
+        """Host gradient of sum_r gE[r] E_r + sum_i gF_i . F_i with respect to the
+        EAM knots: returns (d_phi [nr], d_rho [nr], d_F [nrho])."""
+        nr, nrho = self._eam_sizes
+        gE = None if gE is None else _host_f64(gE, (self.n_rep,))
+        gF = None if gF is None else _host_f64(gF, (self.natoms(), 3))
+        out = np.zeros(2 * nr + nrho)
+        r = self.lib.mdk_eam_vjp(self.h, _ptr(gE), _ptr(gF), _ptr(out), 0)
+        if r in (MDK_ERR_NEIGH_OVERFLOW, MDK_ERR_WORKSPACE):
+            self.alloc_workspace()
+            r = self.lib.mdk_eam_vjp(self.h, _ptr(gE), _ptr(gF), _ptr(out), 0)
+        _check(r, "mdk_eam_vjp")
+        return out[:nr], out[nr:2 * nr], out[2 * nr:]
+
+    def eam_vjp_device(self, gE, gF, out):
+        """Device variant: gE [n_rep], gF [N,3] (either may be None), out
+        [2 nr + nrho] float64 CUDA tensors; returns after enqueueing."""
+        _check(self.lib.mdk_eam_vjp(self.h, _ptr(gE), _ptr(gF), _ptr(out), 1), "mdk_eam_vjp")
+
     def per_atom(self):
         n = self.natoms()
         U = np.zeros(n)
@@ -311,6 +337,7 @@ class Context:
         return U, Wa
 
     def step(self, dt, nsteps, check=True):
+        self.version += 1
         _check(self.lib.mdk_step(self.h, dt, int(nsteps)), "mdk_step")
         if check:
             self.check()
