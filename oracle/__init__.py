@@ -66,11 +66,11 @@ def lib():
         L.ora_md_run.restype = I64
         L.ora_profiles.argtypes = [I64, P, P, P, P, P, I, D, D, I, D, P]
         L.ora_profiles.restype = None
-        L.ora_window_apply.argtypes = [I64, I64, P, P, P, P, P, P, D, D, D, P, P, I64, D, D,
-                                       D, D]
+        L.ora_window_apply.argtypes = [I64, I64, P, P, P, P, P, P, D, D, D, D, D, D, P, P,
+                                       I64, D, D, D, D]
         L.ora_window_apply.restype = I64
         L.ora_md_window.argtypes = [P, I64, P, P, P, P, P, P, P, P, P, I, D, P, P, I, D, P, D,
-                                    D, I64, I, D, D, D, P, P, I64, D, D, D, D]
+                                    D, I64, I, D, D, D, D, P, P, I64, D, D, D, D]
         L.ora_md_window.restype = I64
         L.ora_eam_vjp.argtypes = [I64, P, P, P, P, I, D, P, P, I, D, P, D, P, P]
         L.ora_eam_vjp.restype = I
@@ -315,19 +315,21 @@ class WindowState:
                 "piston": self.pis[:n].astype(bool), "ids": self.ids[:n].copy()}
 
 
-def window_apply(st, u_p, L_behind, L_ahead, slab_x, slab_v, slab_lx, slab_gap, slab_mass,
-                 piston_depth):
+def window_apply(st, x_lo, x_hi, front_bin, u_p, L_behind, L_ahead, slab_x, slab_v, slab_lx,
+                 slab_gap, slab_mass, piston_depth):
+    """One application of the window rules (x_lo, x_hi: the box along x;
+    front_bin: width of the bins that locate the shock front)."""
     sx = _f64(slab_x, (-1, 3))
     sv = _f64(slab_v, (-1, 3))
     st.n = int(lib().ora_window_apply(st.n, st.cap, _p(st.x), _p(st.v), _p(st.m), _p(st.pis),
-                                      _p(st.ids), _p(st.next_id), u_p, L_behind, L_ahead,
-                                      _p(sx), _p(sv), sx.shape[0], slab_lx, slab_gap,
-                                      slab_mass, piston_depth))
+                                      _p(st.ids), _p(st.next_id), x_lo, x_hi, front_bin, u_p,
+                                      L_behind, L_ahead, _p(sx), _p(sv), sx.shape[0], slab_lx,
+                                      slab_gap, slab_mass, piston_depth))
     return st
 
 
-def md_window(st, lo, hi, periodic, tables, dt, nsteps, skin, rebuild_every, u_p, L_behind,
-              L_ahead, slab_x, slab_v, slab_lx, slab_gap, slab_mass, piston_depth):
+def md_window(st, lo, hi, periodic, tables, dt, nsteps, skin, rebuild_every, u_p, front_bin,
+              L_behind, L_ahead, slab_x, slab_v, slab_lx, slab_gap, slab_mass, piston_depth):
     lo, hi, per = _box(lo, hi, periodic)
     phi, rho, Ft = _f64(tables.phi), _f64(tables.rho), _f64(tables.F)
     sx = _f64(slab_x, (-1, 3))
@@ -336,7 +338,8 @@ def md_window(st, lo, hi, periodic, tables, dt, nsteps, skin, rebuild_every, u_p
     nb = lib().ora_md_window(_p(n), st.cap, _p(st.x), _p(st.v), _p(st.m), _p(st.pis),
                              _p(st.ids), _p(st.next_id), _p(lo), _p(hi), _p(per), phi.shape[0],
                              tables.rc, _p(phi), _p(rho), Ft.shape[0], tables.rho_max, _p(Ft),
-                             skin, dt, nsteps, rebuild_every, u_p, L_behind, L_ahead, _p(sx),
+                             skin, dt, nsteps, rebuild_every, u_p, front_bin, L_behind,
+                             L_ahead, _p(sx),
                              _p(sv), sx.shape[0], slab_lx, slab_gap, slab_mass, piston_depth)
     if nb < 0:
         raise RuntimeError(f"oracle md_window failed ({nb})")

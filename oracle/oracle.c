@@ -982,27 +982,56 @@ void ora_profiles(int64_t N, const double *x, const double *v, const double *mas
 /*
  * The window rules applied at a list build (reading of the paper's moving
  * window for a piston-driven shock along x):
- *   x_front = largest x of an atom with v_x > u_p/2 (none: no window action);
+ *   the shock front is found from bins of width w along x, b = floor((x -
+ *   x_lo) / w) clamped to [0, nb - 1], nb = max(1, ceil((x_hi - x_lo) / w)):
+ *   a bin is shocked when its mean v_x exceeds u_p / 2, decided exactly on
+ *   velocities rounded to multiples of 2^-40 Angstrom/fs:
+ *   2 * sum_i q(v_x,i) > n_b * q(u_p), q(v) = rint(v * 2^40);
+ *   x_front = x_lo + (b* + 1) w for the largest shocked bin b* (none: no
+ *   window action);
  *   atoms with x < x_front - L_behind are deleted (order of the rest kept);
  *   while the leading edge x_max < x_front + L_ahead, copies of a fresh slab
- *   are appended: copy c at x offset x_max + gap + c * slab_lx, velocities
+ *   are appended: copy c at x offset (x_max + gap) + c * slab_lx, velocities
  *   slab_v, ids next_id, next_id + 1, ...; k = ceil((x_front + L_ahead -
- *   x_max) / slab_lx) copies, as many as the capacity allows;
+ *   x_max) / slab_lx) copies, at most floor(((x_hi - x_max) - gap) /
+ *   slab_lx) (no copy starts past the box) and as many atoms as the
+ *   capacity allows;
  *   atoms with x < x_min + piston_depth (x_min over the atoms left) become
  *   piston atoms.
  * Returns the new atom count.
  */
 int64_t ora_window_apply(int64_t N, int64_t cap, double *x, double *v, double *mass,
-                         uint8_t *piston, int64_t *ids, int64_t *next_id, double u_p,
-                         double L_behind, double L_ahead, const double *slab_x,
-                         const double *slab_v, int64_t n_slab, double slab_lx,
-                         double slab_gap, double slab_mass, double piston_depth) {
-    double x_front = -INFINITY, x_max = -INFINITY;
+                         uint8_t *piston, int64_t *ids, int64_t *next_id, double x_lo,
+                         double x_hi, double front_bin, double u_p, double L_behind,
+                         double L_ahead, const double *slab_x, const double *slab_v,
+                         int64_t n_slab, double slab_lx, double slab_gap, double slab_mass,
+                         double piston_depth) {
+    const double two40 = 1099511627776.0;
+    int64_t nb = (int64_t)ceil((x_hi - x_lo) / front_bin);
+    if (nb < 1) nb = 1;
+    long long *S = (long long *)calloc((size_t)nb, sizeof(long long));
+    long long *cnt = (long long *)calloc((size_t)nb, sizeof(long long));
+    double x_max = -INFINITY;
     for (int64_t i = 0; i < N; ++i) {
-        if (v[3 * i] > 0.5 * u_p && x[3 * i] > x_front) x_front = x[3 * i];
-        if (x[3 * i] > x_max) x_max = x[3 * i];
+        double xi = x[3 * i], vi = v[3 * i];
+        if (xi > x_max) x_max = xi;
+        if (!isfinite(xi) || !isfinite(vi)) continue;
+        double u = floor((xi - x_lo) / front_bin);
+        int64_t b = u < 0.0 ? 0 : (u > (double)(nb - 1) ? nb - 1 : (int64_t)u);
+        S[b] += llrint(vi * two40);
+        cnt[b] += 1;
     }
-    if (x_front == -INFINITY) return N;
+    long long q_up = llrint(u_p * two40);
+    int64_t bf = -1;
+    for (int64_t b = nb - 1; b >= 0; --b)
+        if (cnt[b] > 0 && 2 * S[b] > cnt[b] * q_up) {
+            bf = b;
+            break;
+        }
+    free(S);
+    free(cnt);
+    if (bf < 0) return N;
+    double x_front = x_lo + (double)(bf + 1) * front_bin;
     double cut = x_front - L_behind;
     int64_t n = 0;
     for (int64_t i = 0; i < N; ++i) {
@@ -1020,8 +1049,11 @@ int64_t ora_window_apply(int64_t N, int64_t cap, double *x, double *v, double *m
     }
     double need = x_front + L_ahead - x_max;
     int64_t copies = need > 0.0 ? (int64_t)ceil(need / slab_lx) : 0;
+    double room = floor(((x_hi - x_max) - slab_gap) / slab_lx);
+    int64_t fit = room > 0.0 ? (int64_t)room : 0;
+    if (copies > fit) copies = fit;
     for (int64_t c = 0; c < copies; ++c) {
-        double x0 = x_max + slab_gap + (double)c * slab_lx;
+        double x0 = (x_max + slab_gap) + (double)c * slab_lx;
         for (int64_t q = 0; q < n_slab && n < cap; ++q) {
             x[3 * n] = slab_x[3 * q] + x0;
             x[3 * n + 1] = slab_x[3 * q + 1];
@@ -1053,9 +1085,9 @@ int64_t ora_md_window(int64_t *n_io, int64_t cap, double *x, double *v, double *
                       const double *hi, const int *per, int nr, double rc_eam,
                       const double *phi, const double *rho, int nrho, double rho_max,
                       const double *Ftab, double skin, double dt, int64_t nsteps,
-                      int rebuild_every, double u_p, double L_behind, double L_ahead,
-                      const double *slab_x, const double *slab_v, int64_t n_slab,
-                      double slab_lx, double slab_gap, double slab_mass,
+                      int rebuild_every, double u_p, double front_bin, double L_behind,
+                      double L_ahead, const double *slab_x, const double *slab_v,
+                      int64_t n_slab, double slab_lx, double slab_gap, double slab_mass,
                       double piston_depth) {
     int64_t N = *n_io;
     ora_box b = make_box(lo, hi, per);
@@ -1085,9 +1117,9 @@ int64_t ora_md_window(int64_t *n_io, int64_t cap, double *x, double *v, double *
             for (int k = 0; k < 3; ++k) x[3 * i + k] += dt * v[3 * i + k];
         }
         if (((step + 1) % rebuild_every) == 0) {
-            N = ora_window_apply(N, cap, x, v, mass, piston, ids, next_id, u_p, L_behind,
-                                 L_ahead, slab_x, slab_v, n_slab, slab_lx, slab_gap,
-                                 slab_mass, piston_depth);
+            N = ora_window_apply(N, cap, x, v, mass, piston, ids, next_id, lo[0], hi[0],
+                                 front_bin, u_p, L_behind, L_ahead, slab_x, slab_v, n_slab,
+                                 slab_lx, slab_gap, slab_mass, piston_depth);
             ora_wrap(N, x, lo, hi, per);
             if (vlist_build(&vl, N, x, &b, rns) != 0) return -2;
             ++nbuild;

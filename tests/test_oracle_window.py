@@ -1,11 +1,15 @@
 """Pins of the oracle's moving-window rules (Sec. "Moving window simulation",
 read for a piston-driven shock along x).
 
-The rules are bookkeeping, so the pins are their invariants: atom-count
-balance (kept + appended), nothing left behind the cut, appended atoms exactly
-at the slab positions shifted to the leading edge, ids unique and increasing
-for appended atoms, the new rear layer flagged as piston, and no action when
-nothing moves faster than u_p / 2.
+The rules are bookkeeping, so the pins are their invariants: the front at
+the upper edge of the last bin whose mean v_x exceeds u_p / 2 (a lattice
+shocked up to a known plane, with bins that do not line up with the planes,
+gives it in closed form), atom-count balance (kept + appended), nothing left
+behind the cut, appended atoms exactly at the slab positions shifted to the
+leading edge, ids unique and increasing for appended atoms, the new rear
+layer flagged as piston, no action when no bin moves faster than u_p / 2 on
+average (a single fast atom in a thermal slab is not a front), and no copy
+started past the box.
 """
 import numpy as np
 
@@ -31,15 +35,22 @@ def state(ora, cap=4000):
     return ora.WindowState(s.x, v, s.masses, pis, cap), s
 
 
+BIN = 3.0   # front bins: edges at -2A + 3k, never on a lattice plane
+
+
 def test_window_rule_invariants(ora):
     st, s = state(ora)
     sx, sv, slx = slab()
     n0 = st.n
     before = st.view()
-    x_front = before["x"][before["v"][:, 0] > 0.0075, 0].max()
+    # planes sit at multiples of A/2 from x = 0; those below x = 20 (the last
+    # at 18.225) move at u_p; the bin [15.9, 18.9) is the last shocked one
+    x_front = -2 * A + 9 * BIN
+    assert abs(x_front - 18.9) < 1e-12
     x_max = before["x"][:, 0].max()
     L_behind, L_ahead, gap, depth = 8.0, 30.0, 0.5 * A, 2 * A
-    ora.window_apply(st, 0.015, L_behind, L_ahead, sx, sv, slx, gap, W.MASS_AL, depth)
+    ora.window_apply(st, s.lo[0], s.hi[0], BIN, 0.015, L_behind, L_ahead, sx, sv, slx, gap,
+                     W.MASS_AL, depth)
     after = st.view()
     cut = x_front - L_behind
     kept = before["x"][:, 0] >= cut
@@ -65,8 +76,37 @@ def test_window_needs_a_front(ora):
     st.pis[:] = 0
     sx, sv, slx = slab()
     n0 = st.n
-    ora.window_apply(st, 0.015, 8.0, 30.0, sx, sv, slx, 2.0, W.MASS_AL, 8.1)
+    ora.window_apply(st, s.lo[0], s.hi[0], BIN, 0.015, 8.0, 30.0, sx, sv, slx, 2.0, W.MASS_AL,
+                     8.1)
     assert st.n == n0 and not st.pis[:n0].any()
+
+
+def test_single_fast_atom_is_not_a_front(ora):
+    st, s = state(ora)
+    st.v[:st.n, 0] = s.v[:, 0]          # thermal everywhere, no shocked region
+    st.pis[:] = 0
+    far = int(np.argmax(s.x[:, 0]))
+    st.v[far, 0] = 0.02                 # one atom faster than u_p / 2
+    sx, sv, slx = slab()
+    n0 = st.n
+    ora.window_apply(st, s.lo[0], s.hi[0], BIN, 0.015, 8.0, 30.0, sx, sv, slx, 0.5 * A,
+                     W.MASS_AL, 2 * A)
+    assert st.n == n0
+
+
+def test_no_copy_starts_past_the_box(ora):
+    st, s = state(ora)
+    sx, sv, slx = slab()
+    x_max = s.x[:, 0].max()
+    gap = 0.5 * A
+    x_hi = x_max + gap + 1.5 * slx      # room for one copy only
+    kept_before = st.n
+    ora.window_apply(st, s.lo[0], x_hi, BIN, 0.015, 8.0, 500.0, sx, sv, slx, gap, W.MASS_AL,
+                     2 * A)
+    v = st.view()
+    new = v["ids"] >= kept_before
+    assert new.sum() == sx.shape[0]
+    assert v["x"][new, 0].max() < x_hi
 
 
 def test_window_md_run_counts(ora):
@@ -74,8 +114,8 @@ def test_window_md_run_counts(ora):
     sx, sv, slx = slab()
     wl = W.config3(ncx=12, ncyz=3)
     n0 = st.n
-    nb = ora.md_window(st, s.lo, s.hi, s.periodic, wl.tables, 1.0, 12, 0.3, 5, 0.015, 8.0, 30.0,
-                       sx, sv, slx, 0.5 * A, W.MASS_AL, 2 * A)
+    nb = ora.md_window(st, s.lo, s.hi, s.periodic, wl.tables, 1.0, 12, 0.3, 5, 0.015, BIN, 8.0,
+                       30.0, sx, sv, slx, 0.5 * A, W.MASS_AL, 2 * A)
     assert nb == 3
     v = st.view()
     assert len(np.unique(v["ids"])) == st.n
