@@ -11,6 +11,13 @@ velocities and integration).  Inputs live in HBM and the per-step working set
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config C] [--impl reference]
 
+Other workloads (--config): 0 LJ argon 256 atoms FP64; 1 Al-like EAM 256,000
+atoms FP64; 3 Al-like EAM shock slab (640,000 atoms, x free) with the rigid
+piston and the moving window, mixed; 4 Cu-like EAM cold curve, 64 uneven
+replicas in one batched context, mixed, plus --vjps adjoint calls of the loss
+sum_r E_r + sum_i |F_i - F_ref,i|^2.  --drift-steps S adds an NVE drift
+measurement (mixed S steps, FP64 --drift-fp64-steps steps).
+
 --impl reference times the CPU oracle (the FP64 C program written from the
 paper) on a bounded sample of the same workload on the host cores.
 Multi-GPU (torchrun): replicas only -- every rank runs its own copy of the
@@ -56,16 +63,125 @@ def workload(cfg: int, cells: int = 128):
         return W.config1()
     if cfg == 2:
         return W.config2(n=cells)
+    if cfg == 3:
+        return W.config3()
+    if cfg == 4:
+        return W.config4()
     raise SystemExit(f"config {cfg} is not a bench workload")
 
 
 def algorithmic_bytes_per_atom(wl, prec, n_avg):
-    """Bytes one fused force+integration launch must move per atom:
-    own gather-copy element, list entries + count, x and v read+write, x_ref
-    and cell word read, next gather-copy element written.  Neighbour
-    positions are assumed to come from cache (spatial order)."""
+    """Bytes one force pass with the fused velocity-Verlet update must move
+    per atom.  LJ (one kernel): own gather-copy element, list entries and
+    count, x and v read + write, x_ref and cell word read, next gather-copy
+    element written.  EAM adds the density pass: its own gather-copy element,
+    list and count again, rho_i and F'(rho_i) written, F'(rho_i) read back.
+    Neighbour positions are assumed to come from cache (spatial order)."""
     g = 16 if prec == "mixed" else 32
-    return g + 4 * n_avg + 4 + 48 + 48 + 24 + 4 + g
+    lj = g + 4 * n_avg + 4 + 48 + 48 + 24 + 4 + g
+    if wl.potential == "lj":
+        return lj
+    r = 4 if prec == "mixed" else 8
+    return lj + g + 4 * n_avg + 4 + 8 + r + r
+
+
+# FP64 arithmetic per unordered pair inside rc (one FMA = 2): LJ 23;
+# EAM 22 (density pass: pair vector, r, spline value) + 40 (force pass:
+# pair vector, r, two spline derivatives, force).  A full list evaluates every
+# pair twice; that doubling is overhead, not algorithmic work.
+FLOPS_PER_PAIR = {"lj": 23.0, "eam": 62.0}
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal dense FP64 (no measured figure exists)
+
+
+def pair_count_within_rc(ctx, wl, sample=20000, seed=0):
+    """Mean number of neighbours inside rc per atom, every periodic image
+    counted, from a random sample of atoms (host k-d tree).  Used for the
+    pair-interactions/s figure only."""
+    from scipy.spatial import cKDTree
+    x, _ = ctx.get_state()
+    rng = np.random.default_rng(seed)
+    rc = wl.rc
+    total, counted, off = 0.0, 0, 0
+    n_all = x.shape[0]
+    for s in wl.systems:
+        n = s.n if len(wl.systems) > 1 else n_all
+        xs = x[off:off + n] - s.lo
+        off += n
+        L = s.hi - s.lo
+        per = np.asarray(s.periodic) > 0
+        k = min(n, max(1, int(round(sample * n / n_all))))
+        pick = rng.choice(n, size=k, replace=False)
+        if np.all(~per | (L >= 2.0 * rc + 1e-6)):
+            # periodic dims by the tree's torus; free dims shifted into a box
+            # wide enough that no wrap reaches rc
+            lo_free = xs.min(axis=0) - rc
+            pts = np.where(per, np.mod(xs, L), xs - lo_free)
+            box = np.where(per, L, (xs.max(axis=0) - lo_free) + 2.0 * rc + 1.0)
+            pts = np.minimum(pts, np.nextafter(box, 0))
+            tree = cKDTree(pts, boxsize=box)
+            c = tree.query_ball_point(pts[pick], rc, return_length=True) - 1
+        else:
+            # small periodic box: tile the images explicitly
+            reps = [np.arange(-int(np.ceil(rc / L[d])), int(np.ceil(rc / L[d])) + 1)
+                    if per[d] else np.array([0]) for d in range(3)]
+            shifts = np.array([[i, j, l] for i in reps[0] for j in reps[1] for l in reps[2]],
+                              dtype=np.float64) * L
+            tiled = (xs[None, :, :] + shifts[:, None, :]).reshape(-1, 3)
+            tree = cKDTree(tiled)
+            c = tree.query_ball_point(xs[pick], rc, return_length=True) - 1
+        total += float(np.mean(c)) * n
+        counted += n
+    return total / max(1, counted)
+
+
+def window_setup(ctx, wl):
+    """Rigid piston (initial x < 2a) and the moving window of the shock slab:
+    fresh one-cell FCC slabs (300 K) appended ahead of the front, atoms more
+    than L_behind behind it deleted; the front is located on bins one
+    lattice constant wide."""
+    s = wl.systems[0]
+    a = wl.extra["a"]
+    ncyz = int(round((s.hi[1] - s.lo[1]) / a))
+    sx = W.fcc_lattice(1, ncyz, ncyz, a, (0.0, s.lo[1], s.lo[2]))
+    sv = W.maxwell_velocities(np.random.default_rng(1), np.full(sx.shape[0], wl.eam.mass), 300.0)
+    ctx.set_piston(wl.extra["u_p"], wl.extra["piston"])
+    ctx.set_window(wl.extra["L_behind"], wl.extra["L_ahead"], sx, sv, a, 0.5 * a, wl.eam.mass,
+                   2.0 * a, a)
+
+
+def drift_run(mdk, wl, prec, steps, every=100):
+    """NVE energy drift: E_tot / N sampled every `every` steps on the GPU, the
+    slope of its least-squares line scaled to 10^4 steps (eV/atom)."""
+    ctx = mdk.make_context(wl, precision=prec)
+    ctx.set_thermo(every, capacity=steps // every + 4)
+    ctx.build_neighbors(wl.rc, wl.skin)
+    ctx.step(wl.dt, steps, check=True)
+    th = ctx.thermo()
+    ctx.close()
+    step = th[:, 0, 0]
+    e = (th[:, :, 1] + th[:, :, 2]).sum(axis=1) / th[:, :, 3].sum(axis=1)
+    slope = float(np.polyfit(step, e, 1)[0]) * 1e4
+    return {"precision": prec, "steps": steps, "samples": int(step.shape[0]),
+            "slope_eV_per_atom_per_1e4_steps": slope,
+            "max_minus_min_eV_per_atom": float(e.max() - e.min()),
+            "E_per_atom_first_last": [float(e[0]), float(e[-1])]}
+
+
+def reference_forces(mdk, wl, x):
+    """F_ref of the force-matching loss: the analytic FS-EAM, evaluated through
+    tables at the largest knot count the library takes (7168), far finer than
+    the 5000-knot tables being differentiated."""
+    tab = W.tabulate_fs_eam(wl.eam, nr=7168, nrho=7168)
+    ss = wl.systems
+    c = mdk.Context([q.lo for q in ss], [q.hi for q in ss], [q.periodic for q in ss],
+                    np.concatenate([q.masses for q in ss]), "fp64", n_atoms=[q.n for q in ss])
+    c.set_potential_eam(tab)
+    c.plan(wl.rc, wl.skin)
+    c.set_state(x)
+    c.build_neighbors(wl.rc, wl.skin)
+    _, F, _ = c.compute()
+    c.close()
+    return F
 
 
 class Clocks:
@@ -197,6 +313,10 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--vjps", type=int, default=100, help="adjoint calls timed (config 4)")
+    ap.add_argument("--drift-steps", type=int, default=0,
+                    help="also run an NVE drift measurement of this many steps")
+    ap.add_argument("--drift-fp64-steps", type=int, default=2000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     wl = workload(args.config, args.cells)
@@ -222,9 +342,14 @@ def main():
     _build.build()
     prec = args.precision or wl.precision
     n_atoms = wl.n_atoms
-    ctx = mdk.make_context(wl, precision=prec)
+    windowed = args.config == 3
+    ctx = mdk.make_context(wl, precision=prec,
+                           capacity=int(n_atoms * 1.1) if windowed else None)
     stream = ctx.stream
     n_avg = float(ctx.neighbor_counts().mean())
+    n_rc = pair_count_within_rc(ctx, wl) if rank == 0 else 0.0
+    if windowed:
+        window_setup(ctx, wl)
     tpa, block, _ = ctx.autotune()
 
     # warm-up (untimed; also captures the step graphs)
@@ -233,6 +358,7 @@ def main():
     clocks = Clocks()
     clocks.start()
     builds_before = ctx.counters()[0]
+    n_start = ctx.natoms()      # the moving window changes N between builds
     ctx.profile(False)          # clears the counters; kernels are still counted
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -258,26 +384,78 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = n_atoms * args.steps * world / (ms / 1e3)
+    n_mean = 0.5 * (n_start + ctx.natoms())
+    value = n_mean * args.steps * world / (ms / 1e3)
 
     # dominant kernel: the fused force + integration pass
     hbm, peak_kind = peaks()
+    n_now = ctx.natoms()
     force_ms = prof["force_ms"] / max(1.0, prof["force_passes"])
     bpa = algorithmic_bytes_per_atom(wl, prec, n_avg)
-    achieved = n_atoms * bpa / (force_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None,
-            "kernel": f"k_lj<{prec}> fused force + velocity Verlet",
-            "bytes_per_atom": bpa, "peak_kind": peak_kind,
-            "force_share_of_step": prof["force_ms"] / (ms * prof_steps / args.steps),
-            "rebuild_share_of_step": prof["rebuild_ms"] / (ms * prof_steps / args.steps),
-            "timed_from": f"CUDA events around each of {int(prof['force_passes'])} force "
-                          f"passes of a {prof_steps}-step profiled segment"}
+    gbs = n_now * bpa / (force_ms / 1e3) / 1e9
+    kname = ("k_lj" if wl.potential == "lj" else "k_rho + k_eam") + f"<{prec}>"
+    common = {"kernel": f"{kname} force pass with the fused velocity-Verlet update",
+              "force_share_of_step": prof["force_ms"] / (ms * prof_steps / args.steps),
+              "rebuild_share_of_step": prof["rebuild_ms"] / (ms * prof_steps / args.steps),
+              "timed_from": f"CUDA events around each of {int(prof['force_passes'])} force "
+                            f"passes of a {prof_steps}-step profiled segment"}
+    if prec == "mixed":
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                "frac": gbs / hbm, "traffic": None, "bytes_per_atom": bpa,
+                "peak_kind": peak_kind, **common}
+    else:
+        tflops = n_now * 0.5 * n_rc * FLOPS_PER_PAIR[wl.potential] / (force_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                "flops_per_pair": FLOPS_PER_PAIR[wl.potential],
+                "peak_kind": "GB300 nominal dense FP64",
+                "hbm": {"achieved": gbs, "peak": hbm, "frac": gbs / hbm,
+                        "bytes_per_atom": bpa}, **common}
+
+    # the adjoint of the cold-curve batch: forward pass, loss gradient and VJP
+    vjp = None
+    if args.config == 4 and args.vjps > 0:
+        import torch as _t
+        x_now, _ = ctx.get_state()
+        Fref = _t.tensor(reference_forces(mdk, wl, x_now), device="cuda")
+        R = ctx.n_rep
+        Ed = _t.empty(R, dtype=_t.float64, device="cuda")
+        Fd = _t.empty((n_atoms, 3), dtype=_t.float64, device="cuda")
+        Wd = _t.empty((R, 6), dtype=_t.float64, device="cuda")
+        gE = _t.ones(R, dtype=_t.float64, device="cuda")
+        nk = 2 * wl.tables.nr + wl.tables.nrho
+        dth = _t.empty(nk, dtype=_t.float64, device="cuda")
+
+        def one():
+            ctx.compute_device(Ed, Fd, Wd)
+            gF = 2.0 * (Fd - Fref)          # d/dF of sum |F - F_ref|^2
+            ctx.eam_vjp_device(gE, gF, dth)
+
+        for _ in range(3):
+            one()
+        barrier()
+        ctx.profile(False)
+        v0 = _t.cuda.Event(enable_timing=True)
+        v1 = _t.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        for _ in range(args.vjps):
+            one()
+        v1.record(stream)
+        barrier()
+        vms = v0.elapsed_time(v1) / args.vjps
+        vjp = {"loss": "sum_r E_r + sum_i |F_i - F_ref,i|^2",
+               "F_ref": "analytic FS-EAM through 7168-knot tables",
+               "knots": nk, "ms_per_vjp": vms, "vjps": args.vjps,
+               "vjp_per_s": 1e3 / vms, "atoms": n_atoms,
+               "pair_evaluations_per_s": n_atoms * 0.5 * n_rc / (vms / 1e3),
+               "includes": "forward force pass + loss gradient + mdk_eam_vjp",
+               "gpu_launches": int(ctx.get_profile()["kernels"])}
+        ctx.check()
 
     # end to end through the C ABI with host buffers: upload the state from
     # pinned memory, run the steps, read positions, velocities and energy back
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not windowed:
         xs = torch.empty((n_atoms, 3), dtype=torch.float64, pin_memory=True)
         vs = torch.empty((n_atoms, 3), dtype=torch.float64, pin_memory=True)
         xg, vg = ctx.get_state()
@@ -303,7 +481,10 @@ def main():
     if prec != "fp64" and args.fp64_steps > 0 and rank == 0:
         del ctx
         torch.cuda.empty_cache()
-        c64 = mdk.make_context(wl, precision="fp64")
+        c64 = mdk.make_context(wl, precision="fp64",
+                               capacity=int(n_atoms * 1.1) if windowed else None)
+        if windowed:
+            window_setup(c64, wl)
         c64.step(wl.dt, 3)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -318,6 +499,12 @@ def main():
                 "ms_per_step": fms / args.fp64_steps, "steps": args.fp64_steps}
         del c64
 
+    drift = None
+    if rank == 0 and args.drift_steps > 0:
+        drift = [drift_run(mdk, wl, prec, args.drift_steps)]
+        if prec != "fp64" and args.drift_fp64_steps > 0:
+            drift.append(drift_run(mdk, wl, "fp64", args.drift_fp64_steps))
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(wl)
@@ -330,7 +517,8 @@ def main():
             "dtype": "f32" if prec == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": wl.name, "atoms": n_atoms, "potential": wl.potential,
                        "precision": prec, "dt_fs": wl.dt, "skin_A": wl.skin,
-                       "neighbors_per_atom": n_avg,
+                       "replicas": len(wl.systems),
+                       "neighbors_per_atom": n_avg, "neighbors_within_rc": n_rc,
                        "launch": {"threads_per_atom": tpa, "block": block,
                                   "picked_by": "mdk_autotune"},
                        "rebuild": "when an atom moved > skin/2 since the last build",
@@ -338,14 +526,21 @@ def main():
                        "step_graphs": "two-step CUDA graphs replayed by mdk_step",
                        "l2": "inputs larger than L2 (~4 GB touched per step); no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "pair_interactions_per_s": value * n_avg / 2.0,
+            "pair_interactions_per_s": value * n_rc / 2.0,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": ck,
             "fp64_path": fp64,
+            "vjp": vjp,
+            "drift": drift,
         }
+        if windowed:
+            line["config"]["piston_u_p_A_per_fs"] = wl.extra["u_p"]
+            line["config"]["window"] = {"L_behind": wl.extra["L_behind"],
+                                        "L_ahead": wl.extra["L_ahead"],
+                                        "atoms_at_end": n_now}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -259,12 +259,17 @@ int mdk_set_piston(mdk_ctx *ctx, double u_p, const uint8_t *is_piston);
  * simulation": atoms are inserted ahead of the shock from a prepared fresh
  * sample and deleted behind it).  Applied at every list build after this
  * call, on the device, in this order:
- *   x_front = largest x of an atom with v_x > u_p/2 (none: nothing happens);
+ *   the front: the box along x is cut into bins of width front_bin from
+ *   box_lo[0] (atoms outside go to the end bins); a bin is shocked when the
+ *   mean v_x of its atoms exceeds u_p/2 (decided exactly on velocities
+ *   rounded to multiples of 2^-40 Angstrom/fs); x_front = upper edge of the
+ *   last shocked bin (none: nothing happens);
  *   atoms with x < x_front - L_behind are deleted;
  *   while the leading edge x_max < x_front + L_ahead, copies of the fresh
  *   slab are appended: k = ceil((x_front + L_ahead - x_max)/slab_lx) copies,
- *   copy c shifted by ((x_max + slab_gap) + c slab_lx, 0, 0), velocities
- *   slab_v, mass slab_mass, new ids counting up from N;
+ *   at most floor(((box_hi[0] - x_max) - slab_gap)/slab_lx) of them (none
+ *   starts past the box), copy c shifted by ((x_max + slab_gap) + c slab_lx,
+ *   0, 0), velocities slab_v, mass slab_mass, new ids counting up from N;
  *   atoms with x < x_min + piston_depth (x_min of the atoms left) join the
  *   piston.
  *   slab_x, slab_v : host [n_slab][3] positions (x in [0, slab_lx)) and
@@ -272,11 +277,12 @@ int mdk_set_piston(mdk_ctx *ctx, double u_p, const uint8_t *is_piston);
  * The atom count changes: reserve room with mdk_set_capacity (appends that
  * do not fit raise MDK_ERR_NEIGH_OVERFLOW's status bit).  Once a window is
  * set, per-atom outputs come in ascending atom-id order (mdk_get_ids).
- * Single-system contexts only.  Takes effect at the next list build.
+ * Single-system contexts with a free (non-periodic) x only; front_bin > 0
+ * with at most 2^24 bins over the box.  Takes effect at the next list build.
  */
 int mdk_set_window(mdk_ctx *ctx, double L_behind, double L_ahead, const double *slab_x,
                    const double *slab_v, int64_t n_slab, double slab_lx, double slab_gap,
-                   double slab_mass, double piston_depth);
+                   double slab_mass, double piston_depth, double front_bin);
 
 /* Ids of the atoms present, ascending (the order of every per-atom output). */
 int mdk_get_ids(mdk_ctx *ctx, int64_t *ids);

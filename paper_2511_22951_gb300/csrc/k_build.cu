@@ -45,7 +45,6 @@ __global__ void k_pre(Sys s, int count_step) {
   st->win_active = (s.win_on && count_step && st->rebuild) ? 1 : 0;
   st->win_cut = -INFINITY;
   if (st->win_active) {
-    st->key_front = dkey(-INFINITY);
     st->key_xmax = dkey(-INFINITY);
     st->key_xmin = dkey(INFINITY);
     st->win_cut = -INFINITY;
@@ -54,39 +53,77 @@ __global__ void k_pre(Sys s, int count_step) {
 }
 
 // ---- moving window (Sec. "Moving window simulation"; rules in the oracle) ----
-// shock front = largest x of an atom with v_x > u_p/2; leading edge = max x
+// Front: bins of width front_bin along x; a bin is shocked when its mean v_x
+// exceeds u_p / 2, decided exactly on velocities rounded to multiples of
+// 2^-40 Angstrom/fs (integer sums, so the order of the atomics is irrelevant).
+// Leading edge = max x.
+constexpr double kTwo40 = 1099511627776.0;
+constexpr int kFbinSmem = 2048;  // bins privatised in shared memory up to this count
+
+__device__ __forceinline__ int front_bin_of(const Sys &s, double x) {
+  const double u = floor(__ddiv_rn(__dsub_rn(x, s.win_xlo), s.front_bin));
+  return u < 0.0 ? 0 : (u > (double)(s.n_fbins - 1) ? s.n_fbins - 1 : (int)u);
+}
+
 __global__ void __launch_bounds__(kBlk) k_win_stats(Sys s) {
+  __shared__ long long sh[2 * kFbinSmem];
   if (!flag_on(s) || !s.st->win_active) return;
+  const bool priv = s.n_fbins <= kFbinSmem;
+  if (priv)
+    for (int q = threadIdx.x; q < 2 * s.n_fbins; q += blockDim.x) sh[q] = 0;
+  __syncthreads();
+  long long *hist = priv ? sh : s.fbin;
   const int N = s.st->N;
-  long long front = dkey(-INFINITY), xmax = dkey(-INFINITY);
+  long long xmax = dkey(-INFINITY);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const double x = s.x[i];
+    const double x = s.x[i], vx = s.v[i];
     const long long k = dkey(x);
-    if (s.v[i] > 0.5 * s.u_p && k > front) front = k;
     if (k > xmax) xmax = k;
+    if (!isfinite(x) || !isfinite(vx)) continue;
+    const int b = front_bin_of(s, x);
+    atomicAdd((unsigned long long *)&hist[2 * b], (unsigned long long)__double2ll_rn(vx * kTwo40));
+    atomicAdd((unsigned long long *)&hist[2 * b + 1], 1ull);
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    front = max(front, __shfl_xor_sync(0xffffffffu, front, o));
-    xmax = max(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&s.st->key_front, front);
-    atomicMax(&s.st->key_xmax, xmax);
+  for (int o = 16; o > 0; o >>= 1) xmax = max(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&s.st->key_xmax, xmax);
+  if (priv) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * s.n_fbins; q += blockDim.x)
+      if (sh[q] != 0) atomicAdd((unsigned long long *)&s.fbin[q], (unsigned long long)sh[q]);
   }
 }
 
-// cut, number of fresh-slab copies to append (capped by the capacity)
-__global__ void k_win_plan(Sys s) {
-  if (threadIdx.x != 0 || blockIdx.x != 0 || !flag_on(s) || !s.st->win_active) return;
+// Front, cut and the number of fresh-slab copies to append (capped by the
+// box along x and by the capacity).  One block; the bin sums are cleared
+// for the next build.
+__global__ void __launch_bounds__(kBlk) k_win_plan(Sys s) {
+  __shared__ int best;
+  if (!flag_on(s) || !s.st->win_active) return;
+  if (threadIdx.x == 0) best = -1;
+  __syncthreads();
+  const long long q_up = __double2ll_rn(s.u_p * kTwo40);
+  int mine = -1;
+  for (int b = threadIdx.x; b < s.n_fbins; b += blockDim.x) {
+    const long long sum = s.fbin[2 * b], cnt = s.fbin[2 * b + 1];
+    if (cnt > 0 && 2 * sum > cnt * q_up) mine = b;
+  }
+  if (mine >= 0) atomicMax(&best, mine);
+  __syncthreads();
+  for (int q = threadIdx.x; q < 2 * s.n_fbins; q += blockDim.x) s.fbin[q] = 0;
+  if (threadIdx.x != 0) return;
   DevStatus *st = s.st;
-  const double front = dkey_inv(st->key_front), xmax = dkey_inv(st->key_xmax);
+  const double xmax = dkey_inv(st->key_xmax);
   st->win_n_old = st->N;
   st->win_insert = 0;
   st->win_cut = -INFINITY;
-  if (!(front > -INFINITY)) return;
+  if (best < 0) return;
+  const double front = __dadd_rn(s.win_xlo, __dmul_rn((double)(best + 1), s.front_bin));
   st->win_cut = front - s.L_behind;
   const double need = front + s.L_ahead - xmax;
   long long copies = need > 0.0 ? (long long)ceil(need / s.slab_lx) : 0;
+  const double fit = floor(__ddiv_rn(__dsub_rn(__dsub_rn(s.win_xhi, xmax), s.slab_gap), s.slab_lx));
+  const long long fit_n = fit > 0.0 ? (long long)fit : 0;
+  if (copies > fit_n) copies = fit_n;
   long long add = copies * (long long)s.n_slab;
   const long long room = (long long)s.N_cap - st->N;
   if (add > room) {
@@ -546,7 +583,7 @@ void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, 
   k_pre<<<1, 32, 0, st>>>(s, count_step);
   if (s.win_on) {
     k_win_stats<<<gN, kBlk, 0, st>>>(s);
-    k_win_plan<<<1, 32, 0, st>>>(s);
+    k_win_plan<<<1, kBlk, 0, st>>>(s);
     k_win_insert<<<gN, kBlk, 0, st>>>(s);
   }
   k_bin<<<gN, kBlk, 0, st>>>(s);

@@ -75,6 +75,10 @@ struct mdk_ctx {
   std::vector<double> win_slab;  // [n][6]
   int64_t win_slab_cap = 0;      // slab atoms the workspace has room for
   double *win_slab_dev = nullptr;
+  double win_front_bin = 1.0;
+  int win_nbins = 1;             // front bins over the box along x
+  int win_nbins_cap = 0;         // bins the workspace has room for
+  long long *win_fbin = nullptr;
   // measurement (mdk_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -141,6 +145,8 @@ size_t layout(mdk_ctx *c, char *base) {
   s.scan_part = cv.take<int32_t>(scan_blocks_for(c->n_cells + 1));
   c->win_slab_cap = (int64_t)(c->win_slab.size() / 6);
   c->win_slab_dev = cv.take<double>(c->win_slab.size());
+  c->win_nbins_cap = c->win_nbins;
+  c->win_fbin = cv.take<long long>(2 * (size_t)c->win_nbins);
   s.cell_of = cv.take<int32_t>(Nc);
   s.order = cv.take<int32_t>(Nc);
   s.grid = cv.take<Grid>(c->n_rep);
@@ -269,6 +275,11 @@ void fill_sys_params(mdk_ctx *c) {
   s.piston_depth = c->win_depth;
   s.slab = c->win_slab_dev;
   s.slab_info = c->win_info;
+  s.win_xlo = c->lo[0];
+  s.win_xhi = c->hi[0];
+  s.front_bin = c->win_front_bin;
+  s.n_fbins = c->win_nbins;
+  s.fbin = c->win_fbin;
 }
 
 int read_status(mdk_ctx *c, DevStatus *out) {
@@ -724,6 +735,7 @@ int mdk_set_workspace(mdk_ctx *c, void *dev_ptr, size_t bytes) {
   Sys &s = c->sys;
   MDK_CK(cudaMemsetAsync(s.st, 0, sizeof(DevStatus), c->stream));
   MDK_CK(cudaMemsetAsync(s.cell_cnt, 0, sizeof(int32_t) * (c->n_cells + 1), c->stream));
+  MDK_CK(cudaMemsetAsync(c->win_fbin, 0, sizeof(long long) * 2 * c->win_nbins, c->stream));
   if (!c->win_slab.empty())
     MDK_CK(cudaMemcpyAsync(c->win_slab_dev, c->win_slab.data(), sizeof(double) * c->win_slab.size(),
                            cudaMemcpyHostToDevice, c->stream));
@@ -1280,11 +1292,14 @@ int mdk_get_profile(mdk_ctx *c, double *out) {
 
 int mdk_set_window(mdk_ctx *c, double L_behind, double L_ahead, const double *slab_x,
                    const double *slab_v, int64_t n_slab, double slab_lx, double slab_gap,
-                   double slab_mass, double piston_depth) {
+                   double slab_mass, double piston_depth, double front_bin) {
   if (check_ctx(c) || c->n_rep != 1 || !slab_x || !slab_v || n_slab < 1 ||
       n_slab >= ((int64_t)1 << 26) || !(slab_lx > 0.0) || !(L_behind >= 0.0) ||
-      !(L_ahead >= 0.0) || !isfinite(slab_gap) || !(slab_mass > 0.0) || !(piston_depth >= 0.0))
+      !(L_ahead >= 0.0) || !isfinite(slab_gap) || !(slab_mass > 0.0) || !(piston_depth >= 0.0) ||
+      !(front_bin > 0.0) || c->per[0])
     return MDK_ERR_BAD_ARG;
+  const double nb = ceil((c->hi[0] - c->lo[0]) / front_bin);
+  if (!(nb <= (double)(1 << 24))) return MDK_ERR_BAD_ARG;
   int t = 0;
   while (t < c->n_types && c->type_mass[t] != slab_mass) ++t;
   if (t == c->n_types) {
@@ -1298,6 +1313,8 @@ int mdk_set_window(mdk_ctx *c, double L_behind, double L_ahead, const double *sl
   c->win_gap = slab_gap;
   c->win_depth = piston_depth;
   c->win_info = (uint32_t)t;
+  c->win_front_bin = front_bin;
+  c->win_nbins = std::max(1, (int)nb);
   c->win_slab.assign((size_t)n_slab * 6, 0.0);
   for (int64_t q = 0; q < n_slab; ++q)
     for (int k = 0; k < 3; ++k) {
@@ -1305,10 +1322,11 @@ int mdk_set_window(mdk_ctx *c, double L_behind, double L_ahead, const double *sl
       c->win_slab[(size_t)q * 6 + 3 + k] = slab_v[3 * q + k];
     }
   if (!c->ws_ok) return MDK_OK;
-  if (n_slab > c->win_slab_cap) {  // the slab area of the workspace is too small
-    c->need_ws = true;
+  if (n_slab > c->win_slab_cap || c->win_nbins > c->win_nbins_cap) {
+    c->need_ws = true;  // the slab or bin area of the workspace is too small
     return MDK_ERR_WORKSPACE;
   }
+  MDK_CK(cudaMemsetAsync(c->win_fbin, 0, sizeof(long long) * 2 * c->win_nbins, c->stream));
   MDK_CK(cudaMemcpyAsync(c->win_slab_dev, c->win_slab.data(), sizeof(double) * c->win_slab.size(),
                          cudaMemcpyHostToDevice, c->stream));
   fill_sys_params(c);

@@ -50,7 +50,7 @@ struct DevStatus {
   int since_build;       // steps since the last build
   int next_id;           // id of the next atom a moving window appends
   // moving window (order-preserving integer keys of doubles, for atomics)
-  long long key_front, key_xmax, key_xmin;
+  long long key_xmax, key_xmin;
   double win_cut;        // atoms with x below are deleted at this build
   double win_x0;         // x offset of the first appended slab copy
   int win_insert;        // atoms appended at this build
@@ -111,6 +111,10 @@ struct Sys {
   double L_behind, L_ahead, slab_lx, slab_gap, piston_depth;
   const double *slab;             // fresh slab: [n_slab][6] = x, y, z, vx, vy, vz
   uint32_t slab_info;             // info word of appended atoms
+  double win_xlo, win_xhi;        // the box along x
+  double front_bin;               // width of the bins that locate the front
+  int n_fbins;                    // bins over [win_xlo, win_xhi)
+  long long *fbin;                // [2 n_fbins]: sum of q(v_x), atom count per bin
 };
 
 // order-preserving map of a double onto a signed 64-bit key (for atomicMax/Min)

@@ -61,7 +61,7 @@ SIGNATURES = {
     "mdk_get_thermo": [_P, _P, _I, ctypes.POINTER(_I)],
     "mdk_get_counters": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "mdk_set_piston": [_P, _D, _P],
-    "mdk_set_window": [_P, _D, _D, _P, _P, _I64, _D, _D, _D, _D],
+    "mdk_set_window": [_P, _D, _D, _P, _P, _I64, _D, _D, _D, _D, _D],
     "mdk_get_ids": [_P, _P],
     "mdk_window_counts": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "mdk_profiles": [_P, _I, _D, _D, _I, _D, _P, _I],
@@ -384,16 +384,17 @@ class Context:
         return dict(zip(keys, out.tolist()))
 
     def set_window(self, L_behind, L_ahead, slab_x, slab_v, slab_lx, slab_gap, slab_mass,
-                   piston_depth):
+                   piston_depth, front_bin):
         sx = _host_f64(slab_x, (-1, 3))
         sv = _host_f64(slab_v, (-1, 3))
-        r = self.lib.mdk_set_window(self.h, L_behind, L_ahead, _ptr(sx), _ptr(sv), sx.shape[0],
-                                    slab_lx, slab_gap, slab_mass, piston_depth)
+        args = (L_behind, L_ahead, _ptr(sx), _ptr(sv), sx.shape[0], slab_lx, slab_gap,
+                slab_mass, piston_depth, front_bin)
+        r = self.lib.mdk_set_window(self.h, *args)
         if r == MDK_ERR_WORKSPACE:
             self.alloc_workspace()
-            r = self.lib.mdk_set_window(self.h, L_behind, L_ahead, _ptr(sx), _ptr(sv),
-                                        sx.shape[0], slab_lx, slab_gap, slab_mass, piston_depth)
+            r = self.lib.mdk_set_window(self.h, *args)
         _check(r, "mdk_set_window")
+        self.version += 1
 
     def ids(self):
         n = self.natoms()
@@ -412,12 +413,13 @@ class Context:
         _check(self.lib.mdk_set_piston(self.h, u_p, _ptr(f)), "mdk_set_piston")
 
 
-def make_context(wl, precision=None, stream=None, rebuild_every=0, max_neighbors=0):
+def make_context(wl, precision=None, stream=None, rebuild_every=0, max_neighbors=0,
+                 capacity=None):
     """Context for a workloads.Workload: potential, plan, workspace, state, lists."""
     prec = precision or wl.precision
     if len(wl.systems) == 1:
         s = wl.systems[0]
-        ctx = Context(s.lo, s.hi, s.periodic, s.masses, prec, stream)
+        ctx = Context(s.lo, s.hi, s.periodic, s.masses, prec, stream, capacity=capacity)
     else:
         ss = wl.systems
         ctx = Context([q.lo for q in ss], [q.hi for q in ss], [q.periodic for q in ss],

@@ -367,14 +367,14 @@ def test_window_matches_oracle(mdk, ora):
     ctx.set_state(s.x, v)
     ctx.build_neighbors(wl.tables.rc, 0.3)
     ctx.set_piston(0.015, pis)
-    ctx.set_window(Lb, La, sx, sv, slx, gap, W.MASS_AL, depth)
+    ctx.set_window(Lb, La, sx, sv, slx, gap, W.MASS_AL, depth, 3.0)
     ctx.step(0.5, 12)
     xg, vg = ctx.get_state()
     ids = ctx.ids()
     ins, dele = ctx.window_counts()
     st = ora.WindowState(s.x, v, s.masses, pis, cap)
-    ora.md_window(st, s.lo, s.hi, s.periodic, wl.tables, 0.5, 12, 0.3, 5, 0.015, Lb, La, sx, sv,
-                  slx, gap, W.MASS_AL, depth)
+    ora.md_window(st, s.lo, s.hi, s.periodic, wl.tables, 0.5, 12, 0.3, 5, 0.015, 3.0, Lb, La, sx,
+                  sv, slx, gap, W.MASS_AL, depth)
     o = st.view()
     order = np.argsort(o["ids"])
     np.testing.assert_array_equal(ids, o["ids"][order])
