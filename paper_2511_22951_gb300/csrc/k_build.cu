@@ -36,7 +36,7 @@ __device__ __forceinline__ bool flag_on(const Sys &s) {
   return *(volatile int *)&s.st->rebuild != 0;
 }
 
-__global__ void k_pre(Sys s, int count_step) {
+__global__ void k_pre(Sys s, int count_step, int use_cond, cudaGraphConditionalHandle h) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   DevStatus *st = s.st;
   if (count_step) st->since_build += 1;
@@ -50,6 +50,7 @@ __global__ void k_pre(Sys s, int count_step) {
     st->win_cut = -INFINITY;
     st->win_insert = 0;
   }
+  if (use_cond) cudaGraphSetConditional(h, st->rebuild ? 1u : 0u);
 }
 
 // ---- moving window (Sec. "Moving window simulation"; rules in the oracle) ----
@@ -535,12 +536,13 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
   }
 }
 
-__global__ void k_finish(Sys s) {
+__global__ void k_finish(Sys s, int from_graph) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   DevStatus *st = s.st;
   if (st->rebuild) {
     st->rebuild = 0;
     st->n_builds += 1;
+    if (from_graph) st->n_graph_builds += 1;
     st->since_build = 0;
   }
 }
@@ -570,7 +572,15 @@ int persistent_blocks(const void *fn, int threads, int smem) {
   return sms * occ;
 }
 
-void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, cudaStream_t st) {
+void launch_rebuild_head(const Sys &s, int count_step, cudaGraphConditionalHandle h,
+                         cudaStream_t st) {
+  k_pre<<<1, 32, 0, st>>>(s, count_step, 1, h);
+}
+
+int rebuild_chain_kernels(const Sys &s) { return 11 + (s.win_on ? 4 : 0); }
+
+int launch_rebuild_body(const Sys &s, int target_pg, int precision, int from_graph,
+                        cudaStream_t st) {
   static int g_atom = 0, g_build = 0, g_cells = 0;
   if (g_atom == 0) {
     g_atom = persistent_blocks((const void *)k_bin, kBlk, 0);
@@ -580,7 +590,6 @@ void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, 
   const int gN = std::min(g_atom, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
   const int gC = std::min(g_cells, nblk(s.n_cells, kBlk));
   const int gB = std::min(g_build, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
-  k_pre<<<1, 32, 0, st>>>(s, count_step);
   if (s.win_on) {
     k_win_stats<<<gN, kBlk, 0, st>>>(s);
     k_win_plan<<<1, kBlk, 0, st>>>(s);
@@ -599,7 +608,13 @@ void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, 
   k_copyback<<<gN, kBlk, 0, st>>>(s);
   if (s.win_on) k_win_trim<<<1, 32, 0, st>>>(s);
   k_build<<<gB, kBlk, 0, st>>>(s);
-  k_finish<<<1, 32, 0, st>>>(s);
+  k_finish<<<1, 32, 0, st>>>(s, from_graph);
+  return rebuild_chain_kernels(s) - 1;
+}
+
+void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, cudaStream_t st) {
+  k_pre<<<1, 32, 0, st>>>(s, count_step, 0, 0);
+  launch_rebuild_body(s, target_pg, precision, 0, st);
 }
 
 int scan_blocks_for(int n_buckets) { return (n_buckets + kScanTile - 1) / kScanTile; }

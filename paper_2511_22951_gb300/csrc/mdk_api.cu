@@ -66,7 +66,10 @@ struct mdk_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   uint64_t gkey[2] = {0, 0};
-  int64_t graph_kernels = 0;  // kernels in one graph
+  cudaStream_t body_stream = nullptr;  // captures the conditional rebuild bodies
+  int64_t graph_kernels = 0;  // kernels of one graph that run at every replay
+  int64_t body_kernels = 0;   // kernels of one conditional rebuild body
+  long long graph_builds0 = 0;  // device count of in-graph builds at mdk_profile
   // moving window
   bool win_on = false;
   double win_L_behind = 0.0, win_L_ahead = 0.0, win_slab_lx = 0.0, win_gap = 0.0,
@@ -371,10 +374,9 @@ int force_pass(mdk_ctx *c, Mode mode, int energy, double dt) {
   });
 }
 
-constexpr int kChainKernels = 11;
 
 int rebuild_chain(mdk_ctx *c, int count_step) {
-  return timed(c, c->ev_chain, kChainKernels, [&] {
+  return timed(c, c->ev_chain, rebuild_chain_kernels(c->sys), [&] {
     launch_rebuild(c->sys, c->cur, c->precision, count_step, c->stream);
   });
 }
@@ -481,10 +483,44 @@ uint64_t graph_key(const mdk_ctx *c, double dt) {
   return h;
 }
 
+// The rebuild chain of a captured step: the head kernel (k_pre) decides and
+// sets the value of an IF conditional node whose body holds the rest of the
+// chain, so a step without a rebuild runs two kernels, not the whole chain.
+int capture_conditional_chain(mdk_ctx *c) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  MDK_CK(cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle h;
+  MDK_CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+  launch_rebuild_head(c->sys, 1, h, c->cap_stream);
+  c->launches += 1;
+  MDK_CK(cudaPeekAtLastError());
+  MDK_CK(cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  MDK_CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+  MDK_CK(cudaStreamUpdateCaptureDependencies(c->cap_stream, &node, nullptr, 1,
+                                             cudaStreamSetCaptureDependencies));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  MDK_CK(cudaStreamBeginCaptureToGraph(c->body_stream, body, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal));
+  c->body_kernels = launch_rebuild_body(c->sys, c->cur, c->precision, 1, c->body_stream);
+  const cudaError_t e = cudaPeekAtLastError();
+  cudaGraph_t out = nullptr;
+  MDK_CK(cudaStreamEndCapture(c->body_stream, &out));
+  return e == cudaSuccess ? MDK_OK : MDK_ERR_CUDA;
+}
+
 // Capture two plain steps (force pass + rebuild chain, twice) starting from
 // gather-copy parity `parity`; the graph ends at the same parity.
 int capture_two_steps(mdk_ctx *c, int parity, double dt, uint64_t key) {
   if (!c->cap_stream) MDK_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  if (!c->body_stream) MDK_CK(cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking));
   const cudaStream_t keep_stream = c->stream;
   const int keep_cur = c->cur;
   const bool keep_prof = c->prof;
@@ -497,7 +533,7 @@ int capture_two_steps(mdk_ctx *c, int parity, double dt, uint64_t key) {
   for (int h = 0; h < 2 && !r; ++h) {
     r = force_pass(c, kStep, 0, dt);
     c->cur ^= 1;
-    if (!r) r = rebuild_chain(c, 1);
+    if (!r) r = capture_conditional_chain(c);
   }
   c->stream = keep_stream;
   c->cur = keep_cur;
@@ -603,6 +639,7 @@ int mdk_destroy(mdk_ctx *c) {
   for (int q = 0; q < 2; ++q)
     if (c->gexec[q]) cudaGraphExecDestroy(c->gexec[q]);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->body_stream) cudaStreamDestroy(c->body_stream);
   delete c;
   return MDK_OK;
 }
@@ -1253,7 +1290,12 @@ int mdk_set_launch(mdk_ctx *c, int tpa, int block) {
 
 int mdk_profile(mdk_ctx *c, int enable) {
   if (check_ctx(c)) return MDK_ERR_BAD_ARG;
-  if (c->ws_ok) MDK_CK(cudaStreamSynchronize(c->stream));
+  if (c->ws_ok) {
+    DevStatus st;
+    int r = read_status(c, &st);
+    if (r) return r;
+    c->graph_builds0 = st.n_graph_builds;
+  }
   c->prof = enable != 0;
   c->ev_used = 0;
   c->ev_force.clear();
@@ -1283,7 +1325,10 @@ int mdk_get_profile(mdk_ctx *c, double *out) {
   out[1] = (double)c->ev_force.size();
   out[2] = total(c->ev_chain);
   out[3] = (double)c->ev_chain.size();
-  out[4] = (double)c->launches;
+  // kernels launched: those enqueued directly, those of every graph replay,
+  // and the rebuild bodies that the graphs' conditional nodes ran
+  out[4] = (double)c->launches + (double)c->body_kernels * (double)(st.n_graph_builds -
+                                                                     c->graph_builds0);
   out[5] = (double)st.n_builds;
   out[6] = total(c->ev_kick);
   out[7] = (double)c->ev_kick.size();

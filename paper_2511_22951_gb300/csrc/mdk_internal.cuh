@@ -46,6 +46,7 @@ struct DevStatus {
   unsigned bits;         // kSt* raised since the host last cleared them
   int max_nnbr;          // longest list seen at a build
   long long n_builds;
+  long long n_graph_builds;  // builds run inside a captured step's conditional node
   long long n_steps;
   int since_build;       // steps since the last build
   int next_id;           // id of the next atom a moving window appends
@@ -249,6 +250,14 @@ struct StepArgs {
 };
 
 void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, cudaStream_t st);
+// The same chain in two parts for a captured step: the head decides whether
+// to rebuild and sets the conditional node's value; the body (run by that
+// node only when the value is 1) rebuilds.  Returns the kernels of the body.
+void launch_rebuild_head(const Sys &s, int count_step, cudaGraphConditionalHandle h,
+                         cudaStream_t st);
+int launch_rebuild_body(const Sys &s, int target_pg, int precision, int from_graph,
+                        cudaStream_t st);
+int rebuild_chain_kernels(const Sys &s);
 void launch_set_piston(const Sys &s, const uint8_t *flags, int64_t n_flags, cudaStream_t st);
 int scan_blocks_for(int n_cells);
 void launch_set_rebuild_flag(const Sys &s, cudaStream_t st);
