@@ -18,13 +18,18 @@
 // Pair distances are recomputed from the gather copy and the Verlet list (no
 // stored r_ij).  Pass c: one thread per atom sums c_i (FP32 pair arithmetic in
 // the mixed path, Kahan-compensated), then, once per atom in FP64, scatters
-// the F-knot weights and stores lambda_i.  Pass pair: one thread per atom
-// scatters the phi- and rho-knot weights of its pairs.  Both passes run on a
-// persistent grid and scatter into FP64 histograms privatised in shared
-// memory (160 KB for 5000 knots per table), which each block adds to the
-// global histograms when it is done; the gradients are FP64 throughout.
-// The order of the shared-memory atomics is not fixed, so the result is
-// reproducible to FP64 rounding, not bit for bit.
+// the F-knot weights (FP64 atomics) and stores lambda_i.  Pass pair: one
+// thread per atom scatters the phi- and rho-knot weights of its pairs into
+// histograms privatised in shared memory (160 KB for 5000 knots per table)
+// that each block adds to the global ones when it is done.  Those sums are
+// 64-bit fixed point: every contribution is bounded by B = max(|gE|/2,
+// |lambda|) + 1.5 |gF| max(1, 2|F'|) / h (Hermite weights are at most 1,
+// their u-derivatives at most 1.5 in magnitude), a knot takes at most
+// P = N * (list capacity) of them, and the scale S = 2^floor(61 -
+// log2(P B)) keeps every sum below 2^62 while resolving 1/S = P B 2^-61.
+// Integer adds are native shared-memory atomics and do not depend on their
+// order, so these sums are bit-reproducible; the F-knot sums (FP64 atomics,
+// four per atom) are reproducible to rounding.
 #include "k_pair.cuh"
 
 namespace mdk {
@@ -33,6 +38,15 @@ namespace {
 using namespace pair;
 
 constexpr int kAdjBlock = 512;
+
+// atomic max of a non-negative double through its bit pattern (monotone there)
+__device__ __forceinline__ void max_bits(long long *slot, double v) {
+  if (v > 0.0) atomicMax(slot, __double_as_longlong(v));
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 
 // Hermite weights at t of the value (w) and of the u-derivative (dw) for the
 // coefficients (y_k, M_k, y_{k+1}, M_{k+1}) of one interval
@@ -58,12 +72,54 @@ __device__ __forceinline__ void scatter(double2 *acc, int k, double a0, double a
   atomicAdd(&acc[k + 1].y, a3);
 }
 
+// A 64-bit fixed-point accumulator in shared memory as two 32-bit words, so
+// that every update is a native 32-bit atomic: the low word takes the low 32
+// bits, the high word the high 32 bits plus the carry out of the low word
+// (sums are exact modulo 2^64, whatever the order).
+struct Fx64 {
+  unsigned *lo;
+  int *hi;
+  __device__ __forceinline__ void add(int slot, long long v) const {
+    const unsigned vl = (unsigned)v;
+    int vh = (int)(v >> 32);
+    const unsigned old = atomicAdd(lo + slot, vl);
+    if (old + vl < old) vh += 1;
+    if (vh != 0) atomicAdd(hi + slot, vh);
+  }
+  __device__ __forceinline__ long long get(int slot) const {
+    return (long long)(((unsigned long long)(unsigned)hi[slot] << 32) | lo[slot]);
+  }
+};
+
+// value * S rounded to an integer, in the pair precision (S is a power of
+// two, so the product is exact; FP64 work per pair is what the FP32 pair
+// arithmetic of the mixed path avoids on GB300's slow FP64 pipe)
+__device__ __forceinline__ long long to_fx(float v, float S) { return __float2ll_rn(v * S); }
+__device__ __forceinline__ long long to_fx(double v, double S) { return __double2ll_rn(v * S); }
+
+// fixed-point add of cv * (value weights) + cd * (derivative weights) to the
+// slots (y_k, M_k, y_{k+1}, M_{k+1}) = 2k .. 2k + 3
+template <class R>
+__device__ __forceinline__ void scatter_fx(const Fx64 &h, int k, R S, R a0, R a1, R a2, R a3) {
+  h.add(2 * k, to_fx(a0, S));
+  h.add(2 * k + 1, to_fx(a1, S));
+  h.add(2 * k + 2, to_fx(a2, S));
+  h.add(2 * k + 3, to_fx(a3, S));
+}
+
 // add a block's shared histogram to the global one (zeros skipped)
 __device__ __forceinline__ void flush(const double2 *sh, double2 *gl, int n) {
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     const double2 v = sh[q];
     if (v.x != 0.0) atomicAdd(&gl[q].x, v.x);
     if (v.y != 0.0) atomicAdd(&gl[q].y, v.y);
+  }
+}
+__device__ __forceinline__ void flush(const Fx64 &sh, longlong2 *gl, int n) {
+  unsigned long long *p = reinterpret_cast<unsigned long long *>(gl);
+  for (int q = threadIdx.x; q < 2 * n; q += blockDim.x) {
+    const long long v = sh.get(q);
+    if (v != 0) atomicAdd(p + q, (unsigned long long)v);
   }
 }
 
@@ -74,15 +130,24 @@ __global__ void __launch_bounds__(256) k_adj_load(Sys s, const double *gF, AdjAr
   using V = typename GP::V;
   const int N = s.st->N;
   const int i = blockIdx.x * 256 + threadIdx.x;
-  if (i >= N) return;
-  const size_t o = (size_t)s.id[i];
   double gx = 0.0, gy = 0.0, gz = 0.0;
-  if (gF) {
-    gx = gF[3 * o];
-    gy = gF[3 * o + 1];
-    gz = gF[3 * o + 2];
+  if (i < N) {
+    const size_t o = (size_t)s.id[i];
+    if (gF) {
+      gx = gF[3 * o];
+      gy = gF[3 * o + 1];
+      gz = gF[3 * o + 2];
+    }
+    GP::st((V *)a.gint + i, gx, gy, gz, 0u);
   }
-  GP::st((V *)a.gint + i, gx, gy, gz, 0u);
+  // bounds for the fixed-point scale: max |gF_i| and (one thread) max |gE_r|
+  const double m = warp_max(sqrt(gx * gx + gy * gy + gz * gz));
+  if ((threadIdx.x & 31) == 0) max_bits(&a.aux[1], m);
+  if (i == 0) {
+    double e = 0.0;
+    for (int r = 0; r < s.n_rep; ++r) e = fmax(e, fabs(a.gE[r]));
+    max_bits(&a.aux[0], e);
+  }
 }
 
 // ---- pass c: c_i, the F-knot weights and lambda_i --------------------------------------
@@ -110,6 +175,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_c(Sys s, EAMParams ep, AdjArg
   const R rc2 = sizeof(R) == 8 ? (R)ep.rc2 : (R)ep.rc2f;
   const R inv_dr = sizeof(R) == 8 ? (R)ep.inv_dr : (R)ep.inv_drf;
   const int kmax = ep.nr - 2;
+  double lam_max = 0.0, fp_max = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const V pi = GP::ld(pg + i);
     const uint32_t inf = GP::info(pi);
@@ -182,11 +248,35 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_c(Sys s, EAMParams ep, AdjArg
       lam = gE * Fp + ci * Fpp;
     }
     a.lam[i] = lam;
+    lam_max = fmax(lam_max, fabs(lam));
+    fp_max = fmax(fp_max, fabs((double)((const R *)s.fp)[i]));
+  }
+  lam_max = warp_max(lam_max);
+  fp_max = warp_max(fp_max);
+  if ((threadIdx.x & 31) == 0) {
+    max_bits(&a.aux[2], lam_max);
+    max_bits(&a.aux[3], fp_max);
   }
   if (a.f_in_smem) {
     __syncthreads();
     flush(accF, a.acc_F, ep.nrho);
   }
+}
+
+// ---- the fixed-point scale of pass pair (one thread) ---------------------------------
+__global__ void k_adj_scale(Sys s, EAMParams ep, AdjArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double gE = __longlong_as_double(a.aux[0]), gF = __longlong_as_double(a.aux[1]);
+  const double lam = __longlong_as_double(a.aux[2]), fp = __longlong_as_double(a.aux[3]);
+  const double B = fmax(0.5 * gE, lam) + 1.5 * gF * fmax(1.0, 2.0 * fp) * ep.inv_dr;
+  const double P = (double)s.st->N * (double)s.nmax;
+  double S = 1.0;
+  if (P * B > 0.0 && isfinite(P * B)) {
+    int e = 61 - (int)ceil(log2(P * B));
+    e = e > 100 ? 100 : (e < -100 ? -100 : e);  // a finite FP32 scale too
+    S = ldexp(1.0, e);
+  }
+  a.aux[4] = __double_as_longlong(S);
 }
 
 // ---- pass pair: phi- and rho-knot weights of every pair -------------------------------
@@ -196,10 +286,13 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_pair(Sys s, EAMParams ep, Adj
   using R = typename GP::R;
   using V = typename GP::V;
   extern __shared__ __align__(16) unsigned char smem[];
-  double2 *hp = reinterpret_cast<double2 *>(smem);
-  double2 *hr = hp + ep.nr;
-  for (int q = threadIdx.x; q < 2 * ep.nr; q += blockDim.x) hp[q] = make_double2(0.0, 0.0);
+  // per table 2 nr low words then 2 nr high words
+  unsigned *w = reinterpret_cast<unsigned *>(smem);
+  const Fx64 hp{w, reinterpret_cast<int *>(w + 2 * ep.nr)};
+  const Fx64 hr{w + 4 * ep.nr, reinterpret_cast<int *>(w + 6 * ep.nr)};
+  for (int q = threadIdx.x; q < 8 * ep.nr; q += blockDim.x) w[q] = 0u;
   __syncthreads();
+  const R S = (R)__longlong_as_double(a.aux[4]);
   const int N = s.st->N;
   const size_t Nc = s.N_cap;
   const V *__restrict__ pg = (const V *)s.pg[a.cur];
@@ -247,11 +340,10 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_pair(Sys s, EAMParams ep, Adj
             const R gd = (gix * dx + giy * dy + giz * dz) * inv_r;
             const R cp = gd * inv_dr;                    // phi': (gF_i . d^) / h
             const R cr = gd * (fpi + q.fp) * inv_dr;     // rho': times F'_i + F'_j
-            scatter(hp, kk, (double)(half_gE * w[0] + cp * dw[0]),
-                    (double)(half_gE * w[1] + cp * dw[1]), (double)(half_gE * w[2] + cp * dw[2]),
-                    (double)(half_gE * w[3] + cp * dw[3]));
-            scatter(hr, kk, (double)(lam * w[0] + cr * dw[0]), (double)(lam * w[1] + cr * dw[1]),
-                    (double)(lam * w[2] + cr * dw[2]), (double)(lam * w[3] + cr * dw[3]));
+            scatter_fx<R>(hp, kk, S, half_gE * w[0] + cp * dw[0], half_gE * w[1] + cp * dw[1],
+                          half_gE * w[2] + cp * dw[2], half_gE * w[3] + cp * dw[3]);
+            scatter_fx<R>(hr, kk, S, lam * w[0] + cr * dw[0], lam * w[1] + cr * dw[1],
+                          lam * w[2] + cr * dw[2], lam * w[3] + cr * dw[3]);
           }
         },
         [] {});
@@ -268,28 +360,31 @@ __global__ void __launch_bounds__(256) k_adj_fin(EAMParams ep, AdjArgs a) {
   const int q = blockIdx.x * 256 + threadIdx.x;
   const int nr = ep.nr, total = 2 * nr + ep.nrho;
   if (q >= total) return;
-  const double2 *acc;
   int n, k;
   if (q < nr) {
-    acc = a.acc_phi;
     n = nr;
     k = q;
   } else if (q < 2 * nr) {
-    acc = a.acc_rho;
     n = nr;
     k = q - nr;
   } else {
-    acc = a.acc_F;
     n = ep.nrho;
     k = q - 2 * nr;
   }
-  double g = acc[k].x;
-  if (k - 1 >= 1 && k - 1 <= n - 2) g += 0.5 * acc[k - 1].y;
-  if (k + 1 >= 1 && k + 1 <= n - 2) g -= 0.5 * acc[k + 1].y;
-  if (k <= 2) g += (k == 0 ? -1.5 : (k == 1 ? 2.0 : -0.5)) * acc[0].y;
+  // (d/dy, d/dM) of knot j of this table
+  const double inv_S = 1.0 / __longlong_as_double(a.aux[4]);
+  auto at = [&](int j) -> double2 {
+    if (q >= 2 * nr) return a.acc_F[j];
+    const longlong2 v = (q < nr ? a.acc_phi : a.acc_rho)[j];
+    return make_double2((double)v.x * inv_S, (double)v.y * inv_S);
+  };
+  double g = at(k).x;
+  if (k - 1 >= 1 && k - 1 <= n - 2) g += 0.5 * at(k - 1).y;
+  if (k + 1 >= 1 && k + 1 <= n - 2) g -= 0.5 * at(k + 1).y;
+  if (k <= 2) g += (k == 0 ? -1.5 : (k == 1 ? 2.0 : -0.5)) * at(0).y;
   if (k >= n - 3) {
     const int m = n - 1 - k;
-    g += (m == 0 ? 1.5 : (m == 1 ? -2.0 : 0.5)) * acc[n - 1].y;
+    g += (m == 0 ? 1.5 : (m == 1 ? -2.0 : 0.5)) * at(n - 1).y;
   }
   a.out[q] = g;
 }
@@ -334,6 +429,7 @@ int run(const Sys &s, const EAMParams &ep, const double *gF, AdjArgs a, int64_t 
   const int N = (int)n_atoms;
   k_adj_load<P><<<nblk(s.N_cap > 0 ? s.N_cap : 1, 256), 256, 0, st>>>(s, gF, a);
   k_adj_c<P><<<persistent_grid(k_adj_c<P>, b_c, N), kAdjBlock, b_c, st>>>(s, ep, a);
+  k_adj_scale<<<1, 32, 0, st>>>(s, ep, a);
   k_adj_pair<P><<<persistent_grid(k_adj_pair<P>, b_p, N), kAdjBlock, b_p, st>>>(s, ep, a);
   k_adj_fin<<<nblk(2 * ep.nr + ep.nrho, 256), 256, 0, st>>>(ep, a);
   return 0;

@@ -10,7 +10,9 @@
 // stage their spline tables in shared memory once per block and run on a
 // persistent grid (one or two blocks per SM), so a table is read from L2 a
 // few hundred times per launch, not once per atom tile.  T lanes own one atom
-// (autotuned), as in the LJ kernel.
+// (autotuned), as in the LJ kernel.  The tables take 80 KB of shared memory
+// per block (5000 knots), so residency comes from large blocks: at most 64
+// registers per thread lets two 512-thread blocks (32 warps) share an SM.
 #include "k_pair.cuh"
 
 namespace mdk {
@@ -19,7 +21,7 @@ namespace {
 using namespace pair;
 
 template <class P, bool ENERGY, int T>
-__global__ void __launch_bounds__(512) k_rho(Sys s, EAMParams ep, StepArgs a) {
+__global__ void __launch_bounds__(512, 2) k_rho(Sys s, EAMParams ep, StepArgs a) {
   using GP = G<P>;
   using R = typename GP::R;
   using V = typename GP::V;
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(512) k_rho(Sys s, EAMParams ep, StepArgs a) {
 }
 
 template <class P, int MODE, bool ENERGY, int T>
-__global__ void __launch_bounds__(512) k_eam(Sys s, EAMParams ep, StepArgs a) {
+__global__ void __launch_bounds__(512, 2) k_eam(Sys s, EAMParams ep, StepArgs a) {
   using GP = G<P>;
   using R = typename GP::R;
   using V = typename GP::V;

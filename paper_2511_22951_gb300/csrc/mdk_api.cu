@@ -50,6 +50,7 @@ struct mdk_ctx {
   char *eam_base = nullptr;
   EAMTablesDev eam_dev{};
   double2 *adj_acc = nullptr;  // adjoint histograms: phi, rho (nr each), F (nrho)
+  long long *adj_aux = nullptr;  // adjoint bounds and fixed-point scale
   double *adj_out = nullptr;   // [2 nr + nrho] knot gradients
   double *adj_gE = nullptr;    // [n_rep] energy weights
   double *thermo_ring = nullptr;
@@ -170,6 +171,7 @@ size_t layout(mdk_ctx *c, char *base) {
   c->adj_acc = cv.take<double2>((size_t)2 * nr + nrho);
   c->adj_out = cv.take<double>((size_t)2 * nr + nrho);
   c->adj_gE = cv.take<double>(c->n_rep);
+  c->adj_aux = cv.take<long long>(8);
   c->eam_base = reinterpret_cast<char *>(kn);
   c->eam.phi64 = t.phi64;
   c->eam.rho64 = t.rho64;
@@ -1035,18 +1037,20 @@ int mdk_eam_vjp(mdk_ctx *c, const double *gE, const double *gF, double *dtheta, 
     gF_dev = s.tmp + 6 * Nc;
   }
   MDK_CK(cudaMemsetAsync(c->adj_acc, 0, sizeof(double2) * n_out, c->stream));
+  MDK_CK(cudaMemsetAsync(c->adj_aux, 0, sizeof(long long) * 8, c->stream));
   AdjArgs a{};
   a.cur = c->cur;
   a.gE = c->adj_gE;
   a.gint = s.tmp;
   a.lam = s.tmp + 4 * Nc;
-  a.acc_phi = c->adj_acc;
-  a.acc_rho = c->adj_acc + e.nr;
+  a.acc_phi = reinterpret_cast<longlong2 *>(c->adj_acc);
+  a.acc_rho = reinterpret_cast<longlong2 *>(c->adj_acc + e.nr);
   a.acc_F = c->adj_acc + 2 * e.nr;
+  a.aux = c->adj_aux;
   a.out = on_device ? dtheta : c->adj_out;
   launch_eam_rho(s, e, c->precision, StepArgs{0.0, c->cur, 0}, c->cfg, c->stream);
   if (launch_eam_adjoint(s, e, c->precision, gF_dev, a, c->N, c->stream)) return MDK_ERR_CUDA;
-  c->launches += 5;
+  c->launches += 6;
   MDK_CK(cudaPeekAtLastError());
   if (on_device) return MDK_OK;
   MDK_CK(cudaMemcpyAsync(dtheta, c->adj_out, sizeof(double) * n_out, cudaMemcpyDeviceToHost,

@@ -300,7 +300,10 @@ struct AdjArgs {
   const double *gE;                  // [n_rep] energy weights
   void *gint;                        // [N_cap] gF in internal order (gather-copy type)
   double *lam;                       // [N_cap] lambda_i = gE F'(rho_i) + c_i F''(rho_i)
-  double2 *acc_phi, *acc_rho, *acc_F;  // per knot: (d/dy, d/dM) accumulators
+  longlong2 *acc_phi, *acc_rho;      // per knot: (d/dy, d/dM), fixed point (units 1/S)
+  double2 *acc_F;                    // per knot: (d/dy, d/dM), FP64
+  long long *aux;                    // [0..3] bounds (bits of max |gE|, |gF_i|, |lambda|,
+                                     // |F'|), [4] the fixed-point scale S (bits of a double)
   double *out;                       // [2 nr + nrho] knot gradients (phi | rho | F)
 };
 int adjoint_smem_bytes(const EAMParams &ep, int precision, int pass);
