@@ -5,9 +5,11 @@
 // support"); m r'' = f integrated by velocity Verlet (Sec. "Molecular
 // dynamics").  V(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6] - shift, cut at rc.
 //
-// Launch bounds: at most 256 threads per block and 5 blocks per SM, so the
-// kernel fits 48 registers (40 resident warps per SM; a few spilled constants
-// are cheaper than the lost occupancy).
+// Launch bounds: at most 256 threads per block and 4 blocks per SM, so the
+// kernel fits 64 registers (32 resident warps per SM).  The registers hold
+// the next list group, loaded while the current one runs; measured on the
+// 8.4M-atom argon step this beats 48 registers with 40 warps (spills) and
+// 80 registers with 24 warps.
 // T lanes own one atom (T = 1, 2 or 4, picked by the autotuner): lane t walks
 // the list groups t, t + T, ... of the full Verlet list, the lanes' sums are
 // combined with shuffles in a fixed order, and lane 0 runs the epilogue
@@ -23,7 +25,7 @@ namespace {
 using namespace pair;
 
 template <class P, int MODE, bool ENERGY, int SHIFT, int T>
-__global__ void __launch_bounds__(256, 5) k_lj(Sys s, LJParams lp, StepArgs a) {
+__global__ void __launch_bounds__(256, 4) k_lj(Sys s, LJParams lp, StepArgs a) {
   using GP = G<P>;
   using R = typename GP::R;
   using V = typename GP::V;
