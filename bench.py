@@ -314,6 +314,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--vjps", type=int, default=100, help="adjoint calls timed (config 4)")
+    ap.add_argument("--launch", default=None,
+                    help="threads-per-atom x block (e.g. 1x128) instead of the autotuner")
     ap.add_argument("--drift-steps", type=int, default=0,
                     help="also run an NVE drift measurement of this many steps")
     ap.add_argument("--drift-fp64-steps", type=int, default=2000)
@@ -350,7 +352,13 @@ def main():
     n_rc = pair_count_within_rc(ctx, wl) if rank == 0 else 0.0
     if windowed:
         window_setup(ctx, wl)
-    tpa, block, _ = ctx.autotune()
+    if args.launch:
+        tpa, block = (int(q) for q in args.launch.split("x"))
+        ctx.set_launch(tpa, block)
+        picked = "--launch"
+    else:
+        tpa, block, _ = ctx.autotune()
+        picked = "mdk_autotune"
 
     # warm-up (untimed; also captures the step graphs)
     ctx.step(wl.dt, args.warmup, check=True)
@@ -520,7 +528,7 @@ def main():
                        "replicas": len(wl.systems),
                        "neighbors_per_atom": n_avg, "neighbors_within_rc": n_rc,
                        "launch": {"threads_per_atom": tpa, "block": block,
-                                  "picked_by": "mdk_autotune"},
+                                  "picked_by": picked},
                        "rebuild": "when an atom moved > skin/2 since the last build",
                        "list_builds_in_timed_region": builds0 - builds_before,
                        "step_graphs": "two-step CUDA graphs replayed by mdk_step",
