@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(512, 2) k_rho(Sys s, EAMParams ep, StepArgs a)
     }
     s.rho[i] = rho_i;
     ((R *)s.fp)[i] = (R)dF;
+    GP::st_fp((V *)s.pgF + i, pi, dF);
     if (ENERGY) s.ea[i] = Fv;
   }
 }
@@ -111,21 +112,18 @@ __global__ void __launch_bounds__(512, 2) k_eam(Sys s, EAMParams ep, StepArgs a)
   using GP = G<P>;
   using R = typename GP::R;
   using V = typename GP::V;
-  using T2 = typename GP::Tab2;
+  using TP = typename GP::TabPR;
   extern __shared__ __align__(16) unsigned char smem[];
-  T2 *pt = reinterpret_cast<T2 *>(smem);
-  T2 *rt = pt + ep.nr;
+  TP *tab = reinterpret_cast<TP *>(smem);
   {
-    const T2 *sp = GP::phi2(ep), *sr = GP::rho2(ep);
-    for (int q = threadIdx.x; q < ep.nr; q += blockDim.x) {
-      pt[q] = sp[q];
-      rt[q] = sr[q];
-    }
+    const TP *src = GP::pr(ep);
+    for (int q = threadIdx.x; q < ep.nr; q += blockDim.x) tab[q] = src[q];
   }
   __syncthreads();
   const int N = s.st->N;
   const size_t Nc = s.N_cap;
   const V *__restrict__ pg = (const V *)s.pg[a.cur];
+  const V *__restrict__ pgf = (const V *)s.pgF;  // neighbours: offsets and F'
   const R *__restrict__ fpa = (const R *)s.fp;
   const R rc2 = sizeof(R) == 8 ? (R)ep.rc2 : (R)ep.rc2f;
   const R inv_dr = sizeof(R) == 8 ? (R)ep.inv_dr : (R)ep.inv_drf;
@@ -148,20 +146,9 @@ __global__ void __launch_bounds__(512, 2) k_eam(Sys s, EAMParams ep, StepArgs a)
     Acc<R> fx, fy, fz;
     R e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     R bx = 0, by = 0, bz = 0;
-    struct Rec {
-      V p;
-      R fp;
-    };
     walk<T>(
-        s.nbr, Nc, i, nn, tl.t,
-        [&](uint32_t j) {
-          Rec q;
-          q.p = GP::ld(pg + j);
-          q.fp = __ldg(fpa + j);
-          return q;
-        },
-        [&](uint32_t ent, const Rec &q) {
-          const V &pj = q.p;
+        s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pgf + j); },
+        [&](uint32_t ent, const V &pj) {
           const R dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
           const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
           const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
@@ -173,14 +160,14 @@ __global__ void __launch_bounds__(512, 2) k_eam(Sys s, EAMParams ep, StepArgs a)
             int kk = (int)u;
             kk = kk > kmax ? kmax : kk;
             const R t = u - (R)kk;
-            const R dphi = GP::der2(pt, kk, t) * inv_dr;
-            const R drho = GP::der2(rt, kk, t) * inv_dr;
-            const R fr = (dphi + (fpi + q.fp) * drho) * inv_r;  // V'(r)/r
+            R dphi, drho;
+            GP::der_pr(tab, kk, t, dphi, drho);
+            const R fr = (dphi + (fpi + GP::fp_of(pj)) * drho) * inv_dr * inv_r;  // V'(r)/r
             bx += fr * dx;
             by += fr * dy;
             bz += fr * dz;
             if (ENERGY) {
-              e += R(0.5) * GP::val2(pt, ep, kk, t);
+              e += R(0.5) * GP::val_pr(tab, ep, kk, t);
               const R hf = R(-0.5) * fr;
               w0 += hf * dx * dx;
               w1 += hf * dy * dy;
@@ -243,6 +230,13 @@ __global__ void k_eam_prepare(int nr, int nrho, const double *phi, const double 
     o.phi_d32[k] = make_float2((float)dp, (float)mp);
     o.rho_d32[k] = make_float2((float)dr, (float)mr);
     o.phi_v32[k] = (float)phi[k];
+    o.pr32[k] = make_float4((float)dp, (float)mp, (float)dr, (float)mr);
+    dvec4 q;
+    q.x = phi[k];
+    q.y = mp;
+    q.z = rho[k];
+    q.w = mr;
+    o.pr64[k] = q;
     if (k + 1 < nr)
       o.rho_i32[k] = make_float4((float)rho[k], (float)dr, (float)mr, (float)hslope(rho, nr, k + 1));
   }
@@ -351,8 +345,8 @@ int attrs(int b1, int b2) {
 }  // namespace
 
 int eam_smem_bytes(const EAMParams &p, int precision, int pass) {
-  if (precision == 0) return (pass == 1 ? 1 : 2) * p.nr * (int)sizeof(double2);
-  return pass == 1 ? (p.nr - 1) * (int)sizeof(float4) : 2 * p.nr * (int)sizeof(float2);
+  if (precision == 0) return p.nr * (int)(pass == 1 ? sizeof(double2) : sizeof(dvec4));
+  return pass == 1 ? (p.nr - 1) * (int)sizeof(float4) : p.nr * (int)sizeof(float4);
 }
 
 int configure_eam_smem(int b1, int b2, int precision) {

@@ -84,6 +84,27 @@ struct G<Fp64> {
     const double2 a = t[k], b = t[k + 1];
     return herm_val<double>(u, a.x, a.y, b.x, b.y);
   }
+  // force pass: interleaved phi / rho knots, h * derivatives of both
+  using TabPR = dvec4;
+  static __device__ __forceinline__ const dvec4 *pr(const EAMParams &e) { return e.pr64; }
+  static __device__ __forceinline__ void der_pr(const dvec4 *t, int k, double u, double &dphi,
+                                                double &drho) {
+    const dvec4 a = t[k], b = t[k + 1];
+    dphi = herm_der<double>(u, a.x, a.y, b.x, b.y);
+    drho = herm_der<double>(u, a.z, a.w, b.z, b.w);
+  }
+  static __device__ __forceinline__ double val_pr(const dvec4 *t, const EAMParams &, int k,
+                                                  double u) {
+    const dvec4 a = t[k], b = t[k + 1];
+    return herm_val<double>(u, a.x, a.y, b.x, b.y);
+  }
+  // gather copy with F'(rho) in place of the info word
+  static __device__ __forceinline__ void st_fp(dvec4 *p, const dvec4 &q, double fp) {
+    double2 *o = reinterpret_cast<double2 *>(p);
+    o[0] = make_double2(q.x, q.y);
+    o[1] = make_double2(q.z, fp);
+  }
+  static __device__ __forceinline__ double fp_of(const dvec4 &q) { return q.w; }
 };
 template <>
 struct G<Mixed> {
@@ -132,6 +153,29 @@ struct G<Mixed> {
     return __ldg(e.phi_v32 + k) + (3.0f * u2 - 2.0f * u3) * a.x + (u3 - 2.0f * u2 + u) * a.y +
            (u3 - u2) * b.y;
   }
+  // force pass: interleaved phi / rho differences and slopes, h * derivatives
+  using TabPR = float4;
+  static __device__ __forceinline__ const float4 *pr(const EAMParams &e) { return e.pr32; }
+  static __device__ __forceinline__ void der_pr(const float4 *t, int k, float u, float &dphi,
+                                                float &drho) {
+    const float4 a = t[k], b = t[k + 1];
+    const float u2 = u * u;
+    const float w0 = 6.0f * u - 6.0f * u2, w1 = 3.0f * u2 - 4.0f * u + 1.0f,
+                w3 = 3.0f * u2 - 2.0f * u;
+    dphi = w0 * a.x + w1 * a.y + w3 * b.y;
+    drho = w0 * a.z + w1 * a.w + w3 * b.w;
+  }
+  static __device__ __forceinline__ float val_pr(const float4 *t, const EAMParams &e, int k,
+                                                 float u) {
+    const float4 a = t[k], b = t[k + 1];
+    const float u2 = u * u, u3 = u2 * u;
+    return __ldg(e.phi_v32 + k) + (3.0f * u2 - 2.0f * u3) * a.x + (u3 - 2.0f * u2 + u) * a.y +
+           (u3 - u2) * b.y;
+  }
+  static __device__ __forceinline__ void st_fp(float4 *p, const float4 &q, double fp) {
+    *p = make_float4(q.x, q.y, q.z, (float)fp);
+  }
+  static __device__ __forceinline__ float fp_of(const float4 &q) { return q.w; }
 };
 
 // ---- the neighbour walk ------------------------------------------------------------

@@ -136,6 +136,7 @@ size_t layout(mdk_ctx *c, char *base) {
   const size_t gsz = c->precision == MDK_FP64 ? 32 : 16;
   s.pg[0] = cv.take<char>(gsz * Nc);
   s.pg[1] = cv.take<char>(gsz * Nc);
+  s.pgF = cv.take<char>(gsz * (c->pot == 2 ? Nc : 1));
   s.nnbr = cv.take<int32_t>(Nc);
   s.nbr = cv.take<uint32_t>((size_t)std::max(c->nmax, c->nmax_grow) * Nc);
   s.ea = cv.take<double>(Nc);
@@ -168,6 +169,8 @@ size_t layout(mdk_ctx *c, char *base) {
   t.phi_d32 = cv.take<float2>(nr);
   t.rho_d32 = cv.take<float2>(nr);
   t.phi_v32 = cv.take<float>(nr);
+  t.pr32 = cv.take<float4>(nr);
+  t.pr64 = cv.take<dvec4>(nr);
   c->adj_acc = cv.take<double2>((size_t)2 * nr + nrho);
   c->adj_out = cv.take<double>((size_t)2 * nr + nrho);
   c->adj_gE = cv.take<double>(c->n_rep);
@@ -180,6 +183,8 @@ size_t layout(mdk_ctx *c, char *base) {
   c->eam.phi_d32 = t.phi_d32;
   c->eam.rho_d32 = t.rho_d32;
   c->eam.phi_v32 = t.phi_v32;
+  c->eam.pr32 = t.pr32;
+  c->eam.pr64 = t.pr64;
   return align256(cv.off);
 }
 

@@ -86,6 +86,7 @@ struct Sys {
   int32_t *id, *tmpi;
   float4 *pf;
   void *pg[2];
+  void *pgF;                // EAM: gather copy with F'(rho_j) in .w (density pass)
   int32_t *nnbr;
   uint32_t *nbr;
   double *ea, *ka, *wa;     // per-atom U_i, K_i, W_i[6] (SoA)
@@ -133,6 +134,11 @@ struct LJParams {
   int shift_mode;
 };
 
+// 32-byte FP64 gather-copy element (x, y, z, info bits in w)
+struct alignas(32) dvec4 {
+  double x, y, z, w;
+};
+
 struct EAMParams {
   int nr, nrho;
   double rc, rc2, inv_dr, dr, rho_max, inv_drho, drho;
@@ -147,6 +153,12 @@ struct EAMParams {
   const float4 *rho_i32;
   const float2 *phi_d32, *rho_d32;
   const float *phi_v32;
+  // force pass: phi and rho interleaved per knot, so one pair of loads
+  // serves both derivatives
+  //   pr32[k] = (phi_{k+1} - phi_k, h m^phi_k, rho_{k+1} - rho_k, h m^rho_k)
+  //   pr64[k] = (phi_k, h m^phi_k, rho_k, h m^rho_k)
+  const float4 *pr32;
+  const dvec4 *pr64;
 };
 
 // writable view of the device tables filled by launch_eam_prepare
@@ -155,6 +167,8 @@ struct EAMTablesDev {
   float4 *rho_i32;
   float2 *phi_d32, *rho_d32;
   float *phi_v32;
+  float4 *pr32;
+  dvec4 *pr64;
 };
 
 // Centre of cell c along d.  Gather copies hold x - centre, so |p| <= h/2
@@ -187,10 +201,6 @@ __host__ __device__ __forceinline__ int cell_coord(uint32_t c, int d) {
   return (int)((c >> (10 * d)) & 1023u);
 }
 
-// 32-byte FP64 gather-copy element (x, y, z, info bits in w)
-struct alignas(32) dvec4 {
-  double x, y, z, w;
-};
 
 // precision traits of the per-step gather copy
 struct Fp64 {
