@@ -321,22 +321,28 @@ __global__ void __launch_bounds__(kBlk) k_scatter(Sys s) {
   }
 }
 
-// order inside each cell by permanent atom id (insertion sort: a cell holds
-// a few tens of atoms), so the layout does not depend on atomic ordering
+// Order inside each cell by permanent atom id, so the layout does not depend
+// on the order of the scatter's atomics: the atom at slot k of its cell takes
+// rank = number of atoms of the cell with a smaller id, and lands at
+// cell_start + rank of the final order (kept in tmpi, which k_permute reads
+// first and overwrites at the same index).  One thread per atom: the
+// comparisons of a cell run in parallel, with independent loads.  Atoms a
+// window deletes (the last bucket) keep the scatter's order.
 __global__ void __launch_bounds__(kBlk) k_cell_sort(Sys s) {
   if (!flag_on(s)) return;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s.n_cells; c += gridDim.x * blockDim.x) {
-  const int a = s.cell_start[c], b = s.cell_start[c + 1];
-  for (int k = a + 1; k < b; ++k) {
+  const int N = s.st->N;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
     const int v = s.order[k];
-    const int key = s.id[v];
-    int q = k - 1;
-    while (q >= a && s.id[s.order[q]] > key) {
-      s.order[q + 1] = s.order[q];
-      --q;
+    const int b = s.cell_of[v];
+    const int a = s.cell_start[b], e = s.cell_start[b + 1];
+    int rank = k - a;
+    if (b < s.n_cells) {
+      const int key = s.id[v];
+      rank = 0;
+#pragma unroll 4
+      for (int q = a; q < e; ++q) rank += s.id[s.order[q]] < key ? 1 : 0;
     }
-    s.order[q + 1] = v;
-  }
+    s.tmpi[a + rank] = v;
   }
 }
 
@@ -346,7 +352,7 @@ __global__ void __launch_bounds__(kBlk) k_permute(Sys s, typename P::vec4 *pg_ta
   const int N = s.st->N;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
   const size_t Nc = s.N_cap;
-  const int o = s.order[k];
+  const int o = s.tmpi[k];  // the cell-sorted order (k_cell_sort)
   double xv[3];
   for (int d = 0; d < 3; ++d) {
     xv[d] = s.x[d * Nc + o];
@@ -588,7 +594,7 @@ int launch_rebuild_body(const Sys &s, int target_pg, int precision, int from_gra
     g_cells = persistent_blocks((const void *)k_cell_sort, kBlk, 0);
   }
   const int gN = std::min(g_atom, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
-  const int gC = std::min(g_cells, nblk(s.n_cells, kBlk));
+  const int gC = std::min(g_cells, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
   const int gB = std::min(g_build, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
   if (s.win_on) {
     k_win_stats<<<gN, kBlk, 0, st>>>(s);
