@@ -85,6 +85,38 @@ def algorithmic_bytes_per_atom(wl, prec, n_avg):
     return lj + g + 4 * n_avg + 4 + 8 + r + r
 
 
+# DRAM bytes per atom of one force-pass launch (dram__bytes_read.sum +
+# dram__bytes_write.sum from an ncu capture, divided by the atoms of the
+# captured case), valid only for the kernel sources they were taken from:
+# the sha256 of those files is checked at run time and `traffic` is null
+# when any of them changed since.
+TRAFFIC = {
+    ("lj", "mixed"): {"bytes_per_atom": 475.2,
+                      "sources_sha256": "6b256684d54b8f75565804bf0f100220c0a90aecf9dc37ff3593cc82fd6d5c40",
+                      "capture": "k_lj<Mixed, kStep, T=1>, 8,388,608 atoms, ncu "
+                                 "dram__bytes_read.sum + dram__bytes_write.sum, 4 launches"},
+}
+TRAFFIC_SOURCES = ("paper_2511_22951_gb300/csrc/k_lj.cu",
+                   "paper_2511_22951_gb300/csrc/k_pair.cuh",
+                   "paper_2511_22951_gb300/csrc/mdk_internal.cuh")
+
+
+def sources_sha256(paths=TRAFFIC_SOURCES):
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def traffic_per_launch(wl, prec, n_atoms):
+    t = TRAFFIC.get((wl.potential, prec))
+    if t is None or t["sources_sha256"] != sources_sha256():
+        return None
+    return t["bytes_per_atom"] * n_atoms
+
+
 # FP64 arithmetic per unordered pair inside rc (one FMA = 2): LJ 23;
 # EAM 22 (density pass: pair vector, r, spline value) + 40 (force pass:
 # pair vector, r, two spline derivatives, force).  A full list evaluates every
@@ -408,9 +440,10 @@ def main():
               "timed_from": f"CUDA events around each of {int(prof['force_passes'])} force "
                             f"passes of a {prof_steps}-step profiled segment"}
     if prec == "mixed":
+        tr = traffic_per_launch(wl, prec, n_now)
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                "frac": gbs / hbm, "traffic": None, "bytes_per_atom": bpa,
-                "peak_kind": peak_kind, **common}
+                "frac": gbs / hbm, "traffic": tr, "bytes_per_atom": bpa,
+                "traffic_unit": "bytes per launch", "peak_kind": peak_kind, **common}
     else:
         tflops = n_now * 0.5 * n_rc * FLOPS_PER_PAIR[wl.potential] / (force_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
