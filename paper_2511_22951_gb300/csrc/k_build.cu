@@ -179,9 +179,11 @@ __global__ void k_set_flag(Sys s) {
 __global__ void __launch_bounds__(kBlk) k_bin(Sys s) {
   if (!flag_on(s)) return;
   const int N = s.st->N;
+  const bool win = s.win_on && s.st->win_active;
+  long long xmin = dkey(INFINITY);  // smallest x kept (window: new rear layer)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
   const Grid &g = s.grid[s.info[i] >> 8];
-  if (s.win_on && s.st->win_active) {
+  if (win) {
     const double x = s.x[i];
     if (x < s.st->win_cut) {  // behind the window: to the deletion bucket
       s.cell_of[i] = s.n_cells;
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(kBlk) k_bin(Sys s) {
       atomicAdd(&s.cell_cnt[s.n_cells], 1);
       continue;
     }
-    atomicMin(&s.st->key_xmin, dkey(x));
+    xmin = min(xmin, dkey(x));
   }
   int c[3];
   for (int d = 0; d < 3; ++d) {
@@ -219,6 +221,10 @@ __global__ void __launch_bounds__(kBlk) k_bin(Sys s) {
   s.cell_of[i] = cell;
   s.tmpu[i] = pack_cell(c[0], c[1], c[2]);
   atomicAdd(&s.cell_cnt[cell], 1);
+  }
+  if (win) {  // one atomic per warp, not per atom
+    for (int o = 16; o > 0; o >>= 1) xmin = min(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(&s.st->key_xmin, xmin);
   }
 }
 
