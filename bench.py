@@ -46,6 +46,20 @@ METRIC = "atom-timesteps/s on 1 GB300 (LJ, EAM): mixed/batched vs FP64 at stated
 UNIT = "atom-timesteps/s"
 
 
+def job_throughput(ms, atoms, steps, dist=None, device="cpu"):
+    """Whole-job atom-timesteps/s: the atoms of every rank over the slowest
+    rank's time (replicas: each rank steps its own copy of the workload).
+    Returns (value, max ms)."""
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        import torch
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        a = torch.tensor([float(atoms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(a, op=dist.ReduceOp.SUM)
+        ms, atoms = float(t.item()), float(a.item())
+    return atoms * steps / (ms / 1e3), ms
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -420,12 +434,8 @@ def main():
     prof = ctx.get_profile()
     ctx.profile(False)
     ctx.check()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     n_mean = 0.5 * (n_start + ctx.natoms())
-    value = n_mean * args.steps * world / (ms / 1e3)
+    value, ms = job_throughput(ms, n_mean, args.steps, dist, "cuda")
 
     # dominant kernel: the fused force + integration pass
     hbm, peak_kind = peaks()

@@ -57,6 +57,9 @@ extern "C" {
                                        (F was extrapolated linearly)       */
 #define MDK_ERR_TOO_LARGE (-11)     /* size above the fixed maximum of
                                        mdk_lj_compute_noalloc             */
+#define MDK_ERR_CAPACITY (-12)      /* the moving window had more atoms to
+                                       append than mdk_set_capacity left
+                                       room for (as many as fit were)     */
 
 /* ---- precision modes ---------------------------------------------------- */
 #define MDK_FP64 0  /* every operation in FP64                               */
@@ -275,7 +278,7 @@ int mdk_set_piston(mdk_ctx *ctx, double u_p, const uint8_t *is_piston);
  *   slab_x, slab_v : host [n_slab][3] positions (x in [0, slab_lx)) and
  *                    velocities of one fresh slab; copied.
  * The atom count changes: reserve room with mdk_set_capacity (appends that
- * do not fit raise MDK_ERR_NEIGH_OVERFLOW's status bit).  Once a window is
+ * do not fit are dropped and raise MDK_ERR_CAPACITY).  Once a window is
  * set, per-atom outputs come in ascending atom-id order (mdk_get_ids).
  * Single-system contexts with a free (non-periodic) x only; front_bin > 0
  * with at most 2^24 bins over the box.  Takes effect at the next list build.

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kBlk) k_win_plan(Sys s) {
   const long long room = (long long)s.N_cap - st->N;
   if (add > room) {
     add = room;
-    atomicOr(&st->bits, kStOverflow);
+    atomicOr(&st->bits, kStCapacity);
   }
   st->win_insert = (int)add;
   st->win_x0 = xmax;

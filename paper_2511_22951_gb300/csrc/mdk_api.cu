@@ -303,6 +303,7 @@ int status_from_bits(unsigned bits) {
   if (bits & kStOverflow) return MDK_ERR_NEIGH_OVERFLOW;
   if (bits & kStAtomLost) return MDK_ERR_ATOM_LOST;
   if (bits & kStTimeout) return MDK_ERR_TIMEOUT;
+  if (bits & kStCapacity) return MDK_ERR_CAPACITY;
   if (bits & kStRhoRange) return MDK_ERR_RHO_RANGE;
   return MDK_OK;
 }
@@ -581,6 +582,7 @@ const char *mdk_status_string(int s) {
     case MDK_ERR_ORDER: return "call made before a required call";
     case MDK_ERR_RHO_RANGE: return "EAM density above the F table (extrapolated)";
     case MDK_ERR_TOO_LARGE: return "size above the fixed maximum of the allocation-free entry point";
+    case MDK_ERR_CAPACITY: return "atom capacity full: the moving window could not append all atoms";
     default: return "unknown status";
   }
 }

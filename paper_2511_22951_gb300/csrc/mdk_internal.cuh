@@ -38,6 +38,7 @@ enum : unsigned {
   kStRhoRange = 4u,
   kStAtomLost = 8u,
   kStTimeout = 16u,
+  kStCapacity = 32u,  // a window append did not fit the capacity
 };
 
 struct DevStatus {

@@ -28,6 +28,7 @@ MDK_ERR_WORKSPACE = -8
 MDK_ERR_ORDER = -9
 MDK_ERR_RHO_RANGE = -10
 MDK_ERR_TOO_LARGE = -11
+MDK_ERR_CAPACITY = -12
 MDK_FP64 = 0
 MDK_MIXED = 1
 
