@@ -72,6 +72,11 @@ def lib():
         L.ora_md_window.argtypes = [P, I64, P, P, P, P, P, P, P, P, P, I, D, P, P, I, D, P, D,
                                     D, I64, I, D, D, D, D, P, P, I64, D, D, D, D]
         L.ora_md_window.restype = I64
+        L.ora_philox4x64.argtypes = [P, P, P]
+        L.ora_philox4x64.restype = None
+        L.ora_md_langevin.argtypes = [I64, P, P, P, P, P, P, I, P, I, D, P, P, I, D, P, D, D,
+                                      I64, I, P, D, P, P, P, P, ctypes.c_uint64, I64]
+        L.ora_md_langevin.restype = I64
         L.ora_eam_vjp.argtypes = [I64, P, P, P, P, I, D, P, P, I, D, P, D, P, P]
         L.ora_eam_vjp.restype = I
         L.ora_eam_jvp.argtypes = [I64, P, P, P, P, I, D, P, P, I, D, P, P, P, P, D, P, P]
@@ -274,6 +279,52 @@ def md_run(x, v, masses, lo, hi, periodic, dt, nsteps, skin, lj_params=None,
                               _p(pis), u_p, _p(thermo), _p(F))
     if nb < 0:
         raise RuntimeError(f"oracle md_run failed ({nb})")
+    return {"x": x, "v": v, "F": F, "thermo": thermo[:nsteps], "n_builds": int(nb)}
+
+
+def philox4x64(ctr, key):
+    """Philox4x64-10 block for a 4-word counter and a 2-word key (uint64)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    lib().ora_philox4x64(_p(c), _p(k), _p(out))
+    return out
+
+
+def md_langevin(x, v, masses, lo, hi, periodic, dt, nsteps, skin, regions, seed,
+                lj_params=None, tables=None, ids=None, step0=0, rebuild_every=0,
+                piston=None, u_p=0.0):
+    """md_run with Langevin thermostat regions: regions = [(x_lo, x_hi, T,
+    (u_x, u_y, u_z), beta), ...] (at most 8); ids = permanent atom ids
+    (default 0..N-1); step0 = steps done before this run."""
+    x = _f64(x, (-1, 3)).copy()
+    v = _f64(v, (-1, 3)).copy()
+    n = x.shape[0]
+    m = _f64(masses, (n,))
+    lo, hi, per = _box(lo, hi, periodic)
+    thermo = np.zeros((max(nsteps, 1), 3))
+    F = np.zeros((n, 3))
+    pis = None if piston is None else np.ascontiguousarray(piston, dtype=np.uint8)
+    lp = [float(len(regions))]
+    for (xl, xh, T, u, beta) in regions:
+        lp += [xl, xh, T, u[0], u[1], u[2], beta]
+    lp = _f64(lp)
+    idv = np.arange(n, dtype=np.int64) if ids is None else np.ascontiguousarray(ids, np.int64)
+    if lj_params is not None:
+        par = _f64([lj_params.eps, lj_params.sigma, lj_params.rc, lj_params.shift_mode])
+        nb = lib().ora_md_langevin(n, _p(x), _p(v), _p(m), _p(lo), _p(hi), _p(per), 0,
+                                   _p(par), 0, 0.0, None, None, 0, 0.0, None, skin, dt, nsteps,
+                                   rebuild_every, _p(pis), u_p, _p(thermo), _p(F), _p(lp),
+                                   _p(idv), int(seed), int(step0))
+    else:
+        phi, rho, Ft = _f64(tables.phi), _f64(tables.rho), _f64(tables.F)
+        nb = lib().ora_md_langevin(n, _p(x), _p(v), _p(m), _p(lo), _p(hi), _p(per), 1, None,
+                                   phi.shape[0], tables.rc, _p(phi), _p(rho), Ft.shape[0],
+                                   tables.rho_max, _p(Ft), skin, dt, nsteps, rebuild_every,
+                                   _p(pis), u_p, _p(thermo), _p(F), _p(lp), _p(idv),
+                                   int(seed), int(step0))
+    if nb < 0:
+        raise RuntimeError(f"oracle md_langevin failed ({nb})")
     return {"x": x, "v": v, "F": F, "thermo": thermo[:nsteps], "n_builds": int(nb)}
 
 

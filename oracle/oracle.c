@@ -25,6 +25,11 @@
  *     dynamics", Eq. MD-system: m_i r_i'' = f_i = -grad_i U)
  *   - per-bin profiles of the Appendix (mass, COM velocity, temperature per
  *     degree of freedom, pressure tensor with the virial term)
+ *   - the moving window's rules (Sec. "Moving window simulation")
+ *   - the gradient of the EAM energy and forces with respect to the table
+ *     knots, in reverse mode and (independently) forward mode
+ *   - Langevin thermostat regions (Sec. "Molecular dynamics" and "Moving
+ *     window simulation") with the Philox4x64-10 counter-based generator
  *
  * Readings of the paper that this file fixes:
  *   * pair vector d_ij = (x_j - x_i) + n*L, rounded in that order;
@@ -811,13 +816,104 @@ int ora_sampled(int kind, int64_t N, const double *x, const double *lo,
  * thermo (may be NULL) receives per step: K, U, W_xx+W_yy+W_zz.
  * Returns the number of list builds (>= 1) or a negative error code.
  */
-int64_t ora_md_run(int64_t N, double *x, double *v, const double *mass,
-                   const double *lo, const double *hi, const int *per,
-                   int kind, const double *lj_par, int nr, double rc_eam,
-                   const double *phi, const double *rho, int nrho,
-                   double rho_max, const double *Ftab, double skin, double dt,
-                   int64_t nsteps, int rebuild_every, const uint8_t *piston,
-                   double u_p, double *thermo, double *F_out) {
+/* ---------------------------------------------------------------------- */
+/* Langevin thermostat (Sec. "Molecular dynamics": a Langevin force added to  */
+/* the right-hand side of Eq. MD-system gives NVT; Sec. "Moving window        */
+/* simulation": thermostats with a target temperature, a target mean         */
+/* velocity and a stiffness beta, acting in regions along x)                  */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Philox4x64-10 counter-based generator (Salmon, Moraes, Dror and Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC 2011): ten rounds of
+ * two 64x64 -> 128-bit multiplications on the counter, the key bumped by
+ * the Weyl constants between rounds.
+ */
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo) {
+    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void ora_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B97F4A7C15ULL;
+            k1 += 0xBB67AE8584CAA73BULL;
+        }
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(0xD2E7470EE14C6C93ULL, c0, &hi0, &lo0);
+        mulhilo64(0xCA5A826395121157ULL, c2, &hi1, &lo1);
+        uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+static const double ORA_KB = 8.617333262e-5; /* eV/K */
+
+/*
+ * Regions along x, each with a target temperature T, a target mean velocity
+ * u and a stiffness beta (1/fs).  Reading (the paper gives no formula): at
+ * every force evaluation of a step, an atom in a region (first r with
+ * x_lo <= x < x_hi at the new positions, piston atoms excluded) gets
+ *   F += -beta m (v - u) / A  +  sqrt(24 beta m k_B T / (dt A)) (xi - 1/2)
+ * per component, with v its half-step velocity, A = ORA_ACC, and xi uniform
+ * on [0, 1): output d of Philox4x64-10 with counter (atom id, step, 0, 0)
+ * and key (seed, 0), xi = (out >> 11) 2^-53.  (Uniform noise with the
+ * variance 2 beta m k_B T / (dt A) of the Gaussian one.)  For a free
+ * particle this velocity-Verlet discretisation leaves the full-step
+ * velocities with variance exactly k_B T A / m.
+ */
+typedef struct {
+    int n;
+    double xlo[8], xhi[8], T[8], u[8][3], beta[8];
+    uint64_t seed;
+    int64_t step0;
+    const int64_t *ids;
+} ora_langevin;
+
+static void langevin_forces(const ora_langevin *lg, int64_t N, const double *x,
+                            const double *v, const double *mass, const uint8_t *piston,
+                            double dt, int64_t step, double *F) {
+    for (int64_t i = 0; i < N; ++i) {
+        if (piston && piston[i]) continue;
+        int r = -1;
+        for (int q = 0; q < lg->n && r < 0; ++q)
+            if (x[3 * i] >= lg->xlo[q] && x[3 * i] < lg->xhi[q]) r = q;
+        if (r < 0) continue;
+        uint64_t ctr[4] = {(uint64_t)lg->ids[i], (uint64_t)step, 0, 0};
+        uint64_t key[2] = {lg->seed, 0};
+        uint64_t out[4];
+        ora_philox4x64(ctr, key, out);
+        double m = mass[i], beta = lg->beta[r];
+        double kT = ORA_KB * lg->T[r];
+        double sigma = sqrt((((24.0 * beta) * m) * kT) / (dt * ORA_ACC));
+        for (int k = 0; k < 3; ++k) {
+            double xi = (double)(out[k] >> 11) * 0x1.0p-53;
+            double fr = ((-beta * m) * (v[3 * i + k] - lg->u[r][k])) / ORA_ACC;
+            double fn = sigma * (xi - 0.5);
+            F[3 * i + k] = (F[3 * i + k] + fr) + fn;
+        }
+    }
+}
+
+static int64_t md_run_impl(int64_t N, double *x, double *v, const double *mass,
+                           const double *lo, const double *hi, const int *per,
+                           int kind, const double *lj_par, int nr, double rc_eam,
+                           const double *phi, const double *rho, int nrho,
+                           double rho_max, const double *Ftab, double skin, double dt,
+                           int64_t nsteps, int rebuild_every, const uint8_t *piston,
+                           double u_p, double *thermo, double *F_out,
+                           const ora_langevin *lg) {
     ora_box b = make_box(lo, hi, per);
     ora_pot p;
     if (kind == 0)
@@ -875,6 +971,7 @@ int64_t ora_md_run(int64_t N, double *x, double *v, const double *mass,
             ++nbuild;
         }
         forces_from_list(&p, N, x, &b, vl.off, vl.j, vl.n, &E, F, W, NULL, NULL, NULL, NULL);
+        if (lg) langevin_forces(lg, N, x, v, mass, piston, dt, lg->step0 + step + 1, F);
         double K = 0.0;
         for (int64_t i = 0; i < N; ++i) {
             if (!(piston && piston[i])) {
@@ -900,6 +997,55 @@ int64_t ora_md_run(int64_t N, double *x, double *v, const double *mass,
     free(xref);
     pot_free(&p);
     return nbuild;
+}
+
+/* Velocity-Verlet NVE (Sec. "Molecular dynamics"); see md_run_impl. */
+int64_t ora_md_run(int64_t N, double *x, double *v, const double *mass,
+                   const double *lo, const double *hi, const int *per,
+                   int kind, const double *lj_par, int nr, double rc_eam,
+                   const double *phi, const double *rho, int nrho,
+                   double rho_max, const double *Ftab, double skin, double dt,
+                   int64_t nsteps, int rebuild_every, const uint8_t *piston,
+                   double u_p, double *thermo, double *F_out) {
+    return md_run_impl(N, x, v, mass, lo, hi, per, kind, lj_par, nr, rc_eam, phi, rho, nrho,
+                       rho_max, Ftab, skin, dt, nsteps, rebuild_every, piston, u_p, thermo,
+                       F_out, NULL);
+}
+
+/*
+ * The same with the Langevin regions (see langevin_forces).  lang_par =
+ * [n, then per region x_lo, x_hi, T, u_x, u_y, u_z, beta]; ids = permanent
+ * atom ids (the generator's counter); step0 = steps done before this run.
+ */
+int64_t ora_md_langevin(int64_t N, double *x, double *v, const double *mass,
+                        const double *lo, const double *hi, const int *per,
+                        int kind, const double *lj_par, int nr, double rc_eam,
+                        const double *phi, const double *rho, int nrho,
+                        double rho_max, const double *Ftab, double skin, double dt,
+                        int64_t nsteps, int rebuild_every, const uint8_t *piston,
+                        double u_p, double *thermo, double *F_out,
+                        const double *lang_par, const int64_t *ids, uint64_t seed,
+                        int64_t step0) {
+    ora_langevin lg;
+    memset(&lg, 0, sizeof(lg));
+    lg.n = (int)lang_par[0];
+    if (lg.n < 0 || lg.n > 8) return -3;
+    for (int q = 0; q < lg.n; ++q) {
+        const double *r = lang_par + 1 + 7 * q;
+        lg.xlo[q] = r[0];
+        lg.xhi[q] = r[1];
+        lg.T[q] = r[2];
+        lg.u[q][0] = r[3];
+        lg.u[q][1] = r[4];
+        lg.u[q][2] = r[5];
+        lg.beta[q] = r[6];
+    }
+    lg.seed = seed;
+    lg.step0 = step0;
+    lg.ids = ids;
+    return md_run_impl(N, x, v, mass, lo, hi, per, kind, lj_par, nr, rc_eam, phi, rho, nrho,
+                       rho_max, Ftab, skin, dt, nsteps, rebuild_every, piston, u_p, thermo,
+                       F_out, &lg);
 }
 
 /* ---------------------------------------------------------------------- */
