@@ -360,6 +360,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--vjps", type=int, default=100, help="adjoint calls timed (config 4)")
+    ap.add_argument("--langevin", default=None,
+                    help="T,beta: a Langevin thermostat on the whole system (K, 1/fs)")
     ap.add_argument("--launch", default=None,
                     help="threads-per-atom x block (e.g. 1x128) instead of the autotuner")
     ap.add_argument("--drift-steps", type=int, default=0,
@@ -398,6 +400,11 @@ def main():
     n_rc = pair_count_within_rc(ctx, wl) if rank == 0 else 0.0
     if windowed:
         window_setup(ctx, wl)
+    lang = None
+    if args.langevin:
+        T_l, beta_l = (float(q) for q in args.langevin.split(","))
+        lang = [(-1e30, 1e30, T_l, (0.0, 0.0, 0.0), beta_l)]
+        ctx.set_langevin(lang, seed=1)
     if args.launch:
         tpa, block = (int(q) for q in args.launch.split("x"))
         ctx.set_launch(tpa, block)
@@ -536,6 +543,8 @@ def main():
                                capacity=int(n_atoms * 1.1) if windowed else None)
         if windowed:
             window_setup(c64, wl)
+        if lang:
+            c64.set_langevin(lang, seed=1)
         c64.step(wl.dt, 3)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -587,6 +596,9 @@ def main():
             "vjp": vjp,
             "drift": drift,
         }
+        if lang:
+            line["config"]["langevin"] = {"T_K": lang[0][2], "beta_per_fs": lang[0][4],
+                                          "regions": "whole system"}
         if windowed:
             line["config"]["piston_u_p_A_per_fs"] = wl.extra["u_p"]
             line["config"]["window"] = {"L_behind": wl.extra["L_behind"],

@@ -290,6 +290,31 @@ int mdk_set_window(mdk_ctx *ctx, double L_behind, double L_ahead, const double *
 /* Ids of the atoms present, ascending (the order of every per-atom output). */
 int mdk_get_ids(mdk_ctx *ctx, int64_t *ids);
 
+/*
+ * Langevin thermostat regions (Sec. "Molecular dynamics": a Langevin force
+ * added to the right-hand side of Eq. MD-system gives the NVT ensemble;
+ * Sec. "Moving window simulation": thermostats with a target temperature, a
+ * target mean velocity and a stiffness beta in the inflow and outflow
+ * regions).  At every force evaluation of mdk_step, an atom whose x lies in
+ * region r (the first with x_lo[r] <= x < x_hi[r], piston atoms excluded)
+ * gets, per component,
+ *   F += -beta m (v - u_r) / A + sqrt(24 beta m k_B T_r / (dt A)) (xi - 1/2)
+ * with v its half-step velocity, A = 9.648533212331e-3 (Angstrom/fs^2 per
+ * eV/(Angstrom u)), k_B = 8.617333262e-5 eV/K, and xi uniform on [0, 1):
+ * component d of Philox4x64-10 (Salmon et al., SC 2011) with counter
+ * (permanent atom id, step index, 0, 0) and key (seed, 0), as (out >> 11)
+ * 2^-53.  The step index counts the force evaluations of mdk_step since
+ * mdk_set_state.  mdk_compute returns conservative forces only.
+ *   n_regions   : 0 (off) to 8
+ *   x_lo, x_hi  : host [n_regions], Angstrom
+ *   T           : host [n_regions], K, >= 0
+ *   u           : host [n_regions][3], Angstrom/fs
+ *   beta        : host [n_regions], 1/fs, >= 0
+ * Errors: MDK_ERR_BAD_ARG.  Takes effect at the next mdk_step.
+ */
+int mdk_set_langevin(mdk_ctx *ctx, int n_regions, const double *x_lo, const double *x_hi,
+                     const double *T, const double *u, const double *beta, uint64_t seed);
+
 /* Atoms appended and deleted by the moving window so far (synchronises). */
 int mdk_window_counts(mdk_ctx *ctx, int64_t *inserted, int64_t *deleted);
 

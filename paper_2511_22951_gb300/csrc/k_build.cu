@@ -39,7 +39,10 @@ __device__ __forceinline__ bool flag_on(const Sys &s) {
 __global__ void k_pre(Sys s, int count_step, int use_cond, cudaGraphConditionalHandle h) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   DevStatus *st = s.st;
-  if (count_step) st->since_build += 1;
+  if (count_step) {
+    st->since_build += 1;
+    st->n_steps += 1;  // index of the force evaluation that follows (Langevin noise)
+  }
   if (s.rebuild_every > 0 && st->since_build >= s.rebuild_every) st->rebuild = 1;
   // the window acts at builds that stepping triggers, not at explicit builds
   st->win_active = (s.win_on && count_step && st->rebuild) ? 1 : 0;

@@ -289,6 +289,57 @@ __device__ __forceinline__ void drift_publish(const Sys &s, const StepArgs &a, i
          inf);
 }
 
+// Philox4x64-10 (Salmon, Moraes, Dror and Shaw, SC 2011): ten rounds of two
+// 64x64 -> 128-bit products on the counter, key bumped by Weyl constants.
+__device__ __forceinline__ void philox4x64(unsigned long long c[4], unsigned long long k0,
+                                           unsigned long long k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B97F4A7C15ULL;
+      k1 += 0xBB67AE8584CAA73BULL;
+    }
+    const unsigned long long m0 = 0xD2E7470EE14C6C93ULL, m1 = 0xCA5A826395121157ULL;
+    const unsigned long long hi0 = __umul64hi(m0, c[0]), lo0 = m0 * c[0];
+    const unsigned long long hi1 = __umul64hi(m1, c[2]), lo1 = m1 * c[2];
+    const unsigned long long n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// Langevin force of atom i (FP64, once per atom and step; regions along x at
+// the new positions, half-step velocity in s.v):
+//   F += -beta m (v - u) / A + sqrt(24 beta m k_B T / (dt A)) (xi - 1/2),
+// xi uniform on [0, 1) from Philox4x64-10 with counter (id, step) and key
+// (seed, 0).  Rounded step by step so that the oracle's arithmetic matches.
+__device__ __forceinline__ void langevin(const Sys &s, const StepArgs &a, int i, int type,
+                                         double &Fx, double &Fy, double &Fz) {
+  const size_t Nc = s.N_cap;
+  const double x = s.x[i];
+  int r = -1;
+  for (int q = 0; q < s.n_lang && r < 0; ++q)
+    if (x >= s.lang_xlo[q] && x < s.lang_xhi[q]) r = q;
+  if (r < 0) return;
+  unsigned long long c[4] = {(unsigned long long)s.id[i],
+                             (unsigned long long)s.st->n_steps, 0ull, 0ull};
+  philox4x64(c, s.lang_seed, 0ull);
+  const double m = s.mass[type], beta = s.lang_beta[r];
+  const double sigma = __dsqrt_rn(__ddiv_rn(
+      __dmul_rn(__dmul_rn(__dmul_rn(24.0, beta), m), s.lang_kT[r]), __dmul_rn(a.dt, kAcc)));
+  const double fb = __dmul_rn(-beta, m);
+  double *F[3] = {&Fx, &Fy, &Fz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double xi = __dmul_rn((double)(c[d] >> 11), 0x1.0p-53);
+    const double fr = __ddiv_rn(__dmul_rn(fb, __dadd_rn(s.v[d * Nc + i], -s.lang_u[r][d])), kAcc);
+    const double fn = __dmul_rn(sigma, __dadd_rn(xi, -0.5));
+    *F[d] = __dadd_rn(__dadd_rn(*F[d], fr), fn);
+  }
+}
+
 template <class P, int MODE, bool ENERGY>
 __device__ __forceinline__ void epilogue(const Sys &s, const StepArgs &a, int i, uint32_t inf,
                                          double Fx, double Fy, double Fz) {
@@ -302,6 +353,7 @@ __device__ __forceinline__ void epilogue(const Sys &s, const StepArgs &a, int i,
   }
   const int type = inf & 15u;
   const bool piston = (inf & kInfoPiston) != 0;
+  if (s.n_lang > 0 && !piston) langevin(s, a, i, type, Fx, Fy, Fz);
   const double c = 0.5 * a.dt * s.acc_over_m[type];
   double vx = s.v[i], vy = s.v[Nc + i], vz = s.v[2 * Nc + i];
   if (piston) {

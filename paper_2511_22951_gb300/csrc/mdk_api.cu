@@ -80,6 +80,11 @@ struct mdk_ctx {
   int64_t win_slab_cap = 0;      // slab atoms the workspace has room for
   double *win_slab_dev = nullptr;
   double win_front_bin = 1.0;
+  // Langevin regions (mdk_set_langevin)
+  int lang_n = 0;
+  double lang_xlo[kMaxLang] = {0}, lang_xhi[kMaxLang] = {0}, lang_kT[kMaxLang] = {0},
+         lang_beta[kMaxLang] = {0}, lang_u[kMaxLang][3] = {{0}};
+  unsigned long long lang_seed = 0;
   int win_nbins = 1;             // front bins over the box along x
   int win_nbins_cap = 0;         // bins the workspace has room for
   long long *win_fbin = nullptr;
@@ -288,6 +293,15 @@ void fill_sys_params(mdk_ctx *c) {
   s.win_xlo = c->lo[0];
   s.win_xhi = c->hi[0];
   s.front_bin = c->win_front_bin;
+  s.n_lang = c->lang_n;
+  for (int q = 0; q < kMaxLang; ++q) {
+    s.lang_xlo[q] = c->lang_xlo[q];
+    s.lang_xhi[q] = c->lang_xhi[q];
+    s.lang_kT[q] = c->lang_kT[q];
+    s.lang_beta[q] = c->lang_beta[q];
+    for (int d = 0; d < 3; ++d) s.lang_u[q][d] = c->lang_u[q][d];
+  }
+  s.lang_seed = c->lang_seed;
   s.n_fbins = c->win_nbins;
   s.fbin = c->win_fbin;
 }
@@ -319,6 +333,7 @@ __global__ void k_init_status(Sys s, int N) {
     st->next_id = N;
     st->n_inserted = 0;
     st->n_deleted = 0;
+    st->n_steps = 0;
   }
 }
 
@@ -1387,6 +1402,29 @@ int mdk_set_window(mdk_ctx *c, double L_behind, double L_ahead, const double *sl
                          cudaMemcpyHostToDevice, c->stream));
   fill_sys_params(c);
   MDK_CK(cudaStreamSynchronize(c->stream));
+  return MDK_OK;
+}
+
+int mdk_set_langevin(mdk_ctx *c, int n_regions, const double *x_lo, const double *x_hi,
+                     const double *T, const double *u, const double *beta, uint64_t seed) {
+  if (check_ctx(c) || n_regions < 0 || n_regions > kMaxLang) return MDK_ERR_BAD_ARG;
+  if (n_regions > 0 && (!x_lo || !x_hi || !T || !u || !beta)) return MDK_ERR_BAD_ARG;
+  for (int q = 0; q < n_regions; ++q)
+    if (!(x_lo[q] < x_hi[q]) || !(T[q] >= 0.0) || !(beta[q] >= 0.0) ||
+        !(isfinite(u[3 * q]) && isfinite(u[3 * q + 1]) && isfinite(u[3 * q + 2])))
+      return MDK_ERR_BAD_ARG;
+  const double kB = 8.617333262e-5;  // eV/K
+  c->lang_n = n_regions;
+  for (int q = 0; q < kMaxLang; ++q) {
+    const bool on = q < n_regions;
+    c->lang_xlo[q] = on ? x_lo[q] : 0.0;
+    c->lang_xhi[q] = on ? x_hi[q] : 0.0;
+    c->lang_kT[q] = on ? kB * T[q] : 0.0;
+    c->lang_beta[q] = on ? beta[q] : 0.0;
+    for (int d = 0; d < 3; ++d) c->lang_u[q][d] = on ? u[3 * q + d] : 0.0;
+  }
+  c->lang_seed = seed;
+  if (c->ws_ok) fill_sys_params(c);
   return MDK_OK;
 }
 

@@ -27,6 +27,7 @@ namespace mdk {
 constexpr double kAcc = 9.648533212331e-3;
 
 constexpr int kMaxTypes = 16;
+constexpr int kMaxLang = 8;  // Langevin regions
 constexpr uint32_t kJMask = (1u << 26) - 1u;
 constexpr uint32_t kInfoPiston = 1u << 4;
 constexpr uint32_t kInfoFar = 1u << 5;
@@ -114,6 +115,12 @@ struct Sys {
   double L_behind, L_ahead, slab_lx, slab_gap, piston_depth;
   const double *slab;             // fresh slab: [n_slab][6] = x, y, z, vx, vy, vz
   uint32_t slab_info;             // info word of appended atoms
+  // Langevin thermostat regions along x (n_lang = 0: off): x in
+  // [lang_xlo, lang_xhi), k_B T (eV), target mean velocity, stiffness (1/fs)
+  int n_lang;
+  double lang_xlo[kMaxLang], lang_xhi[kMaxLang], lang_kT[kMaxLang], lang_beta[kMaxLang];
+  double lang_u[kMaxLang][3];
+  unsigned long long lang_seed;
   double win_xlo, win_xhi;        // the box along x
   double front_bin;               // width of the bins that locate the front
   int n_fbins;                    // bins over [win_xlo, win_xhi)

@@ -75,6 +75,7 @@ SIGNATURES = {
     "mdk_get_profile": [_P, _P],
     "mdk_lj_compute_noalloc": [_P, _I64, _P, _P, _P, _D, _D, _D, _I, _P, _P, _P],
     "mdk_eam_vjp": [_P, _P, _P, _P, _I],
+    "mdk_set_langevin": [_P, _I, _P, _P, _P, _P, _P, ctypes.c_uint64],
 }
 
 _lib = None
@@ -408,6 +409,18 @@ class Context:
         _check(self.lib.mdk_window_counts(self.h, ctypes.byref(a), ctypes.byref(b)),
                "mdk_window_counts")
         return int(a.value), int(b.value)
+
+    def set_langevin(self, regions, seed=0):
+        """regions = [(x_lo, x_hi, T, (u_x, u_y, u_z), beta), ...] (<= 8; [] = off)."""
+        n = len(regions)
+        xl = np.array([r[0] for r in regions], dtype=np.float64)
+        xh = np.array([r[1] for r in regions], dtype=np.float64)
+        T = np.array([r[2] for r in regions], dtype=np.float64)
+        u = np.array([r[3] for r in regions], dtype=np.float64).reshape(n, 3)
+        b = np.array([r[4] for r in regions], dtype=np.float64)
+        _check(self.lib.mdk_set_langevin(self.h, n, _ptr(xl), _ptr(xh), _ptr(T), _ptr(u),
+                                         _ptr(b), int(seed)), "mdk_set_langevin")
+        self.version += 1
 
     def set_piston(self, u_p, flags):
         f = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8)

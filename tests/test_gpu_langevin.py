@@ -1,0 +1,116 @@
+"""Langevin thermostat regions on the GPU (mdk_set_langevin) against the
+oracle (tests/test_oracle_langevin.py pins the oracle).
+
+Bars: the noise is the same Philox4x64-10 stream on both sides (counter =
+atom id, step index), and the thermostat arithmetic is rounded in the same
+order, so FP64 trajectories differ only by the conservative forces'
+summation order: positions within 1e-9 Angstrom and velocities within
+1e-11 Angstrom/fs after 10 steps.  The mixed path is checked statistically:
+a free gas settles at the target temperature and drift velocity.
+"""
+import numpy as np
+import pytest
+
+from paper_2511_22951_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KB = W.K_B
+ACC = W.EV_PER_A_U_TO_A_PER_FS2
+
+
+@pytest.fixture(scope="module")
+def mdk():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_22951_gb300 import _build, mdk as m
+    _build.build()
+    m.load()
+    return m
+
+
+REGIONS = [(-5.0, 10.5, 50.0, (0.001, 0.0, 0.0), 0.01),
+           (10.5, 30.0, 150.0, (0.0, -0.0005, 0.0), 0.02)]
+
+
+def lj_ctx(mdk, s, prec):
+    lj = W.LJ_AR
+    ctx = mdk.Context(s.lo, s.hi, s.periodic, s.masses, prec)
+    ctx.set_potential_lj(lj.eps, lj.sigma, lj.rc, lj.shift_mode)
+    ctx.plan(lj.rc, 0.3)
+    ctx.set_state(s.x, s.v)
+    ctx.build_neighbors(lj.rc, 0.3)
+    return ctx
+
+
+def test_langevin_trajectory_matches_oracle(mdk, ora):
+    wl = W.config0()
+    s = wl.systems[0]
+    ctx = lj_ctx(mdk, s, "fp64")
+    ctx.set_langevin(REGIONS, seed=7)
+    ctx.step(wl.dt, 10)
+    xg, vg = ctx.get_state()
+    o = ora.md_langevin(s.x, s.v, s.masses, s.lo, s.hi, s.periodic, wl.dt, 10, wl.skin,
+                        REGIONS, seed=7, lj_params=wl.lj)
+    L = s.hi - s.lo
+    d = xg - o["x"]
+    d -= np.rint(d / L) * L
+    assert np.max(np.abs(d)) < 1e-9, np.max(np.abs(d))
+    assert np.max(np.abs(vg - o["v"])) < 1e-11, np.max(np.abs(vg - o["v"]))
+    # the thermostat acted: the same run without it ends elsewhere
+    o0 = ora.md_run(s.x, s.v, s.masses, s.lo, s.hi, s.periodic, wl.dt, 10, wl.skin,
+                    lj_params=wl.lj)
+    assert np.max(np.abs(o0["v"] - o["v"])) > 1e-6
+
+
+def test_graphs_and_eager_steps_agree_with_langevin(mdk):
+    wl = W.config0()
+    s = wl.systems[0]
+    out = []
+    for graphs in (True, False):
+        ctx = lj_ctx(mdk, s, "mixed")
+        ctx.set_graphs(graphs)
+        ctx.set_langevin(REGIONS, seed=3)
+        ctx.step(wl.dt, 12)
+        out.append(ctx.get_state())
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_free_gas_settles_at_T_and_u_mixed(mdk):
+    n_side, spacing = 16, 10.0
+    g = np.arange(n_side) * spacing
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) + 1.0
+    L = n_side * spacing
+    n = x.shape[0]
+    lj = W.LJ_AR
+    ctx = mdk.Context([0.0] * 3, [L] * 3, [1] * 3, np.full(n, lj.mass), "mixed")
+    ctx.set_potential_lj(lj.eps, lj.sigma, lj.rc, lj.shift_mode)
+    ctx.plan(lj.rc, 0.3)
+    ctx.set_state(x, np.zeros((n, 3)))
+    ctx.build_neighbors(lj.rc, 0.3)
+    T, u = 300.0, (0.002, -0.001, 0.0)
+    ctx.set_langevin([(-1e9, 1e9, T, u, 0.02)], seed=5)
+    ctx.step(2.0, 500)
+    Ts, us = [], []
+    for _ in range(6):
+        ctx.step(2.0, 100)
+        _, v = ctx.get_state()
+        dv = v - v.mean(axis=0)
+        Ts.append(lj.mass * np.sum(dv * dv) / (3 * n * KB) / ACC)
+        us.append(v.mean(axis=0))
+    assert np.mean(Ts) == pytest.approx(T, rel=0.03)
+    sd = np.sqrt(KB * T * ACC / lj.mass / n / 6)
+    np.testing.assert_allclose(np.mean(us, axis=0), u, atol=5 * sd)
+
+
+def test_langevin_arguments_are_checked(mdk):
+    wl = W.config0()
+    s = wl.systems[0]
+    ctx = lj_ctx(mdk, s, "fp64")
+    with pytest.raises(mdk.MDKError):
+        ctx.set_langevin([(1.0, 0.0, 300.0, (0, 0, 0), 0.01)])   # empty region
+    with pytest.raises(mdk.MDKError):
+        ctx.set_langevin([(0.0, 1.0, -1.0, (0, 0, 0), 0.01)])    # negative T
+    ctx.set_langevin([])                                         # off
