@@ -280,12 +280,18 @@ int mdk_set_piston(mdk_ctx *ctx, double u_p, const uint8_t *is_piston);
  * The atom count changes: reserve room with mdk_set_capacity (appends that
  * do not fit are dropped and raise MDK_ERR_CAPACITY).  Once a window is
  * set, per-atom outputs come in ascending atom-id order (mdk_get_ids).
+ * fixed_front: NaN to locate the front as above; a finite value fixes the
+ * front at that x instead (the paper's stationary-shock window: outflow
+ * deletion at fixed_front - L_behind, inflow layers -- give slab_v the
+ * inflow velocity -- up to fixed_front + L_ahead; combine with
+ * mdk_set_langevin for the inflow and outflow thermostats).
  * Single-system contexts with a free (non-periodic) x only; front_bin > 0
  * with at most 2^24 bins over the box.  Takes effect at the next list build.
  */
 int mdk_set_window(mdk_ctx *ctx, double L_behind, double L_ahead, const double *slab_x,
                    const double *slab_v, int64_t n_slab, double slab_lx, double slab_gap,
-                   double slab_mass, double piston_depth, double front_bin);
+                   double slab_mass, double piston_depth, double front_bin,
+                   double fixed_front);
 
 /* Ids of the atoms present, ascending (the order of every per-atom output). */
 int mdk_get_ids(mdk_ctx *ctx, int64_t *ids);

@@ -66,11 +66,12 @@ def lib():
         L.ora_md_run.restype = I64
         L.ora_profiles.argtypes = [I64, P, P, P, P, P, I, D, D, I, D, P]
         L.ora_profiles.restype = None
-        L.ora_window_apply.argtypes = [I64, I64, P, P, P, P, P, P, D, D, D, D, D, D, P, P,
-                                       I64, D, D, D, D]
+        L.ora_window_apply.argtypes = [I64, I64, P, P, P, P, P, P, D, D, D, D, D, D, D, P,
+                                       P, I64, D, D, D, D]
         L.ora_window_apply.restype = I64
         L.ora_md_window.argtypes = [P, I64, P, P, P, P, P, P, P, P, P, I, D, P, P, I, D, P, D,
-                                    D, I64, I, D, D, D, D, P, P, I64, D, D, D, D]
+                                    D, I64, I, D, D, D, D, D, P, P, I64, D, D, D, D, P,
+                                    ctypes.c_uint64]
         L.ora_md_window.restype = I64
         L.ora_philox4x64.argtypes = [P, P, P]
         L.ora_philox4x64.restype = None
@@ -367,31 +368,39 @@ class WindowState:
 
 
 def window_apply(st, x_lo, x_hi, front_bin, u_p, L_behind, L_ahead, slab_x, slab_v, slab_lx,
-                 slab_gap, slab_mass, piston_depth):
+                 slab_gap, slab_mass, piston_depth, fixed_front=float("nan")):
     """One application of the window rules (x_lo, x_hi: the box along x;
-    front_bin: width of the bins that locate the shock front)."""
+    front_bin: width of the bins that locate the shock front; a finite
+    fixed_front replaces the located front)."""
     sx = _f64(slab_x, (-1, 3))
     sv = _f64(slab_v, (-1, 3))
     st.n = int(lib().ora_window_apply(st.n, st.cap, _p(st.x), _p(st.v), _p(st.m), _p(st.pis),
-                                      _p(st.ids), _p(st.next_id), x_lo, x_hi, front_bin, u_p,
-                                      L_behind, L_ahead, _p(sx), _p(sv), sx.shape[0], slab_lx,
-                                      slab_gap, slab_mass, piston_depth))
+                                      _p(st.ids), _p(st.next_id), x_lo, x_hi, front_bin,
+                                      fixed_front, u_p, L_behind, L_ahead, _p(sx), _p(sv),
+                                      sx.shape[0], slab_lx, slab_gap, slab_mass, piston_depth))
     return st
 
 
 def md_window(st, lo, hi, periodic, tables, dt, nsteps, skin, rebuild_every, u_p, front_bin,
-              L_behind, L_ahead, slab_x, slab_v, slab_lx, slab_gap, slab_mass, piston_depth):
+              L_behind, L_ahead, slab_x, slab_v, slab_lx, slab_gap, slab_mass, piston_depth,
+              fixed_front=float("nan"), regions=None, seed=0):
     lo, hi, per = _box(lo, hi, periodic)
     phi, rho, Ft = _f64(tables.phi), _f64(tables.rho), _f64(tables.F)
     sx = _f64(slab_x, (-1, 3))
     sv = _f64(slab_v, (-1, 3))
+    lp = None
+    if regions is not None:
+        lp = [float(len(regions))]
+        for (xl, xh, T, u, beta) in regions:
+            lp += [xl, xh, T, u[0], u[1], u[2], beta]
+        lp = _f64(lp)
     n = np.array([st.n], dtype=np.int64)
     nb = lib().ora_md_window(_p(n), st.cap, _p(st.x), _p(st.v), _p(st.m), _p(st.pis),
                              _p(st.ids), _p(st.next_id), _p(lo), _p(hi), _p(per), phi.shape[0],
                              tables.rc, _p(phi), _p(rho), Ft.shape[0], tables.rho_max, _p(Ft),
-                             skin, dt, nsteps, rebuild_every, u_p, front_bin, L_behind,
-                             L_ahead, _p(sx),
-                             _p(sv), sx.shape[0], slab_lx, slab_gap, slab_mass, piston_depth)
+                             skin, dt, nsteps, rebuild_every, u_p, front_bin, fixed_front,
+                             L_behind, L_ahead, _p(sx), _p(sv), sx.shape[0], slab_lx, slab_gap,
+                             slab_mass, piston_depth, _p(lp), int(seed))
     if nb < 0:
         raise RuntimeError(f"oracle md_window failed ({nb})")
     st.n = int(n[0])

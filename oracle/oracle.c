@@ -1144,11 +1144,15 @@ void ora_profiles(int64_t N, const double *x, const double *v, const double *mas
  *   capacity allows;
  *   atoms with x < x_min + piston_depth (x_min over the atoms left) become
  *   piston atoms.
+ * With a finite fixed_front the front is that x instead (the paper's
+ * stationary-shock window: outflow deletion at fixed_front - L_behind and
+ * inflow layers up to fixed_front + L_ahead, whatever the velocities).
  * Returns the new atom count.
  */
 int64_t ora_window_apply(int64_t N, int64_t cap, double *x, double *v, double *mass,
                          uint8_t *piston, int64_t *ids, int64_t *next_id, double x_lo,
-                         double x_hi, double front_bin, double u_p, double L_behind,
+                         double x_hi, double front_bin, double fixed_front, double u_p,
+                         double L_behind,
                          double L_ahead, const double *slab_x, const double *slab_v,
                          int64_t n_slab, double slab_lx, double slab_gap, double slab_mass,
                          double piston_depth) {
@@ -1176,8 +1180,13 @@ int64_t ora_window_apply(int64_t N, int64_t cap, double *x, double *v, double *m
         }
     free(S);
     free(cnt);
-    if (bf < 0) return N;
-    double x_front = x_lo + (double)(bf + 1) * front_bin;
+    double x_front;
+    if (isfinite(fixed_front)) {
+        x_front = fixed_front;  /* stationary window: boundaries fixed in the box */
+    } else {
+        if (bf < 0) return N;
+        x_front = x_lo + (double)(bf + 1) * front_bin;
+    }
     double cut = x_front - L_behind;
     int64_t n = 0;
     for (int64_t i = 0; i < N; ++i) {
@@ -1231,11 +1240,32 @@ int64_t ora_md_window(int64_t *n_io, int64_t cap, double *x, double *v, double *
                       const double *hi, const int *per, int nr, double rc_eam,
                       const double *phi, const double *rho, int nrho, double rho_max,
                       const double *Ftab, double skin, double dt, int64_t nsteps,
-                      int rebuild_every, double u_p, double front_bin, double L_behind,
-                      double L_ahead, const double *slab_x, const double *slab_v,
-                      int64_t n_slab, double slab_lx, double slab_gap, double slab_mass,
-                      double piston_depth) {
+                      int rebuild_every, double u_p, double front_bin, double fixed_front,
+                      double L_behind, double L_ahead, const double *slab_x,
+                      const double *slab_v, int64_t n_slab, double slab_lx, double slab_gap,
+                      double slab_mass, double piston_depth, const double *lang_par,
+                      uint64_t seed) {
     int64_t N = *n_io;
+    ora_langevin lg;
+    memset(&lg, 0, sizeof(lg));
+    const ora_langevin *lgp = NULL;
+    if (lang_par) {
+        lg.n = (int)lang_par[0];
+        if (lg.n < 0 || lg.n > 8) return -3;
+        for (int q = 0; q < lg.n; ++q) {
+            const double *r = lang_par + 1 + 7 * q;
+            lg.xlo[q] = r[0];
+            lg.xhi[q] = r[1];
+            lg.T[q] = r[2];
+            lg.u[q][0] = r[3];
+            lg.u[q][1] = r[4];
+            lg.u[q][2] = r[5];
+            lg.beta[q] = r[6];
+        }
+        lg.seed = seed;
+        lg.ids = ids;
+        lgp = &lg;
+    }
     ora_box b = make_box(lo, hi, per);
     ora_pot p;
     pot_eam_init(&p, nr, rc_eam, phi, rho, nrho, rho_max, Ftab);
@@ -1264,13 +1294,14 @@ int64_t ora_md_window(int64_t *n_io, int64_t cap, double *x, double *v, double *
         }
         if (((step + 1) % rebuild_every) == 0) {
             N = ora_window_apply(N, cap, x, v, mass, piston, ids, next_id, lo[0], hi[0],
-                                 front_bin, u_p, L_behind, L_ahead, slab_x, slab_v, n_slab,
-                                 slab_lx, slab_gap, slab_mass, piston_depth);
+                                 front_bin, fixed_front, u_p, L_behind, L_ahead, slab_x,
+                                 slab_v, n_slab, slab_lx, slab_gap, slab_mass, piston_depth);
             ora_wrap(N, x, lo, hi, per);
             if (vlist_build(&vl, N, x, &b, rns) != 0) return -2;
             ++nbuild;
         }
         forces_from_list(&p, N, x, &b, vl.off, vl.j, vl.n, &E, F, W, NULL, NULL, NULL, NULL);
+        if (lgp) langevin_forces(lgp, N, x, v, mass, piston, dt, step + 1, F);
         for (int64_t i = 0; i < N; ++i) {
             if (piston[i]) continue;
             double c = 0.5 * dt * ORA_ACC / mass[i];

@@ -120,8 +120,10 @@ __global__ void __launch_bounds__(kBlk) k_win_plan(Sys s) {
   st->win_n_old = st->N;
   st->win_insert = 0;
   st->win_cut = -INFINITY;
-  if (best < 0) return;
-  const double front = __dadd_rn(s.win_xlo, __dmul_rn((double)(best + 1), s.front_bin));
+  const bool fixed = isfinite(s.fixed_front);
+  if (best < 0 && !fixed) return;
+  const double front =
+      fixed ? s.fixed_front : __dadd_rn(s.win_xlo, __dmul_rn((double)(best + 1), s.front_bin));
   st->win_cut = front - s.L_behind;
   const double need = front + s.L_ahead - xmax;
   long long copies = need > 0.0 ? (long long)ceil(need / s.slab_lx) : 0;

@@ -80,6 +80,7 @@ struct mdk_ctx {
   int64_t win_slab_cap = 0;      // slab atoms the workspace has room for
   double *win_slab_dev = nullptr;
   double win_front_bin = 1.0;
+  double win_fixed_front = NAN;
   // Langevin regions (mdk_set_langevin)
   int lang_n = 0;
   double lang_xlo[kMaxLang] = {0}, lang_xhi[kMaxLang] = {0}, lang_kT[kMaxLang] = {0},
@@ -293,6 +294,7 @@ void fill_sys_params(mdk_ctx *c) {
   s.win_xlo = c->lo[0];
   s.win_xhi = c->hi[0];
   s.front_bin = c->win_front_bin;
+  s.fixed_front = c->win_fixed_front;
   s.n_lang = c->lang_n;
   for (int q = 0; q < kMaxLang; ++q) {
     s.lang_xlo[q] = c->lang_xlo[q];
@@ -1363,7 +1365,8 @@ int mdk_get_profile(mdk_ctx *c, double *out) {
 
 int mdk_set_window(mdk_ctx *c, double L_behind, double L_ahead, const double *slab_x,
                    const double *slab_v, int64_t n_slab, double slab_lx, double slab_gap,
-                   double slab_mass, double piston_depth, double front_bin) {
+                   double slab_mass, double piston_depth, double front_bin,
+                   double fixed_front) {
   if (check_ctx(c) || c->n_rep != 1 || !slab_x || !slab_v || n_slab < 1 ||
       n_slab >= ((int64_t)1 << 26) || !(slab_lx > 0.0) || !(L_behind >= 0.0) ||
       !(L_ahead >= 0.0) || !isfinite(slab_gap) || !(slab_mass > 0.0) || !(piston_depth >= 0.0) ||
@@ -1385,6 +1388,7 @@ int mdk_set_window(mdk_ctx *c, double L_behind, double L_ahead, const double *sl
   c->win_depth = piston_depth;
   c->win_info = (uint32_t)t;
   c->win_front_bin = front_bin;
+  c->win_fixed_front = fixed_front;
   c->win_nbins = std::max(1, (int)nb);
   c->win_slab.assign((size_t)n_slab * 6, 0.0);
   for (int64_t q = 0; q < n_slab; ++q)

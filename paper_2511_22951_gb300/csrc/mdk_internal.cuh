@@ -123,6 +123,7 @@ struct Sys {
   unsigned long long lang_seed;
   double win_xlo, win_xhi;        // the box along x
   double front_bin;               // width of the bins that locate the front
+  double fixed_front;             // finite: the front's x, fixed (stationary window)
   int n_fbins;                    // bins over [win_xlo, win_xhi)
   long long *fbin;                // [2 n_fbins]: sum of q(v_x), atom count per bin
 };

@@ -62,7 +62,7 @@ SIGNATURES = {
     "mdk_get_thermo": [_P, _P, _I, ctypes.POINTER(_I)],
     "mdk_get_counters": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "mdk_set_piston": [_P, _D, _P],
-    "mdk_set_window": [_P, _D, _D, _P, _P, _I64, _D, _D, _D, _D, _D],
+    "mdk_set_window": [_P, _D, _D, _P, _P, _I64, _D, _D, _D, _D, _D, _D],
     "mdk_get_ids": [_P, _P],
     "mdk_window_counts": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "mdk_profiles": [_P, _I, _D, _D, _I, _D, _P, _I],
@@ -386,11 +386,11 @@ class Context:
         return dict(zip(keys, out.tolist()))
 
     def set_window(self, L_behind, L_ahead, slab_x, slab_v, slab_lx, slab_gap, slab_mass,
-                   piston_depth, front_bin):
+                   piston_depth, front_bin, fixed_front=float("nan")):
         sx = _host_f64(slab_x, (-1, 3))
         sv = _host_f64(slab_v, (-1, 3))
         args = (L_behind, L_ahead, _ptr(sx), _ptr(sv), sx.shape[0], slab_lx, slab_gap,
-                slab_mass, piston_depth, front_bin)
+                slab_mass, piston_depth, front_bin, fixed_front)
         r = self.lib.mdk_set_window(self.h, *args)
         if r == MDK_ERR_WORKSPACE:
             self.alloc_workspace()

@@ -114,3 +114,49 @@ def test_langevin_arguments_are_checked(mdk):
     with pytest.raises(mdk.MDKError):
         ctx.set_langevin([(0.0, 1.0, -1.0, (0, 0, 0), 0.01)])    # negative T
     ctx.set_langevin([])                                         # off
+
+
+def test_stationary_window_with_thermostats_matches_oracle(mdk, ora):
+    """The paper's stationary-shock window: material flows in at u_in (< 0)
+    through fixed inflow and outflow boundaries (outflow deletion at
+    x_front - L_behind, fresh layers up to x_front + L_ahead), with Langevin
+    thermostats at the inflow (T0, u_in) and outflow (u_out) ends.  FP64,
+    Al-like slab, rebuild every 5 steps; ids, positions and velocities equal
+    the oracle's window run after 12 steps."""
+    wl = W.config3(ncx=12, ncyz=3)
+    s = wl.systems[0]
+    a = wl.extra["a"]
+    u_in, u_out = -0.01, -0.004
+    v = s.v.copy()
+    v[:, 0] += u_in
+    rng = np.random.default_rng(9)
+    sx = W.fcc_lattice(2, 3, 3, a)
+    sv = W.maxwell_velocities(rng, np.full(sx.shape[0], W.MASS_AL), 300.0)
+    sv[:, 0] += u_in
+    slx, gap, Lb, La, xf = 2 * a, 0.5 * a, 12.0, 32.0, 20.0
+    regions = [(s.lo[0], 14.0, 300.0, (u_out, 0.0, 0.0), 0.02),
+               (40.0, s.hi[0], 300.0, (u_in, 0.0, 0.0), 0.02)]
+    cap = 4000
+    ctx = mdk.Context(s.lo, s.hi, s.periodic, s.masses, "fp64", capacity=cap)
+    ctx.set_potential_eam(wl.tables)
+    ctx.plan(wl.tables.rc, 0.3, rebuild_every=5)
+    ctx.set_state(s.x, v)
+    ctx.build_neighbors(wl.tables.rc, 0.3)
+    ctx.set_window(Lb, La, sx, sv, slx, gap, W.MASS_AL, 0.0, 3.0, fixed_front=xf)
+    ctx.set_langevin(regions, seed=21)
+    ctx.step(0.5, 12)
+    xg, vg = ctx.get_state()
+    ids = ctx.ids()
+    ins, dele = ctx.window_counts()
+    st = ora.WindowState(s.x, v, s.masses, np.zeros(s.n, dtype=bool), cap)
+    ora.md_window(st, s.lo, s.hi, s.periodic, wl.tables, 0.5, 12, 0.3, 5, 0.0, 3.0, Lb, La,
+                  sx, sv, slx, gap, W.MASS_AL, 0.0, fixed_front=xf, regions=regions, seed=21)
+    o = st.view()
+    order = np.argsort(o["ids"])
+    np.testing.assert_array_equal(ids, o["ids"][order])
+    assert ins > 0 and dele > 0
+    L = s.hi - s.lo
+    d = xg - o["x"][order]
+    d[:, 1:] -= np.rint(d[:, 1:] / L[1:]) * L[1:]
+    assert np.max(np.abs(d)) < 1e-9
+    np.testing.assert_allclose(vg, o["v"][order], rtol=0, atol=1e-11)

@@ -121,3 +121,26 @@ def test_window_md_run_counts(ora):
     assert len(np.unique(v["ids"])) == st.n
     assert st.n != n0
     np.testing.assert_allclose(v["v"][v["piston"]], [[0.015, 0, 0]] * v["piston"].sum())
+
+
+def test_fixed_front_window(ora):
+    """The paper's stationary-shock window: boundaries fixed in the box, the
+    same rules with the front given instead of located (velocities play no
+    part)."""
+    st, s = state(ora)
+    st.v[:st.n] = 0.0
+    st.pis[:] = 0
+    sx, sv, slx = slab()
+    before = st.view()
+    n0 = st.n
+    x_front, L_behind, L_ahead, gap = 25.0, 8.0, 40.0, 0.5 * A
+    x_max = before["x"][:, 0].max()
+    ora.window_apply(st, s.lo[0], s.hi[0], BIN, 0.015, L_behind, L_ahead, sx, sv, slx, gap,
+                     W.MASS_AL, 0.0, fixed_front=x_front)
+    after = st.view()
+    kept = before["x"][:, 0] >= x_front - L_behind
+    copies = int(np.ceil((x_front + L_ahead - x_max) / slx))
+    assert copies > 0 and kept.sum() < n0
+    assert st.n == kept.sum() + copies * sx.shape[0]
+    assert after["x"][:, 0].min() >= x_front - L_behind
+    assert not after["piston"].any()  # depth 0: no piston layer
