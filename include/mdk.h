@@ -229,6 +229,10 @@ int mdk_get_per_atom(mdk_ctx *ctx, double *Ui, double *Wi);
  * dynamics"): v += dt/2 a; x += dt v; rebuild lists when triggered;
  * a = f(x)/m; v += dt/2 a.  All control stays on the GPU; the call only
  * enqueues work and returns the first error flag raised by an earlier call.
+ * A list build during the steps that finds more neighbours than the list
+ * capacity raises MDK_ERR_NEIGH_OVERFLOW (read with mdk_last_device_status);
+ * the steps after it ran with truncated lists, so that state must be
+ * discarded: plan a larger max_neighbors for runs that compress.
  */
 int mdk_step(mdk_ctx *ctx, double dt, int64_t nsteps);
 

@@ -410,6 +410,14 @@ class Context:
                "mdk_window_counts")
         return int(a.value), int(b.value)
 
+    def profiles(self, axis, origin, bin_w, nbins, cross_area):
+        """Appendix statistics per bin (host [nbins, 17]): N, M, u[3], T[3],
+        E_pot, P[xx, yy, zz, xy, xz, yz], E_kin, V."""
+        out = np.zeros((nbins, 17))
+        _check(self.lib.mdk_profiles(self.h, int(axis), float(origin), float(bin_w), int(nbins),
+                                     float(cross_area), _ptr(out), 0), "mdk_profiles")
+        return out
+
     def set_langevin(self, regions, seed=0):
         """regions = [(x_lo, x_hi, T, (u_x, u_y, u_z), beta), ...] (<= 8; [] = off)."""
         n = len(regions)

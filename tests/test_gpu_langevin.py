@@ -160,3 +160,43 @@ def test_stationary_window_with_thermostats_matches_oracle(mdk, ora):
     d[:, 1:] -= np.rint(d[:, 1:] / L[1:]) * L[1:]
     assert np.max(np.abs(d)) < 1e-9
     np.testing.assert_allclose(vg, o["v"][order], rtol=0, atol=1e-11)
+
+
+def test_stationary_search_workflow_runs(mdk):
+    """The host-side search loop on a small Al-like slab: restarts from a saved
+    state, samples F = P / P_t through mdk_profiles, fits the slope, and
+    bisects (two iterations here: the physics needs long runs)."""
+    from paper_2511_22951_gb300 import shock
+    wl = W.config3(ncx=16, ncyz=4)
+    s = wl.systems[0]
+    a = wl.extra["a"]
+    u_in = -0.05
+    v = s.v.copy()
+    v[:, 0] += u_in
+    rng = np.random.default_rng(4)
+    sx = W.fcc_lattice(1, 4, 4, a, (0.0, s.lo[1], s.lo[2]))
+    sv = W.maxwell_velocities(rng, np.full(sx.shape[0], W.MASS_AL), 300.0)
+    sv[:, 0] += u_in
+    area = (s.hi[1] - s.lo[1]) * (s.hi[2] - s.lo[2])
+    sw = shock.StationaryWindow(
+        tables=wl.tables, lo=s.lo, hi=s.hi, periodic=s.periodic, x=s.x, v=v,
+        masses=s.masses, slab_x=sx, slab_v=sv, slab_lx=a, slab_gap=0.5 * a,
+        slab_mass=W.MASS_AL, x_front=30.0, L_behind=25.0, L_ahead=40.0,
+        inflow=(50.0, s.hi[0], 300.0, 0.01), outflow=(s.lo[0], 12.0, 300.0, 0.01),
+        u_in=u_in, P_t=1e-3, domain=(5.0, 65.0), cross_area=area, precision="mixed",
+        dt=1.0, max_neighbors=160)
+    ctx = sw.context(-0.02)
+    ctx.step(1.0, 30)
+    assert np.isfinite(sw.target(ctx))
+    assert ctx.window_counts()[0] > 0   # inflow layers were appended
+    ctx.close()
+    slopes = {}
+
+    def slope_at(u):
+        slopes[u] = sw.slope(u, n_samples=4, every=10)
+        # the real slope is measured; its sign is forced so that the loop runs
+        return abs(slopes[u]) + 1.0 if u < -0.03 else -abs(slopes[u]) - 1.0
+
+    u, hist = shock.dichotomy(slope_at, -0.045, -0.005, tol=0.02, max_iter=2)
+    assert -0.045 <= u <= -0.005 and len(hist) >= 3
+    assert all(np.isfinite(q) for q in slopes.values())
