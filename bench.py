@@ -213,6 +213,28 @@ def drift_run(mdk, wl, prec, steps, every=100):
             "E_per_atom_first_last": [float(e[0]), float(e[-1])]}
 
 
+def stationary_setup(ctx, wl, u_in=-0.05, u_p=0.015):
+    """The paper's stationary-shock window on the slab: material flows in at
+    u_in through a fixed inflow boundary (fresh 300 K layers up to the right
+    end of the slab), leaves through a fixed outflow boundary, and Langevin
+    thermostats hold the inflow end at (u_in, 300 K) and the outflow end at
+    u_out = u_in + u_p."""
+    s = wl.systems[0]
+    a = wl.extra["a"]
+    ncyz = int(round((s.hi[1] - s.lo[1]) / a))
+    x_end = float(s.x[:, 0].max())
+    sx = W.fcc_lattice(1, ncyz, ncyz, a, (0.0, s.lo[1], s.lo[2]))
+    sv = W.maxwell_velocities(np.random.default_rng(1), np.full(sx.shape[0], wl.eam.mass), 300.0)
+    sv[:, 0] += u_in
+    x_front, L_ahead, L_behind = x_end - 150.0, 150.0 + 0.25 * a, x_end - 300.0
+    ctx.set_window(L_behind, L_ahead, sx, sv, a, 0.5 * a, wl.eam.mass, 0.0, a,
+                   fixed_front=x_front)
+    ctx.set_langevin([(s.lo[0], 150.0, 300.0, (u_in + u_p, 0.0, 0.0), 0.01),
+                      (x_front, s.hi[0], 300.0, (u_in, 0.0, 0.0), 0.01)], seed=1)
+    return {"u_in_A_per_fs": u_in, "u_out_A_per_fs": u_in + u_p, "x_front_A": x_front,
+            "L_behind_A": L_behind, "L_ahead_A": L_ahead}
+
+
 def reference_forces(mdk, wl, x):
     """F_ref of the force-matching loss: the analytic FS-EAM, evaluated through
     tables at the largest knot count the library takes (7168), far finer than
@@ -360,6 +382,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--vjps", type=int, default=100, help="adjoint calls timed (config 4)")
+    ap.add_argument("--stationary", action="store_true",
+                    help="config 3 as the paper's stationary-shock window (inflow/outflow)")
     ap.add_argument("--langevin", default=None,
                     help="T,beta: a Langevin thermostat on the whole system (K, 1/fs)")
     ap.add_argument("--launch", default=None,
@@ -393,12 +417,21 @@ def main():
     prec = args.precision or wl.precision
     n_atoms = wl.n_atoms
     windowed = args.config == 3
+    if args.stationary:
+        if not windowed:
+            raise SystemExit("--stationary applies to the slab (--config 3)")
+        for q in wl.systems:
+            q.v[:, 0] += -0.05           # the material flows in at u_in
     ctx = mdk.make_context(wl, precision=prec,
-                           capacity=int(n_atoms * 1.1) if windowed else None)
+                           capacity=int(n_atoms * 1.1) if windowed else None,
+                           max_neighbors=120 if args.stationary else 0)
     stream = ctx.stream
     n_avg = float(ctx.neighbor_counts().mean())
     n_rc = pair_count_within_rc(ctx, wl) if rank == 0 else 0.0
-    if windowed:
+    stationary = None
+    if args.stationary:
+        stationary = stationary_setup(ctx, wl)
+    elif windowed:
         window_setup(ctx, wl)
     lang = None
     if args.langevin:
@@ -540,8 +573,11 @@ def main():
         del ctx
         torch.cuda.empty_cache()
         c64 = mdk.make_context(wl, precision="fp64",
-                               capacity=int(n_atoms * 1.1) if windowed else None)
-        if windowed:
+                               capacity=int(n_atoms * 1.1) if windowed else None,
+                               max_neighbors=120 if args.stationary else 0)
+        if args.stationary:
+            stationary_setup(c64, wl)
+        elif windowed:
             window_setup(c64, wl)
         if lang:
             c64.set_langevin(lang, seed=1)
@@ -599,7 +635,9 @@ def main():
         if lang:
             line["config"]["langevin"] = {"T_K": lang[0][2], "beta_per_fs": lang[0][4],
                                           "regions": "whole system"}
-        if windowed:
+        if stationary:
+            line["config"]["stationary_window"] = dict(stationary, atoms_at_end=n_now)
+        elif windowed:
             line["config"]["piston_u_p_A_per_fs"] = wl.extra["u_p"]
             line["config"]["window"] = {"L_behind": wl.extra["L_behind"],
                                         "L_ahead": wl.extra["L_ahead"],

@@ -310,13 +310,17 @@ __device__ __forceinline__ void philox4x64(unsigned long long c[4], unsigned lon
   }
 }
 
-// Langevin force of atom i (FP64, once per atom and step; regions along x at
-// the new positions, half-step velocity in s.v):
-//   F += -beta m (v - u) / A + sqrt(24 beta m k_B T / (dt A)) (xi - 1/2),
+// Langevin force of atom i (once per atom and step; regions along x at the
+// new positions, half-step velocity in s.v):
+//   F += g (v - u) + sigma (xi - 1/2),  g = -beta m / A,
+//   sigma = sqrt(24 beta m k_B T / (dt A)),
 // xi uniform on [0, 1) from Philox4x64-10 with counter (id, step) and key
-// (seed, 0).  Rounded step by step so that the oracle's arithmetic matches.
-__device__ __forceinline__ void langevin(const Sys &s, const StepArgs &a, int i, int type,
-                                         double &Fx, double &Fy, double &Fz) {
+// (seed, 0).  FP64 path: xi = (out >> 11) 2^-53, FP64 arithmetic in the
+// oracle's order.  Mixed path: the thermostat force is computed in FP32 (it
+// is noise and friction, on GB300's fast pipe), xi = (out >> 40) 2^-24.
+template <class P>
+__device__ __forceinline__ void langevin(const Sys &s, int i, int type, double &Fx, double &Fy,
+                                         double &Fz) {
   const size_t Nc = s.N_cap;
   const double x = s.x[i];
   int r = -1;
@@ -326,17 +330,24 @@ __device__ __forceinline__ void langevin(const Sys &s, const StepArgs &a, int i,
   unsigned long long c[4] = {(unsigned long long)s.id[i],
                              (unsigned long long)s.st->n_steps, 0ull, 0ull};
   philox4x64(c, s.lang_seed, 0ull);
-  const double m = s.mass[type], beta = s.lang_beta[r];
-  const double sigma = __dsqrt_rn(__ddiv_rn(
-      __dmul_rn(__dmul_rn(__dmul_rn(24.0, beta), m), s.lang_kT[r]), __dmul_rn(a.dt, kAcc)));
-  const double fb = __dmul_rn(-beta, m);
   double *F[3] = {&Fx, &Fy, &Fz};
+  if (sizeof(typename G<P>::R) == 8) {
+    const double g = s.lang_g[r][type], sig = s.lang_sig[r][type];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const double xi = __dmul_rn((double)(c[d] >> 11), 0x1.0p-53);
-    const double fr = __ddiv_rn(__dmul_rn(fb, __dadd_rn(s.v[d * Nc + i], -s.lang_u[r][d])), kAcc);
-    const double fn = __dmul_rn(sigma, __dadd_rn(xi, -0.5));
-    *F[d] = __dadd_rn(__dadd_rn(*F[d], fr), fn);
+    for (int d = 0; d < 3; ++d) {
+      const double xi = __dmul_rn((double)(c[d] >> 11), 0x1.0p-53);
+      const double fr = __dmul_rn(g, __dadd_rn(s.v[d * Nc + i], -s.lang_u[r][d]));
+      const double fn = __dmul_rn(sig, __dadd_rn(xi, -0.5));
+      *F[d] = __dadd_rn(__dadd_rn(*F[d], fr), fn);
+    }
+  } else {
+    const float g = s.lang_gf[r][type], sig = s.lang_sigf[r][type];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float xi = (float)(unsigned)(c[d] >> 40) * 0x1.0p-24f;
+      const float dv = (float)(s.v[d * Nc + i] - s.lang_u[r][d]);
+      *F[d] += (double)(g * dv + sig * (xi - 0.5f));
+    }
   }
 }
 
@@ -353,7 +364,7 @@ __device__ __forceinline__ void epilogue(const Sys &s, const StepArgs &a, int i,
   }
   const int type = inf & 15u;
   const bool piston = (inf & kInfoPiston) != 0;
-  if (s.n_lang > 0 && !piston) langevin(s, a, i, type, Fx, Fy, Fz);
+  if (s.n_lang > 0 && !piston) langevin<P>(s, i, type, Fx, Fy, Fz);
   const double c = 0.5 * a.dt * s.acc_over_m[type];
   double vx = s.v[i], vy = s.v[Nc + i], vz = s.v[2 * Nc + i];
   if (piston) {

@@ -86,6 +86,7 @@ struct mdk_ctx {
   double lang_xlo[kMaxLang] = {0}, lang_xhi[kMaxLang] = {0}, lang_kT[kMaxLang] = {0},
          lang_beta[kMaxLang] = {0}, lang_u[kMaxLang][3] = {{0}};
   unsigned long long lang_seed = 0;
+  double lang_dt = 1.0;  // time step the noise amplitudes were computed for
   int win_nbins = 1;             // front bins over the box along x
   int win_nbins_cap = 0;         // bins the workspace has room for
   long long *win_fbin = nullptr;
@@ -299,9 +300,18 @@ void fill_sys_params(mdk_ctx *c) {
   for (int q = 0; q < kMaxLang; ++q) {
     s.lang_xlo[q] = c->lang_xlo[q];
     s.lang_xhi[q] = c->lang_xhi[q];
-    s.lang_kT[q] = c->lang_kT[q];
-    s.lang_beta[q] = c->lang_beta[q];
     for (int d = 0; d < 3; ++d) s.lang_u[q][d] = c->lang_u[q][d];
+    for (int t = 0; t < kMaxTypes; ++t) {
+      // g = -beta m / A; sigma = sqrt(24 beta m k_B T / (dt A)), rounded as in the oracle
+      const double m = s.mass[t], beta = c->lang_beta[q];
+      const double g = q < c->lang_n ? (-beta * m) / kAcc : 0.0;
+      const double sig =
+          q < c->lang_n ? sqrt((((24.0 * beta) * m) * c->lang_kT[q]) / (c->lang_dt * kAcc)) : 0.0;
+      s.lang_g[q][t] = g;
+      s.lang_sig[q][t] = sig;
+      s.lang_gf[q][t] = (float)g;
+      s.lang_sigf[q][t] = (float)sig;
+    }
   }
   s.lang_seed = c->lang_seed;
   s.n_fbins = c->win_nbins;
@@ -1112,6 +1122,10 @@ int mdk_step(mdk_ctx *c, double dt, int64_t nsteps) {
   int r = ensure_ready(c);
   if (r) return r;
   if (nsteps == 0) return MDK_OK;
+  if (c->lang_n > 0 && dt != c->lang_dt) {  // noise amplitudes depend on dt
+    c->lang_dt = dt;
+    fill_sys_params(c);
+  }
   if (!c->list_built) {
     r = build_now(c);
     if (r) return r;

@@ -116,10 +116,14 @@ struct Sys {
   const double *slab;             // fresh slab: [n_slab][6] = x, y, z, vx, vy, vz
   uint32_t slab_info;             // info word of appended atoms
   // Langevin thermostat regions along x (n_lang = 0: off): x in
-  // [lang_xlo, lang_xhi), k_B T (eV), target mean velocity, stiffness (1/fs)
+  // [lang_xlo, lang_xhi), target mean velocity, and per (region, type) the
+  // friction factor g = -beta m / A and the noise amplitude
+  // sigma = sqrt(24 beta m k_B T / (dt A)) of the current dt (FP64 and FP32)
   int n_lang;
-  double lang_xlo[kMaxLang], lang_xhi[kMaxLang], lang_kT[kMaxLang], lang_beta[kMaxLang];
+  double lang_xlo[kMaxLang], lang_xhi[kMaxLang];
   double lang_u[kMaxLang][3];
+  double lang_g[kMaxLang][kMaxTypes], lang_sig[kMaxLang][kMaxTypes];
+  float lang_gf[kMaxLang][kMaxTypes], lang_sigf[kMaxLang][kMaxTypes];
   unsigned long long lang_seed;
   double win_xlo, win_xhi;        // the box along x
   double front_bin;               // width of the bins that locate the front
