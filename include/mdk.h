@@ -325,6 +325,19 @@ int mdk_get_ids(mdk_ctx *ctx, int64_t *ids);
 int mdk_set_langevin(mdk_ctx *ctx, int n_regions, const double *x_lo, const double *x_hi,
                      const double *T, const double *u, const double *beta, uint64_t seed);
 
+/*
+ * Per-replica Langevin thermostats for batched contexts (the isotherm runs of
+ * Sec. "Argon shock Hugoniot": each replica of a volume-temperature grid
+ * relaxed by a Langevin thermostat of stiffness beta at its own T).  Every
+ * atom of replica r gets the force of mdk_set_langevin with T = T[r],
+ * beta = beta[r] and target mean velocity 0, whatever its position (region
+ * thermostats are then ignored).
+ *   T, beta : host [n_replicas] (K, 1/fs), >= 0; T = NULL turns them off
+ * Errors: MDK_ERR_BAD_ARG.
+ */
+int mdk_set_langevin_replicas(mdk_ctx *ctx, const double *T, const double *beta,
+                              uint64_t seed);
+
 /* Atoms appended and deleted by the moving window so far (synchronises). */
 int mdk_window_counts(mdk_ctx *ctx, int64_t *inserted, int64_t *deleted);
 

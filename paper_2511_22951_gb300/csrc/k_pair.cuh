@@ -319,34 +319,46 @@ __device__ __forceinline__ void philox4x64(unsigned long long c[4], unsigned lon
 // oracle's order.  Mixed path: the thermostat force is computed in FP32 (it
 // is noise and friction, on GB300's fast pipe), xi = (out >> 40) 2^-24.
 template <class P>
-__device__ __forceinline__ void langevin(const Sys &s, int i, int type, double &Fx, double &Fy,
-                                         double &Fz) {
+__device__ __forceinline__ void langevin(const Sys &s, int i, uint32_t inf, double &Fx,
+                                         double &Fy, double &Fz) {
   const size_t Nc = s.N_cap;
-  const double x = s.x[i];
-  int r = -1;
-  for (int q = 0; q < s.n_lang && r < 0; ++q)
-    if (x >= s.lang_xlo[q] && x < s.lang_xhi[q]) r = q;
-  if (r < 0) return;
+  const int type = inf & 15u;
+  double g, sig, u[3] = {0.0, 0.0, 0.0};
+  if (s.lang_rep_on) {  // the atom's replica, as a whole, at rest
+    const double *q = s.lang_rep + ((size_t)(inf >> 8) * kMaxTypes + type) * 2;
+    g = q[0];
+    sig = q[1];
+  } else {
+    const double x = s.x[i];
+    int r = -1;
+    for (int q = 0; q < s.n_lang && r < 0; ++q)
+      if (x >= s.lang_xlo[q] && x < s.lang_xhi[q]) r = q;
+    if (r < 0) return;
+    g = s.lang_g[r][type];
+    sig = s.lang_sig[r][type];
+    u[0] = s.lang_u[r][0];
+    u[1] = s.lang_u[r][1];
+    u[2] = s.lang_u[r][2];
+  }
   unsigned long long c[4] = {(unsigned long long)s.id[i],
                              (unsigned long long)s.st->n_steps, 0ull, 0ull};
   philox4x64(c, s.lang_seed, 0ull);
   double *F[3] = {&Fx, &Fy, &Fz};
   if (sizeof(typename G<P>::R) == 8) {
-    const double g = s.lang_g[r][type], sig = s.lang_sig[r][type];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double xi = __dmul_rn((double)(c[d] >> 11), 0x1.0p-53);
-      const double fr = __dmul_rn(g, __dadd_rn(s.v[d * Nc + i], -s.lang_u[r][d]));
+      const double fr = __dmul_rn(g, __dadd_rn(s.v[d * Nc + i], -u[d]));
       const double fn = __dmul_rn(sig, __dadd_rn(xi, -0.5));
       *F[d] = __dadd_rn(__dadd_rn(*F[d], fr), fn);
     }
   } else {
-    const float g = s.lang_gf[r][type], sig = s.lang_sigf[r][type];
+    const float gf = (float)g, sigf = (float)sig;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const float xi = (float)(unsigned)(c[d] >> 40) * 0x1.0p-24f;
-      const float dv = (float)(s.v[d * Nc + i] - s.lang_u[r][d]);
-      *F[d] += (double)(g * dv + sig * (xi - 0.5f));
+      const float dv = (float)(s.v[d * Nc + i] - u[d]);
+      *F[d] += (double)(gf * dv + sigf * (xi - 0.5f));
     }
   }
 }
@@ -364,7 +376,7 @@ __device__ __forceinline__ void epilogue(const Sys &s, const StepArgs &a, int i,
   }
   const int type = inf & 15u;
   const bool piston = (inf & kInfoPiston) != 0;
-  if (s.n_lang > 0 && !piston) langevin<P>(s, i, type, Fx, Fy, Fz);
+  if ((s.n_lang > 0 || s.lang_rep_on) && !piston) langevin<P>(s, i, inf, Fx, Fy, Fz);
   const double c = 0.5 * a.dt * s.acc_over_m[type];
   double vx = s.v[i], vy = s.v[Nc + i], vz = s.v[2 * Nc + i];
   if (piston) {

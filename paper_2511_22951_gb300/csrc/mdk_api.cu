@@ -87,6 +87,10 @@ struct mdk_ctx {
          lang_beta[kMaxLang] = {0}, lang_u[kMaxLang][3] = {{0}};
   unsigned long long lang_seed = 0;
   double lang_dt = 1.0;  // time step the noise amplitudes were computed for
+  bool lang_rep_on = false;             // per-replica thermostats (mdk_set_langevin_replicas)
+  std::vector<double> lang_rep_T, lang_rep_beta;
+  std::vector<double> lang_rep_host;    // (g, sigma) per replica and type, as uploaded
+  double *lang_rep_dev = nullptr;
   int win_nbins = 1;             // front bins over the box along x
   int win_nbins_cap = 0;         // bins the workspace has room for
   long long *win_fbin = nullptr;
@@ -182,6 +186,7 @@ size_t layout(mdk_ctx *c, char *base) {
   c->adj_out = cv.take<double>((size_t)2 * nr + nrho);
   c->adj_gE = cv.take<double>(c->n_rep);
   c->adj_aux = cv.take<long long>(8);
+  c->lang_rep_dev = cv.take<double>((size_t)c->n_rep * kMaxTypes * 2);
   c->eam_base = reinterpret_cast<char *>(kn);
   c->eam.phi64 = t.phi64;
   c->eam.rho64 = t.rho64;
@@ -309,13 +314,34 @@ void fill_sys_params(mdk_ctx *c) {
           q < c->lang_n ? sqrt((((24.0 * beta) * m) * c->lang_kT[q]) / (c->lang_dt * kAcc)) : 0.0;
       s.lang_g[q][t] = g;
       s.lang_sig[q][t] = sig;
-      s.lang_gf[q][t] = (float)g;
-      s.lang_sigf[q][t] = (float)sig;
     }
   }
   s.lang_seed = c->lang_seed;
+  s.lang_rep_on = c->lang_rep_on ? 1 : 0;
+  s.lang_rep = c->lang_rep_dev;
   s.n_fbins = c->win_nbins;
   s.fbin = c->win_fbin;
+}
+
+// (g, sigma) of every replica and atom type for the current dt, rounded as in
+// the oracle, copied into the workspace
+int upload_lang_rep(mdk_ctx *c) {
+  if (!c->lang_rep_on || !c->ws_ok) return MDK_OK;
+  const double kB = 8.617333262e-5;  // eV/K
+  c->lang_rep_host.assign((size_t)c->n_rep * kMaxTypes * 2, 0.0);
+  for (int r = 0; r < c->n_rep; ++r)
+    for (int t = 0; t < kMaxTypes; ++t) {
+      const double m = t < c->n_types ? c->type_mass[t] : 1.0, beta = c->lang_rep_beta[r];
+      const double kT = kB * c->lang_rep_T[r];
+      c->lang_rep_host[((size_t)r * kMaxTypes + t) * 2] = (-beta * m) / kAcc;
+      c->lang_rep_host[((size_t)r * kMaxTypes + t) * 2 + 1] =
+          sqrt((((24.0 * beta) * m) * kT) / (c->lang_dt * kAcc));
+    }
+  MDK_CK(cudaMemcpyAsync(c->lang_rep_dev, c->lang_rep_host.data(),
+                         sizeof(double) * c->lang_rep_host.size(), cudaMemcpyHostToDevice,
+                         c->stream));
+  MDK_CK(cudaStreamSynchronize(c->stream));
+  return MDK_OK;
 }
 
 int read_status(mdk_ctx *c, DevStatus *out) {
@@ -839,7 +865,7 @@ int mdk_set_workspace(mdk_ctx *c, void *dev_ptr, size_t bytes) {
   c->forces_valid = false;
   c->cur = 0;
   c->thermo_written = c->thermo_read = 0;
-  return MDK_OK;
+  return upload_lang_rep(c);
 }
 
 int mdk_set_state(mdk_ctx *c, const double *x, const double *v, int on_device) {
@@ -1122,9 +1148,11 @@ int mdk_step(mdk_ctx *c, double dt, int64_t nsteps) {
   int r = ensure_ready(c);
   if (r) return r;
   if (nsteps == 0) return MDK_OK;
-  if (c->lang_n > 0 && dt != c->lang_dt) {  // noise amplitudes depend on dt
+  if ((c->lang_n > 0 || c->lang_rep_on) && dt != c->lang_dt) {  // amplitudes depend on dt
     c->lang_dt = dt;
     fill_sys_params(c);
+    r = upload_lang_rep(c);
+    if (r) return r;
   }
   if (!c->list_built) {
     r = build_now(c);
@@ -1443,6 +1471,27 @@ int mdk_set_langevin(mdk_ctx *c, int n_regions, const double *x_lo, const double
   }
   c->lang_seed = seed;
   if (c->ws_ok) fill_sys_params(c);
+  return MDK_OK;
+}
+
+int mdk_set_langevin_replicas(mdk_ctx *c, const double *T, const double *beta, uint64_t seed) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  if (!T) {  // off
+    c->lang_rep_on = false;
+    if (c->ws_ok) fill_sys_params(c);
+    return MDK_OK;
+  }
+  if (!beta) return MDK_ERR_BAD_ARG;
+  for (int r = 0; r < c->n_rep; ++r)
+    if (!(T[r] >= 0.0) || !(beta[r] >= 0.0)) return MDK_ERR_BAD_ARG;
+  c->lang_rep_T.assign(T, T + c->n_rep);
+  c->lang_rep_beta.assign(beta, beta + c->n_rep);
+  c->lang_rep_on = true;
+  c->lang_seed = seed;
+  if (c->ws_ok) {
+    fill_sys_params(c);
+    return upload_lang_rep(c);
+  }
   return MDK_OK;
 }
 

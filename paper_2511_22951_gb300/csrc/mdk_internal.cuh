@@ -118,13 +118,16 @@ struct Sys {
   // Langevin thermostat regions along x (n_lang = 0: off): x in
   // [lang_xlo, lang_xhi), target mean velocity, and per (region, type) the
   // friction factor g = -beta m / A and the noise amplitude
-  // sigma = sqrt(24 beta m k_B T / (dt A)) of the current dt (FP64 and FP32)
+  // sigma = sqrt(24 beta m k_B T / (dt A)) of the current dt
   int n_lang;
   double lang_xlo[kMaxLang], lang_xhi[kMaxLang];
   double lang_u[kMaxLang][3];
   double lang_g[kMaxLang][kMaxTypes], lang_sig[kMaxLang][kMaxTypes];
-  float lang_gf[kMaxLang][kMaxTypes], lang_sigf[kMaxLang][kMaxTypes];
   unsigned long long lang_seed;
+  // per-replica thermostats (batched contexts; target mean velocity 0):
+  // lang_rep[(replica * kMaxTypes + type) * 2 + {0, 1}] = (g, sigma)
+  int lang_rep_on;
+  const double *lang_rep;
   double win_xlo, win_xhi;        // the box along x
   double front_bin;               // width of the bins that locate the front
   double fixed_front;             // finite: the front's x, fixed (stationary window)

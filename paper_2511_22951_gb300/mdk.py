@@ -76,6 +76,7 @@ SIGNATURES = {
     "mdk_lj_compute_noalloc": [_P, _I64, _P, _P, _P, _D, _D, _D, _I, _P, _P, _P],
     "mdk_eam_vjp": [_P, _P, _P, _P, _I],
     "mdk_set_langevin": [_P, _I, _P, _P, _P, _P, _P, ctypes.c_uint64],
+    "mdk_set_langevin_replicas": [_P, _P, _P, ctypes.c_uint64],
 }
 
 _lib = None
@@ -428,6 +429,18 @@ class Context:
         b = np.array([r[4] for r in regions], dtype=np.float64)
         _check(self.lib.mdk_set_langevin(self.h, n, _ptr(xl), _ptr(xh), _ptr(T), _ptr(u),
                                          _ptr(b), int(seed)), "mdk_set_langevin")
+        self.version += 1
+
+    def set_langevin_replicas(self, T, beta, seed=0):
+        """Whole-replica thermostats: T [n_rep] (K), beta [n_rep] (1/fs); T=None: off."""
+        if T is None:
+            _check(self.lib.mdk_set_langevin_replicas(self.h, None, None, int(seed)),
+                   "mdk_set_langevin_replicas")
+        else:
+            Tv = _host_f64(T, (self.n_rep,))
+            bv = _host_f64(np.broadcast_to(beta, (self.n_rep,)), (self.n_rep,))
+            _check(self.lib.mdk_set_langevin_replicas(self.h, _ptr(Tv), _ptr(bv), int(seed)),
+                   "mdk_set_langevin_replicas")
         self.version += 1
 
     def set_piston(self, u_p, flags):

@@ -200,3 +200,52 @@ def test_stationary_search_workflow_runs(mdk):
     u, hist = shock.dichotomy(slope_at, -0.045, -0.005, tol=0.02, max_iter=2)
     assert -0.045 <= u <= -0.005 and len(hist) >= 3
     assert all(np.isfinite(q) for q in slopes.values())
+
+
+def test_replica_thermostats_match_oracle(mdk, ora):
+    """Per-replica thermostats (mdk_set_langevin_replicas): every replica of
+    a batch at its own T and beta; FP64 trajectories equal the oracle's run of
+    each replica with one whole-box region (ids continue across replicas)."""
+    rng = np.random.default_rng(12)
+    reps, Ts, betas = [], [60.0, 150.0, 400.0], [0.01, 0.02, 0.005]
+    for a in (5.26, 5.1, 5.4):
+        reps.append(W.lattice_system(rng, (4, 4, 4), a, W.MASS_AR, 80.0))
+    lj = W.LJ_AR
+    ctx = mdk.Context([r.lo for r in reps], [r.hi for r in reps], [r.periodic for r in reps],
+                      np.concatenate([r.masses for r in reps]), "fp64",
+                      n_atoms=[r.n for r in reps])
+    ctx.set_potential_lj(lj.eps, lj.sigma, lj.rc, lj.shift_mode)
+    ctx.plan(lj.rc, 0.3)
+    ctx.set_state(np.concatenate([r.x for r in reps]), np.concatenate([r.v for r in reps]))
+    ctx.build_neighbors(lj.rc, 0.3)
+    ctx.set_langevin_replicas(Ts, betas, seed=31)
+    ctx.step(2.0, 10)
+    xg, vg = ctx.get_state()
+    off = 0
+    for r, T, b in zip(reps, Ts, betas):
+        o = ora.md_langevin(r.x, r.v, r.masses, r.lo, r.hi, r.periodic, 2.0, 10, 0.3,
+                            [(-1e30, 1e30, T, (0.0, 0.0, 0.0), b)], seed=31, lj_params=lj,
+                            ids=np.arange(off, off + r.n))
+        L = r.hi - r.lo
+        d = xg[off:off + r.n] - o["x"]
+        d -= np.rint(d / L) * L
+        assert np.max(np.abs(d)) < 1e-9
+        assert np.max(np.abs(vg[off:off + r.n] - o["v"])) < 1e-11
+        off += r.n
+
+
+def test_isotherm_grid_workflow(mdk):
+    """Isotherms as batched replicas, mixed precision: e and P grow with T
+    on every volume line and with compression on every isotherm, and the
+    replicas' kinetic temperatures follow their thermostats."""
+    from paper_2511_22951_gb300 import hugoniot as H
+    grid = H.IsothermGrid(a0=5.26, compressions=np.array([1.0, 0.85, 0.7]),
+                          temperatures=np.array([100.0, 300.0, 900.0]), n_cells=4,
+                          beta=0.01)
+    ctx, ss = grid.context("mixed", max_neighbors=160)
+    E, P, v = grid.run(ctx, ss, 2.0, 600, 10, 20)
+    assert np.all(np.diff(E, axis=1) > 0) and np.all(np.diff(P, axis=1) > 0)
+    assert np.all(np.diff(P, axis=0) > 0)
+    np.testing.assert_allclose(v / v[0], grid.compressions, rtol=1e-12)
+    th = ctx.thermo()
+    assert th.shape[0] == 0  # everything was read by run()
