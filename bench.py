@@ -382,6 +382,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--vjps", type=int, default=100, help="adjoint calls timed (config 4)")
+    ap.add_argument("--hugoniot", action="store_true",
+                    help="the isotherm grid of the Hugoniot runs: 8 x 8 argon replicas")
     ap.add_argument("--stationary", action="store_true",
                     help="config 3 as the paper's stationary-shock window (inflow/outflow)")
     ap.add_argument("--langevin", default=None,
@@ -394,6 +396,18 @@ def main():
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     wl = workload(args.config, args.cells)
+    grid = None
+    if args.hugoniot:
+        from paper_2511_22951_gb300 import hugoniot as H
+        # the paper's isotherm grid: 6912-atom argon replicas, v/v0 from 1 to 0.3,
+        # T from 300 K to 1e5 K, one dt for the batch (the hottest replica's)
+        grid = H.IsothermGrid(a0=5.26, compressions=np.linspace(1.0, 0.3, 8),
+                              temperatures=np.geomspace(300.0, 1e5, 8), n_cells=12,
+                              beta=5e-4)
+        ss = grid.systems()
+        wl = W.Workload("lj_argon_isotherms_64x6912", ss, "lj", W.LJ_AR, None, None,
+                        dt=float(H.paper_dt(grid.temperatures.max())), steps=1000, skin=0.3,
+                        precision="mixed")
     if args.impl == "reference":
         return run_reference(args, wl)
 
@@ -424,7 +438,11 @@ def main():
             q.v[:, 0] += -0.05           # the material flows in at u_in
     ctx = mdk.make_context(wl, precision=prec,
                            capacity=int(n_atoms * 1.1) if windowed else None,
-                           max_neighbors=120 if args.stationary else 0)
+                           max_neighbors=(120 if args.stationary else
+                                          (320 if grid is not None else 0)))
+    if grid is not None:
+        Tr = np.repeat(grid.temperatures[None, :], len(grid.compressions), 0).ravel()
+        ctx.set_langevin_replicas(Tr, np.full(Tr.size, grid.beta), seed=1)
     stream = ctx.stream
     n_avg = float(ctx.neighbor_counts().mean())
     n_rc = pair_count_within_rc(ctx, wl) if rank == 0 else 0.0
@@ -574,13 +592,16 @@ def main():
         torch.cuda.empty_cache()
         c64 = mdk.make_context(wl, precision="fp64",
                                capacity=int(n_atoms * 1.1) if windowed else None,
-                               max_neighbors=120 if args.stationary else 0)
+                               max_neighbors=(120 if args.stationary else
+                                              (320 if grid is not None else 0)))
         if args.stationary:
             stationary_setup(c64, wl)
         elif windowed:
             window_setup(c64, wl)
         if lang:
             c64.set_langevin(lang, seed=1)
+        if grid is not None:
+            c64.set_langevin_replicas(Tr, np.full(Tr.size, grid.beta), seed=1)
         c64.step(wl.dt, 3)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -635,6 +656,11 @@ def main():
         if lang:
             line["config"]["langevin"] = {"T_K": lang[0][2], "beta_per_fs": lang[0][4],
                                           "regions": "whole system"}
+        if grid is not None:
+            line["config"]["isotherms"] = {
+                "v_over_v0": [round(float(c), 4) for c in grid.compressions],
+                "T_K": [round(float(t), 1) for t in grid.temperatures],
+                "thermostat": "per replica, beta 5e-4 1/fs", "dt_fs": wl.dt}
         if stationary:
             line["config"]["stationary_window"] = dict(stationary, atoms_at_end=n_now)
         elif windowed:
