@@ -227,7 +227,6 @@ __global__ void k_eam_prepare(int nr, int nrho, const double *phi, const double 
     o.rho64[k] = make_double2(rho[k], mr);
     const double dp = k + 1 < nr ? phi[k + 1] - phi[k] : 0.0;
     const double dr = k + 1 < nr ? rho[k + 1] - rho[k] : 0.0;
-    o.phi_d32[k] = make_float2((float)dp, (float)mp);
     o.rho_d32[k] = make_float2((float)dr, (float)mr);
     o.phi_v32[k] = (float)phi[k];
     o.pr32[k] = make_float4((float)dp, (float)mp, (float)dr, (float)mr);

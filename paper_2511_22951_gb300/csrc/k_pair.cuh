@@ -63,11 +63,10 @@ struct G<Fp64> {
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
   static __device__ __forceinline__ double sqr(double x) { return sqrt(x); }
-  // EAM tables: (y_k, h m_k) per knot for both passes
+  // EAM tables: (y_k, h m_k) per knot
   using Tab1 = double2;
   using Tab2 = double2;
   static __device__ __forceinline__ const double2 *tab1(const EAMParams &e) { return e.rho64; }
-  static __device__ __forceinline__ const double2 *phi2(const EAMParams &e) { return e.phi64; }
   static __device__ __forceinline__ const double2 *rho2(const EAMParams &e) { return e.rho64; }
   static __device__ __forceinline__ int n1(const EAMParams &e) { return e.nr; }
   static __device__ __forceinline__ double val1(const double2 *t, int k, double u) {
@@ -78,11 +77,6 @@ struct G<Fp64> {
   static __device__ __forceinline__ double der2(const double2 *t, int k, double u) {
     const double2 a = t[k], b = t[k + 1];
     return herm_der<double>(u, a.x, a.y, b.x, b.y);
-  }
-  static __device__ __forceinline__ double val2(const double2 *t, const EAMParams &, int k,
-                                                double u) {
-    const double2 a = t[k], b = t[k + 1];
-    return herm_val<double>(u, a.x, a.y, b.x, b.y);
   }
   // force pass: interleaved phi / rho knots, h * derivatives of both
   using TabPR = dvec4;
@@ -128,11 +122,11 @@ struct G<Mixed> {
   static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
   static __device__ __forceinline__ float sqr(float x) { return sqrtf(x); }
   // EAM tables rounded from FP64 differences (no FP32 cancellation):
-  // pass 1 per interval (y_k, dy_k, h m_k, h m_{k+1}); pass 2 per knot (dy_k, h m_k)
+  // density pass per interval (y_k, dy_k, h m_k, h m_{k+1}); rho per knot
+  // (dy_k, h m_k) for the adjoint
   using Tab1 = float4;
   using Tab2 = float2;
   static __device__ __forceinline__ const float4 *tab1(const EAMParams &e) { return e.rho_i32; }
-  static __device__ __forceinline__ const float2 *phi2(const EAMParams &e) { return e.phi_d32; }
   static __device__ __forceinline__ const float2 *rho2(const EAMParams &e) { return e.rho_d32; }
   static __device__ __forceinline__ int n1(const EAMParams &e) { return e.nr - 1; }
   static __device__ __forceinline__ float val1(const float4 *t, int k, float u) {
@@ -145,13 +139,6 @@ struct G<Mixed> {
     const float u2 = u * u;
     return (6.0f * u - 6.0f * u2) * a.x + (3.0f * u2 - 4.0f * u + 1.0f) * a.y +
            (3.0f * u2 - 2.0f * u) * b.y;
-  }
-  static __device__ __forceinline__ float val2(const float2 *t, const EAMParams &e, int k,
-                                               float u) {
-    const float2 a = t[k], b = t[k + 1];
-    const float u2 = u * u, u3 = u2 * u;
-    return __ldg(e.phi_v32 + k) + (3.0f * u2 - 2.0f * u3) * a.x + (u3 - 2.0f * u2 + u) * a.y +
-           (u3 - u2) * b.y;
   }
   // force pass: interleaved phi / rho differences and slopes, h * derivatives
   using TabPR = float4;

@@ -177,7 +177,6 @@ size_t layout(mdk_ctx *c, char *base) {
   t.rho64 = cv.take<double2>(nr);
   t.F64 = cv.take<double2>(nrho);
   t.rho_i32 = cv.take<float4>(nr);
-  t.phi_d32 = cv.take<float2>(nr);
   t.rho_d32 = cv.take<float2>(nr);
   t.phi_v32 = cv.take<float>(nr);
   t.pr32 = cv.take<float4>(nr);
@@ -192,7 +191,6 @@ size_t layout(mdk_ctx *c, char *base) {
   c->eam.rho64 = t.rho64;
   c->eam.F64 = t.F64;
   c->eam.rho_i32 = t.rho_i32;
-  c->eam.phi_d32 = t.phi_d32;
   c->eam.rho_d32 = t.rho_d32;
   c->eam.phi_v32 = t.phi_v32;
   c->eam.pr32 = t.pr32;

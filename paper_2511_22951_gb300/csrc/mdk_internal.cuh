@@ -164,10 +164,10 @@ struct EAMParams {
   // FP32 tables of the mixed path, rounded from FP64 quantities so that no
   // FP32 subtraction of neighbouring knot values is needed:
   //   rho_i32[k] = (y_k, y_{k+1} - y_k, h m_k, h m_{k+1})   (pass 1, rho value)
-  //   phi_d32[k], rho_d32[k] = (y_{k+1} - y_k, h m_k)         (pass 2, slopes)
+  //   rho_d32[k] = (rho_{k+1} - rho_k, h m_k)                (adjoint, slopes)
   //   phi_v32[k] = y_k                                         (pass 2 energy)
   const float4 *rho_i32;
-  const float2 *phi_d32, *rho_d32;
+  const float2 *rho_d32;
   const float *phi_v32;
   // force pass: phi and rho interleaved per knot, so one pair of loads
   // serves both derivatives
@@ -181,7 +181,7 @@ struct EAMParams {
 struct EAMTablesDev {
   double2 *phi64, *rho64, *F64;
   float4 *rho_i32;
-  float2 *phi_d32, *rho_d32;
+  float2 *rho_d32;
   float *phi_v32;
   float4 *pr32;
   dvec4 *pr64;
