@@ -84,19 +84,23 @@ def workload(cfg: int, cells: int = 128):
     raise SystemExit(f"config {cfg} is not a bench workload")
 
 
-def algorithmic_bytes_per_atom(wl, prec, n_avg):
-    """Bytes one force pass with the fused velocity-Verlet update must move
-    per atom.  LJ (one kernel): own gather-copy element, list entries and
-    count, x and v read + write, x_ref and cell word read, next gather-copy
-    element written.  EAM adds the density pass: its own gather-copy element,
-    list and count again, rho_i and F'(rho_i) written, F'(rho_i) read back.
-    Neighbour positions are assumed to come from cache (spatial order)."""
+def algorithmic_bytes_per_atom(wl, prec, n_list, kind="full"):
+    """Bytes one force pass with the velocity-Verlet update must move per
+    atom (n_list: mean entries of the list in use).  LJ, full lists (one
+    kernel): own gather-copy element, list entries and count, x and v read +
+    write, x_ref and cell word read, next gather-copy element written.  LJ,
+    half lists: the same with half the entries, plus the per-atom force
+    accumulators written and read once (the pair pass and the per-atom pass
+    that finishes the step).  EAM adds the density pass: its own gather-copy
+    element, list and count again, rho_i and F'(rho_i) written, F'(rho_i)
+    read back.  Neighbour positions are assumed to come from cache (spatial
+    order)."""
     g = 16 if prec == "mixed" else 32
-    lj = g + 4 * n_avg + 4 + 48 + 48 + 24 + 4 + g
+    lj = g + 4 * n_list + 4 + 48 + 48 + 24 + 4 + g
     if wl.potential == "lj":
-        return lj
+        return lj + (48 if kind == "half" else 0)
     r = 4 if prec == "mixed" else 8
-    return lj + g + 4 * n_avg + 4 + 8 + r + r
+    return lj + g + 4 * n_list + 4 + 8 + r + r
 
 
 # DRAM bytes per atom of one force-pass launch (dram__bytes_read.sum +
@@ -104,29 +108,28 @@ def algorithmic_bytes_per_atom(wl, prec, n_avg):
 # captured case), valid only for the kernel sources they were taken from:
 # the sha256 of those files is checked at run time and `traffic` is null
 # when any of them changed since.
-TRAFFIC = {
-    ("lj", "mixed"): {"bytes_per_atom": 475.2,
-                      "sources_sha256": "6b256684d54b8f75565804bf0f100220c0a90aecf9dc37ff3593cc82fd6d5c40",
-                      "capture": "k_lj<Mixed, kStep, T=1>, 8,388,608 atoms, ncu "
-                                 "dram__bytes_read.sum + dram__bytes_write.sum, 4 launches"},
+TRAFFIC = {}
+_CSRC = "paper_2511_22951_gb300/csrc/"
+TRAFFIC_SOURCES = {
+    "full": tuple(_CSRC + f for f in ("k_lj.cu", "lj_pair.cuh", "k_pair.cuh",
+                                      "mdk_internal.cuh")),
+    "half": tuple(_CSRC + f for f in ("k_lj_half.cu", "lj_pair.cuh", "k_pair.cuh",
+                                      "mdk_internal.cuh")),
 }
-TRAFFIC_SOURCES = ("paper_2511_22951_gb300/csrc/k_lj.cu",
-                   "paper_2511_22951_gb300/csrc/k_pair.cuh",
-                   "paper_2511_22951_gb300/csrc/mdk_internal.cuh")
 
 
-def sources_sha256(paths=TRAFFIC_SOURCES):
+def sources_sha256(kind="full"):
     import hashlib
     h = hashlib.sha256()
-    for p in paths:
+    for p in TRAFFIC_SOURCES[kind]:
         with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
 
 
-def traffic_per_launch(wl, prec, n_atoms):
-    t = TRAFFIC.get((wl.potential, prec))
-    if t is None or t["sources_sha256"] != sources_sha256():
+def traffic_per_launch(wl, prec, n_atoms, kind="full"):
+    t = TRAFFIC.get((wl.potential, prec, kind))
+    if t is None or t["sources_sha256"] != sources_sha256(kind):
         return None
     return t["bytes_per_atom"] * n_atoms
 
@@ -390,10 +393,14 @@ def main():
                     help="T,beta: a Langevin thermostat on the whole system (K, 1/fs)")
     ap.add_argument("--launch", default=None,
                     help="threads-per-atom x block (e.g. 1x128) instead of the autotuner")
+    ap.add_argument("--list", default=None, choices=("full", "half"),
+                    help="with --launch: the Verlet-list kind (LJ; default full)")
     ap.add_argument("--drift-steps", type=int, default=0,
                     help="also run an NVE drift measurement of this many steps")
     ap.add_argument("--drift-fp64-steps", type=int, default=2000)
     args = ap.parse_args()
+    if args.list and not args.launch:
+        ap.error("--list goes with --launch (the autotuner picks the list kind)")
     args.warmup = max(3, args.warmup)
     wl = workload(args.config, args.cells)
     grid = None
@@ -429,6 +436,8 @@ def main():
     from paper_2511_22951_gb300 import _build, mdk
     _build.build()
     prec = args.precision or wl.precision
+    if prec != wl.precision and wl.name.endswith("_" + wl.precision):
+        wl.name = wl.name[:-len(wl.precision)] + prec   # the workload as run
     n_atoms = wl.n_atoms
     windowed = args.config == 3
     if args.stationary:
@@ -459,10 +468,15 @@ def main():
     if args.launch:
         tpa, block = (int(q) for q in args.launch.split("x"))
         ctx.set_launch(tpa, block)
+        if args.list:
+            ctx.set_list_kind(args.list)
+            ctx.build_neighbors(wl.rc, wl.skin)
         picked = "--launch"
     else:
         tpa, block, _ = ctx.autotune()
         picked = "mdk_autotune"
+    kind = ctx.list_kind
+    n_list = float(ctx.neighbor_counts().mean())
 
     # warm-up (untimed; also captures the step graphs)
     ctx.step(wl.dt, args.warmup, check=True)
@@ -499,16 +513,21 @@ def main():
     hbm, peak_kind = peaks()
     n_now = ctx.natoms()
     force_ms = prof["force_ms"] / max(1.0, prof["force_passes"])
-    bpa = algorithmic_bytes_per_atom(wl, prec, n_avg)
+    bpa = algorithmic_bytes_per_atom(wl, prec, n_list, kind)
     gbs = n_now * bpa / (force_ms / 1e3) / 1e9
-    kname = ("k_lj" if wl.potential == "lj" else "k_rho + k_eam") + f"<{prec}>"
-    common = {"kernel": f"{kname} force pass with the fused velocity-Verlet update",
+    if kind == "half":
+        kdesc = (f"k_lj_half<{prec}> pair pass (half lists, accumulating atomics) + "
+                 "k_half_fin per-atom velocity-Verlet pass")
+    else:
+        kdesc = (("k_lj" if wl.potential == "lj" else "k_rho + k_eam") +
+                 f"<{prec}> force pass with the fused velocity-Verlet update")
+    common = {"kernel": kdesc,
               "force_share_of_step": prof["force_ms"] / (ms * prof_steps / args.steps),
               "rebuild_share_of_step": prof["rebuild_ms"] / (ms * prof_steps / args.steps),
               "timed_from": f"CUDA events around each of {int(prof['force_passes'])} force "
                             f"passes of a {prof_steps}-step profiled segment"}
     if prec == "mixed":
-        tr = traffic_per_launch(wl, prec, n_now)
+        tr = traffic_per_launch(wl, prec, n_now, kind)
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                 "frac": gbs / hbm, "traffic": tr, "bytes_per_atom": bpa,
                 "traffic_unit": "bytes per launch", "peak_kind": peak_kind, **common}
@@ -570,7 +589,7 @@ def main():
         xg, vg = ctx.get_state()
         xs.numpy()[:] = xg
         vs.numpy()[:] = vg
-        E = np.zeros(1)
+        E = np.zeros(len(wl.systems))  # mdk_compute writes one energy per replica
         barrier()
         t0 = time.perf_counter()
         ctx.lib.mdk_set_state(ctx.h, mdk._P(xs.data_ptr()), mdk._P(vs.data_ptr()), 0)
@@ -583,7 +602,7 @@ def main():
         ctx.check()
         e2e = {"value": n_atoms * args.steps * world / t, "unit": UNIT,
                "h2d_bytes_per_step": 48 * n_atoms / args.steps,
-               "d2h_bytes_per_step": (48 * n_atoms + 8) / args.steps}
+               "d2h_bytes_per_step": (48 * n_atoms + 8 * E.size) / args.steps}
 
     # the plain FP64 GPU path on the same workload, for comparison
     fp64 = None
@@ -602,6 +621,7 @@ def main():
             c64.set_langevin(lang, seed=1)
         if grid is not None:
             c64.set_langevin_replicas(Tr, np.full(Tr.size, grid.beta), seed=1)
+        t64, b64, _ = c64.autotune()
         c64.step(wl.dt, 3)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -613,7 +633,9 @@ def main():
         c64.check()
         fms = f0.elapsed_time(f1)
         fp64 = {"value": n_atoms * args.fp64_steps / (fms / 1e3), "unit": UNIT,
-                "ms_per_step": fms / args.fp64_steps, "steps": args.fp64_steps}
+                "ms_per_step": fms / args.fp64_steps, "steps": args.fp64_steps,
+                "launch": {"threads_per_atom": t64, "block": b64, "list": c64.list_kind,
+                           "picked_by": "mdk_autotune"}}
         del c64
 
     drift = None
@@ -637,6 +659,7 @@ def main():
                        "replicas": len(wl.systems),
                        "neighbors_per_atom": n_avg, "neighbors_within_rc": n_rc,
                        "launch": {"threads_per_atom": tpa, "block": block,
+                                  "list": kind, "list_entries_per_atom": n_list,
                                   "picked_by": picked},
                        "rebuild": "when an atom moved > skin/2 since the last build",
                        "list_builds_in_timed_region": builds0 - builds_before,

@@ -14,7 +14,8 @@
 //   k_cell_sort order each cell's atoms by their permanent id (determinism)
 //   k_permute   gather every per-atom array into the new order (scratch)
 //   k_copyback  scratch -> primary arrays
-//   k_build     Verlet lists: FP32 pre-filter on cell-relative offsets,
+//   k_build     Verlet lists (full, or half: each pair once): FP32
+//               pre-filter on cell-relative offsets,
 //               exact FP64 test for the few candidates near r_ns
 //   k_finish    clear the flag, count the build
 #include <math.h>
@@ -467,6 +468,16 @@ __device__ __noinline__ bool exact_pair(const Sys &s, const Grid &g, int i, uint
   return r2 < rns2;
 }
 
+// Half lists keep each unordered pair in one of its two atoms' lists: for
+// j != i in the list of the smaller index when i + j is even and of the
+// larger when it is odd (so every atom keeps about half of its neighbours,
+// whatever its place in the cell order).  (i, j, s) and (j, i, -s) pass the
+// same distance test, so the half list is exactly one of each mirror pair.
+__device__ __forceinline__ bool half_keep(int i, int j, bool s_pos) {
+  if (j == i) return s_pos;
+  return (i < j) == (((i ^ j) & 1) == 0);
+}
+
 __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
   __shared__ uint32_t stage[2 * kGroup][kBlk];
   if (!flag_on(s)) return;
@@ -475,6 +486,7 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
   const float lo_thr = s.filt_lo, hi_thr = s.filt_hi;
   const double rns2 = s.rns2;
   const int ngroups = s.nmax / kGroup;
+  const bool half = s.half != 0;
   const int tx = threadIdx.x;
   for (int i = blockIdx.x * kBlk + tx; i < N; i += gridDim.x * kBlk) {
     const float4 pi = __ldg(s.pf + i);
@@ -507,6 +519,9 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
       const float qz = pi.z - (float)sz * g.hf[2];
       const int self = (nx == 0 && ny == 0 && nz == 0) ? i : -1;
       const uint32_t code = pack_nbr(0, sx, sy, sz);
+      // half lists: an image of i itself is kept for the lexicographically
+      // positive stencil offset only (its mirror has the negative one)
+      const bool s_pos = sz > 0 || (sz == 0 && (sy > 0 || (sy == 0 && sx > 0)));
       for (int j0 = a; j0 < b; j0 += 4) {
         const int before = count;
         float4 pj[4];
@@ -518,7 +533,7 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
           const int j = j0 + u;
           const float dx = pj[u].x - qx, dy = pj[u].y - qy, dz = pj[u].z - qz;
           const float r2f = dx * dx + dy * dy + dz * dz;
-          const bool ok = j < b && j != self;
+          const bool ok = j < b && j != self && (!half || half_keep(i, j, s_pos));
           const bool acc = ok && r2f < lo_thr;
           band = band || (ok && !acc && !(r2f > hi_thr));
           stage[count & 15][tx] = code | (uint32_t)j;  // kept only if accepted
@@ -532,7 +547,7 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
             const int j = j0 + u;
             const float dx = pj[u].x - qx, dy = pj[u].y - qy, dz = pj[u].z - qz;
             const float r2f = dx * dx + dy * dy + dz * dz;
-            const bool ok = j < b && j != self;
+            const bool ok = j < b && j != self && (!half || half_keep(i, j, s_pos));
             bool acc = ok && r2f < lo_thr;
             if (ok && !acc && !(r2f > hi_thr))
               acc = exact_pair(s, g, i, code | (uint32_t)j, c0, c1, c2, rns2);

@@ -17,7 +17,7 @@
 // is d = (p_j - p_i) + s h with p the cell-centre offsets of the gather copy
 // and s the stencil offset stored in the list entry, so FP32 pair arithmetic
 // never subtracts two large coordinates.
-#include "k_pair.cuh"
+#include "lj_pair.cuh"
 
 namespace mdk {
 namespace {
@@ -32,14 +32,7 @@ __global__ void __launch_bounds__(256, 4) k_lj(Sys s, LJParams lp, StepArgs a) {
   const int N = s.st->N;
   const size_t Nc = s.N_cap;
   const V *__restrict__ pg = (const V *)s.pg[a.cur];
-  const bool f64 = sizeof(R) == 8;
-  const R rc2 = f64 ? (R)lp.rc2 : (R)lp.rc2f;
-  const R sig2 = f64 ? (R)lp.sig2 : (R)lp.sig2f;
-  const R eps24 = f64 ? (R)lp.eps24 : (R)lp.eps24f;
-  const R eps4 = f64 ? (R)lp.eps4 : (R)lp.eps4f;
-  const R ush = f64 ? (R)lp.u_shift : (R)lp.u_shiftf;
-  const R durc = f64 ? (R)lp.du_rc : (R)lp.du_rcf;
-  const R rcut = f64 ? (R)lp.rc : (R)lp.rcf;
+  const LJc<R> lc(lp);
   // one warp tile per warp (no shared tables to amortise, so no persistent
   // loop: the loop's extra state costs registers and occupancy)
   const Tiles<T> tl;
@@ -70,22 +63,13 @@ __global__ void __launch_bounds__(256, 4) k_lj(Sys s, LJParams lp, StepArgs a) {
           const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
           const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
           const R r2 = dx * dx + dy * dy + dz * dz;
-          if (r2 < rc2) {
-            const R inv = GP::rcp(r2);
-            const R s2 = sig2 * inv;
-            const R s6 = s2 * s2 * s2;
-            R fr = -eps24 * (R(2) * s6 * s6 - s6) * inv;  // V'(r)/r
-            R r = 0;
-            if (SHIFT == 2) {
-              r = GP::sqr(r2);
-              fr -= durc / r;
-            }
+          if (r2 < lc.rc2) {
+            R fr, v;
+            lj_pair<GP, SHIFT, ENERGY>(lc, r2, fr, v);
             bx += fr * dx;
             by += fr * dy;
             bz += fr * dz;
             if (ENERGY) {
-              R v = eps4 * (s6 * s6 - s6) - ush;
-              if (SHIFT == 2) v -= (r - rcut) * durc;
               e += R(0.5) * v;
               const R hf = R(-0.5) * fr;  // r_ij = -d
               w0 += hf * dx * dx;

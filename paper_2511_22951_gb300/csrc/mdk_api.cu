@@ -150,6 +150,7 @@ size_t layout(mdk_ctx *c, char *base) {
   s.pgF = cv.take<char>(gsz * (c->pot == 2 ? Nc : 1));
   s.nnbr = cv.take<int32_t>(Nc);
   s.nbr = cv.take<uint32_t>((size_t)std::max(c->nmax, c->nmax_grow) * Nc);
+  s.hacc = cv.take<long long>(10 * Nc);
   s.ea = cv.take<double>(Nc);
   s.ka = cv.take<double>(Nc);
   s.wa = cv.take<double>(6 * Nc);
@@ -263,6 +264,15 @@ double pot_rc(const mdk_ctx *c) {
   return 0.0;
 }
 
+// switch between full and half lists; the next call that needs the list
+// rebuilds it
+void use_list_kind(mdk_ctx *c, int kind) {
+  if (c->cfg.half == kind) return;
+  c->cfg.half = kind;
+  c->sys.half = kind;
+  c->list_built = false;
+}
+
 void fill_sys_params(mdk_ctx *c) {
   Sys &s = c->sys;
   s.N_cap = (int)c->N_cap;
@@ -270,6 +280,7 @@ void fill_sys_params(mdk_ctx *c) {
   s.n_rep = c->n_rep;
   s.n_cells = c->n_cells;
   s.n_scan_blocks = scan_blocks_for(c->n_cells + 1);
+  s.half = c->pot == 1 && c->cfg.half ? 1 : 0;
   const double rns = c->rc_list + c->skin;
   s.rns2 = rns * rns;
   // FP32 pre-filter band: the float r^2 of a candidate is within ~6e-6 r_ns^2
@@ -425,8 +436,11 @@ int timed(mdk_ctx *c, std::vector<std::pair<int, int>> &log, int n_kernels, F la
 
 int force_pass(mdk_ctx *c, Mode mode, int energy, double dt) {
   StepArgs a{dt, c->cur, energy};
-  return timed(c, c->ev_force, c->pot == 1 ? 1 : 2, [&] {
-    if (c->pot == 1)
+  const bool half = c->pot == 1 && c->cfg.half;
+  return timed(c, c->ev_force, c->pot == 1 && !half ? 1 : 2, [&] {
+    if (half)
+      launch_lj_half(c->sys, c->lj, c->precision, mode, a, c->cfg, c->stream);
+    else if (c->pot == 1)
       launch_lj(c->sys, c->lj, c->precision, mode, a, c->cfg, c->stream);
     else
       launch_eam(c->sys, c->eam, c->precision, mode, a, c->cfg, c->stream);
@@ -765,6 +779,7 @@ int mdk_set_potential_eam(mdk_ctx *c, int nr, double rc, const double *phi, cons
   c->eam_rho.assign(rho, rho + nr);
   c->eam_F.assign(F, F + nrho);
   c->pot = 2;
+  use_list_kind(c, MDK_LIST_FULL);  // the EAM passes read full lists
   if (!c->planned) plan(c, rc, 0.3, 0, 0);
   if (resized) {
     c->ws_ok = false;  // table area changes size: a new workspace is needed
@@ -832,6 +847,8 @@ int mdk_set_workspace(mdk_ctx *c, void *dev_ptr, size_t bytes) {
   Sys &s = c->sys;
   MDK_CK(cudaMemsetAsync(s.st, 0, sizeof(DevStatus), c->stream));
   MDK_CK(cudaMemsetAsync(s.cell_cnt, 0, sizeof(int32_t) * (c->n_cells + 1), c->stream));
+  MDK_CK(cudaMemsetAsync(s.hacc, 0, sizeof(long long) * 10 * (size_t)std::max<int64_t>(c->N_cap, 1),
+                         c->stream));
   MDK_CK(cudaMemsetAsync(c->win_fbin, 0, sizeof(long long) * 2 * c->win_nbins, c->stream));
   if (!c->win_slab.empty())
     MDK_CK(cudaMemcpyAsync(c->win_slab_dev, c->win_slab.data(), sizeof(double) * c->win_slab.size(),
@@ -1309,9 +1326,17 @@ int mdk_autotune(mdk_ctx *c, int reps, int *tpa_out, int *block_out, double *ms_
   float best_ms = -1.f;
   static const int kTpa[3] = {1, 2, 4};
   static const int kBlock[3] = {128, 256, 512};
-  for (int a = 0; a < 3; ++a)
+  // LJ: full lists in every shape, then half lists (one thread per atom)
+  for (int kind = 0; kind < (c->pot == 1 ? 2 : 1) && !r; ++kind)
+  for (int a = 0; a < 3 && !r; ++a)
     for (int b = 0; b < 3; ++b) {
-      if (c->pot == 1 && kBlock[b] > 256) continue;  // the LJ kernel takes <= 256
+      if (c->pot == 1 && kBlock[b] > 256) continue;  // the LJ kernels take <= 256
+      if (kind == 1 && kTpa[a] != 1) continue;
+      if (c->cfg.half != kind || !c->list_built) {
+        use_list_kind(c, kind);
+        r = build_now(c);
+        if (r) break;
+      }
       c->cfg.tpa = kTpa[a];
       c->cfg.block = kBlock[b];
       r = force_pass(c, kForceOnly, 0, 0.0);  // warm-up (and grid set-up)
@@ -1331,8 +1356,16 @@ int mdk_autotune(mdk_ctx *c, int reps, int *tpa_out, int *block_out, double *ms_
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->prof = prof;
-  c->cfg = r ? keep : best;
-  if (r) return r;
+  if (!r && best.half != c->cfg.half) {
+    use_list_kind(c, best.half);
+    r = build_now(c);
+  }
+  if (r) {
+    use_list_kind(c, keep.half);
+    c->cfg = keep;
+    return r;
+  }
+  c->cfg = best;
   c->forces_valid = true;  // the passes left the forces of the current positions
   c->per_atom_valid = false;
   if (tpa_out) *tpa_out = best.tpa;
@@ -1353,6 +1386,19 @@ int mdk_set_launch(mdk_ctx *c, int tpa, int block) {
     return MDK_ERR_BAD_ARG;
   c->cfg.tpa = tpa;
   c->cfg.block = block;
+  return MDK_OK;
+}
+
+int mdk_set_list_kind(mdk_ctx *c, int kind) {
+  if (check_ctx(c) || (kind != MDK_LIST_FULL && kind != MDK_LIST_HALF)) return MDK_ERR_BAD_ARG;
+  if (kind == MDK_LIST_HALF && c->pot != 1) return c->pot == 0 ? MDK_ERR_ORDER : MDK_ERR_BAD_ARG;
+  use_list_kind(c, kind);
+  return MDK_OK;
+}
+
+int mdk_get_list_kind(const mdk_ctx *c, int *kind) {
+  if (check_ctx(c) || !kind) return MDK_ERR_BAD_ARG;
+  *kind = c->cfg.half ? MDK_LIST_HALF : MDK_LIST_FULL;
   return MDK_OK;
 }
 

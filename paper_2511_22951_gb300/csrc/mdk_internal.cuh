@@ -25,6 +25,9 @@ namespace mdk {
 // 1 eV/(Angstrom u) in Angstrom/fs^2 (elementary charge / atomic mass unit,
 // 1e-10 m, 1e-30 s^2).
 constexpr double kAcc = 9.648533212331e-3;
+// fixed-point unit of the mixed path's half-list accumulators: 2^-40
+// (eV/A, eV); an atom's total must stay below 2^23 in magnitude
+constexpr double kHalfScale = 1099511627776.0;
 
 constexpr int kMaxTypes = 16;
 constexpr int kMaxLang = 8;  // Langevin regions
@@ -91,6 +94,11 @@ struct Sys {
   void *pgF;                // EAM: gather copy with F'(rho_j) in .w (density pass)
   int32_t *nnbr;
   uint32_t *nbr;
+  int half;                 // 1: half lists (each pair once, Newton's third law)
+  // half-list accumulators, [10][N_cap] 8-byte words: F_x, F_y, F_z, U_i,
+  // W_i[6]; int64 fixed point (kHalfScale) in the mixed path, double in the
+  // FP64 path; zero between force passes
+  long long *hacc;
   double *ea, *ka, *wa;     // per-atom U_i, K_i, W_i[6] (SoA)
   double *rho;
   void *fp;                 // F'(rho_i): double (FP64) or float (mixed)
@@ -291,10 +299,14 @@ void launch_set_rebuild_flag(const Sys &s, cudaStream_t st);
 struct LaunchCfg {
   int tpa = 1;      // threads per atom: 1, 2 or 4
   int block = 256;  // threads per block: 128, 256 or 512
+  int half = 0;     // LJ: 1 = half lists with accumulating atomics (tpa 1)
 };
 
 void launch_lj(const Sys &s, const LJParams &p, int precision, Mode mode, StepArgs a,
                const LaunchCfg &cfg, cudaStream_t st);
+// half lists: the pair pass with accumulating atomics, then the per-atom pass
+void launch_lj_half(const Sys &s, const LJParams &p, int precision, Mode mode, StepArgs a,
+                    const LaunchCfg &cfg, cudaStream_t st);
 void launch_eam(const Sys &s, const EAMParams &p, int precision, Mode mode, StepArgs a,
                 const LaunchCfg &cfg, cudaStream_t st);
 void launch_kick_drift(const Sys &s, int precision, StepArgs a, cudaStream_t st);

@@ -31,6 +31,8 @@ MDK_ERR_TOO_LARGE = -11
 MDK_ERR_CAPACITY = -12
 MDK_FP64 = 0
 MDK_MIXED = 1
+MDK_LIST_FULL = 0
+MDK_LIST_HALF = 1
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -70,6 +72,8 @@ SIGNATURES = {
     "mdk_last_device_status": [_P, ctypes.POINTER(_I)],
     "mdk_autotune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)],
     "mdk_set_launch": [_P, _I, _I],
+    "mdk_set_list_kind": [_P, _I],
+    "mdk_get_list_kind": [_P, ctypes.POINTER(_I)],
     "mdk_set_graphs": [_P, _I],
     "mdk_profile": [_P, _I],
     "mdk_get_profile": [_P, _P],
@@ -364,7 +368,8 @@ class Context:
         return int(b.value), int(s.value)
 
     def autotune(self, reps=3):
-        """Pick threads-per-atom and block size by timing every shape."""
+        """Pick threads-per-atom and block size by timing every shape (LJ:
+        full and half lists; `list_kind` tells which won)."""
         t, b, ms = _I(), _I(), _D()
         _check(self.lib.mdk_autotune(self.h, reps, ctypes.byref(t), ctypes.byref(b),
                                      ctypes.byref(ms)), "mdk_autotune")
@@ -375,6 +380,18 @@ class Context:
 
     def set_launch(self, tpa, block):
         _check(self.lib.mdk_set_launch(self.h, tpa, block), "mdk_set_launch")
+
+    def set_list_kind(self, kind):
+        """'full' (every atom lists all its neighbours) or 'half' (each
+        pair once, Newton's third law with accumulating atomics; LJ only)."""
+        k = {"full": MDK_LIST_FULL, "half": MDK_LIST_HALF}[kind]
+        _check(self.lib.mdk_set_list_kind(self.h, k), "mdk_set_list_kind")
+
+    @property
+    def list_kind(self):
+        k = _I()
+        _check(self.lib.mdk_get_list_kind(self.h, ctypes.byref(k)), "mdk_get_list_kind")
+        return "half" if k.value == MDK_LIST_HALF else "full"
 
     def profile(self, enable=True):
         _check(self.lib.mdk_profile(self.h, 1 if enable else 0), "mdk_profile")
