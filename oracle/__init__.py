@@ -64,6 +64,10 @@ def lib():
         L.ora_md_run.argtypes = [I64, P, P, P, P, P, P, I, P, I, D, P, P, I, D, P, D, D,
                                  I64, I, P, D, P, P]
         L.ora_md_run.restype = I64
+        L.ora_bpnn_set_model.argtypes = [D, I, P, P, I, P, P, I, I, P, P, P, P, P, D]
+        L.ora_bpnn_set_model.restype = I
+        L.ora_bpnn.argtypes = [I64, P, P, P, P, P, P, P, P, P, P, P]
+        L.ora_bpnn.restype = I
         L.ora_profiles.argtypes = [I64, P, P, P, P, P, I, D, D, I, D, P]
         L.ora_profiles.restype = None
         L.ora_window_apply.argtypes = [I64, I64, P, P, P, P, P, P, D, D, D, D, D, D, D, P,
@@ -280,6 +284,68 @@ def md_run(x, v, masses, lo, hi, periodic, dt, nsteps, skin, lj_params=None,
                               _p(pis), u_p, _p(thermo), _p(F))
     if nb < 0:
         raise RuntimeError(f"oracle md_run failed ({nb})")
+    return {"x": x, "v": v, "F": F, "thermo": thermo[:nsteps], "n_builds": int(nb)}
+
+
+def _bpnn_set(model):
+    """Hand the model to the oracle (it keeps one model at a time)."""
+    rk = np.ascontiguousarray(model.rad_kind, dtype=np.int32)
+    ak = np.ascontiguousarray(model.ang_kind, dtype=np.int32)
+    rp = _f64(model.rad_par).reshape(-1)
+    ap = _f64(model.ang_par).reshape(-1)
+    H1, H2 = model.W01.shape[1], model.W12.shape[1]
+    r = lib().ora_bpnn_set_model(model.rc, rk.shape[0], _p(rk), _p(rp), ak.shape[0], _p(ak),
+                                 _p(ap), H1, H2, _p(_f64(model.W01)), _p(_f64(model.b1)),
+                                 _p(_f64(model.W12)), _p(_f64(model.b2)), _p(_f64(model.w23)),
+                                 float(model.b3))
+    if r != 0:
+        raise ValueError("oracle rejected the BPNN model")
+
+
+def bpnn(x, lo, hi, periodic, model, per_atom=False, descriptors=False):
+    """BPNN by brute force over all atoms and images within R_c: returns
+    dict(E, F, W[6]) plus Ea, Wa [N, 6] (per_atom) and G, dEdG [N, n_in]
+    (descriptors)."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    lo, hi, per = _box(lo, hi, periodic)
+    _bpnn_set(model)
+    E = np.zeros(1)
+    F = np.zeros((n, 3))
+    W = np.zeros(6)
+    Ea = np.zeros(n) if per_atom else None
+    Wa = np.zeros((n, 6)) if per_atom else None
+    G = np.zeros((n, model.n_in)) if descriptors else None
+    dG = np.zeros((n, model.n_in)) if descriptors else None
+    r = lib().ora_bpnn(n, _p(x), _p(lo), _p(hi), _p(per), _p(E), _p(F), _p(W), _p(Ea), _p(Wa),
+                       _p(G), _p(dG))
+    if r < 0:
+        raise RuntimeError("oracle bpnn failed")
+    out = {"E": float(E[0]), "F": F, "W": W}
+    if per_atom:
+        out["Ea"] = Ea
+        out["Wa"] = Wa
+    if descriptors:
+        out["G"] = G
+        out["dEdG"] = dG
+    return out
+
+
+def md_bpnn(x, v, masses, lo, hi, periodic, dt, nsteps, skin, model, rebuild_every=0):
+    """Velocity-Verlet NVE with Verlet lists and the BPNN model."""
+    x = _f64(x, (-1, 3)).copy()
+    v = _f64(v, (-1, 3)).copy()
+    n = x.shape[0]
+    m = _f64(masses, (n,))
+    lo, hi, per = _box(lo, hi, periodic)
+    _bpnn_set(model)
+    thermo = np.zeros((max(nsteps, 1), 3))
+    F = np.zeros((n, 3))
+    nb = lib().ora_md_run(n, _p(x), _p(v), _p(m), _p(lo), _p(hi), _p(per), 2, None, 0, 0.0,
+                          None, None, 0, 0.0, None, skin, dt, nsteps, rebuild_every, None, 0.0,
+                          _p(thermo), _p(F))
+    if nb < 0:
+        raise RuntimeError(f"oracle md_bpnn failed ({nb})")
     return {"x": x, "v": v, "F": F, "thermo": thermo[:nsteps], "n_builds": int(nb)}
 
 

@@ -456,7 +456,7 @@ static double embed(const ora_table *t, double rho, double *d, int *flag) {
 /* ---------------------------------------------------------------------- */
 
 typedef struct {
-    int kind;              /* 0 = LJ, 1 = EAM */
+    int kind;              /* 0 = LJ, 1 = EAM, 2 = BPNN (model set separately) */
     /* LJ */
     double eps, sigma, rc;
     int shift_mode;
@@ -506,6 +506,15 @@ static void pot_eam_init(ora_pot *p, int nr, double rc, const double *phi,
     table_init(&p->F, F, nrho, rho_max);
 }
 
+static double bpnn_rc(void);
+
+/* BPNN: only the cutoff lives here; the model is the one set last */
+static void pot_bpnn_init(ora_pot *p) {
+    memset(p, 0, sizeof(*p));
+    p->kind = 2;
+    p->rc = bpnn_rc();
+}
+
 static void pot_free(ora_pot *p) {
     if (p->kind == 1) {
         free(p->phi.m);
@@ -523,11 +532,18 @@ static void pot_free(ora_pot *p) {
  * f_i = sum_j [phi'(r) + (F'(rho_i) + F'(rho_j)) rho'(r)] d_ij / r.
  * Per-atom outputs may be NULL.  Returns a bitmask: 1 = rho above the F table.
  */
+static int bpnn_from_list(int64_t N, const double *x, const ora_box *b, const int64_t *off,
+                          const int32_t *jl, const int32_t *nl, double *E, double *F,
+                          double *W, double *Ea, double *Wa, double *G_out,
+                          double *dEdG_out);
+
 static int forces_from_list(const ora_pot *p, int64_t N, const double *x,
                             const ora_box *b, const int64_t *off,
                             const int32_t *jl, const int32_t *nl, double *E,
                             double *F, double *W, double *Ea, double *Wa,
                             double *rho_out, double *fp_out) {
+    if (p->kind == 2)   /* BPNN: the model set by ora_bpnn_set_model */
+        return bpnn_from_list(N, x, b, off, jl, nl, E, F, W, Ea, Wa, NULL, NULL);
     int flag = 0;
     double rc2 = p->rc * p->rc;
     double Etot = 0.0;
@@ -920,8 +936,11 @@ static int64_t md_run_impl(int64_t N, double *x, double *v, const double *mass,
     ora_pot p;
     if (kind == 0)
         pot_lj_init(&p, lj_par[0], lj_par[1], lj_par[2], (int)lj_par[3]);
+    else if (kind == 2)
+        pot_bpnn_init(&p);
     else
         pot_eam_init(&p, nr, rc_eam, phi, rho, nrho, rho_max, Ftab);
+    if (kind == 2 && !(p.rc > 0.0)) return -3;
     double rns = p.rc + skin;
     for (int k = 0; k < 3; ++k)
         if (b.per[k] && b.L[k] < rns) return -1;
@@ -1600,4 +1619,331 @@ int ora_eam_jvp(int64_t N, const double *x, const double *lo, const double *hi, 
     free(vl.j);
     free(vl.n);
     return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Behler-Parrinello neural-network potential (Sec. "Molecular dynamics   */
+/* with Behler-Parrinello neural networks")                               */
+/* ---------------------------------------------------------------------- */
+/*
+ * E = sum_i E_i (Eq. E_as_sum).  Atom i's input layer is a set of symmetry
+ * functions of its neighbourhood N(i) (atoms, with their periodic images,
+ * closer than R_c), cut off smoothly by
+ *     f_c(R) = 1/2 [cos(pi R / R_c) + 1]  for R <= R_c,  0 beyond
+ * (the printed form puts the "+ 1" inside the cosine; read as the standard
+ * cutoff, which is the only reading with f_c(R_c) = 0).
+ * Radial functions (Eqs. G1-G3):
+ *     G1 = sum_j f_c(R_ij)
+ *     G2 = sum_j exp(-eta (R_ij - R_s)^2) f_c(R_ij)   (read with the square of
+ *          the Gaussian the paper says it takes from Behler; without it R_s
+ *          would only rescale the function)
+ *     G3 = sum_j cos(kappa R_ij) f_c(R_ij)
+ * Angular functions (Eqs. G4, G5), over the unordered pairs {j, k} of
+ * distinct neighbours of i (each angle once):
+ *     G4 = 2^(1-zeta) sum (1 + lambda cos theta_ijk)^zeta
+ *          exp(-eta (R_ij^2 + R_ik^2 + R_jk^2)) f_c(R_ij) f_c(R_ik) f_c(R_jk)
+ *     G5 = the same without the R_jk terms.
+ * Atomic network (Eq. AtomicNN, with the activations as the text states them:
+ * tanh on both hidden layers, the output linear):
+ *     h1 = tanh(b1 + G W01),  h2 = tanh(b2 + h1 W12),  E_i = b3 + h2 . w23.
+ * Forces (Eq. force): F_k = -sum_i sum_mu dE_i/dG_mu(i) dG_mu(i)/dR_k, with
+ * dE_i/dG from the network's reverse pass and dG/dR analytic.
+ * Virial: atom i carries the virial of its own energy, W_i = -sum_j r_ij (x)
+ * dE_i/dR_j over its neighbours j (r_ij = R_j + image - R_i), which for a
+ * pair energy E_i = 1/2 sum V reduces to the pair virial used for LJ/EAM.
+ */
+typedef struct {
+    int set;
+    double rc;
+    int n_rad, n_ang, H1, H2;
+    int rad_kind[64];
+    double rad_par[128];   /* G2: (eta, R_s); G3: (kappa, 0); G1: unused */
+    int ang_kind[128];
+    double ang_par[384];   /* (zeta, lambda, eta) */
+    double *W01, *b1, *W12, *b2, *w23;
+    double b3;
+} ora_bpnn_model;
+
+static ora_bpnn_model g_bp;
+
+static double bpnn_rc(void) { return g_bp.set ? g_bp.rc : 0.0; }
+
+int ora_bpnn_set_model(double rc, int n_rad, const int *rad_kind, const double *rad_par,
+                       int n_ang, const int *ang_kind, const double *ang_par, int H1, int H2,
+                       const double *W01, const double *b1, const double *W12,
+                       const double *b2, const double *w23, double b3) {
+    if (!(rc > 0.0) || n_rad < 0 || n_rad > 64 || n_ang < 0 || n_ang > 128 ||
+        n_rad + n_ang < 1 || H1 < 1 || H2 < 1)
+        return -1;
+    free(g_bp.W01);
+    free(g_bp.b1);
+    free(g_bp.W12);
+    free(g_bp.b2);
+    free(g_bp.w23);
+    memset(&g_bp, 0, sizeof(g_bp));
+    int G = n_rad + n_ang;
+    g_bp.rc = rc;
+    g_bp.n_rad = n_rad;
+    g_bp.n_ang = n_ang;
+    g_bp.H1 = H1;
+    g_bp.H2 = H2;
+    for (int m = 0; m < n_rad; ++m) {
+        g_bp.rad_kind[m] = rad_kind[m];
+        g_bp.rad_par[2 * m] = rad_par[2 * m];
+        g_bp.rad_par[2 * m + 1] = rad_par[2 * m + 1];
+    }
+    for (int m = 0; m < n_ang; ++m) {
+        g_bp.ang_kind[m] = ang_kind[m];
+        for (int c = 0; c < 3; ++c) g_bp.ang_par[3 * m + c] = ang_par[3 * m + c];
+    }
+    g_bp.W01 = (double *)malloc(sizeof(double) * (size_t)(G * H1));
+    g_bp.b1 = (double *)malloc(sizeof(double) * (size_t)H1);
+    g_bp.W12 = (double *)malloc(sizeof(double) * (size_t)(H1 * H2));
+    g_bp.b2 = (double *)malloc(sizeof(double) * (size_t)H2);
+    g_bp.w23 = (double *)malloc(sizeof(double) * (size_t)H2);
+    memcpy(g_bp.W01, W01, sizeof(double) * (size_t)(G * H1));
+    memcpy(g_bp.b1, b1, sizeof(double) * (size_t)H1);
+    memcpy(g_bp.W12, W12, sizeof(double) * (size_t)(H1 * H2));
+    memcpy(g_bp.b2, b2, sizeof(double) * (size_t)H2);
+    memcpy(g_bp.w23, w23, sizeof(double) * (size_t)H2);
+    g_bp.b3 = b3;
+    g_bp.set = 1;
+    return 0;
+}
+
+static const double ORA_PI = 3.14159265358979323846;
+
+/* f_c(R) and its derivative */
+static double bp_fc(double R, double rc, double *d) {
+    if (R >= rc) {
+        *d = 0.0;
+        return 0.0;
+    }
+    double a = ORA_PI / rc;
+    *d = -0.5 * a * sin(a * R);
+    return 0.5 * (cos(a * R) + 1.0);
+}
+
+/* radial symmetry function m of one neighbour at R: value, derivative */
+static double bp_radial(int m, double R, double *d) {
+    double fd, f = bp_fc(R, g_bp.rc, &fd);
+    int kind = g_bp.rad_kind[m];
+    double p0 = g_bp.rad_par[2 * m], p1 = g_bp.rad_par[2 * m + 1];
+    if (kind == 1) {
+        *d = fd;
+        return f;
+    }
+    if (kind == 2) {
+        double t = R - p1;
+        double e = exp(-p0 * t * t);
+        *d = e * (-2.0 * p0 * t * f + fd);
+        return e * f;
+    }
+    /* kind 3 */
+    double c = cos(p0 * R), s = sin(p0 * R);
+    *d = -p0 * s * f + c * fd;
+    return c * f;
+}
+
+/*
+ * Angular term of function m for the neighbours u, w of atom i (vectors
+ * from i) and s = w - u: value, and the gradients with respect to u, w.
+ */
+static double bp_angular(int m, const double u[3], const double w[3], double gu[3],
+                         double gw[3]) {
+    double zeta = g_bp.ang_par[3 * m], lam = g_bp.ang_par[3 * m + 1];
+    double eta = g_bp.ang_par[3 * m + 2];
+    int kind = g_bp.ang_kind[m];
+    double s[3] = {w[0] - u[0], w[1] - u[1], w[2] - u[2]};
+    double Ru = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double Rw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double Rs = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    double dot = u[0] * w[0] + u[1] * w[1] + u[2] * w[2];
+    double c = dot / (Ru * Rw);
+    double base = 1.0 + lam * c;
+    double A = pow(base, zeta);
+    double dA = zeta * lam * pow(base, zeta - 1.0);   /* dA/dc */
+    double coef = pow(2.0, 1.0 - zeta);
+    double fud, fu = bp_fc(Ru, g_bp.rc, &fud);
+    double fwd, fw = bp_fc(Rw, g_bp.rc, &fwd);
+    double fsd = 0.0, fs = 1.0;
+    double r2sum = Ru * Ru + Rw * Rw;
+    if (kind == 4) {
+        fs = bp_fc(Rs, g_bp.rc, &fsd);
+        r2sum += Rs * Rs;
+    }
+    double e = exp(-eta * r2sum);
+    double Y = e * fu * fw * fs;
+    /* dY/dR_u, dY/dR_w, dY/dR_s (scalar, along each length) */
+    double Yu = e * fw * fs * (-2.0 * eta * Ru * fu + fud);
+    double Yw = e * fu * fs * (-2.0 * eta * Rw * fw + fwd);
+    double Ys = kind == 4 ? e * fu * fw * (-2.0 * eta * Rs * fs + fsd) : 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double dc_du = w[k] / (Ru * Rw) - c * u[k] / (Ru * Ru);
+        double dc_dw = u[k] / (Ru * Rw) - c * w[k] / (Rw * Rw);
+        double ds = kind == 4 ? Ys * s[k] / Rs : 0.0;   /* dY/ds along s */
+        /* s = w - u: d/du picks -ds, d/dw picks +ds */
+        gu[k] = coef * (dA * dc_du * Y + A * (Yu * u[k] / Ru - ds));
+        gw[k] = coef * (dA * dc_dw * Y + A * (Yw * w[k] / Rw + ds));
+    }
+    return coef * A * Y;
+}
+
+/*
+ * Energies, forces and virials from a CSR list of (j, image) entries (any
+ * list that contains every neighbour closer than R_c; entries beyond R_c are
+ * skipped).  G_out [N][G] and dEdG_out [N][G] may be NULL.
+ */
+static int bpnn_from_list(int64_t N, const double *x, const ora_box *b, const int64_t *off,
+                          const int32_t *jl, const int32_t *nl, double *E, double *F,
+                          double *W, double *Ea, double *Wa, double *G_out,
+                          double *dEdG_out) {
+    if (!g_bp.set) return -1;
+    const int G = g_bp.n_rad + g_bp.n_ang, H1 = g_bp.H1, H2 = g_bp.H2;
+    const double rc = g_bp.rc, rc2 = rc * rc;
+    double Etot = 0.0, Wt[6] = {0, 0, 0, 0, 0, 0};
+    if (F) memset(F, 0, sizeof(double) * 3 * (size_t)N);
+    double *Gv = (double *)malloc(sizeof(double) * (size_t)G);
+    double *dG = (double *)malloc(sizeof(double) * (size_t)G);
+    double *h1 = (double *)malloc(sizeof(double) * (size_t)H1);
+    double *h2 = (double *)malloc(sizeof(double) * (size_t)H2);
+    double *d1 = (double *)malloc(sizeof(double) * (size_t)H1);
+    double *d2 = (double *)malloc(sizeof(double) * (size_t)H2);
+    int64_t cap = 256;
+    double *u = (double *)malloc(sizeof(double) * 3 * (size_t)cap);
+    int64_t *js = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    double *g = (double *)malloc(sizeof(double) * 3 * (size_t)cap);
+    for (int64_t i = 0; i < N; ++i) {
+        /* the neighbourhood N(i) */
+        int64_t n = 0;
+        for (int64_t q = off[i]; q < off[i + 1]; ++q) {
+            double d[3];
+            double r2 = pair_vec(x + 3 * i, x + 3 * (int64_t)jl[q], nl + 3 * q, b, d);
+            if (!(r2 < rc2)) continue;
+            if (n == cap) {
+                cap *= 2;
+                u = (double *)realloc(u, sizeof(double) * 3 * (size_t)cap);
+                js = (int64_t *)realloc(js, sizeof(int64_t) * (size_t)cap);
+                g = (double *)realloc(g, sizeof(double) * 3 * (size_t)cap);
+            }
+            for (int k = 0; k < 3; ++k) u[3 * n + k] = d[k];
+            js[n] = jl[q];
+            ++n;
+        }
+        /* symmetry functions */
+        for (int m = 0; m < G; ++m) Gv[m] = 0.0;
+        for (int64_t a = 0; a < n; ++a) {
+            double R = sqrt(u[3 * a] * u[3 * a] + u[3 * a + 1] * u[3 * a + 1] +
+                            u[3 * a + 2] * u[3 * a + 2]);
+            for (int m = 0; m < g_bp.n_rad; ++m) {
+                double dd;
+                Gv[m] += bp_radial(m, R, &dd);
+            }
+        }
+        for (int64_t a = 0; a < n; ++a)
+            for (int64_t c = a + 1; c < n; ++c)
+                for (int m = 0; m < g_bp.n_ang; ++m) {
+                    double gu[3], gw[3];
+                    Gv[g_bp.n_rad + m] += bp_angular(m, u + 3 * a, u + 3 * c, gu, gw);
+                }
+        /* atomic network: forward, then the reverse pass to dE_i/dG */
+        for (int j = 0; j < H1; ++j) {
+            double z = g_bp.b1[j];
+            for (int m = 0; m < G; ++m) z += Gv[m] * g_bp.W01[m * H1 + j];
+            h1[j] = tanh(z);
+        }
+        for (int k = 0; k < H2; ++k) {
+            double z = g_bp.b2[k];
+            for (int j = 0; j < H1; ++j) z += h1[j] * g_bp.W12[j * H2 + k];
+            h2[k] = tanh(z);
+        }
+        double Ei = g_bp.b3;
+        for (int k = 0; k < H2; ++k) Ei += h2[k] * g_bp.w23[k];
+        for (int k = 0; k < H2; ++k) d2[k] = g_bp.w23[k] * (1.0 - h2[k] * h2[k]);
+        for (int j = 0; j < H1; ++j) {
+            double t = 0.0;
+            for (int k = 0; k < H2; ++k) t += g_bp.W12[j * H2 + k] * d2[k];
+            d1[j] = t * (1.0 - h1[j] * h1[j]);
+        }
+        for (int m = 0; m < G; ++m) {
+            double t = 0.0;
+            for (int j = 0; j < H1; ++j) t += g_bp.W01[m * H1 + j] * d1[j];
+            dG[m] = t;
+        }
+        if (G_out) memcpy(G_out + (size_t)i * G, Gv, sizeof(double) * (size_t)G);
+        if (dEdG_out) memcpy(dEdG_out + (size_t)i * G, dG, sizeof(double) * (size_t)G);
+        /* g_a = dE_i/dR_(j_a), Eq. force */
+        for (int64_t a = 0; a < 3 * n; ++a) g[a] = 0.0;
+        for (int64_t a = 0; a < n; ++a) {
+            double R = sqrt(u[3 * a] * u[3 * a] + u[3 * a + 1] * u[3 * a + 1] +
+                            u[3 * a + 2] * u[3 * a + 2]);
+            double s = 0.0;
+            for (int m = 0; m < g_bp.n_rad; ++m) {
+                double dd;
+                bp_radial(m, R, &dd);
+                s += dG[m] * dd;
+            }
+            for (int k = 0; k < 3; ++k) g[3 * a + k] += s * u[3 * a + k] / R;
+        }
+        for (int64_t a = 0; a < n; ++a)
+            for (int64_t c = a + 1; c < n; ++c)
+                for (int m = 0; m < g_bp.n_ang; ++m) {
+                    double gu[3], gw[3];
+                    bp_angular(m, u + 3 * a, u + 3 * c, gu, gw);
+                    for (int k = 0; k < 3; ++k) {
+                        g[3 * a + k] += dG[g_bp.n_rad + m] * gu[k];
+                        g[3 * c + k] += dG[g_bp.n_rad + m] * gw[k];
+                    }
+                }
+        double wi[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t a = 0; a < n; ++a) {
+            const double *ga = g + 3 * a, *ua = u + 3 * a;
+            if (F)
+                for (int k = 0; k < 3; ++k) {
+                    F[3 * js[a] + k] -= ga[k];   /* -dE_i/dR_j */
+                    F[3 * i + k] += ga[k];       /* dE_i/dR_i = -sum_a g_a */
+                }
+            wi[0] -= ua[0] * ga[0];
+            wi[1] -= ua[1] * ga[1];
+            wi[2] -= ua[2] * ga[2];
+            wi[3] -= ua[0] * ga[1];
+            wi[4] -= ua[0] * ga[2];
+            wi[5] -= ua[1] * ga[2];
+        }
+        if (Ea) Ea[i] = Ei;
+        if (Wa)
+            for (int c = 0; c < 6; ++c) Wa[6 * i + c] = wi[c];
+        Etot += Ei;
+        for (int c = 0; c < 6; ++c) Wt[c] += wi[c];
+    }
+    if (E) *E = Etot;
+    if (W)
+        for (int c = 0; c < 6; ++c) W[c] = Wt[c];
+    free(Gv);
+    free(dG);
+    free(h1);
+    free(h2);
+    free(d1);
+    free(d2);
+    free(u);
+    free(js);
+    free(g);
+    return 0;
+}
+
+/* BPNN by brute force over all atoms and images within R_c (the definition). */
+int ora_bpnn(int64_t N, const double *x, const double *lo, const double *hi, const int *per,
+             double *E, double *F, double *W, double *Ea, double *Wa, double *G_out,
+             double *dEdG_out) {
+    if (!g_bp.set) return -1;
+    ora_box b = make_box(lo, hi, per);
+    ora_vlist vl;
+    memset(&vl, 0, sizeof(vl));
+    vl.off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N + 1));
+    if (brute_list(N, x, &b, g_bp.rc, &vl) != 0) return -2;
+    int r = bpnn_from_list(N, x, &b, vl.off, vl.j, vl.n, E, F, W, Ea, Wa, G_out, dEdG_out);
+    free(vl.off);
+    free(vl.j);
+    free(vl.n);
+    return r;
 }

@@ -248,6 +248,65 @@ class Workload:
         return self.lj.rc if self.potential == "lj" else self.eam.rc
 
 
+@dataclasses.dataclass
+class BPNNModel:
+    """A Behler-Parrinello potential (Sec. "Molecular dynamics with
+    Behler-Parrinello neural networks"): the cutoff R_c, the symmetry-function
+    parameters and the atomic network's weights.  Parameters only."""
+    rc: float
+    rad_kind: np.ndarray      # int32 [n_rad]: 1, 2 or 3 (G1, G2, G3)
+    rad_par: np.ndarray       # [n_rad, 2]: G2 (eta, R_s), G3 (kappa, 0), G1 unused
+    ang_kind: np.ndarray      # int32 [n_ang]: 4 or 5 (G4, G5)
+    ang_par: np.ndarray       # [n_ang, 3]: (zeta, lambda, eta); zeta a positive integer
+    W01: np.ndarray           # [G, H1], G = n_rad + n_ang
+    b1: np.ndarray            # [H1]
+    W12: np.ndarray           # [H1, H2]
+    b2: np.ndarray            # [H2]
+    w23: np.ndarray           # [H2]
+    b3: float
+
+    @property
+    def n_rad(self) -> int:
+        return int(self.rad_kind.shape[0])
+
+    @property
+    def n_ang(self) -> int:
+        return int(self.ang_kind.shape[0])
+
+    @property
+    def n_in(self) -> int:
+        return self.n_rad + self.n_ang
+
+
+def maise_like_bpnn(seed: int = 0, rc: float = 6.0, hidden=(10, 10), n_rad: int = 8,
+                    n_ang: int = 43, w_in: float = 0.05, e_scale: float = 0.5,
+                    e0: float = -3.0) -> BPNNModel:
+    """Synthetic model with the layout the paper reports for MAISE's trained
+    potentials: 8 G2 functions (one R_s, different eta) and 43 G4 functions
+    per element, two hidden layers of 10.  The trained weights are not
+    available, so the weights are seeded Gaussians: W01 ~ N(0, w_in^2),
+    W12 ~ N(0, 1/H1), w23 ~ N(0, e_scale^2 / H2), biases ~ N(0, 0.01),
+    b3 = e0 (eV)."""
+    rng = np.random.default_rng(seed)
+    H1, H2 = hidden
+    rad_kind = np.full(n_rad, 2, dtype=np.int32)
+    etas = np.geomspace(0.003, 0.5, n_rad) if n_rad > 1 else np.array([0.05])
+    rad_par = np.stack([etas, np.zeros(n_rad)], 1)
+    combos = [(z, lam, eta) for eta in (0.0005, 0.003, 0.01, 0.02, 0.035, 0.06)
+              for z in (1.0, 2.0, 4.0, 16.0) for lam in (1.0, -1.0)]
+    ang_par = np.array(combos[:n_ang], dtype=np.float64).reshape(-1, 3)
+    ang_kind = np.full(ang_par.shape[0], 4, dtype=np.int32)
+    G = n_rad + ang_par.shape[0]
+    return BPNNModel(rc=rc, rad_kind=rad_kind, rad_par=rad_par, ang_kind=ang_kind,
+                     ang_par=ang_par,
+                     W01=rng.normal(0.0, w_in, size=(G, H1)),
+                     b1=rng.normal(0.0, 0.1, size=H1),
+                     W12=rng.normal(0.0, 1.0 / np.sqrt(H1), size=(H1, H2)),
+                     b2=rng.normal(0.0, 0.1, size=H2),
+                     w23=rng.normal(0.0, e_scale / np.sqrt(H2), size=H2),
+                     b3=float(e0))
+
+
 def lattice_system(rng, n_cells, a, mass, T, periodic=(1, 1, 1), sigma_jitter=0.0,
                    origin=(0.0, 0.0, 0.0), box_pad=None) -> System:
     nx, ny, nz = n_cells
