@@ -99,6 +99,8 @@ def algorithmic_bytes_per_atom(wl, prec, n_list, kind="full"):
     lj = g + 4 * n_list + 4 + 48 + 48 + 24 + 4 + g
     if wl.potential == "lj":
         return lj + (48 if kind == "half" else 0)
+    if wl.potential == "bpnn":   # full list, force accumulators like half lists
+        return lj + 48
     r = 4 if prec == "mixed" else 8
     return lj + g + 4 * n_list + 4 + 8 + r + r
 
@@ -140,6 +142,32 @@ def traffic_per_launch(wl, prec, n_atoms, kind="full"):
 # pair twice; that doubling is overhead, not algorithmic work.
 FLOPS_PER_PAIR = {"lj": 23.0, "eam": 62.0}
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal dense FP64 (no measured figure exists)
+# FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP at the
+# maximum SM clock (2070 MHz); no measured FP32 figure exists
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def bpnn_flops_per_atom(m, n):
+    """Algorithmic FP work of one BPNN force pass per atom with n neighbours
+    within R_c (one FMA = 2, a transcendental = 1), counted from the
+    arithmetic of the method: per unordered neighbour pair, the angular
+    forward terms (cosine and pair geometry 21, each (eta, kind) group 7, each
+    zeta group 12, each function 2) and the gradients of both neighbours from
+    one evaluation (geometry 50, each group 30, each zeta group 8, each
+    function 16); per neighbour, the radial functions (16 each); per atom,
+    the network forward and reverse pass.  The kernel evaluates each
+    pair's gradient once per ordered pair (twice), which is overhead and not
+    counted."""
+    ak = np.asarray(m.ang_kind)
+    ap = np.asarray(m.ang_par).reshape(-1, 3)
+    nY = len({(float(e), int(k)) for e, k in zip(ap[:, 2], ak)})
+    nZ = len({float(z) for z in ap[:, 0]})
+    nS, nR = ap.shape[0], int(np.asarray(m.rad_kind).shape[0])
+    H1, H2 = m.W01.shape[1], m.W12.shape[1]
+    pairs = n * (n - 1) / 2.0
+    per_pair = (21 + 7 * nY + 12 * nZ + 2 * nS) + (50 + 30 * nY + 8 * nZ + 16 * nS)
+    net = 2 * 2 * ((nR + nS) * H1 + H1 * H2 + H2) + 4 * (H1 + H2)
+    return pairs * per_pair + n * 16 * nR + net
 
 
 def pair_count_within_rc(ctx, wl, sample=20000, seed=0):
@@ -306,28 +334,43 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+def _lattice_of(wl):
+    """(a, T, mass) of the workload's lattice."""
+    if wl.potential == "lj":
+        return 5.26, 80.0, wl.lj.mass
+    if wl.potential == "bpnn":
+        return 4.05, 300.0, W.MASS_AL
+    return wl.eam.a0, 300.0, wl.eam.mass
+
+
+def _oracle_md(wl, x, v, s, nsteps):
+    import oracle
+    if wl.potential == "bpnn":
+        return oracle.md_bpnn(x, v, s.masses, s.lo, s.hi, s.periodic, wl.dt, nsteps, wl.skin,
+                              wl.extra["bpnn"])
+    kw = {"lj_params": wl.lj} if wl.potential == "lj" else {"tables": wl.tables}
+    return oracle.md_run(x, v, s.masses, s.lo, s.hi, s.periodic, wl.dt, nsteps, wl.skin, **kw)
+
+
 def oracle_rate(wl, n_cells, nsteps):
     """Oracle (cell-list Verlet MD, FP64, one host thread) on an FCC n^3-cell
     sub-box of the workload: returns atom-timesteps/s and the sample size."""
-    import oracle
-    a = 5.26 if wl.potential == "lj" else wl.eam.a0
-    T = 80.0 if wl.potential == "lj" else 300.0
+    a, T, mass = _lattice_of(wl)
     rng = np.random.default_rng(100)
-    mass = wl.lj.mass if wl.potential == "lj" else wl.eam.mass
     s = W.lattice_system(rng, (n_cells,) * 3, a, mass, T)
-    kw = {"lj_params": wl.lj} if wl.potential == "lj" else {"tables": wl.tables}
     t0 = time.perf_counter()
-    oracle.md_run(s.x, s.v, s.masses, s.lo, s.hi, s.periodic, wl.dt, nsteps, wl.skin, **kw)
+    _oracle_md(wl, s.x, s.v, s, nsteps)
     t = time.perf_counter() - t0
     return s.n * nsteps / t, s.n, t
 
 
 def cpu_baseline(wl, budget_s=15.0):
     # calibrate on a small box, then size the sample for ~budget_s of work
-    rate0, _, _ = oracle_rate(wl, 6, 4)
-    steps = 20
+    small = 3 if wl.potential == "bpnn" else 6   # BPNN: ~25 ms per atom-step
+    rate0, _, _ = oracle_rate(wl, small, 2 if wl.potential == "bpnn" else 4)
+    steps = 4 if wl.potential == "bpnn" else 20
     target_atoms = rate0 * budget_s / steps
-    n_cells = int(max(6, min(40, round((target_atoms / 4) ** (1 / 3)))))
+    n_cells = int(max(small, min(40, round((target_atoms / 4) ** (1 / 3)))))
     rate, n, t = oracle_rate(wl, n_cells, steps)
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n} atoms ({n_cells}^3 FCC cells of the same lattice, potential, "
@@ -342,19 +385,15 @@ def run_reference(args, wl):
     import oracle
     oracle.build()
     # size each step so that warmup + steps end within ~90 s
-    rate0, _, _ = oracle_rate(wl, 6, 4)
+    small = 3 if wl.potential == "bpnn" else 6
+    rate0, _, _ = oracle_rate(wl, small, 2 if wl.potential == "bpnn" else 4)
     per_step_atoms = rate0 * 90.0 / max(1, args.steps + args.warmup)
     n_cells = int(max(3, min(40, round((per_step_atoms / 4) ** (1 / 3)))))
-    a = 5.26 if wl.potential == "lj" else wl.eam.a0
-    T = 80.0 if wl.potential == "lj" else 300.0
-    mass = wl.lj.mass if wl.potential == "lj" else wl.eam.mass
+    a, T, mass = _lattice_of(wl)
     s = W.lattice_system(np.random.default_rng(100), (n_cells,) * 3, a, mass, T)
-    kw = {"lj_params": wl.lj} if wl.potential == "lj" else {"tables": wl.tables}
-    out = oracle.md_run(s.x, s.v, s.masses, s.lo, s.hi, s.periodic, wl.dt, args.warmup,
-                        wl.skin, **kw)
+    out = _oracle_md(wl, s.x, s.v, s, args.warmup)
     t0 = time.perf_counter()
-    oracle.md_run(out["x"], out["v"], s.masses, s.lo, s.hi, s.periodic, wl.dt, args.steps,
-                  wl.skin, **kw)
+    _oracle_md(wl, out["x"], out["v"], s, args.steps)
     t = time.perf_counter() - t0
     val = s.n * args.steps / t
     sample = (f"{s.n} atoms ({n_cells}^3 FCC cells of the workload's lattice, potential, "
@@ -391,6 +430,9 @@ def main():
                     help="config 3 as the paper's stationary-shock window (inflow/outflow)")
     ap.add_argument("--langevin", default=None,
                     help="T,beta: a Langevin thermostat on the whole system (K, 1/fs)")
+    ap.add_argument("--bpnn", action="store_true",
+                    help="Behler-Parrinello workload: Al-like FCC 40^3 = 256,000 atoms, "
+                         "synthetic 8 G2 + 43 G4 model, 10-10 network")
     ap.add_argument("--launch", default=None,
                     help="threads-per-atom x block (e.g. 1x128) instead of the autotuner")
     ap.add_argument("--list", default=None, choices=("full", "half"),
@@ -403,6 +445,8 @@ def main():
         ap.error("--list goes with --launch (the autotuner picks the list kind)")
     args.warmup = max(3, args.warmup)
     wl = workload(args.config, args.cells)
+    if args.bpnn:
+        wl = W.bpnn_workload()
     grid = None
     if args.hugoniot:
         from paper_2511_22951_gb300 import hugoniot as H
@@ -526,7 +570,18 @@ def main():
               "rebuild_share_of_step": prof["rebuild_ms"] / (ms * prof_steps / args.steps),
               "timed_from": f"CUDA events around each of {int(prof['force_passes'])} force "
                             f"passes of a {prof_steps}-step profiled segment"}
-    if prec == "mixed":
+    if wl.potential == "bpnn":
+        fpa = bpnn_flops_per_atom(wl.extra["bpnn"], n_rc)
+        tflops = n_now * fpa / (force_ms / 1e3) / 1e12
+        pk = FP32_PEAK_TFLOPS if prec == "mixed" else FP64_PEAK_TFLOPS
+        common["kernel"] = (f"k_bpnn<{prec}> (descriptors, network, gradients; one warp per "
+                            "atom) + k_half_fin per-atom velocity-Verlet pass")
+        roof = {"bound": "alu", "achieved": tflops, "peak": pk, "unit": "TFLOP/s",
+                "frac": tflops / pk, "traffic": None, "flops_per_atom": fpa,
+                "peak_kind": ("FP32 FMA peak from unit counts (152 SMs x 128 lanes x 2 x "
+                              "2070 MHz)" if prec == "mixed" else "GB300 nominal dense FP64"),
+                **common}
+    elif prec == "mixed":
         tr = traffic_per_launch(wl, prec, n_now, kind)
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                 "frac": gbs / hbm, "traffic": tr, "bytes_per_atom": bpa,

@@ -135,6 +135,36 @@ int mdk_set_potential_eam(mdk_ctx *ctx, int nr, double rc, const double *phi,
                           const double *rho, int nrho, double rho_max,
                           const double *F);
 
+/*
+ * Behler-Parrinello neural-network potential (Sec. "Molecular dynamics with
+ * Behler-Parrinello neural networks"), single element: E = sum_i E_i, E_i
+ * from atom i's network applied to its symmetry functions over the
+ * neighbours closer than rc, cut off by f_c(R) = 1/2 [cos(pi R/rc) + 1]:
+ *   rad_kind[m] 1: G1 = sum_j f_c(R_ij)                        (rad_par unused)
+ *               2: G2 = sum_j exp(-eta (R_ij - R_s)^2) f_c(R_ij)  rad_par = (eta, R_s)
+ *               3: G3 = sum_j cos(kappa R_ij) f_c(R_ij)          rad_par = (kappa, -)
+ *   ang_kind[m] 4: G4 = 2^(1-zeta) sum_{j<k} (1 + lambda cos theta_ijk)^zeta
+ *                   exp(-eta (R_ij^2 + R_ik^2 + R_jk^2)) f_c(R_ij) f_c(R_ik) f_c(R_jk)
+ *               5: G5 = the same without the R_jk factors
+ *               ang_par = (zeta, lambda, eta): zeta an integer in [1, 64],
+ *               lambda = +1 or -1; sums over unordered pairs of distinct
+ *               neighbours (each angle once).
+ * Network input G = [radial functions, angular functions] in the order
+ * given; h1 = tanh(b1 + G W01), h2 = tanh(b2 + h1 W12), E_i = b3 + h2 . w23.
+ *   W01 [n_rad + n_ang][H1], b1 [H1], W12 [H1][H2], b2 [H2], w23 [H2] (host,
+ *   row-major, copied).
+ * Forces F_k = -dE/dR_k (Eq. force); the virial of E_i is kept by atom i.
+ * Limits (else MDK_ERR_BAD_ARG): n_rad <= 8; n_ang <= 64 with at most 8
+ * distinct (eta, kind) and at most 4 distinct zeta among the angular
+ * functions, no function given twice; 1 <= H1, H2 <= 32; finite values.
+ * Runs on full lists (a half list kind is reset to full).
+ */
+int mdk_set_potential_bpnn(mdk_ctx *ctx, double rc, int n_rad, const int *rad_kind,
+                           const double *rad_par, int n_ang, const int *ang_kind,
+                           const double *ang_par, int H1, int H2, const double *W01,
+                           const double *b1, const double *W12, const double *b2,
+                           const double *w23, double b3);
+
 /* ---- device memory ---------------------------------------------------- */
 
 /* Bytes of device workspace the context needs for its current capacity,

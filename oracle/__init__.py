@@ -3,8 +3,9 @@
 A plain FP64 C implementation (``oracle.c``) of what the hot path computes,
 written from the paper: brute-force neighbour sets over all periodic images,
 the paper's cell-list Verlet-list algorithm, LJ and tabulated-EAM energies,
-forces and virials, velocity-Verlet NVE integration and the Appendix per-bin
-statistics.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of
+forces and virials, velocity-Verlet NVE integration, the Appendix per-bin
+statistics, the moving window, Langevin thermostats, the EAM adjoint and the
+Behler-Parrinello potential.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of
 ``bench.py`` may import this package; the CUDA product path never does.
 
 Parity pins (what fixes the oracle independently of itself) live in

@@ -30,6 +30,9 @@
  *     knots, in reverse mode and (independently) forward mode
  *   - Langevin thermostat regions (Sec. "Molecular dynamics" and "Moving
  *     window simulation") with the Philox4x64-10 counter-based generator
+ *   - the Behler-Parrinello potential (Sec. "Molecular dynamics with
+ *     Behler-Parrinello neural networks"): symmetry functions G1-G5, the
+ *     atomic network, forces by Eq. force (see the BPNN section below)
  *
  * Readings of the paper that this file fixes:
  *   * pair vector d_ij = (x_j - x_i) + n*L, rounded in that order;

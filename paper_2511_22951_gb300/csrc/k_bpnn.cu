@@ -1,0 +1,538 @@
+// k_bpnn.cu -- Behler-Parrinello neural-network forces (GB300, sm_103a).
+//
+// Paper passages (Sec. "Molecular dynamics with Behler-Parrinello neural
+// networks"): E = sum_i E_i (Eq. E_as_sum); atom i's network input is a set
+// of radial (Eqs. G1-G3) and angular (Eqs. G4, G5) symmetry functions of its
+// neighbourhood within R_c, cut off by f_c(R) = 1/2 [cos(pi R / R_c) + 1];
+// E_i comes from a two-hidden-layer network (Eq. AtomicNN: tanh, tanh,
+// linear output); the forces follow Eq. force, F_k = -sum_i sum_mu
+// dE_i/dG_mu(i) dG_mu(i)/dR_k, with dE_i/dG from the network's reverse pass
+// and dG/dR analytic.  G2 is read with the square, (R - R_s)^2; angular sums
+// run over unordered pairs of distinct neighbours.
+//
+// One warp per atom i:
+//  1. the list entries within R_c are compacted into the warp's shared slab:
+//     pair vector u_a, R_a, f_c(R_a), f_c'(R_a) and exp(-eta_p R_a^2) for
+//     every (eta, kind) group p of the angular functions;
+//  2. radial functions, lanes over neighbours; angular functions, lanes over
+//     unordered pairs {a, b}; warp sums;
+//  3. the network forward and reverse pass (lanes over hidden units, weights
+//     staged in shared memory per block) gives E_i and dE_i/dG;
+//  4. lane a takes neighbour a and walks every b != a: g_a = dE_i/dR_(j_a)
+//     collects the radial term and, per angular term T(u_a, u_b, s = u_b -
+//     u_a), dT/du_a - dT/ds.  Atom j_a receives -g_a, atom i receives
+//     sum_a g_a (E_i depends on relative positions only), and i keeps the
+//     virial -sum_a u_a (x) g_a of its own energy.
+// The pair term of each ordered pair (a, b) is evaluated once in step 4 and
+// once per unordered pair in step 2.  Forces are added to the per-atom
+// accumulators s.hacc (64-bit fixed point in the mixed path, FP64 atomics in
+// the FP64 path); launch_half_fin then finishes the step.  The mixed path
+// computes in FP32; a neighbour gradient at or above 2^22 eV/A sets the
+// non-finite status.
+#include "k_pair.cuh"
+
+namespace mdk {
+namespace {
+
+using namespace pair;
+
+template <class R>
+struct BM;
+template <>
+struct BM<float> {
+  static __device__ __forceinline__ void scpi(float x, float *s, float *c) { sincospif(x, s, c); }
+  static __device__ __forceinline__ float ex(float x) { return __expf(x); }
+  static __device__ __forceinline__ float th(float x) { return tanhf(x); }
+  static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ void sc(float x, float *s, float *c) { sincosf(x, s, c); }
+  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+};
+template <>
+struct BM<double> {
+  static __device__ __forceinline__ void scpi(double x, double *s, double *c) {
+    sincospi(x, s, c);
+  }
+  static __device__ __forceinline__ double ex(double x) { return exp(x); }
+  static __device__ __forceinline__ double th(double x) { return tanh(x); }
+  static __device__ __forceinline__ double sq(double x) { return sqrt(x); }
+  static __device__ __forceinline__ void sc(double x, double *s, double *c) { sincos(x, s, c); }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+};
+
+// a parameter in the pair precision
+template <class R>
+__device__ __forceinline__ R pick(double d, float f) {
+  return sizeof(R) == 8 ? (R)d : (R)f;
+}
+
+// x^e for a small non-negative integer e (uniform across the warp)
+template <class R>
+__device__ __forceinline__ R ipow(R x, int e) {
+  R r = R(1);
+  while (e) {
+    if (e & 1) r *= x;
+    x *= x;
+    e >>= 1;
+  }
+  return r;
+}
+
+template <class R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// per-warp shared slab: fields of NB neighbour slots (SoA), then the
+// descriptor / gradient / hidden vectors
+template <class R>
+struct Slab {
+  R *ux, *uy, *uz, *rr, *fc, *dfc, *e;  // e: [nY][NB]
+  int *j;
+  R *G, *dG, *h1, *d1, *d2, *wc;  // wc: dE/dG of each angular slot
+};
+
+constexpr int kVec = 80;  // >= kBpIn, a multiple of 16
+static_assert(kVec >= kBpIn, "device network inputs");
+
+template <class R>
+__device__ __forceinline__ Slab<R> slab_at(char *base, int NB, int nY) {
+  Slab<R> s;
+  R *p = reinterpret_cast<R *>(base);
+  s.ux = p;
+  s.uy = p + NB;
+  s.uz = p + 2 * NB;
+  s.rr = p + 3 * NB;
+  s.fc = p + 4 * NB;
+  s.dfc = p + 5 * NB;
+  s.e = p + 6 * NB;
+  p += (size_t)(6 + nY) * NB;
+  s.G = p;
+  s.dG = p + kVec;
+  s.h1 = p + 2 * kVec;
+  s.d1 = p + 2 * kVec + 32;
+  s.d2 = p + 2 * kVec + 64;
+  s.wc = p + 2 * kVec + 96;
+  s.j = reinterpret_cast<int *>(p + 2 * kVec + 96 + kBpSlots);
+  return s;
+}
+
+__host__ __device__ inline size_t slab_bytes(int NB, int nY, size_t rsz) {
+  size_t b = rsz * ((size_t)(6 + nY) * NB + 2 * kVec + 96 + kBpSlots) +
+             sizeof(int) * (size_t)NB;
+  return (b + 15) / 16 * 16;
+}
+
+// radial symmetry function m at R (f = f_c(R), df = f_c'(R)): value and
+// derivative
+template <class R>
+__device__ __forceinline__ void radial(const BPParams &bp, int m, R r, R f, R df, R &val,
+                                       R &der) {
+  const int kind = bp.rad_kind[m];
+  const R p0 = pick<R>(bp.rad_p0[m], bp.rad_p0f[m]);
+  if (kind == 1) {
+    val = f;
+    der = df;
+  } else if (kind == 2) {
+    const R p1 = pick<R>(bp.rad_p1[m], bp.rad_p1f[m]);
+    const R t = r - p1;
+    const R e = BM<R>::ex(-p0 * t * t);
+    val = e * f;
+    der = e * (R(-2) * p0 * t * f + df);
+  } else {
+    R sn, cs;
+    BM<R>::sc(p0 * r, &sn, &cs);
+    val = cs * f;
+    der = -p0 * sn * f + cs * df;
+  }
+}
+
+template <class P, bool ENERGY>
+__global__ void k_bpnn(Sys s, BPParams bp, StepArgs a) {
+  using GP = G<P>;
+  using H = HalfAcc<P>;
+  using R = typename GP::R;
+  using V = typename GP::V;
+  extern __shared__ __align__(16) char smem[];
+  const int N = s.st->N;
+  const size_t Nc = s.N_cap;
+  const int NB = s.nmax;
+  const int nY = bp.nY, nZ = bp.nZ, nr = bp.n_rad, H1 = bp.H1, H2 = bp.H2;
+  constexpr int n_in = kBpIn;
+  const unsigned long long used = bp.slot_mask;
+  const R rc = pick<R>(bp.rc, bp.rcf), rc2 = rc * rc, inv_rc = R(1) / rc;
+  const R half_pi_rc = R(-0.5) * R(3.14159265358979323846) * inv_rc;
+  // weights, once per block
+  const int nW = n_in * H1 + H1 + H1 * H2 + 2 * H2;
+  R *Wsm = reinterpret_cast<R *>(smem);
+  {
+    const R *src = sizeof(R) == 8 ? reinterpret_cast<const R *>(bp.w64)
+                                  : reinterpret_cast<const R *>(bp.w32);
+    for (int q = threadIdx.x; q < nW; q += blockDim.x) Wsm[q] = src[q];
+  }
+  __syncthreads();
+  const R *W01 = Wsm, *b1 = W01 + n_in * H1, *W12 = b1 + H1, *b2 = W12 + H1 * H2,
+          *w23 = b2 + H2;
+  const size_t wbytes = ((size_t)nW * sizeof(R) + 15) / 16 * 16;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Slab<R> sl = slab_at<R>(smem + wbytes + (size_t)warp * slab_bytes(NB, nY, sizeof(R)), NB, nY);
+  const int i = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (i >= N) return;  // whole warps leave together
+
+  // ---- 1. the neighbourhood within R_c ----------------------------------
+  const V *__restrict__ pg = (const V *)s.pg[a.cur];
+  const V pi = GP::ld(pg + i);
+  R hx, hy, hz;
+  GP::h(s.grid[GP::info(pi) >> 8], hx, hy, hz);
+  const int nn = min(s.nnbr[i], s.nmax);
+  int n = 0;
+  for (int k0 = 0; k0 < nn; k0 += 32) {
+    const int k = k0 + lane;
+    bool keep = false;
+    R dx = 0, dy = 0, dz = 0, r2 = 0;
+    uint32_t j = 0;
+    if (k < nn) {
+      const uint32_t ent = s.nbr[ell_index(k, i, Nc)];
+      j = ent & kJMask;
+      const V pj = GP::ld(pg + j);
+      dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
+      dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
+      dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
+      r2 = dx * dx + dy * dy + dz * dz;
+      keep = r2 < rc2;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int q = n + __popc(m & ((1u << lane) - 1u));
+      const R r = BM<R>::sq(r2);
+      R sn, cs;
+      BM<R>::scpi(r * inv_rc, &sn, &cs);
+      sl.ux[q] = dx;
+      sl.uy[q] = dy;
+      sl.uz[q] = dz;
+      sl.rr[q] = r;
+      sl.fc[q] = R(0.5) * (cs + R(1));
+      sl.dfc[q] = half_pi_rc * sn;
+      for (int p = 0; p < nY; ++p)
+        sl.e[p * NB + q] = BM<R>::ex(-pick<R>(bp.y_eta[p], bp.y_etaf[p]) * r2);
+      sl.j[q] = (int)j;
+    }
+    n += __popc(m);
+  }
+  __syncwarp();
+
+  // ---- 2. symmetry functions ----------------------------------------------
+  R accr[kBpRad];
+#pragma unroll
+  for (int m = 0; m < kBpRad; ++m) accr[m] = 0;
+  for (int q = lane; q < n; q += 32) {
+    const R r = sl.rr[q], f = sl.fc[q], df = sl.dfc[q];
+#pragma unroll
+    for (int m = 0; m < kBpRad; ++m)
+      if (m < nr) {
+        R v, d;
+        radial<R>(bp, m, r, f, df, v, d);
+        accr[m] += v;
+      }
+  }
+  R acca[kBpSlots];
+#pragma unroll
+  for (int m = 0; m < kBpSlots; ++m) acca[m] = 0;
+  {
+    const int npair = n * (n - 1) / 2;
+    int qa = 0, rel = lane;  // pair t = (qa, qa + 1 + rel), rows in order of qa
+    while (qa < n - 1 && rel >= n - 1 - qa) {
+      rel -= n - 1 - qa;
+      ++qa;
+    }
+    for (int t = lane; t < npair; t += 32) {
+      const int qb = qa + 1 + rel;
+      const R ax = sl.ux[qa], ay = sl.uy[qa], az = sl.uz[qa], ra = sl.rr[qa], fa = sl.fc[qa];
+      const R bx = sl.ux[qb], by = sl.uy[qb], bz = sl.uz[qb], rb = sl.rr[qb], fb = sl.fc[qb];
+      const R c = (ax * bx + ay * by + az * bz) * BM<R>::rcp(ra * rb);
+      const R sx = bx - ax, sy = by - ay, sz = bz - az;
+      const R rab2 = sx * sx + sy * sy + sz * sz;
+      const bool near = bp.any4 && rab2 < rc2;
+      R fab = 0;
+      if (near) {
+        R sn, cs;
+        BM<R>::scpi(BM<R>::sq(rab2) * inv_rc, &sn, &cs);
+        fab = R(0.5) * (cs + R(1));
+      }
+      R Y[kBpY];
+#pragma unroll
+      for (int p = 0; p < kBpY; ++p)
+        if (p < nY) {
+          Y[p] = sl.e[p * NB + qa] * sl.e[p * NB + qb] * fa * fb;
+          if (bp.y_kind[p] == 4)
+            Y[p] = near ? Y[p] * BM<R>::ex(-pick<R>(bp.y_eta[p], bp.y_etaf[p]) * rab2) * fab
+                        : R(0);
+        }
+      // 2^(1 - zeta) (1 +- c)^zeta per zeta group
+      R Pp[kBpZ], Pm[kBpZ];
+#pragma unroll
+      for (int z = 0; z < kBpZ; ++z)
+        if (z < nZ) {
+          const R cf = pick<R>(bp.z_coef[z], bp.z_coeff[z]);
+          Pp[z] = cf * ipow<R>(R(1) + c, bp.z_pow[z]) * (R(1) + c);
+          Pm[z] = cf * ipow<R>(R(1) - c, bp.z_pow[z]) * (R(1) - c);
+        }
+#pragma unroll
+      for (int p = 0; p < kBpY; ++p)
+#pragma unroll
+        for (int z = 0; z < kBpZ; ++z) {
+          const int m = (p * kBpZ + z) * 2;
+          if ((used >> m) & 1ull) acca[m] += Pp[z] * Y[p];
+          if ((used >> (m + 1)) & 1ull) acca[m + 1] += Pm[z] * Y[p];
+        }
+      rel += 32;
+      while (qa < n - 1 && rel >= n - 1 - qa) {
+        rel -= n - 1 - qa;
+        ++qa;
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < kBpRad; ++m)
+    if (m < nr) accr[m] = warp_sum(accr[m]);
+#pragma unroll
+  for (int m = 0; m < kBpSlots; ++m)
+    if ((used >> m) & 1ull) acca[m] = warp_sum(acca[m]);
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < kBpRad; ++m) sl.G[m] = m < nr ? accr[m] : R(0);
+#pragma unroll
+    for (int m = 0; m < kBpSlots; ++m) sl.G[kBpRad + m] = ((used >> m) & 1ull) ? acca[m] : R(0);
+  }
+  __syncwarp();
+
+  // ---- 3. the atomic network and its reverse pass -------------------------
+  R h1 = 0;
+  if (lane < H1) {
+    R z = b1[lane];
+    for (int m = 0; m < n_in; ++m) z += sl.G[m] * W01[m * H1 + lane];
+    h1 = BM<R>::th(z);
+  }
+  sl.h1[lane] = h1;
+  __syncwarp();
+  R h2 = 0;
+  if (lane < H2) {
+    R z = b2[lane];
+    for (int q = 0; q < H1; ++q) z += sl.h1[q] * W12[q * H2 + lane];
+    h2 = BM<R>::th(z);
+  }
+  const R Ei = warp_sum(lane < H2 ? h2 * w23[lane] : R(0)) + pick<R>(bp.b3, bp.b3f);
+  sl.d2[lane] = lane < H2 ? w23[lane] * (R(1) - h2 * h2) : R(0);
+  __syncwarp();
+  R d1 = 0;
+  if (lane < H1) {
+    for (int q = 0; q < H2; ++q) d1 += W12[lane * H2 + q] * sl.d2[q];
+    d1 *= R(1) - h1 * h1;
+  }
+  sl.d1[lane] = d1;
+  __syncwarp();
+  for (int m = lane; m < n_in; m += 32) {
+    R t = 0;
+    for (int q = 0; q < H1; ++q) t += W01[m * H1 + q] * sl.d1[q];
+    sl.dG[m] = t;
+    if (m >= kBpRad) sl.wc[m - kBpRad] = t;
+  }
+  __syncwarp();
+
+  // ---- 4. gradients with respect to the neighbours ------------------------
+  // atom i's share is summed from the same rounded terms its neighbours get
+  // (the mixed path's forces then sum to exactly zero)
+  using Q = typename H::Q;
+  Q fix = 0, fiy = 0, fiz = 0;
+  R w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+  bool bad = false;
+  long long *acc = s.hacc;
+  for (int qa = lane; qa < n; qa += 32) {
+    const R ax = sl.ux[qa], ay = sl.uy[qa], az = sl.uz[qa], ra = sl.rr[qa];
+    const R fa = sl.fc[qa], dfa = sl.dfc[qa];
+    const R inv_ra = BM<R>::rcp(ra);
+    R sr = 0;
+#pragma unroll
+    for (int m = 0; m < kBpRad; ++m)
+      if (m < nr) {
+        R v, d;
+        radial<R>(bp, m, ra, fa, dfa, v, d);
+        sr += sl.dG[m] * d;
+      }
+    R gx = sr * inv_ra * ax, gy = sr * inv_ra * ay, gz = sr * inv_ra * az;
+    R ea[kBpY];
+#pragma unroll
+    for (int p = 0; p < kBpY; ++p)
+      if (p < nY) ea[p] = sl.e[p * NB + qa];
+    for (int qb = 0; qb < n; ++qb) {
+      if (qb == qa) continue;
+      const R bx = sl.ux[qb], by = sl.uy[qb], bz = sl.uz[qb], rb = sl.rr[qb], fb = sl.fc[qb];
+      const R inv_ab = BM<R>::rcp(ra * rb);
+      const R c = (ax * bx + ay * by + az * bz) * inv_ab;
+      const R sx = bx - ax, sy = by - ay, sz = bz - az;
+      const R rab2 = sx * sx + sy * sy + sz * sz;
+      const bool near = bp.any4 && rab2 < rc2;
+      R fab = 0, dfab = 0, inv_rab = 0;
+      if (near) {
+        const R rab = BM<R>::sq(rab2);
+        R sn, cs;
+        BM<R>::scpi(rab * inv_rc, &sn, &cs);
+        fab = R(0.5) * (cs + R(1));
+        dfab = half_pi_rc * sn;
+        inv_rab = BM<R>::rcp(rab);
+      }
+      // per (eta, kind) group: Y, (dY/dR_a)/R_a and (dY/dR_ab)/R_ab
+      R Y[kBpY], Yu[kBpY], Ys[kBpY];
+#pragma unroll
+      for (int p = 0; p < kBpY; ++p)
+        if (p < nY) {
+          const R eta = pick<R>(bp.y_eta[p], bp.y_etaf[p]);
+          const R eb = ea[p] * sl.e[p * NB + qb] * fb;
+          R ex = R(1);
+          if (bp.y_kind[p] == 4) ex = near ? BM<R>::ex(-eta * rab2) * fab : R(0);
+          Y[p] = eb * fa * ex;
+          Yu[p] = eb * ex * (R(-2) * eta * ra * fa + dfa) * inv_ra;
+          Ys[p] = (bp.y_kind[p] == 4 && near)
+                      ? eb * fa * BM<R>::ex(-eta * rab2) *
+                            (R(-2) * eta * BM<R>::sq(rab2) * fab + dfab) * inv_rab
+                      : R(0);
+        }
+      // per zeta group: 2^(1 - zeta) (1 +- c)^(zeta - 1)
+      R Pp[kBpZ], Pm[kBpZ];
+#pragma unroll
+      for (int z = 0; z < kBpZ; ++z)
+        if (z < nZ) {
+          const R cf = pick<R>(bp.z_coef[z], bp.z_coeff[z]);
+          Pp[z] = cf * ipow<R>(R(1) + c, bp.z_pow[z]);
+          Pm[z] = cf * ipow<R>(R(1) - c, bp.z_pow[z]);
+        }
+      // T = A(c) Y: dT/du_a = A' Y dc/du_a + A Yu u_a, dT/ds = A Ys s, with
+      // A = 2^(1-zeta) (1 + lambda c)^zeta, A' = zeta lambda 2^(1-zeta) (1 + lambda c)^(zeta-1)
+      R al = 0, be = 0, ga = 0;
+#pragma unroll
+      for (int p = 0; p < kBpY; ++p)
+#pragma unroll
+        for (int z = 0; z < kBpZ; ++z) {
+          const int m = (p * kBpZ + z) * 2;
+          const R zt = pick<R>(bp.z_zeta[z], bp.z_zetaf[z]);
+          if ((used >> m) & 1ull) {  // lambda = +1
+            const R w = sl.wc[m], A = Pp[z] * (R(1) + c);
+            al += w * zt * Pp[z] * Y[p];
+            be += w * A * Yu[p];
+            ga += w * A * Ys[p];
+          }
+          if ((used >> (m + 1)) & 1ull) {  // lambda = -1
+            const R w = sl.wc[m + 1], A = Pm[z] * (R(1) - c);
+            al -= w * zt * Pm[z] * Y[p];
+            be += w * A * Yu[p];
+            ga += w * A * Ys[p];
+          }
+        }
+      // dc/du_a = u_b / (R_a R_b) - c u_a / R_a^2; dT/dR_a = dT/du_a - dT/ds
+      const R cq = c * inv_ra * inv_ra;
+      gx += al * (bx * inv_ab - cq * ax) + be * ax - ga * sx;
+      gy += al * (by * inv_ab - cq * ay) + be * ay - ga * sy;
+      gz += al * (bz * inv_ab - cq * az) + be * az - ga * sz;
+    }
+    // g = dE_i/dR_(j_a): -g to atom j_a, +g to atom i, virial -u (x) g
+    const int j = sl.j[qa];
+    if (sizeof(R) == 4)
+      bad = bad || !(fabs(gx) < R(4194304) && fabs(gy) < R(4194304) && fabs(gz) < R(4194304));
+    const Q qx = H::q(gx), qy = H::q(gy), qz = H::q(gz);
+    H::red(acc + j, -qx);
+    H::red(acc + Nc + j, -qy);
+    H::red(acc + 2 * Nc + j, -qz);
+    fix += qx;
+    fiy += qy;
+    fiz += qz;
+    if (ENERGY) {
+      w0 -= ax * gx;
+      w1 -= ay * gy;
+      w2 -= az * gz;
+      w3 -= ax * gy;
+      w4 -= ax * gz;
+      w5 -= ay * gz;
+    }
+  }
+  fix = warp_sum(fix);
+  fiy = warp_sum(fiy);
+  fiz = warp_sum(fiz);
+  if (ENERGY) {
+    w0 = warp_sum(w0);
+    w1 = warp_sum(w1);
+    w2 = warp_sum(w2);
+    w3 = warp_sum(w3);
+    w4 = warp_sum(w4);
+    w5 = warp_sum(w5);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&s.st->bits, kStNonfinite);
+  if (lane == 0) {
+    H::red(acc + i, fix);
+    H::red(acc + Nc + i, fiy);
+    H::red(acc + 2 * Nc + i, fiz);
+    if (ENERGY) {
+      H::red(acc + 3 * Nc + i, H::q(Ei));
+      H::red(acc + 4 * Nc + i, H::q(w0));
+      H::red(acc + 5 * Nc + i, H::q(w1));
+      H::red(acc + 6 * Nc + i, H::q(w2));
+      H::red(acc + 7 * Nc + i, H::q(w3));
+      H::red(acc + 8 * Nc + i, H::q(w4));
+      H::red(acc + 9 * Nc + i, H::q(w5));
+    }
+  }
+}
+
+int warps_for(int precision) { return precision == 0 ? 4 : 8; }
+
+}  // namespace
+
+size_t bpnn_smem_bytes(const BPParams &p, int precision, int nmax, int *warps) {
+  const size_t rsz = precision == 0 ? 8 : 4;
+  const int nW = kBpIn * p.H1 + p.H1 + p.H1 * p.H2 + 2 * p.H2;
+  const size_t wbytes = ((size_t)nW * rsz + 15) / 16 * 16;
+  const size_t per = slab_bytes(nmax, p.nY, rsz);
+  int w = warps_for(precision);
+  while (w > 1 && wbytes + (size_t)w * per > 200 * 1024) --w;
+  if (warps) *warps = w;
+  return wbytes + (size_t)w * per;
+}
+
+int configure_bpnn_smem(size_t bytes, int precision) {
+  const int b = (int)bytes;
+  cudaError_t e;
+  if (precision == 0) {
+    e = cudaFuncSetAttribute(k_bpnn<Fp64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_bpnn<Fp64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               b);
+  } else {
+    e = cudaFuncSetAttribute(k_bpnn<Mixed, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_bpnn<Mixed, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               b);
+  }
+  return e == cudaSuccess ? 0 : 1;
+}
+
+void launch_bpnn(const Sys &s, const BPParams &p, int precision, Mode mode, StepArgs a,
+                 cudaStream_t st) {
+  int w = 1;
+  const size_t sm = bpnn_smem_bytes(p, precision, s.nmax, &w);
+  const long long n = s.N_cap > 0 ? s.N_cap : 1;
+  const int grid = (int)((n + w - 1) / w);
+  if (precision == 0) {
+    if (a.energy)
+      k_bpnn<Fp64, true><<<grid, 32 * w, sm, st>>>(s, p, a);
+    else
+      k_bpnn<Fp64, false><<<grid, 32 * w, sm, st>>>(s, p, a);
+  } else {
+    if (a.energy)
+      k_bpnn<Mixed, true><<<grid, 32 * w, sm, st>>>(s, p, a);
+    else
+      k_bpnn<Mixed, false><<<grid, 32 * w, sm, st>>>(s, p, a);
+  }
+  launch_half_fin(s, precision, mode, a, st);
+}
+
+}  // namespace mdk

@@ -16,7 +16,8 @@
 // accumulator.  Forces of neighbouring threads meet in those accumulators,
 // so the velocity-Verlet update cannot be fused into this pass: k_half_fin
 // reads each atom's total, clears the accumulator for the next pass and
-// runs the same epilogue as the full-list kernel.
+// runs the same epilogue as the full-list kernel (the Behler-Parrinello
+// forces, which scatter to neighbours too, finish their steps with it).
 //
 // Mixed path: the accumulators are 64-bit fixed point (unit 2^-40 eV/A):
 // every pair term is rounded once, integer addition is associative, so the
@@ -31,38 +32,6 @@ namespace mdk {
 namespace {
 
 using namespace pair;
-
-// what the accumulators hold per precision
-template <class P>
-struct HalfAcc;
-template <>
-struct HalfAcc<Mixed> {
-  using Q = long long;
-  static __device__ __forceinline__ long long q(float v) {
-    return __float2ll_rn(v * 1099511627776.0f);  // 2^40, exact power of two
-  }
-  static __device__ __forceinline__ void red(long long *p, long long v) {
-    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
-  }
-  static __device__ __forceinline__ double take(long long *p) {
-    const long long v = *p;
-    *p = 0;
-    return (double)v * (1.0 / kHalfScale);
-  }
-};
-template <>
-struct HalfAcc<Fp64> {
-  using Q = double;
-  static __device__ __forceinline__ double q(double v) { return v; }
-  static __device__ __forceinline__ void red(long long *p, double v) {
-    atomicAdd(reinterpret_cast<double *>(p), v);
-  }
-  static __device__ __forceinline__ double take(long long *p) {
-    const double v = __longlong_as_double(*p);
-    *p = 0;  // the bit pattern of +0.0
-    return v;
-  }
-};
 
 // 64 registers (32 resident warps per SM) for the mixed force-only pass;
 // FP64 pair values and the energy/virial sums need more (128)
@@ -178,11 +147,8 @@ __global__ void __launch_bounds__(256) k_half_fin(Sys s, StepArgs a) {
 
 inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
-template <class P, bool EN, int SH>
-void go(const Sys &s, const LJParams &p, Mode m, StepArgs a, int block, cudaStream_t st) {
-  if (block > 256) block = 256;
-  const int grid = nblk(s.N_cap > 0 ? s.N_cap : 1, block);
-  k_lj_half<P, EN, SH><<<grid, block, 0, st>>>(s, p, a);
+template <class P, bool EN>
+void fin(const Sys &s, Mode m, StepArgs a, cudaStream_t st) {
   const int fb = 256, fg = nblk(s.N_cap > 0 ? s.N_cap : 1, fb);
   if (m == kForceOnly)
     k_half_fin<P, kForceOnly, EN><<<fg, fb, 0, st>>>(s, a);
@@ -190,6 +156,14 @@ void go(const Sys &s, const LJParams &p, Mode m, StepArgs a, int block, cudaStre
     k_half_fin<P, kStep, EN><<<fg, fb, 0, st>>>(s, a);
   else
     k_half_fin<P, kFinal, EN><<<fg, fb, 0, st>>>(s, a);
+}
+
+template <class P, bool EN, int SH>
+void go(const Sys &s, const LJParams &p, Mode m, StepArgs a, int block, cudaStream_t st) {
+  if (block > 256) block = 256;
+  const int grid = nblk(s.N_cap > 0 ? s.N_cap : 1, block);
+  k_lj_half<P, EN, SH><<<grid, block, 0, st>>>(s, p, a);
+  fin<P, EN>(s, m, a, st);
 }
 
 template <class P, bool EN>
@@ -209,6 +183,13 @@ void by_energy(const Sys &s, const LJParams &p, Mode m, StepArgs a, int block, c
 }
 
 }  // namespace
+
+void launch_half_fin(const Sys &s, int precision, Mode mode, StepArgs a, cudaStream_t st) {
+  if (precision == 0)
+    a.energy ? fin<Fp64, true>(s, mode, a, st) : fin<Fp64, false>(s, mode, a, st);
+  else
+    a.energy ? fin<Mixed, true>(s, mode, a, st) : fin<Mixed, false>(s, mode, a, st);
+}
 
 void launch_lj_half(const Sys &s, const LJParams &p, int precision, Mode mode, StepArgs a,
                     const LaunchCfg &cfg, cudaStream_t st) {

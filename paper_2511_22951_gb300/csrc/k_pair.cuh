@@ -245,6 +245,39 @@ struct Tiles {
   __device__ __forceinline__ int atom(int w) const { return w * kPerWarp + lane / T; }
 };
 
+// what the accumulators s.hacc hold per precision (half lists, BPNN):
+// int64 fixed point in units of 2^-40 in the mixed path, FP64 otherwise
+template <class P>
+struct HalfAcc;
+template <>
+struct HalfAcc<Mixed> {
+  using Q = long long;
+  static __device__ __forceinline__ long long q(float v) {
+    return __float2ll_rn(v * 1099511627776.0f);  // 2^40, exact power of two
+  }
+  static __device__ __forceinline__ void red(long long *p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+  }
+  static __device__ __forceinline__ double take(long long *p) {
+    const long long v = *p;
+    *p = 0;
+    return (double)v * (1.0 / kHalfScale);
+  }
+};
+template <>
+struct HalfAcc<Fp64> {
+  using Q = double;
+  static __device__ __forceinline__ double q(double v) { return v; }
+  static __device__ __forceinline__ void red(long long *p, double v) {
+    atomicAdd(reinterpret_cast<double *>(p), v);
+  }
+  static __device__ __forceinline__ double take(long long *p) {
+    const double v = __longlong_as_double(*p);
+    *p = 0;  // the bit pattern of +0.0
+    return v;
+  }
+};
+
 // ---- per-atom epilogue: store forces or integrate -----------------------------
 template <class P>
 __device__ __forceinline__ void drift_publish(const Sys &s, const StepArgs &a, int i,

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <new>
 #include <vector>
@@ -29,10 +30,15 @@ struct mdk_ctx {
   int n_types = 0;
   double type_mass[kMaxTypes] = {0};
   // potential
-  int pot = 0;  // 0 none, 1 LJ, 2 EAM
+  int pot = 0;  // 0 none, 1 LJ, 2 EAM, 3 BPNN
   LJParams lj{};
   EAMParams eam{};
   std::vector<double> eam_phi, eam_rho, eam_F;
+  BPParams bp{};
+  std::vector<double> bp_w64;  // packed device-order weights (kBpWords)
+  std::vector<float> bp_w32;
+  double *bp_w64_dev = nullptr;
+  float *bp_w32_dev = nullptr;
   // neighbour plan
   bool planned = false;
   double rc_list = 0.0, skin = 0.3;
@@ -187,6 +193,8 @@ size_t layout(mdk_ctx *c, char *base) {
   c->adj_gE = cv.take<double>(c->n_rep);
   c->adj_aux = cv.take<long long>(8);
   c->lang_rep_dev = cv.take<double>((size_t)c->n_rep * kMaxTypes * 2);
+  c->bp_w64_dev = cv.take<double>(kBpWords);
+  c->bp_w32_dev = cv.take<float>(kBpWords);
   c->eam_base = reinterpret_cast<char *>(kn);
   c->eam.phi64 = t.phi64;
   c->eam.rho64 = t.rho64;
@@ -261,6 +269,7 @@ int plan(mdk_ctx *c, double rc, double skin, int max_neighbors, int rebuild_ever
 double pot_rc(const mdk_ctx *c) {
   if (c->pot == 1) return c->lj.rc;
   if (c->pot == 2) return c->eam.rc;
+  if (c->pot == 3) return c->bp.rc;
   return 0.0;
 }
 
@@ -438,7 +447,9 @@ int force_pass(mdk_ctx *c, Mode mode, int energy, double dt) {
   StepArgs a{dt, c->cur, energy};
   const bool half = c->pot == 1 && c->cfg.half;
   return timed(c, c->ev_force, c->pot == 1 && !half ? 1 : 2, [&] {
-    if (half)
+    if (c->pot == 3)
+      launch_bpnn(c->sys, c->bp, c->precision, mode, a, c->stream);
+    else if (half)
       launch_lj_half(c->sys, c->lj, c->precision, mode, a, c->cfg, c->stream);
     else if (c->pot == 1)
       launch_lj(c->sys, c->lj, c->precision, mode, a, c->cfg, c->stream);
@@ -551,6 +562,7 @@ uint64_t graph_key(const mdk_ctx *c, double dt) {
   h = fnv(h, &c->eam, sizeof(EAMParams));
   h = fnv(h, &c->cfg, sizeof(LaunchCfg));
   h = fnv(h, &c->pot, sizeof(int));
+  h = fnv(h, &c->bp, sizeof(BPParams));
   h = fnv(h, &c->precision, sizeof(int));
   h = fnv(h, &dt, sizeof(double));
   return h;
@@ -799,6 +811,120 @@ int mdk_set_potential_eam(mdk_ctx *c, int nr, double rc, const double *phi, cons
   return MDK_OK;
 }
 
+// weights of the BPNN model into the workspace, shared-memory limit of its kernel
+int upload_bpnn(mdk_ctx *c) {
+  if (!c->bp_w64_dev || c->bp_w64.empty()) return MDK_ERR_ORDER;
+  MDK_CK(cudaMemcpyAsync(c->bp_w64_dev, c->bp_w64.data(), sizeof(double) * kBpWords,
+                         cudaMemcpyHostToDevice, c->stream));
+  MDK_CK(cudaMemcpyAsync(c->bp_w32_dev, c->bp_w32.data(), sizeof(float) * kBpWords,
+                         cudaMemcpyHostToDevice, c->stream));
+  c->bp.w64 = c->bp_w64_dev;
+  c->bp.w32 = c->bp_w32_dev;
+  if (configure_bpnn_smem(bpnn_smem_bytes(c->bp, c->precision, c->nmax, nullptr), c->precision))
+    return MDK_ERR_CUDA;
+  return MDK_OK;
+}
+
+int mdk_set_potential_bpnn(mdk_ctx *c, double rc, int n_rad, const int *rad_kind,
+                           const double *rad_par, int n_ang, const int *ang_kind,
+                           const double *ang_par, int H1, int H2, const double *W01,
+                           const double *b1, const double *W12, const double *b2,
+                           const double *w23, double b3) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  if (!(rc > 0.0) || !std::isfinite(rc) || n_rad < 0 || n_rad > kBpRad || n_ang < 0 ||
+      n_ang > kBpSlots || n_rad + n_ang < 1 || H1 < 1 || H1 > kBpH || H2 < 1 || H2 > kBpH ||
+      (n_rad > 0 && (!rad_kind || !rad_par)) || (n_ang > 0 && (!ang_kind || !ang_par)) || !W01 ||
+      !b1 || !W12 || !b2 || !w23 || !std::isfinite(b3))
+    return MDK_ERR_BAD_ARG;
+  BPParams p{};
+  p.n_rad = n_rad;
+  p.H1 = H1;
+  p.H2 = H2;
+  p.rc = rc;
+  p.rcf = (float)rc;
+  p.b3 = b3;
+  p.b3f = (float)b3;
+  for (int m = 0; m < n_rad; ++m) {
+    const int k = rad_kind[m];
+    const double p0 = rad_par[2 * m], p1 = rad_par[2 * m + 1];
+    if ((k != 1 && k != 2 && k != 3) || !std::isfinite(p0) || !std::isfinite(p1))
+      return MDK_ERR_BAD_ARG;
+    p.rad_kind[m] = k;
+    p.rad_p0[m] = p0;
+    p.rad_p1[m] = p1;
+    p.rad_p0f[m] = (float)p0;
+    p.rad_p1f[m] = (float)p1;
+  }
+  // angular functions onto the slot grid
+  std::vector<int> slot_of((size_t)n_ang);
+  for (int m = 0; m < n_ang; ++m) {
+    const int k = ang_kind[m];
+    const double zeta = ang_par[3 * m], lam = ang_par[3 * m + 1], eta = ang_par[3 * m + 2];
+    if ((k != 4 && k != 5) || !(zeta >= 1.0 && zeta <= 64.0) || zeta != floor(zeta) ||
+        (lam != 1.0 && lam != -1.0) || !std::isfinite(eta))
+      return MDK_ERR_BAD_ARG;
+    int y = -1, z = -1;
+    for (int q = 0; q < p.nY; ++q)
+      if (p.y_eta[q] == eta && p.y_kind[q] == k) y = q;
+    if (y < 0) {
+      if (p.nY == kBpY) return MDK_ERR_BAD_ARG;
+      y = p.nY++;
+      p.y_eta[y] = eta;
+      p.y_etaf[y] = (float)eta;
+      p.y_kind[y] = k;
+      if (k == 4) p.any4 = 1;
+    }
+    for (int q = 0; q < p.nZ; ++q)
+      if (p.z_zeta[q] == zeta) z = q;
+    if (z < 0) {
+      if (p.nZ == kBpZ) return MDK_ERR_BAD_ARG;
+      z = p.nZ++;
+      p.z_zeta[z] = zeta;
+      p.z_zetaf[z] = (float)zeta;
+      p.z_pow[z] = (int)zeta - 1;
+      p.z_coef[z] = ldexp(1.0, 1 - (int)zeta);
+      p.z_coeff[z] = (float)p.z_coef[z];
+    }
+    const int slot = (y * kBpZ + z) * 2 + (lam < 0.0 ? 1 : 0);
+    if ((p.slot_mask >> slot) & 1ull) return MDK_ERR_BAD_ARG;  // the same function twice
+    p.slot_mask |= 1ull << slot;
+    slot_of[(size_t)m] = slot;
+  }
+  // weights in device order: rows [radial 0..kBpRad), [slots 0..kBpSlots)
+  std::vector<double> w((size_t)kBpWords, 0.0);
+  const int G = n_rad + n_ang;
+  for (int q = 0; q < G * H1; ++q)
+    if (!std::isfinite(W01[q])) return MDK_ERR_BAD_ARG;
+  for (int m = 0; m < G; ++m) {
+    const int row = m < n_rad ? m : kBpRad + slot_of[(size_t)(m - n_rad)];
+    for (int j = 0; j < H1; ++j) w[(size_t)row * H1 + j] = W01[(size_t)m * H1 + j];
+  }
+  size_t o = (size_t)kBpIn * H1;
+  for (int j = 0; j < H1; ++j) w[o + j] = b1[j];
+  o += H1;
+  for (int q = 0; q < H1 * H2; ++q) w[o + q] = W12[q];
+  o += (size_t)H1 * H2;
+  for (int k = 0; k < H2; ++k) w[o + k] = b2[k];
+  o += H2;
+  for (int k = 0; k < H2; ++k) w[o + k] = w23[k];
+  for (double v : w)
+    if (!std::isfinite(v)) return MDK_ERR_BAD_ARG;
+  c->bp_w64 = w;
+  c->bp_w32.assign(w.begin(), w.end());
+  p.w64 = c->bp_w64_dev;
+  p.w32 = c->bp_w32_dev;
+  c->bp = p;
+  c->pot = 3;
+  use_list_kind(c, MDK_LIST_FULL);  // the BPNN pass reads full lists
+  c->forces_valid = false;
+  if (!c->planned) plan(c, rc, 0.3, 0, 0);
+  if (c->ws_ok) {
+    const int r = upload_bpnn(c);
+    if (r) return r;
+  }
+  return MDK_OK;
+}
+
 int mdk_plan_neighbors(mdk_ctx *c, double rc, double skin, int max_neighbors, int rebuild_every) {
   if (check_ctx(c)) return MDK_ERR_BAD_ARG;
   const int old_nmax = c->nmax, old_cells = c->n_cells;
@@ -858,6 +984,9 @@ int mdk_set_workspace(mdk_ctx *c, void *dev_ptr, size_t bytes) {
   if (c->N > 0)
     MDK_CK(cudaMemcpyAsync(s.info0, c->info0.data(), sizeof(uint32_t) * c->N,
                            cudaMemcpyHostToDevice, c->stream));
+  if (c->pot == 3) {
+    if (upload_bpnn(c)) return MDK_ERR_CUDA;
+  }
   if (c->pot == 2) {
     EAMParams &e = c->eam;
     double *kn = reinterpret_cast<double *>(c->eam_base);
@@ -1331,6 +1460,7 @@ int mdk_autotune(mdk_ctx *c, int reps, int *tpa_out, int *block_out, double *ms_
   for (int a = 0; a < 3 && !r; ++a)
     for (int b = 0; b < 3; ++b) {
       if (c->pot == 1 && kBlock[b] > 256) continue;  // the LJ kernels take <= 256
+      if (c->pot == 3 && (a > 0 || b > 0)) continue;  // BPNN: one warp per atom, one shape
       if (kind == 1 && kTpa[a] != 1) continue;
       if (c->cfg.half != kind || !c->list_built) {
         use_list_kind(c, kind);

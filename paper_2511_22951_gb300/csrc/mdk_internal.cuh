@@ -185,6 +185,40 @@ struct EAMParams {
   const dvec4 *pr64;
 };
 
+// Behler-Parrinello model: symmetry-function parameters by value (read as
+// constant operands inside the triplet loops), network weights in the
+// workspace (staged into shared memory per block).  The angular functions
+// sit on a fixed grid of slots, slot = (p * kBpZ + z) * 2 + (lambda < 0):
+// p the (eta, kind) group, z the zeta group; so every accumulator has a
+// compile-time register index.  The device network input is [kBpRad radial
+// values, kBpSlots slot values] (kBpIn); unused inputs have zero weights.
+constexpr int kBpRad = 8;                  // radial functions (G1, G2, G3)
+constexpr int kBpY = 8;                    // (eta, kind) groups of angular functions
+constexpr int kBpZ = 4;                    // zeta groups
+constexpr int kBpSlots = 2 * kBpY * kBpZ;  // angular slots
+constexpr int kBpIn = kBpRad + kBpSlots;   // device network inputs
+constexpr int kBpH = 32;                   // units per hidden layer
+// words of the packed weight area (largest network)
+constexpr int kBpWords = kBpIn * kBpH + kBpH + kBpH * kBpH + 2 * kBpH;
+struct BPParams {
+  int n_rad, nY, nZ, H1, H2, any4;
+  unsigned long long slot_mask;            // slots holding a function
+  double rc, b3;
+  float rcf, b3f;
+  int rad_kind[kBpRad];
+  double rad_p0[kBpRad], rad_p1[kBpRad];
+  float rad_p0f[kBpRad], rad_p1f[kBpRad];
+  double y_eta[kBpY];
+  float y_etaf[kBpY];
+  int y_kind[kBpY];                        // 4: with the R_jk factors, 5: without
+  int z_pow[kBpZ];                         // zeta - 1 (a non-negative integer)
+  double z_zeta[kBpZ], z_coef[kBpZ];       // zeta, 2^(1 - zeta)
+  float z_zetaf[kBpZ], z_coeff[kBpZ];
+  // packed weights: W01 [kBpIn][H1], b1 [H1], W12 [H1][H2], b2 [H2], w23 [H2]
+  const double *w64;
+  const float *w32;
+};
+
 // writable view of the device tables filled by launch_eam_prepare
 struct EAMTablesDev {
   double2 *phi64, *rho64, *F64;
@@ -304,6 +338,13 @@ struct LaunchCfg {
 
 void launch_lj(const Sys &s, const LJParams &p, int precision, Mode mode, StepArgs a,
                const LaunchCfg &cfg, cudaStream_t st);
+// the per-atom pass that finishes a step from the accumulators in s.hacc
+void launch_half_fin(const Sys &s, int precision, Mode mode, StepArgs a, cudaStream_t st);
+// Behler-Parrinello forces into s.hacc (full lists), then launch_half_fin
+void launch_bpnn(const Sys &s, const BPParams &p, int precision, Mode mode, StepArgs a,
+                 cudaStream_t st);
+size_t bpnn_smem_bytes(const BPParams &p, int precision, int nmax, int *warps);
+int configure_bpnn_smem(size_t bytes, int precision);
 // half lists: the pair pass with accumulating atomics, then the per-atom pass
 void launch_lj_half(const Sys &s, const LJParams &p, int precision, Mode mode, StepArgs a,
                     const LaunchCfg &cfg, cudaStream_t st);

@@ -48,6 +48,7 @@ SIGNATURES = {
     "mdk_set_capacity": [_P, _I64],
     "mdk_set_potential_lj": [_P, _D, _D, _D, _I],
     "mdk_set_potential_eam": [_P, _I, _D, _P, _P, _I, _D, _P],
+    "mdk_set_potential_bpnn": [_P, _D, _I, _P, _P, _I, _P, _P, _I, _I, _P, _P, _P, _P, _P, _D],
     "mdk_workspace_size": [_P, ctypes.POINTER(_SZ)],
     "mdk_set_workspace": [_P, _P, _SZ],
     "mdk_set_state": [_P, _P, _P, _I],
@@ -203,6 +204,24 @@ class Context:
                                               _ptr(rho), F.shape[0], tables.rho_max, _ptr(F)),
                "mdk_set_potential_eam")
         self._eam_sizes = (phi.shape[0], F.shape[0])
+        self.version += 1
+
+    def set_potential_bpnn(self, model):
+        """Behler-Parrinello model (workloads.BPNNModel-like: rc, rad_kind,
+        rad_par [n_rad, 2], ang_kind, ang_par [n_ang, 3], W01, b1, W12, b2,
+        w23, b3)."""
+        rk = np.ascontiguousarray(model.rad_kind, dtype=np.int32)
+        ak = np.ascontiguousarray(model.ang_kind, dtype=np.int32)
+        rp = _host_f64(model.rad_par, (-1,))
+        ap = _host_f64(model.ang_par, (-1,))
+        W01 = _host_f64(model.W01, (-1,))
+        W12 = _host_f64(model.W12, (-1,))
+        H1, H2 = model.W01.shape[1], model.W12.shape[1]
+        _check(self.lib.mdk_set_potential_bpnn(
+            self.h, float(model.rc), rk.shape[0], _ptr(rk), _ptr(rp), ak.shape[0], _ptr(ak),
+            _ptr(ap), H1, H2, _ptr(W01), _ptr(_host_f64(model.b1, (-1,))), _ptr(W12),
+            _ptr(_host_f64(model.b2, (-1,))), _ptr(_host_f64(model.w23, (-1,))),
+            float(model.b3)), "mdk_set_potential_bpnn")
         self.version += 1
 
     def plan(self, rc, skin, max_neighbors=0, rebuild_every=0):
@@ -479,6 +498,8 @@ def make_context(wl, precision=None, stream=None, rebuild_every=0, max_neighbors
                       n_atoms=[q.n for q in ss])
     if wl.potential == "lj":
         ctx.set_potential_lj(wl.lj.eps, wl.lj.sigma, wl.lj.rc, wl.lj.shift_mode)
+    elif wl.potential == "bpnn":
+        ctx.set_potential_bpnn(wl.extra["bpnn"])
     else:
         ctx.set_potential_eam(wl.tables)
     ctx.plan(wl.rc, wl.skin, max_neighbors, rebuild_every)

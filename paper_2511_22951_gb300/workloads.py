@@ -229,7 +229,7 @@ class System:
 class Workload:
     name: str
     systems: list                  # list[System]; one entry unless batched
-    potential: str                 # "lj" | "eam"
+    potential: str                 # "lj" | "eam" | "bpnn" (model in extra["bpnn"])
     lj: Optional[LJParams]
     eam: Optional[FSEAMParams]
     tables: Optional[EAMTables]
@@ -245,6 +245,8 @@ class Workload:
 
     @property
     def rc(self) -> float:
+        if self.potential == "bpnn":
+            return self.extra["bpnn"].rc
         return self.lj.rc if self.potential == "lj" else self.eam.rc
 
 
@@ -385,6 +387,18 @@ def config4(n_rep: int = 64, precision: str = "mixed") -> Workload:
     return Workload(f"eam_cu_coldcurve_{n_rep}rep", systems, "eam", None, CU_LIKE,
                     tabulate_fs_eam(CU_LIKE), dt=1.0, steps=1000, skin=0.3,
                     precision=precision, extra={"a": a_s, "n": n_s})
+
+
+def bpnn_workload(n: int = 40, precision: str = "mixed", seed: int = 1) -> Workload:
+    """Al-like FCC n^3 cells (40^3 = 256,000 atoms, a = 4.05 A, the EAM
+    config's lattice), 300 K, with the synthetic MAISE-layout BPNN
+    (R_c = 6 A: 54 neighbours in the lattice, 1431 neighbour pairs per atom),
+    dt = 1 fs."""
+    rng = np.random.default_rng(seed)
+    s = lattice_system(rng, (n, n, n), 4.05, MASS_AL, 300.0)
+    return Workload(f"bpnn_al_{4 * n ** 3}_{precision}", [s], "bpnn", None, None, None,
+                    dt=1.0, steps=1000, skin=0.3, precision=precision,
+                    extra={"bpnn": maise_like_bpnn(0, rc=6.0)})
 
 
 CONFIGS = {0: config0, 1: config1, 2: config2, 3: config3, 4: config4}
