@@ -520,7 +520,7 @@ def main():
         tpa, block, _ = ctx.autotune()
         picked = "mdk_autotune"
     kind = ctx.list_kind
-    n_list = float(ctx.neighbor_counts().mean())
+    n_list = n_avg if kind == "full" else 0.5 * n_avg   # a half list holds each pair once
 
     # warm-up (untimed; also captures the step graphs)
     ctx.step(wl.dt, args.warmup, check=True)

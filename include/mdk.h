@@ -462,10 +462,10 @@ int mdk_lj_compute_noalloc(const double *x, int64_t N, const double box_lo[3],
  * Autotuner: time every launch shape of the force kernels -- threads per atom
  * in {1, 2, 4} x threads per block in {128, 256, 512} (LJ: <= 256) -- on this
  * context's system (reps force passes each, CUDA events on the context's
- * stream) and keep the fastest for later calls.  With the LJ potential it
- * also times half lists (one thread per atom, 128 and 256 threads per block)
+ * stream) and keep the fastest for later calls.  With LJ and EAM it also
+ * times half lists (one thread per atom; 128 and 256 threads per block)
  * and keeps the faster list kind (mdk_get_list_kind reports it; a switch
- * rebuilds the list).  Outputs may be NULL.  Small systems (few atoms per SM)
+ * rebuilds the list).  The BPNN kernel has one shape (a warp per atom).  Outputs may be NULL.  Small systems (few atoms per SM)
  * and long lists favour several threads per atom.  The state must be set;
  * the lists are built if needed.  (No paper counterpart: the paper chunks
  * arrays over a thread pool.)
@@ -484,13 +484,16 @@ int mdk_set_launch(mdk_ctx *ctx, int tpa, int block);
  *   MDK_LIST_HALF: each unordered pair (i, j, image) appears in one of the
  *     two lists; the force pass adds f_ij to i and -f_ij to j (Newton's
  *     third law) with reduction atomics into per-atom accumulators and a
- *     second per-atom pass finishes the step.  Mixed precision accumulates
- *     in 64-bit fixed point (unit 2^-40 eV/A): bitwise reproducible, the
- *     forces sum to exactly zero, a pair term at or above 2^22 eV/A reports
- *     MDK_ERR_NONFINITE.  FP64 accumulates with FP64 atomics (reproducible
- *     to rounding, not bitwise).  LJ potential only: MDK_ERR_ORDER before a
- *     potential is set, MDK_ERR_BAD_ARG with EAM (whose passes read full
- *     lists; setting an EAM potential returns the context to full lists).
+ *     per-atom pass finishes the step (EAM: the density pass adds rho(r)
+ *     to both atoms, a per-atom pass evaluates F and F', then the force
+ *     pass).  Mixed precision accumulates in 64-bit fixed point (unit 2^-40
+ *     eV/A): bitwise reproducible, the forces sum to exactly zero, a pair
+ *     term at or above 2^22 eV/A reports MDK_ERR_NONFINITE.  FP64
+ *     accumulates with FP64 atomics (reproducible to rounding, not
+ *     bitwise).  LJ and EAM: MDK_ERR_ORDER before a potential is set,
+ *     MDK_ERR_BAD_ARG with the BPNN potential (setting one returns the
+ *     context to full lists).  mdk_eam_vjp walks full lists and switches a
+ *     half-list context back to full lists (the next call rebuilds).
  * A change of kind makes the next call rebuild the list; mdk_get_neighbors
  * returns the list of the current kind.
  */

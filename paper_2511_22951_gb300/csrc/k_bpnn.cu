@@ -18,13 +18,18 @@
 //     unordered pairs {a, b}; warp sums;
 //  3. the network forward and reverse pass (lanes over hidden units, weights
 //     staged in shared memory per block) gives E_i and dE_i/dG;
-//  4. lane a takes neighbour a and walks every b != a: g_a = dE_i/dR_(j_a)
-//     collects the radial term and, per angular term T(u_a, u_b, s = u_b -
-//     u_a), dT/du_a - dT/ds.  Atom j_a receives -g_a, atom i receives
-//     sum_a g_a (E_i depends on relative positions only), and i keeps the
-//     virial -sum_a u_a (x) g_a of its own energy.
-// The pair term of each ordered pair (a, b) is evaluated once in step 4 and
-// once per unordered pair in step 2.  Forces are added to the per-atom
+//  4. the gradients g_a = dE_i/dR_(j_a): every unordered pair {a, b} is
+//     evaluated once and gives, for its angular terms T(u_a, u_b, s = u_b -
+//     u_a), dT/du_a - dT/ds to a and dT/du_b + dT/ds to b.  The pairs run in
+//     a rotation schedule -- round k pairs a with (a + k) mod n -- so in one
+//     warp instruction no two lanes touch the same neighbour's shared sums
+//     (no atomics, and a fixed summation order: reproducible).  Per pair the
+//     angular functions are folded group by group: for each (eta, kind)
+//     group the sums over its functions of w A and w dA/dc (w = dE_i/dG)
+//     multiply the group's Gaussian-cutoff factor and its derivatives.
+//     Atom j_a receives -g_a, atom i receives sum_a g_a (E_i depends on
+//     relative positions only), and i keeps the virial -sum_a u_a (x) g_a of
+//     its own energy.  Forces are added to the per-atom
 // accumulators s.hacc (64-bit fixed point in the mixed path, FP64 atomics in
 // the FP64 path); launch_half_fin then finishes the step.  The mixed path
 // computes in FP32; a neighbour gradient at or above 2^22 eV/A sets the
@@ -40,12 +45,16 @@ template <class R>
 struct BM;
 template <>
 struct BM<float> {
-  static __device__ __forceinline__ void scpi(float x, float *s, float *c) { sincospif(x, s, c); }
+  // x in [0, 1] here (R < R_c): the hardware sine/cosine of pi x are within
+  // ~1e-6 absolute, far inside the mixed path's bar
+  static __device__ __forceinline__ void scpi(float x, float *s, float *c) {
+    __sincosf(3.14159265358979f * x, s, c);
+  }
   static __device__ __forceinline__ float ex(float x) { return __expf(x); }
   static __device__ __forceinline__ float th(float x) { return tanhf(x); }
   static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
   static __device__ __forceinline__ void sc(float x, float *s, float *c) { sincosf(x, s, c); }
-  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 };
 template <>
 struct BM<double> {
@@ -77,6 +86,22 @@ __device__ __forceinline__ R ipow(R x, int e) {
   return r;
 }
 
+// x^e and y^e together (one loop, uniform across the warp)
+template <class R>
+__device__ __forceinline__ void ipow2(R x, R y, int e, R &rx, R &ry) {
+  rx = R(1);
+  ry = R(1);
+  while (e) {
+    if (e & 1) {
+      rx *= x;
+      ry *= y;
+    }
+    x *= x;
+    y *= y;
+    e >>= 1;
+  }
+}
+
 template <class R>
 __device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
@@ -88,10 +113,12 @@ __device__ __forceinline__ R warp_sum(R v) {
 // descriptor / gradient / hidden vectors
 template <class R>
 struct Slab {
-  R *ux, *uy, *uz, *rr, *fc, *dfc, *e;  // e: [nY][NB]
+  R *ux, *uy, *uz, *rr, *ir, *fc, *dfc, *e;  // e: [nY][NB]
+  R *gax, *gay, *gaz, *gbx, *gby, *gbz;      // gradient sums (a side, b side)
   int *j;
   R *G, *dG, *h1, *d1, *d2, *wc;  // wc: dE/dG of each angular slot
 };
+constexpr int kSlabFields = 13;   // per-neighbour reals besides e
 
 constexpr int kVec = 80;  // >= kBpIn, a multiple of 16
 static_assert(kVec >= kBpIn, "device network inputs");
@@ -104,10 +131,17 @@ __device__ __forceinline__ Slab<R> slab_at(char *base, int NB, int nY) {
   s.uy = p + NB;
   s.uz = p + 2 * NB;
   s.rr = p + 3 * NB;
-  s.fc = p + 4 * NB;
-  s.dfc = p + 5 * NB;
-  s.e = p + 6 * NB;
-  p += (size_t)(6 + nY) * NB;
+  s.ir = p + 4 * NB;
+  s.fc = p + 5 * NB;
+  s.dfc = p + 6 * NB;
+  s.gax = p + 7 * NB;
+  s.gay = p + 8 * NB;
+  s.gaz = p + 9 * NB;
+  s.gbx = p + 10 * NB;
+  s.gby = p + 11 * NB;
+  s.gbz = p + 12 * NB;
+  s.e = p + kSlabFields * NB;
+  p += (size_t)(kSlabFields + nY) * NB;
   s.G = p;
   s.dG = p + kVec;
   s.h1 = p + 2 * kVec;
@@ -119,7 +153,7 @@ __device__ __forceinline__ Slab<R> slab_at(char *base, int NB, int nY) {
 }
 
 __host__ __device__ inline size_t slab_bytes(int NB, int nY, size_t rsz) {
-  size_t b = rsz * ((size_t)(6 + nY) * NB + 2 * kVec + 96 + kBpSlots) +
+  size_t b = rsz * ((size_t)(kSlabFields + nY) * NB + 2 * kVec + 96 + kBpSlots) +
              sizeof(int) * (size_t)NB;
   return (b + 15) / 16 * 16;
 }
@@ -148,8 +182,19 @@ __device__ __forceinline__ void radial(const BPParams &bp, int m, R r, R f, R df
   }
 }
 
+// mixed: 8 warps per block, two blocks per SM (128 registers); FP64: 4 warps
+template <class P>
+constexpr int bp_threads() {
+  return sizeof(typename G<P>::R) == 4 ? 256 : 128;
+}
+template <class P>
+constexpr int bp_blocks() {
+  return sizeof(typename G<P>::R) == 4 ? 2 : 1;
+}
+
 template <class P, bool ENERGY>
-__global__ void k_bpnn(Sys s, BPParams bp, StepArgs a) {
+__global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
+    k_bpnn(Sys s, BPParams bp, StepArgs a) {
   using GP = G<P>;
   using H = HalfAcc<P>;
   using R = typename GP::R;
@@ -212,6 +257,9 @@ __global__ void k_bpnn(Sys s, BPParams bp, StepArgs a) {
       sl.uy[q] = dy;
       sl.uz[q] = dz;
       sl.rr[q] = r;
+      sl.ir[q] = BM<R>::rcp(r);
+      sl.gax[q] = sl.gay[q] = sl.gaz[q] = R(0);
+      sl.gbx[q] = sl.gby[q] = sl.gbz[q] = R(0);
       sl.fc[q] = R(0.5) * (cs + R(1));
       sl.dfc[q] = half_pi_rc * sn;
       for (int p = 0; p < nY; ++p)
@@ -250,7 +298,7 @@ __global__ void k_bpnn(Sys s, BPParams bp, StepArgs a) {
       const int qb = qa + 1 + rel;
       const R ax = sl.ux[qa], ay = sl.uy[qa], az = sl.uz[qa], ra = sl.rr[qa], fa = sl.fc[qa];
       const R bx = sl.ux[qb], by = sl.uy[qb], bz = sl.uz[qb], rb = sl.rr[qb], fb = sl.fc[qb];
-      const R c = (ax * bx + ay * by + az * bz) * BM<R>::rcp(ra * rb);
+      const R c = (ax * bx + ay * by + az * bz) * (sl.ir[qa] * sl.ir[qb]);
       const R sx = bx - ax, sy = by - ay, sz = bz - az;
       const R rab2 = sx * sx + sy * sy + sz * sz;
       const bool near = bp.any4 && rab2 < rc2;
@@ -275,17 +323,21 @@ __global__ void k_bpnn(Sys s, BPParams bp, StepArgs a) {
       for (int z = 0; z < kBpZ; ++z)
         if (z < nZ) {
           const R cf = pick<R>(bp.z_coef[z], bp.z_coeff[z]);
-          Pp[z] = cf * ipow<R>(R(1) + c, bp.z_pow[z]) * (R(1) + c);
-          Pm[z] = cf * ipow<R>(R(1) - c, bp.z_pow[z]) * (R(1) - c);
+          ipow2<R>(R(1) + c, R(1) - c, bp.z_pow[z], Pp[z], Pm[z]);
+          Pp[z] *= cf * (R(1) + c);
+          Pm[z] *= cf * (R(1) - c);
         }
+      // every slot of the used groups (a slot without a function has zero
+      // weights, so its sum is never read)
 #pragma unroll
       for (int p = 0; p < kBpY; ++p)
 #pragma unroll
-        for (int z = 0; z < kBpZ; ++z) {
-          const int m = (p * kBpZ + z) * 2;
-          if ((used >> m) & 1ull) acca[m] += Pp[z] * Y[p];
-          if ((used >> (m + 1)) & 1ull) acca[m + 1] += Pm[z] * Y[p];
-        }
+        for (int z = 0; z < kBpZ; ++z)
+          if (p < nY && z < nZ) {
+            const int m = (p * kBpZ + z) * 2;
+            acca[m] += Pp[z] * Y[p];
+            acca[m + 1] += Pm[z] * Y[p];
+          }
       rel += 32;
       while (qa < n - 1 && rel >= n - 1 - qa) {
         rel -= n - 1 - qa;
@@ -298,7 +350,7 @@ __global__ void k_bpnn(Sys s, BPParams bp, StepArgs a) {
     if (m < nr) accr[m] = warp_sum(accr[m]);
 #pragma unroll
   for (int m = 0; m < kBpSlots; ++m)
-    if ((used >> m) & 1ull) acca[m] = warp_sum(acca[m]);
+    if (m / (2 * kBpZ) < nY && (m / 2) % kBpZ < nZ) acca[m] = warp_sum(acca[m]);
   if (lane == 0) {
 #pragma unroll
     for (int m = 0; m < kBpRad; ++m) sl.G[m] = m < nr ? accr[m] : R(0);
@@ -341,8 +393,94 @@ __global__ void k_bpnn(Sys s, BPParams bp, StepArgs a) {
   __syncwarp();
 
   // ---- 4. gradients with respect to the neighbours ------------------------
-  // atom i's share is summed from the same rounded terms its neighbours get
-  // (the mixed path's forces then sum to exactly zero)
+  {
+    const bool even = (n & 1) == 0;
+    const int kmax = even ? n / 2 : (n - 1) / 2;
+    for (int k = 1; k <= kmax; ++k) {
+      const int na_k = (even && k == n / 2) ? n / 2 : n;  // the last shift of an even n pairs each couple once
+      for (int a0 = 0; a0 < na_k; a0 += 32) {
+        const int qa = a0 + lane;
+        if (qa < na_k) {
+          int qb = qa + k;
+          if (qb >= n) qb -= n;
+          const R ax = sl.ux[qa], ay = sl.uy[qa], az = sl.uz[qa], ra = sl.rr[qa];
+          const R bx = sl.ux[qb], by = sl.uy[qb], bz = sl.uz[qb], rb = sl.rr[qb];
+          const R ia = sl.ir[qa], ib = sl.ir[qb];
+          const R fa = sl.fc[qa], dfa = sl.dfc[qa], fb = sl.fc[qb], dfb = sl.dfc[qb];
+          const R iab = ia * ib;
+          const R c = (ax * bx + ay * by + az * bz) * iab;
+          const R sx = bx - ax, sy = by - ay, sz = bz - az;
+          const R rab2 = sx * sx + sy * sy + sz * sz;
+          const bool near = bp.any4 && rab2 < rc2;
+          R rab = 0, fab = 0, dfab = 0, irab = 0;
+          if (near) {
+            rab = BM<R>::sq(rab2);
+            R sn, cs;
+            BM<R>::scpi(rab * inv_rc, &sn, &cs);
+            fab = R(0.5) * (cs + R(1));
+            dfab = half_pi_rc * sn;
+            irab = BM<R>::rcp(rab);
+          }
+          // per zeta group: A = 2^(1-zeta) (1 +- c)^zeta and dA/dc
+          R Ap[kBpZ], Am[kBpZ], dAp[kBpZ], dAm[kBpZ];
+#pragma unroll
+          for (int z = 0; z < kBpZ; ++z)
+            if (z < nZ) {
+              const R cf = pick<R>(bp.z_coef[z], bp.z_coeff[z]);
+              const R zt = pick<R>(bp.z_zeta[z], bp.z_zetaf[z]);
+              R pp, pm;
+              ipow2<R>(R(1) + c, R(1) - c, bp.z_pow[z], pp, pm);
+              pp *= cf;
+              pm *= cf;
+              Ap[z] = pp * (R(1) + c);
+              Am[z] = pm * (R(1) - c);
+              dAp[z] = zt * pp;
+              dAm[z] = -zt * pm;
+            }
+          // per (eta, kind) group: the functions' weighted sums S2 = sum w A,
+          // S1 = sum w dA/dc, times the group's factor Y and its derivatives
+          R al = 0, bu = 0, bw = 0, gs = 0;
+#pragma unroll
+          for (int p = 0; p < kBpY; ++p)
+            if (p < nY) {
+              R S1 = 0, S2 = 0;
+#pragma unroll
+              for (int z = 0; z < kBpZ; ++z)
+                if (z < nZ) {  // slots without a function have w = 0
+                  const int m = (p * kBpZ + z) * 2;
+                  const R wp = sl.wc[m], wm = sl.wc[m + 1];
+                  S2 += wp * Ap[z] + wm * Am[z];
+                  S1 += wp * dAp[z] + wm * dAm[z];
+                }
+              const R eta = pick<R>(bp.y_eta[p], bp.y_etaf[p]);
+              const R E2 = sl.e[p * NB + qa] * sl.e[p * NB + qb];
+              R X = R(1), fX = R(1);
+              const bool k4 = bp.y_kind[p] == 4;
+              if (k4) {
+                X = near ? BM<R>::ex(-eta * rab2) : R(0);
+                fX = X * fab;
+              }
+              const R Y = E2 * fa * fb * fX;
+              al += S1 * Y;
+              bu += S2 * E2 * fb * fX * (R(-2) * eta * ra * fa + dfa) * ia;
+              bw += S2 * E2 * fa * fX * (R(-2) * eta * rb * fb + dfb) * ib;
+              if (k4 && near) gs += S2 * E2 * fa * fb * X * (R(-2) * eta * rab * fab + dfab) * irab;
+            }
+          // dc/du_a = u_b/(R_a R_b) - c u_a/R_a^2, dc/du_b = u_a/(R_a R_b) - c u_b/R_b^2;
+          // to a: dT/du_a - dT/ds, to b: dT/du_b + dT/ds
+          const R ca = c * ia * ia, cb = c * ib * ib;
+          sl.gax[qa] += al * (bx * iab - ca * ax) + bu * ax - gs * sx;
+          sl.gay[qa] += al * (by * iab - ca * ay) + bu * ay - gs * sy;
+          sl.gaz[qa] += al * (bz * iab - ca * az) + bu * az - gs * sz;
+          sl.gbx[qb] += al * (ax * iab - cb * bx) + bw * bx + gs * sx;
+          sl.gby[qb] += al * (ay * iab - cb * by) + bw * by + gs * sy;
+          sl.gbz[qb] += al * (az * iab - cb * bz) + bw * bz + gs * sz;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  // radial terms, then the scatter: -g to atom j_a, +g to atom i
   using Q = typename H::Q;
   Q fix = 0, fiy = 0, fiz = 0;
   R w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
@@ -351,7 +489,6 @@ __global__ void k_bpnn(Sys s, BPParams bp, StepArgs a) {
   for (int qa = lane; qa < n; qa += 32) {
     const R ax = sl.ux[qa], ay = sl.uy[qa], az = sl.uz[qa], ra = sl.rr[qa];
     const R fa = sl.fc[qa], dfa = sl.dfc[qa];
-    const R inv_ra = BM<R>::rcp(ra);
     R sr = 0;
 #pragma unroll
     for (int m = 0; m < kBpRad; ++m)
@@ -360,82 +497,10 @@ __global__ void k_bpnn(Sys s, BPParams bp, StepArgs a) {
         radial<R>(bp, m, ra, fa, dfa, v, d);
         sr += sl.dG[m] * d;
       }
-    R gx = sr * inv_ra * ax, gy = sr * inv_ra * ay, gz = sr * inv_ra * az;
-    R ea[kBpY];
-#pragma unroll
-    for (int p = 0; p < kBpY; ++p)
-      if (p < nY) ea[p] = sl.e[p * NB + qa];
-    for (int qb = 0; qb < n; ++qb) {
-      if (qb == qa) continue;
-      const R bx = sl.ux[qb], by = sl.uy[qb], bz = sl.uz[qb], rb = sl.rr[qb], fb = sl.fc[qb];
-      const R inv_ab = BM<R>::rcp(ra * rb);
-      const R c = (ax * bx + ay * by + az * bz) * inv_ab;
-      const R sx = bx - ax, sy = by - ay, sz = bz - az;
-      const R rab2 = sx * sx + sy * sy + sz * sz;
-      const bool near = bp.any4 && rab2 < rc2;
-      R fab = 0, dfab = 0, inv_rab = 0;
-      if (near) {
-        const R rab = BM<R>::sq(rab2);
-        R sn, cs;
-        BM<R>::scpi(rab * inv_rc, &sn, &cs);
-        fab = R(0.5) * (cs + R(1));
-        dfab = half_pi_rc * sn;
-        inv_rab = BM<R>::rcp(rab);
-      }
-      // per (eta, kind) group: Y, (dY/dR_a)/R_a and (dY/dR_ab)/R_ab
-      R Y[kBpY], Yu[kBpY], Ys[kBpY];
-#pragma unroll
-      for (int p = 0; p < kBpY; ++p)
-        if (p < nY) {
-          const R eta = pick<R>(bp.y_eta[p], bp.y_etaf[p]);
-          const R eb = ea[p] * sl.e[p * NB + qb] * fb;
-          R ex = R(1);
-          if (bp.y_kind[p] == 4) ex = near ? BM<R>::ex(-eta * rab2) * fab : R(0);
-          Y[p] = eb * fa * ex;
-          Yu[p] = eb * ex * (R(-2) * eta * ra * fa + dfa) * inv_ra;
-          Ys[p] = (bp.y_kind[p] == 4 && near)
-                      ? eb * fa * BM<R>::ex(-eta * rab2) *
-                            (R(-2) * eta * BM<R>::sq(rab2) * fab + dfab) * inv_rab
-                      : R(0);
-        }
-      // per zeta group: 2^(1 - zeta) (1 +- c)^(zeta - 1)
-      R Pp[kBpZ], Pm[kBpZ];
-#pragma unroll
-      for (int z = 0; z < kBpZ; ++z)
-        if (z < nZ) {
-          const R cf = pick<R>(bp.z_coef[z], bp.z_coeff[z]);
-          Pp[z] = cf * ipow<R>(R(1) + c, bp.z_pow[z]);
-          Pm[z] = cf * ipow<R>(R(1) - c, bp.z_pow[z]);
-        }
-      // T = A(c) Y: dT/du_a = A' Y dc/du_a + A Yu u_a, dT/ds = A Ys s, with
-      // A = 2^(1-zeta) (1 + lambda c)^zeta, A' = zeta lambda 2^(1-zeta) (1 + lambda c)^(zeta-1)
-      R al = 0, be = 0, ga = 0;
-#pragma unroll
-      for (int p = 0; p < kBpY; ++p)
-#pragma unroll
-        for (int z = 0; z < kBpZ; ++z) {
-          const int m = (p * kBpZ + z) * 2;
-          const R zt = pick<R>(bp.z_zeta[z], bp.z_zetaf[z]);
-          if ((used >> m) & 1ull) {  // lambda = +1
-            const R w = sl.wc[m], A = Pp[z] * (R(1) + c);
-            al += w * zt * Pp[z] * Y[p];
-            be += w * A * Yu[p];
-            ga += w * A * Ys[p];
-          }
-          if ((used >> (m + 1)) & 1ull) {  // lambda = -1
-            const R w = sl.wc[m + 1], A = Pm[z] * (R(1) - c);
-            al -= w * zt * Pm[z] * Y[p];
-            be += w * A * Yu[p];
-            ga += w * A * Ys[p];
-          }
-        }
-      // dc/du_a = u_b / (R_a R_b) - c u_a / R_a^2; dT/dR_a = dT/du_a - dT/ds
-      const R cq = c * inv_ra * inv_ra;
-      gx += al * (bx * inv_ab - cq * ax) + be * ax - ga * sx;
-      gy += al * (by * inv_ab - cq * ay) + be * ay - ga * sy;
-      gz += al * (bz * inv_ab - cq * az) + be * az - ga * sz;
-    }
-    // g = dE_i/dR_(j_a): -g to atom j_a, +g to atom i, virial -u (x) g
+    sr *= sl.ir[qa];
+    const R gx = sr * ax + sl.gax[qa] + sl.gbx[qa];
+    const R gy = sr * ay + sl.gay[qa] + sl.gby[qa];
+    const R gz = sr * az + sl.gaz[qa] + sl.gbz[qa];
     const int j = sl.j[qa];
     if (sizeof(R) == 4)
       bad = bad || !(fabs(gx) < R(4194304) && fabs(gy) < R(4194304) && fabs(gz) < R(4194304));

@@ -78,28 +78,7 @@ __global__ void __launch_bounds__(512, 2) k_rho(Sys s, EAMParams ep, StepArgs a)
     if (!valid || tl.t != 0) continue;
     // F(rho_i) and F'(rho_i) in FP64 (once per atom)
     double Fv, dF;
-    if (rho_i > ep.rho_max) {
-      // above the table: linear continuation of the last knot
-      const int n = ep.nrho;
-      const double2 a0 = ep.F64[n - 2], a1 = ep.F64[n - 1];
-      const double d1 = herm_der<double>(1.0, a0.x, a0.y, a1.x, a1.y) * ep.inv_drho;
-      Fv = a1.x + d1 * (rho_i - ep.rho_max);
-      dF = d1;
-      atomicOr(&s.st->bits, isfinite(rho_i) ? kStRhoRange : kStNonfinite);
-    } else if (!(rho_i == rho_i)) {
-      Fv = 0.0;
-      dF = 0.0;
-      atomicOr(&s.st->bits, kStNonfinite);
-    } else {
-      // inside (or below, by the first piece extended) the table
-      const double u = rho_i * ep.inv_drho;
-      int kk = (int)floor(u);
-      kk = kk > ep.nrho - 2 ? ep.nrho - 2 : (kk < 0 ? 0 : kk);
-      const double t = u - (double)kk;
-      const double2 a0 = ep.F64[kk], a1 = ep.F64[kk + 1];
-      Fv = herm_val<double>(t, a0.x, a0.y, a1.x, a1.y);
-      dF = herm_der<double>(t, a0.x, a0.y, a1.x, a1.y) * ep.inv_drho;
-    }
+    embed_fp64(s, ep, rho_i, Fv, dF);
     s.rho[i] = rho_i;
     ((R *)s.fp)[i] = (R)dF;
     GP::st_fp((V *)s.pgF + i, pi, dF);

@@ -165,6 +165,33 @@ struct G<Mixed> {
   static __device__ __forceinline__ float fp_of(const float4 &q) { return q.w; }
 };
 
+// F(rho) and F'(rho) in FP64 from the F table (once per atom): cubic
+// Hermite inside (the first piece extended below), linear continuation of
+// the last knot above rho_max (flagged), NaN flagged.
+__device__ __forceinline__ void embed_fp64(const Sys &s, const EAMParams &ep, double rho_i,
+                                           double &Fv, double &dF) {
+  if (rho_i > ep.rho_max) {
+    const int n = ep.nrho;
+    const double2 a0 = ep.F64[n - 2], a1 = ep.F64[n - 1];
+    const double d1 = herm_der<double>(1.0, a0.x, a0.y, a1.x, a1.y) * ep.inv_drho;
+    Fv = a1.x + d1 * (rho_i - ep.rho_max);
+    dF = d1;
+    atomicOr(&s.st->bits, isfinite(rho_i) ? kStRhoRange : kStNonfinite);
+  } else if (!(rho_i == rho_i)) {
+    Fv = 0.0;
+    dF = 0.0;
+    atomicOr(&s.st->bits, kStNonfinite);
+  } else {
+    const double u = rho_i * ep.inv_drho;
+    int kk = (int)floor(u);
+    kk = kk > ep.nrho - 2 ? ep.nrho - 2 : (kk < 0 ? 0 : kk);
+    const double t = u - (double)kk;
+    const double2 a0 = ep.F64[kk], a1 = ep.F64[kk + 1];
+    Fv = herm_val<double>(t, a0.x, a0.y, a1.x, a1.y);
+    dF = herm_der<double>(t, a0.x, a0.y, a1.x, a1.y) * ep.inv_drho;
+  }
+}
+
 // ---- the neighbour walk ------------------------------------------------------------
 // Unit stencil offset s_d in {-1, 0, 1} of a list entry, exactly, in the pair
 // precision, without an int-to-float conversion: the 2-bit code c = s_d + 1 is
@@ -255,6 +282,9 @@ struct HalfAcc<Mixed> {
   static __device__ __forceinline__ long long q(float v) {
     return __float2ll_rn(v * 1099511627776.0f);  // 2^40, exact power of two
   }
+  static __device__ __forceinline__ long long qd(double v) {  // a per-atom FP64 value
+    return __double2ll_rn(v * kHalfScale);
+  }
   static __device__ __forceinline__ void red(long long *p, long long v) {
     atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
   }
@@ -268,6 +298,7 @@ template <>
 struct HalfAcc<Fp64> {
   using Q = double;
   static __device__ __forceinline__ double q(double v) { return v; }
+  static __device__ __forceinline__ double qd(double v) { return v; }
   static __device__ __forceinline__ void red(long long *p, double v) {
     atomicAdd(reinterpret_cast<double *>(p), v);
   }

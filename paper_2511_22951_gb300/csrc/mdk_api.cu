@@ -289,7 +289,7 @@ void fill_sys_params(mdk_ctx *c) {
   s.n_rep = c->n_rep;
   s.n_cells = c->n_cells;
   s.n_scan_blocks = scan_blocks_for(c->n_cells + 1);
-  s.half = c->pot == 1 && c->cfg.half ? 1 : 0;
+  s.half = (c->pot == 1 || c->pot == 2) && c->cfg.half ? 1 : 0;
   const double rns = c->rc_list + c->skin;
   s.rns2 = rns * rns;
   // FP32 pre-filter band: the float r^2 of a candidate is within ~6e-6 r_ns^2
@@ -445,10 +445,13 @@ int timed(mdk_ctx *c, std::vector<std::pair<int, int>> &log, int n_kernels, F la
 
 int force_pass(mdk_ctx *c, Mode mode, int energy, double dt) {
   StepArgs a{dt, c->cur, energy};
-  const bool half = c->pot == 1 && c->cfg.half;
-  return timed(c, c->ev_force, c->pot == 1 && !half ? 1 : 2, [&] {
+  const bool half = (c->pot == 1 || c->pot == 2) && c->cfg.half;
+  const int nk = c->pot == 1 ? (half ? 2 : 1) : (c->pot == 2 && half ? 4 : 2);
+  return timed(c, c->ev_force, nk, [&] {
     if (c->pot == 3)
       launch_bpnn(c->sys, c->bp, c->precision, mode, a, c->stream);
+    else if (half && c->pot == 2)
+      launch_eam_half(c->sys, c->eam, c->precision, mode, a, c->cfg, c->stream);
     else if (half)
       launch_lj_half(c->sys, c->lj, c->precision, mode, a, c->cfg, c->stream);
     else if (c->pot == 1)
@@ -791,7 +794,6 @@ int mdk_set_potential_eam(mdk_ctx *c, int nr, double rc, const double *phi, cons
   c->eam_rho.assign(rho, rho + nr);
   c->eam_F.assign(F, F + nrho);
   c->pot = 2;
-  use_list_kind(c, MDK_LIST_FULL);  // the EAM passes read full lists
   if (!c->planned) plan(c, rc, 0.3, 0, 0);
   if (resized) {
     c->ws_ok = false;  // table area changes size: a new workspace is needed
@@ -999,7 +1001,9 @@ int mdk_set_workspace(mdk_ctx *c, void *dev_ptr, size_t bytes) {
     launch_eam_prepare(e, kn, kn + e.nr, kn + 2 * e.nr, c->eam_dev, c->stream);
     MDK_CK(cudaPeekAtLastError());
     if (configure_eam_smem(eam_smem_bytes(e, c->precision, 1), eam_smem_bytes(e, c->precision, 2),
-                           c->precision))
+                           c->precision) ||
+        configure_eam_half_smem(eam_smem_bytes(e, c->precision, 1),
+                                eam_smem_bytes(e, c->precision, 2), c->precision))
       return MDK_ERR_CUDA;
   }
   MDK_CK(cudaStreamSynchronize(c->stream));
@@ -1220,6 +1224,7 @@ int mdk_eam_vjp(mdk_ctx *c, const double *gE, const double *gF, double *dtheta, 
   if (c->pot != 2 || c->win_on) return MDK_ERR_ORDER;
   int r = ensure_ready(c);
   if (r) return r;
+  use_list_kind(c, MDK_LIST_FULL);  // the adjoint passes read full lists
   if (!c->list_built) {
     r = build_now(c);
     if (r) return r;
@@ -1455,13 +1460,13 @@ int mdk_autotune(mdk_ctx *c, int reps, int *tpa_out, int *block_out, double *ms_
   float best_ms = -1.f;
   static const int kTpa[3] = {1, 2, 4};
   static const int kBlock[3] = {128, 256, 512};
-  // LJ: full lists in every shape, then half lists (one thread per atom)
-  for (int kind = 0; kind < (c->pot == 1 ? 2 : 1) && !r; ++kind)
+  // LJ and EAM: full lists in every shape, then half lists (one thread per atom)
+  for (int kind = 0; kind < (c->pot == 1 || c->pot == 2 ? 2 : 1) && !r; ++kind)
   for (int a = 0; a < 3 && !r; ++a)
     for (int b = 0; b < 3; ++b) {
       if (c->pot == 1 && kBlock[b] > 256) continue;  // the LJ kernels take <= 256
       if (c->pot == 3 && (a > 0 || b > 0)) continue;  // BPNN: one warp per atom, one shape
-      if (kind == 1 && kTpa[a] != 1) continue;
+      if (kind == 1 && (kTpa[a] != 1 || kBlock[b] > 256)) continue;  // half: <= 256 threads
       if (c->cfg.half != kind || !c->list_built) {
         use_list_kind(c, kind);
         r = build_now(c);
@@ -1521,7 +1526,8 @@ int mdk_set_launch(mdk_ctx *c, int tpa, int block) {
 
 int mdk_set_list_kind(mdk_ctx *c, int kind) {
   if (check_ctx(c) || (kind != MDK_LIST_FULL && kind != MDK_LIST_HALF)) return MDK_ERR_BAD_ARG;
-  if (kind == MDK_LIST_HALF && c->pot != 1) return c->pot == 0 ? MDK_ERR_ORDER : MDK_ERR_BAD_ARG;
+  if (kind == MDK_LIST_HALF && c->pot != 1 && c->pot != 2)
+    return c->pot == 0 ? MDK_ERR_ORDER : MDK_ERR_BAD_ARG;
   use_list_kind(c, kind);
   return MDK_OK;
 }

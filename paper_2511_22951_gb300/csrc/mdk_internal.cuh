@@ -367,6 +367,11 @@ void launch_profiles(const Sys &s, int axis, double origin, double bin_w, int nb
                      double cross_area, double *acc, cudaStream_t st);
 int eam_smem_bytes(const EAMParams &p, int precision, int pass);
 int configure_eam_smem(int bytes_pass1, int bytes_pass2, int precision);
+int configure_eam_half_smem(int bytes_pass1, int bytes_pass2, int precision);
+// half lists: density pass, embedding, force pass with accumulating atomics,
+// then launch_half_fin
+void launch_eam_half(const Sys &s, const EAMParams &p, int precision, Mode mode, StepArgs a,
+                     const LaunchCfg &cfg, cudaStream_t st);
 // pass 1 of the EAM force loop alone (rho_i and F'(rho_i) of the current positions)
 void launch_eam_rho(const Sys &s, const EAMParams &p, int precision, StepArgs a,
                     const LaunchCfg &cfg, cudaStream_t st);

@@ -1,5 +1,6 @@
 """Half Verlet lists (each pair once, Newton's third law with accumulating
-atomics) against the oracle, through the C ABI.
+atomics) against the oracle, through the C ABI: LJ, and the EAM passes
+(density to both atoms, embedding per atom, forces to both atoms).
 
 The neighbour set of Sec. "Neighbor lists" is the oracle's full set; a half
 list must hold exactly one of each mirror pair (i, j, n) / (j, i, -n).
@@ -16,8 +17,8 @@ import pytest
 
 from paper_2511_22951_gb300 import workloads as W
 
-from test_gpu_parity import (BOXES, assert_fp64, assert_mixed, eam_ctx, gpu_lists,
-                             jittered_lattice, lj_ctx, oracle_lists)
+from test_gpu_parity import (BOXES, assert_fp64, assert_mixed, batch_ctx, eam_ctx, gpu_lists,
+                             jittered_lattice, lj_ctx, oracle_lists, small_coldcurve)
 
 pytestmark = pytest.mark.gpu
 
@@ -160,13 +161,96 @@ def test_list_kind_arguments_and_autotune(mdk, ora):
     E, F, _ = ctx.compute()
     ref = ora.lj(x, lo, hi, [1, 1, 1], W.LJ_AR.eps, W.LJ_AR.sigma, W.LJ_AR.rc, 1)
     assert_mixed(E[0], F, ref)
-    # EAM reads full lists only
+    # EAM: the autotuner times both kinds too
     tab = W.tabulate_fs_eam(W.CU_LIKE)
     xe, loe, hie = jittered_lattice(2, 3, 3.615, 0.05)
     ce = eam_ctx(mdk, xe, loe, hie, [1, 1, 1], "mixed", tab, mass=W.CU_LIKE.mass)
-    with pytest.raises(mdk.MDKError):
-        ce.set_list_kind("half")
-    assert ce.list_kind == "full"
+    ce.autotune()
+    assert ce.list_kind in ("full", "half")
+    E, F, _ = ce.compute()
+    assert_mixed(E[0], F, ora.eam(xe, loe, hie, [1, 1, 1], tab))
+
+
+# --------------------------------------------------------------------------- EAM
+def half_eam(mdk, *args, **kw):
+    ctx = eam_ctx(mdk, *args, **kw)
+    ctx.set_list_kind("half")
+    return ctx
+
+
+@pytest.mark.parametrize("p,a,n", [(W.AL_LIKE, 4.05, 4), (W.CU_LIKE, 3.3, 3),
+                                   (W.CU_LIKE, 3.0, 3)])
+def test_half_eam_fp64(mdk, ora, p, a, n):
+    tab = W.tabulate_fs_eam(p)
+    x, lo, hi = jittered_lattice(n + 10, n, a, 0.08)
+    ctx = half_eam(mdk, x, lo, hi, [1, 1, 1], "fp64", tab, mass=p.mass)
+    E, F, Wv = ctx.compute()
+    U, Wa = ctx.per_atom()
+    ref = ora.eam(x, lo, hi, [1, 1, 1], tab, per_atom=True)
+    assert_fp64(E[0], F, Wv[0], ref)
+    np.testing.assert_allclose(U, ref["Ea"], rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(Wa, ref["Wa"], rtol=0, atol=1e-11 * np.abs(ref["Wa"]).max())
+
+
+@pytest.mark.parametrize("p,a,n", [(W.AL_LIKE, 4.05, 5), (W.CU_LIKE, 3.615, 4)])
+def test_half_eam_mixed(mdk, ora, p, a, n):
+    tab = W.tabulate_fs_eam(p)
+    x, lo, hi = jittered_lattice(n + 20, n, a, 0.1)
+    ctx = half_eam(mdk, x, lo, hi, [1, 1, 1], "mixed", tab, mass=p.mass)
+    E, F, _ = ctx.compute()
+    ref = ora.eam(x, lo, hi, [1, 1, 1], tab)
+    assert_mixed(E[0], F, ref)
+    q = F * 2.0 ** 40
+    assert [sum(int(v) for v in q[:, d]) for d in range(3)] == [0, 0, 0]
+    _, F2, _ = ctx.compute()
+    np.testing.assert_array_equal(F, F2)
+
+
+def test_half_eam_trajectory_and_batch_fp64(mdk, ora):
+    tab = W.tabulate_fs_eam(W.CU_LIKE)
+    reps = small_coldcurve(4)
+    rng = np.random.default_rng(41)
+    for r in reps:
+        r.v = W.maxwell_velocities(rng, r.masses, 500.0)
+    ctx = batch_ctx(mdk, reps, "fp64", tab)
+    ctx.set_list_kind("half")
+    ctx.step(1.0, 10)
+    x, v = ctx.get_state()
+    off = 0
+    for r in reps:
+        o = ora.md_run(r.x, r.v, r.masses, r.lo, r.hi, r.periodic, 1.0, 10, 0.3, tables=tab)
+        L = r.hi - r.lo
+        d = x[off:off + r.n] - o["x"]
+        d -= np.rint(d / L) * L
+        assert np.max(np.abs(d)) < 1e-10
+        np.testing.assert_allclose(v[off:off + r.n], o["v"], rtol=0, atol=1e-11)
+        off += r.n
+
+
+def test_half_eam_mixed_graphs_equal_eager_and_vjp_uses_full_lists(mdk):
+    tab = W.tabulate_fs_eam(W.AL_LIKE)
+    outs = []
+    for graphs in (True, False):
+        x, lo, hi = jittered_lattice(50, 5, 4.05, 0.05)
+        v = W.maxwell_velocities(np.random.default_rng(51), np.full(x.shape[0], W.MASS_AL), 300.0)
+        ctx = half_eam(mdk, x, lo, hi, [1, 1, 1], "mixed", tab, v=v, mass=W.MASS_AL)
+        ctx.set_graphs(graphs)
+        ctx.set_thermo(7, 64)
+        ctx.step(1.0, 30)
+        outs.append(ctx.get_state() + (ctx.thermo(),))
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
+    # the adjoint walks full lists: a half-list context gives the same VJP
+    x, lo, hi = jittered_lattice(52, 4, 4.05, 0.08)
+    gF = np.random.default_rng(53).normal(size=(x.shape[0], 3))
+    res = []
+    for kind in ("full", "half"):
+        c = eam_ctx(mdk, x, lo, hi, [1, 1, 1], "fp64", tab, mass=W.MASS_AL)
+        c.set_list_kind(kind)
+        c.compute()
+        res.append(c.eam_vjp(gE=np.ones(1), gF=gF))
+    for a, b in zip(res[0], res[1]):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-12 * np.abs(a).max())
 
 
 @pytest.mark.slow
