@@ -578,17 +578,23 @@ def main():
               "rebuild_share_of_step": prof["rebuild_ms"] / (ms * prof_steps / args.steps),
               "timed_from": f"CUDA events around each of {int(prof['force_passes'])} force "
                             f"passes of a {prof_steps}-step profiled segment"}
+    # FMA pipe peaks measured on this device (the ALU rooflines' denominators)
+    try:
+        fma_pk = {"fp64": mdk.fma_peak("fp64"), "mixed": mdk.fma_peak("mixed")}
+    except mdk.MDKError:
+        fma_pk = None
     if wl.potential == "bpnn":
         fpa = bpnn_flops_per_atom(wl.extra["bpnn"], n_rc)
         tflops = n_now * fpa / (force_ms / 1e3) / 1e12
-        pk = FP32_PEAK_TFLOPS if prec == "mixed" else FP64_PEAK_TFLOPS
+        nominal = FP32_PEAK_TFLOPS if prec == "mixed" else FP64_PEAK_TFLOPS
+        pk = fma_pk[prec] if fma_pk else nominal
         common["kernel"] = (f"k_bpnn<{prec}> (descriptors, network, gradients; one warp per "
                             "atom) + k_half_fin per-atom velocity-Verlet pass")
         roof = {"bound": "alu", "achieved": tflops, "peak": pk, "unit": "TFLOP/s",
                 "frac": tflops / pk, "traffic": None, "flops_per_atom": fpa,
-                "peak_kind": ("FP32 FMA peak from unit counts (152 SMs x 128 lanes x 2 x "
-                              "2070 MHz)" if prec == "mixed" else "GB300 nominal dense FP64"),
-                **common}
+                "peak_kind": (("measured: FP32" if prec == "mixed" else "measured: FP64") +
+                              " FMA probe (mdk_fma_peak)") if fma_pk else "nominal",
+                "peak_nominal": nominal, **common}
     elif prec == "mixed":
         tr = traffic_per_launch(wl, prec, n_now, kind)
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
@@ -596,10 +602,13 @@ def main():
                 "traffic_unit": "bytes per launch", "peak_kind": peak_kind, **common}
     else:
         tflops = n_now * 0.5 * n_rc * FLOPS_PER_PAIR[wl.potential] / (force_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
+        pk = fma_pk["fp64"] if fma_pk else FP64_PEAK_TFLOPS
+        roof = {"bound": "alu", "achieved": tflops, "peak": pk,
+                "unit": "TFLOP/s", "frac": tflops / pk, "traffic": None,
                 "flops_per_pair": FLOPS_PER_PAIR[wl.potential],
-                "peak_kind": "GB300 nominal dense FP64",
+                "peak_kind": ("measured: FP64 FMA probe (mdk_fma_peak)" if fma_pk
+                              else "GB300 nominal dense FP64"),
+                "peak_nominal": FP64_PEAK_TFLOPS,
                 "hbm": {"achieved": gbs, "peak": hbm, "frac": gbs / hbm,
                         "bytes_per_atom": bpa}, **common}
 

@@ -514,6 +514,16 @@ int mdk_set_graphs(mdk_ctx *ctx, int enable);
 /* ---- measurement ----------------------------------------------------------- */
 
 /*
+ * FMA throughput of the current device in TFLOP/s (one FMA = 2 FLOP):
+ * precision MDK_FP64 times FP64 FMAs, MDK_MIXED FP32 FMAs; 8 independent
+ * chains per thread, 8 blocks of 256 threads per SM, one warm-up launch,
+ * CUDA events around the timed launch (~20-70 ms).  The denominator of the
+ * ALU rooflines (FP64 force loops, FP32 BPNN kernel).  Synchronous; uses
+ * the legacy default stream and a small temporary allocation.
+ */
+int mdk_fma_peak(int precision, double *tflops);
+
+/*
  * enable != 0: from now on bracket every force pass and every list-rebuild
  * chain enqueued by mdk_step / mdk_compute with CUDA events on the context's
  * stream, and count the kernels launched.  enable = 0 stops recording.

@@ -86,6 +86,30 @@ __device__ __forceinline__ R ipow(R x, int e) {
   return r;
 }
 
+// the 2 kBpZ per-slot weights of one (eta, kind) group, with vector loads
+template <class R>
+__device__ __forceinline__ void ld_group(const R *w, R out[2 * kBpZ]) {
+  if (sizeof(R) == 4) {
+    const float4 *q = reinterpret_cast<const float4 *>(w);
+#pragma unroll
+    for (int v = 0; v < kBpZ / 2; ++v) {
+      const float4 a = q[v];
+      out[4 * v] = a.x;
+      out[4 * v + 1] = a.y;
+      out[4 * v + 2] = a.z;
+      out[4 * v + 3] = a.w;
+    }
+  } else {
+    const double2 *q = reinterpret_cast<const double2 *>(w);
+#pragma unroll
+    for (int v = 0; v < kBpZ; ++v) {
+      const double2 a = q[v];
+      out[2 * v] = a.x;
+      out[2 * v + 1] = a.y;
+    }
+  }
+}
+
 // x^e and y^e together (one loop, uniform across the warp)
 template <class R>
 __device__ __forceinline__ void ipow2(R x, R y, int e, R &rx, R &ry) {
@@ -394,87 +418,109 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
 
   // ---- 4. gradients with respect to the neighbours ------------------------
   {
+    auto grad_pair = [&](const int qa, const int qb) {
+      const R ax = sl.ux[qa], ay = sl.uy[qa], az = sl.uz[qa], ra = sl.rr[qa];
+      const R bx = sl.ux[qb], by = sl.uy[qb], bz = sl.uz[qb], rb = sl.rr[qb];
+      const R ia = sl.ir[qa], ib = sl.ir[qb];
+      const R fa = sl.fc[qa], dfa = sl.dfc[qa], fb = sl.fc[qb], dfb = sl.dfc[qb];
+      const R iab = ia * ib;
+      const R c = (ax * bx + ay * by + az * bz) * iab;
+      const R sx = bx - ax, sy = by - ay, sz = bz - az;
+      const R rab2 = sx * sx + sy * sy + sz * sz;
+      const bool near = bp.any4 && rab2 < rc2;
+      R rab = 0, fab = 0, dfab = 0, irab = 0;
+      if (near) {
+        rab = BM<R>::sq(rab2);
+        R sn, cs;
+        BM<R>::scpi(rab * inv_rc, &sn, &cs);
+        fab = R(0.5) * (cs + R(1));
+        dfab = half_pi_rc * sn;
+        irab = BM<R>::rcp(rab);
+      }
+      // per zeta group: A = 2^(1-zeta) (1 +- c)^zeta and dA/dc
+      R Ap[kBpZ], Am[kBpZ], dAp[kBpZ], dAm[kBpZ];
+#pragma unroll
+      for (int z = 0; z < kBpZ; ++z)
+        if (z < nZ) {
+          const R cf = pick<R>(bp.z_coef[z], bp.z_coeff[z]);
+          const R zt = pick<R>(bp.z_zeta[z], bp.z_zetaf[z]);
+          R pp, pm;
+          ipow2<R>(R(1) + c, R(1) - c, bp.z_pow[z], pp, pm);
+          pp *= cf;
+          pm *= cf;
+          Ap[z] = pp * (R(1) + c);
+          Am[z] = pm * (R(1) - c);
+          dAp[z] = zt * pp;
+          dAm[z] = -zt * pm;
+        }
+      // per (eta, kind) group: the functions' weighted sums S2 = sum w A,
+      // S1 = sum w dA/dc, times the group's factor Y and its derivatives
+      R al = 0, bu = 0, bw = 0, gs = 0;
+#pragma unroll
+      for (int p = 0; p < kBpY; ++p)
+        if (p < nY) {
+          R S1 = 0, S2 = 0;
+          R wv[2 * kBpZ];  // the group's slots: (z, lambda = +1), (z, lambda = -1)
+          ld_group<R>(sl.wc + p * 2 * kBpZ, wv);
+#pragma unroll
+          for (int z = 0; z < kBpZ; ++z)
+            if (z < nZ) {  // slots without a function have w = 0
+              S2 += wv[2 * z] * Ap[z] + wv[2 * z + 1] * Am[z];
+              S1 += wv[2 * z] * dAp[z] + wv[2 * z + 1] * dAm[z];
+            }
+          const R eta = pick<R>(bp.y_eta[p], bp.y_etaf[p]);
+          const R E2 = sl.e[p * NB + qa] * sl.e[p * NB + qb];
+          R X = R(1), fX = R(1);
+          const bool k4 = bp.y_kind[p] == 4;
+          if (k4) {
+            X = near ? BM<R>::ex(-eta * rab2) : R(0);
+            fX = X * fab;
+          }
+          const R Y = E2 * fa * fb * fX;
+          al += S1 * Y;
+          bu += S2 * E2 * fb * fX * (R(-2) * eta * ra * fa + dfa) * ia;
+          bw += S2 * E2 * fa * fX * (R(-2) * eta * rb * fb + dfb) * ib;
+          if (k4 && near) gs += S2 * E2 * fa * fb * X * (R(-2) * eta * rab * fab + dfab) * irab;
+        }
+      // dc/du_a = u_b/(R_a R_b) - c u_a/R_a^2, dc/du_b = u_a/(R_a R_b) - c u_b/R_b^2;
+      // to a: dT/du_a - dT/ds, to b: dT/du_b + dT/ds
+      const R ca = c * ia * ia, cb = c * ib * ib;
+      sl.gax[qa] += al * (bx * iab - ca * ax) + bu * ax - gs * sx;
+      sl.gay[qa] += al * (by * iab - ca * ay) + bu * ay - gs * sy;
+      sl.gaz[qa] += al * (bz * iab - ca * az) + bu * az - gs * sz;
+      sl.gbx[qb] += al * (ax * iab - cb * bx) + bw * bx + gs * sx;
+      sl.gby[qb] += al * (ay * iab - cb * by) + bw * by + gs * sy;
+      sl.gbz[qb] += al * (az * iab - cb * bz) + bw * bz + gs * sz;
+    };
     const bool even = (n & 1) == 0;
-    const int kmax = even ? n / 2 : (n - 1) / 2;
-    for (int k = 1; k <= kmax; ++k) {
-      const int na_k = (even && k == n / 2) ? n / 2 : n;  // the last shift of an even n pairs each couple once
-      for (int a0 = 0; a0 < na_k; a0 += 32) {
-        const int qa = a0 + lane;
+    const int kfull = (n - 1) / 2;  // shifts that pair all n neighbours
+    if (n >= 32) {
+      // flat schedule over (shift, a): 32 consecutive entries span at most two
+      // shifts with disjoint a ranges and disjoint b = a + shift ranges, so
+      // no lane of an instruction shares a neighbour's sums with another
+      const int T = kfull * n + (even ? n / 2 : 0);
+      int k = 1, qa = lane;
+      for (int t0 = 0; t0 < T; t0 += 32) {
+        if (t0 + lane < T) {
+          int qb = qa + k;
+          if (qb >= n) qb -= n;
+          grad_pair(qa, qb);
+        }
+        __syncwarp();
+        qa += 32;
+        if (qa >= n) {
+          qa -= n;
+          ++k;
+        }
+      }
+    } else {
+      for (int k = 1; k <= kfull + (even ? 1 : 0); ++k) {
+        const int na_k = k > kfull ? n / 2 : n;  // the last shift of an even n pairs each couple once
+        const int qa = lane;
         if (qa < na_k) {
           int qb = qa + k;
           if (qb >= n) qb -= n;
-          const R ax = sl.ux[qa], ay = sl.uy[qa], az = sl.uz[qa], ra = sl.rr[qa];
-          const R bx = sl.ux[qb], by = sl.uy[qb], bz = sl.uz[qb], rb = sl.rr[qb];
-          const R ia = sl.ir[qa], ib = sl.ir[qb];
-          const R fa = sl.fc[qa], dfa = sl.dfc[qa], fb = sl.fc[qb], dfb = sl.dfc[qb];
-          const R iab = ia * ib;
-          const R c = (ax * bx + ay * by + az * bz) * iab;
-          const R sx = bx - ax, sy = by - ay, sz = bz - az;
-          const R rab2 = sx * sx + sy * sy + sz * sz;
-          const bool near = bp.any4 && rab2 < rc2;
-          R rab = 0, fab = 0, dfab = 0, irab = 0;
-          if (near) {
-            rab = BM<R>::sq(rab2);
-            R sn, cs;
-            BM<R>::scpi(rab * inv_rc, &sn, &cs);
-            fab = R(0.5) * (cs + R(1));
-            dfab = half_pi_rc * sn;
-            irab = BM<R>::rcp(rab);
-          }
-          // per zeta group: A = 2^(1-zeta) (1 +- c)^zeta and dA/dc
-          R Ap[kBpZ], Am[kBpZ], dAp[kBpZ], dAm[kBpZ];
-#pragma unroll
-          for (int z = 0; z < kBpZ; ++z)
-            if (z < nZ) {
-              const R cf = pick<R>(bp.z_coef[z], bp.z_coeff[z]);
-              const R zt = pick<R>(bp.z_zeta[z], bp.z_zetaf[z]);
-              R pp, pm;
-              ipow2<R>(R(1) + c, R(1) - c, bp.z_pow[z], pp, pm);
-              pp *= cf;
-              pm *= cf;
-              Ap[z] = pp * (R(1) + c);
-              Am[z] = pm * (R(1) - c);
-              dAp[z] = zt * pp;
-              dAm[z] = -zt * pm;
-            }
-          // per (eta, kind) group: the functions' weighted sums S2 = sum w A,
-          // S1 = sum w dA/dc, times the group's factor Y and its derivatives
-          R al = 0, bu = 0, bw = 0, gs = 0;
-#pragma unroll
-          for (int p = 0; p < kBpY; ++p)
-            if (p < nY) {
-              R S1 = 0, S2 = 0;
-#pragma unroll
-              for (int z = 0; z < kBpZ; ++z)
-                if (z < nZ) {  // slots without a function have w = 0
-                  const int m = (p * kBpZ + z) * 2;
-                  const R wp = sl.wc[m], wm = sl.wc[m + 1];
-                  S2 += wp * Ap[z] + wm * Am[z];
-                  S1 += wp * dAp[z] + wm * dAm[z];
-                }
-              const R eta = pick<R>(bp.y_eta[p], bp.y_etaf[p]);
-              const R E2 = sl.e[p * NB + qa] * sl.e[p * NB + qb];
-              R X = R(1), fX = R(1);
-              const bool k4 = bp.y_kind[p] == 4;
-              if (k4) {
-                X = near ? BM<R>::ex(-eta * rab2) : R(0);
-                fX = X * fab;
-              }
-              const R Y = E2 * fa * fb * fX;
-              al += S1 * Y;
-              bu += S2 * E2 * fb * fX * (R(-2) * eta * ra * fa + dfa) * ia;
-              bw += S2 * E2 * fa * fX * (R(-2) * eta * rb * fb + dfb) * ib;
-              if (k4 && near) gs += S2 * E2 * fa * fb * X * (R(-2) * eta * rab * fab + dfab) * irab;
-            }
-          // dc/du_a = u_b/(R_a R_b) - c u_a/R_a^2, dc/du_b = u_a/(R_a R_b) - c u_b/R_b^2;
-          // to a: dT/du_a - dT/ds, to b: dT/du_b + dT/ds
-          const R ca = c * ia * ia, cb = c * ib * ib;
-          sl.gax[qa] += al * (bx * iab - ca * ax) + bu * ax - gs * sx;
-          sl.gay[qa] += al * (by * iab - ca * ay) + bu * ay - gs * sy;
-          sl.gaz[qa] += al * (bz * iab - ca * az) + bu * az - gs * sz;
-          sl.gbx[qb] += al * (ax * iab - cb * bx) + bw * bx + gs * sx;
-          sl.gby[qb] += al * (ay * iab - cb * by) + bw * by + gs * sy;
-          sl.gbz[qb] += al * (az * iab - cb * bz) + bw * bz + gs * sz;
+          grad_pair(qa, qb);
         }
         __syncwarp();
       }

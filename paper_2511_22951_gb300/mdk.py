@@ -74,6 +74,7 @@ SIGNATURES = {
     "mdk_autotune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)],
     "mdk_set_launch": [_P, _I, _I],
     "mdk_set_list_kind": [_P, _I],
+    "mdk_fma_peak": [_I, ctypes.POINTER(_D)],
     "mdk_get_list_kind": [_P, ctypes.POINTER(_I)],
     "mdk_set_graphs": [_P, _I],
     "mdk_profile": [_P, _I],
@@ -482,6 +483,16 @@ class Context:
     def set_piston(self, u_p, flags):
         f = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8)
         _check(self.lib.mdk_set_piston(self.h, u_p, _ptr(f)), "mdk_set_piston")
+
+
+def fma_peak(precision="fp64"):
+    """Measured FMA throughput (TFLOP/s) of the current device: "fp64" or
+    "mixed" (FP32)."""
+    lib = load()
+    v = _D()
+    _check(lib.mdk_fma_peak(MDK_FP64 if precision == "fp64" else MDK_MIXED, ctypes.byref(v)),
+           "mdk_fma_peak")
+    return float(v.value)
 
 
 def make_context(wl, precision=None, stream=None, rebuild_every=0, max_neighbors=0,
