@@ -113,6 +113,8 @@ def algorithmic_bytes_per_atom(wl, prec, n_list, kind="full"):
 TRAFFIC = {
     ("lj", "mixed", "full"): {
         "bytes_per_atom": 458.3,
+        "neighbors_per_atom": 78.0,
+        "threads_per_atom": 1,
         "sources_sha256": "c2710d5bab302fa598510dfc1a69c57f85b984cc0971af7a8a8a5361f5ec700b",
         "capture": "k_lj<Mixed, kStep, T=1>, 3 launches on 2,048,000 atoms (80^3 FCC cells, "
                    "the same lattice and 78 neighbours per atom): dram__bytes_read.sum + "
@@ -137,9 +139,15 @@ def sources_sha256(kind="full"):
     return h.hexdigest()
 
 
-def traffic_per_launch(wl, prec, n_atoms, kind="full"):
+def traffic_per_launch(wl, prec, n_atoms, kind="full", n_avg=None, tpa=None):
+    """Measured DRAM bytes per launch, when the captured kernel (same sources,
+    same list length and launch shape) is the one this run uses; else None."""
     t = TRAFFIC.get((wl.potential, prec, kind))
     if t is None or t["sources_sha256"] != sources_sha256(kind):
+        return None
+    if n_avg is not None and abs(n_avg - t["neighbors_per_atom"]) > 1e-9:
+        return None
+    if tpa is not None and tpa != t["threads_per_atom"]:
         return None
     return t["bytes_per_atom"] * n_atoms
 
@@ -596,7 +604,7 @@ def main():
                               " FMA probe (mdk_fma_peak)") if fma_pk else "nominal",
                 "peak_nominal": nominal, **common}
     elif prec == "mixed":
-        tr = traffic_per_launch(wl, prec, n_now, kind)
+        tr = traffic_per_launch(wl, prec, n_now, kind, n_avg, tpa)
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                 "frac": gbs / hbm, "traffic": tr, "bytes_per_atom": bpa,
                 "traffic_unit": "bytes per launch", "peak_kind": peak_kind, **common}
