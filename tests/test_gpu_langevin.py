@@ -34,20 +34,22 @@ REGIONS = [(-5.0, 10.5, 50.0, (0.001, 0.0, 0.0), 0.01),
            (10.5, 30.0, 150.0, (0.0, -0.0005, 0.0), 0.02)]
 
 
-def lj_ctx(mdk, s, prec):
+def lj_ctx(mdk, s, prec, kind="full"):
     lj = W.LJ_AR
     ctx = mdk.Context(s.lo, s.hi, s.periodic, s.masses, prec)
     ctx.set_potential_lj(lj.eps, lj.sigma, lj.rc, lj.shift_mode)
+    ctx.set_list_kind(kind)
     ctx.plan(lj.rc, 0.3)
     ctx.set_state(s.x, s.v)
     ctx.build_neighbors(lj.rc, 0.3)
     return ctx
 
 
-def test_langevin_trajectory_matches_oracle(mdk, ora):
+@pytest.mark.parametrize("kind", ["full", "half"])
+def test_langevin_trajectory_matches_oracle(mdk, ora, kind):
     wl = W.config0()
     s = wl.systems[0]
-    ctx = lj_ctx(mdk, s, "fp64")
+    ctx = lj_ctx(mdk, s, "fp64", kind)
     ctx.set_langevin(REGIONS, seed=7)
     ctx.step(wl.dt, 10)
     xg, vg = ctx.get_state()
@@ -116,7 +118,8 @@ def test_langevin_arguments_are_checked(mdk):
     ctx.set_langevin([])                                         # off
 
 
-def test_stationary_window_with_thermostats_matches_oracle(mdk, ora):
+@pytest.mark.parametrize("kind", ["full", "half"])
+def test_stationary_window_with_thermostats_matches_oracle(mdk, ora, kind):
     """The paper's stationary-shock window: material flows in at u_in (< 0)
     through fixed inflow and outflow boundaries (outflow deletion at
     x_front - L_behind, fresh layers up to x_front + L_ahead), with Langevin
@@ -139,6 +142,7 @@ def test_stationary_window_with_thermostats_matches_oracle(mdk, ora):
     cap = 4000
     ctx = mdk.Context(s.lo, s.hi, s.periodic, s.masses, "fp64", capacity=cap)
     ctx.set_potential_eam(wl.tables)
+    ctx.set_list_kind(kind)
     ctx.plan(wl.tables.rc, 0.3, rebuild_every=5)
     ctx.set_state(s.x, v)
     ctx.build_neighbors(wl.tables.rc, 0.3)
@@ -202,7 +206,8 @@ def test_stationary_search_workflow_runs(mdk):
     assert all(np.isfinite(q) for q in slopes.values())
 
 
-def test_replica_thermostats_match_oracle(mdk, ora):
+@pytest.mark.parametrize("kind", ["full", "half"])
+def test_replica_thermostats_match_oracle(mdk, ora, kind):
     """Per-replica thermostats (mdk_set_langevin_replicas): every replica of
     a batch at its own T and beta; FP64 trajectories equal the oracle's run of
     each replica with one whole-box region (ids continue across replicas)."""
@@ -215,6 +220,7 @@ def test_replica_thermostats_match_oracle(mdk, ora):
                       np.concatenate([r.masses for r in reps]), "fp64",
                       n_atoms=[r.n for r in reps])
     ctx.set_potential_lj(lj.eps, lj.sigma, lj.rc, lj.shift_mode)
+    ctx.set_list_kind(kind)
     ctx.plan(lj.rc, 0.3)
     ctx.set_state(np.concatenate([r.x for r in reps]), np.concatenate([r.v for r in reps]))
     ctx.build_neighbors(lj.rc, 0.3)

@@ -345,7 +345,8 @@ def test_profiles_match_oracle(mdk, ora):
 
 
 # --------------------------------------------------------------------------- moving window
-def test_window_matches_oracle(mdk, ora):
+@pytest.mark.parametrize("kind", ["full", "half"])
+def test_window_matches_oracle(mdk, ora, kind):
     """Piston + moving window (Al-like slab, FP64, rebuild every 5 steps): after
     12 steps the atoms present (ids), their positions and velocities equal the
     oracle's window run.  dt = 0.5 fs keeps every displacement below skin/2, so
@@ -364,6 +365,7 @@ def test_window_matches_oracle(mdk, ora):
     ctx = mdk.Context(s.lo, s.hi, s.periodic, s.masses, "fp64", capacity=cap)
     ctx.set_potential_eam(wl.tables)
     ctx.plan(wl.tables.rc, 0.3, rebuild_every=5)
+    ctx.set_list_kind(kind)
     ctx.set_state(s.x, v)
     ctx.build_neighbors(wl.tables.rc, 0.3)
     ctx.set_piston(0.015, pis)
