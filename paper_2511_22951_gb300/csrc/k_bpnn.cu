@@ -216,7 +216,10 @@ constexpr int bp_blocks() {
   return sizeof(typename G<P>::R) == 4 ? 2 : 1;
 }
 
-template <class P, bool ENERGY>
+// NY: the (eta, kind) groups the kernel is compiled for (nY rounded up to an
+// even number); the padded groups carry zero exponentials, zeta groups past
+// nZ zero coefficients, so the pair loops run without per-group guards.
+template <class P, bool ENERGY, int NY>
 __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
     k_bpnn(Sys s, BPParams bp, StepArgs a) {
   using GP = G<P>;
@@ -227,7 +230,8 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
   const int N = s.st->N;
   const size_t Nc = s.N_cap;
   const int NB = s.nmax;
-  const int nY = bp.nY, nZ = bp.nZ, nr = bp.n_rad, H1 = bp.H1, H2 = bp.H2;
+  const int nY = bp.nY, nr = bp.n_rad, H1 = bp.H1, H2 = bp.H2;
+  constexpr int NS = 2 * NY * kBpZ;  // angular slots of the compiled groups
   constexpr int n_in = kBpIn;
   const unsigned long long used = bp.slot_mask;
   const R rc = pick<R>(bp.rc, bp.rcf), rc2 = rc * rc, inv_rc = R(1) / rc;
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
           *w23 = b2 + H2;
   const size_t wbytes = ((size_t)nW * sizeof(R) + 15) / 16 * 16;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Slab<R> sl = slab_at<R>(smem + wbytes + (size_t)warp * slab_bytes(NB, nY, sizeof(R)), NB, nY);
+  Slab<R> sl = slab_at<R>(smem + wbytes + (size_t)warp * slab_bytes(NB, NY, sizeof(R)), NB, NY);
   const int i = blockIdx.x * (blockDim.x >> 5) + warp;
   if (i >= N) return;  // whole warps leave together
 
@@ -286,8 +290,9 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
       sl.gbx[q] = sl.gby[q] = sl.gbz[q] = R(0);
       sl.fc[q] = R(0.5) * (cs + R(1));
       sl.dfc[q] = half_pi_rc * sn;
-      for (int p = 0; p < nY; ++p)
-        sl.e[p * NB + q] = BM<R>::ex(-pick<R>(bp.y_eta[p], bp.y_etaf[p]) * r2);
+#pragma unroll
+      for (int p = 0; p < NY; ++p)
+        sl.e[p * NB + q] = p < nY ? BM<R>::ex(-pick<R>(bp.y_eta[p], bp.y_etaf[p]) * r2) : R(0);
       sl.j[q] = (int)j;
     }
     n += __popc(m);
@@ -308,9 +313,9 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
         accr[m] += v;
       }
   }
-  R acca[kBpSlots];
+  R acca[NS];
 #pragma unroll
-  for (int m = 0; m < kBpSlots; ++m) acca[m] = 0;
+  for (int m = 0; m < NS; ++m) acca[m] = 0;
   {
     const int npair = n * (n - 1) / 2;
     int qa = 0, rel = lane;  // pair t = (qa, qa + 1 + rel), rows in order of qa
@@ -332,36 +337,33 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
         BM<R>::scpi(BM<R>::sq(rab2) * inv_rc, &sn, &cs);
         fab = R(0.5) * (cs + R(1));
       }
-      R Y[kBpY];
+      R Y[NY];
 #pragma unroll
-      for (int p = 0; p < kBpY; ++p)
-        if (p < nY) {
-          Y[p] = sl.e[p * NB + qa] * sl.e[p * NB + qb] * fa * fb;
-          if (bp.y_kind[p] == 4)
-            Y[p] = near ? Y[p] * BM<R>::ex(-pick<R>(bp.y_eta[p], bp.y_etaf[p]) * rab2) * fab
-                        : R(0);
-        }
+      for (int p = 0; p < NY; ++p) {
+        Y[p] = sl.e[p * NB + qa] * sl.e[p * NB + qb] * fa * fb;
+        if (bp.y_kind[p] == 4)
+          Y[p] = near ? Y[p] * BM<R>::ex(-pick<R>(bp.y_eta[p], bp.y_etaf[p]) * rab2) * fab
+                      : R(0);
+      }
       // 2^(1 - zeta) (1 +- c)^zeta per zeta group
       R Pp[kBpZ], Pm[kBpZ];
 #pragma unroll
-      for (int z = 0; z < kBpZ; ++z)
-        if (z < nZ) {
-          const R cf = pick<R>(bp.z_coef[z], bp.z_coeff[z]);
-          ipow2<R>(R(1) + c, R(1) - c, bp.z_pow[z], Pp[z], Pm[z]);
-          Pp[z] *= cf * (R(1) + c);
-          Pm[z] *= cf * (R(1) - c);
-        }
+      for (int z = 0; z < kBpZ; ++z) {  // zeta groups past nZ have coefficient 0
+        const R cf = pick<R>(bp.z_coef[z], bp.z_coeff[z]);
+        ipow2<R>(R(1) + c, R(1) - c, bp.z_pow[z], Pp[z], Pm[z]);
+        Pp[z] *= cf * (R(1) + c);
+        Pm[z] *= cf * (R(1) - c);
+      }
       // every slot of the used groups (a slot without a function has zero
       // weights, so its sum is never read)
 #pragma unroll
-      for (int p = 0; p < kBpY; ++p)
+      for (int p = 0; p < NY; ++p)
 #pragma unroll
-        for (int z = 0; z < kBpZ; ++z)
-          if (p < nY && z < nZ) {
-            const int m = (p * kBpZ + z) * 2;
-            acca[m] += Pp[z] * Y[p];
-            acca[m + 1] += Pm[z] * Y[p];
-          }
+        for (int z = 0; z < kBpZ; ++z) {
+          const int m = (p * kBpZ + z) * 2;
+          acca[m] += Pp[z] * Y[p];
+          acca[m + 1] += Pm[z] * Y[p];
+        }
       rel += 32;
       while (qa < n - 1 && rel >= n - 1 - qa) {
         rel -= n - 1 - qa;
@@ -373,13 +375,14 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
   for (int m = 0; m < kBpRad; ++m)
     if (m < nr) accr[m] = warp_sum(accr[m]);
 #pragma unroll
-  for (int m = 0; m < kBpSlots; ++m)
-    if (m / (2 * kBpZ) < nY && (m / 2) % kBpZ < nZ) acca[m] = warp_sum(acca[m]);
+  for (int m = 0; m < NS; ++m)
+    if ((used >> m) & 1ull) acca[m] = warp_sum(acca[m]);
   if (lane == 0) {
 #pragma unroll
     for (int m = 0; m < kBpRad; ++m) sl.G[m] = m < nr ? accr[m] : R(0);
 #pragma unroll
-    for (int m = 0; m < kBpSlots; ++m) sl.G[kBpRad + m] = ((used >> m) & 1ull) ? acca[m] : R(0);
+    for (int m = 0; m < kBpSlots; ++m)
+      sl.G[kBpRad + m] = (m < NS && ((used >> m) & 1ull)) ? acca[m < NS ? m : 0] : R(0);
   }
   __syncwarp();
 
@@ -440,48 +443,45 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
       // per zeta group: A = 2^(1-zeta) (1 +- c)^zeta and dA/dc
       R Ap[kBpZ], Am[kBpZ], dAp[kBpZ], dAm[kBpZ];
 #pragma unroll
-      for (int z = 0; z < kBpZ; ++z)
-        if (z < nZ) {
-          const R cf = pick<R>(bp.z_coef[z], bp.z_coeff[z]);
-          const R zt = pick<R>(bp.z_zeta[z], bp.z_zetaf[z]);
-          R pp, pm;
-          ipow2<R>(R(1) + c, R(1) - c, bp.z_pow[z], pp, pm);
-          pp *= cf;
-          pm *= cf;
-          Ap[z] = pp * (R(1) + c);
-          Am[z] = pm * (R(1) - c);
-          dAp[z] = zt * pp;
-          dAm[z] = -zt * pm;
-        }
+      for (int z = 0; z < kBpZ; ++z) {  // zeta groups past nZ have coefficient 0
+        const R cf = pick<R>(bp.z_coef[z], bp.z_coeff[z]);
+        const R zt = pick<R>(bp.z_zeta[z], bp.z_zetaf[z]);
+        R pp, pm;
+        ipow2<R>(R(1) + c, R(1) - c, bp.z_pow[z], pp, pm);
+        pp *= cf;
+        pm *= cf;
+        Ap[z] = pp * (R(1) + c);
+        Am[z] = pm * (R(1) - c);
+        dAp[z] = zt * pp;
+        dAm[z] = -zt * pm;
+      }
       // per (eta, kind) group: the functions' weighted sums S2 = sum w A,
       // S1 = sum w dA/dc, times the group's factor Y and its derivatives
       R al = 0, bu = 0, bw = 0, gs = 0;
 #pragma unroll
-      for (int p = 0; p < kBpY; ++p)
-        if (p < nY) {
-          R S1 = 0, S2 = 0;
-          R wv[2 * kBpZ];  // the group's slots: (z, lambda = +1), (z, lambda = -1)
-          ld_group<R>(sl.wc + p * 2 * kBpZ, wv);
+      for (int p = 0; p < NY; ++p) {  // padded groups: zero exponentials and weights
+        R S1 = 0, S2 = 0;
+        R wv[2 * kBpZ];  // the group's slots: (z, lambda = +1), (z, lambda = -1)
+        ld_group<R>(sl.wc + p * 2 * kBpZ, wv);
 #pragma unroll
-          for (int z = 0; z < kBpZ; ++z)
-            if (z < nZ) {  // slots without a function have w = 0
-              S2 += wv[2 * z] * Ap[z] + wv[2 * z + 1] * Am[z];
-              S1 += wv[2 * z] * dAp[z] + wv[2 * z + 1] * dAm[z];
-            }
-          const R eta = pick<R>(bp.y_eta[p], bp.y_etaf[p]);
-          const R E2 = sl.e[p * NB + qa] * sl.e[p * NB + qb];
-          R X = R(1), fX = R(1);
-          const bool k4 = bp.y_kind[p] == 4;
-          if (k4) {
-            X = near ? BM<R>::ex(-eta * rab2) : R(0);
-            fX = X * fab;
-          }
-          const R Y = E2 * fa * fb * fX;
-          al += S1 * Y;
-          bu += S2 * E2 * fb * fX * (R(-2) * eta * ra * fa + dfa) * ia;
-          bw += S2 * E2 * fa * fX * (R(-2) * eta * rb * fb + dfb) * ib;
-          if (k4 && near) gs += S2 * E2 * fa * fb * X * (R(-2) * eta * rab * fab + dfab) * irab;
+        for (int z = 0; z < kBpZ; ++z) {  // slots without a function have w = 0
+          S2 += wv[2 * z] * Ap[z] + wv[2 * z + 1] * Am[z];
+          S1 += wv[2 * z] * dAp[z] + wv[2 * z + 1] * dAm[z];
         }
+        const R eta = pick<R>(bp.y_eta[p], bp.y_etaf[p]);
+        const R E2 = sl.e[p * NB + qa] * sl.e[p * NB + qb];
+        R X = R(1), fX = R(1);
+        const bool k4 = bp.y_kind[p] == 4;
+        if (k4) {
+          X = near ? BM<R>::ex(-eta * rab2) : R(0);
+          fX = X * fab;
+        }
+        const R Y = E2 * fa * fb * fX;
+        al += S1 * Y;
+        bu += S2 * E2 * fb * fX * (R(-2) * eta * ra * fa + dfa) * ia;
+        bw += S2 * E2 * fa * fX * (R(-2) * eta * rb * fb + dfb) * ib;
+        if (k4 && near) gs += S2 * E2 * fa * fb * X * (R(-2) * eta * rab * fab + dfab) * irab;
+      }
       // dc/du_a = u_b/(R_a R_b) - c u_a/R_a^2, dc/du_b = u_a/(R_a R_b) - c u_b/R_b^2;
       // to a: dT/du_a - dT/ds, to b: dT/du_b + dT/ds
       const R ca = c * ia * ia, cb = c * ib * ib;
@@ -598,31 +598,53 @@ int warps_for(int precision) { return precision == 0 ? 4 : 8; }
 
 }  // namespace
 
+// the compiled group count for nY groups: nY rounded up to an even number
+int ny_compiled(int nY) { return nY <= 2 ? 2 : (nY <= 4 ? 4 : (nY <= 6 ? 6 : 8)); }
+
 size_t bpnn_smem_bytes(const BPParams &p, int precision, int nmax, int *warps) {
   const size_t rsz = precision == 0 ? 8 : 4;
   const int nW = kBpIn * p.H1 + p.H1 + p.H1 * p.H2 + 2 * p.H2;
   const size_t wbytes = ((size_t)nW * rsz + 15) / 16 * 16;
-  const size_t per = slab_bytes(nmax, p.nY, rsz);
+  const size_t per = slab_bytes(nmax, ny_compiled(p.nY), rsz);
   int w = warps_for(precision);
   while (w > 1 && wbytes + (size_t)w * per > 200 * 1024) --w;
   if (warps) *warps = w;
   return wbytes + (size_t)w * per;
 }
 
+namespace {
+template <class P, int NY>
+cudaError_t smem_attr_ny(int b) {
+  cudaError_t e = cudaFuncSetAttribute(k_bpnn<P, true, NY>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_bpnn<P, false, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             b);
+  return e;
+}
+template <class P>
+cudaError_t smem_attr(int b) {
+  cudaError_t e = smem_attr_ny<P, 2>(b);
+  if (e == cudaSuccess) e = smem_attr_ny<P, 4>(b);
+  if (e == cudaSuccess) e = smem_attr_ny<P, 6>(b);
+  if (e == cudaSuccess) e = smem_attr_ny<P, 8>(b);
+  return e;
+}
+template <class P, bool EN>
+void go(const Sys &s, const BPParams &p, StepArgs a, int grid, int threads, size_t sm,
+        cudaStream_t st) {
+  switch (ny_compiled(p.nY)) {
+    case 2: k_bpnn<P, EN, 2><<<grid, threads, sm, st>>>(s, p, a); break;
+    case 4: k_bpnn<P, EN, 4><<<grid, threads, sm, st>>>(s, p, a); break;
+    case 6: k_bpnn<P, EN, 6><<<grid, threads, sm, st>>>(s, p, a); break;
+    default: k_bpnn<P, EN, 8><<<grid, threads, sm, st>>>(s, p, a); break;
+  }
+}
+}  // namespace
+
 int configure_bpnn_smem(size_t bytes, int precision) {
   const int b = (int)bytes;
-  cudaError_t e;
-  if (precision == 0) {
-    e = cudaFuncSetAttribute(k_bpnn<Fp64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_bpnn<Fp64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               b);
-  } else {
-    e = cudaFuncSetAttribute(k_bpnn<Mixed, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_bpnn<Mixed, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               b);
-  }
+  const cudaError_t e = precision == 0 ? smem_attr<Fp64>(b) : smem_attr<Mixed>(b);
   return e == cudaSuccess ? 0 : 1;
 }
 
@@ -632,17 +654,12 @@ void launch_bpnn(const Sys &s, const BPParams &p, int precision, Mode mode, Step
   const size_t sm = bpnn_smem_bytes(p, precision, s.nmax, &w);
   const long long n = s.N_cap > 0 ? s.N_cap : 1;
   const int grid = (int)((n + w - 1) / w);
-  if (precision == 0) {
-    if (a.energy)
-      k_bpnn<Fp64, true><<<grid, 32 * w, sm, st>>>(s, p, a);
-    else
-      k_bpnn<Fp64, false><<<grid, 32 * w, sm, st>>>(s, p, a);
-  } else {
-    if (a.energy)
-      k_bpnn<Mixed, true><<<grid, 32 * w, sm, st>>>(s, p, a);
-    else
-      k_bpnn<Mixed, false><<<grid, 32 * w, sm, st>>>(s, p, a);
-  }
+  if (precision == 0)
+    a.energy ? go<Fp64, true>(s, p, a, grid, 32 * w, sm, st)
+             : go<Fp64, false>(s, p, a, grid, 32 * w, sm, st);
+  else
+    a.energy ? go<Mixed, true>(s, p, a, grid, 32 * w, sm, st)
+             : go<Mixed, false>(s, p, a, grid, 32 * w, sm, st);
   launch_half_fin(s, precision, mode, a, st);
 }
 
