@@ -98,6 +98,8 @@ def algorithmic_bytes_per_atom(wl, prec, n_list, kind="full"):
     g = 16 if prec == "mixed" else 32
     lj = g + 4 * n_list + 4 + 48 + 48 + 24 + 4 + g
     if wl.potential == "lj":
+        if kind == "cells":   # no list entries and no list length
+            return lj - 4
         return lj + (48 if kind == "half" else 0)
     if wl.potential == "bpnn":   # full list, force accumulators like half lists
         return lj + 48
@@ -451,7 +453,7 @@ def main():
                          "synthetic 8 G2 + 43 G4 model, 10-10 network")
     ap.add_argument("--launch", default=None,
                     help="threads-per-atom x block (e.g. 1x128) instead of the autotuner")
-    ap.add_argument("--list", default=None, choices=("full", "half"),
+    ap.add_argument("--list", default=None, choices=("full", "half", "cells"),
                     help="with --launch: the Verlet-list kind (LJ; default full)")
     ap.add_argument("--drift-steps", type=int, default=0,
                     help="also run an NVE drift measurement of this many steps")
@@ -536,7 +538,8 @@ def main():
         tpa, block, _ = ctx.autotune()
         picked = "mdk_autotune"
     kind = ctx.list_kind
-    n_list = n_avg if kind == "full" else 0.5 * n_avg   # a half list holds each pair once
+    # a half list holds each pair once; the cell kernel reads no list
+    n_list = {"full": n_avg, "half": 0.5 * n_avg, "cells": 0.0}[kind]
 
     # warm-up (untimed; also captures the step graphs)
     ctx.step(wl.dt, args.warmup, check=True)
@@ -575,7 +578,10 @@ def main():
     force_ms = prof["force_ms"] / max(1.0, prof["force_passes"])
     bpa = algorithmic_bytes_per_atom(wl, prec, n_list, kind)
     gbs = n_now * bpa / (force_ms / 1e3) / 1e9
-    if kind == "half":
+    if kind == "cells":
+        kdesc = (f"k_lj_cells<{prec}> (one warp per cell, neighbour cells tiled in shared "
+                 "memory, no list) with the fused velocity-Verlet update")
+    elif kind == "half":
         kdesc = (f"k_lj_half<{prec}> pair pass (half lists, accumulating atomics) + "
                  "k_half_fin per-atom velocity-Verlet pass")
     else:

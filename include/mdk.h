@@ -463,8 +463,9 @@ int mdk_lj_compute_noalloc(const double *x, int64_t N, const double box_lo[3],
  * in {1, 2, 4} x threads per block in {128, 256, 512} (LJ: <= 256) -- on this
  * context's system (reps force passes each, CUDA events on the context's
  * stream) and keep the fastest for later calls.  With LJ and EAM it also
- * times half lists (one thread per atom; 128 and 256 threads per block)
- * and keeps the faster list kind (mdk_get_list_kind reports it; a switch
+ * times half lists (one thread per atom; 128 and 256 threads per block),
+ * with LJ the list-free cell kernel (128 and 256 threads per block), and
+ * keeps the fastest list kind (mdk_get_list_kind reports it; a switch
  * rebuilds the list).  The BPNN kernel has one shape (a warp per atom).  Outputs may be NULL.  Small systems (few atoms per SM)
  * and long lists favour several threads per atom.  The state must be set;
  * the lists are built if needed.  (No paper counterpart: the paper chunks
@@ -494,11 +495,21 @@ int mdk_set_launch(mdk_ctx *ctx, int tpa, int block);
  *     MDK_ERR_BAD_ARG with the BPNN potential (setting one returns the
  *     context to full lists).  mdk_eam_vjp walks full lists and switches a
  *     half-list context back to full lists (the next call rebuilds).
+ *   MDK_LIST_CELLS (LJ only): no Verlet list.  A build sorts the atoms into
+ *     cells of size >= rc + skin as usual and skips the list; the force pass
+ *     takes one warp per cell, stages 32 neighbour records at a time from
+ *     the 27 template cells in shared memory and tests all of them against
+ *     the cell's atoms (pairs closer than rc at the current positions are in
+ *     adjacent build cells while no atom has moved more than skin/2).  Same
+ *     definitions and bars as the list kernels; mdk_get_neighbors and
+ *     mdk_neighbor_count return MDK_ERR_ORDER.  Setting an EAM potential
+ *     returns the context to full lists.
  * A change of kind makes the next call rebuild the list; mdk_get_neighbors
  * returns the list of the current kind.
  */
 #define MDK_LIST_FULL 0
 #define MDK_LIST_HALF 1
+#define MDK_LIST_CELLS 2
 int mdk_set_list_kind(mdk_ctx *ctx, int kind);
 int mdk_get_list_kind(const mdk_ctx *ctx, int *kind);
 

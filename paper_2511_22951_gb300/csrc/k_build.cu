@@ -480,13 +480,13 @@ __device__ __forceinline__ bool half_keep(int i, int j, bool s_pos) {
 
 __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
   __shared__ uint32_t stage[2 * kGroup][kBlk];
-  if (!flag_on(s)) return;
+  if (!flag_on(s) || s.half == 2) return;  // 2: forces straight from the cells, no list
   const int N = s.st->N;
   const size_t Nc = s.N_cap;
   const float lo_thr = s.filt_lo, hi_thr = s.filt_hi;
   const double rns2 = s.rns2;
   const int ngroups = s.nmax / kGroup;
-  const bool half = s.half != 0;
+  const bool half = s.half == 1;
   const int tx = threadIdx.x;
   for (int i = blockIdx.x * kBlk + tx; i < N; i += gridDim.x * kBlk) {
     const float4 pi = __ldg(s.pf + i);

@@ -289,7 +289,7 @@ void fill_sys_params(mdk_ctx *c) {
   s.n_rep = c->n_rep;
   s.n_cells = c->n_cells;
   s.n_scan_blocks = scan_blocks_for(c->n_cells + 1);
-  s.half = (c->pot == 1 || c->pot == 2) && c->cfg.half ? 1 : 0;
+  s.half = (c->pot == 1 || (c->pot == 2 && c->cfg.half == 1)) ? c->cfg.half : 0;
   const double rns = c->rc_list + c->skin;
   s.rns2 = rns * rns;
   // FP32 pre-filter band: the float r^2 of a candidate is within ~6e-6 r_ns^2
@@ -445,11 +445,14 @@ int timed(mdk_ctx *c, std::vector<std::pair<int, int>> &log, int n_kernels, F la
 
 int force_pass(mdk_ctx *c, Mode mode, int energy, double dt) {
   StepArgs a{dt, c->cur, energy};
-  const bool half = (c->pot == 1 || c->pot == 2) && c->cfg.half;
+  const bool cells = c->pot == 1 && c->cfg.half == 2;
+  const bool half = (c->pot == 1 || c->pot == 2) && c->cfg.half == 1;
   const int nk = c->pot == 1 ? (half ? 2 : 1) : (c->pot == 2 && half ? 4 : 2);
   return timed(c, c->ev_force, nk, [&] {
     if (c->pot == 3)
       launch_bpnn(c->sys, c->bp, c->precision, mode, a, c->stream);
+    else if (cells)
+      launch_lj_cells(c->sys, c->lj, c->precision, mode, a, c->cfg, c->stream);
     else if (half && c->pot == 2)
       launch_eam_half(c->sys, c->eam, c->precision, mode, a, c->cfg, c->stream);
     else if (half)
@@ -794,6 +797,7 @@ int mdk_set_potential_eam(mdk_ctx *c, int nr, double rc, const double *phi, cons
   c->eam_rho.assign(rho, rho + nr);
   c->eam_F.assign(F, F + nrho);
   c->pot = 2;
+  if (c->cfg.half == MDK_LIST_CELLS) use_list_kind(c, MDK_LIST_FULL);  // LJ only
   if (!c->planned) plan(c, rc, 0.3, 0, 0);
   if (resized) {
     c->ws_ok = false;  // table area changes size: a new workspace is needed
@@ -1096,7 +1100,7 @@ int mdk_build_neighbors(mdk_ctx *c, double rc, double skin) {
 
 int mdk_neighbor_count(mdk_ctx *c, int64_t *total) {
   if (check_ctx(c) || !total) return MDK_ERR_BAD_ARG;
-  if (!c->list_built || c->win_on) return MDK_ERR_ORDER;
+  if (!c->list_built || c->win_on || c->cfg.half == MDK_LIST_CELLS) return MDK_ERR_ORDER;
   std::vector<int32_t> nn((size_t)c->N);
   if (c->N > 0) {
     MDK_CK(cudaMemcpyAsync(nn.data(), c->sys.nnbr, sizeof(int32_t) * c->N, cudaMemcpyDeviceToHost,
@@ -1111,7 +1115,7 @@ int mdk_neighbor_count(mdk_ctx *c, int64_t *total) {
 
 int mdk_get_neighbors(mdk_ctx *c, int64_t *offsets, int32_t *jout, int32_t *img) {
   if (check_ctx(c) || !offsets) return MDK_ERR_BAD_ARG;
-  if (!c->list_built || c->win_on) return MDK_ERR_ORDER;
+  if (!c->list_built || c->win_on || c->cfg.half == MDK_LIST_CELLS) return MDK_ERR_ORDER;
   const int64_t N = c->N;
   const size_t Nc = (size_t)c->N_cap;
   Sys &s = c->sys;
@@ -1460,13 +1464,15 @@ int mdk_autotune(mdk_ctx *c, int reps, int *tpa_out, int *block_out, double *ms_
   float best_ms = -1.f;
   static const int kTpa[3] = {1, 2, 4};
   static const int kBlock[3] = {128, 256, 512};
-  // LJ and EAM: full lists in every shape, then half lists (one thread per atom)
-  for (int kind = 0; kind < (c->pot == 1 || c->pot == 2 ? 2 : 1) && !r; ++kind)
+  // LJ and EAM: full lists in every shape, then half lists (one thread per
+  // atom); LJ also the list-free cell kernel (one warp per cell)
+  const int n_kinds = c->pot == 1 ? 3 : (c->pot == 2 ? 2 : 1);
+  for (int kind = 0; kind < n_kinds && !r; ++kind)
   for (int a = 0; a < 3 && !r; ++a)
     for (int b = 0; b < 3; ++b) {
       if (c->pot == 1 && kBlock[b] > 256) continue;  // the LJ kernels take <= 256
       if (c->pot == 3 && (a > 0 || b > 0)) continue;  // BPNN: one warp per atom, one shape
-      if (kind == 1 && (kTpa[a] != 1 || kBlock[b] > 256)) continue;  // half: <= 256 threads
+      if (kind >= 1 && (kTpa[a] != 1 || kBlock[b] > 256)) continue;  // <= 256 threads
       if (c->cfg.half != kind || !c->list_built) {
         use_list_kind(c, kind);
         r = build_now(c);
@@ -1525,16 +1531,18 @@ int mdk_set_launch(mdk_ctx *c, int tpa, int block) {
 }
 
 int mdk_set_list_kind(mdk_ctx *c, int kind) {
-  if (check_ctx(c) || (kind != MDK_LIST_FULL && kind != MDK_LIST_HALF)) return MDK_ERR_BAD_ARG;
+  if (check_ctx(c) || (kind != MDK_LIST_FULL && kind != MDK_LIST_HALF && kind != MDK_LIST_CELLS))
+    return MDK_ERR_BAD_ARG;
   if (kind == MDK_LIST_HALF && c->pot != 1 && c->pot != 2)
     return c->pot == 0 ? MDK_ERR_ORDER : MDK_ERR_BAD_ARG;
+  if (kind == MDK_LIST_CELLS && c->pot != 1) return c->pot == 0 ? MDK_ERR_ORDER : MDK_ERR_BAD_ARG;
   use_list_kind(c, kind);
   return MDK_OK;
 }
 
 int mdk_get_list_kind(const mdk_ctx *c, int *kind) {
   if (check_ctx(c) || !kind) return MDK_ERR_BAD_ARG;
-  *kind = c->cfg.half ? MDK_LIST_HALF : MDK_LIST_FULL;
+  *kind = c->cfg.half;
   return MDK_OK;
 }
 

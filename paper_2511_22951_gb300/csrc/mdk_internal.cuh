@@ -94,7 +94,8 @@ struct Sys {
   void *pgF;                // EAM: gather copy with F'(rho_j) in .w (density pass)
   int32_t *nnbr;
   uint32_t *nbr;
-  int half;                 // 1: half lists (each pair once, Newton's third law)
+  int half;                 // list kind: 0 full, 1 half (each pair once), 2 none (LJ
+                            // forces straight from the build's cells)
   // half-list accumulators, [10][N_cap] 8-byte words: F_x, F_y, F_z, U_i,
   // W_i[6]; int64 fixed point (kHalfScale) in the mixed path, double in the
   // FP64 path; zero between force passes
@@ -333,7 +334,8 @@ void launch_set_rebuild_flag(const Sys &s, cudaStream_t st);
 struct LaunchCfg {
   int tpa = 1;      // threads per atom: 1, 2 or 4
   int block = 256;  // threads per block: 128, 256 or 512
-  int half = 0;     // LJ: 1 = half lists with accumulating atomics (tpa 1)
+  int half = 0;     // list kind: 1 = half lists with accumulating atomics (tpa 1),
+                    // 2 = LJ from the cells, one warp per cell (no list)
 };
 
 void launch_lj(const Sys &s, const LJParams &p, int precision, Mode mode, StepArgs a,
@@ -345,6 +347,10 @@ void launch_bpnn(const Sys &s, const BPParams &p, int precision, Mode mode, Step
                  cudaStream_t st);
 size_t bpnn_smem_bytes(const BPParams &p, int precision, int nmax, int *warps);
 int configure_bpnn_smem(size_t bytes, int precision);
+// LJ from the build's cells, one warp per cell, neighbour cells tiled in
+// shared memory (list kind 2)
+void launch_lj_cells(const Sys &s, const LJParams &p, int precision, Mode mode, StepArgs a,
+                     const LaunchCfg &cfg, cudaStream_t st);
 // half lists: the pair pass with accumulating atomics, then the per-atom pass
 void launch_lj_half(const Sys &s, const LJParams &p, int precision, Mode mode, StepArgs a,
                     const LaunchCfg &cfg, cudaStream_t st);

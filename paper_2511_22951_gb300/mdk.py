@@ -33,6 +33,8 @@ MDK_FP64 = 0
 MDK_MIXED = 1
 MDK_LIST_FULL = 0
 MDK_LIST_HALF = 1
+MDK_LIST_CELLS = 2
+_KINDS = {"full": MDK_LIST_FULL, "half": MDK_LIST_HALF, "cells": MDK_LIST_CELLS}
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -402,16 +404,16 @@ class Context:
         _check(self.lib.mdk_set_launch(self.h, tpa, block), "mdk_set_launch")
 
     def set_list_kind(self, kind):
-        """'full' (every atom lists all its neighbours) or 'half' (each
-        pair once, Newton's third law with accumulating atomics; LJ only)."""
-        k = {"full": MDK_LIST_FULL, "half": MDK_LIST_HALF}[kind]
-        _check(self.lib.mdk_set_list_kind(self.h, k), "mdk_set_list_kind")
+        """'full' (every atom lists all its neighbours), 'half' (each pair
+        once, Newton's third law with accumulating atomics; LJ and EAM) or
+        'cells' (no list: LJ forces from the cells, one warp per cell)."""
+        _check(self.lib.mdk_set_list_kind(self.h, _KINDS[kind]), "mdk_set_list_kind")
 
     @property
     def list_kind(self):
         k = _I()
         _check(self.lib.mdk_get_list_kind(self.h, ctypes.byref(k)), "mdk_get_list_kind")
-        return "half" if k.value == MDK_LIST_HALF else "full"
+        return {v: n for n, v in _KINDS.items()}[k.value]
 
     def profile(self, enable=True):
         _check(self.lib.mdk_profile(self.h, 1 if enable else 0), "mdk_profile")

@@ -1,6 +1,7 @@
 """Half Verlet lists (each pair once, Newton's third law with accumulating
 atomics) against the oracle, through the C ABI: LJ, and the EAM passes
-(density to both atoms, embedding per atom, forces to both atoms).
+(density to both atoms, embedding per atom, forces to both atoms); and the
+list-free LJ kernel that reads the build's cells (one warp per cell).
 
 The neighbour set of Sec. "Neighbor lists" is the oracle's full set; a half
 list must hold exactly one of each mirror pair (i, j, n) / (j, i, -n).
@@ -153,10 +154,10 @@ def test_list_kind_arguments_and_autotune(mdk, ora):
     x, lo, hi = jittered_lattice(7, 4, 5.26, 0.12)
     ctx = lj_ctx(mdk, x, lo, hi, [1, 1, 1], "mixed")
     assert ctx.list_kind == "full"
-    assert ctx.lib.mdk_set_list_kind(ctx.h, 2) == mdk.MDK_ERR_BAD_ARG
+    assert ctx.lib.mdk_set_list_kind(ctx.h, 3) == mdk.MDK_ERR_BAD_ARG
     t, b, ms = ctx.autotune()
-    assert ctx.list_kind in ("full", "half") and ms > 0.0
-    if ctx.list_kind == "half":
+    assert ctx.list_kind in ("full", "half", "cells") and ms > 0.0
+    if ctx.list_kind != "full":
         assert t == 1 and b in (128, 256)
     E, F, _ = ctx.compute()
     ref = ora.lj(x, lo, hi, [1, 1, 1], W.LJ_AR.eps, W.LJ_AR.sigma, W.LJ_AR.rc, 1)
@@ -272,3 +273,93 @@ def test_half_config2_full_size_sampled(mdk, ora):
     ref = ora.sampled("lj", x, s.lo, s.hi, s.periodic, sel, lj_params=wl.lj)
     rms = np.sqrt(np.mean((F[sel] - ref["F"]) ** 2)) / np.sqrt(np.mean(ref["F"] ** 2))
     assert rms <= 1e-5, rms
+
+
+# --------------------------------------------------------------------------- cells
+def cells_ctx(mdk, *args, **kw):
+    ctx = lj_ctx(mdk, *args, **kw)
+    ctx.set_list_kind("cells")
+    assert ctx.list_kind == "cells"
+    return ctx
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_cells_lj_fp64_config0(mdk, ora, mode):
+    wl = W.config0()
+    s = wl.systems[0]
+    x = s.x + np.random.default_rng(1).normal(0, 0.1, size=s.x.shape)
+    ctx = cells_ctx(mdk, x, s.lo, s.hi, s.periodic, "fp64", mode=mode)
+    E, F, Wv = ctx.compute()
+    ref = ora.lj(x, s.lo, s.hi, s.periodic, wl.lj.eps, wl.lj.sigma, wl.lj.rc, mode)
+    assert_fp64(E[0], F, Wv[0], ref)
+    with pytest.raises(mdk.MDKError):
+        ctx.neighbors()
+
+
+@pytest.mark.parametrize("box", BOXES)
+def test_cells_lj_fp64_boxes(mdk, ora, box):
+    """Random gases in the list tests' boxes: several cells, one cell per
+    dimension (own images), two cells, a free dimension, a cluster, a
+    ragged tail; dense enough for cells of more than 32 atoms."""
+    lo, L, per, n, rns = box
+    lo = np.array(lo)
+    hi = lo + np.array(L)
+    rng = np.random.default_rng(n + 1)
+    x = lo + rng.uniform(0, 1, size=(n, 3)) * (hi - lo)
+    rc = rns - 0.3
+    ctx = cells_ctx(mdk, x, lo, hi, per, "fp64", rc=rc, mode=2)
+    E, F, Wv = ctx.compute()
+    ref = ora.lj(x, lo, hi, per, W.LJ_AR.eps, W.LJ_AR.sigma, rc, 2)
+    assert_fp64(E[0], F, Wv[0], ref)
+    U, Wa = ctx.per_atom()
+    ra = ora.lj(x, lo, hi, per, W.LJ_AR.eps, W.LJ_AR.sigma, rc, 2, per_atom=True)
+    np.testing.assert_allclose(U, ra["Ea"], rtol=1e-11, atol=1e-12 * np.abs(ra["Ea"]).max())
+
+
+@pytest.mark.parametrize("n,seed", [(3, 5), (9, 7)])
+def test_cells_lj_mixed(mdk, ora, n, seed):
+    x, lo, hi = jittered_lattice(seed, n, 5.26, 0.15)
+    ctx = cells_ctx(mdk, x, lo, hi, [1, 1, 1], "mixed")
+    E, F, _ = ctx.compute()
+    ref = ora.lj(x, lo, hi, [1, 1, 1], W.LJ_AR.eps, W.LJ_AR.sigma, W.LJ_AR.rc, 1)
+    assert_mixed(E[0], F, ref)
+
+
+def test_cells_trajectory_fp64_and_graphs(mdk, ora):
+    wl = W.config0()
+    s = wl.systems[0]
+    ctx = mdk.make_context(wl)
+    ctx.set_list_kind("cells")
+    ctx.step(wl.dt, 10)
+    x, v = ctx.get_state()
+    o = ora.md_run(s.x, s.v, s.masses, s.lo, s.hi, s.periodic, wl.dt, 10, wl.skin,
+                   lj_params=wl.lj)
+    L = s.hi - s.lo
+    d = x - o["x"]
+    d -= np.rint(d / L) * L
+    assert np.max(np.abs(d)) < 1e-10
+    np.testing.assert_allclose(v, o["v"], rtol=0, atol=1e-11)
+    outs = []
+    for graphs in (True, False):
+        c = mdk.make_context(wl, precision="mixed")
+        c.set_list_kind("cells")
+        c.set_graphs(graphs)
+        c.set_thermo(5, 256)
+        c.step(wl.dt, 200)
+        outs.append(c.get_state() + (c.thermo(),))
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
+    th = outs[0][2][:, 0, :]
+    etot = th[:, 1] + th[:, 2]
+    assert np.max(np.abs(etot - etot[0])) / s.n < 5e-5
+
+
+def test_cells_kind_rules(mdk):
+    x, lo, hi = jittered_lattice(7, 3, 5.26, 0.1)
+    ctx = lj_ctx(mdk, x, lo, hi, [1, 1, 1], "mixed")
+    ctx.set_list_kind("cells")
+    tab = W.tabulate_fs_eam(W.CU_LIKE)
+    ctx.set_potential_eam(tab)          # EAM takes full lists again
+    assert ctx.list_kind == "full"
+    with pytest.raises(mdk.MDKError):
+        ctx.set_list_kind("cells")

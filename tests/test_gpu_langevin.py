@@ -45,7 +45,7 @@ def lj_ctx(mdk, s, prec, kind="full"):
     return ctx
 
 
-@pytest.mark.parametrize("kind", ["full", "half"])
+@pytest.mark.parametrize("kind", ["full", "half", "cells"])
 def test_langevin_trajectory_matches_oracle(mdk, ora, kind):
     wl = W.config0()
     s = wl.systems[0]
@@ -206,7 +206,7 @@ def test_stationary_search_workflow_runs(mdk):
     assert all(np.isfinite(q) for q in slopes.values())
 
 
-@pytest.mark.parametrize("kind", ["full", "half"])
+@pytest.mark.parametrize("kind", ["full", "half", "cells"])
 def test_replica_thermostats_match_oracle(mdk, ora, kind):
     """Per-replica thermostats (mdk_set_langevin_replicas): every replica of
     a batch at its own T and beta; FP64 trajectories equal the oracle's run of
