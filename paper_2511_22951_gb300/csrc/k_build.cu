@@ -478,6 +478,9 @@ __device__ __forceinline__ bool half_keep(int i, int j, bool s_pos) {
   return (i < j) == (((i ^ j) & 1) == 0);
 }
 
+// HALF: the list kind is a template parameter, so a full list's candidate
+// loop carries no half-list test
+template <bool HALF>
 __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
   __shared__ uint32_t stage[2 * kGroup][kBlk];
   if (!flag_on(s) || s.half == 2) return;  // 2: forces straight from the cells, no list
@@ -486,7 +489,7 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
   const float lo_thr = s.filt_lo, hi_thr = s.filt_hi;
   const double rns2 = s.rns2;
   const int ngroups = s.nmax / kGroup;
-  const bool half = s.half == 1;
+  constexpr bool half = HALF;
   const int tx = threadIdx.x;
   for (int i = blockIdx.x * kBlk + tx; i < N; i += gridDim.x * kBlk) {
     const float4 pi = __ldg(s.pf + i);
@@ -616,7 +619,7 @@ int launch_rebuild_body(const Sys &s, int target_pg, int precision, int from_gra
   static int g_atom = 0, g_build = 0, g_cells = 0;
   if (g_atom == 0) {
     g_atom = persistent_blocks((const void *)k_bin, kBlk, 0);
-    g_build = persistent_blocks((const void *)k_build, kBlk, 0);
+    g_build = persistent_blocks((const void *)k_build<false>, kBlk, 0);
     g_cells = persistent_blocks((const void *)k_cell_sort, kBlk, 0);
   }
   const int gN = std::min(g_atom, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
@@ -639,7 +642,10 @@ int launch_rebuild_body(const Sys &s, int target_pg, int precision, int from_gra
     k_permute<Mixed><<<gN, kBlk, 0, st>>>(s, (float4 *)s.pg[target_pg]);
   k_copyback<<<gN, kBlk, 0, st>>>(s);
   if (s.win_on) k_win_trim<<<1, 32, 0, st>>>(s);
-  k_build<<<gB, kBlk, 0, st>>>(s);
+  if (s.half == 1)
+    k_build<true><<<gB, kBlk, 0, st>>>(s);
+  else
+    k_build<false><<<gB, kBlk, 0, st>>>(s);
   k_finish<<<1, 32, 0, st>>>(s, from_graph);
   return rebuild_chain_kernels(s) - 1;
 }
