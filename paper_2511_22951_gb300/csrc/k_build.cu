@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "mdk_internal.cuh"
 
@@ -525,18 +526,20 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
       // half lists: an image of i itself is kept for the lexicographically
       // positive stencil offset only (its mirror has the negative one)
       const bool s_pos = sz > 0 || (sz == 0 && (sy > 0 || (sy == 0 && sx > 0)));
-      for (int j0 = a; j0 < b; j0 += 4) {
+      // blocks of four candidates; FULL: all four inside the cell's range
+      auto block4 = [&](const int j0, auto full) {
+        constexpr bool FULL = decltype(full)::value;
         const int before = count;
         float4 pj[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) pj[u] = __ldg(s.pf + min(j0 + u, b - 1));
+        for (int u = 0; u < 4; ++u) pj[u] = __ldg(s.pf + (FULL ? j0 + u : min(j0 + u, b - 1)));
         bool band = false;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int j = j0 + u;
           const float dx = pj[u].x - qx, dy = pj[u].y - qy, dz = pj[u].z - qz;
           const float r2f = dx * dx + dy * dy + dz * dz;
-          const bool ok = j < b && j != self && (!half || half_keep(i, j, s_pos));
+          const bool ok = (FULL || j < b) && j != self && (!half || half_keep(i, j, s_pos));
           const bool acc = ok && r2f < lo_thr;
           band = band || (ok && !acc && !(r2f > hi_thr));
           stage[count & 15][tx] = code | (uint32_t)j;  // kept only if accepted
@@ -550,7 +553,7 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
             const int j = j0 + u;
             const float dx = pj[u].x - qx, dy = pj[u].y - qy, dz = pj[u].z - qz;
             const float r2f = dx * dx + dy * dy + dz * dz;
-            const bool ok = j < b && j != self && (!half || half_keep(i, j, s_pos));
+            const bool ok = (FULL || j < b) && j != self && (!half || half_keep(i, j, s_pos));
             bool acc = ok && r2f < lo_thr;
             if (ok && !acc && !(r2f > hi_thr))
               acc = exact_pair(s, g, i, code | (uint32_t)j, c0, c1, c2, rns2);
@@ -560,7 +563,10 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
         }
         // a group of 8 completed in this block: write it out
         if ((before >> 3) != (count >> 3)) flush(before >> 3, kGroup);
-      }
+      };
+      int j0 = a;
+      for (; j0 + 4 <= b; j0 += 4) block4(j0, std::true_type());
+      if (j0 < b) block4(j0, std::false_type());
     }
     if (count & 7) flush(count >> 3, count & 7);
     s.nnbr[i] = count;
