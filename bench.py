@@ -88,7 +88,9 @@ def algorithmic_bytes_per_atom(wl, prec, n_list, kind="full"):
     """Bytes one force pass with the velocity-Verlet update must move per
     atom (n_list: mean entries of the list in use).  LJ, full lists (one
     kernel): own gather-copy element, list entries and count, x and v read +
-    write, x_ref and cell word read, next gather-copy element written.  LJ,
+    write, the reference of the displacement test (the build-time FP32
+    offset in the mixed path, x_ref in FP64) and the cell word read, next
+    gather-copy element written.  LJ,
     half lists: the same with half the entries, plus the per-atom force
     accumulators written and read once (the pair pass and the per-atom pass
     that finishes the step).  EAM adds the density pass: its own gather-copy
@@ -96,7 +98,8 @@ def algorithmic_bytes_per_atom(wl, prec, n_list, kind="full"):
     read back.  Neighbour positions are assumed to come from cache (spatial
     order)."""
     g = 16 if prec == "mixed" else 32
-    lj = g + 4 * n_list + 4 + 48 + 48 + 24 + 4 + g
+    ref = 16 if prec == "mixed" else 24   # build-time offset (float4) or x_ref (FP64)
+    lj = g + 4 * n_list + 4 + 48 + 48 + ref + 4 + g
     if wl.potential == "lj":
         if kind == "cells":   # no list entries and no list length
             return lj - 4

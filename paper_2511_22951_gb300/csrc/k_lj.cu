@@ -87,8 +87,8 @@ __global__ void __launch_bounds__(256, 4) k_lj(Sys s, LJParams lp, StepArgs a) {
           fz.add(bz);
           bx = by = bz = 0;
         });
-    const double Fx = lanes_sum<T>(fx.get()), Fy = lanes_sum<T>(fy.get()),
-                 Fz = lanes_sum<T>(fz.get());
+    const R Fx = lanes_sum<T>(fx.getf()), Fy = lanes_sum<T>(fy.getf()),
+            Fz = lanes_sum<T>(fz.getf());
     double E = 0, W0 = 0, W1 = 0, W2 = 0, W3 = 0, W4 = 0, W5 = 0;
     if (ENERGY) {
       E = lanes_sum<T>((double)e);

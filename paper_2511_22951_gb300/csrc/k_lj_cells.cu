@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256, 4) k_lj_cells(Sys s, LJParams lp, StepArg
         s.wa[4 * Nc + i] = (double)w4;
         s.wa[5 * Nc + i] = (double)w5;
       }
-      epilogue<P, MODE, ENERGY>(s, a, i, inf, fx.get(), fy.get(), fz.get());
+      epilogue<P, MODE, ENERGY>(s, a, i, inf, fx.getf(), fy.getf(), fz.getf());
     }
   }
 }

@@ -415,8 +415,8 @@ __device__ __forceinline__ void langevin(const Sys &s, int i, uint32_t inf, doub
 }
 
 template <class P, int MODE, bool ENERGY>
-__device__ __forceinline__ void epilogue(const Sys &s, const StepArgs &a, int i, uint32_t inf,
-                                         double Fx, double Fy, double Fz) {
+__device__ __forceinline__ void epilogue64(const Sys &s, const StepArgs &a, int i, uint32_t inf,
+                                           double Fx, double Fy, double Fz) {
   const size_t Nc = s.N_cap;
   if (MODE == kForceOnly) {
     s.f[i] = Fx;
@@ -456,6 +456,136 @@ __device__ __forceinline__ void epilogue(const Sys &s, const StepArgs &a, int i,
     vz += c * Fz;
   }
   drift_publish<P>(s, a, i, inf, vx, vy, vz);
+}
+
+// The mixed path's end of a step with FP32 forces: the kick increments
+// dt/2 F/m are formed in FP32 (the forces carry FP32 precision) and added to
+// the FP64 velocities; positions advance in FP64; the next gather copy is
+// rounded from FP64 as always; the displacement since the last build is
+// measured between the new and the build-time FP32 cell offsets (the same
+// cell, both rounded from FP64: a few 1e-7 A against skin/2), except for
+// atoms flagged far, which keep the FP64 test.  This keeps GB300's slow FP64
+// pipe to the state updates themselves.
+__device__ __forceinline__ void langevin_f(const Sys &s, int i, uint32_t inf, float &Fx,
+                                           float &Fy, float &Fz) {
+  const size_t Nc = s.N_cap;
+  const int type = inf & 15u;
+  double g, sig, u[3] = {0.0, 0.0, 0.0};
+  if (s.lang_rep_on) {
+    const double *q = s.lang_rep + ((size_t)(inf >> 8) * kMaxTypes + type) * 2;
+    g = q[0];
+    sig = q[1];
+  } else {
+    const double x = s.x[i];
+    int r = -1;
+    for (int q = 0; q < s.n_lang && r < 0; ++q)
+      if (x >= s.lang_xlo[q] && x < s.lang_xhi[q]) r = q;
+    if (r < 0) return;
+    g = s.lang_g[r][type];
+    sig = s.lang_sig[r][type];
+    u[0] = s.lang_u[r][0];
+    u[1] = s.lang_u[r][1];
+    u[2] = s.lang_u[r][2];
+  }
+  unsigned long long c[4] = {(unsigned long long)s.id[i],
+                             (unsigned long long)s.st->n_steps, 0ull, 0ull};
+  philox4x64(c, s.lang_seed, 0ull);
+  const float gf = (float)g, sigf = (float)sig;
+  float *F[3] = {&Fx, &Fy, &Fz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float xi = (float)(unsigned)(c[d] >> 40) * 0x1.0p-24f;
+    const float dv = (float)(s.v[d * Nc + i] - u[d]);
+    *F[d] += gf * dv + sigf * (xi - 0.5f);
+  }
+}
+
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ void epilogue32(const Sys &s, const StepArgs &a, int i, uint32_t inf,
+                                           float Fx, float Fy, float Fz) {
+  const size_t Nc = s.N_cap;
+  if (MODE == kForceOnly) {
+    s.f[i] = Fx;
+    s.f[Nc + i] = Fy;
+    s.f[2 * Nc + i] = Fz;
+    if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(&s.st->bits, kStNonfinite);
+    return;
+  }
+  const int type = inf & 15u;
+  const bool piston = (inf & kInfoPiston) != 0;
+  if ((s.n_lang > 0 || s.lang_rep_on) && !piston) langevin_f(s, i, inf, Fx, Fy, Fz);
+  const float cf = a.hdtf * s.acc_over_mf[type];
+  const double dx = (double)(cf * Fx), dy = (double)(cf * Fy), dz = (double)(cf * Fz);
+  double vx = s.v[i], vy = s.v[Nc + i], vz = s.v[2 * Nc + i];
+  if (piston) {
+    vx = s.u_p;
+    vy = 0.0;
+    vz = 0.0;
+  } else {
+    vx += dx;
+    vy += dy;
+    vz += dz;
+  }
+  if (ENERGY) s.ka[i] = s.ke_m[type] * (vx * vx + vy * vy + vz * vz);
+  if (MODE == kFinal) {
+    s.v[i] = vx;
+    s.v[Nc + i] = vy;
+    s.v[2 * Nc + i] = vz;
+    s.f[i] = Fx;
+    s.f[Nc + i] = Fy;
+    s.f[2 * Nc + i] = Fz;
+    if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(&s.st->bits, kStNonfinite);
+    return;
+  }
+  if (!piston) {
+    vx += dx;
+    vy += dy;
+    vz += dz;
+  }
+  const double x = s.x[i] + a.dt * vx;
+  const double y = s.x[Nc + i] + a.dt * vy;
+  const double z = s.x[2 * Nc + i] + a.dt * vz;
+  s.x[i] = x;
+  s.x[Nc + i] = y;
+  s.x[2 * Nc + i] = z;
+  s.v[i] = vx;
+  s.v[Nc + i] = vy;
+  s.v[2 * Nc + i] = vz;
+  const Grid &g = s.grid[inf >> 8];
+  const uint32_t cc = s.cellc[i];
+  const float px = (float)(x - cell_center(g, 0, cell_coord(cc, 0)));
+  const float py = (float)(y - cell_center(g, 1, cell_coord(cc, 1)));
+  const float pz = (float)(z - cell_center(g, 2, cell_coord(cc, 2)));
+  bool bad, trig;
+  if (!(inf & kInfoFar)) {
+    const float4 q = s.pf[i];  // the build-time offset in the same cell
+    const float ex = px - q.x, ey = py - q.y, ez = pz - q.z;
+    const float d2 = ex * ex + ey * ey + ez * ez;
+    bad = !isfinite(d2);
+    trig = bad || d2 > s.half_skin2f;
+  } else {
+    const double ex = x - s.xref[i], ey = y - s.xref[Nc + i], ez = z - s.xref[2 * Nc + i];
+    const double d2 = ex * ex + ey * ey + ez * ez;
+    bad = !isfinite(d2);
+    trig = bad || d2 > s.half_skin2;
+  }
+  const unsigned act = __activemask();
+  const unsigned m = __ballot_sync(act, trig);
+  if (m && (threadIdx.x & 31) == (__ffs(m) - 1)) atomicOr(&s.st->rebuild, 1);
+  if (bad) atomicOr(&s.st->bits, kStNonfinite);
+  float4 *out = (float4 *)s.pg[a.cur ^ 1];
+  out[i] = make_float4(px, py, pz, __uint_as_float(inf));
+}
+
+// Finish the step of atom i from its total force: FP32 forces (the mixed
+// path's pair sums) take epilogue32, FP64 forces the FP64 state arithmetic.
+template <class P, int MODE, bool ENERGY, class F>
+__device__ __forceinline__ void epilogue(const Sys &s, const StepArgs &a, int i, uint32_t inf,
+                                         F Fx, F Fy, F Fz) {
+  if (sizeof(F) == 4)
+    epilogue32<MODE, ENERGY>(s, a, i, inf, (float)Fx, (float)Fy, (float)Fz);
+  else
+    epilogue64<P, MODE, ENERGY>(s, a, i, inf, (double)Fx, (double)Fy, (double)Fz);
 }
 
 }  // namespace pair

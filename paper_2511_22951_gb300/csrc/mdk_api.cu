@@ -298,11 +298,13 @@ void fill_sys_params(mdk_ctx *c) {
   s.filt_lo = (float)(s.rns2 * (1.0 - 1e-4));
   s.filt_hi = (float)(s.rns2 * (1.0 + 1e-4));
   s.half_skin2 = 0.25 * c->skin * c->skin;
+  s.half_skin2f = (float)s.half_skin2;
   s.rebuild_every = c->rebuild_every;
   for (int t = 0; t < kMaxTypes; ++t) {
     const double m = t < c->n_types ? c->type_mass[t] : 1.0;
     s.mass[t] = m;
     s.acc_over_m[t] = kAcc / m;
+    s.acc_over_mf[t] = (float)(kAcc / m);
     s.ke_m[t] = 0.5 * m / kAcc;
   }
   s.u_p = c->u_p;
@@ -444,7 +446,7 @@ int timed(mdk_ctx *c, std::vector<std::pair<int, int>> &log, int n_kernels, F la
 }
 
 int force_pass(mdk_ctx *c, Mode mode, int energy, double dt) {
-  StepArgs a{dt, c->cur, energy};
+  StepArgs a{dt, c->cur, energy, (float)(0.5 * dt)};
   const bool cells = c->pot == 1 && c->cfg.half == 2;
   const bool half = (c->pot == 1 || c->pot == 2) && c->cfg.half == 1;
   const int nk = c->pot == 1 ? (half ? 2 : 1) : (c->pot == 2 && half ? 4 : 2);
@@ -1261,7 +1263,7 @@ int mdk_eam_vjp(mdk_ctx *c, const double *gE, const double *gF, double *dtheta, 
   a.acc_F = c->adj_acc + 2 * e.nr;
   a.aux = c->adj_aux;
   a.out = on_device ? dtheta : c->adj_out;
-  launch_eam_rho(s, e, c->precision, StepArgs{0.0, c->cur, 0}, c->cfg, c->stream);
+  launch_eam_rho(s, e, c->precision, StepArgs{0.0, c->cur, 0, 0.0f}, c->cfg, c->stream);
   if (launch_eam_adjoint(s, e, c->precision, gF_dev, a, c->N, c->stream)) return MDK_ERR_CUDA;
   c->launches += 6;
   MDK_CK(cudaPeekAtLastError());
@@ -1316,7 +1318,7 @@ int mdk_step(mdk_ctx *c, double dt, int64_t nsteps) {
     r = force_pass(c, kForceOnly, 0, dt);
     if (r) return r;
   }
-  StepArgs a{dt, c->cur, 0};
+  StepArgs a{dt, c->cur, 0, (float)(0.5 * dt)};
   r = timed(c, c->ev_kick, 1, [&] { launch_kick_drift(s, c->precision, a, c->stream); });
   if (r) return r;
   c->cur ^= 1;

@@ -116,6 +116,8 @@ struct Sys {
   // integration
   double mass[kMaxTypes];         // m of each type (u)
   double acc_over_m[kMaxTypes];   // kAcc / m for each type
+  float acc_over_mf[kMaxTypes];   // the same in FP32 (mixed-path kicks)
+  float half_skin2f;              // (skin/2)^2 in FP32 (mixed-path displacement test)
   double ke_m[kMaxTypes];         // m / (2 kAcc): K in eV from v^2
   double u_p;                     // piston speed
   // moving window along x (off when win_on == 0)
@@ -296,6 +298,7 @@ struct Acc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double v) { s += v; }
   __device__ __forceinline__ double get() const { return s; }
+  __device__ __forceinline__ double getf() const { return s; }
 };
 template <>
 struct Acc<float> {
@@ -307,6 +310,8 @@ struct Acc<float> {
     s = t;
   }
   __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+  // the compensated sum rounded to FP32 (the pair terms are FP32)
+  __device__ __forceinline__ float getf() const { return s - c; }
 };
 
 // launch helpers implemented in the .cu files --------------------------------
@@ -316,6 +321,7 @@ struct StepArgs {
   double dt;
   int cur;              // gather copy read this step (pg[cur]); pg[cur^1] written
   int energy;           // compute per-atom energies / virials this step
+  float hdtf;           // dt / 2 in FP32 (mixed-path kicks)
 };
 
 void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, cudaStream_t st);

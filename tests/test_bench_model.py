@@ -13,13 +13,14 @@ from paper_2511_22951_gb300 import workloads as W  # noqa: E402
 
 def test_algorithmic_bytes_per_atom():
     lj = W.config2(n=4)
-    # own record 16 + list 4 n + count 4 + x, v read and written 96 + x_ref 24 + cell 4 + next 16
-    assert bench.algorithmic_bytes_per_atom(lj, "mixed", 78.0, "full") == 472
-    assert bench.algorithmic_bytes_per_atom(lj, "mixed", 39.0, "half") == 472 - 156 + 48
-    assert bench.algorithmic_bytes_per_atom(lj, "mixed", 0.0, "cells") == 156
-    assert bench.algorithmic_bytes_per_atom(lj, "fp64", 78.0, "full") == 472 + 32
+    # own record 16 + list 4 n + count 4 + x, v read and written 96 + build-time offset 16
+    # (mixed; x_ref 24 in FP64) + cell 4 + next 16
+    assert bench.algorithmic_bytes_per_atom(lj, "mixed", 78.0, "full") == 464
+    assert bench.algorithmic_bytes_per_atom(lj, "mixed", 39.0, "half") == 464 - 156 + 48
+    assert bench.algorithmic_bytes_per_atom(lj, "mixed", 0.0, "cells") == 148
+    assert bench.algorithmic_bytes_per_atom(lj, "fp64", 78.0, "full") == 464 + 8 + 32
     eam = W.config3(ncx=4, ncyz=2)
-    assert bench.algorithmic_bytes_per_atom(eam, "mixed", 54.0, "full") == 196 + 8 * 54
+    assert bench.algorithmic_bytes_per_atom(eam, "mixed", 54.0, "full") == 188 + 8 * 54
 
 
 def test_bpnn_flops_per_atom():
