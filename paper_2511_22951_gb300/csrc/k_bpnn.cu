@@ -126,6 +126,55 @@ __device__ __forceinline__ void ipow2(R x, R y, int e, R &rx, R &ry) {
   }
 }
 
+// Powers of the angular term per zeta group: x = 1 + c, y = 1 - c.  ZS = 1
+// is the zeta set {1, 2, 4, 16} (zeta group z holds zeta = 1, 2, 4, 16): the
+// powers come from one ladder of squares; ZS = 0 takes any integer zeta.
+// The 2^(1 - zeta) factors are applied outside the pair loops (descriptor
+// sums and reverse-pass weights), a power-of-two scaling, so exact.
+// x^zeta, y^zeta (descriptor pass)
+template <class R, int ZS>
+__device__ __forceinline__ void zeta_pow(const BPParams &bp, R x, R y, R px[kBpZ], R py[kBpZ]) {
+  if (ZS == 1) {
+    const R x2 = x * x, x4 = x2 * x2, x8 = x4 * x4;
+    const R y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
+    px[0] = x;
+    py[0] = y;
+    px[1] = x2;
+    py[1] = y2;
+    px[2] = x4;
+    py[2] = y4;
+    px[3] = x8 * x8;
+    py[3] = y8 * y8;
+  } else {
+#pragma unroll
+    for (int z = 0; z < kBpZ; ++z) {
+      ipow2<R>(x, y, bp.z_pow[z], px[z], py[z]);
+      px[z] *= x;
+      py[z] *= y;
+    }
+  }
+}
+// x^(zeta - 1), y^(zeta - 1) (reverse pass: A = x^(zeta-1) x, dA/dc = zeta x^(zeta-1))
+template <class R, int ZS>
+__device__ __forceinline__ void zeta_pow_m1(const BPParams &bp, R x, R y, R px[kBpZ],
+                                            R py[kBpZ]) {
+  if (ZS == 1) {
+    const R x2 = x * x, x4 = x2 * x2, x8 = x4 * x4;
+    const R y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
+    px[0] = R(1);
+    py[0] = R(1);
+    px[1] = x;
+    py[1] = y;
+    px[2] = x2 * x;
+    py[2] = y2 * y;
+    px[3] = (x8 * x4) * (x2 * x);
+    py[3] = (y8 * y4) * (y2 * y);
+  } else {
+#pragma unroll
+    for (int z = 0; z < kBpZ; ++z) ipow2<R>(x, y, bp.z_pow[z], px[z], py[z]);
+  }
+}
+
 template <class R>
 __device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
@@ -217,9 +266,10 @@ constexpr int bp_blocks() {
 }
 
 // NY: the (eta, kind) groups the kernel is compiled for (nY rounded up to an
-// even number); the padded groups carry zero exponentials, zeta groups past
-// nZ zero coefficients, so the pair loops run without per-group guards.
-template <class P, bool ENERGY, int NY>
+// even number); the padded groups carry zero exponentials, and slots without
+// a function zero weights, so the pair loops run without per-group guards.
+// ZS: the zeta set (zeta_pow).
+template <class P, bool ENERGY, int NY, int ZS>
 __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
     k_bpnn(Sys s, BPParams bp, StepArgs a) {
   using GP = G<P>;
@@ -345,15 +395,9 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
           Y[p] = near ? Y[p] * BM<R>::ex(-pick<R>(bp.y_eta[p], bp.y_etaf[p]) * rab2) * fab
                       : R(0);
       }
-      // 2^(1 - zeta) (1 +- c)^zeta per zeta group
+      // (1 +- c)^zeta per zeta group (the factor 2^(1 - zeta) is applied to the sums)
       R Pp[kBpZ], Pm[kBpZ];
-#pragma unroll
-      for (int z = 0; z < kBpZ; ++z) {  // zeta groups past nZ have coefficient 0
-        const R cf = pick<R>(bp.z_coef[z], bp.z_coeff[z]);
-        ipow2<R>(R(1) + c, R(1) - c, bp.z_pow[z], Pp[z], Pm[z]);
-        Pp[z] *= cf * (R(1) + c);
-        Pm[z] *= cf * (R(1) - c);
-      }
+      zeta_pow<R, ZS>(bp, R(1) + c, R(1) - c, Pp, Pm);
       // every slot of the used groups (a slot without a function has zero
       // weights, so its sum is never read)
 #pragma unroll
@@ -376,7 +420,9 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
     if (m < nr) accr[m] = warp_sum(accr[m]);
 #pragma unroll
   for (int m = 0; m < NS; ++m)
-    if ((used >> m) & 1ull) acca[m] = warp_sum(acca[m]);
+    if ((used >> m) & 1ull)
+      acca[m] = warp_sum(acca[m]) *
+                pick<R>(bp.z_coef[(m >> 1) % kBpZ], bp.z_coeff[(m >> 1) % kBpZ]);
   if (lane == 0) {
 #pragma unroll
     for (int m = 0; m < kBpRad; ++m) sl.G[m] = m < nr ? accr[m] : R(0);
@@ -415,7 +461,10 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
     R t = 0;
     for (int q = 0; q < H1; ++q) t += W01[m * H1 + q] * sl.d1[q];
     sl.dG[m] = t;
-    if (m >= kBpRad) sl.wc[m - kBpRad] = t;
+    if (m >= kBpRad) {
+      const int z = ((m - kBpRad) >> 1) % kBpZ;
+      sl.wc[m - kBpRad] = t * pick<R>(bp.z_coef[z], bp.z_coeff[z]);
+    }
   }
   __syncwarp();
 
@@ -440,16 +489,14 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
         dfab = half_pi_rc * sn;
         irab = BM<R>::rcp(rab);
       }
-      // per zeta group: A = 2^(1-zeta) (1 +- c)^zeta and dA/dc
+      // per zeta group: A = (1 +- c)^zeta and dA/dc (2^(1 - zeta) is in the weights)
       R Ap[kBpZ], Am[kBpZ], dAp[kBpZ], dAm[kBpZ];
+      R Qp[kBpZ], Qm[kBpZ];
+      zeta_pow_m1<R, ZS>(bp, R(1) + c, R(1) - c, Qp, Qm);
 #pragma unroll
-      for (int z = 0; z < kBpZ; ++z) {  // zeta groups past nZ have coefficient 0
-        const R cf = pick<R>(bp.z_coef[z], bp.z_coeff[z]);
+      for (int z = 0; z < kBpZ; ++z) {
         const R zt = pick<R>(bp.z_zeta[z], bp.z_zetaf[z]);
-        R pp, pm;
-        ipow2<R>(R(1) + c, R(1) - c, bp.z_pow[z], pp, pm);
-        pp *= cf;
-        pm *= cf;
+        const R pp = Qp[z], pm = Qm[z];
         Ap[z] = pp * (R(1) + c);
         Am[z] = pm * (R(1) - c);
         dAp[z] = zt * pp;
@@ -613,13 +660,19 @@ size_t bpnn_smem_bytes(const BPParams &p, int precision, int nmax, int *warps) {
 }
 
 namespace {
-template <class P, int NY>
-cudaError_t smem_attr_ny(int b) {
-  cudaError_t e = cudaFuncSetAttribute(k_bpnn<P, true, NY>,
+template <class P, int NY, int ZS>
+cudaError_t smem_attr_one(int b) {
+  cudaError_t e = cudaFuncSetAttribute(k_bpnn<P, true, NY, ZS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_bpnn<P, false, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             b);
+    e = cudaFuncSetAttribute(k_bpnn<P, false, NY, ZS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  return e;
+}
+template <class P, int NY>
+cudaError_t smem_attr_ny(int b) {
+  cudaError_t e = smem_attr_one<P, NY, 0>(b);
+  if (e == cudaSuccess) e = smem_attr_one<P, NY, 1>(b);
   return e;
 }
 template <class P>
@@ -630,15 +683,23 @@ cudaError_t smem_attr(int b) {
   if (e == cudaSuccess) e = smem_attr_ny<P, 8>(b);
   return e;
 }
+template <class P, bool EN, int ZS>
+void go_ny(const Sys &s, const BPParams &p, StepArgs a, int grid, int threads, size_t sm,
+           cudaStream_t st) {
+  switch (ny_compiled(p.nY)) {
+    case 2: k_bpnn<P, EN, 2, ZS><<<grid, threads, sm, st>>>(s, p, a); break;
+    case 4: k_bpnn<P, EN, 4, ZS><<<grid, threads, sm, st>>>(s, p, a); break;
+    case 6: k_bpnn<P, EN, 6, ZS><<<grid, threads, sm, st>>>(s, p, a); break;
+    default: k_bpnn<P, EN, 8, ZS><<<grid, threads, sm, st>>>(s, p, a); break;
+  }
+}
 template <class P, bool EN>
 void go(const Sys &s, const BPParams &p, StepArgs a, int grid, int threads, size_t sm,
         cudaStream_t st) {
-  switch (ny_compiled(p.nY)) {
-    case 2: k_bpnn<P, EN, 2><<<grid, threads, sm, st>>>(s, p, a); break;
-    case 4: k_bpnn<P, EN, 4><<<grid, threads, sm, st>>>(s, p, a); break;
-    case 6: k_bpnn<P, EN, 6><<<grid, threads, sm, st>>>(s, p, a); break;
-    default: k_bpnn<P, EN, 8><<<grid, threads, sm, st>>>(s, p, a); break;
-  }
+  if (p.zset == 1)
+    go_ny<P, EN, 1>(s, p, a, grid, threads, sm, st);
+  else
+    go_ny<P, EN, 0>(s, p, a, grid, threads, sm, st);
 }
 }  // namespace
 

@@ -863,7 +863,27 @@ int mdk_set_potential_bpnn(mdk_ctx *c, double rc, int n_rad, const int *rad_kind
     p.rad_p0f[m] = (float)p0;
     p.rad_p1f[m] = (float)p1;
   }
-  // angular functions onto the slot grid
+  // angular functions onto the slot grid.  When every zeta is 1, 2, 4 or 16
+  // the zeta groups are those four, in that order (the kernel's compiled
+  // power ladder); otherwise groups are numbered in order of appearance.
+  static const double kZetaSet[kBpZ] = {1.0, 2.0, 4.0, 16.0};
+  p.zset = 1;
+  for (int m = 0; m < n_ang; ++m) {
+    const double zeta = ang_par[3 * m];
+    bool in = false;
+    for (int q = 0; q < kBpZ; ++q) in = in || zeta == kZetaSet[q];
+    if (!in) p.zset = 0;
+  }
+  if (p.zset == 1) {
+    p.nZ = kBpZ;
+    for (int q = 0; q < kBpZ; ++q) {
+      p.z_zeta[q] = kZetaSet[q];
+      p.z_zetaf[q] = (float)kZetaSet[q];
+      p.z_pow[q] = (int)kZetaSet[q] - 1;
+      p.z_coef[q] = ldexp(1.0, 1 - (int)kZetaSet[q]);
+      p.z_coeff[q] = (float)p.z_coef[q];
+    }
+  }
   std::vector<int> slot_of((size_t)n_ang);
   for (int m = 0; m < n_ang; ++m) {
     const int k = ang_kind[m];

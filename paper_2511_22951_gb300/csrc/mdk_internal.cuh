@@ -214,6 +214,8 @@ struct BPParams {
   double y_eta[kBpY];
   float y_etaf[kBpY];
   int y_kind[kBpY];                        // 4: with the R_jk factors, 5: without
+  int zset;                                // 1: the zetas are among {1, 2, 4, 16}, group z
+                                           // holding zeta = 1, 2, 4, 16; 0: any integers
   int z_pow[kBpZ];                         // zeta - 1 (a non-negative integer)
   double z_zeta[kBpZ], z_coef[kBpZ];       // zeta, 2^(1 - zeta)
   float z_zetaf[kBpZ], z_coeff[kBpZ];

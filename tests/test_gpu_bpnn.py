@@ -98,6 +98,41 @@ def test_fp64_all_kinds_small_box_and_cluster(mdk, ora):
     assert_fp64(E[0], F, Wv[0], ref)
 
 
+# zetas outside {1, 2, 4, 16}: the kernel's generic power loop (the set itself
+# takes the compiled ladder of squares)
+GENERIC_ZETA = dict(rad=[(2, 0.05, 0.0), (3, 0.9, 0.0)],
+                    ang=[(4, 3.0, 1.0, 0.01), (4, 8.0, -1.0, 0.005), (4, 1.0, 1.0, 0.02),
+                         (5, 3.0, -1.0, 0.01), (5, 64.0, 1.0, 0.03), (4, 8.0, 1.0, 0.01)],
+                    H=(6, 5), w_in=0.3)
+
+
+@pytest.mark.parametrize("spec", ["fixed_set", "generic"])
+def test_fp64_zeta_paths(mdk, ora, spec):
+    """Both ways of forming (1 +- cos)^zeta: the zeta set {1, 2, 4, 16} (all
+    four, both lambdas) and zetas 1, 3, 8, 64."""
+    if spec == "generic":
+        m = small_model(**GENERIC_ZETA, rc=4.2, seed=41)
+    else:
+        ang = [(k, z, lam, 0.004 * (1 + q)) for q, (k, z, lam) in enumerate(
+            [(4, 1.0, 1.0), (4, 2.0, -1.0), (4, 4.0, 1.0), (4, 16.0, -1.0),
+             (5, 16.0, 1.0), (5, 4.0, -1.0), (5, 2.0, 1.0), (5, 1.0, -1.0)])]
+        m = small_model(rad=[(2, 0.1, 0.0)], ang=ang, H=(6, 5), w_in=0.3, rc=4.2, seed=42)
+    x, lo, hi = al_box(43, n=2, sigma=0.15)
+    ctx = bp_ctx(mdk, x, lo, hi, [1, 1, 1], "fp64", m)
+    E, F, Wv = ctx.compute()
+    ref = ora.bpnn(x, lo, hi, [1, 1, 1], m)
+    assert_fp64(E[0], F, Wv[0], ref)
+
+
+def test_mixed_generic_zeta(mdk, ora):
+    m = small_model(**GENERIC_ZETA, rc=4.5, seed=44)
+    x, lo, hi = al_box(45, sigma=0.12)
+    ctx = bp_ctx(mdk, x, lo, hi, [1, 1, 1], "mixed", m)
+    E, F, Wv = ctx.compute()
+    ref = ora.bpnn(x, lo, hi, [1, 1, 1], m)
+    assert_mixed(E[0], F, ref)
+
+
 @pytest.mark.parametrize("seed", [3, 4])
 def test_mixed_matches_oracle(mdk, ora, seed):
     m = W.maise_like_bpnn(seed)
