@@ -182,16 +182,49 @@ __device__ __forceinline__ R warp_sum(R v) {
   return v;
 }
 
-// per-warp shared slab: fields of NB neighbour slots (SoA), then the
-// descriptor / gradient / hidden vectors
+// per-warp shared slab: per neighbour slot two 4-vectors -- (u_x, u_y, u_z,
+// R) and (1/R, f_c, f_c', 0) -- so a pair's operands come in few vector loads,
+// the gradient sums (SoA), the exponentials of the (eta, kind) groups in
+// pairs of groups ([nY/2][NB][2]); then the descriptor / gradient / hidden
+// vectors
 template <class R>
 struct Slab {
-  R *ux, *uy, *uz, *rr, *ir, *fc, *dfc, *e;  // e: [nY][NB]
-  R *gax, *gay, *gaz, *gbx, *gby, *gbz;      // gradient sums (a side, b side)
+  R *u4, *f4, *e;
+  R *gax, *gay, *gaz, *gbx, *gby, *gbz;  // gradient sums (a side, b side)
   int *j;
   R *G, *dG, *h1, *d1, *d2, *wc;  // wc: dE/dG of each angular slot
 };
-constexpr int kSlabFields = 13;   // per-neighbour reals besides e
+constexpr int kSlabFields = 14;   // per-neighbour reals besides e
+
+template <class R>
+struct Q4 {
+  R x, y, z, w;
+};
+// 4 consecutive reals (16-byte aligned for float, 32 for double)
+template <class R>
+__device__ __forceinline__ Q4<R> ld4(const R *p) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return {v.x, v.y, v.z, v.w};
+  } else {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0];
+    const double2 b = reinterpret_cast<const double2 *>(p)[1];
+    return {a.x, a.y, b.x, b.y};
+  }
+}
+// the exponentials of groups 2k and 2k + 1 at slot q
+template <class R>
+__device__ __forceinline__ void ld_e2(const R *e, int NB, int k, int q, R &e0, R &e1) {
+  if constexpr (sizeof(R) == 4) {
+    const float2 v = reinterpret_cast<const float2 *>(e + (size_t)2 * k * NB)[q];
+    e0 = v.x;
+    e1 = v.y;
+  } else {
+    const double2 v = reinterpret_cast<const double2 *>(e + (size_t)2 * k * NB)[q];
+    e0 = v.x;
+    e1 = v.y;
+  }
+}
 
 constexpr int kVec = 80;  // >= kBpIn, a multiple of 16
 static_assert(kVec >= kBpIn, "device network inputs");
@@ -200,19 +233,14 @@ template <class R>
 __device__ __forceinline__ Slab<R> slab_at(char *base, int NB, int nY) {
   Slab<R> s;
   R *p = reinterpret_cast<R *>(base);
-  s.ux = p;
-  s.uy = p + NB;
-  s.uz = p + 2 * NB;
-  s.rr = p + 3 * NB;
-  s.ir = p + 4 * NB;
-  s.fc = p + 5 * NB;
-  s.dfc = p + 6 * NB;
-  s.gax = p + 7 * NB;
-  s.gay = p + 8 * NB;
-  s.gaz = p + 9 * NB;
-  s.gbx = p + 10 * NB;
-  s.gby = p + 11 * NB;
-  s.gbz = p + 12 * NB;
+  s.u4 = p;
+  s.f4 = p + 4 * NB;
+  s.gax = p + 8 * NB;
+  s.gay = p + 9 * NB;
+  s.gaz = p + 10 * NB;
+  s.gbx = p + 11 * NB;
+  s.gby = p + 12 * NB;
+  s.gbz = p + 13 * NB;
   s.e = p + kSlabFields * NB;
   p += (size_t)(kSlabFields + nY) * NB;
   s.G = p;
@@ -331,18 +359,21 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
       const R r = BM<R>::sq(r2);
       R sn, cs;
       BM<R>::scpi(r * inv_rc, &sn, &cs);
-      sl.ux[q] = dx;
-      sl.uy[q] = dy;
-      sl.uz[q] = dz;
-      sl.rr[q] = r;
-      sl.ir[q] = BM<R>::rcp(r);
+      R *u = sl.u4 + 4 * q, *f = sl.f4 + 4 * q;
+      u[0] = dx;
+      u[1] = dy;
+      u[2] = dz;
+      u[3] = r;
+      f[0] = BM<R>::rcp(r);
+      f[1] = R(0.5) * (cs + R(1));
+      f[2] = half_pi_rc * sn;
+      f[3] = R(0);
       sl.gax[q] = sl.gay[q] = sl.gaz[q] = R(0);
       sl.gbx[q] = sl.gby[q] = sl.gbz[q] = R(0);
-      sl.fc[q] = R(0.5) * (cs + R(1));
-      sl.dfc[q] = half_pi_rc * sn;
 #pragma unroll
       for (int p = 0; p < NY; ++p)
-        sl.e[p * NB + q] = p < nY ? BM<R>::ex(-pick<R>(bp.y_eta[p], bp.y_etaf[p]) * r2) : R(0);
+        sl.e[(size_t)2 * (p >> 1) * NB + 2 * q + (p & 1)] =
+            p < nY ? BM<R>::ex(-pick<R>(bp.y_eta[p], bp.y_etaf[p]) * r2) : R(0);
       sl.j[q] = (int)j;
     }
     n += __popc(m);
@@ -354,7 +385,9 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
 #pragma unroll
   for (int m = 0; m < kBpRad; ++m) accr[m] = 0;
   for (int q = lane; q < n; q += 32) {
-    const R r = sl.rr[q], f = sl.fc[q], df = sl.dfc[q];
+    const R r = sl.u4[4 * q + 3];
+    const Q4<R> fq = ld4<R>(sl.f4 + 4 * q);
+    const R f = fq.y, df = fq.z;
 #pragma unroll
     for (int m = 0; m < kBpRad; ++m)
       if (m < nr) {
@@ -375,9 +408,11 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
     }
     for (int t = lane; t < npair; t += 32) {
       const int qb = qa + 1 + rel;
-      const R ax = sl.ux[qa], ay = sl.uy[qa], az = sl.uz[qa], ra = sl.rr[qa], fa = sl.fc[qa];
-      const R bx = sl.ux[qb], by = sl.uy[qb], bz = sl.uz[qb], rb = sl.rr[qb], fb = sl.fc[qb];
-      const R c = (ax * bx + ay * by + az * bz) * (sl.ir[qa] * sl.ir[qb]);
+      const Q4<R> ua = ld4<R>(sl.u4 + 4 * qa), ub = ld4<R>(sl.u4 + 4 * qb);
+      const Q4<R> va = ld4<R>(sl.f4 + 4 * qa), vb = ld4<R>(sl.f4 + 4 * qb);
+      const R ax = ua.x, ay = ua.y, az = ua.z, fa = va.y;
+      const R bx = ub.x, by = ub.y, bz = ub.z, fb = vb.y;
+      const R c = (ax * bx + ay * by + az * bz) * (va.x * vb.x);
       const R sx = bx - ax, sy = by - ay, sz = bz - az;
       const R rab2 = sx * sx + sy * sy + sz * sz;
       const bool near = bp.any4 && rab2 < rc2;
@@ -389,8 +424,17 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
       }
       R Y[NY];
 #pragma unroll
+      for (int p = 0; p < NY; p += 2) {
+        R ea0, ea1, eb0, eb1;
+        ld_e2<R>(sl.e, NB, p >> 1, qa, ea0, ea1);
+        ld_e2<R>(sl.e, NB, p >> 1, qb, eb0, eb1);
+        Y[p] = ea0 * eb0;
+        Y[p + 1] = ea1 * eb1;
+      }
+      const R fab2 = fa * fb;
+#pragma unroll
       for (int p = 0; p < NY; ++p) {
-        Y[p] = sl.e[p * NB + qa] * sl.e[p * NB + qb] * fa * fb;
+        Y[p] *= fab2;
         if (bp.y_kind[p] == 4)
           Y[p] = near ? Y[p] * BM<R>::ex(-pick<R>(bp.y_eta[p], bp.y_etaf[p]) * rab2) * fab
                       : R(0);
@@ -471,10 +515,12 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
   // ---- 4. gradients with respect to the neighbours ------------------------
   {
     auto grad_pair = [&](const int qa, const int qb) {
-      const R ax = sl.ux[qa], ay = sl.uy[qa], az = sl.uz[qa], ra = sl.rr[qa];
-      const R bx = sl.ux[qb], by = sl.uy[qb], bz = sl.uz[qb], rb = sl.rr[qb];
-      const R ia = sl.ir[qa], ib = sl.ir[qb];
-      const R fa = sl.fc[qa], dfa = sl.dfc[qa], fb = sl.fc[qb], dfb = sl.dfc[qb];
+      const Q4<R> ua = ld4<R>(sl.u4 + 4 * qa), ub = ld4<R>(sl.u4 + 4 * qb);
+      const Q4<R> va = ld4<R>(sl.f4 + 4 * qa), vb = ld4<R>(sl.f4 + 4 * qb);
+      const R ax = ua.x, ay = ua.y, az = ua.z, ra = ua.w;
+      const R bx = ub.x, by = ub.y, bz = ub.z, rb = ub.w;
+      const R ia = va.x, ib = vb.x;
+      const R fa = va.y, dfa = va.z, fb = vb.y, dfb = vb.z;
       const R iab = ia * ib;
       const R c = (ax * bx + ay * by + az * bz) * iab;
       const R sx = bx - ax, sy = by - ay, sz = bz - az;
@@ -505,6 +551,12 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
       // per (eta, kind) group: the functions' weighted sums S2 = sum w A,
       // S1 = sum w dA/dc, times the group's factor Y and its derivatives
       R al = 0, bu = 0, bw = 0, gs = 0;
+      R ea[NY], eb[NY];
+#pragma unroll
+      for (int p = 0; p < NY; p += 2) {
+        ld_e2<R>(sl.e, NB, p >> 1, qa, ea[p], ea[p + 1]);
+        ld_e2<R>(sl.e, NB, p >> 1, qb, eb[p], eb[p + 1]);
+      }
 #pragma unroll
       for (int p = 0; p < NY; ++p) {  // padded groups: zero exponentials and weights
         R S1 = 0, S2 = 0;
@@ -516,7 +568,7 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
           S1 += wv[2 * z] * dAp[z] + wv[2 * z + 1] * dAm[z];
         }
         const R eta = pick<R>(bp.y_eta[p], bp.y_etaf[p]);
-        const R E2 = sl.e[p * NB + qa] * sl.e[p * NB + qb];
+        const R E2 = ea[p] * eb[p];
         R X = R(1), fX = R(1);
         const bool k4 = bp.y_kind[p] == 4;
         if (k4) {
@@ -580,8 +632,9 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
   bool bad = false;
   long long *acc = s.hacc;
   for (int qa = lane; qa < n; qa += 32) {
-    const R ax = sl.ux[qa], ay = sl.uy[qa], az = sl.uz[qa], ra = sl.rr[qa];
-    const R fa = sl.fc[qa], dfa = sl.dfc[qa];
+    const Q4<R> ua = ld4<R>(sl.u4 + 4 * qa), va = ld4<R>(sl.f4 + 4 * qa);
+    const R ax = ua.x, ay = ua.y, az = ua.z, ra = ua.w;
+    const R fa = va.y, dfa = va.z;
     R sr = 0;
 #pragma unroll
     for (int m = 0; m < kBpRad; ++m)
@@ -590,7 +643,7 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
         radial<R>(bp, m, ra, fa, dfa, v, d);
         sr += sl.dG[m] * d;
       }
-    sr *= sl.ir[qa];
+    sr *= va.x;
     const R gx = sr * ax + sl.gax[qa] + sl.gbx[qa];
     const R gy = sr * ay + sl.gay[qa] + sl.gby[qa];
     const R gz = sr * az + sl.gaz[qa] + sl.gbz[qa];
