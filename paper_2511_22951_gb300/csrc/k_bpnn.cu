@@ -550,6 +550,12 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
       }
       // per (eta, kind) group: the functions' weighted sums S2 = sum w A,
       // S1 = sum w dA/dc, times the group's factor Y and its derivatives
+      // the pair-level factors are taken out of the group sums:
+      //   al = f_a f_b sum_p S1 E2 X f_ab,   bu = f_b / R_a sum_p S2 E2 X f_ab (f_a' - 2 eta R_a f_a),
+      //   bw = f_a / R_b sum_p S2 E2 X f_ab (f_b' - 2 eta R_b f_b),
+      //   gs = f_a f_b / R_ab sum_(G4 groups) S2 E2 X (f_ab' - 2 eta R_ab f_ab)
+      // with E2 = exp(-eta (R_a^2 + R_b^2)), X = exp(-eta R_ab^2) and f_ab the R_ab
+      // cutoff for G4 groups (0 beyond R_c), X = f_ab = 1 for G5 groups
       R al = 0, bu = 0, bw = 0, gs = 0;
       R ea[NY], eb[NY];
 #pragma unroll
@@ -557,6 +563,7 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
         ld_e2<R>(sl.e, NB, p >> 1, qa, ea[p], ea[p + 1]);
         ld_e2<R>(sl.e, NB, p >> 1, qb, eb[p], eb[p + 1]);
       }
+      const R rfa = ra * fa, rfb = rb * fb, rfab = rab * fab;
 #pragma unroll
       for (int p = 0; p < NY; ++p) {  // padded groups: zero exponentials and weights
         R S1 = 0, S2 = 0;
@@ -567,20 +574,24 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
           S2 += wv[2 * z] * Ap[z] + wv[2 * z + 1] * Am[z];
           S1 += wv[2 * z] * dAp[z] + wv[2 * z + 1] * dAm[z];
         }
-        const R eta = pick<R>(bp.y_eta[p], bp.y_etaf[p]);
-        const R E2 = ea[p] * eb[p];
-        R X = R(1), fX = R(1);
+        const R m2eta = R(-2) * pick<R>(bp.y_eta[p], bp.y_etaf[p]);
+        R Ex = ea[p] * eb[p], Exf = Ex;
         const bool k4 = bp.y_kind[p] == 4;
         if (k4) {
-          X = near ? BM<R>::ex(-eta * rab2) : R(0);
-          fX = X * fab;
+          Ex = near ? Ex * BM<R>::ex(R(0.5) * m2eta * rab2) : R(0);
+          Exf = Ex * fab;
         }
-        const R Y = E2 * fa * fb * fX;
-        al += S1 * Y;
-        bu += S2 * E2 * fb * fX * (R(-2) * eta * ra * fa + dfa) * ia;
-        bw += S2 * E2 * fa * fX * (R(-2) * eta * rb * fb + dfb) * ib;
-        if (k4 && near) gs += S2 * E2 * fa * fb * X * (R(-2) * eta * rab * fab + dfab) * irab;
+        al += S1 * Exf;
+        const R T = S2 * Exf;
+        bu += T * (m2eta * rfa + dfa);
+        bw += T * (m2eta * rfb + dfb);
+        if (k4) gs += S2 * Ex * (m2eta * rfab + dfab);
       }
+      const R fab2 = fa * fb;
+      al *= fab2;
+      bu *= fb * ia;
+      bw *= fa * ib;
+      gs *= fab2 * irab;
       // dc/du_a = u_b/(R_a R_b) - c u_a/R_a^2, dc/du_b = u_a/(R_a R_b) - c u_b/R_b^2;
       // to a: dT/du_a - dT/ds, to b: dT/du_b + dT/ds
       const R ca = c * ia * ia, cb = c * ib * ib;
