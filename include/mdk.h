@@ -460,20 +460,22 @@ int mdk_lj_compute_noalloc(const double *x, int64_t N, const double box_lo[3],
 
 /*
  * Autotuner: time every launch shape of the force kernels -- threads per atom
- * in {1, 2, 4} x threads per block in {128, 256, 512} (LJ: <= 256) -- on this
- * context's system (reps force passes each, CUDA events on the context's
- * stream) and keep the fastest for later calls.  With LJ and EAM it also
- * times half lists (one thread per atom; 128 and 256 threads per block),
- * with LJ the list-free cell kernel (128 and 256 threads per block), and
- * keeps the fastest list kind (mdk_get_list_kind reports it; a switch
- * rebuilds the list).  The BPNN kernel has one shape (a warp per atom).  Outputs may be NULL.  Small systems (few atoms per SM)
+ * in {1, 2, 4, 8, 32} (32: a warp per atom) x threads per block in {128, 256,
+ * 512} (LJ: <= 256) -- on this context's system (reps force passes each, CUDA
+ * events on the context's stream) and keep the fastest for later calls.  With
+ * LJ and EAM it also times half lists (one thread per atom; 128 and 256
+ * threads per block), with LJ the list-free cell kernel (128 and 256 threads
+ * per block), and keeps the fastest list kind (mdk_get_list_kind reports it; a
+ * switch rebuilds the list).  The BPNN kernel has one shape (a warp per atom).
+ * Outputs may be NULL.  Small systems (few atoms per SM)
  * and long lists favour several threads per atom.  The state must be set;
  * the lists are built if needed.  (No paper counterpart: the paper chunks
  * arrays over a thread pool.)
  */
 int mdk_autotune(mdk_ctx *ctx, int reps, int *tpa, int *block, double *ms);
 
-/* Set the launch shape directly (tpa in {1, 2, 4}, block in {128, 256, 512}). */
+/* Set the launch shape directly: tpa (list-walking lanes per atom) in {1, 2, 4, 8, 32}
+ * (32: a warp per atom), block in {128, 256, 512}. */
 int mdk_set_launch(mdk_ctx *ctx, int tpa, int block);
 
 /*

@@ -10,9 +10,11 @@
 // stage their spline tables in shared memory once per block and run on a
 // persistent grid (one or two blocks per SM), so a table is read from L2 a
 // few hundred times per launch, not once per atom tile.  T lanes own one atom
-// (autotuned), as in the LJ kernel.  The tables take 80 KB of shared memory
-// per block (5000 knots), so residency comes from large blocks: at most 64
-// registers per thread lets two 512-thread blocks (32 warps) share an SM.
+// (autotuned), as in the LJ kernel.  The mixed tables take 80 KB of shared
+// memory per block (5000 knots), so residency comes from large blocks: at most
+// 64 registers per thread lets two 512-thread blocks (32 warps) share an SM.
+// The FP64 force-pass tables take 160 KB (one block per SM), so the FP64
+// passes take up to 128 registers (no spills of the FP64 pair values).
 #include "k_pair.cuh"
 
 namespace mdk {
@@ -20,8 +22,16 @@ namespace {
 
 using namespace pair;
 
+// FP64 passes: one 512-thread block per SM and up to 128 registers (the FP64
+// pair values need them; the 160 KB FP64 force-pass tables leave room for one
+// block anyway)
+template <class P>
+constexpr int eam_min_blocks() {
+  return sizeof(typename G<P>::R) == 4 ? 2 : 1;
+}
+
 template <class P, bool ENERGY, int T>
-__global__ void __launch_bounds__(512, 2) k_rho(Sys s, EAMParams ep, StepArgs a) {
+__global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_rho(Sys s, EAMParams ep, StepArgs a) {
   using GP = G<P>;
   using R = typename GP::R;
   using V = typename GP::V;
@@ -87,7 +97,7 @@ __global__ void __launch_bounds__(512, 2) k_rho(Sys s, EAMParams ep, StepArgs a)
 }
 
 template <class P, int MODE, bool ENERGY, int T>
-__global__ void __launch_bounds__(512, 2) k_eam(Sys s, EAMParams ep, StepArgs a) {
+__global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_eam(Sys s, EAMParams ep, StepArgs a) {
   using GP = G<P>;
   using R = typename GP::R;
   using V = typename GP::V;
@@ -265,7 +275,11 @@ void go(const Sys &s, const EAMParams &p, StepArgs a, int block, int prec, cudaS
 template <class P, int MODE, bool EN>
 void by_tpa(const Sys &s, const EAMParams &p, StepArgs a, const LaunchCfg &c, int prec,
             cudaStream_t st) {
-  if (c.tpa == 4)
+  if (c.tpa == 32)
+    go<P, MODE, EN, 32>(s, p, a, c.block, prec, st);
+  else if (c.tpa == 8)
+    go<P, MODE, EN, 8>(s, p, a, c.block, prec, st);
+  else if (c.tpa == 4)
     go<P, MODE, EN, 4>(s, p, a, c.block, prec, st);
   else if (c.tpa == 2)
     go<P, MODE, EN, 2>(s, p, a, c.block, prec, st);
@@ -317,6 +331,8 @@ int attrs(int b1, int b2) {
   cudaError_t e = attrs_t<P, 1>(b1, b2);
   if (e == cudaSuccess) e = attrs_t<P, 2>(b1, b2);
   if (e == cudaSuccess) e = attrs_t<P, 4>(b1, b2);
+  if (e == cudaSuccess) e = attrs_t<P, 8>(b1, b2);
+  if (e == cudaSuccess) e = attrs_t<P, 32>(b1, b2);
   return e == cudaSuccess ? 0 : -1;
 }
 
@@ -350,7 +366,11 @@ void rho_only(const Sys &s, const EAMParams &p, StepArgs a, int block, int prec,
 template <class P>
 void rho_by_tpa(const Sys &s, const EAMParams &p, StepArgs a, const LaunchCfg &c, int prec,
                 cudaStream_t st) {
-  if (c.tpa == 4)
+  if (c.tpa == 32)
+    rho_only<P, 32>(s, p, a, c.block, prec, st);
+  else if (c.tpa == 8)
+    rho_only<P, 8>(s, p, a, c.block, prec, st);
+  else if (c.tpa == 4)
     rho_only<P, 4>(s, p, a, c.block, prec, st);
   else if (c.tpa == 2)
     rho_only<P, 2>(s, p, a, c.block, prec, st);

@@ -10,7 +10,8 @@
 // the next list group, loaded while the current one runs; measured on the
 // 8.4M-atom argon step this beats 48 registers with 40 warps (spills) and
 // 80 registers with 24 warps.
-// T lanes own one atom (T = 1, 2 or 4, picked by the autotuner): lane t walks
+// T lanes own one atom (T = 1, 2, 4, 8 or 32 -- a warp per atom --, picked by
+// the autotuner by density and list length): lane t walks
 // the list groups t, t + T, ... of the full Verlet list, the lanes' sums are
 // combined with shuffles in a fixed order, and lane 0 runs the epilogue
 // (store the force, or finish step n and start step n + 1).  The pair vector
@@ -24,8 +25,15 @@ namespace {
 
 using namespace pair;
 
+// mixed: 4 blocks of 256 per SM (64 registers); FP64: 2 blocks (128 registers:
+// the FP64 pair values and sums need them)
+template <class P>
+constexpr int lj_min_blocks() {
+  return sizeof(typename G<P>::R) == 4 ? 4 : 2;
+}
+
 template <class P, int MODE, bool ENERGY, int SHIFT, int T>
-__global__ void __launch_bounds__(256, 4) k_lj(Sys s, LJParams lp, StepArgs a) {
+__global__ void __launch_bounds__(256, lj_min_blocks<P>()) k_lj(Sys s, LJParams lp, StepArgs a) {
   using GP = G<P>;
   using R = typename GP::R;
   using V = typename GP::V;
@@ -125,7 +133,11 @@ void go(const Sys &s, const LJParams &p, StepArgs a, int block, cudaStream_t st)
 
 template <class P, int MODE, bool EN, int SH>
 void by_tpa(const Sys &s, const LJParams &p, StepArgs a, const LaunchCfg &c, cudaStream_t st) {
-  if (c.tpa == 4)
+  if (c.tpa == 32)
+    go<P, MODE, EN, SH, 32>(s, p, a, c.block, st);
+  else if (c.tpa == 8)
+    go<P, MODE, EN, SH, 8>(s, p, a, c.block, st);
+  else if (c.tpa == 4)
     go<P, MODE, EN, SH, 4>(s, p, a, c.block, st);
   else if (c.tpa == 2)
     go<P, MODE, EN, SH, 2>(s, p, a, c.block, st);

@@ -1484,13 +1484,13 @@ int mdk_autotune(mdk_ctx *c, int reps, int *tpa_out, int *block_out, double *ms_
   c->prof = false;
   LaunchCfg best = keep;
   float best_ms = -1.f;
-  static const int kTpa[3] = {1, 2, 4};
+  static const int kTpa[5] = {1, 2, 4, 8, 32};  // 32: a warp per atom
   static const int kBlock[3] = {128, 256, 512};
   // LJ and EAM: full lists in every shape, then half lists (one thread per
   // atom); LJ also the list-free cell kernel (one warp per cell)
   const int n_kinds = c->pot == 1 ? 3 : (c->pot == 2 ? 2 : 1);
   for (int kind = 0; kind < n_kinds && !r; ++kind)
-  for (int a = 0; a < 3 && !r; ++a)
+  for (int a = 0; a < 5 && !r; ++a)
     for (int b = 0; b < 3; ++b) {
       if (c->pot == 1 && kBlock[b] > 256) continue;  // the LJ kernels take <= 256
       if (c->pot == 3 && (a > 0 || b > 0)) continue;  // BPNN: one warp per atom, one shape
@@ -1544,7 +1544,7 @@ int mdk_set_graphs(mdk_ctx *c, int enable) {
 }
 
 int mdk_set_launch(mdk_ctx *c, int tpa, int block) {
-  if (check_ctx(c) || (tpa != 1 && tpa != 2 && tpa != 4) ||
+  if (check_ctx(c) || (tpa != 1 && tpa != 2 && tpa != 4 && tpa != 8 && tpa != 32) ||
       (block != 128 && block != 256 && block != 512))
     return MDK_ERR_BAD_ARG;
   c->cfg.tpa = tpa;

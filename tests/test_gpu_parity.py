@@ -433,7 +433,7 @@ def test_launch_shapes_agree(mdk, ora):
     reps = small_coldcurve()
     ctx = batch_ctx(mdk, reps, "fp64", tab)
     ref = [ora.eam(r.x, r.lo, r.hi, r.periodic, tab) for r in reps]
-    for tpa in (1, 2, 4):
+    for tpa in (1, 2, 4, 8, 32):
         for block in (128, 256, 512):
             ctx.set_launch(tpa, block)
             E, F, Wv = ctx.compute()
@@ -442,14 +442,22 @@ def test_launch_shapes_agree(mdk, ora):
                 assert_fp64(E[q], F[off:off + r.n], Wv[q], ref[q])
                 off += r.n
     t, b, ms = ctx.autotune()
-    assert t in (1, 2, 4) and b in (128, 256, 512) and ms > 0.0
+    assert t in (1, 2, 4, 8, 32) and b in (128, 256, 512) and ms > 0.0
     xj, lo, hi = jittered_lattice(7, 4, 5.26, 0.12)
     c2 = lj_ctx(mdk, xj, lo, hi, [1, 1, 1], "mixed")
     r0 = ora.lj(xj, lo, hi, [1, 1, 1], W.LJ_AR.eps, W.LJ_AR.sigma, W.LJ_AR.rc, 1)
-    for tpa in (2, 4):
+    for tpa in (2, 4, 8, 32):
         c2.set_launch(tpa, 128)
         E, F, _ = c2.compute()
         assert_mixed(E[0], F, r0)
+    # FP64 LJ, a warp per atom, against the oracle at the FP64 bars
+    c3 = lj_ctx(mdk, xj, lo, hi, [1, 1, 1], "fp64")
+    for tpa in (8, 32):
+        c3.set_launch(tpa, 256)
+        E, F, Wv = c3.compute()
+        assert_fp64(E[0], F, Wv[0], r0)
+    with pytest.raises(mdk.MDKError):
+        c3.set_launch(16, 128)
 
 
 def test_batched_dynamics_match_oracle(mdk, ora):
