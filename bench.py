@@ -456,6 +456,10 @@ def main():
                          "synthetic 8 G2 + 43 G4 model, 10-10 network")
     ap.add_argument("--launch", default=None,
                     help="threads-per-atom x block (e.g. 1x128) instead of the autotuner")
+    ap.add_argument("--outer", type=float, default=None,
+                    help="outer-list skin in Angstrom (two-level lists; 0 = off; default: "
+                         "4 x skin for the 8.4M-atom LJ argon config, where it measured "
+                         "faster, else off)")
     ap.add_argument("--list", default=None, choices=("full", "half", "cells"),
                     help="with --launch: the Verlet-list kind (LJ; default full)")
     ap.add_argument("--drift-steps", type=int, default=0,
@@ -505,6 +509,13 @@ def main():
         wl.name = wl.name[:-len(wl.precision)] + prec   # the workload as run
     n_atoms = wl.n_atoms
     windowed = args.config == 3
+    # two-level lists: outer skin (0: off); a moving window rebuilds fully anyway
+    if args.outer is not None:
+        outer_skin = float(args.outer)
+    else:
+        outer_skin = 4.0 * wl.skin if (args.config == 2 and not args.hugoniot and
+                                       not args.bpnn) else 0.0
+    outer_skin = 0.0 if windowed else outer_skin
     if args.stationary:
         if not windowed:
             raise SystemExit("--stationary applies to the slab (--config 3)")
@@ -513,7 +524,8 @@ def main():
     ctx = mdk.make_context(wl, precision=prec,
                            capacity=int(n_atoms * 1.1) if windowed else None,
                            max_neighbors=(120 if args.stationary else
-                                          (320 if grid is not None else 0)))
+                                          (320 if grid is not None else 0)),
+                           skin_outer=outer_skin)
     if grid is not None:
         Tr = np.repeat(grid.temperatures[None, :], len(grid.compressions), 0).ravel()
         ctx.set_langevin_replicas(Tr, np.full(Tr.size, grid.beta), seed=1)
@@ -550,6 +562,7 @@ def main():
     clocks = Clocks()
     clocks.start()
     builds_before = ctx.counters()[0]
+    full_before = ctx.build_counts()[1]
     n_start = ctx.natoms()      # the moving window changes N between builds
     ctx.profile(False)          # clears the counters; kernels are still counted
     barrier()
@@ -562,6 +575,7 @@ def main():
     ms = e0.elapsed_time(e1)
     launches = int(ctx.get_profile()["kernels"])
     builds0 = ctx.counters()[0]
+    full_builds = ctx.build_counts()[1] - full_before
     ck = clocks.stop()
     ctx.check()
     # per-kernel times: a separate segment with CUDA events around every force
@@ -701,7 +715,8 @@ def main():
         c64 = mdk.make_context(wl, precision="fp64",
                                capacity=int(n_atoms * 1.1) if windowed else None,
                                max_neighbors=(120 if args.stationary else
-                                              (320 if grid is not None else 0)))
+                                              (320 if grid is not None else 0)),
+                               skin_outer=outer_skin)
         if args.stationary:
             stationary_setup(c64, wl)
         elif windowed:
@@ -751,6 +766,8 @@ def main():
                                   "list": kind, "list_entries_per_atom": n_list,
                                   "picked_by": picked},
                        "rebuild": "when an atom moved > skin/2 since the last build",
+                       "outer_list": ({"skin_A": outer_skin, "full_builds": full_builds}
+                                      if outer_skin else None),
                        "list_builds_in_timed_region": builds0 - builds_before,
                        "step_graphs": "two-step CUDA graphs replayed by mdk_step",
                        "l2": "inputs larger than L2 (~4 GB touched per step); no flush",

@@ -282,6 +282,30 @@ int mdk_get_thermo(mdk_ctx *ctx, double *out, int max_samples, int *n_out);
 /* Number of list builds and of steps done so far (host, synchronises). */
 int mdk_get_counters(mdk_ctx *ctx, int64_t *n_builds, int64_t *n_steps);
 
+/*
+ * Two-level lists (no paper counterpart: a way of building the same Verlet
+ * list faster).  skin_outer > 0 keeps an outer list of every pair within
+ * rc + skin_outer (full kind, built from cells of that size); at a rebuild
+ * that the displacement trigger asks for, the Verlet list (rc + skin, full or
+ * half) is filtered from the outer list instead of rebuilt from the cells,
+ * as long as the sum of the largest displacements at the builds since the
+ * outer list's build stays <= (skin_outer - skin) / 2 -- then every pair
+ * within rc + skin is in the outer list, and the Verlet list equals the
+ * definition (the same FP32 pre-filter and exact FP64 test as a build from
+ * cells).  Otherwise, and for explicit builds, window builds and the
+ * list-free cell kernel, the build is a full one (re-bin, re-sort, outer
+ * list, Verlet list).  skin_outer must exceed the planned skin; 0 turns the
+ * outer list off (the default).  Call after mdk_plan_neighbors; the cells
+ * grow to rc + skin_outer (periodic boxes must be at least that long:
+ * MDK_ERR_BOX_TOO_SMALL), the workspace grows by the outer list
+ * (mdk_workspace_size), and the next call that needs the list rebuilds it.
+ */
+int mdk_set_outer_skin(mdk_ctx *ctx, double skin_outer);
+
+/* Builds so far and, of them, full builds (with the outer list off every
+ * build is full) (host, synchronises). */
+int mdk_get_build_counts(mdk_ctx *ctx, int64_t *n_builds, int64_t *n_full);
+
 /* ---- shock hook (Sec. "Moving window simulation") -------------------------- */
 
 /*

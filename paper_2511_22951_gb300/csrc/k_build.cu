@@ -37,6 +37,11 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 __device__ __forceinline__ bool flag_on(const Sys &s) {
   return *(volatile int *)&s.st->rebuild != 0;
 }
+// a full build: re-bin, re-sort and rebuild the (outer) list from the cells;
+// with the outer list off every build is full
+__device__ __forceinline__ bool full_on(const Sys &s) {
+  return flag_on(s) && *(volatile int *)&s.st->full != 0;
+}
 
 __global__ void k_pre(Sys s, int count_step, int use_cond, cudaGraphConditionalHandle h) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -48,6 +53,12 @@ __global__ void k_pre(Sys s, int count_step, int use_cond, cudaGraphConditionalH
   if (s.rebuild_every > 0 && st->since_build >= s.rebuild_every) st->rebuild = 1;
   // the window acts at builds that stepping triggers, not at explicit builds
   st->win_active = (s.win_on && count_step && st->rebuild) ? 1 : 0;
+  // explicit builds, window builds, list-free forces and a missing outer
+  // list take a full build; otherwise k_outer_decide checks the budget
+  st->full = (st->rebuild && (!s.outer_on || !count_step || st->win_active ||
+                              !st->outer_valid || s.half == 2))
+                 ? 1
+                 : 0;
   st->win_cut = -INFINITY;
   if (st->win_active) {
     st->key_xmax = dkey(-INFINITY);
@@ -73,7 +84,7 @@ __device__ __forceinline__ int front_bin_of(const Sys &s, double x) {
 
 __global__ void __launch_bounds__(kBlk) k_win_stats(Sys s) {
   __shared__ long long sh[2 * kFbinSmem];
-  if (!flag_on(s) || !s.st->win_active) return;
+  if (!full_on(s) || !s.st->win_active) return;
   const bool priv = s.n_fbins <= kFbinSmem;
   if (priv)
     for (int q = threadIdx.x; q < 2 * s.n_fbins; q += blockDim.x) sh[q] = 0;
@@ -104,7 +115,7 @@ __global__ void __launch_bounds__(kBlk) k_win_stats(Sys s) {
 // for the next build.
 __global__ void __launch_bounds__(kBlk) k_win_plan(Sys s) {
   __shared__ int best;
-  if (!flag_on(s) || !s.st->win_active) return;
+  if (!full_on(s) || !s.st->win_active) return;
   if (threadIdx.x == 0) best = -1;
   __syncthreads();
   const long long q_up = __double2ll_rn(s.u_p * kTwo40);
@@ -147,7 +158,7 @@ __global__ void __launch_bounds__(kBlk) k_win_plan(Sys s) {
 }
 
 __global__ void __launch_bounds__(kBlk) k_win_insert(Sys s) {
-  if (!flag_on(s) || !s.st->win_active) return;
+  if (!full_on(s) || !s.st->win_active) return;
   const DevStatus *st = s.st;
   const int add = st->win_insert, n0 = st->win_n_old, id0 = st->win_id0;
   const size_t Nc = s.N_cap;
@@ -171,7 +182,7 @@ __global__ void __launch_bounds__(kBlk) k_win_insert(Sys s) {
 
 // atoms a window deleted sit in the last bucket, past the kept ones: drop them
 __global__ void k_win_trim(Sys s) {
-  if (threadIdx.x != 0 || blockIdx.x != 0 || !flag_on(s)) return;
+  if (threadIdx.x != 0 || blockIdx.x != 0 || !full_on(s)) return;
   DevStatus *st = s.st;
   const int kept = s.cell_start[s.n_cells];
   st->n_deleted += st->N - kept;
@@ -184,7 +195,7 @@ __global__ void k_set_flag(Sys s) {
 }
 
 __global__ void __launch_bounds__(kBlk) k_bin(Sys s) {
-  if (!flag_on(s)) return;
+  if (!full_on(s)) return;
   const int N = s.st->N;
   const bool win = s.win_on && s.st->win_active;
   long long xmin = dkey(INFINITY);  // smallest x kept (window: new rear layer)
@@ -267,7 +278,7 @@ __device__ __forceinline__ int block_exscan(int v, int *total) {
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Sys s) {
-  if (!flag_on(s)) return;
+  if (!full_on(s)) return;
   const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
   int sum = 0;
 #pragma unroll
@@ -279,7 +290,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Sys s) {
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_top(Sys s) {
-  if (!flag_on(s)) return;
+  if (!full_on(s)) return;
   // n_scan_blocks <= kScanThreads * 8
   constexpr int kPer = 8;
   const int base = threadIdx.x * kPer;
@@ -300,7 +311,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(Sys s) {
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Sys s) {
-  if (!flag_on(s)) return;
+  if (!full_on(s)) return;
   const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
   int loc[kScanItems];
   int sum = 0;
@@ -326,7 +337,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Sys s) {
 }
 
 __global__ void __launch_bounds__(kBlk) k_scatter(Sys s) {
-  if (!flag_on(s)) return;
+  if (!full_on(s)) return;
   const int N = s.st->N;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
   const int pos = atomicAdd(&s.cell_fill[s.cell_of[i]], 1);
@@ -342,7 +353,7 @@ __global__ void __launch_bounds__(kBlk) k_scatter(Sys s) {
 // comparisons of a cell run in parallel, with independent loads.  Atoms a
 // window deletes (the last bucket) keep the scatter's order.
 __global__ void __launch_bounds__(kBlk) k_cell_sort(Sys s) {
-  if (!flag_on(s)) return;
+  if (!full_on(s)) return;
   const int N = s.st->N;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
     const int v = s.order[k];
@@ -361,7 +372,7 @@ __global__ void __launch_bounds__(kBlk) k_cell_sort(Sys s) {
 
 template <class P>
 __global__ void __launch_bounds__(kBlk) k_permute(Sys s, typename P::vec4 *pg_target) {
-  if (!flag_on(s)) return;
+  if (!full_on(s)) return;
   const int N = s.st->N;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
   const size_t Nc = s.N_cap;
@@ -402,7 +413,7 @@ __global__ void __launch_bounds__(kBlk) k_permute(Sys s, typename P::vec4 *pg_ta
 }
 
 __global__ void __launch_bounds__(kBlk) k_copyback(Sys s) {
-  if (!flag_on(s)) return;
+  if (!full_on(s)) return;
   const int N = s.st->N;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
   const size_t Nc = s.N_cap;
@@ -481,15 +492,26 @@ __device__ __forceinline__ bool half_keep(int i, int j, bool s_pos) {
 
 // HALF: the list kind is a template parameter, so a full list's candidate
 // loop carries no half-list test
+// where a build writes: the Verlet list (s.nbr), or with the outer list on
+// the outer list (s.nbr1, radius rc + skin_outer, always full)
+struct ListOut {
+  uint32_t *nbr;
+  int32_t *nnbr;
+  int nmax;
+  double rns2;
+  float lo, hi;
+  int *max_seen;
+};
+
 template <bool HALF>
-__global__ void __launch_bounds__(kBlk) k_build(Sys s) {
+__global__ void __launch_bounds__(kBlk) k_build(Sys s, ListOut lo_) {
   __shared__ uint32_t stage[2 * kGroup][kBlk];
-  if (!flag_on(s) || s.half == 2) return;  // 2: forces straight from the cells, no list
+  if (!full_on(s) || s.half == 2) return;  // 2: forces straight from the cells, no list
   const int N = s.st->N;
   const size_t Nc = s.N_cap;
-  const float lo_thr = s.filt_lo, hi_thr = s.filt_hi;
-  const double rns2 = s.rns2;
-  const int ngroups = s.nmax / kGroup;
+  const float lo_thr = lo_.lo, hi_thr = lo_.hi;
+  const double rns2 = lo_.rns2;
+  const int ngroups = lo_.nmax / kGroup;
   constexpr bool half = HALF;
   const int tx = threadIdx.x;
   for (int i = blockIdx.x * kBlk + tx; i < N; i += gridDim.x * kBlk) {
@@ -504,7 +526,7 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
       uint32_t w[kGroup];
 #pragma unroll
       for (int q = 0; q < kGroup; ++q) w[q] = q < fill ? stage[h + q][tx] : 0u;
-      uint4 *o = reinterpret_cast<uint4 *>(s.nbr) + ((size_t)grp * Nc + i) * 2;
+      uint4 *o = reinterpret_cast<uint4 *>(lo_.nbr) + ((size_t)grp * Nc + i) * 2;
       o[0] = make_uint4(w[0], w[1], w[2], w[3]);
       o[1] = make_uint4(w[4], w[5], w[6], w[7]);
     };
@@ -569,6 +591,173 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s) {
       if (j0 < b) block4(j0, std::false_type());
     }
     if (count & 7) flush(count >> 3, count & 7);
+    lo_.nnbr[i] = count;
+    if (count > lo_.nmax) {
+      atomicOr(&s.st->bits, kStOverflow);
+      atomicMax(lo_.max_seen, count);
+    }
+  }
+}
+
+// ---- two-level lists: the Verlet list filtered from the outer list ----------
+// Every build measures the largest displacement since the last build (the
+// reference positions of the displacement trigger); d_acc, the sum of these
+// maxima since the last full build, bounds every atom's displacement since
+// then (triangle inequality).  While d_acc <= (skin_outer - skin) / 2 no
+// pair has closed in by more than skin_outer - skin, so every pair within
+// rc + skin now was within rc + skin_outer at the full build: the outer list
+// holds it, and filtering the outer list gives the exact Verlet list.
+__global__ void __launch_bounds__(kBlk) k_outer_disp(Sys s) {
+  if (!flag_on(s) || !s.outer_on || s.st->full) return;
+  const int N = s.st->N;
+  const size_t Nc = s.N_cap;
+  double m = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double dx = s.x[i] - s.xref[i], dy = s.x[Nc + i] - s.xref[Nc + i],
+                 dz = s.x[2 * Nc + i] - s.xref[2 * Nc + i];
+    m = fmax(m, dx * dx + dy * dy + dz * dz);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  // non-negative doubles order like their bit patterns
+  if ((threadIdx.x & 31) == 0) atomicMax(&s.st->dmax_key, __double_as_longlong(m));
+}
+
+__global__ void k_outer_decide(Sys s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || !flag_on(s) || !s.outer_on) return;
+  DevStatus *st = s.st;
+  if (!st->full) {
+    // sqrt rounded up by one part in 2^40: the bound stays a bound
+    const double d = sqrt(__longlong_as_double(st->dmax_key)) * (1.0 + 0x1p-40);
+    const double acc = st->d_acc + d;
+    if (acc <= s.outer_budget && acc == acc)
+      st->d_acc = acc;
+    else
+      st->full = 1;
+  }
+  if (st->full) {
+    st->d_acc = 0.0;
+    st->outer_valid = 1;  // the chain below rebuilds the outer list
+    st->n_full_builds += 1;
+  }
+  st->dmax_key = 0;
+}
+
+// filter builds: the trigger's reference positions (FP64 x_ref and the FP32
+// cell-relative record the pre-filter reads) move to the current positions;
+// atoms keep their cells, so the outer list's stencil codes stay exact
+__global__ void __launch_bounds__(kBlk) k_outer_refresh(Sys s) {
+  if (!flag_on(s) || !s.outer_on || s.st->full) return;
+  const int N = s.st->N;
+  const size_t Nc = s.N_cap;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    double p[3];
+    const uint32_t cc = s.cellc[i];
+    const uint32_t inf = s.info[i];
+    const Grid &g = s.grid[inf >> 8];
+    for (int d = 0; d < 3; ++d) {
+      const double xv = s.x[d * Nc + i];
+      s.xref[d * Nc + i] = xv;
+      p[d] = xv - cell_center(g, d, cell_coord(cc, d));
+    }
+    if (!(inf & kInfoFar)) s.pf[i] = Mixed::make(p[0], p[1], p[2], inf);
+  }
+}
+
+// the Verlet list (full or half) from the outer list: the same FP32
+// pre-filter, band and exact FP64 test as k_build, on the outer list's
+// candidates in their order (so the list equals a build from the cells)
+template <bool HALF>
+__global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
+  __shared__ uint32_t stage[2 * kGroup][kBlk];
+  if (!flag_on(s) || !s.outer_on || s.half == 2) return;
+  const int N = s.st->N;
+  const size_t Nc = s.N_cap;
+  const float lo_thr = s.filt_lo, hi_thr = s.filt_hi;
+  const double rns2 = s.rns2;
+  const int ngroups = s.nmax / kGroup;
+  const int tx = threadIdx.x;
+  for (int i = blockIdx.x * kBlk + tx; i < N; i += gridDim.x * kBlk) {
+    const float4 pi = __ldg(s.pf + i);
+    const Grid &g = s.grid[__float_as_uint(pi.w) >> 8];
+    const uint32_t cc = s.cellc[i];
+    const int c0 = cell_coord(cc, 0), c1 = cell_coord(cc, 1), c2 = cell_coord(cc, 2);
+    const int n1 = min(s.nnbr1[i], s.nmax1);
+    int count = 0;
+    auto flush = [&](int grp, int fill) {
+      if (grp >= ngroups) return;
+      const int h = (grp & 1) * kGroup;
+      uint32_t w[kGroup];
+#pragma unroll
+      for (int q = 0; q < kGroup; ++q) w[q] = q < fill ? stage[h + q][tx] : 0u;
+      uint4 *o = reinterpret_cast<uint4 *>(s.nbr) + ((size_t)grp * Nc + i) * 2;
+      o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    };
+    const uint4 *row = reinterpret_cast<const uint4 *>(s.nbr1) + (size_t)i * 2;
+    // four candidates at a time (as k_build's blocks of four)
+    auto block4 = [&](const uint32_t *e, const int k0) {
+      const int before = count;
+      float4 pj[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pj[u] = __ldg(s.pf + (k0 + u < n1 ? (int)(e[u] & kJMask) : i));
+      bool band = false;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t code = e[u];
+        const int j = (int)(code & kJMask);
+        const int sx = nbr_s(code, 0), sy = nbr_s(code, 1), sz = nbr_s(code, 2);
+        const float dx = pj[u].x - (pi.x - (float)sx * g.hf[0]);
+        const float dy = pj[u].y - (pi.y - (float)sy * g.hf[1]);
+        const float dz = pj[u].z - (pi.z - (float)sz * g.hf[2]);
+        const float r2f = dx * dx + dy * dy + dz * dz;
+        const bool s_pos = sz > 0 || (sz == 0 && (sy > 0 || (sy == 0 && sx > 0)));
+        const bool ok = k0 + u < n1 && (!HALF || half_keep(i, j, s_pos));
+        const bool acc = ok && r2f < lo_thr;
+        band = band || (ok && !acc && !(r2f > hi_thr));
+        stage[count & 15][tx] = code;  // kept only if accepted
+        count += acc ? 1 : 0;
+      }
+      if (band) {
+        count = before;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t code = e[u];
+          const int j = (int)(code & kJMask);
+          const int sx = nbr_s(code, 0), sy = nbr_s(code, 1), sz = nbr_s(code, 2);
+          const float dx = pj[u].x - (pi.x - (float)sx * g.hf[0]);
+          const float dy = pj[u].y - (pi.y - (float)sy * g.hf[1]);
+          const float dz = pj[u].z - (pi.z - (float)sz * g.hf[2]);
+          const float r2f = dx * dx + dy * dy + dz * dz;
+          const bool s_pos = sz > 0 || (sz == 0 && (sy > 0 || (sy == 0 && sx > 0)));
+          const bool ok = k0 + u < n1 && (!HALF || half_keep(i, j, s_pos));
+          bool acc = ok && r2f < lo_thr;
+          if (ok && !acc && !(r2f > hi_thr)) acc = exact_pair(s, g, i, code, c0, c1, c2, rns2);
+          stage[count & 15][tx] = code;
+          count += acc ? 1 : 0;
+        }
+      }
+      if ((before >> 3) != (count >> 3)) flush(before >> 3, kGroup);
+    };
+    // the next group's entries are loaded while this group runs (their HBM
+    // latency overlaps the candidate gathers)
+    uint4 na = make_uint4(0, 0, 0, 0), nb = na;
+    if (n1 > 0) {
+      na = __ldcs(row);
+      nb = __ldcs(row + 1);
+    }
+    for (int k0 = 0; k0 < n1; k0 += kGroup) {
+      const uint4 a = na, b = nb;
+      row += Nc * 2;
+      if (k0 + kGroup < n1) {
+        na = __ldcs(row);
+        nb = __ldcs(row + 1);
+      }
+      const uint32_t ea[4] = {a.x, a.y, a.z, a.w};
+      const uint32_t eb[4] = {b.x, b.y, b.z, b.w};
+      block4(ea, k0);
+      if (k0 + 4 < n1) block4(eb, k0 + 4);
+    }
+    if (count & 7) flush(count >> 3, count & 7);
     s.nnbr[i] = count;
     if (count > s.nmax) {
       atomicOr(&s.st->bits, kStOverflow);
@@ -618,19 +807,25 @@ void launch_rebuild_head(const Sys &s, int count_step, cudaGraphConditionalHandl
   k_pre<<<1, 32, 0, st>>>(s, count_step, 1, h);
 }
 
-int rebuild_chain_kernels(const Sys &s) { return 11 + (s.win_on ? 4 : 0); }
+int rebuild_chain_kernels(const Sys &s) { return 11 + (s.win_on ? 4 : 0) + (s.outer_on ? 4 : 0); }
 
 int launch_rebuild_body(const Sys &s, int target_pg, int precision, int from_graph,
                         cudaStream_t st) {
-  static int g_atom = 0, g_build = 0, g_cells = 0;
+  static int g_atom = 0, g_build = 0, g_cells = 0, g_filter = 0;
   if (g_atom == 0) {
     g_atom = persistent_blocks((const void *)k_bin, kBlk, 0);
     g_build = persistent_blocks((const void *)k_build<false>, kBlk, 0);
     g_cells = persistent_blocks((const void *)k_cell_sort, kBlk, 0);
+    g_filter = persistent_blocks((const void *)k_build_filter<false>, kBlk, 0);
   }
   const int gN = std::min(g_atom, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
   const int gC = std::min(g_cells, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
   const int gB = std::min(g_build, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
+  const int gF = std::min(g_filter, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
+  if (s.outer_on) {
+    k_outer_disp<<<gN, kBlk, 0, st>>>(s);
+    k_outer_decide<<<1, 32, 0, st>>>(s);
+  }
   if (s.win_on) {
     k_win_stats<<<gN, kBlk, 0, st>>>(s);
     k_win_plan<<<1, kBlk, 0, st>>>(s);
@@ -648,10 +843,21 @@ int launch_rebuild_body(const Sys &s, int target_pg, int precision, int from_gra
     k_permute<Mixed><<<gN, kBlk, 0, st>>>(s, (float4 *)s.pg[target_pg]);
   k_copyback<<<gN, kBlk, 0, st>>>(s);
   if (s.win_on) k_win_trim<<<1, 32, 0, st>>>(s);
-  if (s.half == 1)
-    k_build<true><<<gB, kBlk, 0, st>>>(s);
-  else
-    k_build<false><<<gB, kBlk, 0, st>>>(s);
+  if (!s.outer_on) {
+    const ListOut lo{s.nbr, s.nnbr, s.nmax, s.rns2, s.filt_lo, s.filt_hi, &s.st->max_nnbr};
+    if (s.half == 1)
+      k_build<true><<<gB, kBlk, 0, st>>>(s, lo);
+    else
+      k_build<false><<<gB, kBlk, 0, st>>>(s, lo);
+  } else {
+    const ListOut lo{s.nbr1, s.nnbr1, s.nmax1, s.rns2_1, s.filt1_lo, s.filt1_hi, &s.st->max_nnbr1};
+    k_build<false><<<gB, kBlk, 0, st>>>(s, lo);
+    k_outer_refresh<<<gN, kBlk, 0, st>>>(s);
+    if (s.half == 1)
+      k_build_filter<true><<<gF, kBlk, 0, st>>>(s);
+    else
+      k_build_filter<false><<<gF, kBlk, 0, st>>>(s);
+  }
   k_finish<<<1, 32, 0, st>>>(s, from_graph);
   return rebuild_chain_kernels(s) - 1;
 }

@@ -45,6 +45,10 @@ struct mdk_ctx {
   int nmax_req = 0, rebuild_every = 0;
   int nmax = 0;
   int nmax_grow = 0;      // capacity wanted after an overflow
+  // outer list (two-level lists): skin of the outer list, 0 = off; it takes
+  // effect when it exceeds the Verlet skin
+  double skin_outer = 0.0;
+  int nmax1 = 0, nmax1_grow = 0;
   bool need_ws = false;   // the current workspace no longer fits the plan
   int n_cells = 0;
   std::vector<Grid> grids;
@@ -156,6 +160,8 @@ size_t layout(mdk_ctx *c, char *base) {
   s.pgF = cv.take<char>(gsz * (c->pot == 2 ? Nc : 1));
   s.nnbr = cv.take<int32_t>(Nc);
   s.nbr = cv.take<uint32_t>((size_t)std::max(c->nmax, c->nmax_grow) * Nc);
+  s.nnbr1 = cv.take<int32_t>(c->nmax1 > 0 ? Nc : 1);
+  s.nbr1 = cv.take<uint32_t>(c->nmax1 > 0 ? (size_t)std::max(c->nmax1, c->nmax1_grow) * Nc : 1);
   s.hacc = cv.take<long long>(10 * Nc);
   s.ea = cv.take<double>(Nc);
   s.ka = cv.take<double>(Nc);
@@ -212,7 +218,10 @@ int check_ctx(const mdk_ctx *c) { return c ? MDK_OK : MDK_ERR_BAD_ARG; }
 int plan(mdk_ctx *c, double rc, double skin, int max_neighbors, int rebuild_every) {
   if (!(rc > 0.0) || !(skin >= 0.0) || max_neighbors < 0 || rebuild_every < 0)
     return MDK_ERR_BAD_ARG;
-  const double rns = rc + skin;
+  const double rns_v = rc + skin;
+  // with the outer list on, cells (and the outer list) span rc + skin_outer
+  const bool outer = c->skin_outer > skin;
+  const double rns = outer ? rc + c->skin_outer : rns_v;
   std::vector<Grid> gs((size_t)c->n_rep);
   int cells = 0;
   double max_density = 0.0;
@@ -251,13 +260,20 @@ int plan(mdk_ctx *c, double rc, double skin, int max_neighbors, int rebuild_ever
   if (scan_blocks_for(cells + 1) > 8192) return MDK_ERR_BAD_ARG;
   int nmax = (max_neighbors + kGroup - 1) / kGroup * kGroup;
   if (nmax == 0) {
-    const double est = 4.0 / 3.0 * M_PI * rns * rns * rns * max_density;
+    const double est = 4.0 / 3.0 * M_PI * rns_v * rns_v * rns_v * max_density;
     nmax = (int)ceil(1.6 * est + 24.0);
     nmax = (nmax + kGroup - 1) / kGroup * kGroup;
+  }
+  int nmax1 = 0;
+  if (outer) {
+    const double est1 = 4.0 / 3.0 * M_PI * rns * rns * rns * max_density;
+    nmax1 = std::max((int)ceil(1.6 * est1 + 24.0), nmax);
+    nmax1 = (nmax1 + kGroup - 1) / kGroup * kGroup;
   }
   c->grids = gs;
   c->n_cells = cells;
   c->nmax = nmax;
+  c->nmax1 = std::max(nmax1, outer ? c->nmax1_grow : 0);
   c->rc_list = rc;
   c->skin = skin;
   c->nmax_req = max_neighbors;
@@ -297,6 +313,15 @@ void fill_sys_params(mdk_ctx *c) {
   // leaves a wide margin, and candidates inside the band take the FP64 test
   s.filt_lo = (float)(s.rns2 * (1.0 - 1e-4));
   s.filt_hi = (float)(s.rns2 * (1.0 + 1e-4));
+  s.outer_on = c->nmax1 > 0 ? 1 : 0;
+  s.nmax1 = c->nmax1;
+  {
+    const double r1 = c->rc_list + (s.outer_on ? c->skin_outer : c->skin);
+    s.rns2_1 = r1 * r1;
+    s.filt1_lo = (float)(s.rns2_1 * (1.0 - 1e-4));
+    s.filt1_hi = (float)(s.rns2_1 * (1.0 + 1e-4));
+    s.outer_budget = s.outer_on ? 0.5 * (c->skin_outer - c->skin) : 0.0;
+  }
   s.half_skin2 = 0.25 * c->skin * c->skin;
   s.half_skin2f = (float)s.half_skin2;
   s.rebuild_every = c->rebuild_every;
@@ -481,6 +506,14 @@ int ensure_ready(mdk_ctx *c) {
   return MDK_OK;
 }
 
+// capacities wanted after a list overflow (Verlet list, outer list)
+void note_overflow(mdk_ctx *c, const DevStatus &st) {
+  if (st.max_nnbr > c->nmax)
+    c->nmax_grow = ((int)ceil(st.max_nnbr * 1.25) + 8 + kGroup - 1) / kGroup * kGroup;
+  if (c->nmax1 > 0 && st.max_nnbr1 > c->nmax1)
+    c->nmax1_grow = ((int)ceil(st.max_nnbr1 * 1.25) + 8 + kGroup - 1) / kGroup * kGroup;
+}
+
 int build_now(mdk_ctx *c) {
   launch_set_rebuild_flag(c->sys, c->stream);
   int rr = rebuild_chain(c, 0);
@@ -489,7 +522,7 @@ int build_now(mdk_ctx *c) {
   int rc = read_status(c, &st);
   if (rc) return rc;
   if (st.bits & kStOverflow) {
-    c->nmax_grow = ((int)ceil(st.max_nnbr * 1.25) + 8 + kGroup - 1) / kGroup * kGroup;
+    note_overflow(c, st);
     c->need_ws = true;
     c->list_built = false;
     return MDK_ERR_NEIGH_OVERFLOW;
@@ -955,10 +988,10 @@ int mdk_set_potential_bpnn(mdk_ctx *c, double rc, int n_rad, const int *rad_kind
 
 int mdk_plan_neighbors(mdk_ctx *c, double rc, double skin, int max_neighbors, int rebuild_every) {
   if (check_ctx(c)) return MDK_ERR_BAD_ARG;
-  const int old_nmax = c->nmax, old_cells = c->n_cells;
+  const int old_nmax = c->nmax, old_cells = c->n_cells, old_nmax1 = c->nmax1;
   int rc_ = plan(c, rc, skin, max_neighbors, rebuild_every);
   if (rc_) return rc_;
-  if (c->nmax != old_nmax || c->n_cells != old_cells) c->need_ws = true;
+  if (c->nmax != old_nmax || c->n_cells != old_cells || c->nmax1 != old_nmax1) c->need_ws = true;
   c->list_built = false;
   return MDK_OK;
 }
@@ -995,6 +1028,8 @@ int mdk_set_workspace(mdk_ctx *c, void *dev_ptr, size_t bytes) {
   c->ws_bytes = bytes;
   c->nmax = std::max(c->nmax, c->nmax_grow);
   c->nmax_grow = 0;
+  if (c->nmax1 > 0) c->nmax1 = std::max(c->nmax1, c->nmax1_grow);
+  c->nmax1_grow = 0;
   c->need_ws = false;
   layout(c, c->ws);
   fill_sys_params(c);
@@ -1396,6 +1431,36 @@ int mdk_set_thermo(mdk_ctx *c, int every, int capacity) {
   return c->ws_ok ? MDK_OK : MDK_ERR_WORKSPACE;
 }
 
+int mdk_set_outer_skin(mdk_ctx *c, double skin_outer) {
+  if (check_ctx(c) || !(skin_outer >= 0.0) || !std::isfinite(skin_outer)) return MDK_ERR_BAD_ARG;
+  if (!c->planned) return MDK_ERR_ORDER;
+  if (skin_outer != 0.0 && !(skin_outer > c->skin)) return MDK_ERR_BAD_ARG;
+  const int old_nmax = c->nmax, old_cells = c->n_cells, old_nmax1 = c->nmax1;
+  const double keep = c->skin_outer;
+  c->skin_outer = skin_outer;
+  c->nmax1_grow = 0;
+  const int r = plan(c, c->rc_list, c->skin, c->nmax_req, c->rebuild_every);
+  if (r) {
+    c->skin_outer = keep;
+    plan(c, c->rc_list, c->skin, c->nmax_req, c->rebuild_every);
+    return r;
+  }
+  if (c->nmax != old_nmax || c->n_cells != old_cells || c->nmax1 != old_nmax1) c->need_ws = true;
+  c->list_built = false;
+  return MDK_OK;
+}
+
+int mdk_get_build_counts(mdk_ctx *c, int64_t *n_builds, int64_t *n_full) {
+  if (check_ctx(c)) return MDK_ERR_BAD_ARG;
+  if (!c->ws_ok) return MDK_ERR_WORKSPACE;
+  DevStatus st;
+  int r = read_status(c, &st);
+  if (r) return r;
+  if (n_builds) *n_builds = st.n_builds;
+  if (n_full) *n_full = c->nmax1 > 0 ? st.n_full_builds : st.n_builds;
+  return MDK_OK;
+}
+
 int mdk_get_thermo(mdk_ctx *c, double *out, int max_samples, int *n_out) {
   if (check_ctx(c) || !n_out) return MDK_ERR_BAD_ARG;
   *n_out = 0;
@@ -1434,7 +1499,7 @@ int mdk_last_device_status(mdk_ctx *c, int *bits) {
   if (r) return r;
   if (bits) *bits = (int)st.bits;
   if (st.bits & kStOverflow) {
-    c->nmax_grow = ((int)ceil(st.max_nnbr * 1.25) + 8 + kGroup - 1) / kGroup * kGroup;
+    note_overflow(c, st);
     c->need_ws = true;
     c->list_built = false;
   }

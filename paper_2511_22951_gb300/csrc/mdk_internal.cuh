@@ -64,6 +64,14 @@ struct DevStatus {
   int win_id0;           // id of the first appended atom
   int win_active;        // the window acts at this build (builds during steps)
   long long n_inserted, n_deleted;
+  // outer list (two-level lists; Sys.outer_on)
+  int full;              // this build re-bins and rebuilds the outer list (else:
+                         // the Verlet list is filtered from the outer list)
+  int outer_valid;       // the outer list holds the pairs of the last full build
+  int max_nnbr1;         // longest outer list seen at a build
+  long long dmax_key;    // max |x - xref|^2 at this build (bits of a double >= 0)
+  double d_acc;          // bound on every displacement since the last full build
+  long long n_full_builds;
 };
 
 // one replica's box and cell grid
@@ -111,6 +119,17 @@ struct Sys {
   // list parameters
   double rns2;              // (rc + skin)^2
   float filt_lo, filt_hi;   // FP32 pre-filter band around rns2
+  // outer list (two-level lists, outer_on != 0): every pair within
+  // rc + skin_outer of the last full build, full kind; the Verlet list above is
+  // filtered from it while every atom has moved less than outer_budget =
+  // (skin_outer - skin) / 2 since that build
+  int outer_on;
+  int nmax1;
+  int32_t *nnbr1;
+  uint32_t *nbr1;
+  double rns2_1;            // (rc + skin_outer)^2
+  float filt1_lo, filt1_hi;
+  double outer_budget;
   double half_skin2;        // (skin/2)^2
   int rebuild_every;
   // integration

@@ -66,6 +66,8 @@ SIGNATURES = {
     "mdk_set_thermo": [_P, _I, _I],
     "mdk_get_thermo": [_P, _P, _I, ctypes.POINTER(_I)],
     "mdk_get_counters": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
+    "mdk_set_outer_skin": [_P, _D],
+    "mdk_get_build_counts": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "mdk_set_piston": [_P, _D, _P],
     "mdk_set_window": [_P, _D, _D, _P, _P, _I64, _D, _D, _D, _D, _D, _D],
     "mdk_get_ids": [_P, _P],
@@ -389,6 +391,21 @@ class Context:
                "mdk_get_counters")
         return int(b.value), int(s.value)
 
+    def set_outer_skin(self, skin_outer):
+        """Two-level lists: an outer list within rc + skin_outer from which
+        the Verlet list is filtered while the displacement budget lasts (0:
+        off).  Call after plan(); the workspace is re-allocated on next use."""
+        _check(self.lib.mdk_set_outer_skin(self.h, float(skin_outer)), "mdk_set_outer_skin")
+        if self.ws is not None:
+            self.alloc_workspace()
+
+    def build_counts(self):
+        """(list builds, full builds) so far."""
+        b, f = _I64(), _I64()
+        _check(self.lib.mdk_get_build_counts(self.h, ctypes.byref(b), ctypes.byref(f)),
+               "mdk_get_build_counts")
+        return int(b.value), int(f.value)
+
     def autotune(self, reps=3):
         """Pick threads-per-atom and block size by timing every shape (LJ:
         full and half lists; `list_kind` tells which won)."""
@@ -498,8 +515,9 @@ def fma_peak(precision="fp64"):
 
 
 def make_context(wl, precision=None, stream=None, rebuild_every=0, max_neighbors=0,
-                 capacity=None):
-    """Context for a workloads.Workload: potential, plan, workspace, state, lists."""
+                 capacity=None, skin_outer=0.0):
+    """Context for a workloads.Workload: potential, plan, workspace, state, lists
+    (skin_outer > 0: two-level lists, see Context.set_outer_skin)."""
     prec = precision or wl.precision
     if len(wl.systems) == 1:
         s = wl.systems[0]
@@ -516,6 +534,8 @@ def make_context(wl, precision=None, stream=None, rebuild_every=0, max_neighbors
     else:
         ctx.set_potential_eam(wl.tables)
     ctx.plan(wl.rc, wl.skin, max_neighbors, rebuild_every)
+    if skin_outer:
+        ctx.set_outer_skin(skin_outer)
     x = np.concatenate([q.x for q in wl.systems])
     v = np.concatenate([q.v for q in wl.systems])
     ctx.set_state(x, v)
