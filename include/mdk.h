@@ -288,9 +288,9 @@ int mdk_get_counters(mdk_ctx *ctx, int64_t *n_builds, int64_t *n_steps);
  * rc + skin_outer (full kind, built from cells of that size); at a rebuild
  * that the displacement trigger asks for, the Verlet list (rc + skin, full or
  * half) is filtered from the outer list instead of rebuilt from the cells,
- * as long as the sum of the largest displacements at the builds since the
- * outer list's build stays <= (skin_outer - skin) / 2 -- then every pair
- * within rc + skin is in the outer list, and the Verlet list equals the
+ * as long as no atom has moved more than (skin_outer - skin) / 2 since the
+ * outer list's build (measured at every build) -- then every pair within
+ * rc + skin is in the outer list, and the Verlet list equals the
  * definition (the same FP32 pre-filter and exact FP64 test as a build from
  * cells).  Otherwise, and for explicit builds, window builds and the
  * list-free cell kernel, the build is a full one (re-bin, re-sort, outer

@@ -600,21 +600,19 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s, ListOut lo_) {
 }
 
 // ---- two-level lists: the Verlet list filtered from the outer list ----------
-// Every build measures the largest displacement since the last build (the
-// reference positions of the displacement trigger); d_acc, the sum of these
-// maxima since the last full build, bounds every atom's displacement since
-// then (triangle inequality).  While d_acc <= (skin_outer - skin) / 2 no
-// pair has closed in by more than skin_outer - skin, so every pair within
-// rc + skin now was within rc + skin_outer at the full build: the outer list
-// holds it, and filtering the outer list gives the exact Verlet list.
+// Every build measures d, the largest displacement of an atom since the last
+// full build (x_full: positions right after that build).  A pair closer than
+// rc + skin now was closer than rc + skin + 2 d then, so while
+// d <= (skin_outer - skin) / 2 the outer list holds every pair within
+// rc + skin, and filtering it gives the exact Verlet list.
 __global__ void __launch_bounds__(kBlk) k_outer_disp(Sys s) {
   if (!flag_on(s) || !s.outer_on || s.st->full) return;
   const int N = s.st->N;
   const size_t Nc = s.N_cap;
   double m = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const double dx = s.x[i] - s.xref[i], dy = s.x[Nc + i] - s.xref[Nc + i],
-                 dz = s.x[2 * Nc + i] - s.xref[2 * Nc + i];
+    const double dx = s.x[i] - s.xfull[i], dy = s.x[Nc + i] - s.xfull[Nc + i],
+                 dz = s.x[2 * Nc + i] - s.xfull[2 * Nc + i];
     m = fmax(m, dx * dx + dy * dy + dz * dz);
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -628,11 +626,8 @@ __global__ void k_outer_decide(Sys s) {
   if (!st->full) {
     // sqrt rounded up by one part in 2^40: the bound stays a bound
     const double d = sqrt(__longlong_as_double(st->dmax_key)) * (1.0 + 0x1p-40);
-    const double acc = st->d_acc + d;
-    if (acc <= s.outer_budget && acc == acc)
-      st->d_acc = acc;
-    else
-      st->full = 1;
+    st->d_acc = d;
+    if (!(d <= s.outer_budget)) st->full = 1;
   }
   if (st->full) {
     st->d_acc = 0.0;
@@ -642,13 +637,19 @@ __global__ void k_outer_decide(Sys s) {
   st->dmax_key = 0;
 }
 
-// filter builds: the trigger's reference positions (FP64 x_ref and the FP32
-// cell-relative record the pre-filter reads) move to the current positions;
-// atoms keep their cells, so the outer list's stencil codes stay exact
+// full builds: x_full = x (after the re-sort); filter builds: the trigger's
+// reference positions (FP64 x_ref and the FP32 cell-relative record the
+// pre-filter reads) move to the current positions; atoms keep their cells,
+// so the outer list's stencil codes stay exact
 __global__ void __launch_bounds__(kBlk) k_outer_refresh(Sys s) {
-  if (!flag_on(s) || !s.outer_on || s.st->full) return;
+  if (!flag_on(s) || !s.outer_on) return;
   const int N = s.st->N;
   const size_t Nc = s.N_cap;
+  if (s.st->full) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+      for (int d = 0; d < 3; ++d) s.xfull[d * Nc + i] = s.x[d * Nc + i];
+    return;
+  }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     double p[3];
     const uint32_t cc = s.cellc[i];

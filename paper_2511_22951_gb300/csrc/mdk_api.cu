@@ -161,6 +161,7 @@ size_t layout(mdk_ctx *c, char *base) {
   s.nnbr = cv.take<int32_t>(Nc);
   s.nbr = cv.take<uint32_t>((size_t)std::max(c->nmax, c->nmax_grow) * Nc);
   s.nnbr1 = cv.take<int32_t>(c->nmax1 > 0 ? Nc : 1);
+  s.xfull = cv.take<double>(c->nmax1 > 0 ? 3 * Nc : 1);
   s.nbr1 = cv.take<uint32_t>(c->nmax1 > 0 ? (size_t)std::max(c->nmax1, c->nmax1_grow) * Nc : 1);
   s.hacc = cv.take<long long>(10 * Nc);
   s.ea = cv.take<double>(Nc);

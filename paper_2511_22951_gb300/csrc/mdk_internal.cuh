@@ -69,8 +69,8 @@ struct DevStatus {
                          // the Verlet list is filtered from the outer list)
   int outer_valid;       // the outer list holds the pairs of the last full build
   int max_nnbr1;         // longest outer list seen at a build
-  long long dmax_key;    // max |x - xref|^2 at this build (bits of a double >= 0)
-  double d_acc;          // bound on every displacement since the last full build
+  long long dmax_key;    // max |x - x_full|^2 at this build (bits of a double >= 0)
+  double d_acc;          // the largest displacement since the last full build
   long long n_full_builds;
 };
 
@@ -122,8 +122,9 @@ struct Sys {
   // outer list (two-level lists, outer_on != 0): every pair within
   // rc + skin_outer of the last full build, full kind; the Verlet list above is
   // filtered from it while every atom has moved less than outer_budget =
-  // (skin_outer - skin) / 2 since that build
+  // (skin_outer - skin) / 2 since that build (positions then: xfull)
   int outer_on;
+  double *xfull;
   int nmax1;
   int32_t *nnbr1;
   uint32_t *nbr1;
