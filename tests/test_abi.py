@@ -82,6 +82,19 @@ def test_argument_checks_without_gpu(lib):
     lib.mdk_workspace_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
     assert lib.mdk_plan_neighbors(h, 8.5125, 0.3, 0, 0) == 0
     assert lib.mdk_workspace_size(h, ctypes.byref(sz)) == 0 and sz.value > 0
+    # two-level lists: the outer skin must exceed the skin, and the cells of
+    # rc + skin_outer must fit the periodic box; the workspace grows by the outer list
+    lib.mdk_set_outer_skin.argtypes = [P, ctypes.c_double]
+    one_level = sz.value
+    assert lib.mdk_set_outer_skin(h, 0.2) == -1
+    assert lib.mdk_set_outer_skin(h, -1.0) == -1
+    assert lib.mdk_set_outer_skin(h, 1.2) == 0           # rc + 1.2 = 9.71 <= 10
+    assert lib.mdk_workspace_size(h, ctypes.byref(sz)) == 0 and sz.value > one_level
+    two_level = sz.value
+    assert lib.mdk_set_outer_skin(h, 2.0) == -2          # rc + 2.0 > 10: box too small
+    assert lib.mdk_workspace_size(h, ctypes.byref(sz)) == 0 and sz.value == two_level
+    assert lib.mdk_set_outer_skin(h, 0.0) == 0
+    assert lib.mdk_workspace_size(h, ctypes.byref(sz)) == 0 and sz.value == one_level
     lib.mdk_step.argtypes = [P, ctypes.c_double, ctypes.c_int64]
     assert lib.mdk_step(h, 1.0, 1) == -8                # no workspace yet
     lib.mdk_destroy.argtypes = [P]
