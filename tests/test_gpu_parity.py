@@ -300,16 +300,21 @@ def test_config1_full_size_sampled(mdk, ora):
 
 
 @pytest.mark.slow
-def test_config2_full_size_sampled(mdk, ora):
+@pytest.mark.parametrize("skin_outer", [0.0, 1.5])
+def test_config2_full_size_sampled(mdk, ora, skin_outer):
     """8,388,608-atom LJ argon, mixed: 78 neighbours each in the lattice; sampled
     forces on a thermalised state (300 steps = 0.6 ps, about one vibration
     period, so that the forces are thermal and not the near-zero forces of the
-    starting lattice) within the mixed-precision bar."""
+    starting lattice) within the mixed-precision bar; with one-level lists and
+    with the two-level lists the bench runs (outer skin 1.5 A)."""
     wl = W.config2()
     s = wl.systems[0]
-    ctx = mdk.make_context(wl)
+    ctx = mdk.make_context(wl, skin_outer=skin_outer)
     assert np.all(ctx.neighbor_counts() == 78)
     ctx.step(wl.dt, 300)
+    if skin_outer:
+        nb, nf = ctx.build_counts()
+        assert nb > nf >= 1, (nb, nf)
     x, _ = ctx.get_state()
     E, F, _ = ctx.compute()
     sel = np.random.default_rng(1).choice(s.n, 16, replace=False)
