@@ -7,7 +7,10 @@ than skin/2 -- the cell-list Verlet-list rebuild (all in libmdk.so kernels).
 Default workload: LJ argon, FCC 128^3 cells = 8,388,608 atoms, 80 K, dt = 2 fs,
 skin 0.3 Angstrom, mixed precision (FP32 pair arithmetic, FP64 positions,
 velocities and integration).  Inputs live in HBM and the per-step working set
-(~4 GB) is larger than L2, so no L2 flush is needed between steps.
+(~4 GB) is larger than L2, so no L2 flush is needed between steps.  The
+Verlet lists are two-level there (--outer, default 1.5 Angstrom: rebuilds
+filter an outer list while the displacement budget lasts; --outer 0 for
+one-level lists); the same trigger and the same lists either way.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config C] [--impl reference]
 
