@@ -97,5 +97,8 @@ def test_argument_checks_without_gpu(lib):
     assert lib.mdk_workspace_size(h, ctypes.byref(sz)) == 0 and sz.value == one_level
     lib.mdk_step.argtypes = [P, ctypes.c_double, ctypes.c_int64]
     assert lib.mdk_step(h, 1.0, 1) == -8                # no workspace yet
+    lib.mdk_get_build_counts.argtypes = [P, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.mdk_get_build_counts(h, None, None) == -8
+    assert lib.mdk_get_build_counts(None, None, None) == -1
     lib.mdk_destroy.argtypes = [P]
     assert lib.mdk_destroy(h) == 0
