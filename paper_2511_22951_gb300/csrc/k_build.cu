@@ -613,7 +613,9 @@ __global__ void __launch_bounds__(kBlk) k_outer_disp(Sys s) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const double dx = s.x[i] - s.xfull[i], dy = s.x[Nc + i] - s.xfull[Nc + i],
                  dz = s.x[2 * Nc + i] - s.xfull[2 * Nc + i];
-    m = fmax(m, dx * dx + dy * dy + dz * dz);
+    const double d2 = dx * dx + dy * dy + dz * dz;
+    // a non-finite position forces a full build (whose binning reports it)
+    m = d2 == d2 ? fmax(m, d2) : INFINITY;
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   // non-negative doubles order like their bit patterns
