@@ -295,10 +295,15 @@ int mdk_get_counters(mdk_ctx *ctx, int64_t *n_builds, int64_t *n_steps);
  * cells).  Otherwise, and for explicit builds, window builds and the
  * list-free cell kernel, the build is a full one (re-bin, re-sort, outer
  * list, Verlet list).  skin_outer must exceed the planned skin; 0 turns the
- * outer list off (the default).  Call after mdk_plan_neighbors; the cells
- * grow to rc + skin_outer (periodic boxes must be at least that long:
- * MDK_ERR_BOX_TOO_SMALL), the workspace grows by the outer list
- * (mdk_workspace_size), and the next call that needs the list rebuilds it.
+ * outer list off (the default).  Call after mdk_plan_neighbors (or after a
+ * potential setter, which plans with its cutoff and skin 0.3 when no plan
+ * exists; MDK_ERR_ORDER with no plan at all); a later plan keeps the outer
+ * skin while it exceeds the new skin.  The cells grow to rc + skin_outer
+ * (periodic boxes must be at least that long: MDK_ERR_BOX_TOO_SMALL, and the
+ * previous setting stays), the workspace grows by the outer list and the
+ * positions of the last full build (mdk_workspace_size), and the next call
+ * that needs the list rebuilds it.  Other errors: MDK_ERR_BAD_ARG for a
+ * negative or non-finite value or one not above the skin.
  */
 int mdk_set_outer_skin(mdk_ctx *ctx, double skin_outer);
 
