@@ -14,6 +14,7 @@ Parity pins (what fixes the oracle independently of itself) live in
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
 import subprocess
 import sys
@@ -26,14 +27,38 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 
+_CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11",
+           "-pthread"]
+
+
+def _fingerprint() -> str:
+    """sha256 of the source, the flags and the compiler's version (the
+    library is rebuilt whenever the stamp beside it differs)."""
+    h = hashlib.sha256()
+    with open(_SRC, "rb") as f:
+        h.update(f.read())
+    h.update(" ".join(_CFLAGS).encode())
+    try:
+        h.update(subprocess.run(["gcc", "--version"], capture_output=True, text=True).stdout.encode())
+    except OSError:
+        h.update(b"no gcc")
+    return h.hexdigest()
+
+
 def build(force: bool = False) -> str:
     """Compile oracle.c with gcc (no FMA contraction) into liboracle.so."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stamp_path = _LIB + ".stamp"
+    fp = _fingerprint()
+    fresh = os.path.exists(_LIB) and os.path.exists(stamp_path) and \
+        open(stamp_path).read().strip() == fp
+    if force or not fresh:
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-std=c11", "-o", tmp, _SRC, "-lm"]
+        cmd = ["gcc", *_CFLAGS, "-o", tmp, _SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
+        with open(stamp_path + f".tmp{os.getpid()}", "w") as f:
+            f.write(fp + "\n")
+        os.replace(stamp_path + f".tmp{os.getpid()}", stamp_path)
     return _LIB
 
 

@@ -884,7 +884,7 @@ static const double ORA_KB = 8.617333262e-5; /* eV/K */
  * u and a stiffness beta (1/fs).  Reading (the paper gives no formula): at
  * every force evaluation of a step, an atom in a region (first r with
  * x_lo <= x < x_hi at the new positions, piston atoms excluded) gets
- *   F += g (v - u)  +  sigma (xi - 1/2),  g = -beta m / A,
+ *   F += -beta m (v - u) / A  +  sigma (xi - 1/2),
  *   sigma = sqrt(24 beta m k_B T / (dt A))
  * per component, with v its half-step velocity, A = ORA_ACC, and xi uniform
  * on [0, 1): output d of Philox4x64-10 with counter (atom id, step, 0, 0)
@@ -916,13 +916,12 @@ static void langevin_forces(const ora_langevin *lg, int64_t N, const double *x,
         ora_philox4x64(ctr, key, out);
         double m = mass[i], beta = lg->beta[r];
         double kT = ORA_KB * lg->T[r];
-        double g = (-beta * m) / ORA_ACC;
-        double sigma = sqrt((((24.0 * beta) * m) * kT) / (dt * ORA_ACC));
+        double sigma = sqrt(24.0 * beta * m * kT / (dt * ORA_ACC));
         for (int k = 0; k < 3; ++k) {
             double xi = (double)(out[k] >> 11) * 0x1.0p-53;
-            double fr = g * (v[3 * i + k] - lg->u[r][k]);
+            double fr = -beta * m * (v[3 * i + k] - lg->u[r][k]) / ORA_ACC;
             double fn = sigma * (xi - 0.5);
-            F[3 * i + k] = (F[3 * i + k] + fr) + fn;
+            F[3 * i + k] = F[3 * i + k] + fr + fn;
         }
     }
 }

@@ -2,9 +2,15 @@
 
 Each .cu file under csrc/ is compiled to an object in parallel, then linked
 into paper_2511_22951_gb300/libmdk.so.  Nothing is installed anywhere else.
+
+Freshness: a stamp file beside the library holds the sha256 of every source
+and header, the compiler flags and `nvcc --version`; the library is rebuilt
+whenever the stamp is missing or differs (file times are not trusted: a copy
+or a checkout can make a stale library look newer than its sources).
 """
 from __future__ import annotations
 
+import hashlib
 import os
 import subprocess
 import sys
@@ -16,6 +22,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmdk.so")
+STAMP = LIB + ".stamp"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -38,16 +45,34 @@ def _deps():
         [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def fingerprint(extra=()) -> str:
+    """sha256 over the sources and headers (names and contents), the flags
+    and the compiler's version string."""
+    h = hashlib.sha256()
+    for d in sorted(_deps()):
+        h.update(os.path.relpath(d, ROOT).encode())
+        with open(d, "rb") as f:
+            h.update(f.read())
+    h.update(" ".join([*ARCH, *NVCC_FLAGS, *extra]).encode())
+    try:
+        v = subprocess.run([nvcc(), "--version"], capture_output=True, text=True).stdout
+    except OSError:
+        v = "no nvcc"
+    h.update(v.encode())
+    return h.hexdigest()
+
+
+def up_to_date(extra=()) -> bool:
+    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    with open(STAMP) as f:
+        return f.read().strip() == fingerprint(extra)
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and up_to_date():
+    if not force and up_to_date(extra):
         return LIB
+    stamp = fingerprint(extra)
     os.makedirs(BUILD, exist_ok=True)
     objs = []
 
@@ -70,6 +95,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP + f".tmp{os.getpid()}", "w") as f:
+        f.write(stamp + "\n")
+    os.replace(STAMP + f".tmp{os.getpid()}", STAMP)
     return LIB
 
 

@@ -69,7 +69,7 @@ __global__ void k_pre(Sys s, int count_step, int use_cond, cudaGraphConditionalH
   if (use_cond) cudaGraphSetConditional(h, st->rebuild ? 1u : 0u);
 }
 
-// ---- moving window (Sec. "Moving window simulation"; rules in the oracle) ----
+// ---- moving window (Sec. "Moving window simulation"; rules in mdk.h) ----
 // Front: bins of width front_bin along x; a bin is shocked when its mean v_x
 // exceeds u_p / 2, decided exactly on velocities rounded to multiples of
 // 2^-40 Angstrom/fs (integer sums, so the order of the atomics is irrelevant).

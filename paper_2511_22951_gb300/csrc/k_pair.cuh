@@ -366,8 +366,10 @@ __device__ __forceinline__ void philox4x64(unsigned long long c[4], unsigned lon
 //   F += g (v - u) + sigma (xi - 1/2),  g = -beta m / A,
 //   sigma = sqrt(24 beta m k_B T / (dt A)),
 // xi uniform on [0, 1) from Philox4x64-10 with counter (id, step) and key
-// (seed, 0).  FP64 path: xi = (out >> 11) 2^-53, FP64 arithmetic in the
-// oracle's order.  Mixed path: the thermostat force is computed in FP32 (it
+// (seed, 0).  FP64 path: xi = (out >> 11) 2^-53, FP64 arithmetic with the
+// friction factor g precomputed per region and type (a few ulps of the
+// friction force away from -beta m (v - u) / A evaluated per atom).  Mixed
+// path: the thermostat force is computed in FP32 (it
 // is noise and friction, on GB300's fast pipe), xi = (out >> 40) 2^-24.
 template <class P>
 __device__ __forceinline__ void langevin(const Sys &s, int i, uint32_t inf, double &Fx,

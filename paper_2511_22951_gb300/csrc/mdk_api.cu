@@ -353,7 +353,8 @@ void fill_sys_params(mdk_ctx *c) {
     s.lang_xhi[q] = c->lang_xhi[q];
     for (int d = 0; d < 3; ++d) s.lang_u[q][d] = c->lang_u[q][d];
     for (int t = 0; t < kMaxTypes; ++t) {
-      // g = -beta m / A; sigma = sqrt(24 beta m k_B T / (dt A)), rounded as in the oracle
+      // friction factor g = -beta m / A and noise amplitude
+      // sigma = sqrt(24 beta m k_B T / (dt A)), once per region and type
       const double m = s.mass[t], beta = c->lang_beta[q];
       const double g = q < c->lang_n ? (-beta * m) / kAcc : 0.0;
       const double sig =
@@ -369,8 +370,8 @@ void fill_sys_params(mdk_ctx *c) {
   s.fbin = c->win_fbin;
 }
 
-// (g, sigma) of every replica and atom type for the current dt, rounded as in
-// the oracle, copied into the workspace
+// (g, sigma) of every replica and atom type for the current dt, copied into
+// the workspace
 int upload_lang_rep(mdk_ctx *c) {
   if (!c->lang_rep_on || !c->ws_ok) return MDK_OK;
   const double kB = 8.617333262e-5;  // eV/K

@@ -8,6 +8,8 @@
 * Dimer: analytic u(r) and u'(r).
 * -dE/dx by central differences; sum F = 0; translation invariance.
 * Virial pressure of the perfect lattice equals -dU/dV of the shell sum.
+* Shifted force (shift_mode 2): dimer closed form u(r) - u(rc) - (r - rc) u'(rc)
+  and its force, lattice shell sum, central differences.
 """
 import numpy as np
 import pytest
@@ -138,3 +140,49 @@ def test_shifted_force_mode_continuous(ora):
     res = ora.lj(x, lo, hi, [0, 0, 0], EPS, SIG, RC, 2)
     assert abs(res["E"]) < 1e-10
     assert np.max(np.abs(res["F"])) < 1e-9
+
+
+def u_sf(r, rc=RC):
+    """Shifted-force LJ written out: u(r) - u(rc) - (r - rc) u'(rc)."""
+    return u_lj(r) - u_lj(rc) - (r - rc) * du_lj(rc)
+
+
+def test_shifted_force_dimer_closed_form(ora):
+    # shift_mode 2: value and slope vanish at rc; the linear term
+    # -(r - rc) u'(rc) is ~10% of the dimer energy at 5 A, so a dropped or
+    # mis-signed term fails the energy check, and the force carries -u'(rc)
+    lo, hi = np.array([-50.0] * 3), np.array([50.0] * 3)
+    for r in (3.2, 3.82, 5.0, 8.0):
+        x = np.array([[0.1, 0.2, 0.3], [0.1 + r * 0.6, 0.2 + r * 0.8, 0.3]])
+        res = ora.lj(x, lo, hi, [0, 0, 0], EPS, SIG, RC, 2)
+        assert res["E"] == pytest.approx(u_sf(r), rel=1e-12, abs=1e-16)
+        dvec = x[1] - x[0]
+        fmag = du_lj(r) - du_lj(RC)
+        np.testing.assert_allclose(res["F"][0], fmag * dvec / r, rtol=1e-12, atol=1e-16)
+        np.testing.assert_allclose(res["F"][1], -res["F"][0], rtol=0, atol=1e-16)
+    # the linear term's size at 5 A (what the check above resolves)
+    assert abs((5.0 - RC) * du_lj(RC)) > 0.05 * abs(u_sf(5.0))
+
+
+def test_shifted_force_lattice_shell_sum(ora):
+    x, lo, hi = lattice()
+    r = ora.lj(x, lo, hi, [1, 1, 1], EPS, SIG, RC, 2)
+    d, z = fcc_shells(5.26, RC)
+    e_ref = 0.5 * np.sum(z * u_sf(d))
+    assert r["E"] / x.shape[0] == pytest.approx(e_ref, rel=1e-12)
+    assert np.max(np.abs(r["F"])) < 1e-13
+
+
+def test_shifted_force_is_minus_gradient(ora):
+    x, lo, hi = jittered(seed=5)
+    r = ora.lj(x, lo, hi, [1, 1, 1], EPS, SIG, RC, 2)
+    h = 1e-5
+    rng = np.random.default_rng(2)
+    for i in rng.choice(x.shape[0], 6, replace=False):
+        for k in range(3):
+            xp = x.copy(); xp[i, k] += h
+            xm = x.copy(); xm[i, k] -= h
+            ep = ora.lj(xp, lo, hi, [1, 1, 1], EPS, SIG, RC, 2)["E"]
+            em = ora.lj(xm, lo, hi, [1, 1, 1], EPS, SIG, RC, 2)["E"]
+            fd = -(ep - em) / (2 * h)
+            assert fd == pytest.approx(r["F"][i, k], rel=1e-6, abs=1e-9)
