@@ -459,13 +459,16 @@ int mdk_eam_vjp(mdk_ctx *ctx, const double *gE, const double *gF, double *dtheta
  * variant of the force kernel behind mdk_compute.)
  *
  * Its scratch (cell histogram and starts, atoms sorted by cell, wrapped
- * positions, per-atom energies: about 1.7 MB) is one file-scope __device__
+ * positions, per-atom energies: about 1.9 MB) is one file-scope __device__
  * array in libmdk.so, which every GPU that loads the library holds until the
  * process exits.  The first call on a device looks that array's address up
- * (with the device current); make the first call on each device before any
- * stream capture.  All calls share the array and each call clears what it
- * needs, so two calls whose work overlaps on one GPU (for example, calls on
- * two streams) race: serialise them.
+ * (with the device current) and keeps it; make the first call on each device
+ * before any stream capture.  The kept address belongs to the device's
+ * context of that moment: after cudaDeviceReset on a device, do not call
+ * this entry point on that device again in the same process.  All calls
+ * share the array and each call clears what it needs, so two calls whose
+ * work overlaps on one GPU (for example, calls on two streams) race:
+ * serialise them.
  *
  *   x        : device [N][3] positions (Angstrom), read only
  *   N        : 0 <= N <= MDK_NOALLOC_MAX_ATOMS, else MDK_ERR_TOO_LARGE
@@ -478,7 +481,10 @@ int mdk_eam_vjp(mdk_ctx *ctx, const double *gE, const double *gF, double *dtheta
  *   cuda_stream : stream to run on (NULL = legacy default stream)
  * Same definitions, pair vectors and FP64 arithmetic as mdk_compute in
  * MDK_FP64 mode (the cell search replaces the Verlet list; pairs with
- * r < rc only).  Returns without synchronising.
+ * r < rc only).  Returns without synchronising, so device-side problems
+ * show in the results: an atom with a NaN or Inf coordinate takes part in
+ * no pair, and its row of F and E are NaN (the other atoms' forces are
+ * those of the system without it).
  */
 int mdk_lj_compute_noalloc(const double *x, int64_t N, const double box_lo[3],
                            const double box_hi[3], const int periodic[3], double eps,

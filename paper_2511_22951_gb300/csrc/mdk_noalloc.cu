@@ -16,6 +16,10 @@
 // with cudaGetSymbolAddress while that device is current, and passes the
 // pointer to the kernels.  Every call shares the array: each call zeroes the
 // histogram it accumulates into, and calls whose work overlaps on a GPU race.
+//
+// An atom with a non-finite coordinate goes to a bucket past the real cells:
+// no pair includes it, and its force row and the energy come out NaN (the
+// call does not synchronise, so the results are its only status channel).
 #include <math.h>
 
 #include <mutex>
@@ -31,20 +35,23 @@ constexpr int kMaxCells = MDK_NOALLOC_MAX_CELLS;
 constexpr int kMaxDevices = 64;
 constexpr int kBlk = 256;
 
-// scratch layout (bytes), every part 256-byte aligned
+// scratch layout (bytes), every part 256-byte aligned; the cell arrays hold
+// n_cells + 1 buckets (the last one for atoms with a non-finite coordinate)
+constexpr size_t kBuckets = (size_t)kMaxCells + 64;
 constexpr size_t kOffCount = 0;
-constexpr size_t kOffStart = kOffCount + 4 * (size_t)kMaxCells;
-constexpr size_t kOffFill = kOffStart + 4 * ((size_t)kMaxCells + 64);
-constexpr size_t kOffCellOf = kOffFill + 4 * (size_t)kMaxCells;
+constexpr size_t kOffStart = kOffCount + 4 * kBuckets;
+constexpr size_t kOffFill = kOffStart + 4 * kBuckets;
+constexpr size_t kOffCellOf = kOffFill + 4 * kBuckets;
 constexpr size_t kOffOrder = kOffCellOf + 4 * (size_t)kMaxAtoms;
-constexpr size_t kOffE = kOffOrder + 4 * (size_t)kMaxAtoms;
+constexpr size_t kOffSorted = kOffOrder + 4 * (size_t)kMaxAtoms;
+constexpr size_t kOffE = kOffSorted + 4 * (size_t)kMaxAtoms;
 constexpr size_t kOffX = kOffE + 8 * (size_t)kMaxAtoms;
 constexpr size_t kScratchBytes = kOffX + 24 * (size_t)kMaxAtoms;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 struct NaScratch {
-  int *count, *start, *fill, *cell_of, *order;
+  int *count, *start, *fill, *cell_of, *order, *sorted;
   double *e, *xw;  // xw: wrapped positions [3][kMaxAtoms]
 };
 
@@ -64,6 +71,7 @@ __host__ __device__ inline NaScratch carve(unsigned char *base) {
   s.fill = reinterpret_cast<int *>(base + kOffFill);
   s.cell_of = reinterpret_cast<int *>(base + kOffCellOf);
   s.order = reinterpret_cast<int *>(base + kOffOrder);
+  s.sorted = reinterpret_cast<int *>(base + kOffSorted);
   s.e = reinterpret_cast<double *>(base + kOffE);
   s.xw = reinterpret_cast<double *>(base + kOffX);
   return s;
@@ -71,20 +79,26 @@ __host__ __device__ inline NaScratch carve(unsigned char *base) {
 
 __global__ void k_na_zero(NaParams p, unsigned char *base) {
   NaScratch s = carve(base);
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < p.n_cells; c += gridDim.x * blockDim.x)
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= p.n_cells; c += gridDim.x * blockDim.x)
     s.count[c] = 0;
 }
 
 // wrap (periodic dimensions, by whole box lengths as in the list build),
-// cell id, histogram
+// cell id, histogram; a non-finite coordinate sends the atom to bucket n_cells
 __global__ void k_na_bin(NaParams p, const double *x, unsigned char *base) {
   NaScratch s = carve(base);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.N) return;
+  const double x0 = x[3 * (size_t)i], x1 = x[3 * (size_t)i + 1], x2 = x[3 * (size_t)i + 2];
+  if (!(isfinite(x0) && isfinite(x1) && isfinite(x2))) {
+    for (int d = 0; d < 3; ++d) s.xw[(size_t)d * kMaxAtoms + i] = NAN;
+    s.cell_of[i] = p.n_cells;
+    atomicAdd(&s.count[p.n_cells], 1);
+    return;
+  }
   int c[3];
   for (int d = 0; d < 3; ++d) {
-    double v = x[3 * (size_t)i + d];
-    if (!isfinite(v)) v = p.lo[d];
+    double v = d == 0 ? x0 : (d == 1 ? x1 : x2);
     if (p.per[d] && (v >= p.hi[d] || v < p.lo[d])) {
       if (fabs(v - p.lo[d]) > 4.0 * p.L[d]) v = v - p.L[d] * floor((v - p.lo[d]) / p.L[d]);
       for (int it = 0; it < 8 && v >= p.hi[d]; ++it) v = v - p.L[d];
@@ -100,10 +114,12 @@ __global__ void k_na_bin(NaParams p, const double *x, unsigned char *base) {
   atomicAdd(&s.count[cell], 1);
 }
 
-// exclusive scan of the histogram, one block (n_cells <= 32 * 1024)
+// exclusive scan of the n_cells + 1 bucket counts, one block
+// (n_cells + 1 <= 1024 * kPer)
 __global__ void __launch_bounds__(1024) k_na_scan(NaParams p, unsigned char *base) {
   NaScratch s = carve(base);
-  constexpr int kPer = kMaxCells / 1024;
+  constexpr int kPer = kMaxCells / 1024 + 1;
+  const int nb = p.n_cells + 1;
   __shared__ int warp_tot[32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   int loc[kPer];
@@ -111,7 +127,7 @@ __global__ void __launch_bounds__(1024) k_na_scan(NaParams p, unsigned char *bas
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
     const int c = t * kPer + q;
-    loc[q] = c < p.n_cells ? s.count[c] : 0;
+    loc[q] = c < nb ? s.count[c] : 0;
     sum += loc[q];
   }
   int incl = sum;
@@ -137,13 +153,13 @@ __global__ void __launch_bounds__(1024) k_na_scan(NaParams p, unsigned char *bas
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
     const int c = t * kPer + q;
-    if (c < p.n_cells) {
+    if (c < nb) {
       s.start[c] = pre;
       s.fill[c] = pre;
     }
     pre += loc[q];
   }
-  if (t == 1023) s.start[p.n_cells] = pre;
+  if (t == 1023) s.start[nb] = pre;
 }
 
 __global__ void k_na_scatter(NaParams p, unsigned char *base) {
@@ -154,21 +170,19 @@ __global__ void k_na_scatter(NaParams p, unsigned char *base) {
 }
 
 // atoms of a cell in increasing index order, so results do not depend on
-// the order of the atomic slots
-__global__ void k_na_sort(NaParams p, unsigned char *base) {
+// the order of the atomic slots: the atom in slot k takes rank = number of
+// atoms of its bucket with a smaller index (one thread per atom, the
+// comparisons of a bucket run in parallel)
+__global__ void k_na_rank(NaParams p, unsigned char *base) {
   NaScratch s = carve(base);
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= p.n_cells) return;
-  const int a = s.start[c], b = s.start[c + 1];
-  for (int k = a + 1; k < b; ++k) {
-    const int v = s.order[k];
-    int q = k - 1;
-    while (q >= a && s.order[q] > v) {
-      s.order[q + 1] = s.order[q];
-      --q;
-    }
-    s.order[q + 1] = v;
-  }
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= p.N) return;
+  const int v = s.order[k];
+  const int b = s.cell_of[v];
+  const int a = s.start[b], e = s.start[b + 1];
+  int rank = 0;
+  for (int q = a; q < e; ++q) rank += s.order[q] < v ? 1 : 0;
+  s.sorted[a + rank] = v;
 }
 
 // the force kernel's variant: 27-cell stencil, each stencil position one
@@ -180,6 +194,13 @@ __global__ void __launch_bounds__(kBlk) k_na_force(NaParams p, unsigned char *ba
   const double *X = s.xw, *Y = s.xw + kMaxAtoms, *Z = s.xw + 2 * kMaxAtoms;
   const double xi = X[i], yi = Y[i], zi = Z[i];
   const int cell = s.cell_of[i];
+  if (cell == p.n_cells) {  // non-finite input: in no pair, NaN results
+    F[3 * (size_t)i + 0] = NAN;
+    F[3 * (size_t)i + 1] = NAN;
+    F[3 * (size_t)i + 2] = NAN;
+    s.e[i] = NAN;
+    return;
+  }
   const int c0 = cell % p.nc[0], c1 = (cell / p.nc[0]) % p.nc[1], c2 = cell / (p.nc[0] * p.nc[1]);
   double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0;
   for (int sz = -1; sz <= 1; ++sz) {
@@ -206,7 +227,7 @@ __global__ void __launch_bounds__(kBlk) k_na_force(NaParams p, unsigned char *ba
         const int cj = cx + p.nc[0] * (cy + p.nc[1] * cz);
         const bool self_img = nx == 0 && ny == 0 && nz == 0;
         for (int q = s.start[cj]; q < s.start[cj + 1]; ++q) {
-          const int j = s.order[q];
+          const int j = s.sorted[q];
           if (j == i && self_img) continue;
           const double dx = (X[j] - xi) + (double)nx * p.L[0];
           const double dy = (Y[j] - yi) + (double)ny * p.L[1];
@@ -316,13 +337,13 @@ extern "C" int mdk_lj_compute_noalloc(const double *x, int64_t N, const double b
   if (r) return r;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int gN = (int)((N + kBlk - 1) / kBlk);
-  const int gC = (p.n_cells + kBlk - 1) / kBlk;
+  const int gC = (p.n_cells + 1 + kBlk - 1) / kBlk;
   k_na_zero<<<gC, kBlk, 0, st>>>(p, base);
   if (N > 0) k_na_bin<<<gN, kBlk, 0, st>>>(p, x, base);
   k_na_scan<<<1, 1024, 0, st>>>(p, base);
   if (N > 0) {
     k_na_scatter<<<gN, kBlk, 0, st>>>(p, base);
-    k_na_sort<<<gC, kBlk, 0, st>>>(p, base);
+    k_na_rank<<<gN, kBlk, 0, st>>>(p, base);
     k_na_force<<<gN, kBlk, 0, st>>>(p, base, F);
   }
   k_na_energy<<<1, 1024, 0, st>>>(p, base, E);

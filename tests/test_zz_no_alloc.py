@@ -2,9 +2,11 @@
 device memory (their memory belongs to another allocator, or their loop must
 not pay for allocations).  It keeps its scratch in a fixed-size array inside
 the library, so this test checks, through the C ABI, that two calls in a row
-each give the same energy and forces as mdk_compute in FP64 mode (the shared
+each give the oracle's energy and forces at the FP64 bars (the shared
 scratch keeps the previous call's contents, which must not leak into the
-next call), and that sizes above the fixed maximum are refused before any
+next call), that a non-finite coordinate shows as NaN in that atom's forces
+and in the energy while every other atom gets the forces of the system
+without it, and that sizes above the fixed maximum are refused before any
 GPU work.  Collected last on purpose (file name)."""
 import ctypes
 
@@ -44,44 +46,58 @@ def systems():
     return out
 
 
-def reference(mdk, x, lo, hi, per):
-    ctx = mdk.Context(lo, hi, per, np.full(x.shape[0], LJ.mass), "fp64")
-    ctx.set_potential_lj(LJ.eps, LJ.sigma, LJ.rc, 1)
-    ctx.plan(LJ.rc, 0.3)
-    ctx.set_state(x, np.zeros_like(x))
-    ctx.build_neighbors(LJ.rc, 0.3)
-    E, F, _ = ctx.compute()
-    ctx.close()
-    return E[0], F
-
-
-def call(torch, lib, x, lo, hi, per):
+def call(torch, lib, x, lo, hi, per, shift_mode=1):
     P = ctypes.c_void_p
     xd = torch.tensor(x, dtype=torch.float64, device="cuda")
-    Fd = torch.full(xd.shape, float("nan"), dtype=torch.float64, device="cuda")
-    Ed = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    Fd = torch.full(xd.shape, 7.0, dtype=torch.float64, device="cuda")
+    Ed = torch.full((1,), 7.0, dtype=torch.float64, device="cuda")
     lo_ = np.ascontiguousarray(lo, dtype=np.float64)
     hi_ = np.ascontiguousarray(hi, dtype=np.float64)
     per_ = np.ascontiguousarray(per, dtype=np.int32)
     st = torch.cuda.current_stream().cuda_stream
     r = lib.mdk_lj_compute_noalloc(P(xd.data_ptr()), x.shape[0], lo_.ctypes.data_as(P),
                                    hi_.ctypes.data_as(P), per_.ctypes.data_as(P), LJ.eps,
-                                   LJ.sigma, LJ.rc, 1, P(Fd.data_ptr()), P(Ed.data_ptr()),
-                                   P(st))
+                                   LJ.sigma, LJ.rc, shift_mode, P(Fd.data_ptr()),
+                                   P(Ed.data_ptr()), P(st))
     torch.cuda.synchronize()
     return r, float(Ed.item()), Fd.cpu().numpy()
 
 
-def test_noalloc_matches_compute_on_two_calls(env):
+def test_noalloc_matches_oracle_on_two_calls(env, ora):
     torch, mdk, lib = env
-    for x, lo, hi, per in systems():
-        E_ref, F_ref = reference(mdk, x, lo, hi, per)
-        fmax = np.max(np.abs(F_ref))
-        for _ in range(2):
-            r, E, F = call(torch, lib, x, lo, hi, per)
-            assert r == 0
-            assert abs(E - E_ref) <= 1e-12 * abs(E_ref)
-            assert np.max(np.abs(F - F_ref)) <= 1e-12 * fmax + 1e-13
+    for mode in (1, 2):
+        for x, lo, hi, per in systems():
+            ref = ora.lj(x, lo, hi, per, LJ.eps, LJ.sigma, LJ.rc, mode)
+            fmax = np.max(np.abs(ref["F"]))
+            for _ in range(2):
+                r, E, F = call(torch, lib, x, lo, hi, per, mode)
+                assert r == 0
+                assert abs(E - ref["E"]) <= 1e-12 * abs(ref["E"])
+                assert np.max(np.abs(F - ref["F"])) <= 1e-12 * fmax + 1e-13
+
+
+def test_noalloc_nonfinite_coordinate_shows_as_nan(env, ora):
+    torch, mdk, lib = env
+    x, lo, hi, per = systems()[1]
+    bad = 1234
+    xb = x.copy()
+    xb[bad, 1] = np.nan
+    xb[bad + 1, 2] = np.inf
+    keep = np.ones(x.shape[0], dtype=bool)
+    keep[[bad, bad + 1]] = False
+    ref = ora.lj(x[keep], lo, hi, per, LJ.eps, LJ.sigma, LJ.rc, 1)
+    fmax = np.max(np.abs(ref["F"]))
+    for _ in range(2):
+        r, E, F = call(torch, lib, xb, lo, hi, per)
+        assert r == 0
+        assert np.isnan(E)
+        assert np.all(np.isnan(F[~keep]))
+        assert np.all(np.isfinite(F[keep]))
+        assert np.max(np.abs(F[keep] - ref["F"])) <= 1e-12 * fmax + 1e-13
+    # the next call with finite input is clean again
+    r, E, F = call(torch, lib, x, lo, hi, per)
+    ref = ora.lj(x, lo, hi, per, LJ.eps, LJ.sigma, LJ.rc, 1)
+    assert r == 0 and abs(E - ref["E"]) <= 1e-12 * abs(ref["E"])
 
 
 def test_noalloc_refuses_sizes_above_the_maximum(env):
