@@ -185,7 +185,9 @@ int mdk_set_workspace(mdk_ctx *ctx, void *dev_ptr, size_t bytes);
 /*
  * Copy positions x [N][3] and velocities v [N][3] (Angstrom, Angstrom/fs)
  * into the context.  on_device: 0 = host pointers, 1 = device pointers.
- * v may be NULL (zero velocities).  Invalidates the neighbour list.
+ * v may be NULL (zero velocities).  Invalidates the neighbour list, numbers
+ * the atoms 0..N-1 and restarts the step counter that keys the Langevin
+ * noise (use a checkpoint to carry those over).
  */
 int mdk_set_state(mdk_ctx *ctx, const double *x, const double *v, int on_device);
 
@@ -193,13 +195,50 @@ int mdk_set_state(mdk_ctx *ctx, const double *x, const double *v, int on_device)
  * Copy the current positions and velocities out, in the caller's atom
  * order.  Periodic coordinates are those wrapped into the box at the last
  * list build (then moved by the integrator since).  Either pointer may be
- * NULL.  Host copies synchronise the stream.
+ * NULL.  Host copies synchronise the stream.  While a step is pending after
+ * a list overflow (mdk_step), the velocities are those of the half step.
  */
 int mdk_get_state(mdk_ctx *ctx, double *x, double *v, int on_device);
 
 /* Current number of atoms (changes with the moving window; synchronises
  * when a window is set). */
 int mdk_get_natoms(mdk_ctx *ctx, int64_t *n);
+
+/*
+ * Checkpoints: the whole dynamic state of a context in one host buffer, so a
+ * run can stop and resume bit for bit (Sec. "Moving window simulation": long
+ * shock runs restart from saved states), and so the Python binding can carry
+ * a run over to a new, larger workspace.  A checkpoint holds, per atom, the
+ * positions, velocities and stored forces, the positions of the last list
+ * build (and of the last full build with two-level lists), the permanent id
+ * and the type/piston word; and the step counter that keys the Langevin
+ * noise, the build counters, the moving window's id counter and counts, the
+ * piston speed and whether a step is pending (see mdk_step).
+ * Configuration is not in it: load into a context made and configured like
+ * the saving one (potential, list plan and kind, outer skin, capacity,
+ * thermostats, window, thermo sampling), with its workspace set.  Loading
+ * rebuilds the lists by replaying the last list build(s) at the saved build
+ * positions, so cells, atom order, lists and the displacement trigger's
+ * references equal the saving run's, and the continued run is bitwise the
+ * uninterrupted one (same launch shape).
+ *   mdk_checkpoint_size : bytes of a checkpoint of the current state
+ *                         (synchronises)
+ *   mdk_save_checkpoint : write it into the host buffer buf (bytes at least
+ *                         mdk_checkpoint_size); synchronises.  Works while a
+ *                         call reports MDK_ERR_WORKSPACE or
+ *                         MDK_ERR_NEIGH_OVERFLOW, as long as the current
+ *                         workspace is still allocated.
+ *   mdk_load_checkpoint : replace the context's state by the checkpoint in
+ *                         buf; synchronises.
+ * Errors: MDK_ERR_ORDER (no state to save), MDK_ERR_BAD_ARG (buffer too
+ * small, not a checkpoint, other precision or replica count, more atoms than
+ * the capacity), MDK_ERR_WORKSPACE (no workspace to load into),
+ * MDK_ERR_NEIGH_OVERFLOW (the replayed lists do not fit this context's list
+ * capacity: the capacity was raised; set a larger workspace and load again).
+ */
+int mdk_checkpoint_size(mdk_ctx *ctx, size_t *bytes);
+int mdk_save_checkpoint(mdk_ctx *ctx, void *buf, size_t bytes);
+int mdk_load_checkpoint(mdk_ctx *ctx, const void *buf, size_t bytes);
 
 /* ---- neighbour lists (Sec. "Neighbor lists construction", Eq. rhrz) ------ */
 
@@ -258,11 +297,20 @@ int mdk_get_per_atom(mdk_ctx *ctx, double *Ui, double *Wi);
  * Advance nsteps velocity-Verlet NVE steps of dt fs (Sec. "Molecular
  * dynamics"): v += dt/2 a; x += dt v; rebuild lists when triggered;
  * a = f(x)/m; v += dt/2 a.  All control stays on the GPU; the call only
- * enqueues work and returns the first error flag raised by an earlier call.
- * A list build during the steps that finds more neighbours than the list
- * capacity raises MDK_ERR_NEIGH_OVERFLOW (read with mdk_last_device_status);
- * the steps after it ran with truncated lists, so that state must be
- * discarded: plan a larger max_neighbors for runs that compress.
+ * enqueues work (errors of the steps themselves are read afterwards with
+ * mdk_last_device_status).
+ * List overflow (Sec. "Neighbor lists construction": every pair within r_ns
+ * must be in the list): when a build triggered during the steps finds more
+ * neighbours than the list capacity, stepping stops there -- every later
+ * kernel of the call does nothing -- and mdk_last_device_status reports
+ * MDK_ERR_NEIGH_OVERFLOW (the capacity is raised; the workspace must grow).
+ * The state is then that of the moment of the build: the steps before it
+ * are complete (mdk_get_counters counts them), positions have drifted and
+ * velocities are at the half step, and that step's force pass is pending.
+ * To resume: save a checkpoint, set a larger workspace, load the
+ * checkpoint, and call mdk_step with the steps not yet done; it starts with
+ * the pending force pass, and the run is bitwise the one a large enough
+ * capacity would have given.  The Python binding does this by itself.
  */
 int mdk_step(mdk_ctx *ctx, double dt, int64_t nsteps);
 
@@ -279,7 +327,8 @@ int mdk_set_thermo(mdk_ctx *ctx, int every, int capacity);
  */
 int mdk_get_thermo(mdk_ctx *ctx, double *out, int max_samples, int *n_out);
 
-/* Number of list builds and of steps done so far (host, synchronises). */
+/* Number of list builds and of steps done so far (host, synchronises); after
+ * a stepping overflow, the steps completed before it. */
 int mdk_get_counters(mdk_ctx *ctx, int64_t *n_builds, int64_t *n_steps);
 
 /*

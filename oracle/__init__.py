@@ -219,6 +219,11 @@ def eam(x, lo, hi, periodic, tables, per_atom=False):
         raise RuntimeError("oracle eam failed")
     out = {"E": float(E[0]), "F": F, "W": W, "rho": rho_o, "Fp": fp_o,
            "rho_flag": bool(flag & 1)}
+    # the embedding part sum_i F(rho_i) of E, through the same spline (its
+    # pair part is E minus this); inside the table only
+    if not out["rho_flag"]:
+        out["E_embed"] = float(np.sum(spline_eval(Ft, tables.rho_max / (Ft.shape[0] - 1),
+                                                  rho_o)[0]))
     if per_atom:
         out["Ea"] = Ea
         out["Wa"] = Wa

@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
   using R = typename GP::R;
   using V = typename GP::V;
   extern __shared__ __align__(16) char smem[];
-  const int N = s.st->N;
+  const int N = run_n(s.st);
   const size_t Nc = s.N_cap;
   const int NB = s.nmax;
   const int nY = bp.nY, nr = bp.n_rad, H1 = bp.H1, H2 = bp.H2;
@@ -639,7 +639,8 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
   // radial terms, then the scatter: -g to atom j_a, +g to atom i
   using Q = typename H::Q;
   Q fix = 0, fiy = 0, fiz = 0;
-  R w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+  // virial sums in FP64 (ENERGY passes only: thermo and compute)
+  double w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
   bool bad = false;
   long long *acc = s.hacc;
   for (int qa = lane; qa < n; qa += 32) {
@@ -669,12 +670,12 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
     fiy += qy;
     fiz += qz;
     if (ENERGY) {
-      w0 -= ax * gx;
-      w1 -= ay * gy;
-      w2 -= az * gz;
-      w3 -= ax * gy;
-      w4 -= ax * gz;
-      w5 -= ay * gz;
+      w0 -= (double)(ax * gx);
+      w1 -= (double)(ay * gy);
+      w2 -= (double)(az * gz);
+      w3 -= (double)(ax * gy);
+      w4 -= (double)(ax * gz);
+      w5 -= (double)(ay * gz);
     }
   }
   fix = warp_sum(fix);
@@ -695,12 +696,12 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
     H::red(acc + 2 * Nc + i, fiz);
     if (ENERGY) {
       H::red(acc + 3 * Nc + i, H::q(Ei));
-      H::red(acc + 4 * Nc + i, H::q(w0));
-      H::red(acc + 5 * Nc + i, H::q(w1));
-      H::red(acc + 6 * Nc + i, H::q(w2));
-      H::red(acc + 7 * Nc + i, H::q(w3));
-      H::red(acc + 8 * Nc + i, H::q(w4));
-      H::red(acc + 9 * Nc + i, H::q(w5));
+      H::red(acc + 4 * Nc + i, H::qd(w0));
+      H::red(acc + 5 * Nc + i, H::qd(w1));
+      H::red(acc + 6 * Nc + i, H::qd(w2));
+      H::red(acc + 7 * Nc + i, H::qd(w3));
+      H::red(acc + 8 * Nc + i, H::qd(w4));
+      H::red(acc + 9 * Nc + i, H::qd(w5));
     }
   }
 }

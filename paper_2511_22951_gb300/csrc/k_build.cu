@@ -46,6 +46,12 @@ __device__ __forceinline__ bool full_on(const Sys &s) {
 __global__ void k_pre(Sys s, int count_step, int use_cond, cudaGraphConditionalHandle h) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   DevStatus *st = s.st;
+  if (st->abort) {  // stepping stopped at an overflowing build: nothing more
+    if (use_cond) cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  st->step_build = count_step;
+  st->build_ovf = 0;
   if (count_step) {
     st->since_build += 1;
     st->n_steps += 1;  // index of the force evaluation that follows (Langevin noise)
@@ -595,6 +601,7 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s, ListOut lo_) {
     if (count > lo_.nmax) {
       atomicOr(&s.st->bits, kStOverflow);
       atomicMax(lo_.max_seen, count);
+      s.st->build_ovf = 1;
     }
   }
 }
@@ -765,10 +772,14 @@ __global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
     if (count > s.nmax) {
       atomicOr(&s.st->bits, kStOverflow);
       atomicMax(&s.st->max_nnbr, count);
+      s.st->build_ovf = 1;
     }
   }
 }
 
+// A build that stepping triggered and whose list outgrew its capacity stops
+// the stepping (st->abort): the lists are truncated, so no force pass may use
+// them; the host regrows the workspace, carries the state over and resumes.
 __global__ void k_finish(Sys s, int from_graph) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   DevStatus *st = s.st;
@@ -777,6 +788,38 @@ __global__ void k_finish(Sys s, int from_graph) {
     st->n_builds += 1;
     if (from_graph) st->n_graph_builds += 1;
     st->since_build = 0;
+    if (st->step_build && st->build_ovf) st->abort = 1;
+  }
+}
+
+// Replay of a filter build (checkpoint restore with two-level lists): the
+// Verlet list is filtered from the outer list of the full build just
+// replayed, at the positions now in x, as a stepping build would.
+__global__ void k_replay_filter_head(Sys s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DevStatus *st = s.st;
+  st->rebuild = 1;
+  st->full = 0;
+  st->win_active = 0;
+  st->win_cut = -INFINITY;
+  st->step_build = 0;
+  st->build_ovf = 0;
+  st->outer_valid = 1;
+}
+
+// gather copy of the positions in x with the cells of the last build (the
+// expression of the step epilogue)
+template <class P>
+__global__ void __launch_bounds__(kBlk) k_regather(Sys s, typename P::vec4 *out) {
+  const int N = s.st->N;
+  const size_t Nc = s.N_cap;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const uint32_t inf = s.info[i];
+    const Grid &g = s.grid[inf >> 8];
+    const uint32_t cc = s.cellc[i];
+    out[i] = P::make(s.x[i] - cell_center(g, 0, cell_coord(cc, 0)),
+                     s.x[Nc + i] - cell_center(g, 1, cell_coord(cc, 1)),
+                     s.x[2 * Nc + i] - cell_center(g, 2, cell_coord(cc, 2)), inf);
   }
 }
 
@@ -868,6 +911,19 @@ int launch_rebuild_body(const Sys &s, int target_pg, int precision, int from_gra
 void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, cudaStream_t st) {
   k_pre<<<1, 32, 0, st>>>(s, count_step, 0, 0);
   launch_rebuild_body(s, target_pg, precision, 0, st);
+}
+
+void launch_replay_filter(const Sys &s, int target_pg, int precision, cudaStream_t st) {
+  k_replay_filter_head<<<1, 32, 0, st>>>(s);
+  launch_rebuild_body(s, target_pg, precision, 0, st);
+}
+
+void launch_regather(const Sys &s, int target_pg, int precision, cudaStream_t st) {
+  const int g = std::min(1024, nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk));
+  if (precision == 0)
+    k_regather<Fp64><<<g, kBlk, 0, st>>>(s, (dvec4 *)s.pg[target_pg]);
+  else
+    k_regather<Mixed><<<g, kBlk, 0, st>>>(s, (float4 *)s.pg[target_pg]);
 }
 
 int scan_blocks_for(int n_buckets) { return (n_buckets + kScanTile - 1) / kScanTile; }

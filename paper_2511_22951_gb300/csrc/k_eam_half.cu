@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256, 2) k_rho_half(Sys s, EAMParams ep, StepAr
     for (int q = threadIdx.x; q < n; q += blockDim.x) rt[q] = src[q];
   }
   __syncthreads();
-  const int N = s.st->N;
+  const int N = run_n(s.st);
   const size_t Nc = s.N_cap;
   const V *__restrict__ pg = (const V *)s.pg[a.cur];
   const R rc2 = sizeof(R) == 8 ? (R)ep.rc2 : (R)ep.rc2f;
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_embed(Sys s, EAMParams ep, StepArgs a) 
   using H = HalfAcc<P>;
   using R = typename GP::R;
   using V = typename GP::V;
-  const int N = s.st->N;
+  const int N = run_n(s.st);
   const size_t Nc = s.N_cap;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256, 2) k_eam_half(Sys s, EAMParams ep, StepAr
     for (int q = threadIdx.x; q < ep.nr; q += blockDim.x) tab[q] = src[q];
   }
   __syncthreads();
-  const int N = s.st->N;
+  const int N = run_n(s.st);
   const size_t Nc = s.N_cap;
   const V *__restrict__ pg = (const V *)s.pg[a.cur];
   const V *__restrict__ pgf = (const V *)s.pgF;  // neighbours: offsets and F'

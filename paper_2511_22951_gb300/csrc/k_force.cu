@@ -13,26 +13,39 @@ using namespace pair;
 constexpr int kBlk = 256;
 
 // ---- first half-kick + drift from the stored forces ---------------------------------
+// The same arithmetic as the second half of the fused step epilogue of the
+// force pass in use (FP64 forces: the kick c F and drift_publish; FP32 forces
+// of the mixed full-list kernels, a.f32: the FP32 kick increment of the FP32
+// force the last pass stored exactly, and drift32), so a run split over
+// several mdk_step calls is bitwise the run in one call.
 template <class P>
 __global__ void __launch_bounds__(kBlk) k_kick_drift(Sys s, StepArgs a) {
-  const int N = s.st->N;
+  const int N = run_n(s.st);
   const int i = blockIdx.x * kBlk + threadIdx.x;
   if (i >= N) return;
   const size_t Nc = s.N_cap;
   const uint32_t inf = s.info[i];
   const int type = inf & 15u;
   double vx = s.v[i], vy = s.v[Nc + i], vz = s.v[2 * Nc + i];
+  const bool mixed = sizeof(typename G<P>::R) == 4 && a.f32;
   if (inf & kInfoPiston) {
     vx = s.u_p;
     vy = 0.0;
     vz = 0.0;
+  } else if (mixed) {
+    vx += kick32(s, a, type, (float)s.f[i]);
+    vy += kick32(s, a, type, (float)s.f[Nc + i]);
+    vz += kick32(s, a, type, (float)s.f[2 * Nc + i]);
   } else {
     const double c = 0.5 * a.dt * s.acc_over_m[type];
     vx += c * s.f[i];
     vy += c * s.f[Nc + i];
     vz += c * s.f[2 * Nc + i];
   }
-  drift_publish<P>(s, a, i, inf, vx, vy, vz);
+  if (mixed)
+    drift32(s, a, i, inf, vx, vy, vz);
+  else
+    drift_publish<P>(s, a, i, inf, vx, vy, vz);
 }
 
 // ---- deterministic per-replica sums (fixed order, no atomics) -----------------------

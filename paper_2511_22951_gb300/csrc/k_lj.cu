@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256, lj_min_blocks<P>()) k_lj(Sys s, LJParams 
   using GP = G<P>;
   using R = typename GP::R;
   using V = typename GP::V;
-  const int N = s.st->N;
+  const int N = run_n(s.st);
   const size_t Nc = s.N_cap;
   const V *__restrict__ pg = (const V *)s.pg[a.cur];
   const LJc<R> lc(lp);
@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(256, lj_min_blocks<P>()) k_lj(Sys s, LJParams 
       nn = min(s.nnbr[i], s.nmax);
     }
     Acc<R> fx, fy, fz;
-    R e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+    // energy and virial sums in FP64 (ENERGY passes only: thermo and compute)
+    double e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     R bx = 0, by = 0, bz = 0;  // block sums of four pairs
     walk<T>(
         s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pg + j); },
@@ -78,14 +79,14 @@ __global__ void __launch_bounds__(256, lj_min_blocks<P>()) k_lj(Sys s, LJParams 
             by += fr * dy;
             bz += fr * dz;
             if (ENERGY) {
-              e += R(0.5) * v;
+              e += 0.5 * (double)v;
               const R hf = R(-0.5) * fr;  // r_ij = -d
-              w0 += hf * dx * dx;
-              w1 += hf * dy * dy;
-              w2 += hf * dz * dz;
-              w3 += hf * dx * dy;
-              w4 += hf * dx * dz;
-              w5 += hf * dy * dz;
+              w0 += (double)(hf * dx * dx);
+              w1 += (double)(hf * dy * dy);
+              w2 += (double)(hf * dz * dz);
+              w3 += (double)(hf * dx * dy);
+              w4 += (double)(hf * dx * dz);
+              w5 += (double)(hf * dy * dz);
             }
           }
         },
@@ -99,13 +100,13 @@ __global__ void __launch_bounds__(256, lj_min_blocks<P>()) k_lj(Sys s, LJParams 
             Fz = lanes_sum<T>(fz.getf());
     double E = 0, W0 = 0, W1 = 0, W2 = 0, W3 = 0, W4 = 0, W5 = 0;
     if (ENERGY) {
-      E = lanes_sum<T>((double)e);
-      W0 = lanes_sum<T>((double)w0);
-      W1 = lanes_sum<T>((double)w1);
-      W2 = lanes_sum<T>((double)w2);
-      W3 = lanes_sum<T>((double)w3);
-      W4 = lanes_sum<T>((double)w4);
-      W5 = lanes_sum<T>((double)w5);
+      E = lanes_sum<T>(e);
+      W0 = lanes_sum<T>(w0);
+      W1 = lanes_sum<T>(w1);
+      W2 = lanes_sum<T>(w2);
+      W3 = lanes_sum<T>(w3);
+      W4 = lanes_sum<T>(w4);
+      W5 = lanes_sum<T>(w5);
     }
     if (valid && tl.t == 0) {
       if (ENERGY) {

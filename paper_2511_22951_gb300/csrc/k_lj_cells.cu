@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256, 4) k_lj_cells(Sys s, LJParams lp, StepArg
   __shared__ V tile[kCellWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (c >= s.n_cells) return;  // whole warps leave together
+  if (c >= s.n_cells || s.st->abort) return;  // whole warps leave together
   const int b0 = s.cell_start[c], b1 = s.cell_start[c + 1];
   if (b0 >= b1) return;
   const size_t Nc = s.N_cap;
@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(256, 4) k_lj_cells(Sys s, LJParams lp, StepArg
       pi = GP::ld(pg + b0);
     }
     Acc<R> fx, fy, fz;
-    R e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+    // energy and virial sums in FP64 (ENERGY passes only: thermo and compute)
+    double e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     for (int t = 0; t < 27; ++t) {
       const int sx = t % 3 - 1, sy = (t / 3) % 3 - 1, sz = t / 9 - 1;
       int cx, cy, cz, nx, ny, nz;
@@ -108,14 +109,14 @@ __global__ void __launch_bounds__(256, 4) k_lj_cells(Sys s, LJParams lp, StepArg
             fy.add(fr * dy);
             fz.add(fr * dz);
             if (ENERGY) {
-              e += R(0.5) * v;
+              e += 0.5 * (double)v;
               const R hf = R(-0.5) * fr;  // r_ij = -d
-              w0 += hf * dx * dx;
-              w1 += hf * dy * dy;
-              w2 += hf * dz * dz;
-              w3 += hf * dx * dy;
-              w4 += hf * dx * dz;
-              w5 += hf * dy * dz;
+              w0 += (double)(hf * dx * dx);
+              w1 += (double)(hf * dy * dy);
+              w2 += (double)(hf * dz * dz);
+              w3 += (double)(hf * dx * dy);
+              w4 += (double)(hf * dx * dz);
+              w5 += (double)(hf * dy * dz);
             }
           }
         }

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256, half_min_blocks<P>(ENERGY))
   using R = typename GP::R;
   using V = typename GP::V;
   using Q = typename H::Q;
-  const int N = s.st->N;
+  const int N = run_n(s.st);
   const size_t Nc = s.N_cap;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) k_half_fin(Sys s, StepArgs a) {
   using GP = G<P>;
   using H = HalfAcc<P>;
   using V = typename GP::V;
-  const int N = s.st->N;
+  const int N = run_n(s.st);
   const size_t Nc = s.N_cap;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;

@@ -502,48 +502,12 @@ __device__ __forceinline__ void langevin_f(const Sys &s, int i, uint32_t inf, fl
   }
 }
 
-template <int MODE, bool ENERGY>
-__device__ __forceinline__ void epilogue32(const Sys &s, const StepArgs &a, int i, uint32_t inf,
-                                           float Fx, float Fy, float Fz) {
+// the mixed path's drift with the new velocities: positions advance in FP64,
+// the displacement since the last build is tested in FP32 on the cell offsets
+// (FP64 for far atoms), and the next gather copy is published
+__device__ __forceinline__ void drift32(const Sys &s, const StepArgs &a, int i, uint32_t inf,
+                                        double vx, double vy, double vz) {
   const size_t Nc = s.N_cap;
-  if (MODE == kForceOnly) {
-    s.f[i] = Fx;
-    s.f[Nc + i] = Fy;
-    s.f[2 * Nc + i] = Fz;
-    if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(&s.st->bits, kStNonfinite);
-    return;
-  }
-  const int type = inf & 15u;
-  const bool piston = (inf & kInfoPiston) != 0;
-  if ((s.n_lang > 0 || s.lang_rep_on) && !piston) langevin_f(s, i, inf, Fx, Fy, Fz);
-  const float cf = a.hdtf * s.acc_over_mf[type];
-  const double dx = (double)(cf * Fx), dy = (double)(cf * Fy), dz = (double)(cf * Fz);
-  double vx = s.v[i], vy = s.v[Nc + i], vz = s.v[2 * Nc + i];
-  if (piston) {
-    vx = s.u_p;
-    vy = 0.0;
-    vz = 0.0;
-  } else {
-    vx += dx;
-    vy += dy;
-    vz += dz;
-  }
-  if (ENERGY) s.ka[i] = s.ke_m[type] * (vx * vx + vy * vy + vz * vz);
-  if (MODE == kFinal) {
-    s.v[i] = vx;
-    s.v[Nc + i] = vy;
-    s.v[2 * Nc + i] = vz;
-    s.f[i] = Fx;
-    s.f[Nc + i] = Fy;
-    s.f[2 * Nc + i] = Fz;
-    if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(&s.st->bits, kStNonfinite);
-    return;
-  }
-  if (!piston) {
-    vx += dx;
-    vy += dy;
-    vz += dz;
-  }
   const double x = s.x[i] + a.dt * vx;
   const double y = s.x[Nc + i] + a.dt * vy;
   const double z = s.x[2 * Nc + i] + a.dt * vz;
@@ -577,6 +541,56 @@ __device__ __forceinline__ void epilogue32(const Sys &s, const StepArgs &a, int 
   if (bad) atomicOr(&s.st->bits, kStNonfinite);
   float4 *out = (float4 *)s.pg[a.cur ^ 1];
   out[i] = make_float4(px, py, pz, __uint_as_float(inf));
+}
+
+// the mixed path's kick increment dt/2 F/m, formed in FP32
+__device__ __forceinline__ double kick32(const Sys &s, const StepArgs &a, int type, float F) {
+  return (double)(a.hdtf * s.acc_over_mf[type] * F);
+}
+
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ void epilogue32(const Sys &s, const StepArgs &a, int i, uint32_t inf,
+                                           float Fx, float Fy, float Fz) {
+  const size_t Nc = s.N_cap;
+  if (MODE == kForceOnly) {
+    s.f[i] = Fx;
+    s.f[Nc + i] = Fy;
+    s.f[2 * Nc + i] = Fz;
+    if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(&s.st->bits, kStNonfinite);
+    return;
+  }
+  const int type = inf & 15u;
+  const bool piston = (inf & kInfoPiston) != 0;
+  if ((s.n_lang > 0 || s.lang_rep_on) && !piston) langevin_f(s, i, inf, Fx, Fy, Fz);
+  const double dx = kick32(s, a, type, Fx), dy = kick32(s, a, type, Fy),
+               dz = kick32(s, a, type, Fz);
+  double vx = s.v[i], vy = s.v[Nc + i], vz = s.v[2 * Nc + i];
+  if (piston) {
+    vx = s.u_p;
+    vy = 0.0;
+    vz = 0.0;
+  } else {
+    vx += dx;
+    vy += dy;
+    vz += dz;
+  }
+  if (ENERGY) s.ka[i] = s.ke_m[type] * (vx * vx + vy * vy + vz * vz);
+  if (MODE == kFinal) {
+    s.v[i] = vx;
+    s.v[Nc + i] = vy;
+    s.v[2 * Nc + i] = vz;
+    s.f[i] = Fx;
+    s.f[Nc + i] = Fy;
+    s.f[2 * Nc + i] = Fz;
+    if (!(isfinite(Fx) && isfinite(Fy) && isfinite(Fz))) atomicOr(&s.st->bits, kStNonfinite);
+    return;
+  }
+  if (!piston) {
+    vx += dx;
+    vy += dy;
+    vz += dz;
+  }
+  drift32(s, a, i, inf, vx, vy, vz);
 }
 
 // Finish the step of atom i from its total force: FP32 forces (the mixed

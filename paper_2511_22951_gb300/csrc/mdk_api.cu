@@ -71,6 +71,13 @@ struct mdk_ctx {
   int thermo_every = 0, thermo_cap = 0;
   int64_t thermo_written = 0, thermo_read = 0;
   int64_t steps_done = 0;
+  // steps_done - (device step counter) while no step is pending: the device
+  // counter restarts at mdk_set_state and is carried by checkpoints
+  int64_t steps_base = 0;
+  // a stepping build overflowed: the state is mid-step (positions drifted,
+  // velocities at the half step); the next mdk_step starts with the force
+  // pass of that step
+  bool pending = false;
   LaunchCfg cfg;  // pair-kernel launch shape (mdk_autotune)
   // CUDA graphs of two plain steps, one per parity of the gather copy
   bool graphs_on = true;
@@ -394,6 +401,14 @@ int upload_lang_rep(mdk_ctx *c) {
 int read_status(mdk_ctx *c, DevStatus *out) {
   MDK_CK(cudaMemcpyAsync(out, c->sys.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
   MDK_CK(cudaStreamSynchronize(c->stream));
+  if (out->abort && !c->pending && c->state_set) {
+    // stepping stopped at an overflowing build: n_steps counts the pending
+    // step's force evaluation, the steps before it are complete
+    c->pending = true;
+    c->steps_done = c->steps_base + (out->n_steps - 1);
+    c->forces_valid = false;
+    c->per_atom_valid = false;
+  }
   return MDK_OK;
 }
 
@@ -411,6 +426,9 @@ __global__ void k_init_status(Sys s, int N) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     DevStatus *st = s.st;
     st->N = N;
+    st->abort = 0;
+    st->step_build = 0;
+    st->build_ovf = 0;
     st->rebuild = 1;
     st->bits = 0;
     st->max_nnbr = 0;
@@ -429,18 +447,50 @@ __global__ void k_clear_bits(Sys s) {
   }
 }
 
+// a sample of a step that did not run (stepping aborted) carries step = NaN
+// and is skipped by mdk_get_thermo
 __global__ void k_thermo_store(Sys s, double *ring, int slot, double step) {
   const int r = threadIdx.x;
   if (r >= s.n_rep) return;
   double *o = ring + ((size_t)slot * s.n_rep + r) * 10;
   const double *q = s.red + 9 * r;
-  o[0] = step;
+  o[0] = s.st->abort ? NAN : step;
   o[1] = q[0];
   o[2] = q[1];
   o[3] = q[8];
   for (int c = 0; c < 6; ++c) o[4 + c] = q[2 + c];
 }
 
+
+// checkpoint restore: the status of a loaded state before the replayed
+// builds, then the saved counters after them
+__global__ void k_ckpt_begin(Sys s, int N) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DevStatus *st = s.st;
+  memset(st, 0, sizeof(DevStatus));
+  st->N = N;
+  st->win_cut = -INFINITY;
+}
+
+struct CkptCounters {
+  long long n_steps, n_builds, n_graph_builds, n_full_builds, n_inserted, n_deleted;
+  int since_build, next_id, outer_valid;
+};
+
+__global__ void k_ckpt_end(Sys s, CkptCounters k) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DevStatus *st = s.st;
+  st->n_steps = k.n_steps;
+  st->n_builds = k.n_builds;
+  st->n_graph_builds = k.n_graph_builds;
+  st->n_full_builds = k.n_full_builds;
+  st->n_inserted = k.n_inserted;
+  st->n_deleted = k.n_deleted;
+  st->since_build = k.since_build;
+  st->next_id = k.next_id;
+  st->outer_valid = k.outer_valid;
+  st->rebuild = 0;
+}
 
 // next free event of the measurement pool (created on first use)
 int take_event(mdk_ctx *c) {
@@ -1072,6 +1122,7 @@ int mdk_set_workspace(mdk_ctx *c, void *dev_ptr, size_t bytes) {
   MDK_CK(cudaStreamSynchronize(c->stream));
   c->ws_ok = true;
   c->state_set = false;
+  c->pending = false;
   c->list_built = false;
   c->forces_valid = false;
   c->cur = 0;
@@ -1098,6 +1149,8 @@ int mdk_set_state(mdk_ctx *c, const double *x, const double *v, int on_device) {
   k_init_status<<<1, 32, 0, c->stream>>>(s, (int)c->N);
   launch_load_state(s, xd, vd, c->precision, c->cur, c->stream);
   MDK_CK(cudaPeekAtLastError());
+  c->pending = false;
+  c->steps_base = c->steps_done;
   c->state_set = true;
   c->list_built = false;
   c->forces_valid = false;
@@ -1137,6 +1190,228 @@ int mdk_get_natoms(mdk_ctx *c, int64_t *n) {
   if (c->win_on && c->ws_ok && c->state_set) return device_n(c, n);
   *n = c->N;
   return MDK_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// ---- checkpoints ---------------------------------------------------------------
+// Layout of a checkpoint (host bytes): the header, then per atom in the saving
+// context's internal order, component-major: x[3][N], v[3][N], f[3][N],
+// x_ref[3][N] (positions of the last list build), x_full[3][N] (two-level
+// lists only: positions of the last full build), id[N] (int32), info[N]
+// (uint32: type, piston flag, replica).
+constexpr char kCkptMagic[8] = {'M', 'D', 'K', 'C', 'K', 'P', 'T', '1'};
+enum : int32_t {
+  kCkList = 1,        // a list existed: x_ref (and x_full) are meaningful
+  kCkForces = 2,      // f holds the forces of x
+  kCkPending = 4,     // mid-step: v at the half step, the force pass pending
+  kCkOuter = 8,       // x_full present (two-level lists)
+  kCkOuterValid = 16  // the outer list of x_full was built
+};
+
+struct CkptHeader {
+  char magic[8];
+  int32_t version, precision, n_rep, flags;
+  int64_t N, steps_done;
+  int64_t n_steps, n_builds, n_graph_builds, n_full_builds, n_inserted, n_deleted;
+  int32_t since_build, next_id;
+  double u_p;
+  int64_t reserved[4];
+};
+
+size_t ckpt_bytes(int64_t N, bool outer) {
+  return sizeof(CkptHeader) + (size_t)N * (sizeof(double) * (outer ? 15 : 12) + 8);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mdk_checkpoint_size(mdk_ctx *c, size_t *bytes) {
+  if (check_ctx(c) || !bytes) return MDK_ERR_BAD_ARG;
+  if (!c->ws || !c->state_set) return MDK_ERR_ORDER;
+  DevStatus st;
+  int r = read_status(c, &st);
+  if (r) return r;
+  *bytes = ckpt_bytes(st.N, c->sys.outer_on != 0);
+  return MDK_OK;
+}
+
+int mdk_save_checkpoint(mdk_ctx *c, void *buf, size_t bytes) {
+  if (check_ctx(c) || !buf) return MDK_ERR_BAD_ARG;
+  if (!c->ws || !c->state_set) return MDK_ERR_ORDER;
+  DevStatus st;
+  int r = read_status(c, &st);
+  if (r) return r;
+  const int64_t N = st.N;
+  const bool outer = c->sys.outer_on != 0;
+  if (bytes < ckpt_bytes(N, outer)) return MDK_ERR_BAD_ARG;
+  CkptHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kCkptMagic, 8);
+  h.version = 1;
+  h.precision = c->precision;
+  h.n_rep = c->n_rep;
+  const bool list = c->list_built || c->pending;
+  h.flags = (list ? kCkList : 0) | (c->forces_valid && !c->pending ? kCkForces : 0) |
+            (c->pending ? kCkPending : 0) | (outer ? kCkOuter : 0) |
+            (outer && st.outer_valid ? kCkOuterValid : 0);
+  h.N = N;
+  h.steps_done = c->steps_done;
+  h.n_steps = st.n_steps;
+  h.n_builds = st.n_builds;
+  h.n_graph_builds = st.n_graph_builds;
+  h.n_full_builds = st.n_full_builds;
+  h.n_inserted = st.n_inserted;
+  h.n_deleted = st.n_deleted;
+  h.since_build = st.since_build;
+  h.next_id = st.next_id;
+  h.u_p = c->u_p;
+  char *o = static_cast<char *>(buf);
+  memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  const Sys &s = c->sys;
+  const size_t Nc = (size_t)c->N_cap;
+  const double *arrs[5] = {s.x, s.v, s.f, s.xref, s.xfull};
+  for (int a = 0; a < (outer ? 5 : 4); ++a)
+    for (int d = 0; d < 3; ++d) {
+      if (N > 0)
+        MDK_CK(cudaMemcpyAsync(o, arrs[a] + d * Nc, sizeof(double) * N, cudaMemcpyDeviceToHost,
+                               c->stream));
+      o += sizeof(double) * N;
+    }
+  if (N > 0) {
+    MDK_CK(cudaMemcpyAsync(o, s.id, 4 * N, cudaMemcpyDeviceToHost, c->stream));
+    MDK_CK(cudaMemcpyAsync(o + 4 * N, s.info, 4 * N, cudaMemcpyDeviceToHost, c->stream));
+  }
+  MDK_CK(cudaStreamSynchronize(c->stream));
+  return MDK_OK;
+}
+
+int mdk_load_checkpoint(mdk_ctx *c, const void *buf, size_t bytes) {
+  if (check_ctx(c) || !buf || bytes < sizeof(CkptHeader)) return MDK_ERR_BAD_ARG;
+  CkptHeader h;
+  memcpy(&h, buf, sizeof(h));
+  if (memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1) return MDK_ERR_BAD_ARG;
+  const bool outer = (h.flags & kCkOuter) != 0;
+  if (h.precision != c->precision || h.n_rep != c->n_rep || h.N < 0 || h.N > c->N_cap ||
+      bytes < ckpt_bytes(h.N, outer) || h.steps_done < 0 || h.n_steps < 0)
+    return MDK_ERR_BAD_ARG;
+  if (c->n_rep > 1 && h.N != c->N) return MDK_ERR_BAD_ARG;
+  if (!c->ws_ok || c->need_ws) return MDK_ERR_WORKSPACE;
+  const bool pending = (h.flags & kCkPending) != 0;
+  const bool list = (h.flags & kCkList) != 0;
+  if (pending && !list) return MDK_ERR_BAD_ARG;
+  const int64_t N = h.N;
+  const size_t Nc = (size_t)c->N_cap;
+  Sys &s = c->sys;
+  const char *base = static_cast<const char *>(buf) + sizeof(CkptHeader);
+  auto arr = [&](int a) {  // array a (x, v, f, x_ref, x_full) of the checkpoint
+    return reinterpret_cast<const double *>(base + (size_t)a * 3 * sizeof(double) * N);
+  };
+  const int n_arr = outer ? 5 : 4;
+  const int32_t *ids = reinterpret_cast<const int32_t *>(base + (size_t)n_arr * 3 * 8 * N);
+  const uint32_t *info = reinterpret_cast<const uint32_t *>(ids + N);
+  // upload array a in the order ord (ord[k]: checkpoint index of internal slot k;
+  // empty: the checkpoint's order) into dst
+  std::vector<double> stage;
+  auto upload = [&](int a, const std::vector<int64_t> &ord, double *dst) -> int {
+    const double *src = arr(a);
+    for (int d = 0; d < 3 && N > 0; ++d) {
+      const double *col = src + (size_t)d * N;
+      if (!ord.empty()) {
+        stage.resize((size_t)N);
+        for (int64_t k = 0; k < N; ++k) stage[(size_t)k] = col[ord[(size_t)k]];
+        col = stage.data();
+      }
+      MDK_CK(cudaMemcpyAsync(dst + d * Nc, col, sizeof(double) * N, cudaMemcpyHostToDevice,
+                             c->stream));
+      if (!ord.empty()) MDK_CK(cudaStreamSynchronize(c->stream));  // stage is reused
+    }
+    return MDK_OK;
+  };
+  c->N = N;
+  c->u_p = h.u_p;
+  fill_sys_params(c);
+  if (N > 0) {
+    MDK_CK(cudaMemcpyAsync(s.id, ids, 4 * N, cudaMemcpyHostToDevice, c->stream));
+    MDK_CK(cudaMemcpyAsync(s.info, info, 4 * N, cudaMemcpyHostToDevice, c->stream));
+  }
+  k_ckpt_begin<<<1, 32, 0, c->stream>>>(s, (int)N);
+  MDK_CK(cudaPeekAtLastError());
+  const std::vector<int64_t> none;
+  int r = MDK_OK;
+  const bool replay_outer = outer && (h.flags & kCkOuterValid) && s.outer_on;
+  if (list) {
+    // replay the last builds exactly: a full build at the positions it was
+    // made at (x_full with two-level lists, else x_ref), then with two-level
+    // lists the filter build at x_ref; cells, order and lists then equal the
+    // saved run's
+    r = upload(replay_outer ? 4 : 3, none, s.x);
+    if (r) return r;
+    launch_set_rebuild_flag(s, c->stream);
+    launch_rebuild(s, 0, c->precision, 0, c->stream);
+    c->launches += rebuild_chain_kernels(s) + 1;
+    // the new order: internal slot k holds the atom of id new_id[k]
+    std::vector<int32_t> new_id((size_t)N);
+    if (N > 0)
+      MDK_CK(cudaMemcpyAsync(new_id.data(), s.id, 4 * N, cudaMemcpyDeviceToHost, c->stream));
+    MDK_CK(cudaStreamSynchronize(c->stream));
+    std::vector<std::pair<int32_t, int64_t>> by_id((size_t)N);
+    for (int64_t q = 0; q < N; ++q) by_id[(size_t)q] = {ids[q], q};
+    std::sort(by_id.begin(), by_id.end());
+    std::vector<int64_t> ord((size_t)N);
+    for (int64_t k = 0; k < N; ++k) {
+      auto it = std::lower_bound(by_id.begin(), by_id.end(),
+                                 std::make_pair(new_id[(size_t)k], (int64_t)-1));
+      if (it == by_id.end() || it->first != new_id[(size_t)k]) return MDK_ERR_BAD_ARG;
+      ord[(size_t)k] = it->second;
+    }
+    if (replay_outer) {
+      r = upload(3, ord, s.x);
+      if (r) return r;
+      launch_replay_filter(s, 0, c->precision, c->stream);
+      c->launches += rebuild_chain_kernels(s);
+    }
+    if (!r) r = upload(0, ord, s.x);
+    if (!r) r = upload(1, ord, s.v);
+    if (!r) r = upload(2, ord, s.f);
+    if (!r) r = upload(3, ord, s.xref);
+    if (!r && replay_outer) r = upload(4, ord, s.xfull);
+    if (r) return r;
+    launch_regather(s, 0, c->precision, c->stream);
+    c->launches += 1;
+  } else {
+    r = upload(0, none, s.x);
+    if (!r) r = upload(1, none, s.v);
+    if (!r) r = upload(2, none, s.f);
+    if (r) return r;
+  }
+  CkptCounters k{h.n_steps, h.n_builds, h.n_graph_builds, h.n_full_builds, h.n_inserted,
+                 h.n_deleted, h.since_build, h.next_id, (list && s.outer_on) ? 1 : 0};
+  k_ckpt_end<<<1, 32, 0, c->stream>>>(s, k);
+  MDK_CK(cudaPeekAtLastError());
+  c->cur = 0;
+  c->state_set = true;
+  c->pending = false;
+  DevStatus st;
+  r = read_status(c, &st);
+  if (r) return r;
+  if (st.bits & kStOverflow) {  // the replayed lists outgrow this context's capacity
+    note_overflow(c, st);
+    c->need_ws = true;
+    c->list_built = false;
+    return MDK_ERR_NEIGH_OVERFLOW;
+  }
+  c->list_built = list;
+  c->pending = pending;
+  c->forces_valid = (h.flags & kCkForces) != 0 && !pending;
+  c->per_atom_valid = false;
+  c->steps_done = h.steps_done;
+  c->steps_base = h.steps_done - (h.n_steps - (pending ? 1 : 0));
+  return status_from_bits(st.bits);
 }
 
 int mdk_build_neighbors(mdk_ctx *c, double rc, double skin) {
@@ -1371,16 +1646,25 @@ int mdk_step(mdk_ctx *c, double dt, int64_t nsteps) {
     if (r) return r;
   }
   Sys &s = c->sys;
-  if (!c->forces_valid) {
-    r = force_pass(c, kForceOnly, 0, dt);
+  if (c->pending) {
+    // a restored mid-step state: its first half-kick, drift and list build
+    // are done; the steps start with the pending force pass
+    c->pending = false;
+  } else {
+    if (!c->forces_valid) {
+      r = force_pass(c, kForceOnly, 0, dt);
+      if (r) return r;
+    }
+    // the force passes of the mixed full-list LJ and EAM kernels end a step
+    // with FP32 forces; half lists and BPNN with FP64 sums
+    const int f32 = c->precision == MDK_MIXED && (c->pot == 1 || c->pot == 2) && c->cfg.half != 1;
+    StepArgs a{dt, c->cur, 0, (float)(0.5 * dt), f32};
+    r = timed(c, c->ev_kick, 1, [&] { launch_kick_drift(s, c->precision, a, c->stream); });
+    if (r) return r;
+    c->cur ^= 1;
+    r = rebuild_chain(c, 1);
     if (r) return r;
   }
-  StepArgs a{dt, c->cur, 0, (float)(0.5 * dt)};
-  r = timed(c, c->ev_kick, 1, [&] { launch_kick_drift(s, c->precision, a, c->stream); });
-  if (r) return r;
-  c->cur ^= 1;
-  r = rebuild_chain(c, 1);
-  if (r) return r;
   const uint64_t key = c->graphs_on ? graph_key(c, dt) : 0;
   auto is_thermo = [&](int64_t q) {
     return c->thermo_every > 0 && ((c->steps_done + q) % c->thermo_every) == 0;
@@ -1475,9 +1759,14 @@ int mdk_get_thermo(mdk_ctx *c, double *out, int max_samples, int *n_out) {
                          cudaMemcpyDeviceToHost, c->stream));
   MDK_CK(cudaStreamSynchronize(c->stream));
   int n = 0;
-  for (int64_t q = first; q < c->thermo_written && n < max_samples; ++q, ++n)
-    memcpy(out + (size_t)n * per, ring.data() + (size_t)(q % cap) * per, sizeof(double) * per);
-  c->thermo_read = first + n;
+  int64_t q = first;
+  for (; q < c->thermo_written && n < max_samples; ++q) {
+    const double *smp = ring.data() + (size_t)(q % cap) * per;
+    if (std::isnan(smp[0])) continue;  // a step that stepping did not reach
+    memcpy(out + (size_t)n * per, smp, sizeof(double) * per);
+    ++n;
+  }
+  c->thermo_read = q;
   *n_out = n;
   return MDK_OK;
 }

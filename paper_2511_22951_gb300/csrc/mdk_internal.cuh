@@ -47,6 +47,10 @@ enum : unsigned {
 
 struct DevStatus {
   int N;                 // atoms present
+  int abort;             // != 0: a list build during stepping overflowed; every
+                         // later kernel of the stepping chain does nothing, so
+                         // the state stays that of the moment of the build
+                         // (positions drifted, velocities at the half step)
   int rebuild;           // != 0: rebuild the lists before the next force pass
   unsigned bits;         // kSt* raised since the host last cleared them
   int max_nnbr;          // longest list seen at a build
@@ -72,7 +76,14 @@ struct DevStatus {
   long long dmax_key;    // max |x - x_full|^2 at this build (bits of a double >= 0)
   double d_acc;          // the largest displacement since the last full build
   long long n_full_builds;
+  int step_build;        // this build was triggered by stepping (k_pre, count_step)
+  int build_ovf;         // a list of this build outgrew its capacity
 };
+
+// atoms a force or integration kernel works on: none once stepping aborted
+__device__ __forceinline__ int run_n(const DevStatus *st) {
+  return st->abort ? 0 : st->N;
+}
 
 // one replica's box and cell grid
 struct Grid {
@@ -344,9 +355,16 @@ struct StepArgs {
   int cur;              // gather copy read this step (pg[cur]); pg[cur^1] written
   int energy;           // compute per-atom energies / virials this step
   float hdtf;           // dt / 2 in FP32 (mixed-path kicks)
+  int f32;              // k_kick_drift: the force pass in use ends its steps with
+                        // FP32 forces (the mixed full-list kernels), so the first
+                        // kick takes the FP32 increment of the stored force
 };
 
 void launch_rebuild(const Sys &s, int target_pg, int precision, int count_step, cudaStream_t st);
+// checkpoint restore: a filter build (two-level lists) at the positions in x,
+// and the gather copy pg[target_pg] of x with the cells of the last build
+void launch_replay_filter(const Sys &s, int target_pg, int precision, cudaStream_t st);
+void launch_regather(const Sys &s, int target_pg, int precision, cudaStream_t st);
 // The same chain in two parts for a captured step: the head decides whether
 // to rebuild and sets the conditional node's value; the body (run by that
 // node only when the value is 1) rebuilds.  Returns the kernels of the body.

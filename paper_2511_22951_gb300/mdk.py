@@ -56,6 +56,9 @@ SIGNATURES = {
     "mdk_set_state": [_P, _P, _P, _I],
     "mdk_get_state": [_P, _P, _P, _I],
     "mdk_get_natoms": [_P, ctypes.POINTER(_I64)],
+    "mdk_checkpoint_size": [_P, ctypes.POINTER(_SZ)],
+    "mdk_save_checkpoint": [_P, _P, _SZ],
+    "mdk_load_checkpoint": [_P, _P, _SZ],
     "mdk_plan_neighbors": [_P, _D, _D, _I, _I],
     "mdk_build_neighbors": [_P, _D, _D],
     "mdk_neighbor_count": [_P, ctypes.POINTER(_I64)],
@@ -179,6 +182,9 @@ class Context:
         self._has_state = False
         self._eam_sizes = None
         self.version = 0  # bumped by every call that changes positions or tables
+        self.regrows = 0  # workspaces grown after a list overflow during steps
+        self._thermo_every = 0
+        self._thermo_stash = []
         if capacity is not None:
             _check(self.lib.mdk_set_capacity(self.h, int(capacity)), "mdk_set_capacity")
 
@@ -239,21 +245,76 @@ class Context:
         return int(b.value)
 
     def alloc_workspace(self):
-        if self.ws is not None and self._has_state:
-            try:  # keep the current state across the new workspace
-                self._save_state()
+        """(Re)allocate the workspace.  A state already in the context is
+        carried over whole by a checkpoint (ids, step counter, a step
+        pending after a list overflow, the lists' build positions)."""
+        ck = None
+        if self.ws is not None and self._thermo_every > 0:
+            try:  # samples not read yet live in the old workspace's ring
+                self._thermo_stash.append(self._read_thermo())
             except MDKError:
                 pass
-        nbytes = self.workspace_bytes()
-        self.ws = self.torch.empty(nbytes + 256, dtype=self.torch.uint8, device=self.device)
-        base = self.ws.data_ptr()
-        off = (-base) % 256
-        _check(self.lib.mdk_set_workspace(self.h, _P(base + off), nbytes), "mdk_set_workspace")
-        if self._state is not None:
-            x, v, on_dev = self._state
-            _check(self.lib.mdk_set_state(self.h, _ptr(x), _ptr(v), on_dev), "mdk_set_state")
+        if self.ws is not None and self._has_state:
+            try:
+                ck = self.save_checkpoint()
+            except MDKError:
+                ck = None
+        for _ in range(4):
+            nbytes = self.workspace_bytes()
+            self.ws = None
+            self.ws = self.torch.empty(nbytes + 256, dtype=self.torch.uint8, device=self.device)
+            base = self.ws.data_ptr()
+            off = (-base) % 256
+            _check(self.lib.mdk_set_workspace(self.h, _P(base + off), nbytes),
+                   "mdk_set_workspace")
+            if ck is not None:
+                r = self.lib.mdk_load_checkpoint(self.h, _ptr(ck), ck.nbytes)
+                if r == MDK_ERR_NEIGH_OVERFLOW:   # the replayed lists need more room
+                    continue
+                _check(r, "mdk_load_checkpoint")
+            elif self._state is not None:
+                x, v, on_dev = self._state
+                _check(self.lib.mdk_set_state(self.h, _ptr(x), _ptr(v), on_dev),
+                       "mdk_set_state")
+            return
+        raise MDKError(MDK_ERR_NEIGH_OVERFLOW, "mdk_load_checkpoint")
+
+    def save_checkpoint(self):
+        """The context's whole dynamic state as a numpy uint8 buffer."""
+        n = _SZ()
+        _check(self.lib.mdk_checkpoint_size(self.h, ctypes.byref(n)), "mdk_checkpoint_size")
+        buf = np.zeros(int(n.value), dtype=np.uint8)
+        _check(self.lib.mdk_save_checkpoint(self.h, _ptr(buf), buf.nbytes),
+               "mdk_save_checkpoint")
+        return buf
+
+    def load_checkpoint(self, buf):
+        """Restore a state saved by save_checkpoint (this context configured
+        like the saving one); continues bitwise like the saving run."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        if self.ws is None:
+            self.alloc_workspace()
+        for _ in range(4):
+            r = self.lib.mdk_load_checkpoint(self.h, _ptr(buf), buf.nbytes)
+            if r in (MDK_ERR_NEIGH_OVERFLOW, MDK_ERR_WORKSPACE):
+                nbytes = self.workspace_bytes()
+                self.ws = None
+                self.ws = self.torch.empty(nbytes + 256, dtype=self.torch.uint8,
+                                           device=self.device)
+                base = self.ws.data_ptr()
+                _check(self.lib.mdk_set_workspace(self.h, _P(base + (-base) % 256), nbytes),
+                       "mdk_set_workspace")
+                continue
+            _check(r, "mdk_load_checkpoint")
+            self._has_state = True
+            self._state = None
+            self.version += 1
+            return
+        raise MDKError(MDK_ERR_NEIGH_OVERFLOW, "mdk_load_checkpoint")
 
     def set_thermo(self, every, capacity=1024):
+        self._thermo_every = int(every)
+        self._thermo_stash = []
         r = self.lib.mdk_set_thermo(self.h, every, capacity)
         if r == MDK_ERR_WORKSPACE:
             if self.ws is not None:
@@ -368,22 +429,54 @@ class Context:
         return U, Wa
 
     def step(self, dt, nsteps, check=True):
+        """nsteps velocity-Verlet steps.  check=True: read the device status
+        afterwards; a list that outgrew its capacity during the steps (which
+        stops them at that build) is handled by growing the workspace,
+        carrying the mid-step state over by a checkpoint and running the
+        remaining steps (each overflow once; `regrows` counts them)."""
         self.version += 1
-        _check(self.lib.mdk_step(self.h, dt, int(nsteps)), "mdk_step")
-        if check:
-            self.check()
+        if not check:
+            _check(self.lib.mdk_step(self.h, dt, int(nsteps)), "mdk_step")
+            return
+        left = int(nsteps)
+        for _ in range(16):
+            s0 = self.counters()[1]
+            _check(self.lib.mdk_step(self.h, dt, left), "mdk_step")
+            try:
+                self.check()
+                return
+            except MDKError as e:
+                if e.code != MDK_ERR_NEIGH_OVERFLOW:
+                    raise
+            done = self.counters()[1] - s0
+            if not 0 <= done < left:
+                raise MDKError(MDK_ERR_NEIGH_OVERFLOW, "mdk_step")
+            left -= done
+            self.regrows += 1
+            self.alloc_workspace()
+        raise MDKError(MDK_ERR_NEIGH_OVERFLOW, "mdk_step: the lists kept outgrowing them")
 
     def check(self):
         bits = _I()
         _check(self.lib.mdk_last_device_status(self.h, ctypes.byref(bits)),
                "device status")
 
-    def thermo(self, max_samples=100000):
+    def _read_thermo(self, max_samples=100000):
         out = np.zeros((max_samples, self.n_rep, 10))
         n = _I()
         _check(self.lib.mdk_get_thermo(self.h, _ptr(out), max_samples, ctypes.byref(n)),
                "mdk_get_thermo")
         return out[:n.value]
+
+    def thermo(self, max_samples=100000):
+        """Samples taken since the last call: [n, n_rep, 10] = step, E_kin,
+        E_pot, n_atoms, virial[6] (including samples kept across a workspace
+        that grew after a list overflow)."""
+        out = self._read_thermo(max_samples)
+        if self._thermo_stash:
+            out = np.concatenate(self._thermo_stash + [out])
+            self._thermo_stash = []
+        return out
 
     def counters(self):
         b, s = _I64(), _I64()

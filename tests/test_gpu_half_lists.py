@@ -8,7 +8,7 @@ list must hold exactly one of each mirror pair (i, j, n) / (j, i, -n).
 Forces, energies and virials carry the bars of the full-list path:
   * FP64: |dE| <= 1e-12 |E|, max|dF| <= 1e-12 max|F| + 1e-13 eV/A, virial
     within 1e-12 of max |W|; per-atom energies rtol 1e-12;
-  * mixed: ||dF||_rms / ||F||_rms <= 1e-5, |dE| / N <= 2e-6 eV/atom.
+  * mixed: ||dF||_rms / ||F||_rms <= 1e-5, |dE| <= 1e-6 (|E_pair| + |E_embed|).
 Mixed half lists accumulate in 64-bit fixed point (unit 2^-40 eV/A), which
 fixes two more properties exactly: the forces sum to zero (every pair term
 is added once with each sign), and the result is bitwise reproducible.

@@ -2,10 +2,12 @@
 oracle (tests/test_oracle_langevin.py pins the oracle).
 
 Bars: the noise is the same Philox4x64-10 stream on both sides (counter =
-atom id, step index), and the thermostat arithmetic is rounded in the same
-order, so FP64 trajectories differ only by the conservative forces'
-summation order: positions within 1e-9 Angstrom and velocities within
-1e-11 Angstrom/fs after 10 steps.  The mixed path is checked statistically:
+atom id, step index); the oracle evaluates the friction -beta m (v - u) / A
+as written and the kernel with a precomputed factor -beta m / A (a few ulps
+of the friction force apart, ~1e-18 Angstrom/fs of velocity per step), so
+FP64 trajectories differ by the conservative forces' summation order and
+that rounding: positions within 1e-9 Angstrom and velocities within 1e-11
+Angstrom/fs after 10 steps.  The mixed path is checked statistically:
 a free gas settles at the target temperature and drift velocity.
 """
 import numpy as np
