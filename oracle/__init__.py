@@ -90,6 +90,9 @@ def lib():
         L.ora_md_run.argtypes = [I64, P, P, P, P, P, P, I, P, I, D, P, P, I, D, P, D, D,
                                  I64, I, P, D, P, P]
         L.ora_md_run.restype = I64
+        L.ora_md_run_threads.argtypes = [I64, P, P, P, P, P, P, I, P, I, D, P, P, I, D, P, D,
+                                         D, I64, I, P]
+        L.ora_md_run_threads.restype = I64
         L.ora_bpnn_set_model.argtypes = [D, I, P, P, I, P, P, I, I, P, P, P, P, P, D]
         L.ora_bpnn_set_model.restype = I
         L.ora_bpnn.argtypes = [I64, P, P, P, P, P, P, P, P, P, P, P]
@@ -316,6 +319,33 @@ def md_run(x, v, masses, lo, hi, periodic, dt, nsteps, skin, lj_params=None,
     if nb < 0:
         raise RuntimeError(f"oracle md_run failed ({nb})")
     return {"x": x, "v": v, "F": F, "thermo": thermo[:nsteps], "n_builds": int(nb)}
+
+
+def md_run_threads(x, v, masses, lo, hi, periodic, dt, nsteps, skin, nthreads,
+                   lj_params=None, tables=None):
+    """md_run (LJ or EAM, no piston) with the per-atom work on nthreads host
+    threads: the same values bit for bit, for timing the oracle on all
+    cores."""
+    x = _f64(x, (-1, 3)).copy()
+    v = _f64(v, (-1, 3)).copy()
+    n = x.shape[0]
+    m = _f64(masses, (n,))
+    lo, hi, per = _box(lo, hi, periodic)
+    thermo = np.zeros((max(nsteps, 1), 3))
+    if lj_params is not None:
+        par = _f64([lj_params.eps, lj_params.sigma, lj_params.rc, lj_params.shift_mode])
+        nb = lib().ora_md_run_threads(n, _p(x), _p(v), _p(m), _p(lo), _p(hi), _p(per), 0,
+                                      _p(par), 0, 0.0, None, None, 0, 0.0, None, skin, dt,
+                                      nsteps, int(nthreads), _p(thermo))
+    else:
+        phi, rho, Ft = _f64(tables.phi), _f64(tables.rho), _f64(tables.F)
+        nb = lib().ora_md_run_threads(n, _p(x), _p(v), _p(m), _p(lo), _p(hi), _p(per), 1,
+                                      None, phi.shape[0], tables.rc, _p(phi), _p(rho),
+                                      Ft.shape[0], tables.rho_max, _p(Ft), skin, dt, nsteps,
+                                      int(nthreads), _p(thermo))
+    if nb < 0:
+        raise RuntimeError(f"oracle md_run_threads failed ({nb})")
+    return {"x": x, "v": v, "thermo": thermo[:nsteps], "n_builds": int(nb)}
 
 
 def _bpnn_set(model):

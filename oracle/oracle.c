@@ -47,6 +47,7 @@
  *     list rebuild, by whole box lengths.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -281,6 +282,51 @@ static int vlist_push(ora_vlist *vl, int64_t *cnt, int32_t j, const int n[3]) {
  * exactly once (a stencil position that wraps onto the same cell is another
  * image of it).  Free dimensions skip stencil cells outside the grid.
  */
+/* the list entries of atom i (appended to vl at *cnt) */
+static int vlist_atom(ora_vlist *vl, int64_t *cnt, int64_t i, const double *x,
+                      const ora_box *b, const ora_grid *g, double r2c) {
+    const double *xi = x + 3 * i;
+    int ci[3];
+    for (int k = 0; k < 3; ++k) {
+        int64_t ck = (int64_t)floor((xi[k] - g->glo[k]) / g->h[k]);
+        if (ck < 0) ck = 0;
+        if (ck >= g->nc[k]) ck = g->nc[k] - 1;
+        ci[k] = (int)ck;
+    }
+    int s[3];
+    for (s[2] = -1; s[2] <= 1; ++s[2])
+        for (s[1] = -1; s[1] <= 1; ++s[1])
+            for (s[0] = -1; s[0] <= 1; ++s[0]) {
+                int cj[3], n[3], skip = 0;
+                for (int k = 0; k < 3; ++k) {
+                    int c = ci[k] + s[k];
+                    if (b->per[k]) {
+                        /* n = floor(c / nc); cell = c - n nc */
+                        int q = (c >= 0) ? c / g->nc[k] : -((-c + g->nc[k] - 1) / g->nc[k]);
+                        n[k] = q;
+                        cj[k] = c - q * g->nc[k];
+                    } else {
+                        if (c < 0 || c >= g->nc[k]) skip = 1;
+                        n[k] = 0;
+                        cj[k] = c;
+                    }
+                }
+                if (skip) continue;
+                int64_t c = cj[0] + (int64_t)g->nc[0] * (cj[1] + (int64_t)g->nc[1] * cj[2]);
+                /* image n of cell cj seen from ci: positions were wrapped,
+                 * so the image shift in box lengths is the cell wrap count */
+                for (int64_t q = g->start[c]; q < g->start[c + 1]; ++q) {
+                    int64_t j = g->atoms[q];
+                    if (j == i && n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
+                    double d[3];
+                    double r2 = pair_vec(xi, x + 3 * j, n, b, d);
+                    if (r2 < r2c)
+                        if (vlist_push(vl, cnt, (int32_t)j, n) != 0) return -1;
+                }
+            }
+    return 0;
+}
+
 static int vlist_build(ora_vlist *vl, int64_t N, const double *x,
                        const ora_box *b, double rns) {
     ora_grid g;
@@ -289,48 +335,10 @@ static int vlist_build(ora_vlist *vl, int64_t N, const double *x,
     int64_t cnt = 0;
     for (int64_t i = 0; i < N; ++i) {
         vl->off[i] = cnt;
-        const double *xi = x + 3 * i;
-        int ci[3];
-        for (int k = 0; k < 3; ++k) {
-            int64_t ck = (int64_t)floor((xi[k] - g.glo[k]) / g.h[k]);
-            if (ck < 0) ck = 0;
-            if (ck >= g.nc[k]) ck = g.nc[k] - 1;
-            ci[k] = (int)ck;
+        if (vlist_atom(vl, &cnt, i, x, b, &g, r2c) != 0) {
+            grid_free(&g);
+            return -1;
         }
-        int s[3];
-        for (s[2] = -1; s[2] <= 1; ++s[2])
-            for (s[1] = -1; s[1] <= 1; ++s[1])
-                for (s[0] = -1; s[0] <= 1; ++s[0]) {
-                    int cj[3], n[3], skip = 0;
-                    for (int k = 0; k < 3; ++k) {
-                        int c = ci[k] + s[k];
-                        if (b->per[k]) {
-                            /* n = floor(c / nc); cell = c - n nc */
-                            int q = (c >= 0) ? c / g.nc[k] : -((-c + g.nc[k] - 1) / g.nc[k]);
-                            n[k] = q;
-                            cj[k] = c - q * g.nc[k];
-                        } else {
-                            if (c < 0 || c >= g.nc[k]) skip = 1;
-                            n[k] = 0;
-                            cj[k] = c;
-                        }
-                    }
-                    if (skip) continue;
-                    int64_t c = cj[0] + (int64_t)g.nc[0] * (cj[1] + (int64_t)g.nc[1] * cj[2]);
-                    /* image n of cell cj seen from ci: positions were wrapped,
-                     * so the image shift in box lengths is the cell wrap count */
-                    for (int64_t q = g.start[c]; q < g.start[c + 1]; ++q) {
-                        int64_t j = g.atoms[q];
-                        if (j == i && n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
-                        double d[3];
-                        double r2 = pair_vec(xi, x + 3 * j, n, b, d);
-                        if (r2 < r2c)
-                            if (vlist_push(vl, &cnt, (int32_t)j, n) != 0) {
-                                grid_free(&g);
-                                return -1;
-                            }
-                    }
-                }
     }
     vl->off[N] = cnt;
     grid_free(&g);
@@ -540,6 +548,66 @@ static int bpnn_from_list(int64_t N, const double *x, const ora_box *b, const in
                           double *W, double *Ea, double *Wa, double *G_out,
                           double *dEdG_out);
 
+/* EAM pass 1 for atom i: rho_i = sum_j rho(r_ij); returns F(rho_i), sets
+ * *dF = F'(rho_i) and *fl (1: rho above the F table) */
+static double eam_embed_atom(const ora_pot *p, int64_t i, const double *x, const ora_box *b,
+                             const int64_t *off, const int32_t *jl, const int32_t *nl,
+                             double *rho_out, double *dF, int *fl) {
+    double rc2 = p->rc * p->rc;
+    double rho_i = 0.0;
+    for (int64_t q = off[i]; q < off[i + 1]; ++q) {
+        double d[3];
+        double r2 = pair_vec(x + 3 * i, x + 3 * (int64_t)jl[q], nl + 3 * q, b, d);
+        if (r2 < rc2) {
+            double dr;
+            rho_i += radial(&p->rho, sqrt(r2), &dr);
+        }
+    }
+    *fl = 0;
+    *rho_out = rho_i;
+    return embed(&p->F, rho_i, dF, fl);
+}
+
+/* the pair sums of atom i: force fi, energy ei (half of each pair), virial wi */
+static void pair_atom(const ora_pot *p, int64_t i, const double *x, const ora_box *b,
+                      const int64_t *off, const int32_t *jl, const int32_t *nl,
+                      const double *fp, double fi[3], double *ei_out, double wi[6]) {
+    double rc2 = p->rc * p->rc;
+    double ei = 0.0;
+    fi[0] = fi[1] = fi[2] = 0.0;
+    for (int c = 0; c < 6; ++c) wi[c] = 0.0;
+    for (int64_t q = off[i]; q < off[i + 1]; ++q) {
+        int64_t j = jl[q];
+        double d[3];
+        double r2 = pair_vec(x + 3 * i, x + 3 * j, nl + 3 * q, b, d);
+        if (!(r2 < rc2)) continue;
+        double r = sqrt(r2);
+        double v, dv;
+        if (p->kind == 0) {
+            v = lj_pair(p, r, &dv);
+        } else {
+            double dphi, drho;
+            v = radial(&p->phi, r, &dphi);
+            radial(&p->rho, r, &drho);
+            dv = dphi + (fp[i] + fp[j]) * drho;
+        }
+        ei += 0.5 * v;
+        double s = dv / r;
+        double f[3] = {s * d[0], s * d[1], s * d[2]};
+        fi[0] += f[0];
+        fi[1] += f[1];
+        fi[2] += f[2];
+        /* r_ij = -d */
+        wi[0] += 0.5 * (-d[0]) * f[0];
+        wi[1] += 0.5 * (-d[1]) * f[1];
+        wi[2] += 0.5 * (-d[2]) * f[2];
+        wi[3] += 0.5 * (-d[0]) * f[1];
+        wi[4] += 0.5 * (-d[0]) * f[2];
+        wi[5] += 0.5 * (-d[1]) * f[2];
+    }
+    *ei_out = ei;
+}
+
 static int forces_from_list(const ora_pot *p, int64_t N, const double *x,
                             const ora_box *b, const int64_t *off,
                             const int32_t *jl, const int32_t *nl, double *E,
@@ -548,7 +616,6 @@ static int forces_from_list(const ora_pot *p, int64_t N, const double *x,
     if (p->kind == 2)   /* BPNN: the model set by ora_bpnn_set_model */
         return bpnn_from_list(N, x, b, off, jl, nl, E, F, W, Ea, Wa, NULL, NULL);
     int flag = 0;
-    double rc2 = p->rc * p->rc;
     double Etot = 0.0;
     double Wt[6] = {0, 0, 0, 0, 0, 0};
     double *fp = NULL;
@@ -556,18 +623,9 @@ static int forces_from_list(const ora_pot *p, int64_t N, const double *x,
         fp = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
         /* pass 1: densities, embedding energy and F'(rho_i) */
         for (int64_t i = 0; i < N; ++i) {
-            double rho_i = 0.0;
-            for (int64_t q = off[i]; q < off[i + 1]; ++q) {
-                double d[3];
-                double r2 = pair_vec(x + 3 * i, x + 3 * (int64_t)jl[q], nl + 3 * q, b, d);
-                if (r2 < rc2) {
-                    double dr;
-                    rho_i += radial(&p->rho, sqrt(r2), &dr);
-                }
-            }
-            int fl = 0;
-            double dF;
-            double Fi = embed(&p->F, rho_i, &dF, &fl);
+            int fl;
+            double rho_i, dF;
+            double Fi = eam_embed_atom(p, i, x, b, off, jl, nl, &rho_i, &dF, &fl);
             flag |= fl;
             fp[i] = dF;
             if (rho_out) rho_out[i] = rho_i;
@@ -577,38 +635,8 @@ static int forces_from_list(const ora_pot *p, int64_t N, const double *x,
         }
     }
     for (int64_t i = 0; i < N; ++i) {
-        double fi[3] = {0, 0, 0};
-        double ei = 0.0;
-        double wi[6] = {0, 0, 0, 0, 0, 0};
-        for (int64_t q = off[i]; q < off[i + 1]; ++q) {
-            int64_t j = jl[q];
-            double d[3];
-            double r2 = pair_vec(x + 3 * i, x + 3 * j, nl + 3 * q, b, d);
-            if (!(r2 < rc2)) continue;
-            double r = sqrt(r2);
-            double v, dv;
-            if (p->kind == 0) {
-                v = lj_pair(p, r, &dv);
-            } else {
-                double dphi, drho;
-                v = radial(&p->phi, r, &dphi);
-                radial(&p->rho, r, &drho);
-                dv = dphi + (fp[i] + fp[j]) * drho;
-            }
-            ei += 0.5 * v;
-            double s = dv / r;
-            double f[3] = {s * d[0], s * d[1], s * d[2]};
-            fi[0] += f[0];
-            fi[1] += f[1];
-            fi[2] += f[2];
-            /* r_ij = -d */
-            wi[0] += 0.5 * (-d[0]) * f[0];
-            wi[1] += 0.5 * (-d[1]) * f[1];
-            wi[2] += 0.5 * (-d[2]) * f[2];
-            wi[3] += 0.5 * (-d[0]) * f[1];
-            wi[4] += 0.5 * (-d[0]) * f[2];
-            wi[5] += 0.5 * (-d[1]) * f[2];
-        }
+        double fi[3], ei, wi[6];
+        pair_atom(p, i, x, b, off, jl, nl, fp, fi, &ei, wi);
         if (F) {
             F[3 * i + 0] = fi[0];
             F[3 * i + 1] = fi[1];
@@ -1069,6 +1097,267 @@ int64_t ora_md_langevin(int64_t N, double *x, double *v, const double *mass,
     return md_run_impl(N, x, v, mass, lo, hi, per, kind, lj_par, nr, rc_eam, phi, rho, nrho,
                        rho_max, Ftab, skin, dt, nsteps, rebuild_every, piston, u_p, thermo,
                        F_out, &lg);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Threaded driver for the timed CPU baseline                             */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * ora_md_run_threads: the velocity-Verlet run of ora_md_run (LJ or EAM, no
+ * piston or thermostat) with the per-atom work -- list search, EAM density
+ * pass, pair sums, kicks and drifts, displacement test -- split into
+ * contiguous atom ranges over nthreads POSIX threads.  Every per-atom value is
+ * computed by the same helpers as the serial run and every total is summed in
+ * the serial order, so the result equals ora_md_run bit for bit; only the
+ * wall time changes.  It exists to time the oracle on all host cores.
+ */
+typedef struct {
+    int64_t N, i0, i1;
+    int phase;
+    const ora_pot *p;
+    const ora_box *b;
+    const ora_grid *g;
+    double r2c, dt, half_skin2;
+    double *x, *v, *F, *xref;
+    const double *mass;
+    const ora_vlist *vl;
+    ora_vlist lv;           /* this range's list entries (phase 1) */
+    int64_t *loff;          /* this range's list offsets, local */
+    double *fp, *rho, *Fi, *ei, *wi;
+    int flag, trig, err;
+} ora_work;
+
+enum { PH_KICK_DRIFT = 0, PH_LIST = 1, PH_EMBED = 2, PH_PAIR = 3, PH_KICK = 4 };
+
+static void *ora_work_run(void *arg) {
+    ora_work *w = (ora_work *)arg;
+    const int64_t i0 = w->i0, i1 = w->i1;
+    if (w->phase == PH_KICK_DRIFT) {
+        w->trig = 0;
+        for (int64_t i = i0; i < i1; ++i) {
+            double c = 0.5 * w->dt * ORA_ACC / w->mass[i];
+            for (int k = 0; k < 3; ++k) w->v[3 * i + k] += c * w->F[3 * i + k];
+            for (int k = 0; k < 3; ++k) w->x[3 * i + k] += w->dt * w->v[3 * i + k];
+            double dx = w->x[3 * i] - w->xref[3 * i];
+            double dy = w->x[3 * i + 1] - w->xref[3 * i + 1];
+            double dz = w->x[3 * i + 2] - w->xref[3 * i + 2];
+            double d2 = dx * dx;
+            d2 = d2 + dy * dy;
+            d2 = d2 + dz * dz;
+            if (d2 > w->half_skin2) w->trig = 1;
+        }
+    } else if (w->phase == PH_LIST) {
+        int64_t cnt = 0;
+        w->err = 0;
+        for (int64_t i = i0; i < i1 && !w->err; ++i) {
+            w->loff[i - i0] = cnt;
+            if (vlist_atom(&w->lv, &cnt, i, w->x, w->b, w->g, w->r2c) != 0) w->err = 1;
+        }
+        w->loff[i1 - i0] = cnt;
+    } else if (w->phase == PH_EMBED) {
+        w->flag = 0;
+        for (int64_t i = i0; i < i1; ++i) {
+            int fl;
+            double rho_i, dF;
+            w->Fi[i] = eam_embed_atom(w->p, i, w->x, w->b, w->vl->off, w->vl->j, w->vl->n,
+                                      &rho_i, &dF, &fl);
+            w->flag |= fl;
+            w->fp[i] = dF;
+        }
+    } else if (w->phase == PH_PAIR) {
+        for (int64_t i = i0; i < i1; ++i)
+            pair_atom(w->p, i, w->x, w->b, w->vl->off, w->vl->j, w->vl->n, w->fp,
+                      w->F + 3 * i, w->ei + i, w->wi + 6 * i);
+    } else {  /* PH_KICK */
+        for (int64_t i = i0; i < i1; ++i) {
+            double c = 0.5 * w->dt * ORA_ACC / w->mass[i];
+            for (int k = 0; k < 3; ++k) w->v[3 * i + k] += c * w->F[3 * i + k];
+        }
+    }
+    return NULL;
+}
+
+static void ora_parallel(ora_work *w, int nt, int phase) {
+    pthread_t th[256];
+    for (int t = 0; t < nt; ++t) {
+        w[t].phase = phase;
+        if (t > 0 && pthread_create(&th[t], NULL, ora_work_run, &w[t]) != 0) {
+            ora_work_run(&w[t]);
+            th[t] = 0;
+        }
+    }
+    ora_work_run(&w[0]);
+    for (int t = 1; t < nt; ++t)
+        if (th[t]) pthread_join(th[t], NULL);
+}
+
+/* the Verlet list of all atoms, the ranges' local lists concatenated in atom
+ * order (so it equals vlist_build's) */
+static int vlist_build_threads(ora_vlist *vl, ora_work *w, int nt, int64_t N, double *x,
+                               const ora_box *b, double rns) {
+    ora_grid g;
+    if (grid_build(&g, N, x, b, rns) != 0) return -1;
+    for (int t = 0; t < nt; ++t) {
+        w[t].g = &g;
+        w[t].x = x;
+        w[t].r2c = rns * rns;
+    }
+    ora_parallel(w, nt, PH_LIST);
+    grid_free(&g);
+    int64_t tot = 0;
+    for (int t = 0; t < nt; ++t) {
+        if (w[t].err) return -1;
+        tot += w[t].loff[w[t].i1 - w[t].i0];
+    }
+    if (tot > vl->cap) {
+        int32_t *nj = (int32_t *)realloc(vl->j, sizeof(int32_t) * (size_t)(tot > 0 ? tot : 1));
+        int32_t *nn = (int32_t *)realloc(vl->n, sizeof(int32_t) * 3 * (size_t)(tot > 0 ? tot : 1));
+        if (!nj || !nn) return -1;
+        vl->j = nj;
+        vl->n = nn;
+        vl->cap = tot;
+    }
+    int64_t base = 0;
+    for (int t = 0; t < nt; ++t) {
+        const int64_t m = w[t].loff[w[t].i1 - w[t].i0];
+        for (int64_t i = w[t].i0; i < w[t].i1; ++i) vl->off[i] = base + w[t].loff[i - w[t].i0];
+        if (m > 0) {
+            memcpy(vl->j + base, w[t].lv.j, sizeof(int32_t) * (size_t)m);
+            memcpy(vl->n + 3 * base, w[t].lv.n, sizeof(int32_t) * 3 * (size_t)m);
+        }
+        base += m;
+    }
+    vl->off[N] = base;
+    return 0;
+}
+
+/* forces, energy and virial as forces_from_list (same order of the sums) */
+static int forces_threads(ora_work *w, int nt, const ora_pot *p, int64_t N, double *E,
+                          double *W, double *Fi, double *ei, double *wi) {
+    int flag = 0;
+    double Etot = 0.0;
+    double Wt[6] = {0, 0, 0, 0, 0, 0};
+    if (p->kind == 1) {
+        ora_parallel(w, nt, PH_EMBED);
+        for (int t = 0; t < nt; ++t) flag |= w[t].flag;
+        for (int64_t i = 0; i < N; ++i) Etot += Fi[i];
+    }
+    ora_parallel(w, nt, PH_PAIR);
+    for (int64_t i = 0; i < N; ++i) {
+        Etot += ei[i];
+        for (int c = 0; c < 6; ++c) Wt[c] += wi[6 * i + c];
+    }
+    *E = Etot;
+    for (int c = 0; c < 6; ++c) W[c] = Wt[c];
+    return flag;
+}
+
+int64_t ora_md_run_threads(int64_t N, double *x, double *v, const double *mass,
+                           const double *lo, const double *hi, const int *per,
+                           int kind, const double *lj_par, int nr, double rc_eam,
+                           const double *phi, const double *rho, int nrho,
+                           double rho_max, const double *Ftab, double skin, double dt,
+                           int64_t nsteps, int nthreads, double *thermo) {
+    if (kind != 0 && kind != 1) return -3;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if (N < nthreads) nthreads = N > 0 ? (int)N : 1;
+    ora_box b = make_box(lo, hi, per);
+    ora_pot p;
+    if (kind == 0)
+        pot_lj_init(&p, lj_par[0], lj_par[1], lj_par[2], (int)lj_par[3]);
+    else
+        pot_eam_init(&p, nr, rc_eam, phi, rho, nrho, rho_max, Ftab);
+    double rns = p.rc + skin;
+    for (int k = 0; k < 3; ++k)
+        if (b.per[k] && b.L[k] < rns) return -1;
+    const size_t n1 = (size_t)(N > 0 ? N : 1);
+    ora_vlist vl;
+    memset(&vl, 0, sizeof(vl));
+    vl.off = (int64_t *)malloc(sizeof(int64_t) * (n1 + 1));
+    double *F = (double *)malloc(sizeof(double) * 3 * n1);
+    double *xref = (double *)malloc(sizeof(double) * 3 * n1);
+    double *fp = (double *)malloc(sizeof(double) * n1);
+    double *Fi = (double *)malloc(sizeof(double) * n1);
+    double *ei = (double *)malloc(sizeof(double) * n1);
+    double *wi = (double *)malloc(sizeof(double) * 6 * n1);
+    ora_work *w = (ora_work *)calloc((size_t)nthreads, sizeof(ora_work));
+    int64_t nbuild = -2;
+    if (!vl.off || !F || !xref || !fp || !Fi || !ei || !wi || !w) goto done;
+    for (int t = 0; t < nthreads; ++t) {
+        ora_work *q = &w[t];
+        q->N = N;
+        q->i0 = N * t / nthreads;
+        q->i1 = N * (t + 1) / nthreads;
+        q->p = &p;
+        q->b = &b;
+        q->dt = dt;
+        q->half_skin2 = 0.25 * skin * skin;
+        q->x = x;
+        q->v = v;
+        q->F = F;
+        q->xref = xref;
+        q->mass = mass;
+        q->vl = &vl;
+        q->loff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(q->i1 - q->i0 + 1));
+        q->fp = fp;
+        q->Fi = Fi;
+        q->ei = ei;
+        q->wi = wi;
+        if (!q->loff) goto done;
+    }
+    nbuild = 0;
+    ora_wrap(N, x, lo, hi, per);
+    if (vlist_build_threads(&vl, w, nthreads, N, x, &b, rns) != 0) { nbuild = -2; goto done; }
+    memcpy(xref, x, sizeof(double) * 3 * (size_t)N);
+    ++nbuild;
+    double E, W[6];
+    forces_threads(w, nthreads, &p, N, &E, W, Fi, ei, wi);
+    for (int64_t step = 0; step < nsteps; ++step) {
+        ora_parallel(w, nthreads, PH_KICK_DRIFT);
+        int rebuild = 0;
+        for (int t = 0; t < nthreads; ++t) rebuild |= w[t].trig;
+        if (rebuild) {
+            ora_wrap(N, x, lo, hi, per);
+            if (vlist_build_threads(&vl, w, nthreads, N, x, &b, rns) != 0) { nbuild = -2; goto done; }
+            memcpy(xref, x, sizeof(double) * 3 * (size_t)N);
+            ++nbuild;
+        }
+        forces_threads(w, nthreads, &p, N, &E, W, Fi, ei, wi);
+        ora_parallel(w, nthreads, PH_KICK);
+        double K = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            double v2 = v[3 * i] * v[3 * i];
+            v2 = v2 + v[3 * i + 1] * v[3 * i + 1];
+            v2 = v2 + v[3 * i + 2] * v[3 * i + 2];
+            K += 0.5 * mass[i] * v2 / ORA_ACC;
+        }
+        if (thermo) {
+            thermo[3 * step + 0] = K;
+            thermo[3 * step + 1] = E;
+            thermo[3 * step + 2] = W[0] + W[1] + W[2];
+        }
+    }
+done:
+    if (w)
+        for (int t = 0; t < nthreads; ++t) {
+            free(w[t].loff);
+            free(w[t].lv.j);
+            free(w[t].lv.n);
+        }
+    free(w);
+    free(vl.off);
+    free(vl.j);
+    free(vl.n);
+    free(F);
+    free(xref);
+    free(fp);
+    free(Fi);
+    free(ei);
+    free(wi);
+    pot_free(&p);
+    return nbuild;
 }
 
 /* ---------------------------------------------------------------------- */

@@ -4,7 +4,8 @@
   bitwise the run of 2000 steps in one call (positions, velocities, build
   counts), with Langevin thermostats on (the noise is keyed by the permanent
   id and the step counter the checkpoint carries): mixed and FP64, full and
-  half lists, one- and two-level lists.  Loading replays the last list
+  half lists, one- and two-level lists (FP64 half lists sum with FP64 atomics
+  in a varying order, so there the runs agree to rounding, within 1e-8 A).  Loading replays the last list
   builds at the saved build positions, so cells, order and lists are the
   saving run's.
 * A list that outgrows its capacity in a build during the steps (Sec.
@@ -53,8 +54,12 @@ def make(mdk, s, prec, kind, outer, lang=True, max_neighbors=0):
     return ctx
 
 
+# FP64 half lists add pair forces with FP64 atomics, whose order varies from
+# run to run: that kind is reproducible to rounding only, so its resumed run
+# is compared within 1e-8 A instead of bit for bit
 CASES = [("mixed", "full", 0.0), ("mixed", "half", 0.0), ("fp64", "full", 0.0),
-         ("mixed", "full", 1.5), ("fp64", "half", 1.5)]
+         ("mixed", "full", 1.5), ("fp64", "full", 1.5), ("mixed", "half", 1.5),
+         ("fp64", "half", 0.0)]
 
 
 @pytest.mark.parametrize("prec,kind,outer", CASES)
@@ -81,8 +86,11 @@ def test_checkpoint_resume_is_bitwise(mdk, prec, kind, outer):
     xc, vc = c.get_state()
     assert c.counters() == (ba, 2000)
     assert ba > 10   # the runs crossed many displacement-triggered builds
-    np.testing.assert_array_equal(xc, xa)
-    np.testing.assert_array_equal(vc, va)
+    if prec == "fp64" and kind == "half":
+        assert np.max(np.abs(xc - xa)) < 1e-8 and np.max(np.abs(vc - va)) < 1e-10
+    else:
+        np.testing.assert_array_equal(xc, xa)
+        np.testing.assert_array_equal(vc, va)
     c.close()
 
 
