@@ -14,6 +14,15 @@ one-level lists); the same trigger and the same lists either way.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config C] [--impl reference]
 
+The default run also reports, outside the timed region: the same workload on
+the FP64 path (`fp64_path`); the NVE drift of the mixed path over 10^4 steps and
+of the FP64 path over 2000 steps, each with its own throughput (`drift`); a
+1000-step steady-state segment with its list and full builds
+(`steady_state`); and the metric's EAM half (`eam`): the Cu-like cold-curve
+batch (64 uneven replicas, one context) and the Al-like bulk (256,000 atoms),
+each mixed against FP64 with rooflines and both drifts, plus the adjoint of
+the batch.  --no-eam, --drift-steps 0 and --steady-steps 0 skip them.
+
 Other workloads (--config): 0 LJ argon 256 atoms FP64; 1 Al-like EAM 256,000
 atoms FP64; 3 Al-like EAM shock slab (640,000 atoms, x free) with the rigid
 piston and the moving window, mixed; 4 Cu-like EAM cold curve, 64 uneven
@@ -22,7 +31,8 @@ sum_r E_r + sum_i |F_i - F_ref,i|^2.  --drift-steps S adds an NVE drift
 measurement (mixed S steps, FP64 --drift-fp64-steps steps).
 
 --impl reference times the CPU oracle (the FP64 C program written from the
-paper) on a bounded sample of the same workload on the host cores.
+paper; cell-list Verlet MD, threaded over all host cores for LJ and EAM) on a
+bounded sample of the same workload.
 Multi-GPU (torchrun): replicas only -- every rank runs its own copy of the
 workload on its own GPU; no data-path collective.
 """
@@ -250,22 +260,40 @@ def window_setup(ctx, wl):
                    2.0 * a, a)
 
 
-def drift_run(mdk, wl, prec, steps, every=100):
+DRIFT_BAR = 1e-5   # eV/atom per 10^4 steps (the mixed-precision drift criterion)
+
+
+def drift_run(mdk, wl, prec, steps, every=100, skin_outer=0.0):
     """NVE energy drift: E_tot / N sampled every `every` steps on the GPU, the
-    slope of its least-squares line scaled to 10^4 steps (eV/atom)."""
-    ctx = mdk.make_context(wl, precision=prec)
+    slope of its least-squares line scaled to 10^4 steps (eV/atom); the same
+    run's throughput (CUDA events around the steps, thermo samples included)."""
+    import torch
+    ctx = mdk.make_context(wl, precision=prec, skin_outer=skin_outer)
     ctx.set_thermo(every, capacity=steps // every + 4)
     ctx.build_neighbors(wl.rc, wl.skin)
-    ctx.step(wl.dt, steps, check=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    ctx.step(wl.dt, steps, check=False)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.check()
+    n = ctx.natoms()
     th = ctx.thermo()
     ctx.close()
     step = th[:, 0, 0]
     e = (th[:, :, 1] + th[:, :, 2]).sum(axis=1) / th[:, :, 3].sum(axis=1)
     slope = float(np.polyfit(step, e, 1)[0]) * 1e4
     return {"precision": prec, "steps": steps, "samples": int(step.shape[0]),
-            "slope_eV_per_atom_per_1e4_steps": slope,
+            "slope_eV_per_atom_per_1e4_steps": slope, "bar": DRIFT_BAR,
+            "within_bar": bool(abs(slope) <= DRIFT_BAR),
             "max_minus_min_eV_per_atom": float(e.max() - e.min()),
-            "E_per_atom_first_last": [float(e[0]), float(e[-1])]}
+            "E_per_atom_first_last": [float(e[0]), float(e[-1])],
+            "value": n * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "timing": "CUDA events around the whole run (default launch shape, thermo "
+                      f"samples every {every} steps included)"}
 
 
 def stationary_setup(ctx, wl, u_in=-0.05, u_p=0.015):
@@ -367,39 +395,69 @@ def _lattice_of(wl):
     return wl.eam.a0, 300.0, wl.eam.mass
 
 
-def _oracle_md(wl, x, v, s, nsteps):
+def host_cores():
+    """Host threads this process may run on (the oracle's thread count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def _oracle_md(wl, x, v, s, nsteps, threads=1):
+    """The oracle's cell-list velocity Verlet on the host: LJ and EAM on
+    `threads` threads (ora_md_run_threads: the serial run's values bit for
+    bit), BPNN on one thread."""
     import oracle
     if wl.potential == "bpnn":
         return oracle.md_bpnn(x, v, s.masses, s.lo, s.hi, s.periodic, wl.dt, nsteps, wl.skin,
                               wl.extra["bpnn"])
     kw = {"lj_params": wl.lj} if wl.potential == "lj" else {"tables": wl.tables}
-    return oracle.md_run(x, v, s.masses, s.lo, s.hi, s.periodic, wl.dt, nsteps, wl.skin, **kw)
+    return oracle.md_run_threads(x, v, s.masses, s.lo, s.hi, s.periodic, wl.dt, nsteps,
+                                 wl.skin, threads, **kw)
+
+
+def oracle_threads(wl):
+    return 1 if wl.potential == "bpnn" else host_cores()
 
 
 def oracle_rate(wl, n_cells, nsteps):
-    """Oracle (cell-list Verlet MD, FP64, one host thread) on an FCC n^3-cell
-    sub-box of the workload: returns atom-timesteps/s and the sample size."""
+    """Oracle (cell-list Verlet MD, FP64, all host cores for LJ and EAM) on an
+    FCC n^3-cell sub-box of the workload: atom-timesteps/s and the sample."""
     a, T, mass = _lattice_of(wl)
     rng = np.random.default_rng(100)
     s = W.lattice_system(rng, (n_cells,) * 3, a, mass, T)
     t0 = time.perf_counter()
-    _oracle_md(wl, s.x, s.v, s, nsteps)
+    _oracle_md(wl, s.x, s.v, s, nsteps, oracle_threads(wl))
     t = time.perf_counter() - t0
     return s.n * nsteps / t, s.n, t
 
 
+def sample_cells(wl, atom_steps_budget, small, cap=64):
+    """FCC cells per side of a sub-box with about atom_steps_budget atom-steps
+    of oracle work per timed step, sized from timing runs that grow the box
+    until a run is long enough to time (the threads' start-up costs dominate
+    tiny boxes)."""
+    n_cells = small
+    while True:
+        rate, n, t = oracle_rate(wl, n_cells, 2 if wl.potential == "bpnn" else 4)
+        want = int(round((rate * atom_steps_budget / 4) ** (1 / 3)))
+        if t > 0.5 or n_cells >= cap or want <= n_cells:
+            return int(max(small, min(cap, want)))
+        n_cells = min(cap, max(2 * n_cells, want // 2))
+
+
 def cpu_baseline(wl, budget_s=15.0):
-    # calibrate on a small box, then size the sample for ~budget_s of work
-    small = 3 if wl.potential == "bpnn" else 6   # BPNN: ~25 ms per atom-step
-    rate0, _, _ = oracle_rate(wl, small, 2 if wl.potential == "bpnn" else 4)
+    # size the sample for ~budget_s of work, then time it
+    small = 3 if wl.potential == "bpnn" else 8   # BPNN: ~25 ms per atom-step
     steps = 4 if wl.potential == "bpnn" else 20
-    target_atoms = rate0 * budget_s / steps
-    n_cells = int(max(small, min(40, round((target_atoms / 4) ** (1 / 3)))))
+    n_cells = sample_cells(wl, budget_s / steps, small)
     rate, n, t = oracle_rate(wl, n_cells, steps)
-    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+    nt = oracle_threads(wl)
+    return {"value": rate, "unit": UNIT, "cores": nt, "kind": "oracle",
             "sample": f"{n} atoms ({n_cells}^3 FCC cells of the same lattice, potential, "
                       f"temperature and dt), {steps} velocity-Verlet steps with Verlet-list "
-                      f"rebuilds, FP64, one host thread, {t:.1f} s"}
+                      f"rebuilds, FP64, cell-list oracle on {nt} host thread(s) "
+                      f"(ora_md_run_threads, bitwise the serial run), {t:.1f} s"}
 
 
 def run_reference(args, wl):
@@ -408,30 +466,211 @@ def run_reference(args, wl):
         return
     import oracle
     oracle.build()
+    nt = oracle_threads(wl)
     # size each step so that warmup + steps end within ~90 s
-    small = 3 if wl.potential == "bpnn" else 6
-    rate0, _, _ = oracle_rate(wl, small, 2 if wl.potential == "bpnn" else 4)
-    per_step_atoms = rate0 * 90.0 / max(1, args.steps + args.warmup)
-    n_cells = int(max(3, min(40, round((per_step_atoms / 4) ** (1 / 3)))))
+    small = 3 if wl.potential == "bpnn" else 8
+    n_cells = sample_cells(wl, 90.0 / max(1, args.steps + args.warmup), small)
     a, T, mass = _lattice_of(wl)
     s = W.lattice_system(np.random.default_rng(100), (n_cells,) * 3, a, mass, T)
-    out = _oracle_md(wl, s.x, s.v, s, args.warmup)
+    out = _oracle_md(wl, s.x, s.v, s, args.warmup, nt)
     t0 = time.perf_counter()
-    _oracle_md(wl, out["x"], out["v"], s, args.steps)
+    _oracle_md(wl, out["x"], out["v"], s, args.steps, nt)
     t = time.perf_counter() - t0
     val = s.n * args.steps / t
     sample = (f"{s.n} atoms ({n_cells}^3 FCC cells of the workload's lattice, potential, "
-              f"temperature and dt) per step, FP64 cell-list Verlet MD, one host thread")
+              f"temperature and dt) per step, FP64 cell-list Verlet MD on {nt} host "
+              f"thread(s)")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "atoms_per_step_sample": s.n},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": nt, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def fma_peaks(mdk):
+    """FMA pipe peaks measured on this device (the ALU rooflines' denominators)."""
+    try:
+        return {"fp64": mdk.fma_peak("fp64"), "mixed": mdk.fma_peak("mixed")}
+    except mdk.MDKError:
+        return None
+
+
+def roofline_for(wl, prec, kind, n_now, n_list, n_avg, n_rc, tpa, prof, ms, prof_steps, steps,
+                 hbm, peak_kind, fma_pk):
+    """The force pass's roofline record: algorithmic bytes (mixed) or FLOPs
+    (FP64, BPNN) over its CUDA-event time from the profiled segment."""
+    force_ms = prof["force_ms"] / max(1.0, prof["force_passes"])
+    bpa = algorithmic_bytes_per_atom(wl, prec, n_list, kind)
+    gbs = n_now * bpa / (force_ms / 1e3) / 1e9
+    if kind == "cells":
+        kdesc = (f"k_lj_cells<{prec}> (one warp per cell, neighbour cells tiled in shared "
+                 "memory, no list) with the fused velocity-Verlet update")
+    elif kind == "half":
+        kdesc = ((f"k_lj_half<{prec}> pair pass" if wl.potential == "lj" else
+                  f"k_rho_half + k_embed + k_eam_half<{prec}> passes") +
+                 " (half lists, accumulating atomics) + k_half_fin per-atom velocity-Verlet pass")
+    else:
+        kdesc = (("k_lj" if wl.potential == "lj" else "k_rho + k_eam") +
+                 f"<{prec}> force pass with the fused velocity-Verlet update")
+    common = {"kernel": kdesc, "force_ms": force_ms,
+              "force_share_of_step": prof["force_ms"] / (ms * prof_steps / steps),
+              "rebuild_share_of_step": prof["rebuild_ms"] / (ms * prof_steps / steps),
+              "timed_from": f"CUDA events around each of {int(prof['force_passes'])} force "
+                            f"passes of a {prof_steps}-step profiled segment"}
+    if wl.potential == "bpnn":
+        fpa = bpnn_flops_per_atom(wl.extra["bpnn"], n_rc)
+        tflops = n_now * fpa / (force_ms / 1e3) / 1e12
+        nominal = FP32_PEAK_TFLOPS if prec == "mixed" else FP64_PEAK_TFLOPS
+        pk = fma_pk[prec] if fma_pk else nominal
+        common["kernel"] = (f"k_bpnn<{prec}> (descriptors, network, gradients; one warp per "
+                            "atom) + k_half_fin per-atom velocity-Verlet pass")
+        return {"bound": "alu", "achieved": tflops, "peak": pk, "unit": "TFLOP/s",
+                "frac": tflops / pk, "traffic": None, "flops_per_atom": fpa,
+                "peak_kind": (("measured: FP32" if prec == "mixed" else "measured: FP64") +
+                              " FMA probe (mdk_fma_peak)") if fma_pk else "nominal",
+                "peak_nominal": nominal, **common}
+    if prec == "mixed":
+        tr = traffic_per_launch(wl, prec, n_now, kind, n_avg, tpa)
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                "frac": gbs / hbm, "traffic": tr, "bytes_per_atom": bpa,
+                "traffic_unit": "bytes per launch", "peak_kind": peak_kind, **common}
+    tflops = n_now * 0.5 * n_rc * FLOPS_PER_PAIR[wl.potential] / (force_ms / 1e3) / 1e12
+    pk = fma_pk["fp64"] if fma_pk else FP64_PEAK_TFLOPS
+    return {"bound": "alu", "achieved": tflops, "peak": pk,
+            "unit": "TFLOP/s", "frac": tflops / pk, "traffic": None,
+            "flops_per_pair": FLOPS_PER_PAIR[wl.potential],
+            "peak_kind": ("measured: FP64 FMA probe (mdk_fma_peak)" if fma_pk
+                          else "GB300 nominal dense FP64"),
+            "peak_nominal": FP64_PEAK_TFLOPS,
+            "hbm": {"achieved": gbs, "peak": hbm, "frac": gbs / hbm,
+                    "bytes_per_atom": bpa}, **common}
+
+
+def vjp_timing(mdk, ctx, wl, vjps, barrier):
+    """The adjoint of the cold-curve batch: forward pass, loss gradient and
+    mdk_eam_vjp, timed with CUDA events over `vjps` repetitions."""
+    import torch as _t
+    n_atoms = ctx.natoms()
+    stream = ctx.stream
+    x_now, _ = ctx.get_state()
+    Fref = _t.tensor(reference_forces(mdk, wl, x_now), device="cuda")
+    R = ctx.n_rep
+    Ed = _t.empty(R, dtype=_t.float64, device="cuda")
+    Fd = _t.empty((n_atoms, 3), dtype=_t.float64, device="cuda")
+    Wd = _t.empty((R, 6), dtype=_t.float64, device="cuda")
+    gE = _t.ones(R, dtype=_t.float64, device="cuda")
+    nk = 2 * wl.tables.nr + wl.tables.nrho
+    dth = _t.empty(nk, dtype=_t.float64, device="cuda")
+
+    def one():
+        ctx.compute_device(Ed, Fd, Wd)
+        gF = 2.0 * (Fd - Fref)          # d/dF of sum |F - F_ref|^2
+        ctx.eam_vjp_device(gE, gF, dth)
+
+    for _ in range(3):
+        one()
+    barrier()
+    ctx.profile(False)
+    v0 = _t.cuda.Event(enable_timing=True)
+    v1 = _t.cuda.Event(enable_timing=True)
+    v0.record(stream)
+    for _ in range(vjps):
+        one()
+    v1.record(stream)
+    barrier()
+    vms = v0.elapsed_time(v1) / vjps
+    n_rc = pair_count_within_rc(ctx, wl)
+    out = {"loss": "sum_r E_r + sum_i |F_i - F_ref,i|^2",
+           "F_ref": "analytic FS-EAM through 7168-knot tables",
+           "knots": nk, "ms_per_vjp": vms, "vjps": vjps,
+           "vjp_per_s": 1e3 / vms, "atoms": n_atoms,
+           "pair_evaluations_per_s": n_atoms * 0.5 * n_rc / (vms / 1e3),
+           "includes": "forward force pass + loss gradient + mdk_eam_vjp",
+           "gpu_launches": int(ctx.get_profile()["kernels"])}
+    ctx.check()
+    return out
+
+
+def measure(mdk, wl, prec, steps, warmup, barrier, hbm, peak_kind, fma_pk, outer_skin=0.0,
+            n_rc=None):
+    """One workload in one precision: autotuned launch, `warmup` untimed steps,
+    `steps` timed with CUDA events on the context's stream (inputs in HBM),
+    then a profiled segment for the force pass's roofline.  Returns the
+    record and the context."""
+    import torch
+    ctx = mdk.make_context(wl, precision=prec, skin_outer=outer_skin)
+    tpa, block, _ = ctx.autotune()
+    kind = ctx.list_kind
+    n_avg = float(ctx.neighbor_counts().mean()) if kind != "cells" else float("nan")
+    if n_rc is None:
+        n_rc = pair_count_within_rc(ctx, wl)
+    n_list = {"full": n_avg, "half": 0.5 * n_avg, "cells": 0.0}[kind]
+    ctx.step(wl.dt, warmup, check=True)
+    barrier()
+    b0 = ctx.build_counts()
+    ctx.profile(False)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    ctx.step(wl.dt, steps, check=False)
+    e1.record(ctx.stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = int(ctx.get_profile()["kernels"])
+    b1 = ctx.build_counts()
+    ctx.check()
+    prof_steps = max(20, min(steps, 200))
+    ctx.profile(True)
+    ctx.step(wl.dt, prof_steps, check=False)
+    prof = ctx.get_profile()
+    ctx.profile(False)
+    ctx.check()
+    n = ctx.natoms()
+    roof = roofline_for(wl, prec, kind, n, n_list, n_avg, n_rc, tpa, prof, ms, prof_steps, steps,
+                        hbm, peak_kind, fma_pk)
+    rec = {"workload": wl.name, "precision": prec, "atoms": n, "replicas": len(wl.systems),
+           "value": n * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+           "steps": steps, "warmup": warmup, "gpu_launches": launches,
+           "pair_interactions_per_s": n * steps / (ms / 1e3) * n_rc / 2.0,
+           "list_builds": b1[0] - b0[0], "full_builds": b1[1] - b0[1],
+           "launch": {"threads_per_atom": tpa, "block": block, "list": kind,
+                      "picked_by": "mdk_autotune"},
+           "roofline": roof}
+    return rec, ctx
+
+
+def eam_record(mdk, barrier, hbm, peak_kind, fma_pk, drift_steps, drift_fp64_steps, vjps):
+    """The metric's EAM half on one GPU: the Cu-like cold-curve batch (64
+    uneven replicas in one context, the batched path) and the Al-like bulk
+    (256,000 atoms), each mixed against FP64 with both NVE drifts, plus the
+    adjoint of the batch."""
+    import torch
+    out = {}
+    for key, wl, steps, fsteps in (("cu_coldcurve_batched", W.config4(), 500, 200),
+                                   ("al_bulk", W.config1(), 200, 100)):
+        mixed, ctx = measure(mdk, wl, "mixed", steps, 10, barrier, hbm, peak_kind, fma_pk)
+        rec = {"mixed": mixed}
+        if key == "cu_coldcurve_batched" and vjps > 0:
+            rec["vjp"] = vjp_timing(mdk, ctx, wl, vjps, barrier)
+        del ctx
+        torch.cuda.empty_cache()
+        fp64, ctx = measure(mdk, wl, "fp64", fsteps, 5, barrier, hbm, peak_kind, fma_pk)
+        del ctx
+        torch.cuda.empty_cache()
+        rec["fp64"] = fp64
+        rec["mixed_over_fp64"] = mixed["value"] / fp64["value"]
+        if drift_steps > 0:
+            rec["drift"] = [drift_run(mdk, wl, "mixed", drift_steps)]
+            if drift_fp64_steps > 0:
+                rec["drift"].append(drift_run(mdk, wl, "fp64", drift_fp64_steps))
+        torch.cuda.empty_cache()
+        out[key] = rec
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -465,9 +704,16 @@ def main():
                          "faster, else off)")
     ap.add_argument("--list", default=None, choices=("full", "half", "cells"),
                     help="with --launch: the Verlet-list kind (LJ; default full)")
-    ap.add_argument("--drift-steps", type=int, default=0,
-                    help="also run an NVE drift measurement of this many steps")
+    ap.add_argument("--drift-steps", type=int, default=None,
+                    help="NVE drift measurement of this many mixed steps (default: 10000 "
+                         "for the 8.4M-atom argon headline, else 0)")
     ap.add_argument("--drift-fp64-steps", type=int, default=2000)
+    ap.add_argument("--no-eam", action="store_true",
+                    help="skip the EAM record (Cu cold-curve batch and Al bulk, mixed "
+                         "against FP64, drifts, adjoint) of the default headline run")
+    ap.add_argument("--steady-steps", type=int, default=1000,
+                    help="headline: when --steps is shorter, also time this many steps "
+                         "(full builds of the two-level lists included)")
     args = ap.parse_args()
     if args.list and not args.launch:
         ap.error("--list goes with --launch (the autotuner picks the list kind)")
@@ -489,6 +735,12 @@ def main():
                         precision="mixed")
     if args.impl == "reference":
         return run_reference(args, wl)
+    # the default run is the headline: LJ argon 8.4M atoms (config 2), which
+    # also reports the NVE drift of both paths and the EAM record
+    headline = (args.config == 2 and not args.hugoniot and not args.bpnn and
+                not args.langevin and args.cells == 128)
+    if args.drift_steps is None:
+        args.drift_steps = 10000 if headline else 0
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -591,100 +843,37 @@ def main():
     ctx.check()
     n_mean = 0.5 * (n_start + ctx.natoms())
     value, ms = job_throughput(ms, n_mean, args.steps, dist, "cuda")
+    # a longer segment at the same settings: a short timed region may hold no
+    # full build of the two-level lists; this one shows the steady state
+    steady = None
+    if rank == 0 and world == 1 and headline and args.steady_steps > args.steps:
+        sb0 = ctx.build_counts()
+        barrier()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        ctx.step(wl.dt, args.steady_steps, check=False)
+        s1.record(stream)
+        barrier()
+        sms = s0.elapsed_time(s1)
+        sb1 = ctx.build_counts()
+        ctx.check()
+        steady = {"steps": args.steady_steps, "value": n_atoms * args.steady_steps / (sms / 1e3),
+                  "ms_per_step": sms / args.steady_steps, "list_builds": sb1[0] - sb0[0],
+                  "full_builds": sb1[1] - sb0[1],
+                  "note": "same context and settings as the timed region, right after it"}
 
     # dominant kernel: the fused force + integration pass
     hbm, peak_kind = peaks()
     n_now = ctx.natoms()
-    force_ms = prof["force_ms"] / max(1.0, prof["force_passes"])
-    bpa = algorithmic_bytes_per_atom(wl, prec, n_list, kind)
-    gbs = n_now * bpa / (force_ms / 1e3) / 1e9
-    if kind == "cells":
-        kdesc = (f"k_lj_cells<{prec}> (one warp per cell, neighbour cells tiled in shared "
-                 "memory, no list) with the fused velocity-Verlet update")
-    elif kind == "half":
-        kdesc = (f"k_lj_half<{prec}> pair pass (half lists, accumulating atomics) + "
-                 "k_half_fin per-atom velocity-Verlet pass")
-    else:
-        kdesc = (("k_lj" if wl.potential == "lj" else "k_rho + k_eam") +
-                 f"<{prec}> force pass with the fused velocity-Verlet update")
-    common = {"kernel": kdesc,
-              "force_share_of_step": prof["force_ms"] / (ms * prof_steps / args.steps),
-              "rebuild_share_of_step": prof["rebuild_ms"] / (ms * prof_steps / args.steps),
-              "timed_from": f"CUDA events around each of {int(prof['force_passes'])} force "
-                            f"passes of a {prof_steps}-step profiled segment"}
-    # FMA pipe peaks measured on this device (the ALU rooflines' denominators)
-    try:
-        fma_pk = {"fp64": mdk.fma_peak("fp64"), "mixed": mdk.fma_peak("mixed")}
-    except mdk.MDKError:
-        fma_pk = None
-    if wl.potential == "bpnn":
-        fpa = bpnn_flops_per_atom(wl.extra["bpnn"], n_rc)
-        tflops = n_now * fpa / (force_ms / 1e3) / 1e12
-        nominal = FP32_PEAK_TFLOPS if prec == "mixed" else FP64_PEAK_TFLOPS
-        pk = fma_pk[prec] if fma_pk else nominal
-        common["kernel"] = (f"k_bpnn<{prec}> (descriptors, network, gradients; one warp per "
-                            "atom) + k_half_fin per-atom velocity-Verlet pass")
-        roof = {"bound": "alu", "achieved": tflops, "peak": pk, "unit": "TFLOP/s",
-                "frac": tflops / pk, "traffic": None, "flops_per_atom": fpa,
-                "peak_kind": (("measured: FP32" if prec == "mixed" else "measured: FP64") +
-                              " FMA probe (mdk_fma_peak)") if fma_pk else "nominal",
-                "peak_nominal": nominal, **common}
-    elif prec == "mixed":
-        tr = traffic_per_launch(wl, prec, n_now, kind, n_avg, tpa)
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                "frac": gbs / hbm, "traffic": tr, "bytes_per_atom": bpa,
-                "traffic_unit": "bytes per launch", "peak_kind": peak_kind, **common}
-    else:
-        tflops = n_now * 0.5 * n_rc * FLOPS_PER_PAIR[wl.potential] / (force_ms / 1e3) / 1e12
-        pk = fma_pk["fp64"] if fma_pk else FP64_PEAK_TFLOPS
-        roof = {"bound": "alu", "achieved": tflops, "peak": pk,
-                "unit": "TFLOP/s", "frac": tflops / pk, "traffic": None,
-                "flops_per_pair": FLOPS_PER_PAIR[wl.potential],
-                "peak_kind": ("measured: FP64 FMA probe (mdk_fma_peak)" if fma_pk
-                              else "GB300 nominal dense FP64"),
-                "peak_nominal": FP64_PEAK_TFLOPS,
-                "hbm": {"achieved": gbs, "peak": hbm, "frac": gbs / hbm,
-                        "bytes_per_atom": bpa}, **common}
+    fma_pk = fma_peaks(mdk)
+    roof = roofline_for(wl, prec, kind, n_now, n_list, n_avg, n_rc, tpa, prof, ms, prof_steps,
+                        args.steps, hbm, peak_kind, fma_pk)
 
     # the adjoint of the cold-curve batch: forward pass, loss gradient and VJP
     vjp = None
     if args.config == 4 and args.vjps > 0:
-        import torch as _t
-        x_now, _ = ctx.get_state()
-        Fref = _t.tensor(reference_forces(mdk, wl, x_now), device="cuda")
-        R = ctx.n_rep
-        Ed = _t.empty(R, dtype=_t.float64, device="cuda")
-        Fd = _t.empty((n_atoms, 3), dtype=_t.float64, device="cuda")
-        Wd = _t.empty((R, 6), dtype=_t.float64, device="cuda")
-        gE = _t.ones(R, dtype=_t.float64, device="cuda")
-        nk = 2 * wl.tables.nr + wl.tables.nrho
-        dth = _t.empty(nk, dtype=_t.float64, device="cuda")
-
-        def one():
-            ctx.compute_device(Ed, Fd, Wd)
-            gF = 2.0 * (Fd - Fref)          # d/dF of sum |F - F_ref|^2
-            ctx.eam_vjp_device(gE, gF, dth)
-
-        for _ in range(3):
-            one()
-        barrier()
-        ctx.profile(False)
-        v0 = _t.cuda.Event(enable_timing=True)
-        v1 = _t.cuda.Event(enable_timing=True)
-        v0.record(stream)
-        for _ in range(args.vjps):
-            one()
-        v1.record(stream)
-        barrier()
-        vms = v0.elapsed_time(v1) / args.vjps
-        vjp = {"loss": "sum_r E_r + sum_i |F_i - F_ref,i|^2",
-               "F_ref": "analytic FS-EAM through 7168-knot tables",
-               "knots": nk, "ms_per_vjp": vms, "vjps": args.vjps,
-               "vjp_per_s": 1e3 / vms, "atoms": n_atoms,
-               "pair_evaluations_per_s": n_atoms * 0.5 * n_rc / (vms / 1e3),
-               "includes": "forward force pass + loss gradient + mdk_eam_vjp",
-               "gpu_launches": int(ctx.get_profile()["kernels"])}
-        ctx.check()
+        vjp = vjp_timing(mdk, ctx, wl, args.vjps, barrier)
 
     # end to end through the C ABI with host buffers: upload the state from
     # pinned memory, run the steps, read positions, velocities and energy back
@@ -746,10 +935,18 @@ def main():
         del c64
 
     drift = None
-    if rank == 0 and args.drift_steps > 0:
-        drift = [drift_run(mdk, wl, prec, args.drift_steps)]
+    if rank == 0 and world == 1 and args.drift_steps > 0:
+        torch.cuda.empty_cache()
+        drift = [drift_run(mdk, wl, prec, args.drift_steps, skin_outer=outer_skin)]
         if prec != "fp64" and args.drift_fp64_steps > 0:
-            drift.append(drift_run(mdk, wl, "fp64", args.drift_fp64_steps))
+            torch.cuda.empty_cache()
+            drift.append(drift_run(mdk, wl, "fp64", args.drift_fp64_steps,
+                                   skin_outer=outer_skin))
+    eam = None
+    if rank == 0 and world == 1 and headline and not args.no_eam:
+        torch.cuda.empty_cache()
+        eam = eam_record(mdk, barrier, hbm, peak_kind, fma_pk, 10000, args.drift_fp64_steps,
+                         args.vjps)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -784,6 +981,8 @@ def main():
             "fp64_path": fp64,
             "vjp": vjp,
             "drift": drift,
+            "steady_state": steady,
+            "eam": eam,
         }
         if lang:
             line["config"]["langevin"] = {"T_K": lang[0][2], "beta_per_fs": lang[0][4],
