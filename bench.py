@@ -269,6 +269,8 @@ def drift_run(mdk, wl, prec, steps, every=100, skin_outer=0.0):
     run's throughput (CUDA events around the steps, thermo samples included)."""
     import torch
     ctx = mdk.make_context(wl, precision=prec, skin_outer=skin_outer)
+    tpa, block, _ = ctx.autotune()
+    kind = ctx.list_kind
     ctx.set_thermo(every, capacity=steps // every + 4)
     ctx.build_neighbors(wl.rc, wl.skin)
     torch.cuda.synchronize()
@@ -292,8 +294,10 @@ def drift_run(mdk, wl, prec, steps, every=100, skin_outer=0.0):
             "max_minus_min_eV_per_atom": float(e.max() - e.min()),
             "E_per_atom_first_last": [float(e[0]), float(e[-1])],
             "value": n * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
-            "timing": "CUDA events around the whole run (default launch shape, thermo "
-                      f"samples every {every} steps included)"}
+            "launch": {"threads_per_atom": tpa, "block": block, "list": kind,
+                       "picked_by": "mdk_autotune"},
+            "timing": "CUDA events around the whole run (thermo samples every "
+                      f"{every} steps included)"}
 
 
 def stationary_setup(ctx, wl, u_in=-0.05, u_p=0.015):

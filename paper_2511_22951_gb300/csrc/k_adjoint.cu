@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_c(Sys s, EAMParams ep, AdjArg
     const V gi = GP::ld(gq + i);
     R hx, hy, hz;
     GP::h(s.grid[inf >> 8], hx, hy, hz);
+    h_scaled(hx, hy, hz);  // for s_scaled
     const int nn = min(s.nnbr[i], s.nmax);
     struct Rec {
       V p, g;
@@ -197,10 +198,10 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_c(Sys s, EAMParams ep, AdjArg
           return q;
         },
         [&](uint32_t ent, const Rec &q) {
-          const R dx = (R)(q.p.x - pi.x) + s_unit(R(0), ent, 0) * hx;
-          const R dy = (R)(q.p.y - pi.y) + s_unit(R(0), ent, 1) * hy;
-          const R dz = (R)(q.p.z - pi.z) + s_unit(R(0), ent, 2) * hz;
-          const R r2 = dx * dx + dy * dy + dz * dz;
+          const R dx = pvec((R)q.p.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
+          const R dy = pvec((R)q.p.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);
+          const R dz = pvec((R)q.p.z, (R)pi.z, s_scaled(R(0), ent, 2), hz);
+          const R r2 = r2_of(dx, dy, dz);
           if (r2 < rc2) {
             const R inv_r = GP::rsq(r2);
             const R u = r2 * inv_r * inv_dr;
@@ -307,6 +308,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_pair(Sys s, EAMParams ep, Adj
     const V gi = GP::ld(gq + i);
     R hx, hy, hz;
     GP::h(s.grid[inf >> 8], hx, hy, hz);
+    h_scaled(hx, hy, hz);  // for s_scaled
     const int nn = min(s.nnbr[i], s.nmax);
     const R half_gE = (R)(0.5 * a.gE[inf >> 8]);
     const R lam = (R)a.lam[i];
@@ -325,10 +327,10 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_pair(Sys s, EAMParams ep, Adj
           return q;
         },
         [&](uint32_t ent, const Rec &q) {
-          const R dx = (R)(q.p.x - pi.x) + s_unit(R(0), ent, 0) * hx;
-          const R dy = (R)(q.p.y - pi.y) + s_unit(R(0), ent, 1) * hy;
-          const R dz = (R)(q.p.z - pi.z) + s_unit(R(0), ent, 2) * hz;
-          const R r2 = dx * dx + dy * dy + dz * dz;
+          const R dx = pvec((R)q.p.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
+          const R dy = pvec((R)q.p.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);
+          const R dz = pvec((R)q.p.z, (R)pi.z, s_scaled(R(0), ent, 2), hz);
+          const R r2 = r2_of(dx, dy, dz);
           if (r2 < rc2) {
             const R inv_r = GP::rsq(r2);
             const R u = r2 * inv_r * inv_dr;

@@ -336,6 +336,7 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
   const V pi = GP::ld(pg + i);
   R hx, hy, hz;
   GP::h(s.grid[GP::info(pi) >> 8], hx, hy, hz);
+  h_scaled(hx, hy, hz);  // for s_scaled
   const int nn = min(s.nnbr[i], s.nmax);
   int n = 0;
   for (int k0 = 0; k0 < nn; k0 += 32) {
@@ -345,12 +346,12 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
     uint32_t j = 0;
     if (k < nn) {
       const uint32_t ent = s.nbr[ell_index(k, i, Nc)];
-      j = ent & kJMask;
+      j = (uint32_t)nbr_j(ent);
       const V pj = GP::ld(pg + j);
-      dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
-      dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
-      dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
-      r2 = dx * dx + dy * dy + dz * dz;
+      dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
+      dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);
+      dz = pvec((R)pj.z, (R)pi.z, s_scaled(R(0), ent, 2), hz);
+      r2 = r2_of(dx, dy, dz);
       keep = r2 < rc2;
     }
     const unsigned m = __ballot_sync(0xffffffffu, keep);

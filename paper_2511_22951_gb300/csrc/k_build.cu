@@ -474,7 +474,7 @@ __device__ __forceinline__ int image_of(int c, int sd, int nc, int per) {
 __device__ __noinline__ bool exact_pair(const Sys &s, const Grid &g, int i, uint32_t code, int c0,
                                         int c1, int c2, double rns2) {
   const size_t Nc = s.N_cap;
-  const int j = (int)(code & kJMask);
+  const int j = nbr_j(code);
   const int nx = image_of(c0, nbr_s(code, 0), g.nc[0], g.per[0]);
   const int ny = image_of(c1, nbr_s(code, 1), g.nc[1], g.per[1]);
   const int nz = image_of(c2, nbr_s(code, 2), g.nc[2], g.per[2]);
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s, ListOut lo_) {
           const bool ok = (FULL || j < b) && j != self && (!half || half_keep(i, j, s_pos));
           const bool acc = ok && r2f < lo_thr;
           band = band || (ok && !acc && !(r2f > hi_thr));
-          stage[count & 15][tx] = code | (uint32_t)j;  // kept only if accepted
+          stage[count & 15][tx] = code | ((uint32_t)j << 6);  // kept only if accepted
           count += acc ? 1 : 0;
         }
         if (band) {
@@ -584,8 +584,8 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s, ListOut lo_) {
             const bool ok = (FULL || j < b) && j != self && (!half || half_keep(i, j, s_pos));
             bool acc = ok && r2f < lo_thr;
             if (ok && !acc && !(r2f > hi_thr))
-              acc = exact_pair(s, g, i, code | (uint32_t)j, c0, c1, c2, rns2);
-            stage[count & 15][tx] = code | (uint32_t)j;
+              acc = exact_pair(s, g, i, code | ((uint32_t)j << 6), c0, c1, c2, rns2);
+            stage[count & 15][tx] = code | ((uint32_t)j << 6);
             count += acc ? 1 : 0;
           }
         }
@@ -709,12 +709,12 @@ __global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
       const int before = count;
       float4 pj[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) pj[u] = __ldg(s.pf + (k0 + u < n1 ? (int)(e[u] & kJMask) : i));
+      for (int u = 0; u < 4; ++u) pj[u] = __ldg(s.pf + (k0 + u < n1 ? nbr_j(e[u]) : i));
       bool band = false;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const uint32_t code = e[u];
-        const int j = (int)(code & kJMask);
+        const int j = nbr_j(code);
         const int sx = nbr_s(code, 0), sy = nbr_s(code, 1), sz = nbr_s(code, 2);
         const float dx = pj[u].x - (pi.x - (float)sx * g.hf[0]);
         const float dy = pj[u].y - (pi.y - (float)sy * g.hf[1]);
@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const uint32_t code = e[u];
-          const int j = (int)(code & kJMask);
+          const int j = nbr_j(code);
           const int sx = nbr_s(code, 0), sy = nbr_s(code, 1), sz = nbr_s(code, 2);
           const float dx = pj[u].x - (pi.x - (float)sx * g.hf[0]);
           const float dy = pj[u].y - (pi.y - (float)sy * g.hf[1]);

@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_rho(Sys s, EAMPara
     if (valid) {
       pi = GP::ld(pg + i);
       GP::h(s.grid[GP::info(pi) >> 8], hx, hy, hz);
+      h_scaled(hx, hy, hz);  // for s_scaled
       nn = min(s.nnbr[i], s.nmax);
     }
     Acc<R> rho;
@@ -67,10 +68,10 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_rho(Sys s, EAMPara
     walk<T>(
         s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pg + j); },
         [&](uint32_t ent, const V &pj) {
-          const R dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
-          const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
-          const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
-          const R r2 = dx * dx + dy * dy + dz * dz;
+          const R dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
+          const R dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);
+          const R dz = pvec((R)pj.z, (R)pi.z, s_scaled(R(0), ent, 2), hz);
+          const R r2 = r2_of(dx, dy, dz);
           if (r2 < rc2) {
             const R r = GP::sqr(r2);
             const R u = r * inv_dr;
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_eam(Sys s, EAMPara
       pi = GP::ld(pg + i);
       inf = GP::info(pi);
       GP::h(s.grid[inf >> 8], hx, hy, hz);
+      h_scaled(hx, hy, hz);  // for s_scaled
       fpi = fpa[i];
       nn = min(s.nnbr[i], s.nmax);
     }
@@ -139,10 +141,10 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_eam(Sys s, EAMPara
     walk<T>(
         s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pgf + j); },
         [&](uint32_t ent, const V &pj) {
-          const R dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
-          const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
-          const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
-          const R r2 = dx * dx + dy * dy + dz * dz;
+          const R dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
+          const R dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);
+          const R dz = pvec((R)pj.z, (R)pi.z, s_scaled(R(0), ent, 2), hz);
+          const R r2 = r2_of(dx, dy, dz);
           if (r2 < rc2) {
             const R inv_r = GP::rsq(r2);
             const R r = r2 * inv_r;

@@ -53,22 +53,23 @@ __global__ void __launch_bounds__(256, 2) k_rho_half(Sys s, EAMParams ep, StepAr
     const V pi = GP::ld(pg + i);
     R hx, hy, hz;
     GP::h(s.grid[GP::info(pi) >> 8], hx, hy, hz);
+    h_scaled(hx, hy, hz);  // for s_scaled
     const int nn = min(s.nnbr[i], s.nmax);
     Q rho = 0;
     walk<1>(
         s.nbr, Nc, i, nn, 0, [&](uint32_t j) { return GP::ld(pg + j); },
         [&](uint32_t ent, const V &pj) {
-          const R dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
-          const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
-          const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
-          const R r2 = dx * dx + dy * dy + dz * dz;
+          const R dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
+          const R dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);
+          const R dz = pvec((R)pj.z, (R)pi.z, s_scaled(R(0), ent, 2), hz);
+          const R r2 = r2_of(dx, dy, dz);
           if (r2 < rc2) {
             const R u = GP::sqr(r2) * inv_dr;
             int kk = (int)u;
             kk = kk > kmax ? kmax : kk;
             const Q q = H::q(GP::val1(rt, kk, u - (R)kk));
             rho += q;
-            H::red(acc + (ent & kJMask), q);
+            H::red(acc + nbr_j(ent), q);
           }
         },
         [] {});
@@ -127,16 +128,17 @@ __global__ void __launch_bounds__(256, 2) k_eam_half(Sys s, EAMParams ep, StepAr
     const V pi = GP::ld(pg + i);
     R hx, hy, hz;
     GP::h(s.grid[GP::info(pi) >> 8], hx, hy, hz);
+    h_scaled(hx, hy, hz);  // for s_scaled
     const R fpi = fpa[i];
     const int nn = min(s.nnbr[i], s.nmax);
     Q fx = 0, fy = 0, fz = 0, e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     walk<1>(
         s.nbr, Nc, i, nn, 0, [&](uint32_t j) { return GP::ld(pgf + j); },
         [&](uint32_t ent, const V &pj) {
-          const R dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
-          const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
-          const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
-          const R r2 = dx * dx + dy * dy + dz * dz;
+          const R dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
+          const R dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);
+          const R dz = pvec((R)pj.z, (R)pi.z, s_scaled(R(0), ent, 2), hz);
+          const R r2 = r2_of(dx, dy, dz);
           if (r2 < rc2) {
             const R inv_r = GP::rsq(r2);
             const R u = r2 * inv_r * inv_dr;
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(256, 2) k_eam_half(Sys s, EAMParams ep, StepAr
             const R fr = (dphi + (fpi + GP::fp_of(pj)) * drho) * inv_dr * inv_r;  // V'(r)/r
             if (sizeof(R) == 4) bad = bad || !(fabs(fr) < fr_max);
             const Q qx = H::q(fr * dx), qy = H::q(fr * dy), qz = H::q(fr * dz);
-            const size_t j = ent & kJMask;
+            const size_t j = (size_t)nbr_j(ent);
             fx += qx;
             fy += qy;
             fz += qz;

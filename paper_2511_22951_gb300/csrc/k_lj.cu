@@ -32,6 +32,114 @@ constexpr int lj_min_blocks() {
   return sizeof(typename G<P>::R) == 4 ? 4 : 2;
 }
 
+// ---- the mixed path: two list entries per instruction ------------------------
+// GB300's packed FP32 instructions (FADD2 / FMUL2 / FFMA2) apply one operation
+// to two FP32 lanes of a register pair, so two list entries share every
+// floating-point instruction of the pair vector, the distance, the LJ force
+// and the accumulation; the issue slots saved go to the gathers and the list
+// decoding.  Each lane's arithmetic is the scalar path's (same roundings, FMA
+// where that path contracts).  Entries past the list end read a far-away
+// record (r^2 ~ 1e36 > rc^2), so the cutoff test is the only mask.  ENERGY
+// passes take the same walk (identical forces) and add the pair energies and
+// virials in FP64.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+template <int T, int SHIFT, bool ENERGY>
+__device__ __forceinline__ void lj_walk_packed(const Sys &s, const float4 *__restrict__ pg,
+                                               int i, int nn, int t, const float4 pi,
+                                               float hx, float hy, float hz,
+                                               const LJc<float> &lc, Acc<float> &fx,
+                                               Acc<float> &fy, Acc<float> &fz, double &esum,
+                                               double (&w)[6]) {
+  const size_t Nc = s.N_cap;
+  const size_t gstride = Nc * 2;  // uint4 per group row
+  const uint4 *__restrict__ row = reinterpret_cast<const uint4 *>(s.nbr) + (size_t)i * 2 +
+                                  (size_t)t * gstride;
+  const float2 mpx = f2(-pi.x, -pi.x), mpy = f2(-pi.y, -pi.y), mpz = f2(-pi.z, -pi.z);
+  const float2 hx2 = f2(hx, hx), hy2 = f2(hy, hy), hz2 = f2(hz, hz);
+  // minus the magic constants of s_scaled (2^23 + 4^d)
+  const float2 k0 = f2(-8388609.0f, -8388609.0f), k1 = f2(-8388612.0f, -8388612.0f),
+               k2 = f2(-8388624.0f, -8388624.0f);
+  const float2 sig2 = f2(lc.sig2, lc.sig2), meps24 = f2(-lc.eps24, -lc.eps24);
+  const float2 two = f2(2.0f, 2.0f), mone = f2(-1.0f, -1.0f);
+  const float4 far = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  uint4 na = make_uint4(0, 0, 0, 0), nb = na;
+  if (kGroup * t < nn) {
+    na = __ldcs(row);
+    nb = __ldcs(row + 1);
+  }
+  for (int k = kGroup * t; k < nn; k += kGroup * T) {
+    const uint4 ga = na, gb = nb;
+    row += gstride * T;
+    if (k + kGroup * T < nn) {
+      na = __ldcs(row);
+      nb = __ldcs(row + 1);
+    }
+    const uint32_t e[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
+    const int m = nn - k;  // valid entries in this group
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float4 q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        q[u] = 4 * h + u < m ? __ldg(pg + nbr_j(e[4 * h + u])) : far;
+      float2 bx = f2(0.f, 0.f), by = bx, bz = bx;
+#pragma unroll
+      for (int pr = 0; pr < 2; ++pr) {
+        const uint32_t ea = e[4 * h + 2 * pr], eb = e[4 * h + 2 * pr + 1];
+        const float4 qa = q[2 * pr], qb = q[2 * pr + 1];
+        // stencil shifts s_d 4^d, then d = (p_j - p_i) + s h (h pre-scaled)
+        const float2 sx = __fadd2_rn(f2(__uint_as_float((ea & 3u) | 0x4B000000u),
+                                        __uint_as_float((eb & 3u) | 0x4B000000u)), k0);
+        const float2 sy = __fadd2_rn(f2(__uint_as_float((ea & 12u) | 0x4B000000u),
+                                        __uint_as_float((eb & 12u) | 0x4B000000u)), k1);
+        const float2 sz = __fadd2_rn(f2(__uint_as_float((ea & 48u) | 0x4B000000u),
+                                        __uint_as_float((eb & 48u) | 0x4B000000u)), k2);
+        const float2 dx = __ffma2_rn(sx, hx2, __fadd2_rn(f2(qa.x, qb.x), mpx));
+        const float2 dy = __ffma2_rn(sy, hy2, __fadd2_rn(f2(qa.y, qb.y), mpy));
+        const float2 dz = __ffma2_rn(sz, hz2, __fadd2_rn(f2(qa.z, qb.z), mpz));
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        // V'(r)/r = -24 eps (2 (sigma/r)^12 - (sigma/r)^6) / r^2
+        const float2 inv = f2(__fdividef(1.0f, r2.x), __fdividef(1.0f, r2.y));
+        const float2 s2 = __fmul2_rn(sig2, inv);
+        const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
+        float2 fr = __fmul2_rn(__fmul2_rn(meps24, __ffma2_rn(s6, two, mone)),
+                               __fmul2_rn(s6, inv));
+        if (SHIFT == 2) {  // shifted force: - V'(rc) / r
+          fr.x -= lc.durc / sqrtf(r2.x);
+          fr.y -= lc.durc / sqrtf(r2.y);
+        }
+        const bool ina = r2.x < lc.rc2, inb = r2.y < lc.rc2;
+        fr.x = ina ? fr.x : 0.0f;
+        fr.y = inb ? fr.y : 0.0f;
+        bx = __ffma2_rn(fr, dx, bx);
+        by = __ffma2_rn(fr, dy, by);
+        bz = __ffma2_rn(fr, dz, bz);
+        if (ENERGY) {  // energy and virial from the same pair values, FP64 sums
+#pragma unroll
+          for (int l = 0; l < 2; ++l) {
+            const float s6l = l ? s6.y : s6.x, frl = l ? fr.y : fr.x;
+            const float dxl = l ? dx.y : dx.x, dyl = l ? dy.y : dy.x, dzl = l ? dz.y : dz.x;
+            float v = lc.eps4 * (s6l * s6l - s6l) - lc.ush;
+            if (SHIFT == 2) v -= (sqrtf(l ? r2.y : r2.x) - lc.rcut) * lc.durc;
+            if (l ? inb : ina) esum += 0.5 * (double)v;
+            const float hf = -0.5f * frl;  // r_ij = -d
+            w[0] += (double)(hf * dxl * dxl);
+            w[1] += (double)(hf * dyl * dyl);
+            w[2] += (double)(hf * dzl * dzl);
+            w[3] += (double)(hf * dxl * dyl);
+            w[4] += (double)(hf * dxl * dzl);
+            w[5] += (double)(hf * dyl * dzl);
+          }
+        }
+      }
+      fx.add(bx.x + bx.y);
+      fy.add(by.x + by.y);
+      fz.add(bz.x + bz.y);
+    }
+  }
+}
+
 template <class P, int MODE, bool ENERGY, int SHIFT, int T>
 __global__ void __launch_bounds__(256, lj_min_blocks<P>()) k_lj(Sys s, LJParams lp, StepArgs a) {
   using GP = G<P>;
@@ -59,19 +167,33 @@ __global__ void __launch_bounds__(256, lj_min_blocks<P>()) k_lj(Sys s, LJParams 
       pi = GP::ld(pg + i);
       inf = GP::info(pi);
       GP::h(s.grid[inf >> 8], hx, hy, hz);
+      h_scaled(hx, hy, hz);  // for s_scaled
       nn = min(s.nnbr[i], s.nmax);
     }
     Acc<R> fx, fy, fz;
     // energy and virial sums in FP64 (ENERGY passes only: thermo and compute)
     double e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     R bx = 0, by = 0, bz = 0;  // block sums of four pairs
+    if constexpr (sizeof(R) == 4) {
+      double wv[6] = {0, 0, 0, 0, 0, 0};
+      lj_walk_packed<T, SHIFT, ENERGY>(s, reinterpret_cast<const float4 *>(pg), i, nn, tl.t,
+                                       *reinterpret_cast<const float4 *>(&pi), hx, hy, hz,
+                                       *reinterpret_cast<const LJc<float> *>(&lc), fx, fy, fz,
+                                       e, wv);
+      w0 = wv[0];
+      w1 = wv[1];
+      w2 = wv[2];
+      w3 = wv[3];
+      w4 = wv[4];
+      w5 = wv[5];
+    } else
     walk<T>(
         s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pg + j); },
         [&](uint32_t ent, const V &pj) {
-          const R dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
-          const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
-          const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
-          const R r2 = dx * dx + dy * dy + dz * dz;
+          const R dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
+          const R dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);
+          const R dz = pvec((R)pj.z, (R)pi.z, s_scaled(R(0), ent, 2), hz);
+          const R r2 = r2_of(dx, dy, dz);
           if (r2 < lc.rc2) {
             R fr, v;
             lj_pair<GP, SHIFT, ENERGY>(lc, r2, fr, v);

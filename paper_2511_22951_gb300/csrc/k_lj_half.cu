@@ -61,22 +61,23 @@ __global__ void __launch_bounds__(256, half_min_blocks<P>(ENERGY))
   const V pi = GP::ld(pg + i);
   R hx, hy, hz;
   GP::h(s.grid[GP::info(pi) >> 8], hx, hy, hz);
+  h_scaled(hx, hy, hz);  // for s_scaled
   const int nn = min(s.nnbr[i], s.nmax);
   Q fx = 0, fy = 0, fz = 0, e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
   bool bad = false;
   walk<1>(
       s.nbr, Nc, i, nn, 0, [&](uint32_t j) { return GP::ld(pg + j); },
       [&](uint32_t ent, const V &pj) {
-        const R dx = (R)(pj.x - pi.x) + s_unit(R(0), ent, 0) * hx;
-        const R dy = (R)(pj.y - pi.y) + s_unit(R(0), ent, 1) * hy;
-        const R dz = (R)(pj.z - pi.z) + s_unit(R(0), ent, 2) * hz;
-        const R r2 = dx * dx + dy * dy + dz * dz;
+        const R dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
+        const R dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);
+        const R dz = pvec((R)pj.z, (R)pi.z, s_scaled(R(0), ent, 2), hz);
+        const R r2 = r2_of(dx, dy, dz);
         if (r2 < lc.rc2) {
           R fr, v;
           lj_pair<GP, SHIFT, ENERGY>(lc, r2, fr, v);
           if (sizeof(R) == 4) bad = bad || !(fabs(fr) < fr_max);
           const Q qx = H::q(fr * dx), qy = H::q(fr * dy), qz = H::q(fr * dz);
-          const size_t j = ent & kJMask;
+          const size_t j = (size_t)nbr_j(ent);
           fx += qx;
           fy += qy;
           fz += qz;

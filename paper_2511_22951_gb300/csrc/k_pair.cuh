@@ -193,16 +193,42 @@ __device__ __forceinline__ void embed_fp64(const Sys &s, const EAMParams &ep, do
 }
 
 // ---- the neighbour walk ------------------------------------------------------------
-// Unit stencil offset s_d in {-1, 0, 1} of a list entry, exactly, in the pair
-// precision, without an int-to-float conversion: the 2-bit code c = s_d + 1 is
-// placed in the low mantissa bits of 2^23 (2^52) and 2^23 + 1 (2^52 + 1) is
-// subtracted.
-__device__ __forceinline__ float s_unit(float, uint32_t e, int d) {
-  return __uint_as_float(((e >> (26 + 2 * d)) & 3u) | 0x4B000000u) - 8388609.0f;
+// Stencil offset of a list entry times 4^d, exactly, in the pair precision,
+// without an int-to-float conversion: the entry's 2-bit code c = s_d + 1 sits
+// at bits 2d..2d+1, so (e & (3 << 2d)) = 4^d c lands in the low mantissa bits
+// of 2^23 (2^52) with one AND/OR, and 2^23 + 4^d (2^52 + 4^d) is subtracted.
+// With the cell size pre-scaled by 4^-d (an exact power-of-two scaling),
+// s_scaled(e, d) * (h_d / 4^d) is exactly s_d h_d.
+__device__ __forceinline__ float s_scaled(float, uint32_t e, int d) {
+  return __uint_as_float((e & (3u << (2 * d))) | 0x4B000000u) - (8388608.0f + (float)(1 << (2 * d)));
 }
-__device__ __forceinline__ double s_unit(double, uint32_t e, int d) {
-  return __longlong_as_double((long long)((e >> (26 + 2 * d)) & 3u) | 0x4330000000000000LL) -
-         4503599627370497.0;
+__device__ __forceinline__ double s_scaled(double, uint32_t e, int d) {
+  return __longlong_as_double((long long)(e & (3u << (2 * d))) | 0x4330000000000000LL) -
+         (4503599627370496.0 + (double)(1 << (2 * d)));
+}
+// The pair vector component (p_j - p_i) + s h and r^2, rounded in one fixed
+// order that every list kernel (and the packed LJ walk) shares: the
+// difference, then the shift by one FMA; r^2 = fma(dz, dz, fma(dy, dy, dx dx)).
+// Seen from j the vector is exactly minus the one seen from i, so both atoms
+// of a pair get the same r^2, bit for bit, and the same cutoff decision.
+__device__ __forceinline__ float pvec(float pj, float pi, float sh, float h) {
+  return __fmaf_rn(sh, h, __fsub_rn(pj, pi));
+}
+__device__ __forceinline__ double pvec(double pj, double pi, double sh, double h) {
+  return __fma_rn(sh, h, __dsub_rn(pj, pi));
+}
+__device__ __forceinline__ float r2_of(float dx, float dy, float dz) {
+  return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+__device__ __forceinline__ double r2_of(double dx, double dy, double dz) {
+  return __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+}
+
+// the cell size scaled for s_scaled: (h_x, h_y / 4, h_z / 16)
+template <class R>
+__device__ __forceinline__ void h_scaled(R &hx, R &hy, R &hz) {
+  hy *= R(0.25);
+  hz *= R(0.0625);
 }
 
 // Walk the list of one atom with T lanes: lane t takes the groups of 8 list
@@ -239,7 +265,7 @@ __device__ __forceinline__ void walk(const uint32_t *__restrict__ nbr, size_t Nc
       Rec q[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (4 * h + u < m) q[u] = load(e[4 * h + u] & kJMask);
+        if (4 * h + u < m) q[u] = load((uint32_t)nbr_j(e[4 * h + u]));
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         if (4 * h + u < m) body(e[4 * h + u], q[u]);

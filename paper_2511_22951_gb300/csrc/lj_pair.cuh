@@ -28,12 +28,17 @@ struct LJc {
 };
 
 // For r^2 < rc^2: fr = V'(r) / r, and with ENERGY the pair energy v = V(r).
+// FP32: rounded in the packed LJ walk's order, fr = (-24 eps (2 s6 - 1))
+// (s6 / r^2), so every mixed LJ kernel gives a pair the same force.
 template <class GP, int SHIFT, bool ENERGY, class R>
 __device__ __forceinline__ void lj_pair(const LJc<R> &c, R r2, R &fr, R &v) {
   const R inv = GP::rcp(r2);
   const R s2 = c.sig2 * inv;
   const R s6 = s2 * s2 * s2;
-  fr = -c.eps24 * (R(2) * s6 * s6 - s6) * inv;
+  if constexpr (sizeof(R) == 4)
+    fr = __fmul_rn(__fmul_rn(-c.eps24, __fmaf_rn(s6, 2.0f, -1.0f)), __fmul_rn(s6, inv));
+  else
+    fr = -c.eps24 * (R(2) * s6 * s6 - s6) * inv;
   R r = 0;
   if (SHIFT == 2) {
     r = GP::sqr(r2);

@@ -1488,11 +1488,11 @@ int mdk_get_neighbors(mdk_ctx *c, int64_t *offsets, int32_t *jout, int32_t *img)
       const Grid &g = c->grids[info[(size_t)i] >> 8];
       for (int k = 0; k < k_n; ++k) {
         const uint32_t e = buf[(size_t)(k / kGroup) * row + (size_t)(i - a) * kGroup + k % kGroup];
-        const int j = (int)(e & kJMask);
+        const int j = nbr_j(e);
         if (jout) jout[base + k] = id[(size_t)j];
         if (img)
           for (int d = 0; d < 3; ++d) {
-            const int sd = (int)((e >> (26 + 2 * d)) & 3u) - 1;
+            const int sd = nbr_s(e, d);
             const int cd = cell_coord(cellc[(size_t)i], d) + sd;
             int n = 0;
             if (g.per[d]) n = cd < 0 ? -1 : (cd >= g.nc[d] ? 1 : 0);

@@ -13,8 +13,10 @@
 //   cell buckets  : n_cells real cells + 1 bucket for atoms a moving window
 //                   deletes (the counting sort moves them past the kept atoms)
 //   nbr           : Verlet lists in groups of 8 entries per atom (ell_index),
-//                   packed j (bits 0-25) | (s_x+1) << 26 | (s_y+1) << 28 |
-//                   (s_z+1) << 30, s = stencil offset of j's cell
+//                   packed (s_x+1) | (s_y+1) << 2 | (s_z+1) << 4 | j << 6,
+//                   s = stencil offset of j's cell; each 2-bit code sits in
+//                   place, so one AND with a constant exponent turns it
+//                   into a float (s_scaled)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,7 +33,6 @@ constexpr double kHalfScale = 1099511627776.0;
 
 constexpr int kMaxTypes = 16;
 constexpr int kMaxLang = 8;  // Langevin regions
-constexpr uint32_t kJMask = (1u << 26) - 1u;
 constexpr uint32_t kInfoPiston = 1u << 4;
 constexpr uint32_t kInfoFar = 1u << 5;
 
@@ -281,12 +282,13 @@ __host__ __device__ __forceinline__ size_t ell_index(int k, int i, size_t Nc) {
   return ((size_t)(k >> 3) * Nc + (size_t)i) * kGroup + (size_t)(k & 7);
 }
 
-__device__ __forceinline__ uint32_t pack_nbr(int j, int sx, int sy, int sz) {
-  return (uint32_t)j | ((uint32_t)(sx + 1) << 26) | ((uint32_t)(sy + 1) << 28) |
-         ((uint32_t)(sz + 1) << 30);
+__host__ __device__ __forceinline__ uint32_t pack_nbr(int j, int sx, int sy, int sz) {
+  return ((uint32_t)j << 6) | (uint32_t)(sx + 1) | ((uint32_t)(sy + 1) << 2) |
+         ((uint32_t)(sz + 1) << 4);
 }
-__device__ __forceinline__ int nbr_s(uint32_t e, int d) {
-  return (int)((e >> (26 + 2 * d)) & 3u) - 1;
+__host__ __device__ __forceinline__ int nbr_j(uint32_t e) { return (int)(e >> 6); }
+__host__ __device__ __forceinline__ int nbr_s(uint32_t e, int d) {
+  return (int)((e >> (2 * d)) & 3u) - 1;
 }
 __host__ __device__ __forceinline__ uint32_t pack_cell(int cx, int cy, int cz) {
   return (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);

@@ -3,10 +3,11 @@ workload (LJ, 80 K, thermalised for 300 steps).
 
 The mixed full-list kernels sum each atom's FP32 pair forces with a
 compensated (Kahan) FP32 sum over blocks of four pairs.  The mixed half-list
-kernels evaluate the same pair terms -- bitwise the same values: the pair
-vector seen from j is exactly minus the one seen from i, for the same cells
--- and sum them in 64-bit fixed point (unit 2^-40 eV/A), exactly up to one
-rounding of each term.  With both lists built at the same positions (same
+kernels evaluate the same pairs -- bitwise the same pair vectors (seen from j
+the vector is exactly minus the one seen from i, for the same cells, rounded
+in the same order) and the same force factors V'(r)/r -- and sum the terms
+in 64-bit fixed point (unit 2^-40 eV/A), exactly up to one rounding of each
+term.  With both lists built at the same positions (same
 cells, same FP32 offsets), the difference of the two force sets is therefore
 the error of the compensated FP32 sum against an exact (FP64-quality) sum of
 the same terms.  It must sit far below the mixed-path bar (RMS 1e-5): the
