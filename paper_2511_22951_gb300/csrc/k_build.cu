@@ -555,18 +555,31 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s, ListOut lo_) {
       // positive stencil offset only (its mirror has the negative one)
       const bool s_pos = sz > 0 || (sz == 0 && (sy > 0 || (sy == 0 && sx > 0)));
       // blocks of four candidates; FULL: all four inside the cell's range
+      const float2 mqx = make_float2(-qx, -qx), mqy = make_float2(-qy, -qy),
+                   mqz = make_float2(-qz, -qz);
       auto block4 = [&](const int j0, auto full) {
         constexpr bool FULL = decltype(full)::value;
         const int before = count;
         float4 pj[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) pj[u] = __ldg(s.pf + (FULL ? j0 + u : min(j0 + u, b - 1)));
+        // r^2 of two candidates per packed FP32 instruction
+        float r2v[4];
+#pragma unroll
+        for (int pr = 0; pr < 2; ++pr) {
+          const float4 &qa = pj[2 * pr], &qb = pj[2 * pr + 1];
+          const float2 dx = __fadd2_rn(make_float2(qa.x, qb.x), mqx);
+          const float2 dy = __fadd2_rn(make_float2(qa.y, qb.y), mqy);
+          const float2 dz = __fadd2_rn(make_float2(qa.z, qb.z), mqz);
+          const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+          r2v[2 * pr] = r2.x;
+          r2v[2 * pr + 1] = r2.y;
+        }
         bool band = false;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int j = j0 + u;
-          const float dx = pj[u].x - qx, dy = pj[u].y - qy, dz = pj[u].z - qz;
-          const float r2f = dx * dx + dy * dy + dz * dz;
+          const float r2f = r2v[u];
           const bool ok = (FULL || j < b) && j != self && (!half || half_keep(i, j, s_pos));
           const bool acc = ok && r2f < lo_thr;
           band = band || (ok && !acc && !(r2f > hi_thr));
@@ -579,8 +592,7 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s, ListOut lo_) {
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int j = j0 + u;
-            const float dx = pj[u].x - qx, dy = pj[u].y - qy, dz = pj[u].z - qz;
-            const float r2f = dx * dx + dy * dy + dz * dz;
+            const float r2f = r2v[u];
             const bool ok = (FULL || j < b) && j != self && (!half || half_keep(i, j, s_pos));
             bool acc = ok && r2f < lo_thr;
             if (ok && !acc && !(r2f > hi_thr))
@@ -618,11 +630,23 @@ __global__ void __launch_bounds__(kBlk) k_outer_disp(Sys s) {
   const size_t Nc = s.N_cap;
   double m = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const double dx = s.x[i] - s.xfull[i], dy = s.x[Nc + i] - s.xfull[Nc + i],
-                 dz = s.x[2 * Nc + i] - s.xfull[2 * Nc + i];
+    const double xv = s.x[i], yv = s.x[Nc + i], zv = s.x[2 * Nc + i];
+    const double dx = xv - s.xfull[i], dy = yv - s.xfull[Nc + i], dz = zv - s.xfull[2 * Nc + i];
     const double d2 = dx * dx + dy * dy + dz * dz;
     // a non-finite position forces a full build (whose binning reports it)
     m = d2 == d2 ? fmax(m, d2) : INFINITY;
+    // so does an atom (not flagged far) that left the |p| <= 2h range the FP32
+    // pre-filter's error bound assumes (possible along a free dimension):
+    // the full build re-bins it and flags it far if it is still outside
+    const uint32_t inf = s.info[i];
+    if (!(inf & kInfoFar)) {
+      const Grid &g = s.grid[inf >> 8];
+      const uint32_t cc = s.cellc[i];
+      if (!(fabs(xv - cell_center(g, 0, cell_coord(cc, 0))) <= 2.0 * g.h[0] &&
+            fabs(yv - cell_center(g, 1, cell_coord(cc, 1))) <= 2.0 * g.h[1] &&
+            fabs(zv - cell_center(g, 2, cell_coord(cc, 2))) <= 2.0 * g.h[2]))
+        m = INFINITY;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   // non-negative doubles order like their bit patterns
@@ -704,24 +728,45 @@ __global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
       o[1] = make_uint4(w[4], w[5], w[6], w[7]);
     };
     const uint4 *row = reinterpret_cast<const uint4 *>(s.nbr1) + (size_t)i * 2;
+    // r^2 (FP32) of two candidates at once with the packed FP32 instructions:
+    // d = (p_j - p_i) + s h, the stencil shifts s 4^d from the entries' codes
+    // (cell size pre-scaled by 4^-d)
+    const float2 mpx = make_float2(-pi.x, -pi.x), mpy = make_float2(-pi.y, -pi.y),
+                 mpz = make_float2(-pi.z, -pi.z);
+    const float2 hx2 = make_float2(g.hf[0], g.hf[0]),
+                 hy2 = make_float2(0.25f * g.hf[1], 0.25f * g.hf[1]),
+                 hz2 = make_float2(0.0625f * g.hf[2], 0.0625f * g.hf[2]);
+    auto r2pair = [&](uint32_t ea, uint32_t eb, const float4 &qa, const float4 &qb) {
+      const float2 sx = __fadd2_rn(make_float2(__uint_as_float((ea & 3u) | 0x4B000000u),
+                                               __uint_as_float((eb & 3u) | 0x4B000000u)),
+                                   make_float2(-8388609.0f, -8388609.0f));
+      const float2 sy = __fadd2_rn(make_float2(__uint_as_float((ea & 12u) | 0x4B000000u),
+                                               __uint_as_float((eb & 12u) | 0x4B000000u)),
+                                   make_float2(-8388612.0f, -8388612.0f));
+      const float2 sz = __fadd2_rn(make_float2(__uint_as_float((ea & 48u) | 0x4B000000u),
+                                               __uint_as_float((eb & 48u) | 0x4B000000u)),
+                                   make_float2(-8388624.0f, -8388624.0f));
+      const float2 dx = __ffma2_rn(sx, hx2, __fadd2_rn(make_float2(qa.x, qb.x), mpx));
+      const float2 dy = __ffma2_rn(sy, hy2, __fadd2_rn(make_float2(qa.y, qb.y), mpy));
+      const float2 dz = __ffma2_rn(sz, hz2, __fadd2_rn(make_float2(qa.z, qb.z), mpz));
+      return __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+    };
     // four candidates at a time (as k_build's blocks of four)
     auto block4 = [&](const uint32_t *e, const int k0) {
       const int before = count;
       float4 pj[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) pj[u] = __ldg(s.pf + (k0 + u < n1 ? nbr_j(e[u]) : i));
+      const float2 r01 = r2pair(e[0], e[1], pj[0], pj[1]);
+      const float2 r23 = r2pair(e[2], e[3], pj[2], pj[3]);
+      const float r2v[4] = {r01.x, r01.y, r23.x, r23.y};
       bool band = false;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const uint32_t code = e[u];
-        const int j = nbr_j(code);
-        const int sx = nbr_s(code, 0), sy = nbr_s(code, 1), sz = nbr_s(code, 2);
-        const float dx = pj[u].x - (pi.x - (float)sx * g.hf[0]);
-        const float dy = pj[u].y - (pi.y - (float)sy * g.hf[1]);
-        const float dz = pj[u].z - (pi.z - (float)sz * g.hf[2]);
-        const float r2f = dx * dx + dy * dy + dz * dz;
-        const bool s_pos = sz > 0 || (sz == 0 && (sy > 0 || (sy == 0 && sx > 0)));
-        const bool ok = k0 + u < n1 && (!HALF || half_keep(i, j, s_pos));
+        const float r2f = r2v[u];
+        // lexicographically positive stencil offset <=> 6-bit code > 21
+        const bool ok = k0 + u < n1 && (!HALF || half_keep(i, nbr_j(code), (code & 63u) > 21u));
         const bool acc = ok && r2f < lo_thr;
         band = band || (ok && !acc && !(r2f > hi_thr));
         stage[count & 15][tx] = code;  // kept only if accepted
@@ -732,14 +777,8 @@ __global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const uint32_t code = e[u];
-          const int j = nbr_j(code);
-          const int sx = nbr_s(code, 0), sy = nbr_s(code, 1), sz = nbr_s(code, 2);
-          const float dx = pj[u].x - (pi.x - (float)sx * g.hf[0]);
-          const float dy = pj[u].y - (pi.y - (float)sy * g.hf[1]);
-          const float dz = pj[u].z - (pi.z - (float)sz * g.hf[2]);
-          const float r2f = dx * dx + dy * dy + dz * dz;
-          const bool s_pos = sz > 0 || (sz == 0 && (sy > 0 || (sy == 0 && sx > 0)));
-          const bool ok = k0 + u < n1 && (!HALF || half_keep(i, j, s_pos));
+          const float r2f = r2v[u];
+          const bool ok = k0 + u < n1 && (!HALF || half_keep(i, nbr_j(code), (code & 63u) > 21u));
           bool acc = ok && r2f < lo_thr;
           if (ok && !acc && !(r2f > hi_thr)) acc = exact_pair(s, g, i, code, c0, c1, c2, rns2);
           stage[count & 15][tx] = code;

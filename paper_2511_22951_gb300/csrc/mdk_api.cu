@@ -13,10 +13,23 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mdk.h"
 #include "mdk_internal.cuh"
 
 using namespace mdk;
+
+namespace {
+// NVTX range over a C-ABI call (visible in Nsight timelines; a no-op when no
+// tool is attached)
+struct Nvtx {
+  explicit Nvtx(const char *name) { nvtxRangePushA(name); }
+  ~Nvtx() { nvtxRangePop(); }
+  Nvtx(const Nvtx &) = delete;
+  Nvtx &operator=(const Nvtx &) = delete;
+};
+}  // namespace
 
 struct mdk_ctx {
   cudaStream_t stream = nullptr;
@@ -316,9 +329,13 @@ void fill_sys_params(mdk_ctx *c) {
   s.half = (c->pot == 1 || (c->pot == 2 && c->cfg.half == 1)) ? c->cfg.half : 0;
   const double rns = c->rc_list + c->skin;
   s.rns2 = rns * rns;
-  // FP32 pre-filter band: the float r^2 of a candidate is within ~6e-6 r_ns^2
-  // of the exact one (cell-relative offsets, |p| <= 2h, h < 2 r_ns); 1e-4
-  // leaves a wide margin, and candidates inside the band take the FP64 test
+  // FP32 pre-filter band: with cell-relative offsets |p| <= 2h (atoms beyond
+  // are flagged far and always take the exact test; with two-level lists a
+  // filter build that finds one beyond turns into a full build), each offset
+  // carries <= ulp(2h)/2 of rounding, so the float r^2 of a candidate near r_ns
+  // is within ~2 r_ns (2 ulp(2h) + ulp(r_ns)) + 3 ulp(r_ns^2) of the exact
+  // one: ~5e-7 r_ns^2 even for cells of rc + 1.5 A; 1e-4 leaves a wide
+  // margin, and candidates inside the band take the FP64 test
   s.filt_lo = (float)(s.rns2 * (1.0 - 1e-4));
   s.filt_hi = (float)(s.rns2 * (1.0 + 1e-4));
   s.outer_on = c->nmax1 > 0 ? 1 : 0;
@@ -567,6 +584,7 @@ void note_overflow(mdk_ctx *c, const DevStatus &st) {
 }
 
 int build_now(mdk_ctx *c) {
+  Nvtx range("mdk list build");
   launch_set_rebuild_flag(c->sys, c->stream);
   int rr = rebuild_chain(c, 0);
   if (rr) return rr;
@@ -1240,6 +1258,7 @@ int mdk_checkpoint_size(mdk_ctx *c, size_t *bytes) {
 }
 
 int mdk_save_checkpoint(mdk_ctx *c, void *buf, size_t bytes) {
+  Nvtx range("mdk_save_checkpoint");
   if (check_ctx(c) || !buf) return MDK_ERR_BAD_ARG;
   if (!c->ws || !c->state_set) return MDK_ERR_ORDER;
   DevStatus st;
@@ -1291,6 +1310,7 @@ int mdk_save_checkpoint(mdk_ctx *c, void *buf, size_t bytes) {
 }
 
 int mdk_load_checkpoint(mdk_ctx *c, const void *buf, size_t bytes) {
+  Nvtx range("mdk_load_checkpoint");
   if (check_ctx(c) || !buf || bytes < sizeof(CkptHeader)) return MDK_ERR_BAD_ARG;
   CkptHeader h;
   memcpy(&h, buf, sizeof(h));
@@ -1415,6 +1435,7 @@ int mdk_load_checkpoint(mdk_ctx *c, const void *buf, size_t bytes) {
 }
 
 int mdk_build_neighbors(mdk_ctx *c, double rc, double skin) {
+  Nvtx range("mdk_build_neighbors");
   if (check_ctx(c)) return MDK_ERR_BAD_ARG;
   if (!c->planned || rc != c->rc_list || skin != c->skin) {
     const int old_nmax = c->nmax, old_cells = c->n_cells;
@@ -1505,6 +1526,7 @@ int mdk_get_neighbors(mdk_ctx *c, int64_t *offsets, int32_t *jout, int32_t *img)
 }
 
 int mdk_compute(mdk_ctx *c, double *E, double *F, double *virial, int on_device) {
+  Nvtx range("mdk_compute");
   if (check_ctx(c)) return MDK_ERR_BAD_ARG;
   int r = ensure_ready(c);
   if (r) return r;
@@ -1558,6 +1580,7 @@ int mdk_compute(mdk_ctx *c, double *E, double *F, double *virial, int on_device)
 }
 
 int mdk_eam_vjp(mdk_ctx *c, const double *gE, const double *gF, double *dtheta, int on_device) {
+  Nvtx range("mdk_eam_vjp");
   if (check_ctx(c) || !dtheta) return MDK_ERR_BAD_ARG;
   if (c->pot != 2 || c->win_on) return MDK_ERR_ORDER;
   int r = ensure_ready(c);
@@ -1631,6 +1654,7 @@ int mdk_get_per_atom(mdk_ctx *c, double *Ui, double *Wi) {
 }
 
 int mdk_step(mdk_ctx *c, double dt, int64_t nsteps) {
+  Nvtx range("mdk_step");
   if (check_ctx(c) || nsteps < 0 || !(dt > 0.0)) return MDK_ERR_BAD_ARG;
   int r = ensure_ready(c);
   if (r) return r;
@@ -1824,6 +1848,7 @@ int mdk_set_piston(mdk_ctx *c, double u_p, const uint8_t *is_piston) {
 }
 
 int mdk_autotune(mdk_ctx *c, int reps, int *tpa_out, int *block_out, double *ms_out) {
+  Nvtx range("mdk_autotune");
   if (check_ctx(c) || reps < 0) return MDK_ERR_BAD_ARG;
   int r = ensure_ready(c);
   if (r) return r;
@@ -2087,6 +2112,7 @@ int mdk_window_counts(mdk_ctx *c, int64_t *inserted, int64_t *deleted) {
 
 int mdk_profiles(mdk_ctx *c, int axis, double origin, double bin_w, int nbins,
                  double cross_area, double *out, int on_device) {
+  Nvtx range("mdk_profiles");
   if (check_ctx(c) || axis < 0 || axis > 2 || !(bin_w > 0.0) || nbins < 1 || !out ||
       !(cross_area > 0.0))
     return MDK_ERR_BAD_ARG;
