@@ -46,8 +46,10 @@ extern "C" {
 #define MDK_ERR_NEIGH_OVERFLOW (-3) /* a list outgrew its capacity; the
                                        capacity was raised: resize the
                                        workspace and repeat the call       */
-#define MDK_ERR_ATOM_LOST (-4)      /* an atom moved more than one cell
-                                       between list builds                 */
+#define MDK_ERR_ATOM_LOST (-4)      /* reserved: an atom moved more than one
+                                       cell between list builds (the
+                                       displacement trigger rebuilds first,
+                                       so no kernel raises it)             */
 #define MDK_ERR_NONFINITE (-5)      /* NaN or Inf in a position or force   */
 #define MDK_ERR_TIMEOUT (-6)        /* a bounded device-side wait ran out  */
 #define MDK_ERR_CUDA (-7)           /* a CUDA runtime call failed          */
@@ -60,6 +62,11 @@ extern "C" {
 #define MDK_ERR_CAPACITY (-12)      /* the moving window had more atoms to
                                        append than mdk_set_capacity left
                                        room for (as many as fit were)     */
+#define MDK_ERR_BOUNDS (-13)        /* debug builds only (libmdk_debug.so,
+                                       compiled with MDK_DEBUG): a kernel
+                                       caught an index outside its array,
+                                       skipped the access and went on; the
+                                       results of the call are not valid  */
 
 /* ---- precision modes ---------------------------------------------------- */
 #define MDK_FP64 0  /* every operation in FP64                               */

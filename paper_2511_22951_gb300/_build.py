@@ -23,6 +23,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmdk.so")
 STAMP = LIB + ".stamp"
+# debug build: the kernels' index checks compiled in (MDK_DEBUG), its own
+# objects, library and stamp
+DEBUG_LIB = os.path.join(HERE, "libmdk_debug.so")
+DEBUG_FLAGS = ("-DMDK_DEBUG=1",)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -62,22 +66,27 @@ def fingerprint(extra=()) -> str:
     return h.hexdigest()
 
 
-def up_to_date(extra=()) -> bool:
-    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
+def up_to_date(extra=(), lib=LIB) -> bool:
+    stamp = lib + ".stamp"
+    if not (os.path.exists(lib) and os.path.exists(stamp)):
         return False
-    with open(STAMP) as f:
+    with open(stamp) as f:
         return f.read().strip() == fingerprint(extra)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and up_to_date(extra):
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra=(), debug: bool = False) -> str:
+    """Build libmdk.so (debug=True: libmdk_debug.so with the index checks)."""
+    lib = DEBUG_LIB if debug else LIB
+    extra = tuple(extra) + (DEBUG_FLAGS if debug else ())
+    if not force and up_to_date(extra, lib):
+        return lib
     stamp = fingerprint(extra)
-    os.makedirs(BUILD, exist_ok=True)
+    bdir = BUILD + ("_debug" if debug else "")
+    os.makedirs(bdir, exist_ok=True)
     objs = []
 
     def one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -88,19 +97,20 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl",
            "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    with open(STAMP + f".tmp{os.getpid()}", "w") as f:
+    os.replace(tmp, lib)
+    with open(lib + f".stamp.tmp{os.getpid()}", "w") as f:
         f.write(stamp + "\n")
-    os.replace(STAMP + f".tmp{os.getpid()}", STAMP)
-    return LIB
+    os.replace(lib + f".stamp.tmp{os.getpid()}", lib + ".stamp")
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True,
-                extra=("-Xptxas", "-v") if "--ptxas" in sys.argv else ()))
+                extra=("-Xptxas", "-v") if "--ptxas" in sys.argv else (),
+                debug="--debug" in sys.argv))

@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(bp_threads<P>(), bp_blocks<P>())
     uint32_t j = 0;
     if (k < nn) {
       const uint32_t ent = s.nbr[ell_index(k, i, Nc)];
-      j = (uint32_t)nbr_j(ent);
+      j = dbg_idx(s, nbr_j(ent), Nc, i);
       const V pj = GP::ld(pg + j);
       dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
       dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);

@@ -346,8 +346,8 @@ __global__ void __launch_bounds__(kBlk) k_scatter(Sys s) {
   if (!full_on(s)) return;
   const int N = s.st->N;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-  const int pos = atomicAdd(&s.cell_fill[s.cell_of[i]], 1);
-  s.order[pos] = i;
+  const int pos = atomicAdd(&s.cell_fill[dbg_idx(s, s.cell_of[i], s.n_cells + 1)], 1);
+  s.order[dbg_idx(s, pos, s.N_cap)] = i;
   }
 }
 
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(kBlk) k_cell_sort(Sys s) {
 #pragma unroll 4
       for (int q = a; q < e; ++q) rank += s.id[s.order[q]] < key ? 1 : 0;
     }
-    s.tmpi[a + rank] = v;
+    s.tmpi[dbg_idx(s, a + rank, s.N_cap)] = v;
   }
 }
 
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(kBlk) k_permute(Sys s, typename P::vec4 *pg_ta
   const int N = s.st->N;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
   const size_t Nc = s.N_cap;
-  const int o = s.tmpi[k];  // the cell-sorted order (k_cell_sort)
+  const int o = dbg_idx(s, s.tmpi[k], s.N_cap);  // the cell-sorted order (k_cell_sort)
   double xv[3];
   for (int d = 0; d < 3; ++d) {
     xv[d] = s.x[d * Nc + o];
@@ -543,8 +543,8 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s, ListOut lo_) {
           !stencil_cell(c1, sy, g.nc[1], g.per[1], &cy, &ny) ||
           !stencil_cell(c2, sz, g.nc[2], g.per[2], &cz, &nz))
         continue;
-      const int cj = g.cell_off + cx + g.nc[0] * (cy + g.nc[1] * cz);
-      const int a = s.cell_start[cj], b = s.cell_start[cj + 1];
+      const int cj = dbg_idx(s, g.cell_off + cx + g.nc[0] * (cy + g.nc[1] * cz), s.n_cells);
+      const int a = s.cell_start[cj], b = dbg_idx(s, s.cell_start[cj + 1], s.N_cap + 1, a);
       // d = p_j - q with q = p_i - s h (the shifted own offset, once per cell)
       const float qx = pi.x - (float)sx * g.hf[0];
       const float qy = pi.y - (float)sy * g.hf[1];
@@ -756,7 +756,8 @@ __global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
       const int before = count;
       float4 pj[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) pj[u] = __ldg(s.pf + (k0 + u < n1 ? nbr_j(e[u]) : i));
+      for (int u = 0; u < 4; ++u)
+        pj[u] = __ldg(s.pf + (k0 + u < n1 ? dbg_idx(s, nbr_j(e[u]), Nc, i) : i));
       const float2 r01 = r2pair(e[0], e[1], pj[0], pj[1]);
       const float2 r23 = r2pair(e[2], e[3], pj[2], pj[3]);
       const float r2v[4] = {r01.x, r01.y, r23.x, r23.y};

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_rho(Sys s, EAMPara
     Acc<R> rho;
     R br = 0;
     walk<T>(
-        s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pg + j); },
+        s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pg + dbg_idx(s, j, Nc)); },
         [&](uint32_t ent, const V &pj) {
           const R dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
           const R dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_eam(Sys s, EAMPara
     double e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     R bx = 0, by = 0, bz = 0;
     walk<T>(
-        s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pgf + j); },
+        s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pgf + dbg_idx(s, j, Nc)); },
         [&](uint32_t ent, const V &pj) {
           const R dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
           const R dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256, 2) k_rho_half(Sys s, EAMParams ep, StepAr
     const int nn = min(s.nnbr[i], s.nmax);
     Q rho = 0;
     walk<1>(
-        s.nbr, Nc, i, nn, 0, [&](uint32_t j) { return GP::ld(pg + j); },
+        s.nbr, Nc, i, nn, 0, [&](uint32_t j) { return GP::ld(pg + dbg_idx(s, j, Nc)); },
         [&](uint32_t ent, const V &pj) {
           const R dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
           const R dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256, 2) k_rho_half(Sys s, EAMParams ep, StepAr
             kk = kk > kmax ? kmax : kk;
             const Q q = H::q(GP::val1(rt, kk, u - (R)kk));
             rho += q;
-            H::red(acc + nbr_j(ent), q);
+            H::red(acc + dbg_idx(s, nbr_j(ent), Nc, i), q);
           }
         },
         [] {});
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256, 2) k_eam_half(Sys s, EAMParams ep, StepAr
     const int nn = min(s.nnbr[i], s.nmax);
     Q fx = 0, fy = 0, fz = 0, e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     walk<1>(
-        s.nbr, Nc, i, nn, 0, [&](uint32_t j) { return GP::ld(pgf + j); },
+        s.nbr, Nc, i, nn, 0, [&](uint32_t j) { return GP::ld(pgf + dbg_idx(s, j, Nc)); },
         [&](uint32_t ent, const V &pj) {
           const R dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
           const R dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256, 2) k_eam_half(Sys s, EAMParams ep, StepAr
             const R fr = (dphi + (fpi + GP::fp_of(pj)) * drho) * inv_dr * inv_r;  // V'(r)/r
             if (sizeof(R) == 4) bad = bad || !(fabs(fr) < fr_max);
             const Q qx = H::q(fr * dx), qy = H::q(fr * dy), qz = H::q(fr * dz);
-            const size_t j = (size_t)nbr_j(ent);
+            const size_t j = dbg_idx(s, nbr_j(ent), Nc, i);
             fx += qx;
             fy += qy;
             fz += qz;

@@ -82,7 +82,7 @@ __device__ __forceinline__ void lj_walk_packed(const Sys &s, const float4 *__res
       float4 q[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        q[u] = 4 * h + u < m ? __ldg(pg + nbr_j(e[4 * h + u])) : far;
+        q[u] = 4 * h + u < m ? __ldg(pg + dbg_idx(s, nbr_j(e[4 * h + u]), Nc)) : far;
       float2 bx = f2(0.f, 0.f), by = bx, bz = bx;
 #pragma unroll
       for (int pr = 0; pr < 2; ++pr) {
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256, lj_min_blocks<P>()) k_lj(Sys s, LJParams 
       w5 = wv[5];
     } else
     walk<T>(
-        s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pg + j); },
+        s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pg + dbg_idx(s, j, Nc)); },
         [&](uint32_t ent, const V &pj) {
           const R dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
           const R dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256, half_min_blocks<P>(ENERGY))
   Q fx = 0, fy = 0, fz = 0, e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
   bool bad = false;
   walk<1>(
-      s.nbr, Nc, i, nn, 0, [&](uint32_t j) { return GP::ld(pg + j); },
+      s.nbr, Nc, i, nn, 0, [&](uint32_t j) { return GP::ld(pg + dbg_idx(s, j, Nc)); },
       [&](uint32_t ent, const V &pj) {
         const R dx = pvec((R)pj.x, (R)pi.x, s_scaled(R(0), ent, 0), hx);
         const R dy = pvec((R)pj.y, (R)pi.y, s_scaled(R(0), ent, 1), hy);
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256, half_min_blocks<P>(ENERGY))
           lj_pair<GP, SHIFT, ENERGY>(lc, r2, fr, v);
           if (sizeof(R) == 4) bad = bad || !(fabs(fr) < fr_max);
           const Q qx = H::q(fr * dx), qy = H::q(fr * dy), qz = H::q(fr * dz);
-          const size_t j = (size_t)nbr_j(ent);
+          const size_t j = dbg_idx(s, nbr_j(ent), Nc, i);
           fx += qx;
           fy += qy;
           fz += qz;

@@ -430,6 +430,7 @@ int read_status(mdk_ctx *c, DevStatus *out) {
 }
 
 int status_from_bits(unsigned bits) {
+  if (bits & kStBounds) return MDK_ERR_BOUNDS;
   if (bits & kStNonfinite) return MDK_ERR_NONFINITE;
   if (bits & kStOverflow) return MDK_ERR_NEIGH_OVERFLOW;
   if (bits & kStAtomLost) return MDK_ERR_ATOM_LOST;
@@ -771,6 +772,7 @@ const char *mdk_status_string(int s) {
     case MDK_ERR_RHO_RANGE: return "EAM density above the F table (extrapolated)";
     case MDK_ERR_TOO_LARGE: return "size above the fixed maximum of the allocation-free entry point";
     case MDK_ERR_CAPACITY: return "atom capacity full: the moving window could not append all atoms";
+    case MDK_ERR_BOUNDS: return "index out of range caught by a debug-build check (results invalid)";
     default: return "unknown status";
   }
 }

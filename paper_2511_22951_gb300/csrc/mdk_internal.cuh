@@ -44,6 +44,7 @@ enum : unsigned {
   kStAtomLost = 8u,
   kStTimeout = 16u,
   kStCapacity = 32u,  // a window append did not fit the capacity
+  kStBounds = 64u,    // debug builds: an index outside its array was caught
 };
 
 struct DevStatus {
@@ -177,6 +178,25 @@ struct Sys {
   int n_fbins;                    // bins over [win_xlo, win_xhi)
   long long *fbin;                // [2 n_fbins]: sum of q(v_x), atom count per bin
 };
+
+// Debug builds (compiled with MDK_DEBUG): an index about to be read or
+// written is checked against its array's extent n; a bad one raises
+// kStBounds in the status word and is replaced by `safe` (in range), so the
+// kernel finishes without touching memory it does not own and the call
+// reports MDK_ERR_BOUNDS.  Release builds compile the check away.
+__device__ __forceinline__ uint32_t dbg_idx(const Sys &s, uint32_t j, uint32_t n,
+                                            uint32_t safe = 0) {
+#ifdef MDK_DEBUG
+  if (j >= n) {
+    atomicOr(&s.st->bits, kStBounds);
+    return safe;
+  }
+#endif
+  (void)s;
+  (void)n;
+  (void)safe;
+  return j;
+}
 
 // order-preserving map of a double onto a signed 64-bit key (for atomicMax/Min)
 __device__ __forceinline__ long long dkey(double v) {

@@ -15,6 +15,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmdk.so")
+# MDK_DEBUG=1 in the environment: load the debug build (index checks in the
+# kernels, MDK_ERR_BOUNDS), built on first use
+DEBUG_LIB_PATH = os.path.join(_HERE, "libmdk_debug.so")
 
 MDK_OK = 0
 MDK_ERR_BAD_ARG = -1
@@ -29,6 +32,7 @@ MDK_ERR_ORDER = -9
 MDK_ERR_RHO_RANGE = -10
 MDK_ERR_TOO_LARGE = -11
 MDK_ERR_CAPACITY = -12
+MDK_ERR_BOUNDS = -13
 MDK_FP64 = 0
 MDK_MIXED = 1
 MDK_LIST_FULL = 0
@@ -95,11 +99,18 @@ SIGNATURES = {
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libmdk.so and declare every C-ABI function.  Raises if missing."""
+def load(path: str = None):
+    """Load libmdk.so (libmdk_debug.so when MDK_DEBUG=1) and declare every
+    C-ABI function.  Raises if missing."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        if os.environ.get("MDK_DEBUG", "0") not in ("", "0"):
+            from . import _build
+            path = _build.build(debug=True)
+        else:
+            path = LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(
             f"libmdk.so not found at {path}: build it with "

@@ -102,3 +102,19 @@ def test_argument_checks_without_gpu(lib):
     assert lib.mdk_get_build_counts(None, None, None) == -1
     lib.mdk_destroy.argtypes = [P]
     assert lib.mdk_destroy(h) == 0
+
+
+def test_debug_build_compiles():
+    """The kernels compile with their debug-build index checks (MDK_DEBUG)."""
+    import shutil
+    import subprocess
+    import tempfile
+    from paper_2511_22951_gb300 import _build
+    if shutil.which(_build.nvcc()) is None and not os.path.exists(_build.nvcc()):
+        pytest.skip("no nvcc")
+    src = os.path.join(_build.CSRC, "k_build.cu")
+    with tempfile.TemporaryDirectory() as d:
+        cmd = [_build.nvcc(), *_build.ARCH, *_build.NVCC_FLAGS, *_build.DEBUG_FLAGS, "-I",
+               _build.INCLUDE, "-I", _build.CSRC, "-c", src, "-o", os.path.join(d, "k.o")]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
