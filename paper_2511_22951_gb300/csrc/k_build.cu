@@ -630,23 +630,11 @@ __global__ void __launch_bounds__(kBlk) k_outer_disp(Sys s) {
   const size_t Nc = s.N_cap;
   double m = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const double xv = s.x[i], yv = s.x[Nc + i], zv = s.x[2 * Nc + i];
-    const double dx = xv - s.xfull[i], dy = yv - s.xfull[Nc + i], dz = zv - s.xfull[2 * Nc + i];
+    const double dx = s.x[i] - s.xfull[i], dy = s.x[Nc + i] - s.xfull[Nc + i],
+                 dz = s.x[2 * Nc + i] - s.xfull[2 * Nc + i];
     const double d2 = dx * dx + dy * dy + dz * dz;
     // a non-finite position forces a full build (whose binning reports it)
     m = d2 == d2 ? fmax(m, d2) : INFINITY;
-    // so does an atom (not flagged far) that left the |p| <= 2h range the FP32
-    // pre-filter's error bound assumes (possible along a free dimension):
-    // the full build re-bins it and flags it far if it is still outside
-    const uint32_t inf = s.info[i];
-    if (!(inf & kInfoFar)) {
-      const Grid &g = s.grid[inf >> 8];
-      const uint32_t cc = s.cellc[i];
-      if (!(fabs(xv - cell_center(g, 0, cell_coord(cc, 0))) <= 2.0 * g.h[0] &&
-            fabs(yv - cell_center(g, 1, cell_coord(cc, 1))) <= 2.0 * g.h[1] &&
-            fabs(zv - cell_center(g, 2, cell_coord(cc, 2))) <= 2.0 * g.h[2]))
-        m = INFINITY;
-    }
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   // non-negative doubles order like their bit patterns

@@ -329,13 +329,14 @@ void fill_sys_params(mdk_ctx *c) {
   s.half = (c->pot == 1 || (c->pot == 2 && c->cfg.half == 1)) ? c->cfg.half : 0;
   const double rns = c->rc_list + c->skin;
   s.rns2 = rns * rns;
-  // FP32 pre-filter band: with cell-relative offsets |p| <= 2h (atoms beyond
-  // are flagged far and always take the exact test; with two-level lists a
-  // filter build that finds one beyond turns into a full build), each offset
-  // carries <= ulp(2h)/2 of rounding, so the float r^2 of a candidate near r_ns
-  // is within ~2 r_ns (2 ulp(2h) + ulp(r_ns)) + 3 ulp(r_ns^2) of the exact
-  // one: ~5e-7 r_ns^2 even for cells of rc + 1.5 A; 1e-4 leaves a wide
-  // margin, and candidates inside the band take the FP64 test
+  // FP32 pre-filter band: cell-relative offsets have |p| <= 2h at a full
+  // build (atoms beyond are flagged far and always take the exact test), and
+  // with two-level lists at most (skin_outer - skin)/2 more at a filter build
+  // (the displacement budget); each offset carries <= ulp(|p|)/2 of
+  // rounding, so the float r^2 of a candidate near r_ns is within
+  // ~2 r_ns (2 ulp(2h) + ulp(r_ns)) + 3 ulp(r_ns^2) of the exact one:
+  // ~5e-7 r_ns^2 even for cells of rc + 1.5 A; 1e-4 leaves a wide margin, and
+  // candidates inside the band take the FP64 test
   s.filt_lo = (float)(s.rns2 * (1.0 - 1e-4));
   s.filt_hi = (float)(s.rns2 * (1.0 + 1e-4));
   s.outer_on = c->nmax1 > 0 ? 1 : 0;
