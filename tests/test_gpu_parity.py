@@ -309,13 +309,13 @@ def test_config1_full_size_sampled(mdk, ora):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("skin_outer", [0.0, 1.5])
+@pytest.mark.parametrize("skin_outer", [0.0, 2.1])
 def test_config2_full_size_sampled(mdk, ora, skin_outer):
     """8,388,608-atom LJ argon, mixed: 78 neighbours each in the lattice; sampled
     forces on a thermalised state (300 steps = 0.6 ps, about one vibration
     period, so that the forces are thermal and not the near-zero forces of the
     starting lattice) within the mixed-precision bar; with one-level lists and
-    with the two-level lists the bench runs (outer skin 1.5 A)."""
+    with the two-level lists the bench runs (outer skin 2.1 A)."""
     wl = W.config2()
     s = wl.systems[0]
     ctx = mdk.make_context(wl, skin_outer=skin_outer)

@@ -46,3 +46,14 @@ def test_serial_run_matches_all_pairs_definition(ora):
     ref = ora.lj(s.x, s.lo, s.hi, s.periodic, wl.lj.eps, wl.lj.sigma, wl.lj.rc, 1)
     fmax = np.max(np.abs(ref["F"])) + 1e-30
     assert np.max(np.abs(a["F"] - ref["F"])) <= 1e-12 * fmax + 1e-13
+
+
+def test_serial_eam_run_matches_all_pairs_definition(ora):
+    # the same for the Al-like EAM of the 256,000-atom workload, on a 4^3-cell box
+    tab = W.tabulate_fs_eam(W.AL_LIKE)
+    s = W.lattice_system(np.random.default_rng(5), (4, 4, 4), 4.05, W.MASS_AL, 300.0,
+                         sigma_jitter=0.05)
+    a = ora.md_run(s.x, s.v, s.masses, s.lo, s.hi, s.periodic, 1.0, 0, 0.3, tables=tab)
+    ref = ora.eam(s.x, s.lo, s.hi, s.periodic, tab)
+    fmax = np.max(np.abs(ref["F"])) + 1e-30
+    assert np.max(np.abs(a["F"] - ref["F"])) <= 1e-12 * fmax + 1e-13
