@@ -7,17 +7,25 @@
 //   f_i = sum_j [phi'(r) + (F'(rho_i) + F'(rho_j)) rho'(r)] r_ji / r.
 // Pass 1 sums rho_i and evaluates F(rho_i), F'(rho_i) (FP64, once per atom);
 // pass 2 needs F'(rho_j) of every neighbour, so it is a second launch.  Both
-// stage their spline tables in shared memory once per block and run on a
-// persistent grid (one or two blocks per SM), so a table is read from L2 a
-// few hundred times per launch, not once per atom tile.  T lanes own one atom
-// (autotuned), as in the LJ kernel.  The mixed tables take 80 KB of shared
-// memory per block (5000 knots), so residency comes from large blocks: at most
-// 64 registers per thread lets two 512-thread blocks (32 warps) share an SM.
-// The FP64 force-pass tables take 160 KB (one block per SM), so the FP64
-// passes take up to 128 registers (no spills of the FP64 pair values).
+// run on a persistent grid; T lanes own one atom (autotuned), as in the LJ
+// kernel.  Where the spline tables are read from:
+//  * FP64: staged in shared memory once per block (160 KB for the force pass:
+//    one block per SM, up to 128 registers, no spills of the FP64 pair values);
+//  * mixed: straight from the workspace through L1 (80 KB per pass, which L1
+//    holds once no shared memory is carved out).  A pair's table load lands at
+//    a random knot; in shared memory the lanes of a quarter-warp then collide
+//    in banks (9.6 / 7.4 wavefronts per 16-byte load instead of 4), and an A/B
+//    on one GB300 measured L1 faster: cold-curve batch 1.18e9 against 1.07e9
+//    atom-timesteps/s, Al bulk and slab +1%.
 #include "k_pair.cuh"
 
 namespace mdk {
+
+// shared memory of the full-list passes (the mixed tables are read through L1)
+static int full_pass_smem(const EAMParams &p, int precision, int pass) {
+  return precision == 0 ? eam_smem_bytes(p, precision, pass) : 0;
+}
+
 namespace {
 
 using namespace pair;
@@ -37,13 +45,17 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_rho(Sys s, EAMPara
   using V = typename GP::V;
   using T1 = typename GP::Tab1;
   extern __shared__ __align__(16) unsigned char smem[];
-  T1 *rt = reinterpret_cast<T1 *>(smem);
-  {
+  const T1 *rt;
+  if constexpr (sizeof(R) == 4) {
+    rt = GP::tab1(ep);  // mixed: through L1
+  } else {
+    T1 *w = reinterpret_cast<T1 *>(smem);
     const T1 *src = GP::tab1(ep);
     const int n = GP::n1(ep);
-    for (int q = threadIdx.x; q < n; q += blockDim.x) rt[q] = src[q];
+    for (int q = threadIdx.x; q < n; q += blockDim.x) w[q] = src[q];
+    __syncthreads();
+    rt = w;
   }
-  __syncthreads();
   const int N = run_n(s.st);
   const size_t Nc = s.N_cap;
   const V *__restrict__ pg = (const V *)s.pg[a.cur];
@@ -104,12 +116,16 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_eam(Sys s, EAMPara
   using V = typename GP::V;
   using TP = typename GP::TabPR;
   extern __shared__ __align__(16) unsigned char smem[];
-  TP *tab = reinterpret_cast<TP *>(smem);
-  {
+  const TP *tab;
+  if constexpr (sizeof(R) == 4) {
+    tab = GP::pr(ep);  // mixed: through L1
+  } else {
+    TP *w = reinterpret_cast<TP *>(smem);
     const TP *src = GP::pr(ep);
-    for (int q = threadIdx.x; q < ep.nr; q += blockDim.x) tab[q] = src[q];
+    for (int q = threadIdx.x; q < ep.nr; q += blockDim.x) w[q] = src[q];
+    __syncthreads();
+    tab = w;
   }
-  __syncthreads();
   const int N = run_n(s.st);
   const size_t Nc = s.N_cap;
   const V *__restrict__ pg = (const V *)s.pg[a.cur];
@@ -260,7 +276,7 @@ int grid_for(K kern, int block, int smem, long long threads_needed) {
 
 template <class P, int MODE, bool EN, int T>
 void go(const Sys &s, const EAMParams &p, StepArgs a, int block, int prec, cudaStream_t st) {
-  const int b1 = eam_smem_bytes(p, prec, 1), b2 = eam_smem_bytes(p, prec, 2);
+  const int b1 = full_pass_smem(p, prec, 1), b2 = full_pass_smem(p, prec, 2);
   auto k1 = k_rho<P, EN, T>;
   auto k2 = k_eam<P, MODE, EN, T>;
   static int cb = 0, cs = -1, g1 = 0, g2 = 0, cap = -1;
@@ -362,7 +378,7 @@ namespace {
 template <class P, int T>
 void rho_only(const Sys &s, const EAMParams &p, StepArgs a, int block, int prec,
               cudaStream_t st) {
-  const int b1 = eam_smem_bytes(p, prec, 1);
+  const int b1 = full_pass_smem(p, prec, 1);
   auto k1 = k_rho<P, false, T>;
   k1<<<grid_for(k1, block, b1, (long long)s.N_cap * T), block, b1, st>>>(s, p, a);
 }
