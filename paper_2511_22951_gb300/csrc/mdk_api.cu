@@ -264,6 +264,7 @@ int plan(mdk_ctx *c, double rc, double skin, int max_neighbors, int rebuild_ever
       g.L[d] = L;
       g.nc[d] = nc;
       g.h[d] = L / nc;
+      g.lo_c[d] = lo + 0.5 * g.h[d];
       g.inv_h[d] = 1.0 / g.h[d];
       g.hf[d] = (float)g.h[d];
       g.per[d] = c->per[3 * r + d] ? 1 : 0;

@@ -90,6 +90,7 @@ __device__ __forceinline__ int run_n(const DevStatus *st) {
 // one replica's box and cell grid
 struct Grid {
   double lo[3], hi[3], L[3], h[3], inv_h[3];
+  double lo_c[3];  // lo + h/2: the centre of cell 0
   float hf[3];
   int nc[3];
   int per[3];
@@ -290,7 +291,7 @@ struct EAMTablesDev {
 // right after a build (h/2 + skin/2 later); the build and every step use
 // this one expression, so the offsets of one list lifetime are consistent.
 __device__ __forceinline__ double cell_center(const Grid &g, int d, int c) {
-  return g.lo[d] + ((double)c + 0.5) * g.h[d];
+  return fma((double)c, g.h[d], g.lo_c[d]);
 }
 
 // Verlet-list layout: entries in groups of 8 per atom; group g of atom i is

@@ -510,12 +510,28 @@ class Context:
                "mdk_get_build_counts")
         return int(b.value), int(f.value)
 
-    def autotune(self, reps=3):
+    def autotune(self, reps=3, key=None):
         """Pick threads-per-atom and block size by timing every shape (LJ:
-        full and half lists; `list_kind` tells which won)."""
+        full and half lists; `list_kind` tells which won).  With the
+        environment variable MDK_AUTOTUNE_CACHE naming a JSON file and a `key`
+        describing the workload (any string), a shape found before for that
+        key and device is reused instead of timed again (ms is then NaN)."""
+        path = os.environ.get("MDK_AUTOTUNE_CACHE", "")
+        ck = None
+        if path and key is not None:
+            ck = autotune_cache_key(key, self.prec, self.torch.cuda.get_device_name(self.device))
+            hit = autotune_cache_get(path, ck)
+            if hit is not None:
+                self.set_launch(hit["tpa"], hit["block"])
+                if self.list_kind != hit["list"]:
+                    self.set_list_kind(hit["list"])
+                return hit["tpa"], hit["block"], float("nan")
         t, b, ms = _I(), _I(), _D()
         _check(self.lib.mdk_autotune(self.h, reps, ctypes.byref(t), ctypes.byref(b),
                                      ctypes.byref(ms)), "mdk_autotune")
+        if ck is not None:
+            autotune_cache_put(path, ck, {"tpa": int(t.value), "block": int(b.value),
+                                          "list": self.list_kind, "ms": float(ms.value)})
         return int(t.value), int(b.value), float(ms.value)
 
     def set_graphs(self, enable=True):
@@ -606,6 +622,42 @@ class Context:
     def set_piston(self, u_p, flags):
         f = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8)
         _check(self.lib.mdk_set_piston(self.h, u_p, _ptr(f)), "mdk_set_piston")
+
+
+def autotune_cache_key(key, precision, device_name):
+    """The cache entry of a workload key on a device model and precision."""
+    return f"{device_name}|{'fp64' if precision in (MDK_FP64, 'fp64') else 'mixed'}|{key}"
+
+
+def autotune_cache_get(path, ck):
+    """The stored launch shape of cache key ck, or None."""
+    import json
+    try:
+        with open(path) as f:
+            e = json.load(f).get(ck)
+    except (OSError, ValueError):
+        return None
+    if not isinstance(e, dict) or e.get("list") not in _KINDS or \
+            e.get("tpa") not in (1, 2, 4, 8, 32) or e.get("block") not in (128, 256, 512):
+        return None
+    return e
+
+
+def autotune_cache_put(path, ck, entry):
+    """Store a launch shape under key ck (the file is rewritten atomically)."""
+    import json
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if not isinstance(d, dict):
+            d = {}
+    except (OSError, ValueError):
+        d = {}
+    d[ck] = entry
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 def fma_peak(precision="fp64"):
