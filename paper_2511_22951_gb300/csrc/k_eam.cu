@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_eam(Sys s, EAMPara
   extern __shared__ __align__(16) unsigned char smem[];
   const TP *tab;
   if constexpr (sizeof(R) == 4) {
-    tab = GP::pr(ep);  // mixed: through L1
+    tab = GP::pr8(ep);  // mixed: through L1, one 32-byte record per interval
   } else {
     TP *w = reinterpret_cast<TP *>(smem);
     const TP *src = GP::pr(ep);
@@ -168,14 +168,22 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_eam(Sys s, EAMPara
             int kk = (int)u;
             kk = kk > kmax ? kmax : kk;
             const R t = u - (R)kk;
-            R dphi, drho;
-            GP::der_pr(tab, kk, t, dphi, drho);
+            R dphi, drho, vphi = 0;
+            if constexpr (sizeof(R) == 4) {
+              float4 qa, qb;
+              GP::ld_pr8(tab, kk, qa, qb);
+              GP::der_ab(qa, qb, t, dphi, drho);
+              if (ENERGY) vphi = GP::val_ab(qa, qb, t);
+            } else {
+              GP::der_pr(tab, kk, t, dphi, drho);
+              if (ENERGY) vphi = GP::val_pr(tab, ep, kk, t);
+            }
             const R fr = (dphi + (fpi + GP::fp_of(pj)) * drho) * inv_dr * inv_r;  // V'(r)/r
             bx += fr * dx;
             by += fr * dy;
             bz += fr * dz;
             if (ENERGY) {
-              e += 0.5 * (double)GP::val_pr(tab, ep, kk, t);
+              e += 0.5 * (double)vphi;
               const R hf = R(-0.5) * fr;
               w0 += (double)(hf * dx * dx);
               w1 += (double)(hf * dy * dy);
@@ -238,6 +246,11 @@ __global__ void k_eam_prepare(int nr, int nrho, const double *phi, const double 
     o.rho_d32[k] = make_float2((float)dr, (float)mr);
     o.phi_v32[k] = (float)phi[k];
     o.pr32[k] = make_float4((float)dp, (float)mp, (float)dr, (float)mr);
+    o.pr8[2 * k] = o.pr32[k];
+    o.pr8[2 * k + 1] =
+        k + 1 < nr ? make_float4((float)phi[k], (float)hslope(phi, nr, k + 1), 0.0f,
+                                 (float)hslope(rho, nr, k + 1))
+                   : make_float4((float)phi[k], 0.0f, 0.0f, 0.0f);
     dvec4 q;
     q.x = phi[k];
     q.y = mp;

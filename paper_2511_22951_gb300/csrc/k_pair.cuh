@@ -143,21 +143,38 @@ struct G<Mixed> {
   // force pass: interleaved phi / rho differences and slopes, h * derivatives
   using TabPR = float4;
   static __device__ __forceinline__ const float4 *pr(const EAMParams &e) { return e.pr32; }
-  static __device__ __forceinline__ void der_pr(const float4 *t, int k, float u, float &dphi,
-                                                float &drho) {
-    const float4 a = t[k], b = t[k + 1];
+  // derivatives (and the phi value) of interval k from a = pr32[k] and the
+  // next knot's slopes in b.y (phi) and b.w (rho)
+  static __device__ __forceinline__ void der_ab(const float4 &a, const float4 &b, float u,
+                                                float &dphi, float &drho) {
     const float u2 = u * u;
     const float w0 = 6.0f * u - 6.0f * u2, w1 = 3.0f * u2 - 4.0f * u + 1.0f,
                 w3 = 3.0f * u2 - 2.0f * u;
     dphi = w0 * a.x + w1 * a.y + w3 * b.y;
     drho = w0 * a.z + w1 * a.w + w3 * b.w;
   }
+  static __device__ __forceinline__ float val_ab(float phi_k, const float4 &a, const float4 &b,
+                                                 float u) {
+    const float u2 = u * u, u3 = u2 * u;
+    return phi_k + (3.0f * u2 - 2.0f * u3) * a.x + (u3 - 2.0f * u2 + u) * a.y + (u3 - u2) * b.y;
+  }
+  static __device__ __forceinline__ void der_pr(const float4 *t, int k, float u, float &dphi,
+                                                float &drho) {
+    der_ab(t[k], t[k + 1], u, dphi, drho);
+  }
   static __device__ __forceinline__ float val_pr(const float4 *t, const EAMParams &e, int k,
                                                  float u) {
-    const float4 a = t[k], b = t[k + 1];
-    const float u2 = u * u, u3 = u2 * u;
-    return __ldg(e.phi_v32 + k) + (3.0f * u2 - 2.0f * u3) * a.x + (u3 - 2.0f * u2 + u) * a.y +
-           (u3 - u2) * b.y;
+    return val_ab(__ldg(e.phi_v32 + k), t[k], t[k + 1], u);
+  }
+  // the 32-byte interval records (pr8): one 256-bit read-only load per pair
+  static __device__ __forceinline__ const float4 *pr8(const EAMParams &e) { return e.pr8; }
+  static __device__ __forceinline__ void ld_pr8(const float4 *t, int k, float4 &a, float4 &b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(t + 2 * (size_t)k));
+  }
+  static __device__ __forceinline__ float val_ab(const float4 &a, const float4 &b, float u) {
+    return val_ab(b.x, a, b, u);
   }
   static __device__ __forceinline__ void st_fp(float4 *p, const float4 &q, double fp) {
     *p = make_float4(q.x, q.y, q.z, (float)fp);

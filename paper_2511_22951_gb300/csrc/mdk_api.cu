@@ -215,6 +215,7 @@ size_t layout(mdk_ctx *c, char *base) {
   t.phi_v32 = cv.take<float>(nr);
   t.pr32 = cv.take<float4>(nr);
   t.pr64 = cv.take<dvec4>(nr);
+  t.pr8 = cv.take<float4>((size_t)2 * nr);
   c->adj_acc = cv.take<double2>((size_t)2 * nr + nrho);
   c->adj_out = cv.take<double>((size_t)2 * nr + nrho);
   c->adj_gE = cv.take<double>(c->n_rep);
@@ -231,6 +232,7 @@ size_t layout(mdk_ctx *c, char *base) {
   c->eam.phi_v32 = t.phi_v32;
   c->eam.pr32 = t.pr32;
   c->eam.pr64 = t.pr64;
+  c->eam.pr8 = t.pr8;
   return align256(cv.off);
 }
 

@@ -239,6 +239,10 @@ struct EAMParams {
   //   pr64[k] = (phi_k, h m^phi_k, rho_k, h m^rho_k)
   const float4 *pr32;
   const dvec4 *pr64;
+  // the full-list mixed force pass: one 32-byte record per interval k, read
+  // with one 256-bit load per pair:
+  //   pr8[2k] = pr32[k],  pr8[2k + 1] = (phi_k, h m^phi_{k+1}, 0, h m^rho_{k+1})
+  const float4 *pr8;
 };
 
 // Behler-Parrinello model: symmetry-function parameters by value (read as
@@ -285,6 +289,7 @@ struct EAMTablesDev {
   float *phi_v32;
   float4 *pr32;
   dvec4 *pr64;
+  float4 *pr8;
 };
 
 // Centre of cell c along d.  Gather copies hold x - centre, so |p| <= h/2
