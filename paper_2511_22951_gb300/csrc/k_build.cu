@@ -780,15 +780,13 @@ __global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
     // latency overlaps the candidate gathers)
     uint4 na = make_uint4(0, 0, 0, 0), nb = na;
     if (n1 > 0) {
-      na = __ldcs(row);
-      nb = __ldcs(row + 1);
+      ld_group(row, na, nb);
     }
     for (int k0 = 0; k0 < n1; k0 += kGroup) {
       const uint4 a = na, b = nb;
       row += Nc * 2;
       if (k0 + kGroup < n1) {
-        na = __ldcs(row);
-        nb = __ldcs(row + 1);
+        ld_group(row, na, nb);
       }
       const uint32_t ea[4] = {a.x, a.y, a.z, a.w};
       const uint32_t eb[4] = {b.x, b.y, b.z, b.w};

@@ -65,15 +65,13 @@ __device__ __forceinline__ void lj_walk_packed(const Sys &s, const float4 *__res
   const float4 far = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
   uint4 na = make_uint4(0, 0, 0, 0), nb = na;
   if (kGroup * t < nn) {
-    na = __ldcs(row);
-    nb = __ldcs(row + 1);
+    ld_group(row, na, nb);
   }
   for (int k = kGroup * t; k < nn; k += kGroup * T) {
     const uint4 ga = na, gb = nb;
     row += gstride * T;
     if (k + kGroup * T < nn) {
-      na = __ldcs(row);
-      nb = __ldcs(row + 1);
+      ld_group(row, na, nb);
     }
     const uint32_t e[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
     const int m = nn - k;  // valid entries in this group

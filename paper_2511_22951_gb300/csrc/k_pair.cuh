@@ -261,19 +261,17 @@ __device__ __forceinline__ void walk(const uint32_t *__restrict__ nbr, size_t Nc
   const size_t gstride = Nc * 2;  // uint4 per group row
   const uint4 *__restrict__ row = reinterpret_cast<const uint4 *>(nbr) + (size_t)i * 2 +
                                   (size_t)t * gstride;
-  // the next group's two loads are issued before this group's pairs run, so
+  // the next group's load is issued before this group's pairs run, so
   // the list latency overlaps the neighbour gathers and the arithmetic
   uint4 na = make_uint4(0, 0, 0, 0), nb = na;
   if (kGroup * t < nn) {
-    na = __ldcs(row);
-    nb = __ldcs(row + 1);
+    ld_group(row, na, nb);
   }
   for (int k = kGroup * t; k < nn; k += kGroup * T) {
     const uint4 a = na, b = nb;
     row += gstride * T;
     if (k + kGroup * T < nn) {
-      na = __ldcs(row);
-      nb = __ldcs(row + 1);
+      ld_group(row, na, nb);
     }
     const uint32_t e[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
     const int m = nn - k;  // valid entries in this group

@@ -313,6 +313,17 @@ __host__ __device__ __forceinline__ uint32_t pack_nbr(int j, int sx, int sy, int
          ((uint32_t)(sz + 1) << 4);
 }
 __host__ __device__ __forceinline__ int nbr_j(uint32_t e) { return (int)(e >> 6); }
+
+#ifdef __CUDACC__
+// One ELL8 group (8 entries, a 32-byte sector) with one 256-bit streaming
+// load (new with sm_100): a warp's 32 groups are 1 KB contiguous, read as
+// whole sectors by one instruction instead of two 16-byte halves.
+__device__ __forceinline__ void ld_group(const uint4 *p, uint4 &a, uint4 &b) {
+  asm("ld.global.cs.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+      : "l"(p));
+}
+#endif
 __host__ __device__ __forceinline__ int nbr_s(uint32_t e, int d) {
   return (int)((e >> (2 * d)) & 3u) - 1;
 }
