@@ -30,12 +30,13 @@ namespace {
 
 using namespace pair;
 
-// FP64 passes: one 512-thread block per SM and up to 128 registers (the FP64
-// pair values need them; the 160 KB FP64 force-pass tables leave room for one
-// block anyway)
-template <class P>
+// FP64 passes and the energy passes (thermo and compute steps only): one
+// 512-thread block per SM and up to 128 registers (the FP64 pair values, and
+// the per-atom energy and virial sums, spill at 64; the 160 KB FP64 force-pass
+// tables leave room for one block anyway)
+template <class P, bool ENERGY = false>
 constexpr int eam_min_blocks() {
-  return sizeof(typename G<P>::R) == 4 ? 2 : 1;
+  return sizeof(typename G<P>::R) == 4 && !ENERGY ? 2 : 1;
 }
 
 template <class P, bool ENERGY, int T>
@@ -110,7 +111,8 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_rho(Sys s, EAMPara
 }
 
 template <class P, int MODE, bool ENERGY, int T>
-__global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_eam(Sys s, EAMParams ep, StepArgs a) {
+__global__ void __launch_bounds__(512, eam_min_blocks<P, ENERGY>()) k_eam(Sys s, EAMParams ep,
+                                                                       StepArgs a) {
   using GP = G<P>;
   using R = typename GP::R;
   using V = typename GP::V;
@@ -151,9 +153,11 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_eam(Sys s, EAMPara
       nn = min(s.nnbr[i], s.nmax);
     }
     Acc<R> fx, fy, fz;
-    // energy and virial sums in FP64 (ENERGY passes only: thermo and compute)
+    // energy and virial sums in FP64 (ENERGY passes only: thermo and compute),
+    // each fed by the block sums of four pairs in the pair precision
     double e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     R bx = 0, by = 0, bz = 0;
+    R be = 0, bw0 = 0, bw1 = 0, bw2 = 0, bw3 = 0, bw4 = 0, bw5 = 0;
     walk<T>(
         s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pgf + dbg_idx(s, j, Nc)); },
         [&](uint32_t ent, const V &pj) {
@@ -183,14 +187,14 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_eam(Sys s, EAMPara
             by += fr * dy;
             bz += fr * dz;
             if (ENERGY) {
-              e += 0.5 * (double)vphi;
+              be += vphi;
               const R hf = R(-0.5) * fr;
-              w0 += (double)(hf * dx * dx);
-              w1 += (double)(hf * dy * dy);
-              w2 += (double)(hf * dz * dz);
-              w3 += (double)(hf * dx * dy);
-              w4 += (double)(hf * dx * dz);
-              w5 += (double)(hf * dy * dz);
+              bw0 += hf * dx * dx;
+              bw1 += hf * dy * dy;
+              bw2 += hf * dz * dz;
+              bw3 += hf * dx * dy;
+              bw4 += hf * dx * dz;
+              bw5 += hf * dy * dz;
             }
           }
         },
@@ -199,6 +203,16 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_eam(Sys s, EAMPara
           fy.add(by);
           fz.add(bz);
           bx = by = bz = 0;
+          if (ENERGY) {
+            e += 0.5 * (double)be;
+            w0 += (double)bw0;
+            w1 += (double)bw1;
+            w2 += (double)bw2;
+            w3 += (double)bw3;
+            w4 += (double)bw4;
+            w5 += (double)bw5;
+            be = bw0 = bw1 = bw2 = bw3 = bw4 = bw5 = 0;
+          }
         });
     const R Fx = lanes_sum<T>(fx.getf()), Fy = lanes_sum<T>(fy.getf()),
             Fz = lanes_sum<T>(fz.getf());

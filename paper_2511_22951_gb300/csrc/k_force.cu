@@ -49,35 +49,70 @@ __global__ void __launch_bounds__(kBlk) k_kick_drift(Sys s, StepArgs a) {
 }
 
 // ---- deterministic per-replica sums (fixed order, no atomics) -----------------------
-constexpr int kRedThreads = 1024;
-__global__ void __launch_bounds__(kRedThreads) k_reduce(Sys s, int with_ke) {
+// Two passes: every block sums one chunk of kRedChunk atoms of one replica
+// (a fixed partition, so the result does not depend on the launch), then one
+// block per replica sums its chunks' partials in chunk order.  All SMs share
+// the first pass, so the sums of an 8.4M-atom system take a fraction of a
+// millisecond instead of one SM's tens of milliseconds.
+constexpr int kRedThreads = 256;
+constexpr int kRedTop = 1024;
+
+// the block's sums of acc[0..7] (fixed shuffle tree, then warps in order);
+// value c ends in thread c (c < 8)
+template <int NT>
+__device__ __forceinline__ double block_sum8(double (&acc)[8]) {
+  __shared__ double sh[8][NT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    double v = acc[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[c][wid] = v;
+  }
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 8)
+    for (int w = 0; w < NT / 32; ++w) t += sh[threadIdx.x][w];
+  return t;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_chunks(Sys s, int with_ke) {
   const int r = blockIdx.x;
   const Grid &g = s.grid[r];
-  const int a0 = g.atom_off;
   const int n = (s.n_rep == 1) ? s.st->N : g.n_atoms;
   const size_t Nc = s.N_cap;
+  for (int k = blockIdx.y; k < s.red_chunks; k += gridDim.y) {
+    const int q1 = min(n, (k + 1) * kRedChunk);
+    double acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = 0.0;
+    for (int q = k * kRedChunk + threadIdx.x; q < q1; q += kRedThreads) {
+      const int i = g.atom_off + q;
+      acc[0] += with_ke ? s.ka[i] : 0.0;
+      acc[1] += s.ea[i];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc[2 + c] += s.wa[c * Nc + i];
+    }
+    const double t = block_sum8<kRedThreads>(acc);
+    if (threadIdx.x < 8) s.red_part[((size_t)r * s.red_chunks + k) * 8 + threadIdx.x] = t;
+    __syncthreads();  // block_sum8's shared slots are reused by the next chunk
+  }
+}
+
+__global__ void __launch_bounds__(kRedTop) k_reduce_top(Sys s) {
+  const int r = blockIdx.x;
   double acc[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) acc[c] = 0.0;
-  for (int q = threadIdx.x; q < n; q += kRedThreads) {
-    const int i = a0 + q;
-    acc[0] += with_ke ? s.ka[i] : 0.0;
-    acc[1] += s.ea[i];
+  const double *p = s.red_part + (size_t)r * s.red_chunks * 8;
+  for (int k = threadIdx.x; k < s.red_chunks; k += kRedTop) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) acc[2 + c] += s.wa[c * Nc + i];
+    for (int c = 0; c < 8; ++c) acc[c] += p[(size_t)k * 8 + c];
   }
-  __shared__ double sh[kRedThreads];
-  for (int c = 0; c < 8; ++c) {
-    sh[threadIdx.x] = acc[c];
-    __syncthreads();
-    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) s.red[r * 9 + c] = sh[0];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) s.red[r * 9 + 8] = (double)n;
+  const double t = block_sum8<kRedTop>(acc);
+  if (threadIdx.x < 8) s.red[r * 9 + threadIdx.x] = t;
+  if (threadIdx.x == 0) s.red[r * 9 + 8] = (double)((s.n_rep == 1) ? s.st->N : s.grid[r].n_atoms);
 }
 
 // ---- state in / out in the caller's order -------------------------------------------
@@ -147,8 +182,11 @@ void launch_kick_drift(const Sys &s, int precision, StepArgs a, cudaStream_t st)
     k_kick_drift<Mixed><<<g, kBlk, 0, st>>>(s, a);
 }
 
-void launch_reduce(const Sys &s, int with_ke, cudaStream_t st) {
-  k_reduce<<<s.n_rep, kRedThreads, 0, st>>>(s, with_ke);
+int launch_reduce(const Sys &s, int with_ke, cudaStream_t st) {
+  k_reduce_chunks<<<dim3(s.n_rep, std::min(s.red_chunks, 65535)), kRedThreads, 0, st>>>(s,
+                                                                                      with_ke);
+  k_reduce_top<<<s.n_rep, kRedTop, 0, st>>>(s);
+  return 2;
 }
 
 

@@ -25,11 +25,12 @@ namespace {
 
 using namespace pair;
 
-// mixed: 4 blocks of 256 per SM (64 registers); FP64: 2 blocks (128 registers:
-// the FP64 pair values and sums need them)
-template <class P>
+// mixed: 4 blocks of 256 per SM (64 registers); FP64 and the energy passes
+// (thermo and compute steps only): 2 blocks (128 registers: the FP64 pair
+// values, and the per-atom energy and virial sums, spill at 64)
+template <class P, bool ENERGY>
 constexpr int lj_min_blocks() {
-  return sizeof(typename G<P>::R) == 4 ? 4 : 2;
+  return sizeof(typename G<P>::R) == 4 && !ENERGY ? 4 : 2;
 }
 
 // ---- the mixed path: two list entries per instruction ------------------------
@@ -82,6 +83,9 @@ __device__ __forceinline__ void lj_walk_packed(const Sys &s, const float4 *__res
       for (int u = 0; u < 4; ++u)
         q[u] = 4 * h + u < m ? __ldg(pg + dbg_idx(s, nbr_j(e[4 * h + u]), Nc)) : far;
       float2 bx = f2(0.f, 0.f), by = bx, bz = bx;
+      // ENERGY: FP32 sums of this block's four pair energies and virial
+      // terms, added to the FP64 per-atom sums once per block
+      float2 be = bx, bw0 = bx, bw1 = bx, bw2 = bx, bw3 = bx, bw4 = bx, bw5 = bx;
 #pragma unroll
       for (int pr = 0; pr < 2; ++pr) {
         const uint32_t ea = e[4 * h + 2 * pr], eb = e[4 * h + 2 * pr + 1];
@@ -113,33 +117,44 @@ __device__ __forceinline__ void lj_walk_packed(const Sys &s, const float4 *__res
         bx = __ffma2_rn(fr, dx, bx);
         by = __ffma2_rn(fr, dy, by);
         bz = __ffma2_rn(fr, dz, bz);
-        if (ENERGY) {  // energy and virial from the same pair values, FP64 sums
-#pragma unroll
-          for (int l = 0; l < 2; ++l) {
-            const float s6l = l ? s6.y : s6.x, frl = l ? fr.y : fr.x;
-            const float dxl = l ? dx.y : dx.x, dyl = l ? dy.y : dy.x, dzl = l ? dz.y : dz.x;
-            float v = lc.eps4 * (s6l * s6l - s6l) - lc.ush;
-            if (SHIFT == 2) v -= (sqrtf(l ? r2.y : r2.x) - lc.rcut) * lc.durc;
-            if (l ? inb : ina) esum += 0.5 * (double)v;
-            const float hf = -0.5f * frl;  // r_ij = -d
-            w[0] += (double)(hf * dxl * dxl);
-            w[1] += (double)(hf * dyl * dyl);
-            w[2] += (double)(hf * dzl * dzl);
-            w[3] += (double)(hf * dxl * dyl);
-            w[4] += (double)(hf * dxl * dzl);
-            w[5] += (double)(hf * dyl * dzl);
+        if (ENERGY) {  // energy and virial from the same pair values
+          float2 v = __ffma2_rn(f2(lc.eps4, lc.eps4), __ffma2_rn(s6, s6, f2(-s6.x, -s6.y)),
+                                f2(-lc.ush, -lc.ush));
+          if (SHIFT == 2) {
+            v.x -= (sqrtf(r2.x) - lc.rcut) * lc.durc;
+            v.y -= (sqrtf(r2.y) - lc.rcut) * lc.durc;
           }
+          v.x = ina ? v.x : 0.0f;
+          v.y = inb ? v.y : 0.0f;
+          be = __fadd2_rn(be, v);
+          const float2 hf = __fmul2_rn(f2(-0.5f, -0.5f), fr);  // r_ij = -d
+          const float2 hx_ = __fmul2_rn(hf, dx), hy_ = __fmul2_rn(hf, dy);
+          bw0 = __ffma2_rn(hx_, dx, bw0);
+          bw1 = __ffma2_rn(hy_, dy, bw1);
+          bw2 = __ffma2_rn(__fmul2_rn(hf, dz), dz, bw2);
+          bw3 = __ffma2_rn(hx_, dy, bw3);
+          bw4 = __ffma2_rn(hx_, dz, bw4);
+          bw5 = __ffma2_rn(hy_, dz, bw5);
         }
       }
       fx.add(bx.x + bx.y);
       fy.add(by.x + by.y);
       fz.add(bz.x + bz.y);
+      if (ENERGY) {
+        esum += (double)(0.5f * (be.x + be.y));
+        w[0] += (double)(bw0.x + bw0.y);
+        w[1] += (double)(bw1.x + bw1.y);
+        w[2] += (double)(bw2.x + bw2.y);
+        w[3] += (double)(bw3.x + bw3.y);
+        w[4] += (double)(bw4.x + bw4.y);
+        w[5] += (double)(bw5.x + bw5.y);
+      }
     }
   }
 }
 
 template <class P, int MODE, bool ENERGY, int SHIFT, int T>
-__global__ void __launch_bounds__(256, lj_min_blocks<P>()) k_lj(Sys s, LJParams lp, StepArgs a) {
+__global__ void __launch_bounds__(256, lj_min_blocks<P, ENERGY>()) k_lj(Sys s, LJParams lp, StepArgs a) {
   using GP = G<P>;
   using R = typename GP::R;
   using V = typename GP::V;

@@ -249,7 +249,7 @@ __device__ __forceinline__ void h_scaled(R &hx, R &hy, R &hz) {
 }
 
 // Walk the list of one atom with T lanes: lane t takes the groups of 8 list
-// words t, t + T, t + 2T, ...  A group comes in two 16-byte loads; its
+// words t, t + T, t + 2T, ...  A group comes in one 32-byte load; its
 // neighbour records are loaded four at a time before the four bodies run,
 // so each thread keeps several independent loads in flight.  `commit` runs
 // after every four pairs: the compensated per-atom sums take one block sum

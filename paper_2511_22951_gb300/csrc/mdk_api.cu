@@ -202,6 +202,15 @@ size_t layout(mdk_ctx *c, char *base) {
   s.grid = cv.take<Grid>(c->n_rep);
   s.st = cv.take<DevStatus>(1);
   s.red = cv.take<double>((size_t)9 * c->n_rep);
+  {
+    // chunks per replica for the first pass of the sums: a single replica
+    // may grow to N_cap atoms (window appends), batched replicas keep theirs
+    int64_t per = c->n_rep == 1 ? (int64_t)Nc : 1;
+    if (c->n_rep > 1)
+      for (const Grid &g : c->grids) per = std::max<int64_t>(per, g.n_atoms);
+    s.red_chunks = (int)std::max<int64_t>(1, (per + kRedChunk - 1) / kRedChunk);
+    s.red_part = cv.take<double>((size_t)8 * c->n_rep * s.red_chunks);
+  }
   c->thermo_ring = cv.take<double>((size_t)std::max(c->thermo_cap, 1) * c->n_rep * 10);
   // EAM tables: raw knots, (y, h m) FP64 and FP32 copies
   const int nr = c->pot == 2 ? c->eam.nr : 1, nrho = c->pot == 2 ? c->eam.nrho : 1;
@@ -1543,8 +1552,7 @@ int mdk_compute(mdk_ctx *c, double *E, double *F, double *virial, int on_device)
   Sys &s = c->sys;
   r = force_pass(c, kForceOnly, 1, 0.0);
   if (r) return r;
-  launch_reduce(s, 0, c->stream);
-  c->launches += 1;
+  c->launches += launch_reduce(s, 0, c->stream);
   MDK_CK(cudaPeekAtLastError());
   c->forces_valid = true;
   c->per_atom_valid = true;
@@ -1718,8 +1726,7 @@ int mdk_step(mdk_ctx *c, double dt, int64_t nsteps) {
     r = force_pass(c, last ? kFinal : kStep, thermo, dt);
     if (r) return r;
     if (thermo) {
-      launch_reduce(s, 1, c->stream);
-      c->launches += 2;
+      c->launches += launch_reduce(s, 1, c->stream) + 1;
       const int slot = (int)(c->thermo_written % std::max(c->thermo_cap, 1));
       k_thermo_store<<<1, std::max(32, ((c->n_rep + 31) / 32) * 32), 0, c->stream>>>(
           s, c->thermo_ring, slot, (double)gstep);

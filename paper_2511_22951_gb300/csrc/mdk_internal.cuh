@@ -130,6 +130,8 @@ struct Sys {
   Grid *grid;
   DevStatus *st;
   double *red;              // reductions: per replica [K, U, W0..W5, N]
+  double *red_part;         // per replica and chunk of kRedChunk atoms: the 8 partial sums
+  int red_chunks;           // chunks per replica (ceil of its largest atom count / kRedChunk)
   // list parameters
   double rns2;              // (rc + skin)^2
   float filt_lo, filt_hi;   // FP32 pre-filter band around rns2
@@ -304,6 +306,8 @@ __device__ __forceinline__ double cell_center(const Grid &g, int d, int c) {
 // entries with two 16-byte loads, a warp reads 1 KB contiguous, and the build
 // writes whole sectors (no partial-sector read-modify-write in L2).
 constexpr int kGroup = 8;
+// atoms per block of the first pass of the per-replica sums
+constexpr int kRedChunk = 8192;
 __host__ __device__ __forceinline__ size_t ell_index(int k, int i, size_t Nc) {
   return ((size_t)(k >> 3) * Nc + (size_t)i) * kGroup + (size_t)(k & 7);
 }
@@ -442,7 +446,8 @@ void launch_lj_half(const Sys &s, const LJParams &p, int precision, Mode mode, S
 void launch_eam(const Sys &s, const EAMParams &p, int precision, Mode mode, StepArgs a,
                 const LaunchCfg &cfg, cudaStream_t st);
 void launch_kick_drift(const Sys &s, int precision, StepArgs a, cudaStream_t st);
-void launch_reduce(const Sys &s, int with_ke, cudaStream_t st);
+// returns the number of kernels launched
+int launch_reduce(const Sys &s, int with_ke, cudaStream_t st);
 void launch_eam_prepare(const EAMParams &p, const double *phi, const double *rho,
                         const double *F, EAMTablesDev out, cudaStream_t st);
 void launch_load_state(const Sys &s, const double *x_aos, const double *v_aos,
