@@ -153,11 +153,12 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P, ENERGY>()) k_eam(Sys s,
       nn = min(s.nnbr[i], s.nmax);
     }
     Acc<R> fx, fy, fz;
-    // energy and virial sums in FP64 (ENERGY passes only: thermo and compute),
-    // each fed by the block sums of four pairs in the pair precision
-    double e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+    // energy and virial (ENERGY passes only: thermo and compute): block sums
+    // of four pairs, summed like the forces (mixed: compensated FP32), in FP64
+    // once per atom
     R bx = 0, by = 0, bz = 0;
     R be = 0, bw0 = 0, bw1 = 0, bw2 = 0, bw3 = 0, bw4 = 0, bw5 = 0;
+    Acc<R> ae, aw0, aw1, aw2, aw3, aw4, aw5;
     walk<T>(
         s.nbr, Nc, i, nn, tl.t, [&](uint32_t j) { return GP::ld(pgf + dbg_idx(s, j, Nc)); },
         [&](uint32_t ent, const V &pj) {
@@ -204,16 +205,18 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P, ENERGY>()) k_eam(Sys s,
           fz.add(bz);
           bx = by = bz = 0;
           if (ENERGY) {
-            e += 0.5 * (double)be;
-            w0 += (double)bw0;
-            w1 += (double)bw1;
-            w2 += (double)bw2;
-            w3 += (double)bw3;
-            w4 += (double)bw4;
-            w5 += (double)bw5;
+            ae.add(R(0.5) * be);
+            aw0.add(bw0);
+            aw1.add(bw1);
+            aw2.add(bw2);
+            aw3.add(bw3);
+            aw4.add(bw4);
+            aw5.add(bw5);
             be = bw0 = bw1 = bw2 = bw3 = bw4 = bw5 = 0;
           }
         });
+    const double e = ae.get(), w0 = aw0.get(), w1 = aw1.get(), w2 = aw2.get(), w3 = aw3.get(),
+                 w4 = aw4.get(), w5 = aw5.get();
     const R Fx = lanes_sum<T>(fx.getf()), Fy = lanes_sum<T>(fy.getf()),
             Fz = lanes_sum<T>(fz.getf());
     double E = 0, W0 = 0, W1 = 0, W2 = 0, W3 = 0, W4 = 0, W5 = 0;

@@ -25,12 +25,13 @@ namespace {
 
 using namespace pair;
 
-// mixed: 4 blocks of 256 per SM (64 registers); FP64 and the energy passes
-// (thermo and compute steps only): 2 blocks (128 registers: the FP64 pair
-// values, and the per-atom energy and virial sums, spill at 64)
-template <class P, bool ENERGY>
+// mixed: 4 blocks of 256 per SM (64 registers); its energy passes (thermo
+// and compute steps only) 3 blocks (80 registers: the per-atom energy and
+// virial sums spill at 64), 2 with the shifted-force terms; FP64: 2 blocks
+// (128 registers: the FP64 pair values need them)
+template <class P, bool ENERGY, int SHIFT>
 constexpr int lj_min_blocks() {
-  return sizeof(typename G<P>::R) == 4 && !ENERGY ? 4 : 2;
+  return sizeof(typename G<P>::R) == 4 ? (ENERGY ? (SHIFT == 2 ? 2 : 3) : 4) : 2;
 }
 
 // ---- the mixed path: two list entries per instruction ------------------------
@@ -64,6 +65,9 @@ __device__ __forceinline__ void lj_walk_packed(const Sys &s, const float4 *__res
   const float2 sig2 = f2(lc.sig2, lc.sig2), meps24 = f2(-lc.eps24, -lc.eps24);
   const float2 two = f2(2.0f, 2.0f), mone = f2(-1.0f, -1.0f);
   const float4 far = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+  // ENERGY: compensated FP32 sums of the block sums (as the forces), in FP64
+  // once per atom at the end
+  Acc<float> ae, aw[6];
   uint4 na = make_uint4(0, 0, 0, 0), nb = na;
   if (kGroup * t < nn) {
     ld_group(row, na, nb);
@@ -141,20 +145,25 @@ __device__ __forceinline__ void lj_walk_packed(const Sys &s, const float4 *__res
       fy.add(by.x + by.y);
       fz.add(bz.x + bz.y);
       if (ENERGY) {
-        esum += (double)(0.5f * (be.x + be.y));
-        w[0] += (double)(bw0.x + bw0.y);
-        w[1] += (double)(bw1.x + bw1.y);
-        w[2] += (double)(bw2.x + bw2.y);
-        w[3] += (double)(bw3.x + bw3.y);
-        w[4] += (double)(bw4.x + bw4.y);
-        w[5] += (double)(bw5.x + bw5.y);
+        ae.add(0.5f * (be.x + be.y));
+        aw[0].add(bw0.x + bw0.y);
+        aw[1].add(bw1.x + bw1.y);
+        aw[2].add(bw2.x + bw2.y);
+        aw[3].add(bw3.x + bw3.y);
+        aw[4].add(bw4.x + bw4.y);
+        aw[5].add(bw5.x + bw5.y);
       }
     }
+  }
+  if (ENERGY) {
+    esum += ae.get();
+#pragma unroll
+    for (int c = 0; c < 6; ++c) w[c] += aw[c].get();
   }
 }
 
 template <class P, int MODE, bool ENERGY, int SHIFT, int T>
-__global__ void __launch_bounds__(256, lj_min_blocks<P, ENERGY>()) k_lj(Sys s, LJParams lp, StepArgs a) {
+__global__ void __launch_bounds__(256, lj_min_blocks<P, ENERGY, SHIFT>()) k_lj(Sys s, LJParams lp, StepArgs a) {
   using GP = G<P>;
   using R = typename GP::R;
   using V = typename GP::V;
