@@ -1,5 +1,5 @@
-"""How the mixed path sums its forces, measured on the 8,388,608-atom argon
-workload (LJ, 80 K, thermalised for 300 steps).
+"""How the mixed path sums its forces (and its energies and virials), measured
+on the 8,388,608-atom argon workload (LJ, 80 K, thermalised for 300 steps).
 
 The mixed full-list kernels sum each atom's FP32 pair forces with a
 compensated (Kahan) FP32 sum over blocks of four pairs.  The mixed half-list
@@ -41,9 +41,9 @@ def test_compensated_fp32_force_sum_equals_exact_sum(mdk, ora):
     ctx.step(wl.dt, 300)
     ctx.build_neighbors(wl.rc, wl.skin)     # lists and cells of the current positions
     x, _ = ctx.get_state()
-    _, F_kahan, _ = ctx.compute()           # full lists: compensated FP32 sums
+    E_kahan, F_kahan, W_kahan = ctx.compute()   # full lists: compensated FP32 sums
     ctx.set_list_kind("half")               # rebuilt at the same positions: same cells
-    _, F_exact, _ = ctx.compute()           # half lists: 64-bit fixed-point sums
+    E_exact, F_exact, W_exact = ctx.compute()   # half lists: 64-bit fixed-point sums
     scale = np.sqrt(np.mean(F_exact ** 2))
     d = F_kahan - F_exact
     rel_rms = np.sqrt(np.mean(d ** 2)) / scale
@@ -54,6 +54,17 @@ def test_compensated_fp32_force_sum_equals_exact_sum(mdk, ora):
     # the rest compensated: ~1e-7 of the RMS force expected, bar 1e-5
     assert rel_rms <= 1e-6
     assert rel_max <= 1e-5
+    # energy and virial: the full-list pass sums each atom's four-pair FP32
+    # block sums with compensation too (the pair energies differ from the
+    # half-list ones by at most an FP32 rounding each), so the totals agree
+    # far below the mixed energy bar (1e-6 of |E|)
+    E_kahan, E_exact = float(np.sum(E_kahan)), float(np.sum(E_exact))
+    W_kahan, W_exact = np.asarray(W_kahan, float).ravel(), np.asarray(W_exact, float).ravel()
+    dE = abs(E_kahan - E_exact) / abs(E_exact)
+    dW = np.max(np.abs(W_kahan - W_exact)) / np.max(np.abs(W_exact))
+    print(f"energy {dE:.3e}, virial {dW:.3e} (relative)")
+    assert dE <= 1e-9
+    assert dW <= 1e-8
     # and both against the FP64 oracle on sampled atoms: the pair arithmetic,
     # not the summation, sets the mixed error
     sel = np.random.default_rng(3).choice(s.n, 16, replace=False)
