@@ -359,7 +359,9 @@ int mdk_get_counters(mdk_ctx *ctx, int64_t *n_builds, int64_t *n_steps);
  * previous setting stays), the workspace grows by the outer list and the
  * positions of the last full build (mdk_workspace_size), and the next call
  * that needs the list rebuilds it.  Other errors: MDK_ERR_BAD_ARG for a
- * negative or non-finite value or one not above the skin.
+ * negative or non-finite value, one not above the skin, or one above
+ * 10 (rc + skin) (the FP32 pre-filter's error bound, proportional to the
+ * cell size, stays far inside its band below that).
  */
 int mdk_set_outer_skin(mdk_ctx *ctx, double skin_outer);
 

@@ -99,6 +99,8 @@ struct mdk_ctx {
   uint64_t gkey[2] = {0, 0};
   cudaStream_t body_stream = nullptr;  // captures the conditional rebuild bodies
   int64_t graph_kernels = 0;  // kernels of one graph that run at every replay
+  double *ctr_dev = nullptr;     // cell-centre tables in the workspace
+  std::vector<double> ctr_host;  // their values (kept until the upload completes)
   int64_t body_kernels = 0;   // kernels of one conditional rebuild body
   long long graph_builds0 = 0;  // device count of in-graph builds at mdk_profile
   // moving window
@@ -200,6 +202,21 @@ size_t layout(mdk_ctx *c, char *base) {
   s.cell_of = cv.take<int32_t>(Nc);
   s.order = cv.take<int32_t>(Nc);
   s.grid = cv.take<Grid>(c->n_rep);
+  {
+    // cell-centre tables: per replica, nc[0] + nc[1] + nc[2] doubles
+    size_t n_ctr = 0;
+    for (const Grid &g : c->grids) n_ctr += (size_t)g.nc[0] + g.nc[1] + g.nc[2];
+    double *ctr = cv.take<double>(std::max<size_t>(n_ctr, 1));
+    c->ctr_dev = ctr;
+    if (base) {
+      size_t off = 0;
+      for (Grid &g : c->grids)
+        for (int d = 0; d < 3; ++d) {
+          g.ctr[d] = ctr + off;
+          off += (size_t)g.nc[d];
+        }
+    }
+  }
   s.st = cv.take<DevStatus>(1);
   s.red = cv.take<double>((size_t)9 * c->n_rep);
   {
@@ -1129,6 +1146,16 @@ int mdk_set_workspace(mdk_ctx *c, void *dev_ptr, size_t bytes) {
                            cudaMemcpyHostToDevice, c->stream));
   MDK_CK(cudaMemcpyAsync(s.grid, c->grids.data(), sizeof(Grid) * c->n_rep,
                          cudaMemcpyHostToDevice, c->stream));
+  {
+    // the cell centres, with the expression the kernels used to evaluate
+    c->ctr_host.clear();
+    for (const Grid &g : c->grids)
+      for (int d = 0; d < 3; ++d)
+        for (int q = 0; q < g.nc[d]; ++q) c->ctr_host.push_back(std::fma((double)q, g.h[d], g.lo_c[d]));
+    if (!c->ctr_host.empty())
+      MDK_CK(cudaMemcpyAsync(c->ctr_dev, c->ctr_host.data(), sizeof(double) * c->ctr_host.size(),
+                             cudaMemcpyHostToDevice, c->stream));
+  }
   if (c->N > 0)
     MDK_CK(cudaMemcpyAsync(s.info0, c->info0.data(), sizeof(uint32_t) * c->N,
                            cudaMemcpyHostToDevice, c->stream));
@@ -1758,6 +1785,9 @@ int mdk_set_outer_skin(mdk_ctx *c, double skin_outer) {
   if (check_ctx(c) || !(skin_outer >= 0.0) || !std::isfinite(skin_outer)) return MDK_ERR_BAD_ARG;
   if (!c->planned) return MDK_ERR_ORDER;
   if (skin_outer != 0.0 && !(skin_outer > c->skin)) return MDK_ERR_BAD_ARG;
+  // the pre-filter band (1e-4 of r^2) holds FP32 offsets of cells up to
+  // ~100 r_ns; refuse outer cells beyond a tenth of that
+  if (skin_outer > 10.0 * (c->rc_list + c->skin)) return MDK_ERR_BAD_ARG;
   const int old_nmax = c->nmax, old_cells = c->n_cells, old_nmax1 = c->nmax1;
   const double keep = c->skin_outer;
   c->skin_outer = skin_outer;

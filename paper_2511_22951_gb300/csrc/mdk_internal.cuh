@@ -97,6 +97,9 @@ struct Grid {
   int cell_off;   // first global cell id of this replica
   int atom_off;   // first atom of this replica (atoms stay grouped by replica)
   int n_atoms;
+  // cell centres along each dimension, fma(c, h, lo_c) for c < nc (device
+  // memory in the workspace, filled when the workspace is set)
+  const double *ctr[3];
 };
 
 struct Sys {
@@ -294,11 +297,13 @@ struct EAMTablesDev {
   float4 *pr8;
 };
 
-// Centre of cell c along d.  Gather copies hold x - centre, so |p| <= h/2
-// right after a build (h/2 + skin/2 later); the build and every step use
-// this one expression, so the offsets of one list lifetime are consistent.
+// Centre of cell c along d, fma(c, h, lo_c), read from the grid's table
+// (GB300's FP64 pipe is slow; a cached load replaces the conversion and the
+// FMA).  Gather copies hold x - centre, so |p| <= h/2 right after a build
+// (h/2 + skin/2 later); the build and every step read the same table, so the
+// offsets of one list lifetime are consistent.
 __device__ __forceinline__ double cell_center(const Grid &g, int d, int c) {
-  return fma((double)c, g.h[d], g.lo_c[d]);
+  return __ldg(g.ctr[d] + c);
 }
 
 // Verlet-list layout: entries in groups of 8 per atom; group g of atom i is

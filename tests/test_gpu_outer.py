@@ -173,7 +173,8 @@ def test_outer_skin_arguments(mdk):
     ctx = mdk.Context(lo, hi, [1, 1, 1], np.full(n, W.MASS_AR), "mixed")
     ctx.set_potential_lj(W.LJ_AR.eps, W.LJ_AR.sigma, W.LJ_AR.rc, 1)
     ctx.plan(W.LJ_AR.rc, 0.3)
-    for bad in (0.3, 0.1, -1.0, float("nan")):
+    # not above the skin, negative, NaN, beyond 10 (rc + skin)
+    for bad in (0.3, 0.1, -1.0, float("nan"), 10.0 * (W.LJ_AR.rc + 0.3) + 1.0):
         with pytest.raises(mdk.MDKError):
             ctx.set_outer_skin(bad)
     ctx.set_outer_skin(1.2)
