@@ -529,9 +529,10 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s, ListOut lo_) {
     auto flush = [&](int grp, int fill) {
       if (grp >= ngroups) return;
       const int h = (grp & 1) * kGroup;
+      const uint32_t pad = pad_entry(Nc);
       uint32_t w[kGroup];
 #pragma unroll
-      for (int q = 0; q < kGroup; ++q) w[q] = q < fill ? stage[h + q][tx] : 0u;
+      for (int q = 0; q < kGroup; ++q) w[q] = q < fill ? stage[h + q][tx] : pad;
       uint4 *o = reinterpret_cast<uint4 *>(lo_.nbr) + ((size_t)grp * Nc + i) * 2;
       o[0] = make_uint4(w[0], w[1], w[2], w[3]);
       o[1] = make_uint4(w[4], w[5], w[6], w[7]);
@@ -708,9 +709,10 @@ __global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
     auto flush = [&](int grp, int fill) {
       if (grp >= ngroups) return;
       const int h = (grp & 1) * kGroup;
+      const uint32_t pad = pad_entry(Nc);
       uint32_t w[kGroup];
 #pragma unroll
-      for (int q = 0; q < kGroup; ++q) w[q] = q < fill ? stage[h + q][tx] : 0u;
+      for (int q = 0; q < kGroup; ++q) w[q] = q < fill ? stage[h + q][tx] : pad;
       uint4 *o = reinterpret_cast<uint4 *>(s.nbr) + ((size_t)grp * Nc + i) * 2;
       o[0] = make_uint4(w[0], w[1], w[2], w[3]);
       o[1] = make_uint4(w[4], w[5], w[6], w[7]);

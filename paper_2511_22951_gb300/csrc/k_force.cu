@@ -190,6 +190,23 @@ int launch_reduce(const Sys &s, int with_ke, cudaStream_t st) {
 }
 
 
+namespace {
+template <class P>
+__global__ void k_init_far(Sys s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const size_t Nc = s.N_cap;
+  for (int b = 0; b < 2; ++b)
+    reinterpret_cast<typename P::vec4 *>(s.pg[b])[Nc] = P::make(1e18, 1e18, 1e18, 0u);
+}
+}  // namespace
+
+void launch_init_far(const Sys &s, int precision, cudaStream_t st) {
+  if (precision == 0)
+    k_init_far<Fp64><<<1, 32, 0, st>>>(s);
+  else
+    k_init_far<Mixed><<<1, 32, 0, st>>>(s);
+}
+
 void launch_load_state(const Sys &s, const double *x, const double *v, int precision,
                        int target_pg, cudaStream_t st) {
   const int g = nblk(s.N_cap > 0 ? s.N_cap : 1, kBlk);

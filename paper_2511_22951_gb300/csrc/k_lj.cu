@@ -40,10 +40,11 @@ constexpr int lj_min_blocks() {
 // floating-point instruction of the pair vector, the distance, the LJ force
 // and the accumulation; the issue slots saved go to the gathers and the list
 // decoding.  Each lane's arithmetic is the scalar path's (same roundings, FMA
-// where that path contracts).  Entries past the list end read a far-away
-// record (r^2 ~ 1e36 > rc^2), so the cutoff test is the only mask.  ENERGY
-// passes take the same walk (identical forces) and add the pair energies and
-// virials in FP64.
+// where that path contracts).  Entries past the list end (pad_entry) read a
+// far-away record (r^2 ~ 1e36 > rc^2), so the cutoff test is the only mask.
+// ENERGY passes take the same walk (identical forces) and sum the pair
+// energies and virials as the forces (block sums of four, compensated across
+// blocks, FP64 once per atom).
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 template <int T, int SHIFT, bool ENERGY>
@@ -64,7 +65,6 @@ __device__ __forceinline__ void lj_walk_packed(const Sys &s, const float4 *__res
                k2 = f2(-8388624.0f, -8388624.0f);
   const float2 sig2 = f2(lc.sig2, lc.sig2), meps24 = f2(-lc.eps24, -lc.eps24);
   const float2 two = f2(2.0f, 2.0f), mone = f2(-1.0f, -1.0f);
-  const float4 far = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
   // ENERGY: compensated FP32 sums of the block sums (as the forces), in FP64
   // once per atom at the end
   Acc<float> ae, aw[6];
@@ -79,13 +79,13 @@ __device__ __forceinline__ void lj_walk_packed(const Sys &s, const float4 *__res
       ld_group(row, na, nb);
     }
     const uint32_t e[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
-    const int m = nn - k;  // valid entries in this group
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
+      // whole groups: the slots past the list's length hold pad_entry, whose
+      // record lies 1e18 A away (r^2 ~ 1e36 > rc^2)
       float4 q[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        q[u] = 4 * h + u < m ? __ldg(pg + dbg_idx(s, nbr_j(e[4 * h + u]), Nc)) : far;
+      for (int u = 0; u < 4; ++u) q[u] = __ldg(pg + dbg_idx(s, nbr_j(e[4 * h + u]), Nc + 1));
       float2 bx = f2(0.f, 0.f), by = bx, bz = bx;
       // ENERGY: FP32 sums of this block's four pair energies and virial
       // terms, added to the FP64 per-atom sums once per block

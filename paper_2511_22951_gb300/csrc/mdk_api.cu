@@ -177,8 +177,8 @@ size_t layout(mdk_ctx *c, char *base) {
   s.tmpi = cv.take<int32_t>(Nc);
   s.pf = cv.take<float4>(Nc);
   const size_t gsz = c->precision == MDK_FP64 ? 32 : 16;
-  s.pg[0] = cv.take<char>(gsz * Nc);
-  s.pg[1] = cv.take<char>(gsz * Nc);
+  s.pg[0] = cv.take<char>(gsz * (Nc + 1));  // + the far record (pad_entry)
+  s.pg[1] = cv.take<char>(gsz * (Nc + 1));
   s.pgF = cv.take<char>(gsz * (c->pot == 2 ? Nc : 1));
   s.nnbr = cv.take<int32_t>(Nc);
   s.nbr = cv.take<uint32_t>((size_t)std::max(c->nmax, c->nmax_grow) * Nc);
@@ -1137,6 +1137,7 @@ int mdk_set_workspace(mdk_ctx *c, void *dev_ptr, size_t bytes) {
   fill_sys_params(c);
   Sys &s = c->sys;
   MDK_CK(cudaMemsetAsync(s.st, 0, sizeof(DevStatus), c->stream));
+  launch_init_far(s, c->precision, c->stream);
   MDK_CK(cudaMemsetAsync(s.cell_cnt, 0, sizeof(int32_t) * (c->n_cells + 1), c->stream));
   MDK_CK(cudaMemsetAsync(s.hacc, 0, sizeof(long long) * 10 * (size_t)std::max<int64_t>(c->N_cap, 1),
                          c->stream));

@@ -323,6 +323,14 @@ __host__ __device__ __forceinline__ uint32_t pack_nbr(int j, int sx, int sy, int
 }
 __host__ __device__ __forceinline__ int nbr_j(uint32_t e) { return (int)(e >> 6); }
 
+// The slots of a list's last group past its length hold this entry: atom
+// index N_cap (a record of the gather copies kept 1e18 A away, past the last
+// atom) with a zero stencil offset, so a walk can read whole groups without
+// bounds tests; no pair with it is ever inside a cutoff.
+__host__ __device__ __forceinline__ uint32_t pad_entry(size_t n_cap) {
+  return 21u | ((uint32_t)n_cap << 6);
+}
+
 #ifdef __CUDACC__
 // One ELL8 group (8 entries, a 32-byte sector) with one 256-bit streaming
 // load (new with sm_100): a warp's 32 groups are 1 KB contiguous, read as
@@ -455,6 +463,8 @@ void launch_kick_drift(const Sys &s, int precision, StepArgs a, cudaStream_t st)
 int launch_reduce(const Sys &s, int with_ke, cudaStream_t st);
 void launch_eam_prepare(const EAMParams &p, const double *phi, const double *rho,
                         const double *F, EAMTablesDev out, cudaStream_t st);
+// the far records at index N_cap of both gather copies (see pad_entry)
+void launch_init_far(const Sys &s, int precision, cudaStream_t st);
 void launch_load_state(const Sys &s, const double *x_aos, const double *v_aos,
                        int precision, int target_pg, cudaStream_t st);
 void launch_store_state(const Sys &s, double *x_aos, double *v_aos, cudaStream_t st);
