@@ -133,7 +133,7 @@ TRAFFIC = {
         "bytes_per_atom": 464.9,
         "neighbors_per_atom": 78.0,
         "threads_per_atom": 1,
-        "sources_sha256": "06228fce4e6fcff7d877dc956809c6a437e43693373b6e037685fcbb25966fec",
+        "sources_sha256": "ed8416191c168ed686fe36cee2b382d9f087723d5f14cf7021542bd7dee4524b",
         "capture": "k_lj<Mixed, kStep, T=1>, 3 launches on 2,048,000 atoms (80^3 FCC cells, "
                    "the same lattice and 78 neighbours per atom): dram__bytes_read.sum + "
                    "dram__bytes_write.sum = 952.2 MB per launch; per-atom traffic does not "
@@ -889,13 +889,22 @@ def main():
         xs.numpy()[:] = xg
         vs.numpy()[:] = vg
         E = np.zeros(len(wl.systems))  # mdk_compute writes one energy per replica
+
+        def e2e_call():
+            ctx.lib.mdk_set_state(ctx.h, mdk._P(xs.data_ptr()), mdk._P(vs.data_ptr()), 0)
+            ctx.lib.mdk_build_neighbors(ctx.h, wl.rc, wl.skin)
+            ctx.lib.mdk_step(ctx.h, wl.dt, args.steps)
+            ctx.lib.mdk_get_state(ctx.h, mdk._P(xs.data_ptr()), mdk._P(vs.data_ptr()), 0)
+            ctx.lib.mdk_compute(ctx.h, mdk._ptr(E), None, None, 0)
+
+        # one untimed call first: the first transfers from freshly pinned
+        # buffers pay one-time mapping costs (~15 ms on 400 MB)
+        e2e_call()
+        xs.numpy()[:] = xg
+        vs.numpy()[:] = vg
         barrier()
         t0 = time.perf_counter()
-        ctx.lib.mdk_set_state(ctx.h, mdk._P(xs.data_ptr()), mdk._P(vs.data_ptr()), 0)
-        ctx.lib.mdk_build_neighbors(ctx.h, wl.rc, wl.skin)
-        ctx.lib.mdk_step(ctx.h, wl.dt, args.steps)
-        ctx.lib.mdk_get_state(ctx.h, mdk._P(xs.data_ptr()), mdk._P(vs.data_ptr()), 0)
-        ctx.lib.mdk_compute(ctx.h, mdk._ptr(E), None, None, 0)
+        e2e_call()
         barrier()
         t = time.perf_counter() - t0
         ctx.check()

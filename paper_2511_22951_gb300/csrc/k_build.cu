@@ -742,12 +742,13 @@ __global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
       return __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
     };
     // four candidates at a time (as k_build's blocks of four)
-    auto block4 = [&](const uint32_t *e, const int k0) {
+    auto block4 = [&](const uint32_t *e) {
       const int before = count;
+      // whole groups: slots past n1 hold pad_entry, whose record (pf[N_cap])
+      // lies 1e18 A away and fails the pre-filter outright
       float4 pj[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        pj[u] = __ldg(s.pf + (k0 + u < n1 ? dbg_idx(s, nbr_j(e[u]), Nc, i) : i));
+      for (int u = 0; u < 4; ++u) pj[u] = __ldg(s.pf + dbg_idx(s, nbr_j(e[u]), Nc + 1, i));
       const float2 r01 = r2pair(e[0], e[1], pj[0], pj[1]);
       const float2 r23 = r2pair(e[2], e[3], pj[2], pj[3]);
       const float r2v[4] = {r01.x, r01.y, r23.x, r23.y};
@@ -757,7 +758,7 @@ __global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
         const uint32_t code = e[u];
         const float r2f = r2v[u];
         // lexicographically positive stencil offset <=> 6-bit code > 21
-        const bool ok = k0 + u < n1 && (!HALF || half_keep(i, nbr_j(code), (code & 63u) > 21u));
+        const bool ok = !HALF || half_keep(i, nbr_j(code), (code & 63u) > 21u);
         const bool acc = ok && r2f < lo_thr;
         band = band || (ok && !acc && !(r2f > hi_thr));
         stage[count & 15][tx] = code;  // kept only if accepted
@@ -769,7 +770,7 @@ __global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
         for (int u = 0; u < 4; ++u) {
           const uint32_t code = e[u];
           const float r2f = r2v[u];
-          const bool ok = k0 + u < n1 && (!HALF || half_keep(i, nbr_j(code), (code & 63u) > 21u));
+          const bool ok = !HALF || half_keep(i, nbr_j(code), (code & 63u) > 21u);
           bool acc = ok && r2f < lo_thr;
           if (ok && !acc && !(r2f > hi_thr)) acc = exact_pair(s, g, i, code, c0, c1, c2, rns2);
           stage[count & 15][tx] = code;
@@ -792,8 +793,8 @@ __global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
       }
       const uint32_t ea[4] = {a.x, a.y, a.z, a.w};
       const uint32_t eb[4] = {b.x, b.y, b.z, b.w};
-      block4(ea, k0);
-      if (k0 + 4 < n1) block4(eb, k0 + 4);
+      block4(ea);
+      block4(eb);
     }
     if (count & 7) flush(count >> 3, count & 7);
     s.nnbr[i] = count;

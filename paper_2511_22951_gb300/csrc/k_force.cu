@@ -197,6 +197,7 @@ __global__ void k_init_far(Sys s) {
   const size_t Nc = s.N_cap;
   for (int b = 0; b < 2; ++b)
     reinterpret_cast<typename P::vec4 *>(s.pg[b])[Nc] = P::make(1e18, 1e18, 1e18, 0u);
+  s.pf[Nc] = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
 }
 }  // namespace
 

@@ -175,7 +175,7 @@ size_t layout(mdk_ctx *c, char *base) {
   s.tmpu = cv.take<uint32_t>(2 * Nc);
   s.id = cv.take<int32_t>(Nc);
   s.tmpi = cv.take<int32_t>(Nc);
-  s.pf = cv.take<float4>(Nc);
+  s.pf = cv.take<float4>(Nc + 1);  // + the far record (pad_entry)
   const size_t gsz = c->precision == MDK_FP64 ? 32 : 16;
   s.pg[0] = cv.take<char>(gsz * (Nc + 1));  // + the far record (pad_entry)
   s.pg[1] = cv.take<char>(gsz * (Nc + 1));
