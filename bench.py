@@ -133,7 +133,7 @@ TRAFFIC = {
         "bytes_per_atom": 464.9,
         "neighbors_per_atom": 78.0,
         "threads_per_atom": 1,
-        "sources_sha256": "ed8416191c168ed686fe36cee2b382d9f087723d5f14cf7021542bd7dee4524b",
+        "sources_sha256": "1991ab6b4e4c5a89a5962bddc4934012faf9ba79b7cce900bb62a3c309d36792",
         "capture": "k_lj<Mixed, kStep, T=1>, 3 launches on 2,048,000 atoms (80^3 FCC cells, "
                    "the same lattice and 78 neighbours per atom): dram__bytes_read.sum + "
                    "dram__bytes_write.sum = 952.2 MB per launch; per-atom traffic does not "

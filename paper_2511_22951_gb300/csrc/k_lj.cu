@@ -193,7 +193,9 @@ __global__ void __launch_bounds__(256, lj_min_blocks<P, ENERGY, SHIFT>()) k_lj(S
       nn = min(s.nnbr[i], s.nmax);
     }
     Acc<R> fx, fy, fz;
-    // energy and virial sums in FP64 (ENERGY passes only: thermo and compute)
+    // per-atom energy and virial (ENERGY passes only: thermo and compute):
+    // FP64 sums on the FP64 path, the packed walk's compensated sums (in
+    // FP64 once per atom) on the mixed path
     double e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     R bx = 0, by = 0, bz = 0;  // block sums of four pairs
     if constexpr (sizeof(R) == 4) {
