@@ -14,8 +14,11 @@ one-level lists); the same trigger and the same lists either way.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config C] [--impl reference]
 
-The default run also reports, outside the timed region: the same workload on
-the FP64 path (`fp64_path`); the NVE drift of the mixed path over 10^4 steps and
+The default run also reports, outside the timed region: `e2e`, the same
+metric through the C ABI from pinned host buffers (upload of x and v, a list
+build, the steps, download of x and v, mdk_compute for E; timed on the host
+around the second such call, the first warming the buffers); the same workload
+on the FP64 path (`fp64_path`); the NVE drift of the mixed path over 10^4 steps and
 of the FP64 path over 2000 steps, each with its own throughput (`drift`); a
 1000-step steady-state segment with its list and full builds
 (`steady_state`); and the metric's EAM half (`eam`): the Cu-like cold-curve
