@@ -549,15 +549,17 @@ __device__ __forceinline__ void langevin_f(const Sys &s, int i, uint32_t inf, fl
 __device__ __forceinline__ void drift32(const Sys &s, const StepArgs &a, int i, uint32_t inf,
                                         double vx, double vy, double vz) {
   const size_t Nc = s.N_cap;
-  const double x = s.x[i] + a.dt * vx;
-  const double y = s.x[Nc + i] + a.dt * vy;
-  const double z = s.x[2 * Nc + i] + a.dt * vz;
-  s.x[i] = x;
-  s.x[Nc + i] = y;
-  s.x[2 * Nc + i] = z;
-  s.v[i] = vx;
-  s.v[Nc + i] = vy;
-  s.v[2 * Nc + i] = vz;
+  // the state streams through once per step: evict-first loads and stores
+  // leave L1 to the neighbour records
+  const double x = __ldcs(s.x + i) + a.dt * vx;
+  const double y = __ldcs(s.x + Nc + i) + a.dt * vy;
+  const double z = __ldcs(s.x + 2 * Nc + i) + a.dt * vz;
+  __stcs(s.x + i, x);
+  __stcs(s.x + Nc + i, y);
+  __stcs(s.x + 2 * Nc + i, z);
+  __stcs(s.v + i, vx);
+  __stcs(s.v + Nc + i, vy);
+  __stcs(s.v + 2 * Nc + i, vz);
   const Grid &g = s.grid[inf >> 8];
   const uint32_t cc = s.cellc[i];
   const float px = (float)(x - cell_center(g, 0, cell_coord(cc, 0)));
@@ -565,7 +567,7 @@ __device__ __forceinline__ void drift32(const Sys &s, const StepArgs &a, int i, 
   const float pz = (float)(z - cell_center(g, 2, cell_coord(cc, 2)));
   bool bad, trig;
   if (!(inf & kInfoFar)) {
-    const float4 q = s.pf[i];  // the build-time offset in the same cell
+    const float4 q = __ldcs(s.pf + i);  // the build-time offset in the same cell
     const float ex = px - q.x, ey = py - q.y, ez = pz - q.z;
     const float d2 = ex * ex + ey * ey + ez * ez;
     bad = !isfinite(d2);
@@ -605,7 +607,7 @@ __device__ __forceinline__ void epilogue32(const Sys &s, const StepArgs &a, int 
   if ((s.n_lang > 0 || s.lang_rep_on) && !piston) langevin_f(s, i, inf, Fx, Fy, Fz);
   const double dx = kick32(s, a, type, Fx), dy = kick32(s, a, type, Fy),
                dz = kick32(s, a, type, Fz);
-  double vx = s.v[i], vy = s.v[Nc + i], vz = s.v[2 * Nc + i];
+  double vx = __ldcs(s.v + i), vy = __ldcs(s.v + Nc + i), vz = __ldcs(s.v + 2 * Nc + i);
   if (piston) {
     vx = s.u_p;
     vy = 0.0;
