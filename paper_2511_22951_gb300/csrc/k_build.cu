@@ -534,8 +534,10 @@ __global__ void __launch_bounds__(kBlk) k_build(Sys s, ListOut lo_) {
 #pragma unroll
       for (int q = 0; q < kGroup; ++q) w[q] = q < fill ? stage[h + q][tx] : pad;
       uint4 *o = reinterpret_cast<uint4 *>(lo_.nbr) + ((size_t)grp * Nc + i) * 2;
-      o[0] = make_uint4(w[0], w[1], w[2], w[3]);
-      o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+      // lists are written once per build and read by the next pass from
+      // HBM: evict-first stores keep L2 for the records the builds gather
+      __stcs(o, make_uint4(w[0], w[1], w[2], w[3]));
+      __stcs(o + 1, make_uint4(w[4], w[5], w[6], w[7]));
     };
     for (int t = 0; t < 27; ++t) {
       const int sx = t % 3 - 1, sy = (t / 3) % 3 - 1, sz = t / 9 - 1;
@@ -714,8 +716,10 @@ __global__ void __launch_bounds__(kBlk) k_build_filter(Sys s) {
 #pragma unroll
       for (int q = 0; q < kGroup; ++q) w[q] = q < fill ? stage[h + q][tx] : pad;
       uint4 *o = reinterpret_cast<uint4 *>(s.nbr) + ((size_t)grp * Nc + i) * 2;
-      o[0] = make_uint4(w[0], w[1], w[2], w[3]);
-      o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+      // lists are written once per build and read by the next pass from
+      // HBM: evict-first stores keep L2 for the records the builds gather
+      __stcs(o, make_uint4(w[0], w[1], w[2], w[3]));
+      __stcs(o + 1, make_uint4(w[4], w[5], w[6], w[7]));
     };
     const uint4 *row = reinterpret_cast<const uint4 *>(s.nbr1) + (size_t)i * 2;
     // r^2 (FP32) of two candidates at once with the packed FP32 instructions:

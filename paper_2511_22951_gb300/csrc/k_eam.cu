@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P>()) k_rho(Sys s, EAMPara
     // F(rho_i) and F'(rho_i) in FP64 (once per atom)
     double Fv, dF;
     embed_fp64(s, ep, rho_i, Fv, dF);
-    s.rho[i] = rho_i;
-    ((R *)s.fp)[i] = (R)dF;
+    __stcs(s.rho + i, rho_i);  // per-atom results: streamed
+    __stcs((R *)s.fp + i, (R)dF);
     GP::st_fp((V *)s.pgF + i, pi, dF);
     if (ENERGY) s.ea[i] = Fv;
   }
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(512, eam_min_blocks<P, ENERGY>()) k_eam(Sys s,
       inf = GP::info(pi);
       GP::h(s.grid[inf >> 8], hx, hy, hz);
       h_scaled(hx, hy, hz);  // for s_scaled
-      fpi = fpa[i];
+      fpi = __ldcs(fpa + i);
       nn = min(s.nnbr[i], s.nmax);
     }
     Acc<R> fx, fy, fz;
